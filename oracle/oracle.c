@@ -1,0 +1,526 @@
+/*
+ * FP64 CPU oracle for real-space grid integration with numeric atom-centred orbitals.
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is compiled into liboracle.so and is called by the
+ * tests, by the package's smoke check and by the benchmark's CPU-baseline leg. The CUDA
+ * library never includes, links or calls it, and it shares no code with that library.
+ *
+ * What it computes (all in IEEE FP64, compiled with -ffp-contract=off, no fast-math):
+ *   - basis functions phi_i(r) = R_f(|r - R_A|) Y_lm(r^) and their gradients, with the
+ *     radial part a natural cubic spline through the tabulated R_f on a logarithmic grid
+ *     and Y_lm real, orthonormal spherical harmonics evaluated through spherical
+ *     coordinates (theta = acos(z/r), phi = atan2(y,x)) and the associated-Legendre
+ *     recurrence. (Sec. 3.2.1: NAO basis functions confined to a cutoff radius.)
+ *   - the Hamiltonian matrix as the plain discrete definition (Eq. H_int_aims with the
+ *     symmetric kinetic form of Eq. RealSpaceHamNonPeriodic):
+ *         H_ij = sum_p w_p [ phi_i v_p phi_j + 1/2 grad phi_i . grad phi_j ]
+ *     summed point by point over the basis functions that are non-zero at p;
+ *   - the density as the plain definition (Eq. Density): n_p = sum_ij phi_i P_ij phi_j;
+ *   - the electron count N_e = sum_p w_p n_p;
+ *   - the batch partition (Sec. 3.3.1, grid-adapted cut planes) and the per-batch reduced
+ *     basis sets nnz(B) (Sec. 3.3.2), both under the integer rules stated at each function.
+ * Cross-point sums use Neumaier's compensated summation (Neumaier 1974).
+ *
+ * Readings of the paper used here (the paper is silent on them):
+ *   - radial spline: natural cubic spline in the index coordinate s = ln(r/r0)/Delta;
+ *     for r < r0 the radial part is taken at r0 (value and derivative); R = 0 for r >= rc;
+ *   - real Y_lm without the Condon-Shortley phase; m > 0 carries cos(m phi), m < 0 carries
+ *     sin(|m| phi); basis order is atom, then species radial function, then m = -l..l;
+ *   - a point that coincides with a nucleus is an error (status -2); a point on the polar
+ *     axis of an atom (sin theta < 1e-12) is reported through the pole counter and its
+ *     angular gradient is not formed (status -3), because the spherical formula divides
+ *     by sin theta there.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_LMAX 6
+
+typedef struct {
+    int32_t n_atoms;
+    const double *atom_xyz;       /* [n_atoms*3] */
+    const int32_t *atom_species;  /* [n_atoms] */
+    int32_t n_species;
+    const int32_t *species_fn_offset; /* [n_species+1] */
+    const int32_t *fn_l;          /* [n_fn] */
+    const double *fn_cutoff;      /* [n_fn] */
+    int32_t n_rgrid;
+    double r0, r_last;
+    const double *fn_table;       /* [n_fn*n_rgrid] R_f(r_k) */
+    const double *spline_M;       /* [n_fn*n_rgrid] second derivatives in s (from or_spline_M) */
+} or_sys;
+
+/* ------------------------------------------------------------------------------------ */
+/* compensated summation                                                                */
+/* ------------------------------------------------------------------------------------ */
+static inline void neu_add(double *s, double *c, double x) {
+    double t = *s + x;
+    if (fabs(*s) >= fabs(x)) *c += (*s - t) + x;
+    else *c += (x - t) + *s;
+    *s = t;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* natural cubic spline in the index coordinate                                         */
+/* ------------------------------------------------------------------------------------ */
+/* Second derivatives M_k of the natural cubic spline through (k, y_k), k = 0..n-1:
+ * M_{k-1} + 4 M_k + M_{k+1} = 6 (y_{k+1} - 2 y_k + y_{k-1}),  M_0 = M_{n-1} = 0,
+ * solved with the Thomas algorithm. */
+int or_spline_M(const double *y, int32_t n, double *M) {
+    if (n < 2) return -1;
+    M[0] = 0.0;
+    M[n - 1] = 0.0;
+    if (n == 2) return 0;
+    int32_t m = n - 2; /* unknowns M_1..M_{n-2} */
+    double *c = (double *)malloc(sizeof(double) * (size_t)m);
+    double *d = (double *)malloc(sizeof(double) * (size_t)m);
+    if (!c || !d) { free(c); free(d); return -1; }
+    for (int32_t i = 0; i < m; i++) {
+        int32_t k = i + 1;
+        double rhs = 6.0 * (y[k + 1] - 2.0 * y[k] + y[k - 1]);
+        if (i == 0) {
+            c[i] = 1.0 / 4.0;
+            d[i] = rhs / 4.0;
+        } else {
+            double den = 4.0 - c[i - 1];
+            c[i] = 1.0 / den;
+            d[i] = (rhs - d[i - 1]) / den;
+        }
+    }
+    M[m] = d[m - 1];
+    for (int32_t i = m - 2; i >= 0; i--) M[i + 1] = d[i] - c[i] * M[i + 2];
+    free(c);
+    free(d);
+    return 0;
+}
+
+/* Value and d/ds of the spline at s (segment k = floor(s), clamped to [0, n-2]). */
+static void spline_eval(const double *y, const double *M, int32_t n, double s, double *val, double *dval) {
+    int32_t k = (int32_t)floor(s);
+    if (k < 0) k = 0;
+    if (k > n - 2) k = n - 2;
+    double t = s - (double)k;
+    double u = 1.0 - t;
+    *val = u * y[k] + t * y[k + 1] + ((u * u * u - u) * M[k] + (t * t * t - t) * M[k + 1]) / 6.0;
+    *dval = (y[k + 1] - y[k]) + ((1.0 - 3.0 * u * u) * M[k] + (3.0 * t * t - 1.0) * M[k + 1]) / 6.0;
+}
+
+/* R_f(r) and dR_f/dr. Zero for r >= rc_f; the radial part is taken at r0 for r < r0. */
+void or_radial(const or_sys *S, int32_t f, double r, double *R, double *dR) {
+    if (r >= S->fn_cutoff[f]) { *R = 0.0; *dR = 0.0; return; }
+    double delta = log(S->r_last / S->r0) / (double)(S->n_rgrid - 1);
+    double rr = r < S->r0 ? S->r0 : r;
+    double s = log(rr / S->r0) / delta;
+    double v, dv;
+    spline_eval(S->fn_table + (size_t)f * S->n_rgrid, S->spline_M + (size_t)f * S->n_rgrid, S->n_rgrid, s, &v, &dv);
+    *R = v;
+    *dR = dv / (rr * delta);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* real spherical harmonics through spherical coordinates                               */
+/* ------------------------------------------------------------------------------------ */
+static double factorial(int n) { double f = 1.0; for (int i = 2; i <= n; i++) f *= (double)i; return f; }
+
+/* Associated Legendre functions without the Condon-Shortley phase, P[l][m] for 0<=m<=l<=L,
+ * at x = cos(theta), st = sin(theta):
+ *   P_m^m = (2m-1)!! st^m,  P_{m+1}^m = (2m+1) x P_m^m,
+ *   (l-m) P_l^m = (2l-1) x P_{l-1}^m - (l+m-1) P_{l-2}^m.                               */
+static void legendre(int L, double x, double st, double P[OR_LMAX + 2][OR_LMAX + 2]) {
+    memset(P, 0, sizeof(double) * (OR_LMAX + 2) * (OR_LMAX + 2));
+    double pmm = 1.0;
+    for (int m = 0; m <= L; m++) {
+        if (m > 0) pmm *= (double)(2 * m - 1) * st;
+        P[m][m] = pmm;
+        if (m + 1 <= L) P[m + 1][m] = (double)(2 * m + 1) * x * pmm;
+        for (int l = m + 2; l <= L; l++)
+            P[l][m] = ((double)(2 * l - 1) * x * P[l - 1][m] - (double)(l + m - 1) * P[l - 2][m]) / (double)(l - m);
+    }
+}
+
+/* Y_lm(theta, phi) for m = -l..l, with dY/dtheta and (1/sin theta) dY/dphi.
+ * Y_l0 = K_l0 P_l^0; Y_lm = sqrt2 K_lm P_l^m cos(m phi); Y_l,-m = sqrt2 K_lm P_l^m sin(m phi);
+ * K_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!).
+ * dP_l^0/dtheta = -P_l^1;  dP_l^m/dtheta = ((l+m)(l-m+1) P_l^{m-1} - P_l^{m+1}) / 2 for m >= 1. */
+static void ylm_sph(int l, double theta, double phi, double *Y, double *dYt, double *dYp_over_st) {
+    double x = cos(theta), st = sin(theta);
+    double P[OR_LMAX + 2][OR_LMAX + 2];
+    legendre(l + 1 <= OR_LMAX + 1 ? l + 1 : OR_LMAX + 1, x, st, P);
+    for (int m = 0; m <= l; m++) {
+        double K = sqrt((2.0 * l + 1.0) / (4.0 * M_PI) * factorial(l - m) / factorial(l + m));
+        double dP;
+        if (m == 0) dP = -P[l][1];
+        else dP = 0.5 * ((double)(l + m) * (double)(l - m + 1) * P[l][m - 1] - (m + 1 <= l ? P[l][m + 1] : 0.0));
+        if (m == 0) {
+            Y[l] = K * P[l][0];
+            dYt[l] = K * dP;
+            dYp_over_st[l] = 0.0;
+        } else {
+            double c = cos(m * phi), s = sin(m * phi);
+            double Pm_over_st = st > 0.0 ? P[l][m] / st : 0.0;
+            Y[l + m] = M_SQRT2 * K * P[l][m] * c;
+            Y[l - m] = M_SQRT2 * K * P[l][m] * s;
+            dYt[l + m] = M_SQRT2 * K * dP * c;
+            dYt[l - m] = M_SQRT2 * K * dP * s;
+            dYp_over_st[l + m] = -M_SQRT2 * K * Pm_over_st * (double)m * s;
+            dYp_over_st[l - m] = M_SQRT2 * K * Pm_over_st * (double)m * c;
+        }
+    }
+}
+
+/* Public helper for the tests: Y_lm (m=-l..l, 2l+1 values) at direction (x,y,z), any length. */
+int or_ylm(int32_t l, double x, double y, double z, double *Y) {
+    if (l < 0 || l > OR_LMAX) return -1;
+    double r = sqrt(x * x + y * y + z * z);
+    if (r == 0.0) return -2;
+    double dt[2 * OR_LMAX + 1], dp[2 * OR_LMAX + 1];
+    ylm_sph(l, acos(z / r), atan2(y, x), Y, dt, dp);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* basis functions                                                                      */
+/* ------------------------------------------------------------------------------------ */
+int64_t or_n_basis(const or_sys *S) {
+    int64_t nb = 0;
+    for (int32_t a = 0; a < S->n_atoms; a++) {
+        int32_t sp = S->atom_species[a];
+        for (int32_t f = S->species_fn_offset[sp]; f < S->species_fn_offset[sp + 1]; f++) nb += 2 * S->fn_l[f] + 1;
+    }
+    return nb;
+}
+
+/* All basis functions that are non-zero at point p (r < rc of their radial function), in
+ * ascending basis order, with phi and grad phi.  Returns the count, or a negative status.
+ * pole_count is incremented for each atom whose polar axis the point lies on.            */
+static int64_t point_basis(const or_sys *S, const double p[3], int64_t *idx, double *phi, double *grad,
+                           int64_t *pole_count, int all) {
+    int64_t cnt = 0, base = 0;
+    for (int32_t a = 0; a < S->n_atoms; a++) {
+        int32_t sp = S->atom_species[a];
+        double dx = p[0] - S->atom_xyz[3 * a + 0];
+        double dy = p[1] - S->atom_xyz[3 * a + 1];
+        double dz = p[2] - S->atom_xyz[3 * a + 2];
+        double r = sqrt(dx * dx + dy * dy + dz * dz);
+        int have_angles = 0;
+        double theta = 0, ph = 0, st = 0, ct = 0, sp_ = 0, cp = 0;
+        for (int32_t f = S->species_fn_offset[sp]; f < S->species_fn_offset[sp + 1]; f++) {
+            int l = S->fn_l[f];
+            int nm = 2 * l + 1;
+            if (!(r < S->fn_cutoff[f])) {
+                if (all) {
+                    for (int m = 0; m < nm; m++) {
+                        idx[cnt] = base + m; phi[cnt] = 0.0;
+                        grad[3 * cnt] = grad[3 * cnt + 1] = grad[3 * cnt + 2] = 0.0; cnt++;
+                    }
+                }
+                base += nm;
+                continue;
+            }
+            if (r == 0.0) return -2;
+            if (!have_angles) {
+                theta = acos(dz / r);
+                ph = atan2(dy, dx);
+                st = sin(theta); ct = cos(theta); sp_ = sin(ph); cp = cos(ph);
+                if (st < 1e-12) { (*pole_count)++; return -3; }
+                have_angles = 1;
+            }
+            double R, dR;
+            or_radial(S, f, r, &R, &dR);
+            double Y[2 * OR_LMAX + 1], dYt[2 * OR_LMAX + 1], dYp[2 * OR_LMAX + 1];
+            ylm_sph(l, theta, ph, Y, dYt, dYp);
+            /* grad = R' Y r_hat + (R/r) [dY/dtheta theta_hat + (1/sin) dY/dphi phi_hat] */
+            double rh[3] = {st * cp, st * sp_, ct};
+            double th[3] = {ct * cp, ct * sp_, -st};
+            double fh[3] = {-sp_, cp, 0.0};
+            for (int m = 0; m < nm; m++) {
+                idx[cnt] = base + m;
+                phi[cnt] = R * Y[m];
+                for (int c = 0; c < 3; c++)
+                    grad[3 * cnt + c] = dR * Y[m] * rh[c] + (R / r) * (dYt[m] * th[c] + dYp[m] * fh[c]);
+                cnt++;
+            }
+            base += nm;
+        }
+    }
+    return cnt;
+}
+
+/* Dense phi [n_pts][nb] and grad [n_pts][nb][3] for every basis function (zeros included). */
+int or_eval_dense(const or_sys *S, int64_t n_pts, const double *pts, double *phi, double *grad, int64_t *pole_count) {
+    int64_t nb = or_n_basis(S);
+    int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nb > 0 ? nb : 1));
+    if (!idx) return -1;
+    for (int64_t p = 0; p < n_pts; p++) {
+        int64_t c = point_basis(S, pts + 3 * p, idx, phi + p * nb, grad + 3 * p * nb, pole_count, 1);
+        if (c < 0) { free(idx); return (int)c; }
+    }
+    free(idx);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Hamiltonian (Eq. H_int_aims) and density (Eq. Density): plain point-by-point sums   */
+/* ------------------------------------------------------------------------------------ */
+/* H [nb*nb] (full, both triangles formed independently) and the error denominator
+ * A_ij = sum_p w_p [ |phi_i v phi_j| + 1/2 |grad phi_i . grad phi_j| ].
+ * terms: bit 0 = potential term (v == NULL means v = 1), bit 1 = kinetic term.           */
+int or_hamiltonian(const or_sys *S, int64_t n_pts, const double *pts, const double *w, const double *v,
+                   uint32_t terms, double *H, double *A, int64_t *pole_count) {
+    int64_t nb = or_n_basis(S);
+    size_t nn = (size_t)nb * (size_t)nb;
+    double *Hc = (double *)calloc(nn ? nn : 1, sizeof(double));
+    double *Ac = (double *)calloc(nn ? nn : 1, sizeof(double));
+    int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nb ? nb : 1));
+    double *phi = (double *)malloc(sizeof(double) * (size_t)(nb ? nb : 1));
+    double *grad = (double *)malloc(sizeof(double) * 3 * (size_t)(nb ? nb : 1));
+    if (!Hc || !Ac || !idx || !phi || !grad) { free(Hc); free(Ac); free(idx); free(phi); free(grad); return -1; }
+    memset(H, 0, nn * sizeof(double));
+    memset(A, 0, nn * sizeof(double));
+    int pot = (terms & 1u) != 0, kin = (terms & 2u) != 0;
+    int status = 0;
+    for (int64_t p = 0; p < n_pts; p++) {
+        int64_t cnt = point_basis(S, pts + 3 * p, idx, phi, grad, pole_count, 0);
+        if (cnt < 0) { status = (int)cnt; break; }
+        double wp = w[p], vp = v ? v[p] : 1.0;
+        for (int64_t a = 0; a < cnt; a++) {
+            size_t row = (size_t)idx[a] * (size_t)nb;
+            for (int64_t b = 0; b < cnt; b++) {
+                double tv = pot ? wp * (phi[a] * vp * phi[b]) : 0.0;
+                double gg = grad[3 * a] * grad[3 * b] + grad[3 * a + 1] * grad[3 * b + 1] + grad[3 * a + 2] * grad[3 * b + 2];
+                double tk = kin ? wp * 0.5 * gg : 0.0;
+                size_t e = row + (size_t)idx[b];
+                neu_add(&H[e], &Hc[e], tv + tk);
+                neu_add(&A[e], &Ac[e], fabs(tv) + fabs(tk));
+            }
+        }
+    }
+    for (size_t e = 0; e < nn; e++) { H[e] += Hc[e]; A[e] += Ac[e]; }
+    free(Hc); free(Ac); free(idx); free(phi); free(grad);
+    return status;
+}
+
+/* H and A restricted to a list of basis functions F (the block H[F,F]), from the same
+ * definition: every point is visited and phi is evaluated for the listed functions only. */
+int or_hamiltonian_block(const or_sys *S, int64_t n_pts, const double *pts, const double *w, const double *v,
+                         uint32_t terms, int32_t nF, const int64_t *F, double *H, double *A, int64_t *pole_count) {
+    int64_t nb = or_n_basis(S);
+    size_t nn = (size_t)nF * (size_t)nF;
+    double *Hc = (double *)calloc(nn ? nn : 1, sizeof(double));
+    double *Ac = (double *)calloc(nn ? nn : 1, sizeof(double));
+    int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nb ? nb : 1));
+    double *phi = (double *)malloc(sizeof(double) * (size_t)(nb ? nb : 1));
+    double *grad = (double *)malloc(sizeof(double) * 3 * (size_t)(nb ? nb : 1));
+    int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nb ? nb : 1));
+    double *fp = (double *)malloc(sizeof(double) * (size_t)(nF ? nF : 1));
+    double *fg = (double *)malloc(sizeof(double) * 3 * (size_t)(nF ? nF : 1));
+    if (!Hc || !Ac || !idx || !phi || !grad || !pos || !fp || !fg) {
+        free(Hc); free(Ac); free(idx); free(phi); free(grad); free(pos); free(fp); free(fg); return -1;
+    }
+    memset(H, 0, nn * sizeof(double));
+    memset(A, 0, nn * sizeof(double));
+    int pot = (terms & 1u) != 0, kin = (terms & 2u) != 0;
+    int status = 0;
+    for (int64_t p = 0; p < n_pts; p++) {
+        int64_t cnt = point_basis(S, pts + 3 * p, idx, phi, grad, pole_count, 1);
+        if (cnt < 0) { status = (int)cnt; break; }
+        for (int32_t a = 0; a < nF; a++) {
+            fp[a] = phi[F[a]];
+            fg[3 * a] = grad[3 * F[a]]; fg[3 * a + 1] = grad[3 * F[a] + 1]; fg[3 * a + 2] = grad[3 * F[a] + 2];
+        }
+        double wp = w[p], vp = v ? v[p] : 1.0;
+        for (int32_t a = 0; a < nF; a++) {
+            for (int32_t b = 0; b < nF; b++) {
+                double tv = pot ? wp * (fp[a] * vp * fp[b]) : 0.0;
+                double gg = fg[3 * a] * fg[3 * b] + fg[3 * a + 1] * fg[3 * b + 1] + fg[3 * a + 2] * fg[3 * b + 2];
+                double tk = kin ? wp * 0.5 * gg : 0.0;
+                size_t e = (size_t)a * (size_t)nF + (size_t)b;
+                neu_add(&H[e], &Hc[e], tv + tk);
+                neu_add(&A[e], &Ac[e], fabs(tv) + fabs(tk));
+            }
+        }
+    }
+    for (size_t e = 0; e < nn; e++) { H[e] += Hc[e]; A[e] += Ac[e]; }
+    free(Hc); free(Ac); free(idx); free(phi); free(grad); free(pos); free(fp); free(fg);
+    return status;
+}
+
+/* n_p = sum_ij phi_i P_ij phi_j over the functions non-zero at p; D_p = sum_ij |phi_i P_ij phi_j|;
+ * N_e = sum_p w_p n_p (w may be NULL, then N_e is not formed).                           */
+int or_density(const or_sys *S, int64_t n_pts, const double *pts, const double *w, const double *P,
+               double *n, double *D, double *Ne, int64_t *pole_count) {
+    int64_t nb = or_n_basis(S);
+    int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nb ? nb : 1));
+    double *phi = (double *)malloc(sizeof(double) * (size_t)(nb ? nb : 1));
+    double *grad = (double *)malloc(sizeof(double) * 3 * (size_t)(nb ? nb : 1));
+    if (!idx || !phi || !grad) { free(idx); free(phi); free(grad); return -1; }
+    double nes = 0.0, nec = 0.0;
+    int status = 0;
+    for (int64_t p = 0; p < n_pts; p++) {
+        int64_t cnt = point_basis(S, pts + 3 * p, idx, phi, grad, pole_count, 0);
+        if (cnt < 0) { status = (int)cnt; break; }
+        double s = 0.0, c = 0.0, ds = 0.0, dc = 0.0;
+        for (int64_t a = 0; a < cnt; a++) {
+            const double *row = P + (size_t)idx[a] * (size_t)nb;
+            for (int64_t b = 0; b < cnt; b++) {
+                double t = phi[a] * row[idx[b]] * phi[b];
+                neu_add(&s, &c, t);
+                neu_add(&ds, &dc, fabs(t));
+            }
+        }
+        n[p] = s + c;
+        if (D) D[p] = ds + dc;
+        if (w) neu_add(&nes, &nec, w[p] * n[p]);
+    }
+    if (Ne) *Ne = nes + nec;
+    free(idx); free(phi); free(grad);
+    return status;
+}
+
+/* Brute force for tiny inputs: phi for every basis function at every point (zeros
+ * included) and a triple loop over p, i, j, with no batching and no relevance pruning.   */
+int or_bruteforce(const or_sys *S, int64_t n_pts, const double *pts, const double *w, const double *v,
+                  const double *P, double *H, double *n, int64_t *pole_count) {
+    int64_t nb = or_n_basis(S);
+    double *phi = (double *)malloc(sizeof(double) * (size_t)(n_pts * nb + 1));
+    double *grad = (double *)malloc(sizeof(double) * 3 * (size_t)(n_pts * nb + 1));
+    if (!phi || !grad) { free(phi); free(grad); return -1; }
+    int st = or_eval_dense(S, n_pts, pts, phi, grad, pole_count);
+    if (st) { free(phi); free(grad); return st; }
+    for (int64_t i = 0; i < nb; i++)
+        for (int64_t j = 0; j < nb; j++) {
+            double s = 0.0, c = 0.0;
+            for (int64_t p = 0; p < n_pts; p++) {
+                const double *fi = phi + p * nb, *gi = grad + 3 * p * nb;
+                double t = w[p] * (fi[i] * v[p] * fi[j] +
+                                   0.5 * (gi[3 * i] * gi[3 * j] + gi[3 * i + 1] * gi[3 * j + 1] + gi[3 * i + 2] * gi[3 * j + 2]));
+                neu_add(&s, &c, t);
+            }
+            H[i * nb + j] = s + c;
+        }
+    for (int64_t p = 0; p < n_pts; p++) {
+        double s = 0.0, c = 0.0;
+        const double *f = phi + p * nb;
+        for (int64_t i = 0; i < nb; i++)
+            for (int64_t j = 0; j < nb; j++) neu_add(&s, &c, f[i] * P[i * nb + j] * f[j]);
+        n[p] = s + c;
+    }
+    free(phi); free(grad);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* batch partition (Sec. 3.3.1)                                                         */
+/* ------------------------------------------------------------------------------------ */
+/* Rule: split(S) with n = |S|, k = ceil(n/B). If k <= 1, S is one batch (in its current
+ * order). Otherwise take the axis of largest bounding-box extent (max - min in FP64; ties
+ * go x < y < z), stable-sort S by (coordinate, point index), put the first
+ * n_L = floor(n * floor(k/2) / k) points left, recurse left then right. Batches are
+ * numbered in that depth-first order.                                                     */
+typedef struct { double key; int64_t idx; } or_keyed;
+
+static int cmp_keyed(const void *a, const void *b) {
+    const or_keyed *x = (const or_keyed *)a, *y = (const or_keyed *)b;
+    if (x->key < y->key) return -1;
+    if (x->key > y->key) return 1;
+    return (x->idx > y->idx) - (x->idx < y->idx);
+}
+
+typedef struct {
+    const double *xyz;
+    int64_t B;
+    int64_t *perm;
+    int64_t pos;
+    int64_t *offsets;
+    int64_t nbatch;
+    or_keyed *tmp;
+} or_part;
+
+static void split(or_part *st, int64_t *S, int64_t n) {
+    int64_t k = (n + st->B - 1) / st->B;
+    if (k <= 1) {
+        for (int64_t i = 0; i < n; i++) st->perm[st->pos + i] = S[i];
+        st->pos += n;
+        st->nbatch++;
+        st->offsets[st->nbatch] = st->pos;
+        return;
+    }
+    double ext[3];
+    for (int c = 0; c < 3; c++) {
+        double lo = st->xyz[3 * S[0] + c], hi = lo;
+        for (int64_t i = 1; i < n; i++) {
+            double v = st->xyz[3 * S[i] + c];
+            if (v < lo) lo = v;
+            if (v > hi) hi = v;
+        }
+        ext[c] = hi - lo;
+    }
+    int ax = 0;
+    if (ext[1] > ext[ax]) ax = 1;
+    if (ext[2] > ext[ax]) ax = 2;
+    for (int64_t i = 0; i < n; i++) { st->tmp[i].key = st->xyz[3 * S[i] + ax]; st->tmp[i].idx = S[i]; }
+    qsort(st->tmp, (size_t)n, sizeof(or_keyed), cmp_keyed);
+    for (int64_t i = 0; i < n; i++) S[i] = st->tmp[i].idx;
+    int64_t kL = k / 2;
+    int64_t nL = (n * kL) / k;
+    split(st, S, nL);
+    split(st, S + nL, n - nL);
+}
+
+/* offsets must hold ceil(n/B)+1 entries, perm n entries. Returns the number of batches. */
+int64_t or_partition(int64_t n_pts, const double *xyz, int64_t B, int64_t *offsets, int64_t *perm) {
+    if (n_pts <= 0 || B <= 0) return -1;
+    int64_t *S = (int64_t *)malloc(sizeof(int64_t) * (size_t)n_pts);
+    or_keyed *tmp = (or_keyed *)malloc(sizeof(or_keyed) * (size_t)n_pts);
+    if (!S || !tmp) { free(S); free(tmp); return -1; }
+    for (int64_t i = 0; i < n_pts; i++) S[i] = i;
+    or_part st = {xyz, B, perm, 0, offsets, 0, tmp};
+    offsets[0] = 0;
+    split(&st, S, n_pts);
+    free(S);
+    free(tmp);
+    return st.nbatch;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* reduced basis per batch, nnz(B) (Sec. 3.3.2)                                          */
+/* ------------------------------------------------------------------------------------ */
+/* Rule: basis function (atom A, radial function f, m) is relevant to batch b iff some
+ * point p of b has r2 < rc_f * rc_f with r2 = (dx*dx + dy*dy) + dz*dz, each operation a
+ * separately rounded FP64 operation (no fused multiply-add). Indices ascending.
+ * With rel_idx == NULL only the offsets are written. Returns the total count.           */
+int64_t or_relevance(const or_sys *S, const double *pts, int64_t n_batches, const int64_t *offsets,
+                     const int64_t *perm, int64_t *rel_offsets, int32_t *rel_idx) {
+    int64_t total = 0;
+    rel_offsets[0] = 0;
+    for (int64_t b = 0; b < n_batches; b++) {
+        int64_t base = 0;
+        for (int32_t a = 0; a < S->n_atoms; a++) {
+            int32_t sp = S->atom_species[a];
+            double minr2 = INFINITY;
+            for (int64_t q = offsets[b]; q < offsets[b + 1]; q++) {
+                const double *p = pts + 3 * perm[q];
+                double dx = p[0] - S->atom_xyz[3 * a + 0];
+                double dy = p[1] - S->atom_xyz[3 * a + 1];
+                double dz = p[2] - S->atom_xyz[3 * a + 2];
+                double r2 = (dx * dx + dy * dy) + dz * dz;
+                if (r2 < minr2) minr2 = r2;
+            }
+            for (int32_t f = S->species_fn_offset[sp]; f < S->species_fn_offset[sp + 1]; f++) {
+                int nm = 2 * S->fn_l[f] + 1;
+                double rc = S->fn_cutoff[f];
+                if (minr2 < rc * rc) {
+                    for (int m = 0; m < nm; m++) {
+                        if (rel_idx) rel_idx[total] = (int32_t)(base + m);
+                        total++;
+                    }
+                }
+                base += nm;
+            }
+        }
+        rel_offsets[b + 1] = total;
+    }
+    return total;
+}

@@ -1,0 +1,317 @@
+"""Seeded synthetic inputs for real-space grid integration with numeric atom-centred orbitals.
+
+This module only *generates inputs*: atoms, per-species radial function tables, the
+integration grid with its partition-of-unity weights, a local potential v and a
+symmetric positive semi-definite density matrix P. It holds none of the integration
+method's arithmetic (no spline, no spherical harmonics, no batch contraction), so both
+the CUDA path and the FP64 oracle can consume the same arrays without sharing code.
+
+Inputs follow the paper's statement of the problem:
+  * points are atom-centred radial shells x angular points, weighted by a
+    partition of unity (Sec. 3.2.1, Eq. H_int_aims);
+  * radial functions are confined so that they reach zero at a cutoff radius and
+    stay zero beyond it (Sec. 3.2.1, NAO basis paragraph);
+  * the paper's Lebedev grids, Blum09 radial rule, Stratmann weights and NAO species
+    files are not available, so the stand-ins are: Gauss-Chebyshev (2nd kind) radial
+    shells with a Becke map, Gauss-Legendre(theta) x uniform(phi) angular product
+    grids, plain Becke (1988) cell functions, and cutoff-smoothed Gaussian radial
+    functions N r^l exp(-alpha r^2) c(r).
+
+Seeds use numpy's PCG64 everywhere.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+try:  # scipy is present on both machines; keep the import local to what needs it
+    from scipy.special import erf as _erf
+except Exception:  # pragma: no cover
+    _erf = np.vectorize(math.erf)
+
+R0_DEFAULT = 1e-4
+RLAST_DEFAULT = 8.0
+NRGRID_DEFAULT = 1000
+RCUT_DEFAULT = 6.0
+
+
+# ----------------------------------------------------------------------------------------
+# radial functions (inputs): N r^l exp(-alpha r^2) with a smooth cutoff
+# ----------------------------------------------------------------------------------------
+def gaussian_norm(l: int, alpha: float) -> float:
+    """N with N^2 int_0^inf r^(2l) e^(-2 alpha r^2) r^2 dr = 1."""
+    return math.sqrt(2.0 * (2.0 * alpha) ** (l + 1.5) / math.gamma(l + 1.5))
+
+
+def cutoff_smoothing(r: np.ndarray, rc: float) -> np.ndarray:
+    """1 inside rc-1, a C2 quintic step down to 0 on [rc-1, rc], 0 beyond."""
+    r = np.asarray(r, dtype=np.float64)
+    t = np.clip(r - (rc - 1.0), 0.0, 1.0)
+    c = 1.0 - (10.0 * t**3 - 15.0 * t**4 + 6.0 * t**5)
+    return np.where(r >= rc, 0.0, c)
+
+
+def radial_function(r: np.ndarray, l: int, alpha: float, rc: float) -> np.ndarray:
+    r = np.asarray(r, dtype=np.float64)
+    return gaussian_norm(l, alpha) * r**l * np.exp(-alpha * r * r) * cutoff_smoothing(r, rc)
+
+
+def log_grid(n: int, r0: float, r_last: float) -> np.ndarray:
+    k = np.arange(n, dtype=np.float64)
+    return r0 * (r_last / r0) ** (k / (n - 1))
+
+
+# ----------------------------------------------------------------------------------------
+# integration grid (inputs)
+# ----------------------------------------------------------------------------------------
+def radial_shells(n: int, rm: float = 1.0):
+    """Gauss-Chebyshev (2nd kind) nodes mapped by r = rm (1+x)/(1-x); weights include r^2."""
+    i = np.arange(1, n + 1, dtype=np.float64)
+    th = i * math.pi / (n + 1)
+    x = np.cos(th)
+    r = rm * (1.0 + x) / (1.0 - x)
+    w = math.pi / (n + 1) * np.sin(th) * (2.0 * rm / (1.0 - x) ** 2) * r * r
+    return r, w
+
+
+def angular_product_grid(n_theta: int, n_phi: int):
+    """Gauss-Legendre in cos(theta) times a uniform phi grid (phi_0 = 0); weights sum to 4 pi."""
+    u, wu = np.polynomial.legendre.leggauss(n_theta)
+    phi = 2.0 * math.pi * np.arange(n_phi, dtype=np.float64) / n_phi
+    ct = np.repeat(u, n_phi)
+    st = np.sqrt(np.maximum(0.0, 1.0 - ct * ct))
+    ph = np.tile(phi, n_theta)
+    dirs = np.stack([st * np.cos(ph), st * np.sin(ph), ct], axis=1)
+    w = np.repeat(wu, n_phi) * (2.0 * math.pi / n_phi)
+    return dirs, w
+
+
+def becke_weights(pts: np.ndarray, owner: np.ndarray, atoms: np.ndarray, device: str | None = None,
+                  chunk: int = 8192) -> np.ndarray:
+    """Plain Becke (1988) partition weight of each point for the atom that owns it.
+
+    Vectorised with torch (CPU threads, or a CUDA device when one is given or present):
+    this is input generation, not part of the integration method.
+    """
+    import torch
+
+    n_atoms = atoms.shape[0]
+    if n_atoms == 1:
+        return np.ones(pts.shape[0], dtype=np.float64)
+    if device is None:
+        device = "cuda" if torch.cuda.is_available() else "cpu"
+    A = torch.as_tensor(atoms, dtype=torch.float64, device=device)
+    Rab = torch.cdist(A, A)
+    Rab.fill_diagonal_(1.0)
+    inv = 1.0 / Rab
+    eye = torch.eye(n_atoms, dtype=torch.bool, device=device)
+    P = torch.as_tensor(pts, dtype=torch.float64, device=device)
+    own = torch.as_tensor(owner, dtype=torch.int64, device=device)
+    out = torch.empty(pts.shape[0], dtype=torch.float64, device=device)
+    step = max(1, chunk * 64 * 64 // (n_atoms * n_atoms))
+    for s in range(0, pts.shape[0], step):
+        p = P[s : s + step]
+        d = torch.sqrt(((p[:, None, :] - A[None, :, :]) ** 2).sum(-1))  # [c, A]
+        mu = (d[:, :, None] - d[:, None, :]) * inv[None]  # [c, A, B]
+        f = mu
+        for _ in range(3):
+            f = 1.5 * f - 0.5 * f * f * f
+        sv = 0.5 * (1.0 - f)
+        sv = torch.where(eye[None], torch.ones_like(sv), sv)
+        cell = sv.prod(dim=2)  # [c, A]
+        tot = cell.sum(dim=1)
+        mine = cell.gather(1, own[s : s + step, None])[:, 0]
+        out[s : s + step] = torch.where(tot > 0, mine / torch.where(tot > 0, tot, torch.ones_like(tot)), torch.zeros_like(tot))
+    return out.cpu().numpy()
+
+
+def build_grid(atoms: np.ndarray, n_rad, n_theta, n_phi, rm: float = 1.0):
+    """Atom-major point list: for each atom, radial shell, theta, phi."""
+    n_atoms = atoms.shape[0]
+    n_rad = np.broadcast_to(np.asarray(n_rad), (n_atoms,))
+    n_theta = np.broadcast_to(np.asarray(n_theta), (n_atoms,))
+    n_phi = np.broadcast_to(np.asarray(n_phi), (n_atoms,))
+    pts, wts, own = [], [], []
+    for a in range(n_atoms):
+        r, wr = radial_shells(int(n_rad[a]), rm)
+        dirs, wa = angular_product_grid(int(n_theta[a]), int(n_phi[a]))
+        p = atoms[a][None, None, :] + r[:, None, None] * dirs[None, :, :]
+        pts.append(p.reshape(-1, 3))
+        wts.append((wr[:, None] * wa[None, :]).reshape(-1))
+        own.append(np.full(p.shape[0] * p.shape[1], a, dtype=np.int64))
+    pts = np.concatenate(pts)
+    wts = np.concatenate(wts)
+    own = np.concatenate(own)
+    wb = becke_weights(pts, own, atoms)
+    return np.ascontiguousarray(pts), wts * wb
+
+
+def model_potential(pts: np.ndarray, atoms: np.ndarray, Z: np.ndarray) -> np.ndarray:
+    """v(r) = sum_A [ -Z_A erf(r_A)/r_A + 0.3 exp(-r_A^2) ], with erf(r)/r -> 2/sqrt(pi) at r = 0."""
+    v = np.zeros(pts.shape[0], dtype=np.float64)
+    for a in range(atoms.shape[0]):
+        r = np.linalg.norm(pts - atoms[a][None, :], axis=1)
+        safe = np.where(r > 0.0, r, 1.0)
+        ef = np.where(r > 0.0, _erf(r) / safe, 2.0 / math.sqrt(math.pi))
+        v += -Z[a] * ef + 0.3 * np.exp(-r * r)
+    return v
+
+
+def random_psd(nb: int, seed: int, rank: int | None = None) -> np.ndarray:
+    """P = X X^T / k with X ~ N(0,1) of shape nb x k (k = nb unless a rank is given)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    k = nb if rank is None else rank
+    X = rng.standard_normal((nb, k))
+    P = X @ X.T / k
+    return np.ascontiguousarray(0.5 * (P + P.T))
+
+
+# ----------------------------------------------------------------------------------------
+# systems
+# ----------------------------------------------------------------------------------------
+@dataclass
+class Species:
+    ls: list  # angular momentum of each radial function
+    alphas: list  # Gaussian exponent of each radial function
+    rc: float = RCUT_DEFAULT
+    Z: float = 1.0
+
+
+@dataclass
+class System:
+    """Everything a grid handle is created from, plus generator metadata (alphas, Z)."""
+
+    atom_xyz: np.ndarray
+    atom_species: np.ndarray
+    species_fn_offset: np.ndarray
+    fn_l: np.ndarray
+    fn_cutoff: np.ndarray
+    fn_alpha: np.ndarray
+    n_rgrid: int
+    r0: float
+    r_last: float
+    fn_table: np.ndarray
+    pt_xyz: np.ndarray
+    pt_w: np.ndarray
+    Z: np.ndarray
+    max_batch_points: int = 200
+    name: str = "custom"
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_atoms(self) -> int:
+        return int(self.atom_xyz.shape[0])
+
+    @property
+    def n_points(self) -> int:
+        return int(self.pt_xyz.shape[0])
+
+    @property
+    def n_basis(self) -> int:
+        per_species = [
+            int(sum(2 * self.fn_l[f] + 1 for f in range(self.species_fn_offset[s], self.species_fn_offset[s + 1])))
+            for s in range(len(self.species_fn_offset) - 1)
+        ]
+        return int(sum(per_species[s] for s in self.atom_species))
+
+    def potential(self) -> np.ndarray:
+        return model_potential(self.pt_xyz, self.atom_xyz, self.Z)
+
+
+def make_system(
+    atoms,
+    species_of_atom,
+    species: list,
+    n_rad=40,
+    n_theta=10,
+    n_phi=11,
+    rm: float = 1.0,
+    n_rgrid: int = NRGRID_DEFAULT,
+    r0: float = R0_DEFAULT,
+    r_last: float = RLAST_DEFAULT,
+    max_batch_points: int = 200,
+    name: str = "custom",
+) -> System:
+    atoms = np.ascontiguousarray(np.asarray(atoms, dtype=np.float64).reshape(-1, 3))
+    species_of_atom = np.asarray(species_of_atom, dtype=np.int32)
+    fn_l, fn_alpha, fn_rc, off = [], [], [], [0]
+    for sp in species:
+        fn_l += list(sp.ls)
+        fn_alpha += list(sp.alphas)
+        fn_rc += [sp.rc] * len(sp.ls)
+        off.append(len(fn_l))
+    rg = log_grid(n_rgrid, r0, r_last)
+    table = np.stack([radial_function(rg, l, a, rc) for l, a, rc in zip(fn_l, fn_alpha, fn_rc)]) if fn_l else np.zeros((0, n_rgrid))
+    pts, w = build_grid(atoms, n_rad, n_theta, n_phi, rm)
+    Z = np.array([species[s].Z for s in species_of_atom], dtype=np.float64)
+    return System(
+        atom_xyz=atoms,
+        atom_species=species_of_atom,
+        species_fn_offset=np.asarray(off, dtype=np.int32),
+        fn_l=np.asarray(fn_l, dtype=np.int32),
+        fn_cutoff=np.asarray(fn_rc, dtype=np.float64),
+        fn_alpha=np.asarray(fn_alpha, dtype=np.float64),
+        n_rgrid=n_rgrid,
+        r0=r0,
+        r_last=r_last,
+        fn_table=np.ascontiguousarray(table),
+        pt_xyz=pts,
+        pt_w=w,
+        Z=Z,
+        max_batch_points=max_batch_points,
+        name=name,
+    )
+
+
+def _log_uniform(rng, lo, hi, n):
+    return np.exp(rng.uniform(math.log(lo), math.log(hi), n))
+
+
+def config_water(n_rad=40, n_theta=10, n_phi=11, max_batch_points=200) -> System:
+    """3-atom molecule: heavy atom at the origin, light atoms at (+-1.43, 1.11, 0) bohr; 20 basis functions."""
+    atoms = [[0.0, 0.0, 0.0], [1.43, 1.11, 0.0], [-1.43, 1.11, 0.0]]
+    heavy = Species(ls=[0, 0, 1, 2], alphas=[10.0, 1.5, 0.4, 0.6], Z=8.0)
+    light = Species(ls=[0, 0, 1], alphas=[1.2, 0.3, 0.8], Z=1.0)
+    return make_system(atoms, [0, 1, 1], [heavy, light], n_rad, n_theta, n_phi, max_batch_points=max_batch_points, name="water3")
+
+
+def diamond_cluster(a: float = 10.26, cells: int = 2) -> np.ndarray:
+    base = np.array(
+        [[0, 0, 0], [0, 0.5, 0.5], [0.5, 0, 0.5], [0.5, 0.5, 0],
+         [0.25, 0.25, 0.25], [0.25, 0.75, 0.75], [0.75, 0.25, 0.75], [0.75, 0.75, 0.25]]
+    )
+    out = []
+    for i in range(cells):
+        for j in range(cells):
+            for k in range(cells):
+                out.append((base + np.array([i, j, k])) * a)
+    return np.concatenate(out)
+
+
+def silicon_species(seed: int = 1) -> Species:
+    """2s,2p,2d,1f radial functions (25 basis functions), alpha log-uniform in [0.1, 20]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ls = [0, 0, 1, 1, 2, 2, 3]
+    return Species(ls=ls, alphas=list(_log_uniform(rng, 0.1, 20.0, len(ls))), Z=14.0)
+
+
+def config_diamond64(n_rad=60, n_theta=17, n_phi=18, max_batch_points=300, cells=2) -> System:
+    """64-atom diamond-lattice cluster (cubic cell 10.26 bohr), 1600 basis functions, ~1.17M points."""
+    atoms = diamond_cluster(10.26, cells)
+    sp = silicon_species(1)
+    return make_system(atoms, np.zeros(len(atoms), np.int32), [sp], n_rad, n_theta, n_phi,
+                       max_batch_points=max_batch_points, name=f"diamond{len(atoms)}")
+
+
+def density_matrix(sys: System, seed: int, rank: int | None = None) -> np.ndarray:
+    return random_psd(sys.n_basis, seed, rank)
+
+
+def config(k: int, **kw) -> System:
+    if k == 0:
+        return config_water(**kw)
+    if k == 1:
+        return config_diamond64(**kw)
+    raise ValueError(f"unknown configuration {k}")
