@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Throughput of Hamiltonian integration + density update on one GB300 (points/s).
+
+One step = nao_integrate_h (evaluate phi, grad phi per batch; h[B] contraction; scatter into
+H; mirror) followed by nao_update_density (evaluate phi; density contraction; N_e) over the
+whole grid of the 64-atom diamond-lattice cluster (1600 basis functions, 1,175,040 points,
+batches of <= 300 points), inputs resident in device memory. Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec split|fp64|fp32] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload on its own
+GPU (the path has no exchange step on one handle); the line reports all ranks' points
+divided by the slowest rank's time. ``--impl reference`` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Hamiltonian integration + density update pts/s, split-prec vs FP64; p99 latency"
+WORKLOAD = ("diamond64: 64-atom diamond-lattice cluster (cubic cell 10.26 bohr), 1600 basis functions "
+            "(2s2p2d1f per atom), 60x306 points per atom = 1,175,040 points, batches <= 300 points")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default=None, choices=[None, "fp64", "fp32", "split"])
+    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--cpu-sample", type=int, default=12000, help="oracle sample size (points)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--compare", action="store_true", help="also time the other precisions (extra keys)")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p))
+    except Exception:
+        return {}
+
+
+# FP64 FMA throughput of one GB300 (measured on this machine's GPUs by a DFMA loop).
+FP64_PEAK_TFLOPS_MEASURED = None  # filled from profiles/fp64_peak.txt when present
+
+
+def fp64_peak():
+    path = os.path.join(ROOT, "profiles", "fp64_peak.txt")
+    try:
+        for line in open(path):
+            if line.startswith("fp64_fma_tflops"):
+                return float(line.split()[1]), "measured (profiles/fp64_peak.txt)"
+    except Exception:
+        pass
+    return 1.25, "nominal GB300 FP64"
+
+
+# ---------------------------------------------------------------------------------------
+def make_workload(config: int, device: str):
+    from paper_1912_06636_gb300 import synth
+
+    s = synth.config(config)
+    v = s.potential()
+    P = synth.density_matrix(s, config)
+    return s, v, P
+
+
+def cpu_baseline(s, v, P, n_sample: int, seed: int = 12345):
+    """The FP64 oracle as it stands, on a seeded sample of the workload's points (1 thread)."""
+    import numpy as np
+
+    import oracle
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    idx = np.sort(rng.choice(s.n_points, size=min(n_sample, s.n_points), replace=False))
+    pts, w, vv = s.pt_xyz[idx], s.pt_w[idx], v[idx]
+    o = oracle.Oracle(s)
+    t0 = time.perf_counter()
+    o.hamiltonian(pts, w, vv)
+    t1 = time.perf_counter()
+    o.density(pts, P, w)
+    t2 = time.perf_counter()
+    return {"value": len(idx) / (t2 - t0), "unit": "points/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(idx)} seeded points of the workload (H over those points, then n on them): "
+                      f"H {t1 - t0:.1f} s + n {t2 - t1:.1f} s"}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    s, v, P = make_workload(args.config, "cpu")
+    times = []
+    for _ in range(args.warmup + args.steps):
+        cb = cpu_baseline(s, v, P, max(200, args.cpu_sample // 4))
+        times.append(cb)
+    timed = times[args.warmup:]
+    val = statistics.mean(t["value"] for t in timed)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "points/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * s.n_points / val,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "fp64", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": val, "unit": "points/s", "cores": 1, "kind": "oracle",
+                             "sample": timed[0]["sample"] + " per step"},
+            "e2e": {"value": val, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    __graft_entry__.build()
+    from paper_1912_06636_gb300 import nao
+
+    prec = args.prec or "fp64"
+    s, v_np, P_np = make_workload(args.config, f"cuda:{local_rank}")
+    dev = torch.device("cuda", local_rank)
+    t0 = time.perf_counter()
+    g = nao.Grid(s, device=local_rank, max_batch_points=s.max_batch_points)
+    torch.cuda.synchronize()
+    create_s = time.perf_counter() - t0
+    info = g.info
+    v = torch.from_numpy(v_np).to(dev)
+    P = torch.from_numpy(P_np).to(dev)
+    H = torch.empty((g.nb, g.nb), dtype=torch.float64, device=dev)
+    n = torch.empty(g.n_points, dtype=torch.float64, device=dev)
+    ne = torch.empty(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(p=prec):
+        g.integrate_h(v, prec=p, H=H, stream=stream)
+        g.update_density(P, prec=p, n=n, ne=ne, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    g.sync()
+
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    nao.nao_profile_enable(g.h, True)
+    nao.nao_profile_read(g.h, reset=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    prof = nao.nao_profile_read(g.h, reset=True)
+    nao.nao_profile_enable(g.h, False)
+    g.sync()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = evs[0][0].elapsed_time(evs[-1][1])
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps * g.n_points / (total_ms / 1e3)
+    bo, _, ro, _ = g.batches()
+    Pb, Nb = np.diff(bo), np.diff(ro)
+    Ppad = (Pb + 15) // 16 * 16
+    scratch_gb = float(np.sum(Nb * Ppad * 8 * 5)) / 1e9
+
+    # roofline of the dominant kernel (per launch: algorithmic FLOPs / event-timed duration)
+    fam = max(prof, key=lambda k: prof[k][1])
+    launches, fam_ms = prof[fam]
+    flops_per_step = {"h_fp64": info.flops_h, "h_fp32": info.flops_h, "h_split": info.flops_h,
+                      "n_fp64": info.flops_n, "n_fp32": info.flops_n, "n_split": info.flops_n}.get(fam)
+    roofline = None
+    if flops_per_step and fam_ms > 0:
+        achieved = flops_per_step * args.steps / (fam_ms / 1e3) / 1e12
+        if fam.endswith("fp64"):
+            peak, peak_src = fp64_peak()
+            roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "traffic": None, "kernel": fam, "peak_source": peak_src,
+                        "launches": launches, "avg_launch_ms": fam_ms / max(launches, 1)}
+        else:
+            pk = measured_peaks().get("bf16_tflops_sustained", 1700.0)
+            roofline = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                        "frac": achieved / pk, "traffic": None, "kernel": fam,
+                        "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",
+                        "launches": launches, "avg_launch_ms": fam_ms / max(launches, 1)}
+    gpu_launches = int(sum(l for l, _ in prof.values()))
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "split": "bf16x-slices+f64"}[prec],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": prec, "parallelism": f"replicas{world}",
+                   "l2": f"inputs/working set larger than L2: {scratch_gb:.1f} GB of evaluated basis functions "
+                         "written and re-read per step",
+                   "n_points": g.n_points, "n_basis": g.nb, "n_batches": int(info.n_batches),
+                   "max_batch_basis": int(info.max_batch_basis)},
+        "p50_ms": statistics.median(step_ms), "p99_ms": float(np.percentile(step_ms, 99)),
+        "gflops_algorithmic": (info.flops_h + info.flops_n) / (total_ms / args.steps / 1e3) / 1e9,
+        "create_s": create_s,
+        "roofline": roofline, "gpu_launches": gpu_launches, "clocks": clocks,
+        "kernel_ms_per_step": {k: ms / args.steps for k, (l, ms) in prof.items() if l},
+    }
+
+    if not args.no_e2e:
+        Hh = torch.empty((g.nb, g.nb), dtype=torch.float64).pin_memory().numpy()
+        nh = torch.empty(g.n_points, dtype=torch.float64).pin_memory().numpy()
+        vh = torch.from_numpy(v_np).pin_memory().numpy()
+        Ph = torch.from_numpy(P_np).pin_memory().numpy()
+        e2e_steps = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            nao.nao_integrate_h_host(g.h, vh, 3, prec, Hh, stream)
+            nao.nao_update_density_host(g.h, Ph, prec, nh, stream)
+        dt = (time.perf_counter() - t0) / e2e_steps
+        line["e2e"] = {"value": g.n_points / dt, "unit": "points/s",
+                       "h2d_bytes_per_step": int(8 * (g.n_points + g.nb * g.nb)),
+                       "d2h_bytes_per_step": int(8 * (g.nb * g.nb + g.n_points + 1))}
+
+    if args.compare:
+        other = {}
+        for p in ("fp64", "fp32", "split"):
+            if p == prec:
+                continue
+            try:
+                step(p)
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                step(p)
+                b.record(stream)
+                torch.cuda.synchronize()
+                other[p] = {"points_per_s": g.n_points / (a.elapsed_time(b) / 1e3), "ms_per_step": a.elapsed_time(b)}
+            except nao.NaoError as e:
+                other[p] = {"unavailable": str(e)}
+        line["other_precisions"] = other
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(s, v_np, P_np, args.cpu_sample)
+    g.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,219 @@
+/*
+ * nao.h -- C ABI of the GB300 real-space grid-integration library (libnao.so).
+ *
+ * The library integrates, on one GPU, the two real-space operations of an all-electron
+ * Kohn-Sham code with numeric atom-centred orbitals (Huhn et al., "GPGPU Acceleration of
+ * All-Electron Electronic Structure Theory Using Localized Numeric Atom-Centered Basis
+ * Functions", arXiv:1912.06636):
+ *
+ *   Hamiltonian  h_ij = sum_r w(r) [ phi_i(r) v(r) phi_j(r) + 1/2 grad phi_i . grad phi_j ]
+ *                (Eq. H_int_aims with the kinetic operator written in its symmetric form;
+ *                 Eqs. H_decomp / H_contrib_batch split it over batches of points)
+ *   Density      n(r) = sum_ij phi_i(r) n_ij phi_j(r)          (Eq. Density)
+ *
+ * where phi_i(r) = R_f(|r - R_A|) Y_lm(r^) is basis function i (atom A, radial function f
+ * of A's species, m), R_f a cubic spline through a tabulated radial function that is zero
+ * beyond its cutoff (Sec. 3.2.1), and Y_lm a real spherical harmonic.
+ *
+ * Conventions for every call:
+ *   - Status codes; nothing aborts, traps or throws across the ABI.
+ *   - "_dev" pointers are CUDA device pointers on the handle's device; "host" pointers are
+ *     ordinary host memory. The caller owns every buffer it passes in and keeps it alive
+ *     until the work on the given stream has completed. The library owns the handle and
+ *     the device tables and scratch it allocated at create time, and frees them in
+ *     nao_destroy.
+ *   - Work is enqueued asynchronously on the CUDA stream passed in (cudaStream_t as void*,
+ *     NULL = the legacy default stream). A handle serves one stream at a time: calls on
+ *     the same handle must not overlap on the GPU.
+ *   - Device-side failures (a kernel's own bounds or timeout check) are recorded in the
+ *     handle and reported by nao_sync_status and by the next call on the handle.
+ *   - There is no CPU fallback: every numeric step runs in the library's CUDA kernels.
+ */
+#ifndef NAO_H
+#define NAO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nao_grid nao_grid; /* opaque, library-owned */
+
+typedef enum {
+    NAO_OK = 0,
+    NAO_ERR_INVALID_ARG = 1,   /* a bad pointer, size, index, non-finite value or option */
+    NAO_ERR_OUT_OF_MEMORY = 2, /* a device or host allocation failed */
+    NAO_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed */
+    NAO_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up */
+    NAO_ERR_INTERNAL = 5,      /* a device-side consistency check failed */
+    NAO_ERR_UNSUPPORTED = 6    /* valid request the build or device cannot serve */
+} nao_status;
+
+/* Arithmetic of the contractions (Eq. batch_matrix_mult and the density analogue).
+ *   NAO_FP64  : FP64 everywhere.
+ *   NAO_FP32  : basis functions and contractions in FP32 (FP64 inside 0.1 bohr of a
+ *               nucleus), per-batch results accumulated into H / n in FP64.
+ *   NAO_SPLIT : FP64 basis functions cut into bf16 integer slices (Ozaki splitting);
+ *               the slice products run on the tcgen05 tensor cores with exact FP32
+ *               accumulation and are recombined in FP64.                                 */
+typedef enum { NAO_FP64 = 0, NAO_FP32 = 1, NAO_SPLIT = 2 } nao_precision;
+
+/* Terms of nao_integrate_h. The overlap s_ij (Eq. OverlapNoPeriodic) is
+ * NAO_TERM_POTENTIAL with v_dev == NULL (v = 1): the paper integrates it with the same
+ * code as h (Sec. 3.2.1).                                                                */
+enum { NAO_TERM_POTENTIAL = 1u, NAO_TERM_KINETIC = 2u };
+
+/* The system, exactly as the paper states the problem (Sec. 3.2.1, Sec. 3.3):
+ * atoms with species; per species a list of radial functions (angular momentum l and a
+ * cutoff radius); each radial function tabulated on the logarithmic grid
+ * r_k = r0 (r_last/r0)^(k/(n_rgrid-1)); and the integration points with their weights.
+ * All pointers are HOST pointers, read during nao_grid_create only.
+ * Basis order: atom, then the species' radial functions in order, then m = -l..l.         */
+typedef struct {
+    int32_t n_atoms;
+    const double *atom_xyz;          /* [n_atoms*3] bohr */
+    const int32_t *atom_species;     /* [n_atoms], 0..n_species-1 */
+    int32_t n_species;
+    const int32_t *species_fn_offset; /* [n_species+1] radial functions of species s are
+                                         species_fn_offset[s] .. species_fn_offset[s+1]-1 */
+    const int32_t *fn_l;             /* [n_fn] angular momentum 0..6 */
+    const double *fn_cutoff;         /* [n_fn] bohr, 0 < cutoff <= r_last; R_f = 0 beyond */
+    int32_t n_rgrid;                 /* >= 4 */
+    double r0, r_last;               /* 0 < r0 < r_last */
+    const double *fn_table;          /* [n_fn*n_rgrid] R_f(r_k) (the radial function itself) */
+    int64_t n_points;                /* >= 1, < 2^31 */
+    const double *pt_xyz;            /* [n_points*3] bohr; no point may coincide with a nucleus */
+    const double *pt_w;              /* [n_points] integration weights (finite) */
+} nao_system_desc;
+
+typedef struct {
+    int32_t max_batch_points; /* target batch size B (Sec. 3.3.1; the paper uses 200 on GPUs); default 200 */
+    int32_t split_slices;     /* slices per operand on the NAO_SPLIT path, 4..10; default 8 */
+    int32_t deterministic;    /* reserved; results are already run-to-run reproducible up to
+                                 the order of FP64 atomic additions into H */
+    int32_t device;           /* CUDA device ordinal; -1 = the calling thread's current device */
+    int64_t scratch_bytes;    /* device scratch for evaluated basis functions; 0 = library default */
+} nao_options;
+
+typedef struct {
+    int64_t n_basis;          /* nb: H and P are nb x nb, row-major */
+    int64_t n_points;
+    int64_t n_batches;
+    int64_t rel_total;        /* sum over batches of |nnz(B)| */
+    int32_t max_batch_points; /* largest |B| */
+    int32_t max_batch_basis;  /* largest |nnz(B)| */
+    int64_t device_bytes;     /* device memory held by the handle */
+    int64_t flops_h;          /* algorithmic FLOPs of one nao_integrate_h: sum_b 4 P_b N_b (N_b+1) */
+    int64_t flops_n;          /* algorithmic FLOPs of one nao_update_density: sum_b 2 P_b N_b^2 + 2 P_b N_b */
+} nao_grid_info;
+
+/* Fill *opts with the defaults above. */
+nao_status nao_default_options(nao_options *opts);
+
+/* Build a handle (Sec. 3.3.1-3.3.2): partition the points into batches by recursive
+ * bisection (the batch-partition rule below), find each batch's reduced basis nnz(B)
+ * (the relevance rule below), fit the radial splines, and upload everything to the device.
+ *   Batch-partition rule: split(S) with n = |S| and k = ceil(n/B); if k <= 1, S is a batch
+ *     (points kept in their current order); otherwise cut along the axis of largest
+ *     bounding-box extent (ties x < y < z), ordering S by (coordinate, point index), the
+ *     first floor(n*floor(k/2)/k) points going left; recurse left, then right.
+ *   Relevance rule: (A, f, m) is in nnz(B) iff some point of B has
+ *     (dx*dx + dy*dy) + dz*dz < rc_f*rc_f in separately rounded FP64 operations.
+ * desc, opts: host pointers (opts may be NULL for defaults). On success *out holds the new
+ * handle; on failure *out is set to NULL and nothing is leaked.
+ * Errors: NAO_ERR_INVALID_ARG (see nao_system_desc), NAO_ERR_OUT_OF_MEMORY, NAO_ERR_CUDA. */
+nao_status nao_grid_create(const nao_system_desc *desc, const nao_options *opts, nao_grid **out);
+
+/* Release the handle and all its device memory. NULL-safe. Synchronises the device work
+ * the handle has enqueued before freeing.                                                */
+nao_status nao_destroy(nao_grid *g);
+
+/* Sizes and algorithmic work counts of the handle. */
+nao_status nao_get_info(const nao_grid *g, nao_grid_info *info);
+
+/* Copy the partition and the reduced bases to caller-allocated HOST arrays:
+ * batch_offsets[n_batches+1], point_perm[n_points] (original index of each batch-ordered
+ * point), rel_offsets[n_batches+1], rel_idx[rel_total] (ascending global basis indices
+ * per batch). Any pointer may be NULL to skip that array.                                 */
+nao_status nao_export_batches(const nao_grid *g, int64_t *batch_offsets, int64_t *point_perm,
+                              int64_t *rel_offsets, int32_t *rel_idx);
+
+/* Hamiltonian integration (Eq. H_int_aims; Eqs. H_decomp, H_contrib_batch,
+ * batch_matrix_mult): H_dev[i*nb+j] = sum_p w_p [ phi_i v_p phi_j (if POTENTIAL)
+ *                                              + 1/2 grad phi_i . grad phi_j (if KINETIC) ].
+ * v_dev: device [n_points] in the caller's original point order, or NULL for v = 1.
+ * H_dev: device [nb*nb] row-major, overwritten (both triangles; exactly symmetric).
+ * terms: a non-empty subset of NAO_TERM_POTENTIAL | NAO_TERM_KINETIC.
+ * Errors: NAO_ERR_INVALID_ARG (NULL handle/H, bad terms or precision), NAO_ERR_CUDA,
+ * NAO_ERR_UNSUPPORTED (precision not built for this device).                               */
+nao_status nao_integrate_h(nao_grid *g, const double *v_dev, uint32_t terms, nao_precision prec,
+                           double *H_dev, void *cuda_stream);
+
+/* Density update (Eq. Density, Sec. 3.3.5): n_dev[p] = sum_ij phi_i(r_p) P_ij phi_j(r_p)
+ * for every point p (original order; 0 for points in batches without basis functions),
+ * and, if n_electrons_dev is not NULL, n_electrons_dev[0] = sum_p w_p n_p (FP64).
+ * P_dev: device [nb*nb] row-major, symmetric (only the upper triangle P[i][j], i <= j, is
+ * read). n_dev: device [n_points]. n_electrons_dev: device [1] or NULL.                    */
+nao_status nao_update_density(nao_grid *g, const double *P_dev, nao_precision prec, double *n_dev,
+                              double *n_electrons_dev, void *cuda_stream);
+
+/* The same two operations with HOST buffers: the library copies the inputs to the device,
+ * runs the operation on the given stream, copies the results back and synchronises the
+ * stream before returning. Host buffers may be pageable or pinned (pinned is faster).
+ * v_host may be NULL (v = 1); n_electrons_host may be NULL.                                */
+nao_status nao_integrate_h_host(nao_grid *g, const double *v_host, uint32_t terms, nao_precision prec,
+                                double *H_host, void *cuda_stream);
+nao_status nao_update_density_host(nao_grid *g, const double *P_host, nao_precision prec, double *n_host,
+                                   double *n_electrons_host, void *cuda_stream);
+
+/* Basis functions of one batch (Sec. 3.4, the evaluation phase), for parity checks:
+ * phi_dev[j*P_b + q] = phi_{rel_j}(r_q) and grad_dev[(c*N_b + j)*P_b + q] = d/dx_c of it,
+ * for the batch's q = 0..P_b-1 points in batch order and j = 0..N_b-1 reduced-basis
+ * positions. grad_dev may be NULL. prec selects the evaluation arithmetic
+ * (NAO_FP32 evaluates in FP32 and widens; NAO_FP64 and NAO_SPLIT evaluate in FP64).      */
+nao_status nao_evaluate_batch(nao_grid *g, int64_t batch, nao_precision prec, double *phi_dev, double *grad_dev,
+                              void *cuda_stream);
+
+/* Kernel timing. When enabled, every kernel launch the handle makes is bracketed by CUDA
+ * events recorded on the call's stream; nao_profile_read synchronises the device, converts
+ * the event pairs to milliseconds and returns per kernel family the number of launches and
+ * their summed duration (optionally resetting the record). Families are indexed by
+ * nao_kernel_id.                                                                         */
+typedef enum {
+    NAO_K_EVAL_GRAD = 0, /* phi and grad phi of a chunk of batches */
+    NAO_K_EVAL_PHI,      /* phi alone (density)                    */
+    NAO_K_H_FP64,        /* FP64 h[B] contraction + scatter into H */
+    NAO_K_H_FP32,        /* FP32 h[B] contraction + scatter        */
+    NAO_K_H_SPLIT,       /* tensor-core slice products + scatter   */
+    NAO_K_SLICE,         /* Ozaki slicing of evaluated functions    */
+    NAO_K_MIRROR,        /* upper -> lower triangle copy of H      */
+    NAO_K_N_FP64,        /* FP64 density contraction               */
+    NAO_K_N_FP32,        /* FP32 density contraction               */
+    NAO_K_N_SPLIT,       /* tensor-core density contraction        */
+    NAO_K_REDUCE,        /* electron-count reduction               */
+    NAO_K_COUNT
+} nao_kernel_id;
+
+typedef struct {
+    int64_t launches[NAO_K_COUNT];
+    double ms[NAO_K_COUNT];
+} nao_profile;
+
+nao_status nao_profile_enable(nao_grid *g, int32_t enable);
+nao_status nao_profile_read(nao_grid *g, nao_profile *out, int32_t reset);
+
+/* Wait for the handle's enqueued work and report a device-side failure, if any. */
+nao_status nao_sync_status(nao_grid *g);
+
+/* Static text for a status code. */
+const char *nao_status_string(nao_status s);
+
+/* Text of the most recent failure on the calling thread (empty if none). */
+const char *nao_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NAO_H */

@@ -302,36 +302,75 @@ int or_hamiltonian(const or_sys *S, int64_t n_pts, const double *pts, const doub
     return status;
 }
 
+/* phi and grad phi of the single basis function (atom a, radial function f, m) at p.
+ * Same formulas as point_basis; returns 0 or a negative status.                        */
+static int basis_one(const or_sys *S, int32_t a, int32_t f, int32_t m, const double p[3], double *phi, double g[3],
+                     int64_t *pole_count) {
+    double dx = p[0] - S->atom_xyz[3 * a + 0];
+    double dy = p[1] - S->atom_xyz[3 * a + 1];
+    double dz = p[2] - S->atom_xyz[3 * a + 2];
+    double r = sqrt(dx * dx + dy * dy + dz * dz);
+    *phi = 0.0; g[0] = g[1] = g[2] = 0.0;
+    if (!(r < S->fn_cutoff[f])) return 0;
+    if (r == 0.0) return -2;
+    double theta = acos(dz / r), ph = atan2(dy, dx);
+    double st = sin(theta), ct = cos(theta), sp_ = sin(ph), cp = cos(ph);
+    if (st < 1e-12) { (*pole_count)++; return -3; }
+    int l = S->fn_l[f];
+    double R, dR;
+    or_radial(S, f, r, &R, &dR);
+    double Y[2 * OR_LMAX + 1], dYt[2 * OR_LMAX + 1], dYp[2 * OR_LMAX + 1];
+    ylm_sph(l, theta, ph, Y, dYt, dYp);
+    double rh[3] = {st * cp, st * sp_, ct};
+    double th[3] = {ct * cp, ct * sp_, -st};
+    double fh[3] = {-sp_, cp, 0.0};
+    int k = m + l;
+    *phi = R * Y[k];
+    for (int c = 0; c < 3; c++) g[c] = dR * Y[k] * rh[c] + (R / r) * (dYt[k] * th[c] + dYp[k] * fh[c]);
+    return 0;
+}
+
 /* H and A restricted to a list of basis functions F (the block H[F,F]), from the same
- * definition: every point is visited and phi is evaluated for the listed functions only. */
+ * definition: every point is visited and only the listed functions are evaluated.       */
 int or_hamiltonian_block(const or_sys *S, int64_t n_pts, const double *pts, const double *w, const double *v,
                          uint32_t terms, int32_t nF, const int64_t *F, double *H, double *A, int64_t *pole_count) {
     int64_t nb = or_n_basis(S);
     size_t nn = (size_t)nF * (size_t)nF;
     double *Hc = (double *)calloc(nn ? nn : 1, sizeof(double));
     double *Ac = (double *)calloc(nn ? nn : 1, sizeof(double));
-    int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nb ? nb : 1));
-    double *phi = (double *)malloc(sizeof(double) * (size_t)(nb ? nb : 1));
-    double *grad = (double *)malloc(sizeof(double) * 3 * (size_t)(nb ? nb : 1));
-    int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nb ? nb : 1));
+    int32_t *fa = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nF ? nF : 1));
+    int32_t *ff = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nF ? nF : 1));
+    int32_t *fm = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nF ? nF : 1));
     double *fp = (double *)malloc(sizeof(double) * (size_t)(nF ? nF : 1));
     double *fg = (double *)malloc(sizeof(double) * 3 * (size_t)(nF ? nF : 1));
-    if (!Hc || !Ac || !idx || !phi || !grad || !pos || !fp || !fg) {
-        free(Hc); free(Ac); free(idx); free(phi); free(grad); free(pos); free(fp); free(fg); return -1;
+    if (!Hc || !Ac || !fa || !ff || !fm || !fp || !fg) {
+        free(Hc); free(Ac); free(fa); free(ff); free(fm); free(fp); free(fg); return -1;
+    }
+    /* decode each listed index into (atom, radial function, m) by walking the basis order */
+    for (int32_t q = 0; q < nF; q++) {
+        int64_t base = 0;
+        fa[q] = -1;
+        for (int32_t a = 0; a < S->n_atoms && fa[q] < 0; a++) {
+            int32_t sp = S->atom_species[a];
+            for (int32_t f = S->species_fn_offset[sp]; f < S->species_fn_offset[sp + 1]; f++) {
+                int nm = 2 * S->fn_l[f] + 1;
+                if (F[q] >= base && F[q] < base + nm) { fa[q] = a; ff[q] = f; fm[q] = (int32_t)(F[q] - base) - S->fn_l[f]; break; }
+                base += nm;
+            }
+        }
+        if (fa[q] < 0 || F[q] >= nb) { free(Hc); free(Ac); free(fa); free(ff); free(fm); free(fp); free(fg); return -1; }
     }
     memset(H, 0, nn * sizeof(double));
     memset(A, 0, nn * sizeof(double));
     int pot = (terms & 1u) != 0, kin = (terms & 2u) != 0;
     int status = 0;
-    for (int64_t p = 0; p < n_pts; p++) {
-        int64_t cnt = point_basis(S, pts + 3 * p, idx, phi, grad, pole_count, 1);
-        if (cnt < 0) { status = (int)cnt; break; }
-        for (int32_t a = 0; a < nF; a++) {
-            fp[a] = phi[F[a]];
-            fg[3 * a] = grad[3 * F[a]]; fg[3 * a + 1] = grad[3 * F[a] + 1]; fg[3 * a + 2] = grad[3 * F[a] + 2];
-        }
+    for (int64_t p = 0; p < n_pts && !status; p++) {
+        for (int32_t q = 0; q < nF && !status; q++)
+            status = basis_one(S, fa[q], ff[q], fm[q], pts + 3 * p, &fp[q], &fg[3 * q], pole_count);
+        if (status) break;
         double wp = w[p], vp = v ? v[p] : 1.0;
         for (int32_t a = 0; a < nF; a++) {
+            if (fp[a] == 0.0 && fg[3 * a] == 0.0 && fg[3 * a + 1] == 0.0 && fg[3 * a + 2] == 0.0) continue;
             for (int32_t b = 0; b < nF; b++) {
                 double tv = pot ? wp * (fp[a] * vp * fp[b]) : 0.0;
                 double gg = fg[3 * a] * fg[3 * b] + fg[3 * a + 1] * fg[3 * b + 1] + fg[3 * a + 2] * fg[3 * b + 2];
@@ -343,7 +382,7 @@ int or_hamiltonian_block(const or_sys *S, int64_t n_pts, const double *pts, cons
         }
     }
     for (size_t e = 0; e < nn; e++) { H[e] += Hc[e]; A[e] += Ac[e]; }
-    free(Hc); free(Ac); free(idx); free(phi); free(grad); free(pos); free(fp); free(fg);
+    free(Hc); free(Ac); free(fa); free(ff); free(fm); free(fp); free(fg);
     return status;
 }
 

@@ -1,0 +1,617 @@
+// C ABI of libnao (see include/nao.h): validation, set-up of a grid handle, and the
+// per-call dispatch of the evaluation and contraction kernels onto the caller's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "nao_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+nao_status fail(nao_status s, const std::string &msg) {
+    g_last_error = msg;
+    return s;
+}
+
+nao_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(NAO_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define NAO_CUDA(expr)                                     \
+    do {                                                   \
+        cudaError_t e_ = (expr);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #expr); \
+    } while (0)
+
+// Makes g's device current for the lifetime of the guard and restores the caller's.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { prev = -1; ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <class T>
+nao_status dev_alloc(nao_grid *g, T **p, size_t count) {
+    void *q = nullptr;
+    const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    const cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(NAO_ERR_OUT_OF_MEMORY, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    g->allocs.push_back(q);
+    g->dev_bytes += (int64_t)bytes;
+    *p = static_cast<T *>(q);
+    return NAO_OK;
+}
+
+template <class T>
+nao_status upload(nao_grid *g, T **p, const T *src, size_t count) {
+    nao_status st = dev_alloc(g, p, count);
+    if (st != NAO_OK) return st;
+    if (count) NAO_CUDA(cudaMemcpy(*p, src, count * sizeof(T), cudaMemcpyHostToDevice));
+    return NAO_OK;
+}
+
+void free_grid(nao_grid *g) {
+    if (!g) return;
+    for (auto &t : g->timed) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    for (cudaEvent_t e : g->event_pool) cudaEventDestroy(e);
+    for (void *p : g->allocs) cudaFree(p);
+    delete g;
+}
+
+double factorial(int n) {
+    double f = 1.0;
+    for (int i = 2; i <= n; i++) f *= (double)i;
+    return f;
+}
+
+inline bool finite(double x) { return std::isfinite(x); }
+
+nao_status validate(const nao_system_desc *d, const nao_options &o) {
+    if (!d) return fail(NAO_ERR_INVALID_ARG, "desc is NULL");
+    if (d->n_atoms < 1 || !d->atom_xyz || !d->atom_species) return fail(NAO_ERR_INVALID_ARG, "no atoms");
+    if (d->n_species < 1 || !d->species_fn_offset || !d->fn_l || !d->fn_cutoff || !d->fn_table)
+        return fail(NAO_ERR_INVALID_ARG, "no species or radial functions");
+    if (d->n_rgrid < 4) return fail(NAO_ERR_INVALID_ARG, "n_rgrid < 4");
+    if (!(d->r0 > 0.0) || !(d->r_last > d->r0) || !finite(d->r_last)) return fail(NAO_ERR_INVALID_ARG, "bad r0/r_last");
+    if (d->n_points < 1 || d->n_points >= (int64_t(1) << 31) || !d->pt_xyz || !d->pt_w)
+        return fail(NAO_ERR_INVALID_ARG, "bad points");
+    if (o.max_batch_points < 1 || o.max_batch_points > NAO_MAX_BATCH)
+        return fail(NAO_ERR_INVALID_ARG, "max_batch_points must be in 1.." + std::to_string(NAO_MAX_BATCH));
+    if (o.split_slices < 4 || o.split_slices > 10) return fail(NAO_ERR_INVALID_ARG, "split_slices must be in 4..10");
+    if (d->species_fn_offset[0] != 0) return fail(NAO_ERR_INVALID_ARG, "species_fn_offset[0] != 0");
+    for (int s = 0; s < d->n_species; s++)
+        if (d->species_fn_offset[s + 1] < d->species_fn_offset[s])
+            return fail(NAO_ERR_INVALID_ARG, "species_fn_offset not ascending");
+    const int n_fn = d->species_fn_offset[d->n_species];
+    for (int f = 0; f < n_fn; f++) {
+        if (d->fn_l[f] < 0 || d->fn_l[f] > NAO_LMAX) return fail(NAO_ERR_INVALID_ARG, "fn_l outside 0..6");
+        if (!(d->fn_cutoff[f] > 0.0) || !(d->fn_cutoff[f] <= d->r_last))
+            return fail(NAO_ERR_INVALID_ARG, "fn_cutoff outside (0, r_last]");
+    }
+    for (int64_t k = 0; k < (int64_t)n_fn * d->n_rgrid; k++)
+        if (!finite(d->fn_table[k])) return fail(NAO_ERR_INVALID_ARG, "non-finite fn_table entry");
+    for (int a = 0; a < d->n_atoms; a++) {
+        if (d->atom_species[a] < 0 || d->atom_species[a] >= d->n_species)
+            return fail(NAO_ERR_INVALID_ARG, "atom_species out of range");
+        for (int c = 0; c < 3; c++)
+            if (!finite(d->atom_xyz[3 * a + c])) return fail(NAO_ERR_INVALID_ARG, "non-finite atom coordinate");
+    }
+    for (int64_t p = 0; p < d->n_points; p++) {
+        if (!finite(d->pt_xyz[3 * p]) || !finite(d->pt_xyz[3 * p + 1]) || !finite(d->pt_xyz[3 * p + 2]) ||
+            !finite(d->pt_w[p]))
+            return fail(NAO_ERR_INVALID_ARG, "non-finite point or weight");
+    }
+    return NAO_OK;
+}
+
+nao_status build(nao_grid *g, const nao_system_desc *d) {
+    const int64_t n = d->n_points;
+    g->n_atoms = d->n_atoms;
+    g->n_species = d->n_species;
+    g->n_fn = d->species_fn_offset[d->n_species];
+    g->n_rgrid = d->n_rgrid;
+    g->r0 = d->r0;
+    g->r_last = d->r_last;
+    g->delta = std::log(d->r_last / d->r0) / (double)(d->n_rgrid - 1);
+    g->n_points = n;
+
+    // basis functions per atom (atom, species radial function, m)
+    std::vector<int64_t> atom_basis(d->n_atoms + 1, 0);
+    for (int a = 0; a < d->n_atoms; a++) {
+        const int sp = d->atom_species[a];
+        int64_t c = 0;
+        for (int f = d->species_fn_offset[sp]; f < d->species_fn_offset[sp + 1]; f++) c += 2 * d->fn_l[f] + 1;
+        atom_basis[a + 1] = atom_basis[a] + c;
+    }
+    g->nb = atom_basis[d->n_atoms];
+    if (g->nb < 1) return fail(NAO_ERR_INVALID_ARG, "no basis functions");
+    if (g->nb >= (int64_t(1) << 31)) return fail(NAO_ERR_INVALID_ARG, "too many basis functions");
+
+    // Sec. 3.3.1: batches
+    g->n_batches = nao_partition(n, d->pt_xyz, g->opt.max_batch_points, g->batch_off, g->perm);
+    const int64_t nbat = g->n_batches;
+
+    // points in batch order, structure of arrays
+    std::vector<double> px(n), py(n), pz(n), pw(n);
+    std::vector<int32_t> perm32(n), boff32(nbat + 1);
+    for (int64_t i = 0; i < n; i++) {
+        const int64_t p = g->perm[i];
+        px[i] = d->pt_xyz[3 * p];
+        py[i] = d->pt_xyz[3 * p + 1];
+        pz[i] = d->pt_xyz[3 * p + 2];
+        pw[i] = d->pt_w[p];
+        perm32[i] = (int32_t)p;
+    }
+    for (int64_t b = 0; b <= nbat; b++) boff32[b] = (int32_t)g->batch_off[b];
+
+    nao_status st;
+    double *d_px, *d_py, *d_pz, *d_pw, *d_atoms;
+    int32_t *d_perm, *d_boff;
+    if ((st = upload(g, &d_px, px.data(), n)) || (st = upload(g, &d_py, py.data(), n)) ||
+        (st = upload(g, &d_pz, pz.data(), n)) || (st = upload(g, &d_pw, pw.data(), n)) ||
+        (st = upload(g, &d_perm, perm32.data(), n)) || (st = upload(g, &d_boff, boff32.data(), nbat + 1)) ||
+        (st = upload(g, &d_atoms, d->atom_xyz, 3 * (size_t)d->n_atoms)))
+        return st;
+
+    // Sec. 3.3.2: nnz(B) from the per-(batch, atom) minimum distance
+    std::vector<double> minr2((size_t)nbat * d->n_atoms);
+    {
+        double *d_minr2;
+        if ((st = dev_alloc(g, &d_minr2, minr2.size()))) return st;
+        NAO_CUDA(launch_relevance_minr2(d_atoms, d->n_atoms, d_px, d_py, d_pz, d_boff, nbat, d_minr2, 0));
+        NAO_CUDA(cudaMemcpy(minr2.data(), d_minr2, minr2.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        cudaFree(d_minr2);
+        g->allocs.pop_back();
+        g->dev_bytes -= (int64_t)std::max<size_t>(minr2.size() * sizeof(double), 16);
+    }
+    for (double m : minr2)
+        if (m == 0.0) return fail(NAO_ERR_INVALID_ARG, "a grid point coincides with a nucleus");
+
+    std::vector<RfnEntry> rfn;
+    std::vector<int32_t> rfn_off32(nbat + 1, 0), rel_off32(nbat + 1, 0);
+    g->rel_off.assign(nbat + 1, 0);
+    g->Pb.resize(nbat);
+    g->Nb.resize(nbat);
+    for (int64_t b = 0; b < nbat; b++) {
+        int32_t pos = 0;
+        for (int a = 0; a < d->n_atoms; a++) {
+            const int sp = d->atom_species[a];
+            const double m2 = minr2[(size_t)b * d->n_atoms + a];
+            int64_t base = atom_basis[a];
+            for (int f = d->species_fn_offset[sp]; f < d->species_fn_offset[sp + 1]; f++) {
+                const int l = d->fn_l[f];
+                const double rc = d->fn_cutoff[f];
+                if (m2 < rc * rc) {
+                    rfn.push_back({a, f, pos, l});
+                    for (int m = 0; m < 2 * l + 1; m++) g->rel_idx.push_back((int32_t)(base + m));
+                    pos += 2 * l + 1;
+                }
+                base += 2 * l + 1;
+            }
+        }
+        g->rel_off[b + 1] = (int64_t)g->rel_idx.size();
+        rfn_off32[b + 1] = (int32_t)rfn.size();
+        g->Pb[b] = (int32_t)(g->batch_off[b + 1] - g->batch_off[b]);
+        g->Nb[b] = pos;
+        g->max_P = std::max(g->max_P, g->Pb[b]);
+        g->max_N = std::max(g->max_N, pos);
+        const double P = g->Pb[b], N = pos;
+        g->flops_h += (int64_t)(4.0 * P * N * (N + 1.0));
+        g->flops_n += (int64_t)(2.0 * P * N * N + 2.0 * P * N);
+    }
+    g->rel_total = (int64_t)g->rel_idx.size();
+    g->rfn_total = (int64_t)rfn.size();
+    if (g->rel_total >= (int64_t(1) << 31)) return fail(NAO_ERR_UNSUPPORTED, "reduced bases too large");
+    for (int64_t b = 0; b <= nbat; b++) rel_off32[b] = (int32_t)g->rel_off[b];
+
+    // radial splines
+    std::vector<double> coef((size_t)g->n_fn * (d->n_rgrid - 1) * 4);
+    for (int f = 0; f < g->n_fn; f++)
+        nao_spline_coefficients(d->fn_table + (size_t)f * d->n_rgrid, d->n_rgrid,
+                                coef.data() + (size_t)f * (d->n_rgrid - 1) * 4);
+    std::vector<float> coef32(coef.begin(), coef.end());
+
+    // work lists and chunks of batches that fit the scratch
+    std::vector<HWork> hw;
+    std::vector<DWork> dw;
+    std::vector<int64_t> scr_off(nbat, 0);
+    int64_t budget = (g->opt.scratch_bytes > 0 ? g->opt.scratch_bytes : (int64_t(2) << 30)) / (int64_t)sizeof(double);
+    int64_t need_max = 0, need_total = 0;
+    for (int64_t b = 0; b < nbat; b++) {
+        const int64_t Ppad = (g->Pb[b] + NAO_PPAD - 1) / NAO_PPAD * NAO_PPAD;
+        const int64_t e = (int64_t)g->Nb[b] * 4 * Ppad;
+        need_max = std::max(need_max, e);
+        need_total += e;
+    }
+    budget = std::max(budget, need_max);
+    budget = std::min(budget, std::max<int64_t>(need_total, 16));
+    Chunk cur{0, 0, 0, 0, 0, 0};
+    int64_t used = 0;
+    for (int64_t b = 0; b < nbat; b++) {
+        const int64_t Ppad = (g->Pb[b] + NAO_PPAD - 1) / NAO_PPAD * NAO_PPAD;
+        const int64_t e = (int64_t)g->Nb[b] * 4 * Ppad;
+        if (used + e > budget && b > cur.b0) {
+            cur.b1 = (int32_t)b;
+            cur.hw1 = (int32_t)hw.size();
+            cur.dw1 = (int32_t)dw.size();
+            g->chunks.push_back(cur);
+            cur = Chunk{(int32_t)b, 0, (int32_t)hw.size(), 0, (int32_t)dw.size(), 0};
+            used = 0;
+        }
+        scr_off[b] = used;
+        used += e;
+        const int nt = (g->Nb[b] + NAO_TILE - 1) / NAO_TILE;
+        for (int i = 0; i < nt; i++)
+            for (int j = i; j < nt; j++) hw.push_back({(int32_t)b, i, j, 0});
+        const int np = (g->Pb[b] + NAO_TILE - 1) / NAO_TILE;
+        for (int t = 0; t < np; t++) dw.push_back({(int32_t)b, t});
+    }
+    cur.b1 = (int32_t)nbat;
+    cur.hw1 = (int32_t)hw.size();
+    cur.dw1 = (int32_t)dw.size();
+    g->chunks.push_back(cur);
+    g->scratch_elems = budget;
+    g->n_hwork = (int64_t)hw.size();
+    g->n_dwork = (int64_t)dw.size();
+
+    double *d_coef, *d_rc;
+    float *d_coef32;
+    int32_t *d_rel_off, *d_rel_idx, *d_rfn_off;
+    RfnEntry *d_rfn;
+    int64_t *d_scr_off;
+    if ((st = upload(g, &d_coef, coef.data(), coef.size())) || (st = upload(g, &d_coef32, coef32.data(), coef32.size())) ||
+        (st = upload(g, &d_rc, d->fn_cutoff, (size_t)g->n_fn)) ||
+        (st = upload(g, &d_rel_off, rel_off32.data(), rel_off32.size())) ||
+        (st = upload(g, &d_rel_idx, g->rel_idx.data(), g->rel_idx.size())) ||
+        (st = upload(g, &d_rfn_off, rfn_off32.data(), rfn_off32.size())) ||
+        (st = upload(g, &d_rfn, rfn.data(), rfn.size())) || (st = upload(g, &d_scr_off, scr_off.data(), scr_off.size())) ||
+        (st = upload(g, &g->d_hwork, hw.data(), hw.size())) || (st = upload(g, &g->d_dwork, dw.data(), dw.size())) ||
+        (st = dev_alloc(g, &g->d_scratch, (size_t)g->scratch_elems)) ||
+        (st = dev_alloc(g, &g->d_ne_part, (size_t)std::max<int64_t>(g->n_dwork, 1))) ||
+        (st = dev_alloc(g, &g->d_err, 4)))
+        return st;
+    NAO_CUDA(cudaMemset(g->d_err, 0, 4 * sizeof(int32_t)));
+
+    DevSystem &s = g->sys;
+    s.atom_xyz = d_atoms;
+    s.coef = d_coef;
+    s.coef_f32 = d_coef32;
+    s.fn_rc = d_rc;
+    s.px = d_px;
+    s.py = d_py;
+    s.pz = d_pz;
+    s.pw = d_pw;
+    s.perm = d_perm;
+    s.batch_off = d_boff;
+    s.rel_off = d_rel_off;
+    s.rel_idx = d_rel_idx;
+    s.rfn_off = d_rfn_off;
+    s.rfn = d_rfn;
+    s.scr_off = d_scr_off;
+    s.n_rgrid = d->n_rgrid;
+    s.r0 = d->r0;
+    s.inv_delta = 1.0 / g->delta;
+    s.nb = g->nb;
+    for (int l = 0; l <= NAO_LMAX; l++)
+        for (int m = 0; m <= NAO_LMAX; m++) {
+            double k = 0.0;
+            if (m <= l) {
+                k = std::sqrt((2.0 * l + 1.0) / (4.0 * M_PI) * factorial(l - m) / factorial(l + m));
+                if (m > 0) k *= std::sqrt(2.0);
+            }
+            s.knorm[l][m] = k;
+        }
+    NAO_CUDA(cudaDeviceSynchronize());
+    return NAO_OK;
+}
+
+cudaEvent_t take_event(nao_grid *g) {
+    if (!g->event_pool.empty()) {
+        cudaEvent_t e = g->event_pool.back();
+        g->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Runs one launcher; when profiling, brackets it with events on the stream.
+template <class F>
+cudaError_t timed(nao_grid *g, int kid, cudaStream_t st, F &&launch) {
+    if (!g->profiling) return launch();
+    cudaEvent_t a = take_event(g), b = take_event(g);
+    if (!a || !b) return launch();
+    cudaEventRecord(a, st);
+    const cudaError_t e = launch();
+    cudaEventRecord(b, st);
+    g->timed.push_back({kid, a, b});
+    return e;
+}
+
+nao_status check_handle(const nao_grid *g) {
+    if (!g) return fail(NAO_ERR_INVALID_ARG, "handle is NULL");
+    return NAO_OK;
+}
+
+nao_status check_prec(nao_precision p) {
+    if (p != NAO_FP64 && p != NAO_FP32 && p != NAO_SPLIT) return fail(NAO_ERR_INVALID_ARG, "unknown precision");
+    if (p != NAO_FP64) return fail(NAO_ERR_UNSUPPORTED, "precision not available in this build");
+    return NAO_OK;
+}
+
+nao_status run_h(nao_grid *g, const double *v, uint32_t terms, nao_precision prec, double *H, cudaStream_t st) {
+    const DevSystem &s = g->sys;
+    NAO_CUDA(cudaMemsetAsync(H, 0, (size_t)g->nb * g->nb * sizeof(double), st));
+    for (const Chunk &c : g->chunks) {
+        NAO_CUDA(timed(g, NAO_K_EVAL_GRAD, st, [&] { return launch_eval(s, c.b0, c.b1, prec, true, g->d_scratch, st); }));
+        NAO_CUDA(timed(g, NAO_K_H_FP64, st, [&] {
+            return launch_h_f64(s, g->d_hwork + c.hw0, c.hw1 - c.hw0, g->d_scratch, v, terms, H, st);
+        }));
+    }
+    NAO_CUDA(timed(g, NAO_K_MIRROR, st, [&] { return launch_mirror(H, g->nb, st); }));
+    return NAO_OK;
+}
+
+nao_status run_n(nao_grid *g, const double *P, nao_precision prec, double *n, double *ne, cudaStream_t st) {
+    const DevSystem &s = g->sys;
+    for (const Chunk &c : g->chunks) {
+        NAO_CUDA(timed(g, NAO_K_EVAL_PHI, st, [&] { return launch_eval(s, c.b0, c.b1, prec, false, g->d_scratch, st); }));
+        NAO_CUDA(timed(g, NAO_K_N_FP64, st, [&] {
+            return launch_density_f64(s, g->d_dwork, c.dw0, c.dw1 - c.dw0, g->d_scratch, P, n, g->d_ne_part, st);
+        }));
+    }
+    if (ne) NAO_CUDA(timed(g, NAO_K_REDUCE, st, [&] { return launch_reduce_sum(g->d_ne_part, g->n_dwork, ne, st); }));
+    return NAO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nao_status nao_default_options(nao_options *o) {
+    if (!o) return fail(NAO_ERR_INVALID_ARG, "opts is NULL");
+    std::memset(o, 0, sizeof(*o));
+    o->max_batch_points = 200;
+    o->split_slices = 8;
+    o->deterministic = 0;
+    o->device = -1;
+    o->scratch_bytes = 0;
+    return NAO_OK;
+}
+
+nao_status nao_grid_create(const nao_system_desc *desc, const nao_options *opts, nao_grid **out) {
+    if (!out) return fail(NAO_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    nao_options o;
+    nao_default_options(&o);
+    if (opts) o = *opts;
+    nao_status st = validate(desc, o);
+    if (st != NAO_OK) return st;
+    int dev = o.device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return fail(NAO_ERR_CUDA, "no CUDA device");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || dev >= ndev) {
+        cudaGetLastError();
+        return fail(NAO_ERR_INVALID_ARG, "bad device ordinal");
+    }
+    DeviceGuard guard(dev);
+    if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    nao_grid *g = new (std::nothrow) nao_grid();
+    if (!g) return fail(NAO_ERR_OUT_OF_MEMORY, "host allocation failed");
+    g->device = dev;
+    g->opt = o;
+    g->opt.device = dev;
+    try {
+        st = build(g, desc);
+    } catch (const std::bad_alloc &) {
+        st = fail(NAO_ERR_OUT_OF_MEMORY, "host allocation failed");
+    } catch (...) {
+        st = fail(NAO_ERR_INTERNAL, "unexpected host exception");
+    }
+    if (st != NAO_OK) {
+        free_grid(g);
+        return st;
+    }
+    *out = g;
+    return NAO_OK;
+}
+
+nao_status nao_destroy(nao_grid *g) {
+    if (!g) return NAO_OK;
+    DeviceGuard guard(g->device);
+    cudaDeviceSynchronize();
+    free_grid(g);
+    return NAO_OK;
+}
+
+nao_status nao_get_info(const nao_grid *g, nao_grid_info *info) {
+    nao_status st = check_handle(g);
+    if (st) return st;
+    if (!info) return fail(NAO_ERR_INVALID_ARG, "info is NULL");
+    info->n_basis = g->nb;
+    info->n_points = g->n_points;
+    info->n_batches = g->n_batches;
+    info->rel_total = g->rel_total;
+    info->max_batch_points = g->max_P;
+    info->max_batch_basis = g->max_N;
+    info->device_bytes = g->dev_bytes;
+    info->flops_h = g->flops_h;
+    info->flops_n = g->flops_n;
+    return NAO_OK;
+}
+
+nao_status nao_export_batches(const nao_grid *g, int64_t *batch_offsets, int64_t *point_perm, int64_t *rel_offsets,
+                              int32_t *rel_idx) {
+    nao_status st = check_handle(g);
+    if (st) return st;
+    if (batch_offsets) std::memcpy(batch_offsets, g->batch_off.data(), g->batch_off.size() * sizeof(int64_t));
+    if (point_perm) std::memcpy(point_perm, g->perm.data(), g->perm.size() * sizeof(int64_t));
+    if (rel_offsets) std::memcpy(rel_offsets, g->rel_off.data(), g->rel_off.size() * sizeof(int64_t));
+    if (rel_idx && g->rel_total) std::memcpy(rel_idx, g->rel_idx.data(), g->rel_idx.size() * sizeof(int32_t));
+    return NAO_OK;
+}
+
+nao_status nao_integrate_h(nao_grid *g, const double *v_dev, uint32_t terms, nao_precision prec, double *H_dev,
+                           void *cuda_stream) {
+    nao_status st = check_handle(g);
+    if (st) return st;
+    if (!H_dev) return fail(NAO_ERR_INVALID_ARG, "H_dev is NULL");
+    if (terms == 0 || (terms & ~3u)) return fail(NAO_ERR_INVALID_ARG, "bad terms");
+    if ((st = check_prec(prec))) return st;
+    DeviceGuard guard(g->device);
+    if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    return run_h(g, v_dev, terms, prec, H_dev, static_cast<cudaStream_t>(cuda_stream));
+}
+
+nao_status nao_update_density(nao_grid *g, const double *P_dev, nao_precision prec, double *n_dev,
+                              double *n_electrons_dev, void *cuda_stream) {
+    nao_status st = check_handle(g);
+    if (st) return st;
+    if (!P_dev || !n_dev) return fail(NAO_ERR_INVALID_ARG, "P_dev or n_dev is NULL");
+    if ((st = check_prec(prec))) return st;
+    DeviceGuard guard(g->device);
+    if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    return run_n(g, P_dev, prec, n_dev, n_electrons_dev, static_cast<cudaStream_t>(cuda_stream));
+}
+
+static nao_status ensure_staging(nao_grid *g) {
+    if (g->d_stage_in) return NAO_OK;
+    const size_t big = (size_t)std::max<int64_t>(g->nb * g->nb, g->n_points);
+    nao_status st;
+    if ((st = dev_alloc(g, &g->d_stage_in, big)) || (st = dev_alloc(g, &g->d_stage_out, big)) ||
+        (st = dev_alloc(g, &g->d_stage_ne, 1)))
+        return st;
+    return NAO_OK;
+}
+
+nao_status nao_integrate_h_host(nao_grid *g, const double *v_host, uint32_t terms, nao_precision prec, double *H_host,
+                                void *cuda_stream) {
+    nao_status st = check_handle(g);
+    if (st) return st;
+    if (!H_host) return fail(NAO_ERR_INVALID_ARG, "H_host is NULL");
+    if (terms == 0 || (terms & ~3u)) return fail(NAO_ERR_INVALID_ARG, "bad terms");
+    if ((st = check_prec(prec))) return st;
+    DeviceGuard guard(g->device);
+    if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    if ((st = ensure_staging(g))) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const double *v = nullptr;
+    if (v_host) {
+        NAO_CUDA(cudaMemcpyAsync(g->d_stage_in, v_host, (size_t)g->n_points * sizeof(double), cudaMemcpyHostToDevice, s));
+        v = g->d_stage_in;
+    }
+    if ((st = run_h(g, v, terms, prec, g->d_stage_out, s))) return st;
+    NAO_CUDA(cudaMemcpyAsync(H_host, g->d_stage_out, (size_t)g->nb * g->nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+    NAO_CUDA(cudaStreamSynchronize(s));
+    return NAO_OK;
+}
+
+nao_status nao_update_density_host(nao_grid *g, const double *P_host, nao_precision prec, double *n_host,
+                                   double *n_electrons_host, void *cuda_stream) {
+    nao_status st = check_handle(g);
+    if (st) return st;
+    if (!P_host || !n_host) return fail(NAO_ERR_INVALID_ARG, "P_host or n_host is NULL");
+    if ((st = check_prec(prec))) return st;
+    DeviceGuard guard(g->device);
+    if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    if ((st = ensure_staging(g))) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    NAO_CUDA(cudaMemcpyAsync(g->d_stage_in, P_host, (size_t)g->nb * g->nb * sizeof(double), cudaMemcpyHostToDevice, s));
+    if ((st = run_n(g, g->d_stage_in, prec, g->d_stage_out, n_electrons_host ? g->d_stage_ne : nullptr, s))) return st;
+    NAO_CUDA(cudaMemcpyAsync(n_host, g->d_stage_out, (size_t)g->n_points * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (n_electrons_host)
+        NAO_CUDA(cudaMemcpyAsync(n_electrons_host, g->d_stage_ne, sizeof(double), cudaMemcpyDeviceToHost, s));
+    NAO_CUDA(cudaStreamSynchronize(s));
+    return NAO_OK;
+}
+
+nao_status nao_evaluate_batch(nao_grid *g, int64_t batch, nao_precision prec, double *phi_dev, double *grad_dev,
+                              void *cuda_stream) {
+    nao_status st = check_handle(g);
+    if (st) return st;
+    if (batch < 0 || batch >= g->n_batches) return fail(NAO_ERR_INVALID_ARG, "batch out of range");
+    if (!phi_dev) return fail(NAO_ERR_INVALID_ARG, "phi_dev is NULL");
+    if ((st = check_prec(prec))) return st;
+    DeviceGuard guard(g->device);
+    if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    NAO_CUDA(launch_eval_one(g->sys, (int32_t)batch, prec, phi_dev, grad_dev, static_cast<cudaStream_t>(cuda_stream)));
+    return NAO_OK;
+}
+
+nao_status nao_profile_enable(nao_grid *g, int32_t enable) {
+    nao_status st = check_handle(g);
+    if (st) return st;
+    g->profiling = enable != 0;
+    return NAO_OK;
+}
+
+nao_status nao_profile_read(nao_grid *g, nao_profile *out, int32_t reset) {
+    nao_status st = check_handle(g);
+    if (st) return st;
+    DeviceGuard guard(g->device);
+    NAO_CUDA(cudaDeviceSynchronize());
+    for (auto &t : g->timed) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+            g->prof.ms[t.kid] += ms;
+            g->prof.launches[t.kid] += 1;
+        } else {
+            cudaGetLastError();
+        }
+        g->event_pool.push_back(t.a);
+        g->event_pool.push_back(t.b);
+    }
+    g->timed.clear();
+    if (out) *out = g->prof;
+    if (reset) g->prof = nao_profile{};
+    return NAO_OK;
+}
+
+nao_status nao_sync_status(nao_grid *g) {
+    nao_status st = check_handle(g);
+    if (st) return st;
+    DeviceGuard guard(g->device);
+    NAO_CUDA(cudaDeviceSynchronize());
+    int32_t err[4] = {0, 0, 0, 0};
+    NAO_CUDA(cudaMemcpy(err, g->d_err, sizeof(err), cudaMemcpyDeviceToHost));
+    if (err[0] != 0) return fail((nao_status)err[0], "device-side check failed (code " + std::to_string(err[1]) + ")");
+    return NAO_OK;
+}
+
+const char *nao_status_string(nao_status s) {
+    switch (s) {
+        case NAO_OK: return "ok";
+        case NAO_ERR_INVALID_ARG: return "invalid argument";
+        case NAO_ERR_OUT_OF_MEMORY: return "out of memory";
+        case NAO_ERR_CUDA: return "CUDA error";
+        case NAO_ERR_TIMEOUT: return "device wait timed out";
+        case NAO_ERR_INTERNAL: return "internal error";
+        case NAO_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char *nao_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,113 @@
+// Internal declarations of libnao: the handle, kernel argument blocks and launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "nao.h"
+
+#define NAO_LMAX 6
+#define NAO_TILE 64          // tile edge of the SIMT contractions (basis functions and points)
+#define NAO_PPAD 16          // batch points are padded to a multiple of this in scratch
+#define NAO_MAX_BATCH 1024   // largest accepted max_batch_points
+
+// One radial function instance relevant to a batch: atom, radial function, position of
+// its m = -l entry in the batch's reduced basis, l.
+struct RfnEntry {
+    int32_t atom, fn, pos, l;
+};
+
+// Geometry and tables shared by every kernel (device pointers).
+struct DevSystem {
+    const double *atom_xyz;   // [n_atoms*3]
+    const double *coef;       // [n_fn][n_rgrid-1][4] spline coefficients in t
+    const float *coef_f32;    // same in FP32
+    const double *fn_rc;      // [n_fn]
+    const double *px, *py, *pz, *pw;  // points in batch order
+    const int32_t *perm;      // batch order -> original index
+    const int32_t *batch_off; // [n_batches+1]
+    const int32_t *rel_off;   // [n_batches+1]
+    const int32_t *rel_idx;   // [rel_total]
+    const int32_t *rfn_off;   // [n_batches+1]
+    const RfnEntry *rfn;      // [rfn_total]
+    const int64_t *scr_off;   // [n_batches] element offset of the batch's block in scratch
+    int32_t n_rgrid;
+    double r0, inv_delta;
+    int64_t nb;
+    double knorm[NAO_LMAX + 1][NAO_LMAX + 1];  // sqrt((2l+1)/(4pi) (l-m)!/(l+m)!) (x sqrt2 for m>0)
+};
+
+struct HWork {  // one upper-triangular tile pair of one batch's h[B] (Eq. batch_matrix_mult)
+    int32_t batch, ti, tj, pad;
+};
+struct DWork {  // one tile of points of one batch for the density
+    int32_t batch, tp;
+};
+
+struct Chunk {  // a run of batches whose evaluated basis functions fit the scratch at once
+    int32_t b0, b1;
+    int32_t hw0, hw1;  // H work items of these batches
+    int32_t dw0, dw1;  // density work items of these batches
+};
+
+struct nao_grid {
+    int device = 0;
+    nao_options opt{};
+    // host copies of the problem
+    int32_t n_atoms = 0, n_species = 0, n_fn = 0, n_rgrid = 0;
+    int64_t nb = 0, n_points = 0, n_batches = 0, rel_total = 0, rfn_total = 0;
+    double r0 = 0, r_last = 0, delta = 0;
+    std::vector<int64_t> batch_off, perm, rel_off;
+    std::vector<int32_t> rel_idx;
+    std::vector<int32_t> Pb, Nb;
+    int32_t max_P = 0, max_N = 0;
+    int64_t flops_h = 0, flops_n = 0;
+    std::vector<Chunk> chunks;
+    int64_t scratch_elems = 0;  // doubles
+    int64_t n_hwork = 0, n_dwork = 0;
+    // device memory
+    std::vector<void *> allocs;
+    int64_t dev_bytes = 0;
+    DevSystem sys{};
+    HWork *d_hwork = nullptr;
+    DWork *d_dwork = nullptr;
+    double *d_scratch = nullptr;
+    double *d_ne_part = nullptr;    // [n_dwork] per-tile sums of w n
+    int32_t *d_err = nullptr;       // device error word
+    // kernel timing (nao_profile_enable)
+    bool profiling = false;
+    struct Timed {
+        int kid;
+        cudaEvent_t a, b;
+    };
+    std::vector<Timed> timed;
+    std::vector<cudaEvent_t> event_pool;
+    nao_profile prof{};
+    // staging for the host-buffer entry points (allocated on first use)
+    double *d_stage_in = nullptr, *d_stage_out = nullptr, *d_stage_ne = nullptr;
+};
+
+// ---- launchers (eval.cu, contract_f64.cu) ----------------------------------------------
+cudaError_t launch_relevance_minr2(const double *atom_xyz, int32_t n_atoms, const double *px, const double *py,
+                                   const double *pz, const int32_t *batch_off, int64_t n_batches, double *minr2,
+                                   cudaStream_t st);
+cudaError_t launch_eval(const DevSystem &s, int32_t b0, int32_t b1, nao_precision prec, bool grad, double *scratch,
+                        cudaStream_t st);
+cudaError_t launch_eval_one(const DevSystem &s, int32_t b, nao_precision prec, double *phi, double *grad,
+                            cudaStream_t st);
+cudaError_t launch_h_f64(const DevSystem &s, const HWork *work, int32_t n_work, const double *scratch,
+                         const double *v, uint32_t terms, double *H, cudaStream_t st);
+cudaError_t launch_mirror(double *H, int64_t nb, cudaStream_t st);
+cudaError_t launch_density_f64(const DevSystem &s, const DWork *work, int32_t w0, int32_t n_work,
+                               const double *scratch, const double *P, double *n, double *ne_part, cudaStream_t st);
+cudaError_t launch_reduce_sum(const double *part, int64_t n, double *out, cudaStream_t st);
+
+// ---- host helpers (partition.cpp) --------------------------------------------------------
+// Recursive bisection (see nao_grid_create in nao.h); returns the number of batches.
+int64_t nao_partition(int64_t n, const double *xyz, int64_t B, std::vector<int64_t> &offsets,
+                      std::vector<int64_t> &perm);
+// Natural cubic spline in the index coordinate: coefficients of y_k + c1 t + c2 t^2 + c3 t^3.
+void nao_spline_coefficients(const double *y, int32_t n, double *coef /* [(n-1)*4] */);

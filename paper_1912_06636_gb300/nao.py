@@ -1,0 +1,319 @@
+"""Thin ctypes binding of libnao (include/nao.h): argument marshalling only.
+
+Every numeric step runs in the CUDA library; this module only turns torch tensors into
+device pointers and streams, numpy arrays into host pointers, and status codes into
+exceptions. The functions keep the C names; ``Grid`` is a small owner object around a
+handle. There is no fallback: if libnao.so is missing or cannot be loaded, importing the
+library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+from pathlib import Path
+
+import numpy as np
+
+_LIB_PATH = Path(__file__).resolve().parent / "lib" / "libnao.so"
+_lib = None
+
+NAO_FP64, NAO_FP32, NAO_SPLIT = 0, 1, 2
+NAO_TERM_POTENTIAL, NAO_TERM_KINETIC = 1, 2
+PRECISIONS = {"fp64": NAO_FP64, "fp32": NAO_FP32, "split": NAO_SPLIT}
+
+STATUS = {0: "NAO_OK", 1: "NAO_ERR_INVALID_ARG", 2: "NAO_ERR_OUT_OF_MEMORY", 3: "NAO_ERR_CUDA",
+          4: "NAO_ERR_TIMEOUT", 5: "NAO_ERR_INTERNAL", 6: "NAO_ERR_UNSUPPORTED"}
+
+# exported symbols declared in include/nao.h
+SYMBOLS = [
+    "nao_default_options", "nao_grid_create", "nao_destroy", "nao_get_info", "nao_export_batches",
+    "nao_integrate_h", "nao_update_density", "nao_integrate_h_host", "nao_update_density_host",
+    "nao_evaluate_batch", "nao_sync_status", "nao_status_string", "nao_last_error",
+    "nao_profile_enable", "nao_profile_read",
+]
+KERNELS = ["eval_grad", "eval_phi", "h_fp64", "h_fp32", "h_split", "slice", "mirror", "n_fp64", "n_fp32",
+           "n_split", "reduce"]
+
+
+class NaoError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class SystemDesc(C.Structure):
+    _fields_ = [
+        ("n_atoms", C.c_int32), ("atom_xyz", C.c_void_p), ("atom_species", C.c_void_p),
+        ("n_species", C.c_int32), ("species_fn_offset", C.c_void_p), ("fn_l", C.c_void_p),
+        ("fn_cutoff", C.c_void_p), ("n_rgrid", C.c_int32), ("r0", C.c_double), ("r_last", C.c_double),
+        ("fn_table", C.c_void_p), ("n_points", C.c_int64), ("pt_xyz", C.c_void_p), ("pt_w", C.c_void_p),
+    ]
+
+
+class Options(C.Structure):
+    _fields_ = [
+        ("max_batch_points", C.c_int32), ("split_slices", C.c_int32), ("deterministic", C.c_int32),
+        ("device", C.c_int32), ("scratch_bytes", C.c_int64),
+    ]
+
+
+class Profile(C.Structure):
+    _fields_ = [("launches", C.c_int64 * 11), ("ms", C.c_double * 11)]
+
+
+class GridInfo(C.Structure):
+    _fields_ = [
+        ("n_basis", C.c_int64), ("n_points", C.c_int64), ("n_batches", C.c_int64), ("rel_total", C.c_int64),
+        ("max_batch_points", C.c_int32), ("max_batch_basis", C.c_int32), ("device_bytes", C.c_int64),
+        ("flops_h", C.c_int64), ("flops_n", C.c_int64),
+    ]
+
+
+def lib_path() -> Path:
+    return _LIB_PATH
+
+
+def load():
+    """Load libnao.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not _LIB_PATH.exists():
+        raise ImportError(f"libnao.so not built at {_LIB_PATH}; run __graft_entry__.build()")
+    lib = C.CDLL(str(_LIB_PATH))
+    P, I32, I64, U32 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32
+    sig = {
+        "nao_default_options": ([P], C.c_int),
+        "nao_grid_create": ([P, P, P], C.c_int),
+        "nao_destroy": ([P], C.c_int),
+        "nao_get_info": ([P, P], C.c_int),
+        "nao_export_batches": ([P, P, P, P, P], C.c_int),
+        "nao_integrate_h": ([P, P, U32, C.c_int, P, P], C.c_int),
+        "nao_update_density": ([P, P, C.c_int, P, P, P], C.c_int),
+        "nao_integrate_h_host": ([P, P, U32, C.c_int, P, P], C.c_int),
+        "nao_update_density_host": ([P, P, C.c_int, P, P, P], C.c_int),
+        "nao_evaluate_batch": ([P, I64, C.c_int, P, P, P], C.c_int),
+        "nao_sync_status": ([P], C.c_int),
+        "nao_status_string": ([C.c_int], C.c_char_p),
+        "nao_last_error": ([], C.c_char_p),
+        "nao_profile_enable": ([P, I32], C.c_int),
+        "nao_profile_read": ([P, P, I32], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        msg = load().nao_last_error().decode(errors="replace")
+        raise NaoError(code, where, msg)
+
+
+def _prec(p) -> int:
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+def _dptr(t) -> int | None:
+    """Device pointer of a CUDA tensor (None stays None)."""
+    if t is None:
+        return None
+    import torch
+
+    if not t.is_cuda or not t.is_contiguous() or t.dtype != torch.float64:
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+# ---- C-named functions --------------------------------------------------------------------
+def nao_default_options() -> Options:
+    o = Options()
+    _check(load().nao_default_options(C.byref(o)), "nao_default_options")
+    return o
+
+
+def nao_grid_create(system, options: Options | None = None, **opts) -> C.c_void_p:
+    """Create a handle from a system (any object with the fields of nao_system_desc)."""
+    lib = load()
+    keep = {
+        "atom_xyz": np.ascontiguousarray(system.atom_xyz, dtype=np.float64),
+        "atom_species": np.ascontiguousarray(system.atom_species, dtype=np.int32),
+        "species_fn_offset": np.ascontiguousarray(system.species_fn_offset, dtype=np.int32),
+        "fn_l": np.ascontiguousarray(system.fn_l, dtype=np.int32),
+        "fn_cutoff": np.ascontiguousarray(system.fn_cutoff, dtype=np.float64),
+        "fn_table": np.ascontiguousarray(system.fn_table, dtype=np.float64),
+        "pt_xyz": np.ascontiguousarray(system.pt_xyz, dtype=np.float64),
+        "pt_w": np.ascontiguousarray(system.pt_w, dtype=np.float64),
+    }
+    d = SystemDesc(
+        int(keep["atom_xyz"].size // 3), keep["atom_xyz"].ctypes.data, keep["atom_species"].ctypes.data,
+        int(keep["species_fn_offset"].size - 1), keep["species_fn_offset"].ctypes.data, keep["fn_l"].ctypes.data,
+        keep["fn_cutoff"].ctypes.data, int(system.n_rgrid), float(system.r0), float(system.r_last),
+        keep["fn_table"].ctypes.data, int(keep["pt_w"].size), keep["pt_xyz"].ctypes.data, keep["pt_w"].ctypes.data,
+    )
+    o = options if options is not None else nao_default_options()
+    for k, v in opts.items():
+        setattr(o, k, v)
+    h = C.c_void_p()
+    _check(lib.nao_grid_create(C.byref(d), C.byref(o), C.byref(h)), "nao_grid_create")
+    return h
+
+
+def nao_destroy(h) -> None:
+    _check(load().nao_destroy(h), "nao_destroy")
+
+
+def nao_get_info(h) -> GridInfo:
+    info = GridInfo()
+    _check(load().nao_get_info(h, C.byref(info)), "nao_get_info")
+    return info
+
+
+def nao_export_batches(h):
+    info = nao_get_info(h)
+    bo = np.zeros(info.n_batches + 1, np.int64)
+    pp = np.zeros(info.n_points, np.int64)
+    ro = np.zeros(info.n_batches + 1, np.int64)
+    ri = np.zeros(max(info.rel_total, 1), np.int32)
+    _check(load().nao_export_batches(h, bo.ctypes.data, pp.ctypes.data, ro.ctypes.data, ri.ctypes.data),
+           "nao_export_batches")
+    return bo, pp, ro, ri[: info.rel_total]
+
+
+def nao_integrate_h(h, v, terms: int, prec, H, stream=None) -> None:
+    _check(load().nao_integrate_h(h, _dptr(v), int(terms), _prec(prec), _dptr(H), _stream(stream)), "nao_integrate_h")
+
+
+def nao_update_density(h, P, prec, n, ne=None, stream=None) -> None:
+    _check(load().nao_update_density(h, _dptr(P), _prec(prec), _dptr(n), _dptr(ne), _stream(stream)),
+           "nao_update_density")
+
+
+def nao_integrate_h_host(h, v: np.ndarray | None, terms: int, prec, H: np.ndarray, stream=None) -> None:
+    vp = None if v is None else np.ascontiguousarray(v, dtype=np.float64).ctypes.data
+    assert H.dtype == np.float64 and H.flags.c_contiguous
+    _check(load().nao_integrate_h_host(h, vp, int(terms), _prec(prec), H.ctypes.data, _stream(stream)),
+           "nao_integrate_h_host")
+
+
+def nao_update_density_host(h, P: np.ndarray, prec, n: np.ndarray, stream=None) -> float:
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    assert n.dtype == np.float64 and n.flags.c_contiguous
+    ne = C.c_double(0.0)
+    _check(load().nao_update_density_host(h, P.ctypes.data, _prec(prec), n.ctypes.data, C.byref(ne), _stream(stream)),
+           "nao_update_density_host")
+    return ne.value
+
+
+def nao_evaluate_batch(h, batch: int, prec, phi, grad=None, stream=None) -> None:
+    _check(load().nao_evaluate_batch(h, int(batch), _prec(prec), _dptr(phi), _dptr(grad), _stream(stream)),
+           "nao_evaluate_batch")
+
+
+def nao_sync_status(h) -> None:
+    _check(load().nao_sync_status(h), "nao_sync_status")
+
+
+def nao_profile_enable(h, enable: bool = True) -> None:
+    _check(load().nao_profile_enable(h, 1 if enable else 0), "nao_profile_enable")
+
+
+def nao_profile_read(h, reset: bool = True) -> dict:
+    p = Profile()
+    _check(load().nao_profile_read(h, C.byref(p), 1 if reset else 0), "nao_profile_read")
+    return {k: (int(p.launches[i]), float(p.ms[i])) for i, k in enumerate(KERNELS)}
+
+
+def nao_status_string(code: int) -> str:
+    return load().nao_status_string(int(code)).decode()
+
+
+# ---- owner object -------------------------------------------------------------------------
+@dataclass
+class _Sizes:
+    nb: int
+    n_points: int
+    n_batches: int
+
+
+class Grid:
+    """Owns one nao_grid handle; allocates outputs as torch tensors on the handle's device."""
+
+    def __init__(self, system, device: int | None = None, **opts):
+        import torch
+
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = torch.device("cuda", device)
+        with torch.cuda.device(self.device):
+            self.h = nao_grid_create(system, device=device, **opts)
+        self.info = nao_get_info(self.h)
+        self.nb = int(self.info.n_basis)
+        self.n_points = int(self.info.n_points)
+
+    def close(self):
+        if getattr(self, "h", None):
+            nao_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def integrate_h(self, v=None, terms=NAO_TERM_POTENTIAL | NAO_TERM_KINETIC, prec="fp64", H=None, stream=None):
+        import torch
+
+        if H is None:
+            H = torch.empty((self.nb, self.nb), dtype=torch.float64, device=self.device)
+        nao_integrate_h(self.h, v, terms, prec, H, stream)
+        return H
+
+    def overlap(self, prec="fp64", S=None, stream=None):
+        return self.integrate_h(None, NAO_TERM_POTENTIAL, prec, S, stream)
+
+    def update_density(self, P, prec="fp64", n=None, ne=None, stream=None, want_ne=True):
+        import torch
+
+        if n is None:
+            n = torch.empty(self.n_points, dtype=torch.float64, device=self.device)
+        if ne is None and want_ne:
+            ne = torch.empty(1, dtype=torch.float64, device=self.device)
+        nao_update_density(self.h, P, prec, n, ne, stream)
+        return n, ne
+
+    def evaluate_batch(self, b: int, prec="fp64", grad=True, stream=None):
+        import torch
+
+        bo, _, ro, _ = self.batches()
+        P, N = int(bo[b + 1] - bo[b]), int(ro[b + 1] - ro[b])
+        phi = torch.zeros((N, P), dtype=torch.float64, device=self.device)
+        g = torch.zeros((3, N, P), dtype=torch.float64, device=self.device) if grad else None
+        nao_evaluate_batch(self.h, b, prec, phi, g, stream)
+        return phi, g
+
+    def batches(self):
+        if not hasattr(self, "_batches"):
+            self._batches = nao_export_batches(self.h)
+        return self._batches
+
+    def sync(self):
+        nao_sync_status(self.h)

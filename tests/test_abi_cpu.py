@@ -1,0 +1,73 @@
+"""The C-ABI library loads, exports every symbol include/nao.h declares, and rejects bad
+input before touching a GPU (these tests make no compute call)."""
+import ctypes as C
+import re
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+from paper_1912_06636_gb300 import nao, synth
+
+HEADER = Path(__file__).resolve().parents[1] / "include" / "nao.h"
+
+
+def declared_functions():
+    text = HEADER.read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(nao_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported():
+    lib = nao.load()
+    decl = declared_functions()
+    assert len(decl) >= 13
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert sorted(nao.SYMBOLS) == sorted(set(nao.SYMBOLS) & set(decl))
+
+
+def test_status_strings_and_defaults():
+    assert nao.nao_status_string(0) == "ok"
+    assert nao.nao_status_string(1) == "invalid argument"
+    o = nao.nao_default_options()
+    assert o.max_batch_points == 200 and o.split_slices == 8 and o.device == -1
+
+
+def _bad(sys_, **opts):
+    with pytest.raises(nao.NaoError) as e:
+        nao.nao_grid_create(sys_, **opts)
+    return e.value.code
+
+
+def test_invalid_input_is_rejected_without_gpu():
+    s = synth.config_water(n_rad=4, n_theta=2, n_phi=3)
+    bad = synth.System(**{**s.__dict__})
+    bad.fn_l = s.fn_l.copy()
+    bad.fn_l[0] = 7
+    assert _bad(bad) == 1
+    bad = synth.System(**{**s.__dict__})
+    bad.fn_cutoff = s.fn_cutoff.copy()
+    bad.fn_cutoff[1] = 9.0  # beyond r_last
+    assert _bad(bad) == 1
+    bad = synth.System(**{**s.__dict__})
+    bad.pt_xyz = s.pt_xyz.copy()
+    bad.pt_xyz[3, 1] = np.nan
+    assert _bad(bad) == 1
+    bad = synth.System(**{**s.__dict__})
+    bad.atom_species = np.array([0, 1, 5], np.int32)
+    assert _bad(bad) == 1
+    assert _bad(s, max_batch_points=0) == 1
+    assert _bad(s, max_batch_points=5000) == 1
+    assert _bad(s, split_slices=2) == 1
+
+
+def test_null_handle_calls_fail_cleanly():
+    lib = nao.load()
+    assert lib.nao_destroy(None) == 0
+    assert lib.nao_integrate_h(None, None, 3, 0, None, None) == 1
+    assert lib.nao_update_density(None, None, 0, None, None, None) == 1
+    info = nao.GridInfo()
+    assert lib.nao_get_info(None, C.byref(info)) == 1
+    out = C.c_void_p(123)
+    assert lib.nao_grid_create(None, None, C.byref(out)) == 1 and out.value is None
