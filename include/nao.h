@@ -89,7 +89,7 @@ typedef struct {
 
 typedef struct {
     int32_t max_batch_points; /* target batch size B (Sec. 3.3.1; the paper uses 200 on GPUs); default 200 */
-    int32_t split_slices;     /* slices per operand on the NAO_SPLIT path, 4..10; default 8 */
+    int32_t split_slices;     /* slices per operand on the NAO_SPLIT path, 4..10; default 10 */
     int32_t deterministic;    /* reserved; results are already run-to-run reproducible up to
                                  the order of FP64 atomic additions into H */
     int32_t device;           /* CUDA device ordinal; -1 = the calling thread's current device */
@@ -170,7 +170,8 @@ nao_status nao_update_density_host(nao_grid *g, const double *P_host, nao_precis
 /* Basis functions of one batch (Sec. 3.4, the evaluation phase), for parity checks:
  * phi_dev[j*P_b + q] = phi_{rel_j}(r_q) and grad_dev[(c*N_b + j)*P_b + q] = d/dx_c of it,
  * for the batch's q = 0..P_b-1 points in batch order and j = 0..N_b-1 reduced-basis
- * positions. grad_dev may be NULL. prec selects the evaluation arithmetic
+ * positions. grad_dev may be NULL; for a batch with N_b = 0 nothing is written and both
+ * pointers may be NULL. prec selects the evaluation arithmetic
  * (NAO_FP32 evaluates in FP32 and widens; NAO_FP64 and NAO_SPLIT evaluate in FP64).      */
 nao_status nao_evaluate_batch(nao_grid *g, int64_t batch, nao_precision prec, double *phi_dev, double *grad_dev,
                               void *cuda_stream);

@@ -227,6 +227,9 @@ nao_status build(nao_grid *g, const nao_system_desc *d) {
         nao_spline_coefficients(d->fn_table + (size_t)f * d->n_rgrid, d->n_rgrid,
                                 coef.data() + (size_t)f * (d->n_rgrid - 1) * 4);
     std::vector<float> coef32(coef.begin(), coef.end());
+    std::vector<double> inv_rk((size_t)d->n_rgrid);
+    for (int k = 0; k < d->n_rgrid; k++)
+        inv_rk[(size_t)k] = 1.0 / (d->r0 * std::exp((double)k * g->delta));
 
     // work lists and chunks of batches that fit the scratch
     std::vector<HWork> hw;
@@ -273,10 +276,12 @@ nao_status build(nao_grid *g, const nao_system_desc *d) {
 
     double *d_coef, *d_rc;
     float *d_coef32;
+    double *d_inv_rk;
     int32_t *d_rel_off, *d_rel_idx, *d_rfn_off;
     RfnEntry *d_rfn;
     int64_t *d_scr_off;
     if ((st = upload(g, &d_coef, coef.data(), coef.size())) || (st = upload(g, &d_coef32, coef32.data(), coef32.size())) ||
+        (st = upload(g, &d_inv_rk, inv_rk.data(), inv_rk.size())) ||
         (st = upload(g, &d_rc, d->fn_cutoff, (size_t)g->n_fn)) ||
         (st = upload(g, &d_rel_off, rel_off32.data(), rel_off32.size())) ||
         (st = upload(g, &d_rel_idx, g->rel_idx.data(), g->rel_idx.size())) ||
@@ -293,6 +298,7 @@ nao_status build(nao_grid *g, const nao_system_desc *d) {
     s.atom_xyz = d_atoms;
     s.coef = d_coef;
     s.coef_f32 = d_coef32;
+    s.inv_rk = d_inv_rk;
     s.fn_rc = d_rc;
     s.px = d_px;
     s.py = d_py;
@@ -356,17 +362,136 @@ nao_status check_handle(const nao_grid *g) {
 
 nao_status check_prec(nao_precision p) {
     if (p != NAO_FP64 && p != NAO_FP32 && p != NAO_SPLIT) return fail(NAO_ERR_INVALID_ARG, "unknown precision");
-    if (p != NAO_FP64) return fail(NAO_ERR_UNSUPPORTED, "precision not available in this build");
+    return NAO_OK;
+}
+
+// Plan and allocate the split path: sub-chunks of the evaluation chunks whose slices fit the
+// slice budget, work lists of 128 x 64 tiles, per-batch slice offsets and exponent arrays.
+nao_status split_setup(nao_grid *g) {
+    if (g->split_ready) return NAO_OK;
+    const int S = g->opt.split_slices;
+    if (S > NAO_SPLIT_MAX_SLICES)
+        return fail(NAO_ERR_UNSUPPORTED, "split path supports at most " + std::to_string(NAO_SPLIT_MAX_SLICES) + " slices");
+    for (int64_t b = 0; b < g->n_batches; b++) {
+        const int64_t Ppad = (g->Pb[b] + NAO_PPAD - 1) / NAO_PPAD * NAO_PPAD;
+        const int64_t N64 = (g->Nb[b] + 63) / 64 * 64;
+        // every slice-group sum must stay below 2^24: K (g+1) 2^10 with g + 1 <= S
+        if (Ppad > NAO_SPLIT_MAX_PPAD || 4 * Ppad * S >= 16384 || N64 * S >= 16384)
+            return fail(NAO_ERR_UNSUPPORTED, "batch too large for exact slice sums (points " + std::to_string(g->Pb[b]) +
+                                                 ", basis " + std::to_string(g->Nb[b]) + ", slices " + std::to_string(S) + ")");
+    }
+    NAO_CUDA(split_configure());
+    const int64_t budget = std::max<int64_t>(g->opt.scratch_bytes > 0 ? 2 * g->opt.scratch_bytes : (int64_t(4) << 30),
+                                             int64_t(1) << 20);
+    std::vector<int64_t> off_h(g->n_batches, 0), off_n(g->n_batches, 0);
+    std::vector<HWork> hw, nw;
+    int64_t max_used = 0;
+    for (const Chunk &c : g->chunks) {
+        nao_grid::SplitChunk cur{c.b0, c.b0, (int32_t)hw.size(), 0, (int32_t)nw.size(), 0, 0, 0};
+        int64_t used = 0;
+        for (int32_t b = c.b0; b < c.b1; b++) {
+            const int P = g->Pb[b], N = g->Nb[b];
+            const SplitGeom G(P, N);
+            const int64_t need = N == 0 ? 0 : (int64_t)std::max(G.h_bytes(S), G.n_bytes(S));
+            if (used + need > budget && b > cur.b0) {
+                cur.b1 = b;
+                cur.hw1 = (int32_t)hw.size();
+                cur.nw1 = (int32_t)nw.size();
+                g->split_chunks.push_back(cur);
+                cur = nao_grid::SplitChunk{b, b, (int32_t)hw.size(), 0, (int32_t)nw.size(), 0, 0, 0};
+                used = 0;
+            }
+            off_h[b] = used;
+            off_n[b] = used;
+            used += need;
+            max_used = std::max(max_used, used);
+            if (N > 0) {
+                cur.max_rt = std::max<int32_t>(cur.max_rt, G.h_slice_tiles());
+                cur.max_qt = std::max<int32_t>(cur.max_qt, G.n_qt);
+                const int nI = (N + 127) / 128, nJ = G.n_jt;
+                for (int I = 0; I < nI; I++)
+                    for (int J = 0; J < nJ; J++)
+                        if (I * 128 <= J * NAO_SPLIT_TN + NAO_SPLIT_TN - 1) hw.push_back({b, I, J, 0});
+                for (int Q = 0; Q < G.n_qt; Q++)
+                    for (int J = 0; J < G.n_jtN; J++) nw.push_back({b, Q, J, 0});
+            }
+        }
+        cur.b1 = c.b1;
+        cur.hw1 = (int32_t)hw.size();
+        cur.nw1 = (int32_t)nw.size();
+        g->split_chunks.push_back(cur);
+    }
+    g->n_split_hw = (int64_t)hw.size();
+    g->n_split_nw = (int64_t)nw.size();
+    nao_status st;
+    if ((st = dev_alloc(g, &g->d_slices, (size_t)std::max<int64_t>(max_used, 1024))) ||
+        (st = upload(g, &g->d_sl_off_h, off_h.data(), off_h.size())) ||
+        (st = upload(g, &g->d_sl_off_n, off_n.data(), off_n.size())) ||
+        (st = dev_alloc(g, &g->d_expo_h, (size_t)std::max<int64_t>(g->rel_total, 1))) ||
+        (st = dev_alloc(g, &g->d_expo_q, (size_t)g->n_points)) ||
+        (st = dev_alloc(g, &g->d_expo_b, (size_t)g->n_batches)) ||
+        (st = upload(g, &g->d_split_hw, hw.data(), hw.size())) || (st = upload(g, &g->d_split_nw, nw.data(), nw.size())))
+        return st;
+    g->split_S = S;
+    g->split_ready = true;
+    return NAO_OK;
+}
+
+nao_status run_h_split(nao_grid *g, const double *v, uint32_t terms, double *H, cudaStream_t st) {
+    nao_status sst = split_setup(g);
+    if (sst) return sst;
+    const DevSystem &s = g->sys;
+    const int S = g->split_S;
+    NAO_CUDA(cudaMemsetAsync(H, 0, (size_t)g->nb * g->nb * sizeof(double), st));
+    for (const auto &c : g->split_chunks) {
+        NAO_CUDA(timed(g, NAO_K_EVAL_GRAD, st, [&] { return launch_eval(s, c.b0, c.b1, NAO_FP64, true, g->d_scratch, st); }));
+        NAO_CUDA(timed(g, NAO_K_SLICE, st, [&] {
+            return launch_slice_h(s, c.b0, c.b1, c.max_rt, g->d_scratch, v, terms, g->d_slices, g->d_sl_off_h, g->d_expo_h,
+                                  S, st);
+        }));
+        NAO_CUDA(timed(g, NAO_K_H_SPLIT, st, [&] {
+            return launch_h_tc(s, g->d_split_hw, c.hw0, c.hw1 - c.hw0, g->d_slices, g->d_sl_off_h, g->d_expo_h, S, H,
+                               g->d_err, st);
+        }));
+    }
+    NAO_CUDA(timed(g, NAO_K_MIRROR, st, [&] { return launch_mirror(H, g->nb, st); }));
+    return NAO_OK;
+}
+
+nao_status run_n_split(nao_grid *g, const double *P, double *n, double *ne, cudaStream_t st) {
+    nao_status sst = split_setup(g);
+    if (sst) return sst;
+    const DevSystem &s = g->sys;
+    const int S = g->split_S;
+    NAO_CUDA(cudaMemsetAsync(n, 0, (size_t)g->n_points * sizeof(double), st));
+    for (const auto &c : g->split_chunks) {
+        NAO_CUDA(timed(g, NAO_K_EVAL_PHI, st, [&] { return launch_eval(s, c.b0, c.b1, NAO_FP64, false, g->d_scratch, st); }));
+        NAO_CUDA(timed(g, NAO_K_SLICE, st, [&] {
+            return launch_slice_n(s, c.b0, c.b1, c.max_qt, g->d_scratch, P, g->d_slices, g->d_sl_off_n, g->d_expo_q,
+                                  g->d_expo_b, S, st);
+        }));
+        NAO_CUDA(timed(g, NAO_K_N_SPLIT, st, [&] {
+            return launch_n_tc(s, g->d_split_nw, c.nw0, c.nw1 - c.nw0, g->d_slices, g->d_sl_off_n, g->d_expo_q,
+                               g->d_expo_b, g->d_scratch, S, n, g->d_err, st);
+        }));
+    }
+    if (ne) {
+        NAO_CUDA(timed(g, NAO_K_REDUCE, st, [&] {
+            cudaError_t e = launch_wn_partial(s, g->d_dwork, 0, (int32_t)g->n_dwork, n, g->d_ne_part, st);
+            return e != cudaSuccess ? e : launch_reduce_sum(g->d_ne_part, g->n_dwork, ne, st);
+        }));
+    }
     return NAO_OK;
 }
 
 nao_status run_h(nao_grid *g, const double *v, uint32_t terms, nao_precision prec, double *H, cudaStream_t st) {
+    if (prec == NAO_SPLIT) return run_h_split(g, v, terms, H, st);
     const DevSystem &s = g->sys;
     NAO_CUDA(cudaMemsetAsync(H, 0, (size_t)g->nb * g->nb * sizeof(double), st));
     for (const Chunk &c : g->chunks) {
         NAO_CUDA(timed(g, NAO_K_EVAL_GRAD, st, [&] { return launch_eval(s, c.b0, c.b1, prec, true, g->d_scratch, st); }));
-        NAO_CUDA(timed(g, NAO_K_H_FP64, st, [&] {
-            return launch_h_f64(s, g->d_hwork + c.hw0, c.hw1 - c.hw0, g->d_scratch, v, terms, H, st);
+        NAO_CUDA(timed(g, prec == NAO_FP32 ? NAO_K_H_FP32 : NAO_K_H_FP64, st, [&] {
+            return launch_h_simt(s, prec, g->d_hwork + c.hw0, c.hw1 - c.hw0, g->d_scratch, v, terms, H, st);
         }));
     }
     NAO_CUDA(timed(g, NAO_K_MIRROR, st, [&] { return launch_mirror(H, g->nb, st); }));
@@ -374,11 +499,12 @@ nao_status run_h(nao_grid *g, const double *v, uint32_t terms, nao_precision pre
 }
 
 nao_status run_n(nao_grid *g, const double *P, nao_precision prec, double *n, double *ne, cudaStream_t st) {
+    if (prec == NAO_SPLIT) return run_n_split(g, P, n, ne, st);
     const DevSystem &s = g->sys;
     for (const Chunk &c : g->chunks) {
         NAO_CUDA(timed(g, NAO_K_EVAL_PHI, st, [&] { return launch_eval(s, c.b0, c.b1, prec, false, g->d_scratch, st); }));
-        NAO_CUDA(timed(g, NAO_K_N_FP64, st, [&] {
-            return launch_density_f64(s, g->d_dwork, c.dw0, c.dw1 - c.dw0, g->d_scratch, P, n, g->d_ne_part, st);
+        NAO_CUDA(timed(g, prec == NAO_FP32 ? NAO_K_N_FP32 : NAO_K_N_FP64, st, [&] {
+            return launch_density_simt(s, prec, g->d_dwork, c.dw0, c.dw1 - c.dw0, g->d_scratch, P, n, g->d_ne_part, st);
         }));
     }
     if (ne) NAO_CUDA(timed(g, NAO_K_REDUCE, st, [&] { return launch_reduce_sum(g->d_ne_part, g->n_dwork, ne, st); }));
@@ -393,7 +519,7 @@ nao_status nao_default_options(nao_options *o) {
     if (!o) return fail(NAO_ERR_INVALID_ARG, "opts is NULL");
     std::memset(o, 0, sizeof(*o));
     o->max_batch_points = 200;
-    o->split_slices = 8;
+    o->split_slices = 10;
     o->deterministic = 0;
     o->device = -1;
     o->scratch_bytes = 0;
@@ -551,6 +677,7 @@ nao_status nao_evaluate_batch(nao_grid *g, int64_t batch, nao_precision prec, do
     nao_status st = check_handle(g);
     if (st) return st;
     if (batch < 0 || batch >= g->n_batches) return fail(NAO_ERR_INVALID_ARG, "batch out of range");
+    if (g->Nb[batch] == 0) return NAO_OK;  // nothing to write
     if (!phi_dev) return fail(NAO_ERR_INVALID_ARG, "phi_dev is NULL");
     if ((st = check_prec(prec))) return st;
     DeviceGuard guard(g->device);

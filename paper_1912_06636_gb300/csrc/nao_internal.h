@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "nao.h"
@@ -13,6 +14,9 @@
 #define NAO_TILE 64          // tile edge of the SIMT contractions (basis functions and points)
 #define NAO_PPAD 16          // batch points are padded to a multiple of this in scratch
 #define NAO_MAX_BATCH 1024   // largest accepted max_batch_points
+#define NAO_SPLIT_MAX_SLICES 10  // tensor-memory budget: 10 groups x 48 FP32 columns <= 512 columns
+#define NAO_SPLIT_TN 48          // split path: MMA N (B-tile rows)
+#define NAO_SPLIT_MAX_PPAD 512   // split path: padded batch points (4 Ppad S < 2^14 keeps sums exact)
 
 // One radial function instance relevant to a batch: atom, radial function, position of
 // its m = -l entry in the batch's reduced basis, l.
@@ -25,6 +29,7 @@ struct DevSystem {
     const double *atom_xyz;   // [n_atoms*3]
     const double *coef;       // [n_fn][n_rgrid-1][4] spline coefficients in t
     const float *coef_f32;    // same in FP32
+    const double *inv_rk;     // [n_rgrid] 1 / r_k of the logarithmic grid
     const double *fn_rc;      // [n_fn]
     const double *px, *py, *pz, *pw;  // points in batch order
     const int32_t *perm;      // batch order -> original index
@@ -38,6 +43,32 @@ struct DevSystem {
     double r0, inv_delta;
     int64_t nb;
     double knorm[NAO_LMAX + 1][NAO_LMAX + 1];  // sqrt((2l+1)/(4pi) (l-m)!/(l+m)!) (x sqrt2 for m>0)
+};
+
+// Geometry of one batch's operand slices on the split path (shared by host and device code).
+// H: A rows (basis functions) in 64-row blocks, 128-row MMA tiles; B rows in 48-row blocks;
+//    K = 4 Ppad in chunks of 64. Density: A rows (points) in 128-row blocks, K = basis in
+//    chunks of 64; B rows (basis) in 48-row blocks. One block = rows x 64 bf16, 128 B per row.
+struct SplitGeom {
+    int n_kc, n_rt, n_jt;        // H: K chunks, A 64-row blocks (even), B 48-row blocks
+    int n_kcN, n_qt, n_jtN;      // density: K chunks, A 128-point blocks, B 48-row blocks
+    __host__ __device__ SplitGeom(int P, int N) {
+        const int Ppad = (P + NAO_PPAD - 1) / NAO_PPAD * NAO_PPAD;
+        n_kc = Ppad / 16;
+        n_rt = 2 * ((N + 127) / 128);
+        n_jt = (N + NAO_SPLIT_TN - 1) / NAO_SPLIT_TN;
+        n_kcN = (N + 63) / 64;
+        n_qt = (P + 127) / 128;
+        n_jtN = n_jt;
+    }
+    __host__ __device__ size_t h_setA(int S) const { return (size_t)S * n_kc * n_rt * 8192; }
+    __host__ __device__ size_t h_bytes(int S) const { return h_setA(S) + (size_t)S * n_kc * n_jt * (NAO_SPLIT_TN * 128); }
+    __host__ __device__ int h_slice_tiles() const {  // 64-row tiles the H slicing covers
+        const int ra = n_rt * 64, rb = n_jt * NAO_SPLIT_TN;
+        return ((ra > rb ? ra : rb) + 63) / 64;
+    }
+    __host__ __device__ size_t n_setA(int S) const { return (size_t)S * n_kcN * n_qt * 16384; }
+    __host__ __device__ size_t n_bytes(int S) const { return n_setA(S) + (size_t)S * n_kcN * n_jtN * (NAO_SPLIT_TN * 128); }
 };
 
 struct HWork {  // one upper-triangular tile pair of one batch's h[B] (Eq. batch_matrix_mult)
@@ -77,6 +108,21 @@ struct nao_grid {
     double *d_scratch = nullptr;
     double *d_ne_part = nullptr;    // [n_dwork] per-tile sums of w n
     int32_t *d_err = nullptr;       // device error word
+    // split (tensor-core) path, set up on its first use
+    struct SplitChunk {
+        int32_t b0, b1;    // batches (inside one chunk of the evaluation scratch)
+        int32_t hw0, hw1;  // items of the split H list
+        int32_t nw0, nw1;  // items of the split density list
+        int32_t max_rt, max_qt;  // grid extents of the slicing kernels
+    };
+    bool split_ready = false;
+    int split_S = 0;
+    std::vector<SplitChunk> split_chunks;
+    uint8_t *d_slices = nullptr;
+    int64_t *d_sl_off_h = nullptr, *d_sl_off_n = nullptr;
+    int32_t *d_expo_h = nullptr, *d_expo_q = nullptr, *d_expo_b = nullptr;
+    HWork *d_split_hw = nullptr, *d_split_nw = nullptr;
+    int64_t n_split_hw = 0, n_split_nw = 0;
     // kernel timing (nao_profile_enable)
     bool profiling = false;
     struct Timed {
@@ -90,7 +136,7 @@ struct nao_grid {
     double *d_stage_in = nullptr, *d_stage_out = nullptr, *d_stage_ne = nullptr;
 };
 
-// ---- launchers (eval.cu, contract_f64.cu) ----------------------------------------------
+// ---- launchers (eval.cu, contract_simt.cu) ----------------------------------------------
 cudaError_t launch_relevance_minr2(const double *atom_xyz, int32_t n_atoms, const double *px, const double *py,
                                    const double *pz, const int32_t *batch_off, int64_t n_batches, double *minr2,
                                    cudaStream_t st);
@@ -98,12 +144,29 @@ cudaError_t launch_eval(const DevSystem &s, int32_t b0, int32_t b1, nao_precisio
                         cudaStream_t st);
 cudaError_t launch_eval_one(const DevSystem &s, int32_t b, nao_precision prec, double *phi, double *grad,
                             cudaStream_t st);
-cudaError_t launch_h_f64(const DevSystem &s, const HWork *work, int32_t n_work, const double *scratch,
-                         const double *v, uint32_t terms, double *H, cudaStream_t st);
+cudaError_t launch_h_simt(const DevSystem &s, nao_precision prec, const HWork *work, int32_t n_work,
+                          const double *scratch, const double *v, uint32_t terms, double *H, cudaStream_t st);
 cudaError_t launch_mirror(double *H, int64_t nb, cudaStream_t st);
-cudaError_t launch_density_f64(const DevSystem &s, const DWork *work, int32_t w0, int32_t n_work,
-                               const double *scratch, const double *P, double *n, double *ne_part, cudaStream_t st);
+cudaError_t launch_density_simt(const DevSystem &s, nao_precision prec, const DWork *work, int32_t w0, int32_t n_work,
+                                const double *scratch, const double *P, double *n, double *ne_part, cudaStream_t st);
 cudaError_t launch_reduce_sum(const double *part, int64_t n, double *out, cudaStream_t st);
+
+// ---- split path (split_tc.cu) ------------------------------------------------------------
+size_t split_smem_bytes(int S);
+cudaError_t split_configure();
+cudaError_t launch_slice_h(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_rt, const double *scratch,
+                           const double *v, uint32_t terms, uint8_t *slices, const int64_t *sl_off, int32_t *expo, int S,
+                           cudaStream_t st);
+cudaError_t launch_h_tc(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
+                        const int64_t *sl_off, const int32_t *expo, int S, double *H, int32_t *err, cudaStream_t st);
+cudaError_t launch_slice_n(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_qt, const double *scratch,
+                           const double *P, uint8_t *slices, const int64_t *sl_off, int32_t *expo_q, int32_t *expo_b,
+                           int S, cudaStream_t st);
+cudaError_t launch_n_tc(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
+                        const int64_t *sl_off, const int32_t *expo_q, const int32_t *expo_b, const double *scratch, int S,
+                        double *n, int32_t *err, cudaStream_t st);
+cudaError_t launch_wn_partial(const DevSystem &s, const DWork *work, int32_t w0, int32_t n_work, const double *n,
+                              double *ne_part, cudaStream_t st);
 
 // ---- host helpers (partition.cpp) --------------------------------------------------------
 // Recursive bisection (see nao_grid_create in nao.h); returns the number of batches.

@@ -1,0 +1,540 @@
+// Split-precision (Ozaki) contractions on the tcgen05 tensor cores.
+//
+// The batch products of Eq. batch_matrix_mult (Hamiltonian) and of the density (Eq. Density
+// restricted to nnz(B)) are dense matrix products whose inputs are FP64. Each input row x
+// (one basis function over the batch's points for H; one point over the basis for n; one
+// density-matrix row for n) is scaled by a power of two 2^-e so that |x 2^-e| <= 1/2, rounded
+// to an integer X = round(x 2^(6S-e)) and cut into S balanced base-64 digits
+//     X = sum_s d_s 64^(S-1-s),  d_s in [-32, 32],
+// (Ozaki, Ogita, Oishi, Rump, "Error-free transformations of matrix multiplication by using
+// fast routines of matrix multiplication", Numer. Algorithms 59 (2012): a splitting whose
+// slice products are exact in the working precision of the fast product). Every digit is an
+// exact bf16 integer, every digit product is at most 2^10, and a K-long sum of the products of
+// one slice-order group g = s + t (g + 1 pairs) stays below K (g+1) 2^10 < 2^24, so it is exact
+// in the FP32 accumulator. Each group therefore has its own accumulator in tensor memory;
+// pairs with s + t >= S are dropped (their weight is below 64^-S). The epilogue recombines the
+// groups as integers (two 64-bit halves) and scales once in FP64:
+//     x_i . y_j = 2^(e_i + e_j) sum_g M_g 64^-(g+2).
+//
+// Hamiltonian: A = F (rows i, K = 4 Ppad: phi | d/dx | d/dy | d/dz weighted by sqrt|d_k|) and
+// B = sign(d_k) F (rows j), tiles of 128 x 48 (10 groups x 48 FP32 columns fill 480 of the 512
+// tensor-memory columns), tile pairs crossing the upper triangle, FP64 atomic scatter.
+// Density: A = Phi^T (rows = points, K = basis), B = P' (rows j, P'_ij = c_IJ P_ij for 48-function
+// tiles I <= J with c_II = 1, c_IJ = 2, else 0) so that T_qj = sum_i phi_qi P'_ij and
+// n_q = sum_j T_qj phi_qj; one per-batch exponent is used for P'.
+#include <cmath>
+
+#include "nao_internal.h"
+#include "tc_ptx.h"
+
+namespace {
+
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: bounded mbarrier waits
+
+// bf16 bit pattern of a small integer (|d| <= 256 is exact).
+__device__ __forceinline__ uint32_t bf16_bits(int d) { return __float_as_uint((float)d) >> 16; }
+
+// S balanced base-64 digits of X, |X| <= 32 * 64^(S-1) (most significant first in dig[0]).
+// The S-1 lower digits are taken in [-32, 31]; the top digit is what remains, which the bound
+// on |X| keeps in [-32, 32] (it must not be reduced modulo 64, or a carry would be lost).
+__device__ __forceinline__ void digits(long long X, int S, int (&dig)[NAO_SPLIT_MAX_SLICES]) {
+#pragma unroll
+    for (int s = NAO_SPLIT_MAX_SLICES - 1; s >= 1; s--) {
+        if (s < S) {
+            const int d = (int)(((X + 32) & 63LL)) - 32;
+            dig[s] = d;
+            X = (X - d) >> 6;
+        } else {
+            dig[s] = 0;
+        }
+    }
+    dig[0] = (int)X;
+}
+
+// Exponent e with max * 2^-e in [0.25, 0.5); rows whose magnitude is below 2^-900 are taken
+// as zero (flag -10000).
+__device__ __forceinline__ int row_exponent(double mx) {
+    if (!(mx > 0.0)) return -10000;
+    int ex;
+    frexp(mx, &ex);
+    return ex < -900 ? -10000 : ex + 1;
+}
+
+// 2^E as an FP64 (0 below the normal range).
+__device__ __forceinline__ double pow2(int E) {
+    if (E < -1022) return 0.0;
+    if (E > 1023) E = 1023;
+    return __longlong_as_double((long long)(1023 + E) << 52);
+}
+
+constexpr int TN = NAO_SPLIT_TN;            // 48
+constexpr uint32_t B_BLOCK = TN * 128;      // bytes of a 48-row block
+
+// ----------------------------------------------------------------------------------------
+// Hamiltonian slicing: one CTA per (batch, 64-row tile of basis functions)
+// ----------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) slice_h_kernel(DevSystem s, int32_t b0, const double *__restrict__ scratch,
+                                                     const double *__restrict__ v, uint32_t terms,
+                                                     uint8_t *__restrict__ slices, const int64_t *__restrict__ sl_off,
+                                                     int32_t *__restrict__ expo, int S) {
+    __shared__ double sd[4 * NAO_SPLIT_MAX_PPAD];
+    __shared__ int sgn[4 * NAO_SPLIT_MAX_PPAD];
+    __shared__ int ex_s[64];
+    const int b = b0 + blockIdx.x, rt = blockIdx.y;
+    const int p0 = s.batch_off[b], P = s.batch_off[b + 1] - p0;
+    const int Ppad = (P + NAO_PPAD - 1) & ~(NAO_PPAD - 1);
+    const int N = s.rel_off[b + 1] - s.rel_off[b];
+    const SplitGeom G(P, N);
+    if (N == 0 || rt >= G.h_slice_tiles()) return;
+    const int K = 4 * Ppad;
+    const double *E = scratch + s.scr_off[b];
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        const int c = k / Ppad, q = k - c * Ppad;
+        const double w = q < P ? s.pw[p0 + q] : 0.0;
+        double d;
+        if (c == 0) d = (terms & NAO_TERM_POTENTIAL) && q < P ? w * (v ? v[s.perm[p0 + q]] : 1.0) : 0.0;
+        else d = (terms & NAO_TERM_KINETIC) ? 0.5 * w : 0.0;
+        sd[k] = sqrt(fabs(d));
+        sgn[k] = d < 0.0 ? -1 : 1;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int lr = warp; lr < 64; lr += 8) {
+        const int r = rt * 64 + lr;
+        double mx = 0.0;
+        if (r < N)
+            for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(E[(int64_t)r * K + k] * sd[k]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) {
+            const int e = row_exponent(mx);
+            ex_s[lr] = e;
+            if (r < N) expo[s.rel_off[b] + r] = e;
+        }
+    }
+    __syncthreads();
+    uint8_t *setA = slices + sl_off[b];
+    uint8_t *setB = setA + G.h_setA(S);
+    const int rowsA = G.n_rt * 64, rowsB = G.n_jt * TN;
+    const int groups = K / 8;
+    for (int u = threadIdx.x; u < 64 * groups; u += blockDim.x) {
+        const int lr = u / groups, k0 = (u - lr * groups) * 8;
+        const int r = rt * 64 + lr;
+        if (r >= rowsA && r >= rowsB) continue;
+        const int e = ex_s[lr];
+        int dg[8][NAO_SPLIT_MAX_SLICES];
+        if (r < N && e > -10000) {
+            const double scale = pow2(6 * S - e);
+            const double2 *src = reinterpret_cast<const double2 *>(E + (int64_t)r * K + k0);
+#pragma unroll
+            for (int h = 0; h < 4; h++) {
+                const double2 x = src[h];
+                digits(__double2ll_rn((x.x * sd[k0 + 2 * h]) * scale), S, dg[2 * h]);
+                digits(__double2ll_rn((x.y * sd[k0 + 2 * h + 1]) * scale), S, dg[2 * h + 1]);
+            }
+        } else {
+#pragma unroll
+            for (int h = 0; h < 8; h++)
+#pragma unroll
+                for (int q = 0; q < NAO_SPLIT_MAX_SLICES; q++) dg[h][q] = 0;
+        }
+        const int kc = k0 >> 6;
+        const uint32_t offA = tc::sw128_offset((uint32_t)lr, (uint32_t)(k0 & 63));
+        const int jt = r / TN;
+        const uint32_t offB = tc::sw128_offset((uint32_t)(r - jt * TN), (uint32_t)(k0 & 63));
+        for (int sl = 0; sl < S; sl++) {
+            uint4 va, vb;
+            uint32_t *pa = &va.x, *pb = &vb.x;
+#pragma unroll
+            for (int h = 0; h < 4; h++) {
+                pa[h] = bf16_bits(dg[2 * h][sl]) | (bf16_bits(dg[2 * h + 1][sl]) << 16);
+                pb[h] = bf16_bits(dg[2 * h][sl] * sgn[k0 + 2 * h]) | (bf16_bits(dg[2 * h + 1][sl] * sgn[k0 + 2 * h + 1]) << 16);
+            }
+            if (r < rowsA) *reinterpret_cast<uint4 *>(setA + ((size_t)(sl * G.n_kc + kc) * G.n_rt + rt) * 8192 + offA) = va;
+            if (r < rowsB)
+                *reinterpret_cast<uint4 *>(setB + ((size_t)(sl * G.n_kc + kc) * G.n_jt + jt) * B_BLOCK + offB) = vb;
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------------------
+// Density slicing. Phi^T: one CTA (128 threads, one point each) per (batch, 128-point tile).
+// ----------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) slice_nphi_kernel(DevSystem s, int32_t b0, const double *__restrict__ scratch,
+                                                        uint8_t *__restrict__ slices, const int64_t *__restrict__ sl_off,
+                                                        int32_t *__restrict__ expo_q, int S) {
+    const int b = b0 + blockIdx.x, qt = blockIdx.y;
+    const int p0 = s.batch_off[b], P = s.batch_off[b + 1] - p0;
+    const int Ppad = (P + NAO_PPAD - 1) & ~(NAO_PPAD - 1);
+    const int N = s.rel_off[b + 1] - s.rel_off[b];
+    const SplitGeom G(P, N);
+    if (N == 0 || qt >= G.n_qt) return;
+    const double *E = scratch + s.scr_off[b];  // phi[i][q], stride Ppad
+    const int ql = threadIdx.x, q = qt * 128 + ql;
+    double mx = 0.0;
+    if (q < P)
+        for (int i = 0; i < N; i++) mx = fmax(mx, fabs(E[(int64_t)i * Ppad + q]));
+    const int e = q < P ? row_exponent(mx) : -10000;
+    if (q < P) expo_q[p0 + q] = e;
+    const double scale = e > -10000 ? pow2(6 * S - e) : 0.0;
+    uint8_t *setA = slices + sl_off[b];
+    for (int i0 = 0; i0 < G.n_kcN * 64; i0 += 8) {
+        int dg[8][NAO_SPLIT_MAX_SLICES];
+#pragma unroll
+        for (int h = 0; h < 8; h++) {
+            const int i = i0 + h;
+            const double x = (q < P && i < N && e > -10000) ? E[(int64_t)i * Ppad + q] : 0.0;
+            digits(__double2ll_rn(x * scale), S, dg[h]);
+        }
+        const int kc = i0 >> 6;
+        const uint32_t off = tc::sw128_offset((uint32_t)ql, (uint32_t)(i0 & 63));
+        for (int sl = 0; sl < S; sl++) {
+            uint4 va;
+            uint32_t *pa = &va.x;
+#pragma unroll
+            for (int h = 0; h < 4; h++) pa[h] = bf16_bits(dg[2 * h][sl]) | (bf16_bits(dg[2 * h + 1][sl]) << 16);
+            *reinterpret_cast<uint4 *>(setA + ((size_t)(sl * G.n_kcN + kc) * G.n_qt + qt) * 16384 + off) = va;
+        }
+    }
+}
+
+// P'_ij = c_IJ P[rel_i][rel_j] over 48-function tiles I = i/48 <= J = j/48 (c_II = 1,
+// c_IJ = 2), read from P's upper triangle. One CTA per batch: a per-batch exponent, then the
+// digits of rows j (48-row blocks), K = i (chunks of 64).
+__global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, const double *__restrict__ Pm,
+                                                      uint8_t *__restrict__ slices, const int64_t *__restrict__ sl_off,
+                                                      int32_t *__restrict__ expo_b, int S) {
+    __shared__ double red[8];
+    __shared__ int e_sh;
+    const int b = b0 + blockIdx.x;
+    const int P = s.batch_off[b + 1] - s.batch_off[b];
+    const int N = s.rel_off[b + 1] - s.rel_off[b];
+    if (N == 0) return;
+    const SplitGeom G(P, N);
+    const int32_t *rel = s.rel_idx + s.rel_off[b];
+    auto pval = [&](int i, int j) -> double {
+        if (i >= N || j >= N || i / TN > j / TN) return 0.0;
+        int64_t gi = rel[i], gj = rel[j];
+        if (gi > gj) { const int64_t t = gi; gi = gj; gj = t; }
+        const double c = i / TN < j / TN ? 2.0 : 1.0;
+        return c * Pm[gi * s.nb + gj];
+    };
+    double mx = 0.0;
+    for (int u = threadIdx.x; u < N * N; u += blockDim.x) mx = fmax(mx, fabs(pval(u / N, u % N)));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < 8; w++) m = fmax(m, red[w]);
+        e_sh = row_exponent(m);
+        expo_b[b] = e_sh;
+    }
+    __syncthreads();
+    const int e = e_sh;
+    const double scale = e > -10000 ? pow2(6 * S - e) : 0.0;
+    uint8_t *setB = slices + sl_off[b] + G.n_setA(S);
+    const int groups = G.n_kcN * 8;  // 8-wide groups along K = i
+    for (int u = threadIdx.x; u < G.n_jtN * TN * groups; u += blockDim.x) {
+        const int j = u / groups, i0 = (u - j * groups) * 8;
+        int dg[8][NAO_SPLIT_MAX_SLICES];
+#pragma unroll
+        for (int h = 0; h < 8; h++) digits(__double2ll_rn(pval(i0 + h, j) * scale), S, dg[h]);
+        const int jt = j / TN, kc = i0 >> 6;
+        const uint32_t off = tc::sw128_offset((uint32_t)(j - jt * TN), (uint32_t)(i0 & 63));
+        for (int sl = 0; sl < S; sl++) {
+            uint4 vb;
+            uint32_t *pb = &vb.x;
+#pragma unroll
+            for (int h = 0; h < 4; h++) pb[h] = bf16_bits(dg[2 * h][sl]) | (bf16_bits(dg[2 * h + 1][sl]) << 16);
+            *reinterpret_cast<uint4 *>(setB + ((size_t)(sl * G.n_kcN + kc) * G.n_jtN + jt) * B_BLOCK + off) = vb;
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------------------
+// Slice-product main loop: per K chunk of 64, the S A-slices (128 rows) and S B-slices
+// (48 rows) are copied into shared memory by the TMA unit, then one thread issues, for every
+// pair (s, t) with s + t < S, four 128x48x16 MMAs into accumulator group s + t (tensor-memory
+// columns 48 (s + t) .. 48 (s + t) + 47). Returns false if a bounded wait gave up.
+// ----------------------------------------------------------------------------------------
+__device__ __forceinline__ bool slice_mainloop(uint8_t *sA, uint8_t *sB, uint64_t *bar_full, uint64_t *bar_mma,
+                                               uint32_t tm, int S, int n_kc, const uint8_t *a_blk0, size_t a_kc_stride,
+                                               size_t a_s_stride, const uint8_t *b_blk0, size_t b_kc_stride,
+                                               size_t b_s_stride) {
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, TN);
+    uint32_t ph = 0;
+    for (int kc = 0; kc < n_kc; kc++) {
+        tc::mbar_arrive_expect_tx(bar_full, (uint32_t)S * (16384u + B_BLOCK));
+        for (int sl = 0; sl < S; sl++) {
+            tc::bulk_g2s(sA + sl * 16384, a_blk0 + sl * a_s_stride + kc * a_kc_stride, 16384u, bar_full);
+            tc::bulk_g2s(sB + sl * B_BLOCK, b_blk0 + sl * b_s_stride + kc * b_kc_stride, B_BLOCK, bar_full);
+        }
+        if (!tc::mbar_wait(bar_full, ph, kWaitCycles)) {
+            tc::mbar_wait(bar_full, ph, kWaitCycles);  // once more for the copies still in flight
+            return false;
+        }
+        tc::fence_after_sync();
+        for (int sa = 0; sa < S; sa++) {
+            const uint64_t ad = tc::sdesc_sw128(tc::smem_addr(sA + sa * 16384));
+            for (int tb = 0; sa + tb < S; tb++) {
+                const uint64_t bd = tc::sdesc_sw128(tc::smem_addr(sB + tb * B_BLOCK));
+                const uint32_t dt = tm + (uint32_t)((sa + tb) * TN);
+#pragma unroll
+                for (int ks = 0; ks < 4; ks++)
+                    tc::mma_bf16(dt, ad + 2 * ks, bd + 2 * ks, idesc, (kc | sa | ks) ? 1u : 0u);
+            }
+        }
+        tc::mma_commit(bar_mma);
+        if (!tc::mbar_wait(bar_mma, ph, kWaitCycles)) {
+            tc::mbar_wait(bar_mma, ph, kWaitCycles);  // once more for the MMAs still in flight
+            return false;
+        }
+        ph ^= 1;
+    }
+    return true;
+}
+
+// Integer recombination of the S group accumulators for 16 columns of this thread's row:
+// value = hi 64^-8 + lo 64^-11 (in units of 2^(e_i + e_j)), hi = sum_{g<=6} M_g 64^(6-g),
+// lo = sum_{g>=7} M_g 64^(9-g); both exact in 64 bits (|M_g| < 2^24).
+__device__ __forceinline__ void combine16(uint32_t tm_row, int c0, int S, long long (&hi)[16], long long (&lo)[16]) {
+#pragma unroll
+    for (int jj = 0; jj < 16; jj++) hi[jj] = lo[jj] = 0;
+    for (int g = 0; g < S; g++) {
+        uint32_t r[16];
+        tc::tmem_ld16(tm_row + (uint32_t)(g * TN + c0), r);
+        tc::tmem_ld_wait();
+        const long long w = g <= 6 ? (1LL << (6 * (6 - g))) : (1LL << (6 * (9 - g)));
+#pragma unroll
+        for (int jj = 0; jj < 16; jj++) {
+            const long long m = (long long)__float2int_rn(__uint_as_float(r[jj]));
+            if (g <= 6) hi[jj] += m * w;
+            else lo[jj] += m * w;
+        }
+    }
+}
+
+// 2^(e_i + e_j) (hi 64^-8 + lo 64^-11)
+__device__ __forceinline__ double recombine(long long hi, long long lo, int eij) {
+    return fma((double)lo, pow2(eij - 66), (double)hi * pow2(eij - 48));
+}
+
+struct TcShared {
+    uint64_t bar_full, bar_mma;
+    uint32_t tmem;
+    int abort;
+};
+
+__device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
+    return reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+}
+
+__device__ __forceinline__ uint32_t tc_setup(TcShared &sh) {
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&sh.bar_full, 1);
+        tc::mbar_init(&sh.bar_mma, 1);
+        tc::fence_mbar_init();
+        sh.abort = 0;
+    }
+    __syncwarp();
+    if (warp == 0) {
+        tc::tmem_alloc(&sh.tmem, 512);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    return sh.tmem;
+}
+
+__device__ __forceinline__ void tc_teardown(uint32_t tm) {
+    tc::fence_before_sync();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(tm, 512);
+}
+
+__global__ void __launch_bounds__(128, 1) h_tc_kernel(DevSystem s, const HWork *__restrict__ work, int32_t w0,
+                                                     const uint8_t *__restrict__ slices, const int64_t *__restrict__ sl_off,
+                                                     const int32_t *__restrict__ expo, int S, double *__restrict__ H,
+                                                     int32_t *__restrict__ err) {
+    extern __shared__ uint8_t smem_dyn[];
+    __shared__ TcShared sh;
+    uint8_t *sA = align1024(smem_dyn), *sB = sA + S * 16384;
+    const HWork it = work[w0 + blockIdx.x];  // batch, 128-row tile, 48-column tile
+    const int b = it.batch;
+    const int P = s.batch_off[b + 1] - s.batch_off[b];
+    const int N = s.rel_off[b + 1] - s.rel_off[b];
+    const SplitGeom G(P, N);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t tm = tc_setup(sh);
+    if (threadIdx.x == 0) {
+        const uint8_t *setA = slices + sl_off[b];
+        const uint8_t *setB = setA + G.h_setA(S);
+        const bool ok = slice_mainloop(sA, sB, &sh.bar_full, &sh.bar_mma, tm, S, G.n_kc,
+                                       setA + (size_t)(2 * it.ti) * 8192, (size_t)G.n_rt * 8192,
+                                       (size_t)G.n_kc * G.n_rt * 8192, setB + (size_t)it.tj * B_BLOCK,
+                                       (size_t)G.n_jt * B_BLOCK, (size_t)G.n_kc * G.n_jt * B_BLOCK);
+        if (!ok) {
+            sh.abort = 1;
+            atomicExch(err, (int)NAO_ERR_TIMEOUT);
+        }
+    }
+    __syncthreads();
+    tc::fence_after_sync();
+    if (!sh.abort) {
+        const int i = it.ti * 128 + warp * 32 + lane;
+        const bool row_ok = i < N;
+        const int32_t *rel = s.rel_idx + s.rel_off[b];
+        const int32_t *ex = expo + s.rel_off[b];
+        const int ei = row_ok ? ex[i] : -10000;
+        const int64_t gi = row_ok ? rel[i] : 0;
+        const uint32_t tm_row = tm + ((uint32_t)(warp * 32) << 16);
+        for (int c0 = 0; c0 < TN; c0 += 16) {
+            long long hi[16], lo[16];
+            combine16(tm_row, c0, S, hi, lo);
+#pragma unroll
+            for (int jj = 0; jj < 16; jj++) {
+                const int j = it.tj * TN + c0 + jj;
+                if (!row_ok || j >= N || j < i) continue;
+                const int ej = ex[j];
+                if (ei <= -10000 || ej <= -10000) continue;
+                atomicAdd(H + gi * s.nb + rel[j], recombine(hi[jj], lo[jj], ei + ej));
+            }
+        }
+    }
+    tc_teardown(tm);
+}
+
+__global__ void __launch_bounds__(128, 1) n_tc_kernel(DevSystem s, const HWork *__restrict__ work, int32_t w0,
+                                                     const uint8_t *__restrict__ slices, const int64_t *__restrict__ sl_off,
+                                                     const int32_t *__restrict__ expo_q, const int32_t *__restrict__ expo_b,
+                                                     const double *__restrict__ scratch, int S, double *__restrict__ nout,
+                                                     int32_t *__restrict__ err) {
+    extern __shared__ uint8_t smem_dyn[];
+    __shared__ TcShared sh;
+    uint8_t *sA = align1024(smem_dyn), *sB = sA + S * 16384;
+    const HWork it = work[w0 + blockIdx.x];  // batch, 128-point tile, 48-function tile
+    const int b = it.batch;
+    const int p0 = s.batch_off[b], P = s.batch_off[b + 1] - p0;
+    const int Ppad = (P + NAO_PPAD - 1) & ~(NAO_PPAD - 1);
+    const int N = s.rel_off[b + 1] - s.rel_off[b];
+    const SplitGeom G(P, N);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t tm = tc_setup(sh);
+    if (threadIdx.x == 0) {
+        const uint8_t *setA = slices + sl_off[b];
+        const uint8_t *setB = setA + G.n_setA(S);
+        // P' is zero for basis functions beyond tile J, so K stops at 48 (J + 1)
+        int n_kc = ((it.tj + 1) * TN + 63) / 64;
+        n_kc = n_kc < G.n_kcN ? n_kc : G.n_kcN;
+        const bool ok = slice_mainloop(sA, sB, &sh.bar_full, &sh.bar_mma, tm, S, n_kc,
+                                       setA + (size_t)it.ti * 16384, (size_t)G.n_qt * 16384,
+                                       (size_t)G.n_kcN * G.n_qt * 16384, setB + (size_t)it.tj * B_BLOCK,
+                                       (size_t)G.n_jtN * B_BLOCK, (size_t)G.n_kcN * G.n_jtN * B_BLOCK);
+        if (!ok) {
+            sh.abort = 1;
+            atomicExch(err, (int)NAO_ERR_TIMEOUT);
+        }
+    }
+    __syncthreads();
+    tc::fence_after_sync();
+    if (!sh.abort) {
+        const int q = it.ti * 128 + warp * 32 + lane;
+        const bool row_ok = q < P;
+        const int eq = row_ok ? expo_q[p0 + q] : -10000;
+        const int eb = expo_b[b];
+        const double *E = scratch + s.scr_off[b];
+        const uint32_t tm_row = tm + ((uint32_t)(warp * 32) << 16);
+        double part_hi = 0.0, part_lo = 0.0;
+        for (int c0 = 0; c0 < TN; c0 += 16) {
+            long long hi[16], lo[16];
+            combine16(tm_row, c0, S, hi, lo);
+#pragma unroll
+            for (int jj = 0; jj < 16; jj++) {
+                const int j = it.tj * TN + c0 + jj;
+                if (row_ok && j < N) {
+                    const double f = E[(int64_t)j * Ppad + q];
+                    part_hi = fma((double)hi[jj], f, part_hi);
+                    part_lo = fma((double)lo[jj], f, part_lo);
+                }
+            }
+        }
+        if (row_ok && eq > -10000 && eb > -10000)
+            atomicAdd(nout + s.perm[p0 + q], fma(part_lo, pow2(eq + eb - 66), part_hi * pow2(eq + eb - 48)));
+    }
+    tc_teardown(tm);
+}
+
+// sum over each density tile of 64 points of w n (then the deterministic final reduction)
+__global__ void __launch_bounds__(256) wn_partial_kernel(DevSystem s, const DWork *__restrict__ work, int32_t w0,
+                                                        const double *__restrict__ nout, double *__restrict__ ne_part) {
+    __shared__ double red[8];
+    const DWork it = work[w0 + blockIdx.x];
+    const int p0 = s.batch_off[it.batch], P = s.batch_off[it.batch + 1] - p0;
+    const int q = it.tp * NAO_TILE + threadIdx.x;
+    double wn = 0.0;
+    if (threadIdx.x < NAO_TILE && q < P) wn = s.pw[p0 + q] * nout[s.perm[p0 + q]];
+    for (int o = 16; o > 0; o >>= 1) wn += __shfl_xor_sync(0xffffffffu, wn, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = wn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; w++) t += red[w];
+        ne_part[w0 + blockIdx.x] = t;
+    }
+}
+
+}  // namespace
+
+size_t split_smem_bytes(int S) { return (size_t)S * (16384 + B_BLOCK) + 1024; }
+
+cudaError_t split_configure() {
+    const int bytes = (int)split_smem_bytes(NAO_SPLIT_MAX_SLICES);
+    cudaError_t e = cudaFuncSetAttribute(h_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(n_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+cudaError_t launch_slice_h(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_rt, const double *scratch,
+                           const double *v, uint32_t terms, uint8_t *slices, const int64_t *sl_off, int32_t *expo, int S,
+                           cudaStream_t st) {
+    if (b1 <= b0 || max_rt <= 0) return cudaSuccess;
+    slice_h_kernel<<<dim3(b1 - b0, max_rt), 256, 0, st>>>(s, b0, scratch, v, terms, slices, sl_off, expo, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_h_tc(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
+                        const int64_t *sl_off, const int32_t *expo, int S, double *H, int32_t *err, cudaStream_t st) {
+    if (n_work <= 0) return cudaSuccess;
+    h_tc_kernel<<<n_work, 128, split_smem_bytes(S), st>>>(s, work, w0, slices, sl_off, expo, S, H, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slice_n(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_qt, const double *scratch,
+                           const double *P, uint8_t *slices, const int64_t *sl_off, int32_t *expo_q, int32_t *expo_b,
+                           int S, cudaStream_t st) {
+    if (b1 <= b0) return cudaSuccess;
+    if (max_qt > 0) slice_nphi_kernel<<<dim3(b1 - b0, max_qt), 128, 0, st>>>(s, b0, scratch, slices, sl_off, expo_q, S);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    slice_np_kernel<<<b1 - b0, 256, 0, st>>>(s, b0, P, slices, sl_off, expo_b, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_n_tc(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
+                        const int64_t *sl_off, const int32_t *expo_q, const int32_t *expo_b, const double *scratch, int S,
+                        double *n, int32_t *err, cudaStream_t st) {
+    if (n_work <= 0) return cudaSuccess;
+    n_tc_kernel<<<n_work, 128, split_smem_bytes(S), st>>>(s, work, w0, slices, sl_off, expo_q, expo_b, scratch, S, n,
+                                                          err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wn_partial(const DevSystem &s, const DWork *work, int32_t w0, int32_t n_work, const double *n,
+                              double *ne_part, cudaStream_t st) {
+    if (n_work <= 0) return cudaSuccess;
+    wn_partial_kernel<<<n_work, 256, 0, st>>>(s, work, w0, n, ne_part);
+    return cudaGetLastError();
+}

@@ -19,6 +19,8 @@ _lib = None
 
 NAO_FP64, NAO_FP32, NAO_SPLIT = 0, 1, 2
 NAO_TERM_POTENTIAL, NAO_TERM_KINETIC = 1, 2
+NAO_OK, NAO_ERR_INVALID_ARG, NAO_ERR_OUT_OF_MEMORY, NAO_ERR_CUDA = 0, 1, 2, 3
+NAO_ERR_TIMEOUT, NAO_ERR_INTERNAL, NAO_ERR_UNSUPPORTED = 4, 5, 6
 PRECISIONS = {"fp64": NAO_FP64, "fp32": NAO_FP32, "split": NAO_SPLIT}
 
 STATUS = {0: "NAO_OK", 1: "NAO_ERR_INVALID_ARG", 2: "NAO_ERR_OUT_OF_MEMORY", 3: "NAO_ERR_CUDA",

@@ -31,7 +31,7 @@ def test_status_strings_and_defaults():
     assert nao.nao_status_string(0) == "ok"
     assert nao.nao_status_string(1) == "invalid argument"
     o = nao.nao_default_options()
-    assert o.max_batch_points == 200 and o.split_slices == 8 and o.device == -1
+    assert o.max_batch_points == 200 and o.split_slices == 10 and o.device == -1
 
 
 def _bad(sys_, **opts):

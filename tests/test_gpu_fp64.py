@@ -50,7 +50,12 @@ def test_partition_and_relevance_bit_exact(water):
 def test_basis_functions_match_oracle(water):
     s, o, g = water["s"], water["o"], water["g"]
     bo, pp, ro, ri = g.batches()
-    for b in [0, 7, 33, 65]:
+    nonempty = np.nonzero(np.diff(ro))[0]
+    empty = np.nonzero(np.diff(ro) == 0)[0]
+    assert len(nonempty) > 4 and len(empty) > 0
+    phi, grad = g.evaluate_batch(int(empty[0]))
+    assert phi.numel() == 0
+    for b in [int(nonempty[0]), int(nonempty[len(nonempty) // 2]), int(nonempty[-1])]:
         phi, grad = g.evaluate_batch(b)
         pts = s.pt_xyz[pp[bo[b]:bo[b + 1]]]
         rphi, rgrad = o.eval_dense(pts)

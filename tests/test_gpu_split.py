@@ -1,0 +1,83 @@
+"""GPU parity of the split-precision (Ozaki slices on tcgen05 tensor cores) path against the
+FP64 oracle: e_H, e_n <= 1e-10 (tests/_metrics.py); the error falls as slices are added."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_1912_06636_gb300 import nao, synth
+from tests._metrics import raw_rel_err, rel_err
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.fixture(scope="module")
+def water():
+    s = synth.config_water()
+    o = oracle.Oracle(s)
+    v = s.potential()
+    P = synth.density_matrix(s, 0)
+    H, A = o.hamiltonian(s.pt_xyz, s.pt_w, v)
+    n, D, ne = o.density(s.pt_xyz, P, s.pt_w)
+    return dict(s=s, o=o, v=v, P=P, H=H, A=A, n=n, D=D, ne=ne)
+
+
+def run(water, **opts):
+    with nao.Grid(water["s"], device=0, **opts) as g:
+        H = g.integrate_h(cuda(water["v"]), prec="split")
+        n, ne = g.update_density(cuda(water["P"]), prec="split")
+        torch.cuda.synchronize()
+        g.sync()
+        return H.cpu().numpy(), n.cpu().numpy(), float(ne.item())
+
+
+def test_split_hamiltonian_and_density(water):
+    H, n, ne = run(water)
+    assert np.array_equal(H, H.T)
+    eH = rel_err(H, water["H"], water["A"])
+    en = rel_err(n, water["n"], water["D"])
+    print(f"split e_H={eH:.2e} (raw {raw_rel_err(H, water['H'], water['A']):.2e}) e_n={en:.2e}")
+    assert eH <= TOL and en <= TOL
+    assert abs(ne - water["ne"]) <= TOL * abs(water["ne"])
+
+
+def test_split_overlap_and_kinetic(water):
+    s, o = water["s"], water["o"]
+    S_ref, SA = o.overlap(s.pt_xyz, s.pt_w)
+    T_ref, TA = o.hamiltonian(s.pt_xyz, s.pt_w, None, oracle.TERM_KINETIC)
+    with nao.Grid(s, device=0) as g:
+        S = g.overlap(prec="split").cpu().numpy()
+        T = g.integrate_h(None, nao.NAO_TERM_KINETIC, prec="split").cpu().numpy()
+    assert rel_err(S, S_ref, SA) <= TOL
+    assert rel_err(T, T_ref, TA) <= TOL
+
+
+def test_split_error_falls_with_slices(water):
+    errs = []
+    for S in (4, 6, 8, 10):
+        H, n, _ = run(water, split_slices=S)
+        errs.append((rel_err(H, water["H"], water["A"]), rel_err(n, water["n"], water["D"])))
+    print("split errors by slices 4,6,8,10:", errs)
+    assert errs[0][0] > errs[2][0] and errs[0][1] > errs[2][1]
+    assert errs[3][0] <= TOL and errs[3][1] <= TOL
+
+
+@pytest.mark.parametrize("B", [1, 37, 128, 400])
+def test_split_independent_of_batch_size(water, B):
+    H, n, _ = run(water, max_batch_points=B)
+    assert rel_err(H, water["H"], water["A"]) <= TOL
+    assert rel_err(n, water["n"], water["D"]) <= TOL
+
+
+def test_split_rejects_batches_too_large_for_exact_sums(water):
+    with nao.Grid(water["s"], device=0, max_batch_points=1024) as g:
+        with pytest.raises(nao.NaoError) as e:
+            g.integrate_h(cuda(water["v"]), prec="split")
+        assert e.value.code == nao.NAO_ERR_UNSUPPORTED

@@ -144,3 +144,24 @@ def test_polar_axis_and_nucleus_are_reported():
         o.eval_dense(np.array([[0.0, 0.0, 0.7]]))
     with pytest.raises(orc.OracleError):
         o.eval_dense(np.array([[0.0, 0.0, 0.0]]))
+
+
+def test_spline_near_cutoff_is_only_absolutely_accurate():
+    """Near the cutoff the spline crosses zero, so R is ill-conditioned in r: moving r by a
+    few ulps (the rounding of s = ln(r/r0)/Delta is ~1e-13 at s ~ 970) changes R by ~1e-12
+    relative while the change stays ~1e-21 of the table's scale. Two correct FP64 evaluations
+    therefore agree there only absolutely, which is why the parity measures floor their
+    denominators (tests/_metrics.py)."""
+    s = synth.config_water(n_rad=4, n_theta=2, n_phi=3)
+    o = Oracle(s)
+    f = 2  # l = 1, alpha = 0.4: non-negligible all the way to the cutoff
+    scale = np.abs(s.fn_table[f]).max()
+    worst_rel = 0.0
+    for r in np.linspace(5.95, 5.9999, 200):
+        r2 = r * (1.0 + 4e-16)
+        R1, _ = o.radial(f, r)
+        R2, _ = o.radial(f, r2)
+        assert abs(R1 - R2) <= 1e-15 * scale
+        if R1 != 0.0:
+            worst_rel = max(worst_rel, abs(R1 - R2) / abs(R1))
+    assert worst_rel > 1e-13
