@@ -32,6 +32,7 @@
 #ifndef NAO_H
 #define NAO_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -203,6 +204,27 @@ typedef struct {
 
 nao_status nao_profile_enable(nao_grid *g, int32_t enable);
 nao_status nao_profile_read(nao_grid *g, nao_profile *out, int32_t reset);
+
+/* Hamiltonian integration that allocates nothing. The paper has no counterpart; this is a
+ * library convenience. Some callers cannot allocate device memory where they integrate:
+ * an application whose own memory manager owns all device memory, or a latency-bound loop
+ * that must not call cudaMalloc/cudaFree (they can synchronise the device). This call
+ * computes the same H as nao_integrate_h with NAO_FP64 (same kernels) but evaluates the
+ * basis functions into a fixed device array of NAO_NOALLOC_SCRATCH_BYTES compiled into the
+ * library, and calls no allocating routine.
+ *   - The handle's evaluation chunks must fit the array: create the handle with
+ *     options.scratch_bytes <= NAO_NOALLOC_SCRATCH_BYTES; otherwise NAO_ERR_INVALID_ARG and
+ *     nothing is enqueued.
+ *   - Every GPU that loads the library holds the array until the process exits.
+ *   - All calls on a device share the array; it keeps the last call's contents (nothing in
+ *     it needs clearing: every entry read is first written by the same call). Calls whose
+ *     work overlaps on the GPU (other streams or handles) race on it.
+ *   - The first call on a device looks up the array's device address; make that first call
+ *     before any stream capture.
+ * Arguments and errors as nao_integrate_h (no precision argument: FP64).                    */
+#define NAO_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+nao_status nao_integrate_h_noalloc(nao_grid *g, const double *v_dev, uint32_t terms, double *H_dev,
+                                   void *cuda_stream);
 
 /* Wait for the handle's enqueued work and report a device-side failure, if any. */
 nao_status nao_sync_status(nao_grid *g);

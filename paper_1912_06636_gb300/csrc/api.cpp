@@ -513,6 +513,8 @@ nao_status run_n(nao_grid *g, const double *P, nao_precision prec, double *n, do
 
 }  // namespace
 
+void nao_set_last_error(const std::string &msg) { g_last_error = msg; }
+
 extern "C" {
 
 nao_status nao_default_options(nao_options *o) {

@@ -168,6 +168,9 @@ cudaError_t launch_n_tc(const DevSystem &s, const HWork *work, int32_t w0, int32
 cudaError_t launch_wn_partial(const DevSystem &s, const DWork *work, int32_t w0, int32_t n_work, const double *n,
                               double *ne_part, cudaStream_t st);
 
+// Records the text nao_last_error() returns on the calling thread (api.cpp).
+void nao_set_last_error(const std::string &msg);
+
 // ---- host helpers (partition.cpp) --------------------------------------------------------
 // Recursive bisection (see nao_grid_create in nao.h); returns the number of batches.
 int64_t nao_partition(int64_t n, const double *xyz, int64_t B, std::vector<int64_t> &offsets,

@@ -31,8 +31,9 @@ SYMBOLS = [
     "nao_default_options", "nao_grid_create", "nao_destroy", "nao_get_info", "nao_export_batches",
     "nao_integrate_h", "nao_update_density", "nao_integrate_h_host", "nao_update_density_host",
     "nao_evaluate_batch", "nao_sync_status", "nao_status_string", "nao_last_error",
-    "nao_profile_enable", "nao_profile_read",
+    "nao_profile_enable", "nao_profile_read", "nao_integrate_h_noalloc",
 ]
+NAO_NOALLOC_SCRATCH_BYTES = 32 << 20
 KERNELS = ["eval_grad", "eval_phi", "h_fp64", "h_fp32", "h_split", "slice", "mirror", "n_fp64", "n_fp32",
            "n_split", "reduce"]
 
@@ -100,6 +101,7 @@ def load():
         "nao_last_error": ([], C.c_char_p),
         "nao_profile_enable": ([P, I32], C.c_int),
         "nao_profile_read": ([P, P, I32], C.c_int),
+        "nao_integrate_h_noalloc": ([P, P, U32, P, P], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -225,6 +227,12 @@ def nao_evaluate_batch(h, batch: int, prec, phi, grad=None, stream=None) -> None
 
 def nao_sync_status(h) -> None:
     _check(load().nao_sync_status(h), "nao_sync_status")
+
+
+def nao_integrate_h_noalloc(h, v, terms: int, H, stream=None) -> None:
+    """FP64 Hamiltonian with the library's fixed device scratch (no allocation of any kind)."""
+    _check(load().nao_integrate_h_noalloc(h, _dptr(v), int(terms), _dptr(H), _stream(stream)),
+           "nao_integrate_h_noalloc")
 
 
 def nao_profile_enable(h, enable: bool = True) -> None:
