@@ -117,7 +117,7 @@ FP64_PEAK_TFLOPS_MEASURED = None  # filled from profiles/fp64_peak.txt when pres
 
 
 def fp64_peak():
-    path = os.path.join(ROOT, "profiles", "fp64_peak.txt")
+    path = os.path.join(ROOT, "profiles", "peaks_fp64_fp32_dmma.txt")
     try:
         for line in open(path):
             if line.startswith("fp64_fma_tflops"):

@@ -408,7 +408,7 @@ nao_status split_setup(nao_grid *g) {
             if (N > 0) {
                 cur.max_rt = std::max<int32_t>(cur.max_rt, G.h_slice_tiles());
                 cur.max_qt = std::max<int32_t>(cur.max_qt, G.n_qt);
-                const int nI = (N + 127) / 128, nJ = G.n_jt;
+                const int nI = (N + 127) / 128, nJ = (N + NAO_SPLIT_TN - 1) / NAO_SPLIT_TN;
                 for (int I = 0; I < nI; I++)
                     for (int J = 0; J < nJ; J++)
                         if (I * 128 <= J * NAO_SPLIT_TN + NAO_SPLIT_TN - 1) hw.push_back({b, I, J, 0});
@@ -430,6 +430,7 @@ nao_status split_setup(nao_grid *g) {
         (st = dev_alloc(g, &g->d_expo_h, (size_t)std::max<int64_t>(g->rel_total, 1))) ||
         (st = dev_alloc(g, &g->d_expo_q, (size_t)g->n_points)) ||
         (st = dev_alloc(g, &g->d_expo_b, (size_t)g->n_batches)) ||
+        (st = dev_alloc(g, &g->d_neg16, (size_t)g->n_batches)) ||
         (st = upload(g, &g->d_split_hw, hw.data(), hw.size())) || (st = upload(g, &g->d_split_nw, nw.data(), nw.size())))
         return st;
     g->split_S = S;
@@ -447,11 +448,11 @@ nao_status run_h_split(nao_grid *g, const double *v, uint32_t terms, double *H, 
         NAO_CUDA(timed(g, NAO_K_EVAL_GRAD, st, [&] { return launch_eval(s, c.b0, c.b1, NAO_FP64, true, g->d_scratch, st); }));
         NAO_CUDA(timed(g, NAO_K_SLICE, st, [&] {
             return launch_slice_h(s, c.b0, c.b1, c.max_rt, g->d_scratch, v, terms, g->d_slices, g->d_sl_off_h, g->d_expo_h,
-                                  S, st);
+                                  g->d_neg16, S, st);
         }));
         NAO_CUDA(timed(g, NAO_K_H_SPLIT, st, [&] {
-            return launch_h_tc(s, g->d_split_hw, c.hw0, c.hw1 - c.hw0, g->d_slices, g->d_sl_off_h, g->d_expo_h, S, H,
-                               g->d_err, st);
+            return launch_h_tc(s, g->d_split_hw, c.hw0, c.hw1 - c.hw0, g->d_slices, g->d_sl_off_h, g->d_expo_h,
+                               g->d_neg16, S, H, g->d_err, st);
         }));
     }
     NAO_CUDA(timed(g, NAO_K_MIRROR, st, [&] { return launch_mirror(H, g->nb, st); }));

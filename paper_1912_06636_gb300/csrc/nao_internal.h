@@ -46,27 +46,27 @@ struct DevSystem {
 };
 
 // Geometry of one batch's operand slices on the split path (shared by host and device code).
-// H: A rows (basis functions) in 64-row blocks, 128-row MMA tiles; B rows in 48-row blocks;
-//    K = 4 Ppad in chunks of 64. Density: A rows (points) in 128-row blocks, K = basis in
-//    chunks of 64; B rows (basis) in 48-row blocks. One block = rows x 64 bf16, 128 B per row.
+// H: one digit set; per (slice, K chunk of 64) a row-contiguous block of R_pad rows x 128 B
+//    (128-byte swizzle inside 8-row atoms), so a 128-row A tile and a 48-row B tile are plain
+//    byte ranges. K holds the 4 Ppad weighted columns reordered so that negative-weight
+//    columns come first, padded to a multiple of 16 (the MMA negates B on those K steps).
+// Density: A rows (points) in 128-row blocks, K = basis in chunks of 64; B rows (basis) in
+//    48-row blocks. One block = rows x 64 bf16, 128 B per row.
 struct SplitGeom {
-    int n_kc, n_rt, n_jt;        // H: K chunks, A 64-row blocks (even), B 48-row blocks
+    int n_kc, R_pad;             // H: K chunks, padded rows
     int n_kcN, n_qt, n_jtN;      // density: K chunks, A 128-point blocks, B 48-row blocks
     __host__ __device__ SplitGeom(int P, int N) {
         const int Ppad = (P + NAO_PPAD - 1) / NAO_PPAD * NAO_PPAD;
-        n_kc = Ppad / 16;
-        n_rt = 2 * ((N + 127) / 128);
-        n_jt = (N + NAO_SPLIT_TN - 1) / NAO_SPLIT_TN;
+        n_kc = (4 * Ppad + 16 + 63) / 64;
+        const int ra = 128 * ((N + 127) / 128), rb = NAO_SPLIT_TN * ((N + NAO_SPLIT_TN - 1) / NAO_SPLIT_TN);
+        R_pad = ra > rb ? ra : rb;
         n_kcN = (N + 63) / 64;
         n_qt = (P + 127) / 128;
-        n_jtN = n_jt;
+        n_jtN = (N + NAO_SPLIT_TN - 1) / NAO_SPLIT_TN;
     }
-    __host__ __device__ size_t h_setA(int S) const { return (size_t)S * n_kc * n_rt * 8192; }
-    __host__ __device__ size_t h_bytes(int S) const { return h_setA(S) + (size_t)S * n_kc * n_jt * (NAO_SPLIT_TN * 128); }
-    __host__ __device__ int h_slice_tiles() const {  // 64-row tiles the H slicing covers
-        const int ra = n_rt * 64, rb = n_jt * NAO_SPLIT_TN;
-        return ((ra > rb ? ra : rb) + 63) / 64;
-    }
+    __host__ __device__ size_t h_block(int s, int kc) const { return ((size_t)s * n_kc + kc) * (size_t)R_pad * 128; }
+    __host__ __device__ size_t h_bytes(int S) const { return (size_t)S * n_kc * (size_t)R_pad * 128; }
+    __host__ __device__ int h_slice_tiles() const { return R_pad / 64 + (R_pad % 64 ? 1 : 0); }
     __host__ __device__ size_t n_setA(int S) const { return (size_t)S * n_kcN * n_qt * 16384; }
     __host__ __device__ size_t n_bytes(int S) const { return n_setA(S) + (size_t)S * n_kcN * n_jtN * (NAO_SPLIT_TN * 128); }
 };
@@ -121,6 +121,7 @@ struct nao_grid {
     uint8_t *d_slices = nullptr;
     int64_t *d_sl_off_h = nullptr, *d_sl_off_n = nullptr;
     int32_t *d_expo_h = nullptr, *d_expo_q = nullptr, *d_expo_b = nullptr;
+    int32_t *d_neg16 = nullptr;  // per batch: leading negative-weight K steps of 16 columns
     HWork *d_split_hw = nullptr, *d_split_nw = nullptr;
     int64_t n_split_hw = 0, n_split_nw = 0;
     // kernel timing (nao_profile_enable)
@@ -155,10 +156,11 @@ cudaError_t launch_reduce_sum(const double *part, int64_t n, double *out, cudaSt
 size_t split_smem_bytes(int S);
 cudaError_t split_configure();
 cudaError_t launch_slice_h(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_rt, const double *scratch,
-                           const double *v, uint32_t terms, uint8_t *slices, const int64_t *sl_off, int32_t *expo, int S,
-                           cudaStream_t st);
+                           const double *v, uint32_t terms, uint8_t *slices, const int64_t *sl_off, int32_t *expo,
+                           int32_t *neg16, int S, cudaStream_t st);
 cudaError_t launch_h_tc(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
-                        const int64_t *sl_off, const int32_t *expo, int S, double *H, int32_t *err, cudaStream_t st);
+                        const int64_t *sl_off, const int32_t *expo, const int32_t *neg16, int S, double *H, int32_t *err,
+                        cudaStream_t st);
 cudaError_t launch_slice_n(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_qt, const double *scratch,
                            const double *P, uint8_t *slices, const int64_t *sl_off, int32_t *expo_q, int32_t *expo_b,
                            int S, cudaStream_t st);

@@ -37,16 +37,13 @@ __device__ __forceinline__ uint32_t bf16_bits(int d) { return __float_as_uint((f
 // S balanced base-64 digits of X, |X| <= 32 * 64^(S-1) (most significant first in dig[0]).
 // The S-1 lower digits are taken in [-32, 31]; the top digit is what remains, which the bound
 // on |X| keeps in [-32, 32] (it must not be reduced modulo 64, or a carry would be lost).
-__device__ __forceinline__ void digits(long long X, int S, int (&dig)[NAO_SPLIT_MAX_SLICES]) {
+template <int S>
+__device__ __forceinline__ void digits(long long X, int (&dig)[S]) {
 #pragma unroll
-    for (int s = NAO_SPLIT_MAX_SLICES - 1; s >= 1; s--) {
-        if (s < S) {
-            const int d = (int)(((X + 32) & 63LL)) - 32;
-            dig[s] = d;
-            X = (X - d) >> 6;
-        } else {
-            dig[s] = 0;
-        }
+    for (int s = S - 1; s >= 1; s--) {
+        const int d = (int)(((X + 32) & 63LL)) - 32;
+        dig[s] = d;
+        X = (X - d) >> 6;
     }
     dig[0] = (int)X;
 }
@@ -71,14 +68,19 @@ constexpr int TN = NAO_SPLIT_TN;            // 48
 constexpr uint32_t B_BLOCK = TN * 128;      // bytes of a 48-row block
 
 // ----------------------------------------------------------------------------------------
-// Hamiltonian slicing: one CTA per (batch, 64-row tile of basis functions)
+// Hamiltonian slicing: one CTA per (batch, 64-row tile of basis functions). Columns are
+// reordered: the negative-weight ones (v < 0 on the potential part) first, padded to a
+// multiple of 16, then the rest, so that B = A and the sign is applied per 16-column K step.
 // ----------------------------------------------------------------------------------------
+template <int S>
 __global__ void __launch_bounds__(256) slice_h_kernel(DevSystem s, int32_t b0, const double *__restrict__ scratch,
                                                      const double *__restrict__ v, uint32_t terms,
                                                      uint8_t *__restrict__ slices, const int64_t *__restrict__ sl_off,
-                                                     int32_t *__restrict__ expo, int S) {
+                                                     int32_t *__restrict__ expo, int32_t *__restrict__ neg16) {
     __shared__ double sd[4 * NAO_SPLIT_MAX_PPAD];
-    __shared__ int sgn[4 * NAO_SPLIT_MAX_PPAD];
+    __shared__ short src[4 * NAO_SPLIT_MAX_PPAD + 64];
+    __shared__ unsigned char negf[4 * NAO_SPLIT_MAX_PPAD];
+    __shared__ int wsum[8];
     __shared__ int ex_s[64];
     const int b = b0 + blockIdx.x, rt = blockIdx.y;
     const int p0 = s.batch_off[b], P = s.batch_off[b + 1] - p0;
@@ -86,7 +88,7 @@ __global__ void __launch_bounds__(256) slice_h_kernel(DevSystem s, int32_t b0, c
     const int N = s.rel_off[b + 1] - s.rel_off[b];
     const SplitGeom G(P, N);
     if (N == 0 || rt >= G.h_slice_tiles()) return;
-    const int K = 4 * Ppad;
+    const int K = 4 * Ppad, Kp = 64 * G.n_kc;
     const double *E = scratch + s.scr_off[b];
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         const int c = k / Ppad, q = k - c * Ppad;
@@ -95,10 +97,38 @@ __global__ void __launch_bounds__(256) slice_h_kernel(DevSystem s, int32_t b0, c
         if (c == 0) d = (terms & NAO_TERM_POTENTIAL) && q < P ? w * (v ? v[s.perm[p0 + q]] : 1.0) : 0.0;
         else d = (terms & NAO_TERM_KINETIC) ? 0.5 * w : 0.0;
         sd[k] = sqrt(fabs(d));
-        sgn[k] = d < 0.0 ? -1 : 1;
+        negf[k] = d < 0.0 ? 1 : 0;
     }
+    for (int k = threadIdx.x; k < Kp; k += blockDim.x) src[k] = -1;
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // exclusive scan of the negative flags: thread t owns columns [t*per, t*per + per)
+    const int per = (K + 255) / 256;
+    const int kb = threadIdx.x * per, ke = min(K, kb + per);
+    int cnt = 0;
+    for (int k = kb; k < ke; k++) cnt += negf[k];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < 8; w++) {
+        if (w < warp) before += wsum[w];
+        total += wsum[w];
+    }
+    before += incl - cnt;
+    const int negpad = (total + 15) & ~15;
+    for (int k = kb; k < ke; k++) {
+        const int pos = negf[k] ? before : negpad + k - before;
+        before += negf[k];
+        src[pos] = (short)k;
+    }
+    if (rt == 0 && threadIdx.x == 0) neg16[b] = negpad / 16;
+    __syncthreads();
     for (int lr = warp; lr < 64; lr += 8) {
         const int r = rt * 64 + lr;
         double mx = 0.0;
@@ -113,46 +143,32 @@ __global__ void __launch_bounds__(256) slice_h_kernel(DevSystem s, int32_t b0, c
         }
     }
     __syncthreads();
-    uint8_t *setA = slices + sl_off[b];
-    uint8_t *setB = setA + G.h_setA(S);
-    const int rowsA = G.n_rt * 64, rowsB = G.n_jt * TN;
-    const int groups = K / 8;
+    uint8_t *base = slices + sl_off[b];
+    const int groups = Kp / 8;
     for (int u = threadIdx.x; u < 64 * groups; u += blockDim.x) {
         const int lr = u / groups, k0 = (u - lr * groups) * 8;
         const int r = rt * 64 + lr;
-        if (r >= rowsA && r >= rowsB) continue;
+        if (r >= G.R_pad) continue;
         const int e = ex_s[lr];
-        int dg[8][NAO_SPLIT_MAX_SLICES];
-        if (r < N && e > -10000) {
-            const double scale = pow2(6 * S - e);
-            const double2 *src = reinterpret_cast<const double2 *>(E + (int64_t)r * K + k0);
+        int dg[8][S];
+        const double scale = (r < N && e > -10000) ? pow2(6 * S - e) : 0.0;
+        const double *row = E + (int64_t)(r < N ? r : 0) * K;
 #pragma unroll
-            for (int h = 0; h < 4; h++) {
-                const double2 x = src[h];
-                digits(__double2ll_rn((x.x * sd[k0 + 2 * h]) * scale), S, dg[2 * h]);
-                digits(__double2ll_rn((x.y * sd[k0 + 2 * h + 1]) * scale), S, dg[2 * h + 1]);
-            }
-        } else {
-#pragma unroll
-            for (int h = 0; h < 8; h++)
-#pragma unroll
-                for (int q = 0; q < NAO_SPLIT_MAX_SLICES; q++) dg[h][q] = 0;
+        for (int h = 0; h < 8; h++) {
+            const int kk = src[k0 + h];
+            const double x = (kk >= 0 && scale != 0.0) ? row[kk] * sd[kk] : 0.0;
+            digits<S>(__double2ll_rn(x * scale), dg[h]);
         }
         const int kc = k0 >> 6;
-        const uint32_t offA = tc::sw128_offset((uint32_t)lr, (uint32_t)(k0 & 63));
-        const int jt = r / TN;
-        const uint32_t offB = tc::sw128_offset((uint32_t)(r - jt * TN), (uint32_t)(k0 & 63));
-        for (int sl = 0; sl < S; sl++) {
-            uint4 va, vb;
-            uint32_t *pa = &va.x, *pb = &vb.x;
+        const uint32_t off = tc::sw128_offset((uint32_t)r, (uint32_t)(k0 & 63));
 #pragma unroll
-            for (int h = 0; h < 4; h++) {
-                pa[h] = bf16_bits(dg[2 * h][sl]) | (bf16_bits(dg[2 * h + 1][sl]) << 16);
-                pb[h] = bf16_bits(dg[2 * h][sl] * sgn[k0 + 2 * h]) | (bf16_bits(dg[2 * h + 1][sl] * sgn[k0 + 2 * h + 1]) << 16);
-            }
-            if (r < rowsA) *reinterpret_cast<uint4 *>(setA + ((size_t)(sl * G.n_kc + kc) * G.n_rt + rt) * 8192 + offA) = va;
-            if (r < rowsB)
-                *reinterpret_cast<uint4 *>(setB + ((size_t)(sl * G.n_kc + kc) * G.n_jt + jt) * B_BLOCK + offB) = vb;
+        for (int sl = 0; sl < S; sl++) {
+            uint4 va;
+            va.x = bf16_bits(dg[0][sl]) | (bf16_bits(dg[1][sl]) << 16);
+            va.y = bf16_bits(dg[2][sl]) | (bf16_bits(dg[3][sl]) << 16);
+            va.z = bf16_bits(dg[4][sl]) | (bf16_bits(dg[5][sl]) << 16);
+            va.w = bf16_bits(dg[6][sl]) | (bf16_bits(dg[7][sl]) << 16);
+            *reinterpret_cast<uint4 *>(base + G.h_block(sl, kc) + off) = va;
         }
     }
 }
@@ -160,9 +176,10 @@ __global__ void __launch_bounds__(256) slice_h_kernel(DevSystem s, int32_t b0, c
 // ----------------------------------------------------------------------------------------
 // Density slicing. Phi^T: one CTA (128 threads, one point each) per (batch, 128-point tile).
 // ----------------------------------------------------------------------------------------
+template <int S>
 __global__ void __launch_bounds__(128) slice_nphi_kernel(DevSystem s, int32_t b0, const double *__restrict__ scratch,
                                                         uint8_t *__restrict__ slices, const int64_t *__restrict__ sl_off,
-                                                        int32_t *__restrict__ expo_q, int S) {
+                                                        int32_t *__restrict__ expo_q) {
     const int b = b0 + blockIdx.x, qt = blockIdx.y;
     const int p0 = s.batch_off[b], P = s.batch_off[b + 1] - p0;
     const int Ppad = (P + NAO_PPAD - 1) & ~(NAO_PPAD - 1);
@@ -179,20 +196,22 @@ __global__ void __launch_bounds__(128) slice_nphi_kernel(DevSystem s, int32_t b0
     const double scale = e > -10000 ? pow2(6 * S - e) : 0.0;
     uint8_t *setA = slices + sl_off[b];
     for (int i0 = 0; i0 < G.n_kcN * 64; i0 += 8) {
-        int dg[8][NAO_SPLIT_MAX_SLICES];
+        int dg[8][S];
 #pragma unroll
         for (int h = 0; h < 8; h++) {
             const int i = i0 + h;
             const double x = (q < P && i < N && e > -10000) ? E[(int64_t)i * Ppad + q] : 0.0;
-            digits(__double2ll_rn(x * scale), S, dg[h]);
+            digits<S>(__double2ll_rn(x * scale), dg[h]);
         }
         const int kc = i0 >> 6;
         const uint32_t off = tc::sw128_offset((uint32_t)ql, (uint32_t)(i0 & 63));
+#pragma unroll
         for (int sl = 0; sl < S; sl++) {
             uint4 va;
-            uint32_t *pa = &va.x;
-#pragma unroll
-            for (int h = 0; h < 4; h++) pa[h] = bf16_bits(dg[2 * h][sl]) | (bf16_bits(dg[2 * h + 1][sl]) << 16);
+            va.x = bf16_bits(dg[0][sl]) | (bf16_bits(dg[1][sl]) << 16);
+            va.y = bf16_bits(dg[2][sl]) | (bf16_bits(dg[3][sl]) << 16);
+            va.z = bf16_bits(dg[4][sl]) | (bf16_bits(dg[5][sl]) << 16);
+            va.w = bf16_bits(dg[6][sl]) | (bf16_bits(dg[7][sl]) << 16);
             *reinterpret_cast<uint4 *>(setA + ((size_t)(sl * G.n_kcN + kc) * G.n_qt + qt) * 16384 + off) = va;
         }
     }
@@ -201,9 +220,10 @@ __global__ void __launch_bounds__(128) slice_nphi_kernel(DevSystem s, int32_t b0
 // P'_ij = c_IJ P[rel_i][rel_j] over 48-function tiles I = i/48 <= J = j/48 (c_II = 1,
 // c_IJ = 2), read from P's upper triangle. One CTA per batch: a per-batch exponent, then the
 // digits of rows j (48-row blocks), K = i (chunks of 64).
+template <int S>
 __global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, const double *__restrict__ Pm,
                                                       uint8_t *__restrict__ slices, const int64_t *__restrict__ sl_off,
-                                                      int32_t *__restrict__ expo_b, int S) {
+                                                      int32_t *__restrict__ expo_b) {
     __shared__ double red[8];
     __shared__ int e_sh;
     const int b = b0 + blockIdx.x;
@@ -237,62 +257,110 @@ __global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, 
     const int groups = G.n_kcN * 8;  // 8-wide groups along K = i
     for (int u = threadIdx.x; u < G.n_jtN * TN * groups; u += blockDim.x) {
         const int j = u / groups, i0 = (u - j * groups) * 8;
-        int dg[8][NAO_SPLIT_MAX_SLICES];
+        int dg[8][S];
 #pragma unroll
-        for (int h = 0; h < 8; h++) digits(__double2ll_rn(pval(i0 + h, j) * scale), S, dg[h]);
+        for (int h = 0; h < 8; h++) digits<S>(__double2ll_rn(pval(i0 + h, j) * scale), dg[h]);
         const int jt = j / TN, kc = i0 >> 6;
         const uint32_t off = tc::sw128_offset((uint32_t)(j - jt * TN), (uint32_t)(i0 & 63));
+#pragma unroll
         for (int sl = 0; sl < S; sl++) {
             uint4 vb;
-            uint32_t *pb = &vb.x;
-#pragma unroll
-            for (int h = 0; h < 4; h++) pb[h] = bf16_bits(dg[2 * h][sl]) | (bf16_bits(dg[2 * h + 1][sl]) << 16);
+            vb.x = bf16_bits(dg[0][sl]) | (bf16_bits(dg[1][sl]) << 16);
+            vb.y = bf16_bits(dg[2][sl]) | (bf16_bits(dg[3][sl]) << 16);
+            vb.z = bf16_bits(dg[4][sl]) | (bf16_bits(dg[5][sl]) << 16);
+            vb.w = bf16_bits(dg[6][sl]) | (bf16_bits(dg[7][sl]) << 16);
             *reinterpret_cast<uint4 *>(setB + ((size_t)(sl * G.n_kcN + kc) * G.n_jtN + jt) * B_BLOCK + off) = vb;
         }
     }
 }
 
 // ----------------------------------------------------------------------------------------
-// Slice-product main loop: per K chunk of 64, the S A-slices (128 rows) and S B-slices
-// (48 rows) are copied into shared memory by the TMA unit, then one thread issues, for every
-// pair (s, t) with s + t < S, four 128x48x16 MMAs into accumulator group s + t (tensor-memory
-// columns 48 (s + t) .. 48 (s + t) + 47). Returns false if a bounded wait gave up.
+// Slice-product pipeline. Shared memory: a ring of 4 A-tile buffers (128 rows x 64 bf16,
+// 16 KB, one slice of one K chunk each) and two sets of S B-tile buffers (48 rows, 6 KB).
+// Producer (warp 0, one lane): for each K chunk, the S B slices into B set kc % 2, then the
+// S A slices one by one into the ring, each copy a single bulk (TMA) transfer completing on a
+// "full" mbarrier. MMA issuer (warp 1, one lane): for each A slice s, the pairs (s, t) with
+// s + t < S, four 128x48x16 tcgen05.mma each into accumulator group s + t (tensor-memory
+// columns 48 (s + t) ...); commits release A buffers and B sets back to the producer through
+// "empty" mbarriers. The 16-column K steps with index < neg16 negate B (descriptor bit 14).
+// Every wait is bounded; on a timeout the CTA records NAO_ERR_TIMEOUT and skips its epilogue.
 // ----------------------------------------------------------------------------------------
-__device__ __forceinline__ bool slice_mainloop(uint8_t *sA, uint8_t *sB, uint64_t *bar_full, uint64_t *bar_mma,
-                                               uint32_t tm, int S, int n_kc, const uint8_t *a_blk0, size_t a_kc_stride,
-                                               size_t a_s_stride, const uint8_t *b_blk0, size_t b_kc_stride,
-                                               size_t b_s_stride) {
-    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, TN);
-    uint32_t ph = 0;
-    for (int kc = 0; kc < n_kc; kc++) {
-        tc::mbar_arrive_expect_tx(bar_full, (uint32_t)S * (16384u + B_BLOCK));
-        for (int sl = 0; sl < S; sl++) {
-            tc::bulk_g2s(sA + sl * 16384, a_blk0 + sl * a_s_stride + kc * a_kc_stride, 16384u, bar_full);
-            tc::bulk_g2s(sB + sl * B_BLOCK, b_blk0 + sl * b_s_stride + kc * b_kc_stride, B_BLOCK, bar_full);
-        }
-        if (!tc::mbar_wait(bar_full, ph, kWaitCycles)) {
-            tc::mbar_wait(bar_full, ph, kWaitCycles);  // once more for the copies still in flight
-            return false;
-        }
-        tc::fence_after_sync();
+constexpr int RING = 4;
+
+struct Pipe {
+    uint64_t fullA[RING], emptyA[RING], fullB[2], emptyB[2], done;
+    uint32_t tmem;
+    int abort;
+};
+
+struct LoopArgs {
+    const uint8_t *a0;  // A tile (slice s, chunk kc) at a0 + s a_s + kc a_kc
+    size_t a_s, a_kc;
+    const uint8_t *b0;  // B tile (slice t, chunk kc) at b0 + t b_s + kc b_kc
+    size_t b_s, b_kc;
+    int n_kc, neg16, S;
+};
+
+__host__ __device__ constexpr size_t pipe_smem_bytes(int S) { return (size_t)RING * 16384 + 2 * (size_t)S * B_BLOCK + 1024; }
+
+__device__ __forceinline__ void pipe_producer(Pipe &p, uint8_t *sA, uint8_t *sB, const LoopArgs &L) {
+    const int S = L.S;
+    for (int kc = 0; kc < L.n_kc; kc++) {
+        const int bb = kc & 1, ub = kc >> 1;
+        if (ub >= 1 && !tc::mbar_wait(&p.emptyB[bb], (ub - 1) & 1, kWaitCycles)) { p.abort = 1; return; }
+        tc::mbar_arrive_expect_tx(&p.fullB[bb], (uint32_t)S * B_BLOCK);
+        for (int t = 0; t < S; t++)
+            tc::bulk_g2s(sB + ((size_t)bb * S + t) * B_BLOCK, L.b0 + t * L.b_s + kc * L.b_kc, B_BLOCK, &p.fullB[bb]);
         for (int sa = 0; sa < S; sa++) {
-            const uint64_t ad = tc::sdesc_sw128(tc::smem_addr(sA + sa * 16384));
+            const int idx = kc * S + sa, a = idx % RING, ua = idx / RING;
+            if (ua >= 1 && !tc::mbar_wait(&p.emptyA[a], (ua - 1) & 1, kWaitCycles)) { p.abort = 1; return; }
+            tc::mbar_arrive_expect_tx(&p.fullA[a], 16384u);
+            tc::bulk_g2s(sA + (size_t)a * 16384, L.a0 + sa * L.a_s + kc * L.a_kc, 16384u, &p.fullA[a]);
+        }
+        if (*(volatile int *)&p.abort) return;
+    }
+}
+
+__device__ __forceinline__ void pipe_mma(Pipe &p, uint8_t *sA, uint8_t *sB, uint32_t tm, const LoopArgs &L) {
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, TN);
+    const int S = L.S;
+    for (int kc = 0; kc < L.n_kc; kc++) {
+        const int bb = kc & 1, ub = kc >> 1;
+        // on a timeout: flag it, and still commit "done" so the teardown waits for issued MMAs
+        if (!tc::mbar_wait(&p.fullB[bb], ub & 1, kWaitCycles)) { p.abort = 1; tc::mma_commit(&p.done); return; }
+        for (int sa = 0; sa < S; sa++) {
+            const int idx = kc * S + sa, a = idx % RING, ua = idx / RING;
+            if (!tc::mbar_wait(&p.fullA[a], ua & 1, kWaitCycles)) { p.abort = 1; tc::mma_commit(&p.done); return; }
+            tc::fence_after_sync();
+            const uint64_t ad = tc::sdesc_sw128(tc::smem_addr(sA + (size_t)a * 16384));
             for (int tb = 0; sa + tb < S; tb++) {
-                const uint64_t bd = tc::sdesc_sw128(tc::smem_addr(sB + tb * B_BLOCK));
+                const uint64_t bd = tc::sdesc_sw128(tc::smem_addr(sB + ((size_t)bb * S + tb) * B_BLOCK));
                 const uint32_t dt = tm + (uint32_t)((sa + tb) * TN);
 #pragma unroll
-                for (int ks = 0; ks < 4; ks++)
-                    tc::mma_bf16(dt, ad + 2 * ks, bd + 2 * ks, idesc, (kc | sa | ks) ? 1u : 0u);
+                for (int ks = 0; ks < 4; ks++) {
+                    const uint32_t id = (kc * 4 + ks < L.neg16) ? (idesc | (1u << 14)) : idesc;
+                    tc::mma_bf16(dt, ad + 2 * ks, bd + 2 * ks, id, (kc | sa | ks) ? 1u : 0u);
+                }
             }
+            tc::mma_commit(&p.emptyA[a]);
         }
-        tc::mma_commit(bar_mma);
-        if (!tc::mbar_wait(bar_mma, ph, kWaitCycles)) {
-            tc::mbar_wait(bar_mma, ph, kWaitCycles);  // once more for the MMAs still in flight
-            return false;
-        }
-        ph ^= 1;
+        tc::mma_commit(&p.emptyB[bb]);
     }
-    return true;
+    tc::mma_commit(&p.done);
+}
+
+// Runs the pipeline; on return (all threads) the accumulators are complete unless p.abort.
+__device__ __forceinline__ void pipe_run(Pipe &p, uint8_t *smem, uint32_t tm, const LoopArgs &L, int32_t *err) {
+    uint8_t *sA = smem, *sB = smem + (size_t)RING * 16384;
+    if (threadIdx.x == 0) pipe_producer(p, sA, sB, L);
+    else if (threadIdx.x == 32) pipe_mma(p, sA, sB, tm, L);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (!tc::mbar_wait(&p.done, 0, kWaitCycles)) p.abort = 1;
+        if (p.abort) atomicExch(err, (int)NAO_ERR_TIMEOUT);
+    }
+    __syncthreads();
+    tc::fence_after_sync();
 }
 
 // Integer recombination of the S group accumulators for 16 columns of this thread's row:
@@ -320,33 +388,34 @@ __device__ __forceinline__ double recombine(long long hi, long long lo, int eij)
     return fma((double)lo, pow2(eij - 66), (double)hi * pow2(eij - 48));
 }
 
-struct TcShared {
-    uint64_t bar_full, bar_mma;
-    uint32_t tmem;
-    int abort;
-};
-
 __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
     return reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
 }
 
-__device__ __forceinline__ uint32_t tc_setup(TcShared &sh) {
+__device__ __forceinline__ uint32_t tc_setup(Pipe &p) {
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
-        tc::mbar_init(&sh.bar_full, 1);
-        tc::mbar_init(&sh.bar_mma, 1);
+        for (int i = 0; i < RING; i++) {
+            tc::mbar_init(&p.fullA[i], 1);
+            tc::mbar_init(&p.emptyA[i], 1);
+        }
+        for (int i = 0; i < 2; i++) {
+            tc::mbar_init(&p.fullB[i], 1);
+            tc::mbar_init(&p.emptyB[i], 1);
+        }
+        tc::mbar_init(&p.done, 1);
         tc::fence_mbar_init();
-        sh.abort = 0;
+        p.abort = 0;
     }
     __syncwarp();
     if (warp == 0) {
-        tc::tmem_alloc(&sh.tmem, 512);
+        tc::tmem_alloc(&p.tmem, 512);
         tc::tmem_relinquish();
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    return sh.tmem;
+    return p.tmem;
 }
 
 __device__ __forceinline__ void tc_teardown(uint32_t tm) {
@@ -357,33 +426,30 @@ __device__ __forceinline__ void tc_teardown(uint32_t tm) {
 
 __global__ void __launch_bounds__(128, 1) h_tc_kernel(DevSystem s, const HWork *__restrict__ work, int32_t w0,
                                                      const uint8_t *__restrict__ slices, const int64_t *__restrict__ sl_off,
-                                                     const int32_t *__restrict__ expo, int S, double *__restrict__ H,
-                                                     int32_t *__restrict__ err) {
+                                                     const int32_t *__restrict__ expo, const int32_t *__restrict__ neg16,
+                                                     int S, double *__restrict__ H, int32_t *__restrict__ err) {
     extern __shared__ uint8_t smem_dyn[];
-    __shared__ TcShared sh;
-    uint8_t *sA = align1024(smem_dyn), *sB = sA + S * 16384;
+    __shared__ Pipe pp;
+    uint8_t *smem = align1024(smem_dyn);
     const HWork it = work[w0 + blockIdx.x];  // batch, 128-row tile, 48-column tile
     const int b = it.batch;
     const int P = s.batch_off[b + 1] - s.batch_off[b];
     const int N = s.rel_off[b + 1] - s.rel_off[b];
     const SplitGeom G(P, N);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t tm = tc_setup(sh);
-    if (threadIdx.x == 0) {
-        const uint8_t *setA = slices + sl_off[b];
-        const uint8_t *setB = setA + G.h_setA(S);
-        const bool ok = slice_mainloop(sA, sB, &sh.bar_full, &sh.bar_mma, tm, S, G.n_kc,
-                                       setA + (size_t)(2 * it.ti) * 8192, (size_t)G.n_rt * 8192,
-                                       (size_t)G.n_kc * G.n_rt * 8192, setB + (size_t)it.tj * B_BLOCK,
-                                       (size_t)G.n_jt * B_BLOCK, (size_t)G.n_kc * G.n_jt * B_BLOCK);
-        if (!ok) {
-            sh.abort = 1;
-            atomicExch(err, (int)NAO_ERR_TIMEOUT);
-        }
-    }
-    __syncthreads();
-    tc::fence_after_sync();
-    if (!sh.abort) {
+    const uint32_t tm = tc_setup(pp);
+    const uint8_t *base = slices + sl_off[b];
+    const size_t blk = (size_t)G.R_pad * 128;
+    LoopArgs L;
+    L.a0 = base + (size_t)it.ti * 128 * 128;
+    L.b0 = base + (size_t)it.tj * TN * 128;
+    L.a_s = L.b_s = (size_t)G.n_kc * blk;
+    L.a_kc = L.b_kc = blk;
+    L.n_kc = G.n_kc;
+    L.neg16 = neg16[b];
+    L.S = S;
+    pipe_run(pp, smem, tm, L, err);
+    if (!pp.abort) {
         const int i = it.ti * 128 + warp * 32 + lane;
         const bool row_ok = i < N;
         const int32_t *rel = s.rel_idx + s.rel_off[b];
@@ -413,8 +479,8 @@ __global__ void __launch_bounds__(128, 1) n_tc_kernel(DevSystem s, const HWork *
                                                      const double *__restrict__ scratch, int S, double *__restrict__ nout,
                                                      int32_t *__restrict__ err) {
     extern __shared__ uint8_t smem_dyn[];
-    __shared__ TcShared sh;
-    uint8_t *sA = align1024(smem_dyn), *sB = sA + S * 16384;
+    __shared__ Pipe pp;
+    uint8_t *smem = align1024(smem_dyn);
     const HWork it = work[w0 + blockIdx.x];  // batch, 128-point tile, 48-function tile
     const int b = it.batch;
     const int p0 = s.batch_off[b], P = s.batch_off[b + 1] - p0;
@@ -422,25 +488,23 @@ __global__ void __launch_bounds__(128, 1) n_tc_kernel(DevSystem s, const HWork *
     const int N = s.rel_off[b + 1] - s.rel_off[b];
     const SplitGeom G(P, N);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t tm = tc_setup(sh);
-    if (threadIdx.x == 0) {
-        const uint8_t *setA = slices + sl_off[b];
-        const uint8_t *setB = setA + G.n_setA(S);
-        // P' is zero for basis functions beyond tile J, so K stops at 48 (J + 1)
-        int n_kc = ((it.tj + 1) * TN + 63) / 64;
-        n_kc = n_kc < G.n_kcN ? n_kc : G.n_kcN;
-        const bool ok = slice_mainloop(sA, sB, &sh.bar_full, &sh.bar_mma, tm, S, n_kc,
-                                       setA + (size_t)it.ti * 16384, (size_t)G.n_qt * 16384,
-                                       (size_t)G.n_kcN * G.n_qt * 16384, setB + (size_t)it.tj * B_BLOCK,
-                                       (size_t)G.n_jtN * B_BLOCK, (size_t)G.n_kcN * G.n_jtN * B_BLOCK);
-        if (!ok) {
-            sh.abort = 1;
-            atomicExch(err, (int)NAO_ERR_TIMEOUT);
-        }
-    }
-    __syncthreads();
-    tc::fence_after_sync();
-    if (!sh.abort) {
+    const uint32_t tm = tc_setup(pp);
+    const uint8_t *setA = slices + sl_off[b];
+    const uint8_t *setB = setA + G.n_setA(S);
+    LoopArgs L;
+    L.a0 = setA + (size_t)it.ti * 16384;
+    L.a_s = (size_t)G.n_kcN * G.n_qt * 16384;
+    L.a_kc = (size_t)G.n_qt * 16384;
+    L.b0 = setB + (size_t)it.tj * B_BLOCK;
+    L.b_s = (size_t)G.n_kcN * G.n_jtN * B_BLOCK;
+    L.b_kc = (size_t)G.n_jtN * B_BLOCK;
+    // P' is zero for basis functions beyond tile J, so K stops at 48 (J + 1)
+    const int nk = ((it.tj + 1) * TN + 63) / 64;
+    L.n_kc = nk < G.n_kcN ? nk : G.n_kcN;
+    L.neg16 = 0;
+    L.S = S;
+    pipe_run(pp, smem, tm, L, err);
+    if (!pp.abort) {
         const int q = it.ti * 128 + warp * 32 + lane;
         const bool row_ok = q < P;
         const int eq = row_ok ? expo_q[p0 + q] : -10000;
@@ -488,7 +552,7 @@ __global__ void __launch_bounds__(256) wn_partial_kernel(DevSystem s, const DWor
 
 }  // namespace
 
-size_t split_smem_bytes(int S) { return (size_t)S * (16384 + B_BLOCK) + 1024; }
+size_t split_smem_bytes(int S) { return pipe_smem_bytes(S); }
 
 cudaError_t split_configure() {
     const int bytes = (int)split_smem_bytes(NAO_SPLIT_MAX_SLICES);
@@ -497,18 +561,33 @@ cudaError_t split_configure() {
     return cudaFuncSetAttribute(n_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
+#define NAO_SPLIT_DISPATCH(S, CALL)                  \
+    switch (S) {                                    \
+        case 4: CALL(4); break;                     \
+        case 5: CALL(5); break;                     \
+        case 6: CALL(6); break;                     \
+        case 7: CALL(7); break;                     \
+        case 8: CALL(8); break;                     \
+        case 9: CALL(9); break;                     \
+        default: CALL(10); break;                   \
+    }
+
 cudaError_t launch_slice_h(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_rt, const double *scratch,
-                           const double *v, uint32_t terms, uint8_t *slices, const int64_t *sl_off, int32_t *expo, int S,
-                           cudaStream_t st) {
+                           const double *v, uint32_t terms, uint8_t *slices, const int64_t *sl_off, int32_t *expo,
+                           int32_t *neg16, int S, cudaStream_t st) {
     if (b1 <= b0 || max_rt <= 0) return cudaSuccess;
-    slice_h_kernel<<<dim3(b1 - b0, max_rt), 256, 0, st>>>(s, b0, scratch, v, terms, slices, sl_off, expo, S);
+#define NAO_SLICE_H(SS) \
+    slice_h_kernel<SS><<<dim3(b1 - b0, max_rt), 256, 0, st>>>(s, b0, scratch, v, terms, slices, sl_off, expo, neg16)
+    NAO_SPLIT_DISPATCH(S, NAO_SLICE_H)
+#undef NAO_SLICE_H
     return cudaGetLastError();
 }
 
 cudaError_t launch_h_tc(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
-                        const int64_t *sl_off, const int32_t *expo, int S, double *H, int32_t *err, cudaStream_t st) {
+                        const int64_t *sl_off, const int32_t *expo, const int32_t *neg16, int S, double *H, int32_t *err,
+                        cudaStream_t st) {
     if (n_work <= 0) return cudaSuccess;
-    h_tc_kernel<<<n_work, 128, split_smem_bytes(S), st>>>(s, work, w0, slices, sl_off, expo, S, H, err);
+    h_tc_kernel<<<n_work, 128, split_smem_bytes(S), st>>>(s, work, w0, slices, sl_off, expo, neg16, S, H, err);
     return cudaGetLastError();
 }
 
@@ -516,10 +595,17 @@ cudaError_t launch_slice_n(const DevSystem &s, int32_t b0, int32_t b1, int32_t m
                            const double *P, uint8_t *slices, const int64_t *sl_off, int32_t *expo_q, int32_t *expo_b,
                            int S, cudaStream_t st) {
     if (b1 <= b0) return cudaSuccess;
-    if (max_qt > 0) slice_nphi_kernel<<<dim3(b1 - b0, max_qt), 128, 0, st>>>(s, b0, scratch, slices, sl_off, expo_q, S);
+    if (max_qt > 0) {
+#define NAO_SLICE_NPHI(SS) \
+    slice_nphi_kernel<SS><<<dim3(b1 - b0, max_qt), 128, 0, st>>>(s, b0, scratch, slices, sl_off, expo_q)
+        NAO_SPLIT_DISPATCH(S, NAO_SLICE_NPHI)
+#undef NAO_SLICE_NPHI
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    slice_np_kernel<<<b1 - b0, 256, 0, st>>>(s, b0, P, slices, sl_off, expo_b, S);
+#define NAO_SLICE_NP(SS) slice_np_kernel<SS><<<b1 - b0, 256, 0, st>>>(s, b0, P, slices, sl_off, expo_b)
+    NAO_SPLIT_DISPATCH(S, NAO_SLICE_NP)
+#undef NAO_SLICE_NP
     return cudaGetLastError();
 }
 
