@@ -218,6 +218,21 @@ nao_status build(nao_grid *g, const nao_system_desc *d) {
     }
     g->rel_total = (int64_t)g->rel_idx.size();
     g->rfn_total = (int64_t)rfn.size();
+    // atom groups: consecutive entries of one atom, sorted by l (positions are kept)
+    std::vector<AtomGroup> agrp;
+    std::vector<int32_t> agrp_off32(nbat + 1, 0);
+    for (int64_t b = 0; b < nbat; b++) {
+        int32_t i = rfn_off32[b];
+        while (i < rfn_off32[b + 1]) {
+            int32_t j = i;
+            while (j < rfn_off32[b + 1] && rfn[j].atom == rfn[i].atom) j++;
+            std::stable_sort(rfn.begin() + i, rfn.begin() + j,
+                             [](const RfnEntry &x, const RfnEntry &y) { return x.l < y.l; });
+            agrp.push_back({rfn[i].atom, i, j - i, rfn[j - 1].l});
+            i = j;
+        }
+        agrp_off32[b + 1] = (int32_t)agrp.size();
+    }
     if (g->rel_total >= (int64_t(1) << 31)) return fail(NAO_ERR_UNSUPPORTED, "reduced bases too large");
     for (int64_t b = 0; b <= nbat; b++) rel_off32[b] = (int32_t)g->rel_off[b];
 
@@ -279,6 +294,8 @@ nao_status build(nao_grid *g, const nao_system_desc *d) {
     double *d_inv_rk;
     int32_t *d_rel_off, *d_rel_idx, *d_rfn_off;
     RfnEntry *d_rfn;
+    AtomGroup *d_agrp;
+    int32_t *d_agrp_off;
     int64_t *d_scr_off;
     if ((st = upload(g, &d_coef, coef.data(), coef.size())) || (st = upload(g, &d_coef32, coef32.data(), coef32.size())) ||
         (st = upload(g, &d_inv_rk, inv_rk.data(), inv_rk.size())) ||
@@ -287,6 +304,8 @@ nao_status build(nao_grid *g, const nao_system_desc *d) {
         (st = upload(g, &d_rel_idx, g->rel_idx.data(), g->rel_idx.size())) ||
         (st = upload(g, &d_rfn_off, rfn_off32.data(), rfn_off32.size())) ||
         (st = upload(g, &d_rfn, rfn.data(), rfn.size())) || (st = upload(g, &d_scr_off, scr_off.data(), scr_off.size())) ||
+        (st = upload(g, &d_agrp, agrp.data(), agrp.size())) ||
+        (st = upload(g, &d_agrp_off, agrp_off32.data(), agrp_off32.size())) ||
         (st = upload(g, &g->d_hwork, hw.data(), hw.size())) || (st = upload(g, &g->d_dwork, dw.data(), dw.size())) ||
         (st = dev_alloc(g, &g->d_scratch, (size_t)g->scratch_elems)) ||
         (st = dev_alloc(g, &g->d_ne_part, (size_t)std::max<int64_t>(g->n_dwork, 1))) ||
@@ -310,6 +329,8 @@ nao_status build(nao_grid *g, const nao_system_desc *d) {
     s.rel_idx = d_rel_idx;
     s.rfn_off = d_rfn_off;
     s.rfn = d_rfn;
+    s.agrp = d_agrp;
+    s.agrp_off = d_agrp_off;
     s.scr_off = d_scr_off;
     s.n_rgrid = d->n_rgrid;
     s.r0 = d->r0;

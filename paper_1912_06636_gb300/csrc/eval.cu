@@ -47,108 +47,6 @@ __global__ void minr2_kernel(const double *__restrict__ atom_xyz, int n_atoms, c
     }
 }
 
-// ----------------------------------------------------------------------------------------
-// solid harmonics of degree L with gradients (T = double or float)
-// ----------------------------------------------------------------------------------------
-template <int L, typename T>
-__device__ __forceinline__ void solid_harmonics(T x, T y, T z, T q, const DevSystem &s, T (&S)[2 * L + 1],
-                                                T (&Gx)[2 * L + 1], T (&Gy)[2 * L + 1], T (&Gz)[2 * L + 1]) {
-    T A = T(1), B = T(0), Ap = T(0), Bp = T(0);
-#pragma unroll
-    for (int m = 0; m <= L; m++) {
-        T p = T(double_factorial_odd(m)), pz = T(0), pq = T(0);
-        if (L > m) {
-            T p2 = p, p2z = T(0), p2q = T(0);
-            T p1 = T(2 * m + 1) * z * p, p1z = T(2 * m + 1) * p, p1q = T(0);
-#pragma unroll
-            for (int l = m + 2; l <= L; l++) {
-                const T c1 = T((double)(2 * l - 1) / (double)(l - m));
-                const T c2 = T((double)(l + m - 1) / (double)(l - m));
-                const T pn = c1 * z * p1 - c2 * q * p2;
-                const T pnz = c1 * (p1 + z * p1z) - c2 * q * p2z;
-                const T pnq = c1 * z * p1q - c2 * (p2 + q * p2q);
-                p2 = p1; p2z = p1z; p2q = p1q;
-                p1 = pn; p1z = pnz; p1q = pnq;
-            }
-            p = p1; pz = p1z; pq = p1q;
-        }
-        const T dPx = T(2) * x * pq, dPy = T(2) * y * pq, dPz = pz + T(2) * z * pq;
-        const T kn = T(s.knorm[L][m]);
-        if (m == 0) {
-            S[L] = kn * p;
-            Gx[L] = kn * dPx;
-            Gy[L] = kn * dPy;
-            Gz[L] = kn * dPz;
-        } else {
-            const T fm = T(m);
-            S[L + m] = kn * p * A;
-            Gx[L + m] = kn * (dPx * A + p * fm * Ap);
-            Gy[L + m] = kn * (dPy * A - p * fm * Bp);
-            Gz[L + m] = kn * dPz * A;
-            S[L - m] = kn * p * B;
-            Gx[L - m] = kn * (dPx * B + p * fm * Bp);
-            Gy[L - m] = kn * (dPy * B + p * fm * Ap);
-            Gz[L - m] = kn * dPz * B;
-        }
-        Ap = A;
-        Bp = B;
-        A = x * Ap - y * Bp;
-        B = x * Bp + y * Ap;
-    }
-}
-
-// R and dR/dr in FP64: s = ln(max(r, r0)/r0)/Delta, segment k = floor(s), t = s - k.
-__device__ __forceinline__ void radial_f64(const DevSystem &s, int fn, double r, double &R, double &dR) {
-    const double rr = fmax(r, s.r0);
-    const double sc = log(rr / s.r0) * s.inv_delta;
-    int k = (int)floor(sc);
-    k = k < 0 ? 0 : (k > s.n_rgrid - 2 ? s.n_rgrid - 2 : k);
-    const double t = sc - (double)k;
-    const double2 *c = reinterpret_cast<const double2 *>(s.coef + ((size_t)fn * (s.n_rgrid - 1) + k) * 4);
-    const double2 c01 = __ldg(c), c23 = __ldg(c + 1);
-    R = fma(fma(fma(c23.y, t, c23.x), t, c01.y), t, c01.x);
-    dR = fma(fma(3.0 * c23.y, t, 2.0 * c23.x), t, c01.y) * s.inv_delta / rr;
-}
-
-// R and dR/dr in FP32. The segment comes from an FP32 logarithm; t is then refined as
-// ln(r / r_k)/Delta = log1p(r * (1/r_k) - 1)/Delta with r and 1/r_k in FP64 (one FMA), so
-// that t is accurate to ~1e-7 although r itself only has FP32's relative precision in the
-// rest of the evaluation (for steep functions ln R changes ~2 alpha r^2 times faster than r).
-__device__ __forceinline__ void radial_f32(const DevSystem &s, int fn, double r64, float &R, float &dR) {
-    const double rr64 = fmax(r64, s.r0);
-    const float rr = (float)rr64;
-    const float sa = __logf(rr * (float)(1.0 / s.r0)) * (float)s.inv_delta;
-    int k = (int)floorf(sa);
-    k = k < 0 ? 0 : (k > s.n_rgrid - 2 ? s.n_rgrid - 2 : k);
-    const double x = fma(rr64, __ldg(s.inv_rk + k), -1.0);
-    const float t = log1pf((float)x) * (float)s.inv_delta;
-    const float4 c = __ldg(reinterpret_cast<const float4 *>(s.coef_f32 + ((size_t)fn * (s.n_rgrid - 1) + k) * 4));
-    R = fmaf(fmaf(fmaf(c.w, t, c.z), t, c.y), t, c.x);
-    dR = fmaf(fmaf(3.0f * c.w, t, 2.0f * c.z), t, c.y) * (float)s.inv_delta / rr;
-}
-
-// phi and grad phi of the 2L+1 functions of one radial function at one point.
-template <int L, typename T>
-__device__ __forceinline__ void basis_values(const DevSystem &s, int fn, T dx, T dy, T dz, T r2, T r, T R, T dR,
-                                             T (&phi)[2 * L + 1], T (&gx)[2 * L + 1], T (&gy)[2 * L + 1],
-                                             T (&gz)[2 * L + 1]) {
-    T S[2 * L + 1], Gx[2 * L + 1], Gy[2 * L + 1], Gz[2 * L + 1];
-    solid_harmonics<L, T>(dx, dy, dz, r2, s, S, Gx, Gy, Gz);
-    const T u = T(1) / r;
-    T ul = T(1);
-#pragma unroll
-    for (int i = 0; i < L; i++) ul *= u;
-    const T g = R * ul;
-    const T gpu = (dR - T(L) * R * u) * ul * u;  // g'(r) / r
-#pragma unroll
-    for (int m = 0; m < 2 * L + 1; m++) {
-        phi[m] = g * S[m];
-        gx[m] = gpu * dx * S[m] + g * Gx[m];
-        gy[m] = gpu * dy * S[m] + g * Gy[m];
-        gz[m] = gpu * dz * S[m] + g * Gz[m];
-    }
-}
-
 // Output addressing of one evaluation launch.
 template <typename OutT>
 struct EvalOut {
@@ -161,38 +59,13 @@ struct EvalOut {
 // Distance below which the FP32 path evaluates in FP64 (bohr).
 constexpr double kNearNucleus = 0.1;
 
-template <int L, bool GRAD, typename T, typename OutT>
-__device__ __forceinline__ void eval_one(const DevSystem &s, const RfnEntry &e, double dx, double dy, double dz,
-                                         double r2, bool inside, const EvalOut<OutT> &o, int q) {
-    OutT phi[2 * L + 1], gx[2 * L + 1], gy[2 * L + 1], gz[2 * L + 1];
-#pragma unroll
-    for (int m = 0; m < 2 * L + 1; m++) phi[m] = gx[m] = gy[m] = gz[m] = OutT(0);
-    if (inside) {
-        const double r = __dsqrt_rn(r2);
-        if (std::is_same<T, double>::value || r < kNearNucleus) {
-            double R, dR, f[2 * L + 1], a[2 * L + 1], b[2 * L + 1], c[2 * L + 1];
-            radial_f64(s, e.fn, r, R, dR);
-            basis_values<L, double>(s, e.fn, dx, dy, dz, r2, r, R, dR, f, a, b, c);
-#pragma unroll
-            for (int m = 0; m < 2 * L + 1; m++) {
-                phi[m] = OutT(f[m]); gx[m] = OutT(a[m]); gy[m] = OutT(b[m]); gz[m] = OutT(c[m]);
-            }
-        } else {
-            float R, dR, f[2 * L + 1], a[2 * L + 1], b[2 * L + 1], c[2 * L + 1];
-            radial_f32(s, e.fn, r, R, dR);
-            const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
-            basis_values<L, float>(s, e.fn, fx, fy, fz, (float)r2, (float)r, R, dR, f, a, b, c);
-#pragma unroll
-            for (int m = 0; m < 2 * L + 1; m++) {
-                phi[m] = OutT(f[m]); gx[m] = OutT(a[m]); gy[m] = OutT(b[m]); gz[m] = OutT(c[m]);
-            }
-        }
-    }
-#pragma unroll
-    for (int m = 0; m < 2 * L + 1; m++) {
-        const int64_t j = e.pos + m;
+template <typename OutT>
+__device__ __forceinline__ void store_rows(const EvalOut<OutT> &o, int pos, int nm, int q, const OutT *phi,
+                                           const OutT *gx, const OutT *gy, const OutT *gz, bool grad) {
+    for (int m = 0; m < nm; m++) {
+        const int64_t j = pos + m;
         o.phi[j * o.phi_rs + q] = phi[m];
-        if (GRAD) {
+        if (grad) {
             o.grad[j * o.grad_rs + q] = gx[m];
             o.grad[o.grad_cs + j * o.grad_rs + q] = gy[m];
             o.grad[2 * o.grad_cs + j * o.grad_rs + q] = gz[m];
@@ -200,33 +73,168 @@ __device__ __forceinline__ void eval_one(const DevSystem &s, const RfnEntry &e, 
     }
 }
 
+// All relevant radial functions of one atom at one point, in arithmetic T. Distance, square
+// root, logarithm, reciprocals and the solid-harmonic recurrence are shared by the atom's
+// radial functions, which are visited in increasing l.
+template <int LMAX, typename T, bool GRAD, typename OutT>
+__device__ __noinline__ void eval_group(const DevSystem &s, const AtomGroup &ag, double dx, double dy, double dz,
+                                           double r2, double r, const EvalOut<OutT> &o, int q) {
+    // radial coordinate: segment k and t in [0, 1)
+    const double rr = fmax(r, s.r0);
+    int k;
+    T t;
+    if constexpr (std::is_same<T, double>::value) {
+        const double sc = log(rr / s.r0) * s.inv_delta;
+        k = (int)floor(sc);
+        k = k < 0 ? 0 : (k > s.n_rgrid - 2 ? s.n_rgrid - 2 : k);
+        t = sc - (double)k;
+    } else {
+        // FP32 segment, refined as ln(r / r_k)/Delta = log1p(r * (1/r_k) - 1)/Delta with one FP64
+        // FMA: t keeps ~1e-7 although a plain FP32 ln(r/r0) carries ~1e-6.
+        const float sa = __logf((float)rr * (float)(1.0 / s.r0)) * (float)s.inv_delta;
+        k = (int)floorf(sa);
+        k = k < 0 ? 0 : (k > s.n_rgrid - 2 ? s.n_rgrid - 2 : k);
+        const double xk = fma(rr, __ldg(s.inv_rk + k), -1.0);
+        t = log1pf((float)xk) * (float)s.inv_delta;
+    }
+    const T dr_scale = T(s.inv_delta / rr);  // dR/dr = dR/ds * inv_delta / rr
+    const T u = T(1.0 / r);
+    const T x = T(dx), y = T(dy), z = T(dz), qq = T(r2);
+    // A_m + i B_m = (x + i y)^m
+    T A[LMAX + 1], B[LMAX + 1];
+    A[0] = T(1);
+    B[0] = T(0);
+#pragma unroll
+    for (int m = 1; m <= LMAX; m++) {
+        A[m] = x * A[m - 1] - y * B[m - 1];
+        B[m] = x * B[m - 1] + y * A[m - 1];
+    }
+    // Pi_{l-1}^m (c) and Pi_{l-2}^m (p) with their z and r^2 derivatives
+    T Pc[LMAX + 1], Pcz[LMAX + 1], Pcq[LMAX + 1], Pp[LMAX + 1], Ppz[LMAX + 1], Ppq[LMAX + 1];
+#pragma unroll
+    for (int m = 0; m <= LMAX; m++) Pc[m] = Pcz[m] = Pcq[m] = Pp[m] = Ppz[m] = Ppq[m] = T(0);
+    int ri = ag.r0;
+    const int re = ag.r0 + ag.nr;
+    T ul = T(1);  // u^l
+#pragma unroll
+    for (int l = 0; l <= LMAX; l++) {
+        T S[2 * LMAX + 1], Gx[2 * LMAX + 1], Gy[2 * LMAX + 1], Gz[2 * LMAX + 1];
+#pragma unroll
+        for (int m = 0; m <= l; m++) {
+            T p, pz, pq;
+            if (m == l) {
+                p = T(double_factorial_odd(m));
+                pz = pq = T(0);
+            } else if (m == l - 1) {
+                p = T(2 * m + 1) * z * Pc[m];
+                pz = T(2 * m + 1) * Pc[m];
+                pq = T(0);
+            } else {
+                const T c1 = T((double)(2 * l - 1) / (double)(l - m));
+                const T c2 = T((double)(l + m - 1) / (double)(l - m));
+                p = c1 * z * Pc[m] - c2 * qq * Pp[m];
+                pz = c1 * (Pc[m] + z * Pcz[m]) - c2 * qq * Ppz[m];
+                pq = c1 * z * Pcq[m] - c2 * (Pp[m] + qq * Ppq[m]);
+            }
+            Pp[m] = Pc[m]; Ppz[m] = Pcz[m]; Ppq[m] = Pcq[m];
+            Pc[m] = p; Pcz[m] = pz; Pcq[m] = pq;
+            const T dPx = T(2) * x * pq, dPy = T(2) * y * pq, dPz = pz + T(2) * z * pq;
+            const T kn = T(s.knorm[l][m]);
+            if (m == 0) {
+                S[l] = kn * p;
+                Gx[l] = kn * dPx;
+                Gy[l] = kn * dPy;
+                Gz[l] = kn * dPz;
+            } else {
+                const T fm = T(m);
+                S[l + m] = kn * p * A[m];
+                Gx[l + m] = kn * (dPx * A[m] + p * fm * A[m - 1]);
+                Gy[l + m] = kn * (dPy * A[m] - p * fm * B[m - 1]);
+                Gz[l + m] = kn * dPz * A[m];
+                S[l - m] = kn * p * B[m];
+                Gx[l - m] = kn * (dPx * B[m] + p * fm * B[m - 1]);
+                Gy[l - m] = kn * (dPy * B[m] + p * fm * A[m - 1]);
+                Gz[l - m] = kn * dPz * B[m];
+            }
+        }
+        // the atom's radial functions of this l
+        for (; ri < re; ri++) {
+            const RfnEntry e = s.rfn[ri];
+            if (e.l != l) break;
+            OutT fo[2 * LMAX + 1], xo[2 * LMAX + 1], yo[2 * LMAX + 1], zo[2 * LMAX + 1];
+            if (r < s.fn_rc[e.fn]) {
+                T R, dRds;
+                if constexpr (std::is_same<T, double>::value) {
+                    const double2 *c = reinterpret_cast<const double2 *>(s.coef + ((size_t)e.fn * (s.n_rgrid - 1) + k) * 4);
+                    const double2 c01 = __ldg(c), c23 = __ldg(c + 1);
+                    R = fma(fma(fma(c23.y, t, c23.x), t, c01.y), t, c01.x);
+                    dRds = fma(fma(3.0 * c23.y, t, 2.0 * c23.x), t, c01.y);
+                } else {
+                    const float4 c = __ldg(reinterpret_cast<const float4 *>(s.coef_f32 + ((size_t)e.fn * (s.n_rgrid - 1) + k) * 4));
+                    R = fmaf(fmaf(fmaf(c.w, t, c.z), t, c.y), t, c.x);
+                    dRds = fmaf(fmaf(3.0f * c.w, t, 2.0f * c.z), t, c.y);
+                }
+                const T g = R * ul;
+                const T gpu = (dRds * dr_scale - T(l) * R * u) * ul * u;  // g'(r) / r
+#pragma unroll
+                for (int m = 0; m < 2 * l + 1; m++) {
+                    fo[m] = OutT(g * S[m]);
+                    xo[m] = OutT(gpu * x * S[m] + g * Gx[m]);
+                    yo[m] = OutT(gpu * y * S[m] + g * Gy[m]);
+                    zo[m] = OutT(gpu * z * S[m] + g * Gz[m]);
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < 2 * l + 1; m++) fo[m] = xo[m] = yo[m] = zo[m] = OutT(0);
+            }
+            store_rows(o, e.pos, 2 * l + 1, q, fo, xo, yo, zo, GRAD);
+        }
+        ul *= u;
+    }
+}
+
+template <int LMAX, bool GRAD, typename T, typename OutT>
+__device__ __forceinline__ void eval_group_dispatch(const DevSystem &s, const AtomGroup &ag, double dx, double dy,
+                                                    double dz, double r2, double r, const EvalOut<OutT> &o, int q) {
+    if (std::is_same<T, double>::value || r < kNearNucleus)
+        eval_group<LMAX, double, GRAD, OutT>(s, ag, dx, dy, dz, r2, r, o, q);
+    else
+        eval_group<LMAX, float, GRAD, OutT>(s, ag, dx, dy, dz, r2, r, o, q);
+}
+
 template <bool GRAD, typename T, typename OutT>
 __device__ __forceinline__ void eval_batch(const DevSystem &s, int b, const EvalOut<OutT> &o) {
     const int p0 = s.batch_off[b], P = s.batch_off[b + 1] - p0;
-    const int r0 = s.rfn_off[b], nr = s.rfn_off[b + 1] - r0;
+    const int g0 = s.agrp_off[b], ng = s.agrp_off[b + 1] - g0;
     const int qmax = o.qmax;
-    const int total = nr * qmax;
+    const int total = ng * qmax;
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        const int rl = idx / qmax, q = idx - rl * qmax;
-        const RfnEntry e = s.rfn[r0 + rl];
-        double dx = 0.0, dy = 0.0, dz = 0.0, r2 = 0.0;
-        bool inside = false;
-        if (q < P) {
-            const int p = p0 + q;
-            dx = __dsub_rn(s.px[p], s.atom_xyz[3 * e.atom]);
-            dy = __dsub_rn(s.py[p], s.atom_xyz[3 * e.atom + 1]);
-            dz = __dsub_rn(s.pz[p], s.atom_xyz[3 * e.atom + 2]);
-            r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-            inside = __dsqrt_rn(r2) < s.fn_rc[e.fn];
+        const int gl = idx / qmax, q = idx - gl * qmax;
+        const AtomGroup ag = s.agrp[g0 + gl];
+        if (q >= P) {  // padding points: zero rows
+            OutT z0[2 * NAO_LMAX + 1];
+#pragma unroll
+            for (int m = 0; m < 2 * NAO_LMAX + 1; m++) z0[m] = OutT(0);
+            for (int ri = ag.r0; ri < ag.r0 + ag.nr; ri++) {
+                const RfnEntry e = s.rfn[ri];
+                store_rows(o, e.pos, 2 * e.l + 1, q, z0, z0, z0, z0, GRAD);
+            }
+            continue;
         }
-        switch (e.l) {
-            case 0: eval_one<0, GRAD, T>(s, e, dx, dy, dz, r2, inside, o, q); break;
-            case 1: eval_one<1, GRAD, T>(s, e, dx, dy, dz, r2, inside, o, q); break;
-            case 2: eval_one<2, GRAD, T>(s, e, dx, dy, dz, r2, inside, o, q); break;
-            case 3: eval_one<3, GRAD, T>(s, e, dx, dy, dz, r2, inside, o, q); break;
-            case 4: eval_one<4, GRAD, T>(s, e, dx, dy, dz, r2, inside, o, q); break;
-            case 5: eval_one<5, GRAD, T>(s, e, dx, dy, dz, r2, inside, o, q); break;
-            default: eval_one<6, GRAD, T>(s, e, dx, dy, dz, r2, inside, o, q); break;
+        const int p = p0 + q;
+        const double dx = __dsub_rn(s.px[p], s.atom_xyz[3 * ag.atom]);
+        const double dy = __dsub_rn(s.py[p], s.atom_xyz[3 * ag.atom + 1]);
+        const double dz = __dsub_rn(s.pz[p], s.atom_xyz[3 * ag.atom + 2]);
+        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+        const double r = __dsqrt_rn(r2);
+        switch (ag.lmax) {
+            case 0: eval_group_dispatch<0, GRAD, T>(s, ag, dx, dy, dz, r2, r, o, q); break;
+            case 1: eval_group_dispatch<1, GRAD, T>(s, ag, dx, dy, dz, r2, r, o, q); break;
+            case 2: eval_group_dispatch<2, GRAD, T>(s, ag, dx, dy, dz, r2, r, o, q); break;
+            case 3: eval_group_dispatch<3, GRAD, T>(s, ag, dx, dy, dz, r2, r, o, q); break;
+            case 4: eval_group_dispatch<4, GRAD, T>(s, ag, dx, dy, dz, r2, r, o, q); break;
+            case 5: eval_group_dispatch<5, GRAD, T>(s, ag, dx, dy, dz, r2, r, o, q); break;
+            default: eval_group_dispatch<6, GRAD, T>(s, ag, dx, dy, dz, r2, r, o, q); break;
         }
     }
 }

@@ -24,6 +24,12 @@ struct RfnEntry {
     int32_t atom, fn, pos, l;
 };
 
+// The relevant radial functions of one atom for one batch: rfn entries [r0, r0 + nr), sorted
+// by l; lmax is the largest l among them.
+struct AtomGroup {
+    int32_t atom, r0, nr, lmax;
+};
+
 // Geometry and tables shared by every kernel (device pointers).
 struct DevSystem {
     const double *atom_xyz;   // [n_atoms*3]
@@ -38,6 +44,8 @@ struct DevSystem {
     const int32_t *rel_idx;   // [rel_total]
     const int32_t *rfn_off;   // [n_batches+1]
     const RfnEntry *rfn;      // [rfn_total]
+    const int32_t *agrp_off;  // [n_batches+1] atom groups of each batch
+    const AtomGroup *agrp;    // [agrp_total]
     const int64_t *scr_off;   // [n_batches] element offset of the batch's block in scratch
     int32_t n_rgrid;
     double r0, inv_delta;
