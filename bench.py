@@ -36,15 +36,17 @@ WORKLOAD = ("diamond64: 64-atom diamond-lattice cluster (cubic cell 10.26 bohr),
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default=None, choices=[None, "fp64", "fp32", "split"])
     ap.add_argument("--config", type=int, default=1)
-    ap.add_argument("--cpu-sample", type=int, default=12000, help="oracle sample size (points)")
+    ap.add_argument("--slices", type=int, default=10,
+                    help="split path: slices per operand (10 meets e <= 1e-10 on this workload; the library default is 12)")
+    ap.add_argument("--cpu-sample", type=int, default=200000, help="oracle sample size (points)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--compare", action="store_true", help="also time the other precisions (extra keys)")
+    ap.add_argument("--no-compare", action="store_true", help="skip timing the other precisions")
     return ap.parse_args()
 
 
@@ -112,19 +114,25 @@ def measured_peaks():
         return {}
 
 
-# FP64 FMA throughput of one GB300 (measured on this machine's GPUs by a DFMA loop).
-FP64_PEAK_TFLOPS_MEASURED = None  # filled from profiles/fp64_peak.txt when present
 
 
-def fp64_peak():
+def alu_peak(kind: str):
+    """FP64 or FP32 FMA throughput measured on this machine (profiles/peaks_fp64_fp32_dmma.txt)."""
+    key = {"fp64": "fp64_fma_tflops", "fp32": "fp32_fma_tflops"}[kind]
     path = os.path.join(ROOT, "profiles", "peaks_fp64_fp32_dmma.txt")
     try:
         for line in open(path):
-            if line.startswith("fp64_fma_tflops"):
-                return float(line.split()[1]), "measured (profiles/fp64_peak.txt)"
+            if line.startswith(key):
+                return float(line.split()[1]), "measured FMA loop (profiles/peaks_fp64_fp32_dmma.txt)"
     except Exception:
         pass
-    return 1.25, "nominal GB300 FP64"
+    return ({"fp64": 1.25, "fp32": 80.0}[kind], "nominal")
+
+
+def g_split_pairs(g) -> int:
+    """Slice products per contraction on the split path: S (S + 1) / 2 for S slices."""
+    S = int(g.split_slices)
+    return S * (S + 1) // 2
 
 
 # ---------------------------------------------------------------------------------------
@@ -197,11 +205,11 @@ def main():
     __graft_entry__.build()
     from paper_1912_06636_gb300 import nao
 
-    prec = args.prec or "fp64"
+    prec = args.prec or "split"
     s, v_np, P_np = make_workload(args.config, f"cuda:{local_rank}")
     dev = torch.device("cuda", local_rank)
     t0 = time.perf_counter()
-    g = nao.Grid(s, device=local_rank, max_batch_points=s.max_batch_points)
+    g = nao.Grid(s, device=local_rank, max_batch_points=s.max_batch_points, split_slices=args.slices)
     torch.cuda.synchronize()
     create_s = time.perf_counter() - t0
     info = g.info
@@ -252,25 +260,26 @@ def main():
     Ppad = (Pb + 15) // 16 * 16
     scratch_gb = float(np.sum(Nb * Ppad * 8 * 5)) / 1e9
 
-    # roofline of the dominant kernel (per launch: algorithmic FLOPs / event-timed duration)
+    # roofline of the dominant kernel family (per launch: algorithmic work / event-timed duration)
     fam = max(prof, key=lambda k: prof[k][1])
     launches, fam_ms = prof[fam]
-    flops_per_step = {"h_fp64": info.flops_h, "h_fp32": info.flops_h, "h_split": info.flops_h,
-                      "n_fp64": info.flops_n, "n_fp32": info.flops_n, "n_split": info.flops_n}.get(fam)
+    pairs = {"split": g_split_pairs(g)}.get(prec, 1)
+    work = {"h_fp64": info.flops_h, "h_fp32": info.flops_h, "h_split": pairs * info.flops_h,
+            "n_fp64": info.flops_n, "n_fp32": info.flops_n, "n_split": pairs * info.flops_n}
     roofline = None
-    if flops_per_step and fam_ms > 0:
-        achieved = flops_per_step * args.steps / (fam_ms / 1e3) / 1e12
-        if fam.endswith("fp64"):
-            peak, peak_src = fp64_peak()
-            roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                        "frac": achieved / peak, "traffic": None, "kernel": fam, "peak_source": peak_src,
-                        "launches": launches, "avg_launch_ms": fam_ms / max(launches, 1)}
+    if fam in work and fam_ms > 0:
+        achieved = work[fam] * args.steps / (fam_ms / 1e3) / 1e12
+        if fam.endswith("fp64") or fam.endswith("fp32"):
+            peak, peak_src = alu_peak(fam[-4:])
+            roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                        "traffic": None, "kernel": fam, "peak_source": peak_src}
         else:
-            pk = measured_peaks().get("bf16_tflops_sustained", 1700.0)
-            roofline = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
-                        "frac": achieved / pk, "traffic": None, "kernel": fam,
-                        "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",
-                        "launches": launches, "avg_launch_ms": fam_ms / max(launches, 1)}
+            pk = measured_peaks().get("bf16_tflops_sustained", 1719.5)
+            roofline = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
+                        "traffic": None, "kernel": fam,
+                        "work": f"{pairs} slice products x algorithmic FLOPs (sum_b 4 P_b N_b (N_b+1) for H)",
+                        "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}
+        roofline.update({"launches": launches, "avg_launch_ms": fam_ms / max(launches, 1)})
     gpu_launches = int(sum(l for l, _ in prof.values()))
 
     line = {
@@ -279,6 +288,7 @@ def main():
         "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "split": "bf16x-slices+f64"}[prec],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": prec, "parallelism": f"replicas{world}",
+                   "split_slices": args.slices if prec == "split" else None,
                    "l2": f"inputs/working set larger than L2: {scratch_gb:.1f} GB of evaluated basis functions "
                          "written and re-read per step",
                    "n_points": g.n_points, "n_basis": g.nb, "n_batches": int(info.n_batches),
@@ -306,7 +316,7 @@ def main():
                        "h2d_bytes_per_step": int(8 * (g.n_points + g.nb * g.nb)),
                        "d2h_bytes_per_step": int(8 * (g.nb * g.nb + g.n_points + 1))}
 
-    if args.compare:
+    if not args.no_compare:
         other = {}
         for p in ("fp64", "fp32", "split"):
             if p == prec:
@@ -320,8 +330,31 @@ def main():
                 b.record(stream)
                 torch.cuda.synchronize()
                 other[p] = {"points_per_s": g.n_points / (a.elapsed_time(b) / 1e3), "ms_per_step": a.elapsed_time(b)}
+                if p == "fp64":
+                    line["fp64_points_per_s"] = other[p]["points_per_s"]
+                    line["speedup_vs_fp64"] = value / other[p]["points_per_s"]
             except nao.NaoError as e:
                 other[p] = {"unavailable": str(e)}
+        # the split path at the library's default slice count
+        d = nao.nao_default_options().split_slices
+        if d != args.slices:
+            try:
+                g2 = nao.Grid(s, device=local_rank, max_batch_points=s.max_batch_points)
+                g2.integrate_h(v, prec="split", H=H, stream=stream)
+                g2.update_density(P, prec="split", n=n, ne=ne, stream=stream)
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                g2.integrate_h(v, prec="split", H=H, stream=stream)
+                g2.update_density(P, prec="split", n=n, ne=ne, stream=stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                g2.sync()
+                other[f"split_{d}_slices"] = {"points_per_s": g.n_points / (a.elapsed_time(b) / 1e3),
+                                              "ms_per_step": a.elapsed_time(b)}
+                g2.close()
+            except nao.NaoError as e:
+                other[f"split_{d}_slices"] = {"unavailable": str(e)}
         line["other_precisions"] = other
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

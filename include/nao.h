@@ -90,11 +90,22 @@ typedef struct {
 
 typedef struct {
     int32_t max_batch_points; /* target batch size B (Sec. 3.3.1; the paper uses 200 on GPUs); default 200 */
-    int32_t split_slices;     /* slices per operand on the NAO_SPLIT path, 4..10; default 10 */
+    int32_t split_slices;     /* slices per operand on the NAO_SPLIT path, 4..12; default 12. Each
+                                 slice adds 6 bits: the error of an element falls about 64x per
+                                 slice (measured e_H on an 8-atom cell with 20 radial shells:
+                                 1.6e-9 at 10, 4.6e-11 at 11, 8.6e-13 at 12 slices). 4..10 slices
+                                 run 128x48 tensor-core tiles, 11..12 slices 128x32 tiles. */
     int32_t deterministic;    /* reserved; results are already run-to-run reproducible up to
                                  the order of FP64 atomic additions into H */
     int32_t device;           /* CUDA device ordinal; -1 = the calling thread's current device */
     int64_t scratch_bytes;    /* device scratch for evaluated basis functions; 0 = library default */
+    int32_t capture_graph;    /* 1: the first call of each (operation, precision, terms) records
+                                 its kernel launches as a CUDA graph on a stream the handle
+                                 owns; later calls upload that call's pointer tables and replay
+                                 the graph, ordered after the caller's stream's earlier work and
+                                 before its later work (events). Not used while profiling.
+                                 Default 0 (plain launches on the caller's stream). */
+    int32_t reserved0;        /* must be 0 */
 } nao_options;
 
 typedef struct {
@@ -107,6 +118,8 @@ typedef struct {
     int64_t device_bytes;     /* device memory held by the handle */
     int64_t flops_h;          /* algorithmic FLOPs of one nao_integrate_h: sum_b 4 P_b N_b (N_b+1) */
     int64_t flops_n;          /* algorithmic FLOPs of one nao_update_density: sum_b 2 P_b N_b^2 + 2 P_b N_b */
+    int32_t n_systems;        /* systems of the handle (1 for nao_grid_create) */
+    int32_t reserved0;
 } nao_grid_info;
 
 /* Fill *opts with the defaults above. */
@@ -125,6 +138,25 @@ nao_status nao_default_options(nao_options *opts);
  * handle; on failure *out is set to NULL and nothing is leaked.
  * Errors: NAO_ERR_INVALID_ARG (see nao_system_desc), NAO_ERR_OUT_OF_MEMORY, NAO_ERR_CUDA. */
 nao_status nao_grid_create(const nao_system_desc *desc, const nao_options *opts, nao_grid **out);
+
+/* One handle over several independent systems (molecules) that share the logarithmic
+ * radial grid (n_rgrid, r0, r_last): each system is partitioned into its own batches
+ * (no batch mixes systems), and one launch of each kernel covers the batches of all of
+ * them, so many small molecules fill the GPU together (the batch loop of Sec. 3.3 runs
+ * over the union of their batches). Global numbering: basis functions, points and atoms
+ * of system m follow those of systems 0..m-1; nao_get_info, nao_export_batches and
+ * nao_evaluate_batch use it. descs: host array [n_systems], each as for nao_grid_create;
+ * n_systems >= 1. The single-system calls (nao_integrate_h, nao_update_density and their
+ * host and noalloc forms) require n_systems == 1; use the _many forms otherwise.
+ * Errors: as nao_grid_create; NAO_ERR_INVALID_ARG if the radial grids differ.              */
+nao_status nao_grid_create_many(const nao_system_desc *descs, int32_t n_systems, const nao_options *opts,
+                                nao_grid **out);
+
+/* Basis and point ranges of system m in the global numbering: basis functions
+ * basis_offset .. basis_offset+n_basis-1, points point_offset .. point_offset+n_points-1,
+ * batches batch_begin .. batch_end-1. Any output pointer may be NULL.                      */
+nao_status nao_get_system(const nao_grid *g, int32_t m, int64_t *basis_offset, int64_t *n_basis,
+                          int64_t *point_offset, int64_t *n_points, int64_t *batch_begin, int64_t *batch_end);
 
 /* Release the handle and all its device memory. NULL-safe. Synchronises the device work
  * the handle has enqueued before freeing.                                                */
@@ -158,6 +190,21 @@ nao_status nao_integrate_h(nao_grid *g, const double *v_dev, uint32_t terms, nao
  * read). n_dev: device [n_points]. n_electrons_dev: device [1] or NULL.                    */
 nao_status nao_update_density(nao_grid *g, const double *P_dev, nao_precision prec, double *n_dev,
                               double *n_electrons_dev, void *cuda_stream);
+
+/* Grouped forms: the same operations for every system of the handle in one pass of the
+ * kernels (one launch per kernel for all systems). Arrays are HOST arrays of n_systems
+ * DEVICE pointers, read during the call; entry m refers to system m in its own numbering
+ * (H_dev[m] is n_basis(m) x n_basis(m), v_dev[m] and n_dev[m] have n_points(m) entries in
+ * system m's original point order).
+ *   nao_integrate_h_many: v_dev may be NULL (v = 1 for every system), or an array whose
+ *     NULL entries mean v = 1 for that system; every H_dev[m] is required.
+ *   nao_update_density_many: every P_dev[m] and n_dev[m] is required; n_electrons_dev may
+ *     be NULL, or an array whose non-NULL entries receive sum_p w_p n_p of that system.
+ * Errors: as the single-system forms.                                                      */
+nao_status nao_integrate_h_many(nao_grid *g, const double *const *v_dev, uint32_t terms, nao_precision prec,
+                                double *const *H_dev, void *cuda_stream);
+nao_status nao_update_density_many(nao_grid *g, const double *const *P_dev, nao_precision prec,
+                                   double *const *n_dev, double *const *n_electrons_dev, void *cuda_stream);
 
 /* The same two operations with HOST buffers: the library copies the inputs to the device,
  * runs the operation on the given stream, copies the results back and synchronises the

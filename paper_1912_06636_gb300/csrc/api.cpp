@@ -71,6 +71,10 @@ void free_grid(nao_grid *g) {
         cudaEventDestroy(t.b);
     }
     for (cudaEvent_t e : g->event_pool) cudaEventDestroy(e);
+    for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
+    if (g->ev_in) cudaEventDestroy(g->ev_in);
+    if (g->ev_out) cudaEventDestroy(g->ev_out);
+    if (g->gstream) cudaStreamDestroy(g->gstream);
     for (void *p : g->allocs) cudaFree(p);
     delete g;
 }
@@ -94,7 +98,8 @@ nao_status validate(const nao_system_desc *d, const nao_options &o) {
         return fail(NAO_ERR_INVALID_ARG, "bad points");
     if (o.max_batch_points < 1 || o.max_batch_points > NAO_MAX_BATCH)
         return fail(NAO_ERR_INVALID_ARG, "max_batch_points must be in 1.." + std::to_string(NAO_MAX_BATCH));
-    if (o.split_slices < 4 || o.split_slices > 10) return fail(NAO_ERR_INVALID_ARG, "split_slices must be in 4..10");
+    if (o.split_slices < 4 || o.split_slices > NAO_SPLIT_MAX_SLICES)
+        return fail(NAO_ERR_INVALID_ARG, "split_slices must be in 4.." + std::to_string(NAO_SPLIT_MAX_SLICES));
     if (d->species_fn_offset[0] != 0) return fail(NAO_ERR_INVALID_ARG, "species_fn_offset[0] != 0");
     for (int s = 0; s < d->n_species; s++)
         if (d->species_fn_offset[s + 1] < d->species_fn_offset[s])
@@ -121,31 +126,81 @@ nao_status validate(const nao_system_desc *d, const nao_options &o) {
     return NAO_OK;
 }
 
-nao_status build(nao_grid *g, const nao_system_desc *d) {
-    const int64_t n = d->n_points;
-    g->n_atoms = d->n_atoms;
-    g->n_species = d->n_species;
-    g->n_fn = d->species_fn_offset[d->n_species];
-    g->n_rgrid = d->n_rgrid;
-    g->r0 = d->r0;
-    g->r_last = d->r_last;
-    g->delta = std::log(d->r_last / d->r0) / (double)(d->n_rgrid - 1);
+// One or more systems concatenated: atoms, radial functions and points get global indices;
+// each system is partitioned on its own, so no batch mixes systems.
+nao_status build(nao_grid *g, const nao_system_desc *descs, int32_t n_sys, const int32_t *batch_points) {
+    const nao_system_desc *d0 = &descs[0];
+    g->n_sys = n_sys;
+    g->n_rgrid = d0->n_rgrid;
+    g->r0 = d0->r0;
+    g->r_last = d0->r_last;
+    g->delta = std::log(d0->r_last / d0->r0) / (double)(d0->n_rgrid - 1);
+
+    // global atoms, radial functions and points
+    std::vector<double> atoms, fn_cut, fn_tab;
+    std::vector<int32_t> atom_fn0, atom_fn1, fn_l;
+    std::vector<int64_t> atom_basis(1, 0);
+    std::vector<double> pts, wts;
+    g->sys_boff.assign(n_sys, 0);
+    g->sys_nb.assign(n_sys, 0);
+    g->sys_poff.assign(n_sys, 0);
+    g->sys_np.assign(n_sys, 0);
+    g->sys_aoff.assign(n_sys + 1, 0);
+    int32_t fn_base = 0;
+    for (int m = 0; m < n_sys; m++) {
+        const nao_system_desc *d = &descs[m];
+        if (d->n_rgrid != d0->n_rgrid || d->r0 != d0->r0 || d->r_last != d0->r_last)
+            return fail(NAO_ERR_INVALID_ARG, "systems of one handle must share n_rgrid, r0 and r_last");
+        const int nfn = d->species_fn_offset[d->n_species];
+        for (int f = 0; f < nfn; f++) {
+            fn_l.push_back(d->fn_l[f]);
+            fn_cut.push_back(d->fn_cutoff[f]);
+        }
+        fn_tab.insert(fn_tab.end(), d->fn_table, d->fn_table + (size_t)nfn * d->n_rgrid);
+        g->sys_boff[m] = (int32_t)atom_basis.back();
+        g->sys_aoff[m] = (int32_t)(atoms.size() / 3);
+        for (int a = 0; a < d->n_atoms; a++) {
+            const int sp = d->atom_species[a];
+            int64_t c = 0;
+            for (int f = d->species_fn_offset[sp]; f < d->species_fn_offset[sp + 1]; f++) c += 2 * d->fn_l[f] + 1;
+            atoms.insert(atoms.end(), d->atom_xyz + 3 * a, d->atom_xyz + 3 * a + 3);
+            atom_fn0.push_back(fn_base + d->species_fn_offset[sp]);
+            atom_fn1.push_back(fn_base + d->species_fn_offset[sp + 1]);
+            atom_basis.push_back(atom_basis.back() + c);
+        }
+        g->sys_aoff[m + 1] = (int32_t)(atoms.size() / 3);
+        g->sys_nb[m] = (int32_t)(atom_basis.back() - g->sys_boff[m]);
+        if (g->sys_nb[m] < 1) return fail(NAO_ERR_INVALID_ARG, "a system has no basis functions");
+        g->sys_poff[m] = (int32_t)(pts.size() / 3);
+        g->sys_np[m] = (int32_t)d->n_points;
+        pts.insert(pts.end(), d->pt_xyz, d->pt_xyz + 3 * d->n_points);
+        wts.insert(wts.end(), d->pt_w, d->pt_w + d->n_points);
+        fn_base += nfn;
+        if ((int64_t)pts.size() / 3 >= (int64_t(1) << 31)) return fail(NAO_ERR_INVALID_ARG, "too many points");
+    }
+    g->n_atoms = (int32_t)(atoms.size() / 3);
+    g->n_fn = fn_base;
+    g->nb = atom_basis.back();
+    if (g->nb >= (int64_t(1) << 31)) return fail(NAO_ERR_INVALID_ARG, "too many basis functions");
+    const int64_t n = (int64_t)wts.size();
     g->n_points = n;
 
-    // basis functions per atom (atom, species radial function, m)
-    std::vector<int64_t> atom_basis(d->n_atoms + 1, 0);
-    for (int a = 0; a < d->n_atoms; a++) {
-        const int sp = d->atom_species[a];
-        int64_t c = 0;
-        for (int f = d->species_fn_offset[sp]; f < d->species_fn_offset[sp + 1]; f++) c += 2 * d->fn_l[f] + 1;
-        atom_basis[a + 1] = atom_basis[a] + c;
+    // Sec. 3.3.1: batches, system by system
+    std::vector<int32_t> bmol;
+    g->batch_off.assign(1, 0);
+    g->perm.clear();
+    for (int m = 0; m < n_sys; m++) {
+        std::vector<int64_t> off, perm;
+        const int B = batch_points ? batch_points[m] : g->opt.max_batch_points;
+        if (B < 1 || B > NAO_MAX_BATCH) return fail(NAO_ERR_INVALID_ARG, "batch size outside 1..1024");
+        nao_partition(descs[m].n_points, descs[m].pt_xyz, B, off, perm);
+        for (size_t k = 1; k < off.size(); k++) {
+            g->batch_off.push_back(g->sys_poff[m] + off[k]);
+            bmol.push_back(m);
+        }
+        for (int64_t p : perm) g->perm.push_back(g->sys_poff[m] + p);
     }
-    g->nb = atom_basis[d->n_atoms];
-    if (g->nb < 1) return fail(NAO_ERR_INVALID_ARG, "no basis functions");
-    if (g->nb >= (int64_t(1) << 31)) return fail(NAO_ERR_INVALID_ARG, "too many basis functions");
-
-    // Sec. 3.3.1: batches
-    g->n_batches = nao_partition(n, d->pt_xyz, g->opt.max_batch_points, g->batch_off, g->perm);
+    g->n_batches = (int64_t)bmol.size();
     const int64_t nbat = g->n_batches;
 
     // points in batch order, structure of arrays
@@ -153,36 +208,37 @@ nao_status build(nao_grid *g, const nao_system_desc *d) {
     std::vector<int32_t> perm32(n), boff32(nbat + 1);
     for (int64_t i = 0; i < n; i++) {
         const int64_t p = g->perm[i];
-        px[i] = d->pt_xyz[3 * p];
-        py[i] = d->pt_xyz[3 * p + 1];
-        pz[i] = d->pt_xyz[3 * p + 2];
-        pw[i] = d->pt_w[p];
+        px[i] = pts[3 * p];
+        py[i] = pts[3 * p + 1];
+        pz[i] = pts[3 * p + 2];
+        pw[i] = wts[p];
         perm32[i] = (int32_t)p;
     }
     for (int64_t b = 0; b <= nbat; b++) boff32[b] = (int32_t)g->batch_off[b];
 
     nao_status st;
     double *d_px, *d_py, *d_pz, *d_pw, *d_atoms;
-    int32_t *d_perm, *d_boff;
+    int32_t *d_perm, *d_boff, *d_bmol, *d_aoff;
     if ((st = upload(g, &d_px, px.data(), n)) || (st = upload(g, &d_py, py.data(), n)) ||
         (st = upload(g, &d_pz, pz.data(), n)) || (st = upload(g, &d_pw, pw.data(), n)) ||
         (st = upload(g, &d_perm, perm32.data(), n)) || (st = upload(g, &d_boff, boff32.data(), nbat + 1)) ||
-        (st = upload(g, &d_atoms, d->atom_xyz, 3 * (size_t)d->n_atoms)))
+        (st = upload(g, &d_atoms, atoms.data(), atoms.size())) || (st = upload(g, &d_bmol, bmol.data(), bmol.size())) ||
+        (st = upload(g, &d_aoff, g->sys_aoff.data(), g->sys_aoff.size())))
         return st;
 
-    // Sec. 3.3.2: nnz(B) from the per-(batch, atom) minimum distance
-    std::vector<double> minr2((size_t)nbat * d->n_atoms);
+    // Sec. 3.3.2: nnz(B) from the per-(batch, atom of its system) minimum distance
+    int32_t max_atoms = 0;
+    for (int m = 0; m < n_sys; m++) max_atoms = std::max(max_atoms, g->sys_aoff[m + 1] - g->sys_aoff[m]);
+    std::vector<double> minr2((size_t)nbat * max_atoms);
     {
         double *d_minr2;
         if ((st = dev_alloc(g, &d_minr2, minr2.size()))) return st;
-        NAO_CUDA(launch_relevance_minr2(d_atoms, d->n_atoms, d_px, d_py, d_pz, d_boff, nbat, d_minr2, 0));
+        NAO_CUDA(launch_relevance_minr2(d_atoms, d_bmol, d_aoff, max_atoms, d_px, d_py, d_pz, d_boff, nbat, d_minr2, 0));
         NAO_CUDA(cudaMemcpy(minr2.data(), d_minr2, minr2.size() * sizeof(double), cudaMemcpyDeviceToHost));
         cudaFree(d_minr2);
         g->allocs.pop_back();
         g->dev_bytes -= (int64_t)std::max<size_t>(minr2.size() * sizeof(double), 16);
     }
-    for (double m : minr2)
-        if (m == 0.0) return fail(NAO_ERR_INVALID_ARG, "a grid point coincides with a nucleus");
 
     std::vector<RfnEntry> rfn;
     std::vector<int32_t> rfn_off32(nbat + 1, 0), rel_off32(nbat + 1, 0);
@@ -190,17 +246,18 @@ nao_status build(nao_grid *g, const nao_system_desc *d) {
     g->Pb.resize(nbat);
     g->Nb.resize(nbat);
     for (int64_t b = 0; b < nbat; b++) {
+        const int m = bmol[b];
         int32_t pos = 0;
-        for (int a = 0; a < d->n_atoms; a++) {
-            const int sp = d->atom_species[a];
-            const double m2 = minr2[(size_t)b * d->n_atoms + a];
+        for (int a = g->sys_aoff[m]; a < g->sys_aoff[m + 1]; a++) {
+            const double m2 = minr2[(size_t)b * max_atoms + (a - g->sys_aoff[m])];
+            if (m2 == 0.0) return fail(NAO_ERR_INVALID_ARG, "a grid point coincides with a nucleus");
             int64_t base = atom_basis[a];
-            for (int f = d->species_fn_offset[sp]; f < d->species_fn_offset[sp + 1]; f++) {
-                const int l = d->fn_l[f];
-                const double rc = d->fn_cutoff[f];
+            for (int f = atom_fn0[a]; f < atom_fn1[a]; f++) {
+                const int l = fn_l[f];
+                const double rc = fn_cut[f];
                 if (m2 < rc * rc) {
                     rfn.push_back({a, f, pos, l});
-                    for (int m = 0; m < 2 * l + 1; m++) g->rel_idx.push_back((int32_t)(base + m));
+                    for (int q = 0; q < 2 * l + 1; q++) g->rel_idx.push_back((int32_t)(base + q));
                     pos += 2 * l + 1;
                 }
                 base += 2 * l + 1;
@@ -237,14 +294,13 @@ nao_status build(nao_grid *g, const nao_system_desc *d) {
     for (int64_t b = 0; b <= nbat; b++) rel_off32[b] = (int32_t)g->rel_off[b];
 
     // radial splines
-    std::vector<double> coef((size_t)g->n_fn * (d->n_rgrid - 1) * 4);
+    const int nr = g->n_rgrid;
+    std::vector<double> coef((size_t)g->n_fn * (nr - 1) * 4);
     for (int f = 0; f < g->n_fn; f++)
-        nao_spline_coefficients(d->fn_table + (size_t)f * d->n_rgrid, d->n_rgrid,
-                                coef.data() + (size_t)f * (d->n_rgrid - 1) * 4);
+        nao_spline_coefficients(fn_tab.data() + (size_t)f * nr, nr, coef.data() + (size_t)f * (nr - 1) * 4);
     std::vector<float> coef32(coef.begin(), coef.end());
-    std::vector<double> inv_rk((size_t)d->n_rgrid);
-    for (int k = 0; k < d->n_rgrid; k++)
-        inv_rk[(size_t)k] = 1.0 / (d->r0 * std::exp((double)k * g->delta));
+    std::vector<double> inv_rk((size_t)nr);
+    for (int k = 0; k < nr; k++) inv_rk[(size_t)k] = 1.0 / (g->r0 * std::exp((double)k * g->delta));
 
     // work lists and chunks of batches that fit the scratch
     std::vector<HWork> hw;
@@ -288,6 +344,18 @@ nao_status build(nao_grid *g, const nao_system_desc *d) {
     g->scratch_elems = budget;
     g->n_hwork = (int64_t)hw.size();
     g->n_dwork = (int64_t)dw.size();
+    // per system: density items, H zeroing chunks and mirror tiles
+    g->sys_dw0.assign(n_sys + 1, 0);
+    for (int64_t w = 0; w < g->n_dwork; w++) g->sys_dw0[bmol[dw[w].batch] + 1] = (int32_t)(w + 1);
+    for (int m = 0; m < n_sys; m++) g->sys_dw0[m + 1] = std::max(g->sys_dw0[m + 1], g->sys_dw0[m]);
+    for (int m = 0; m < n_sys; m++) {
+        const int64_t tot = (int64_t)g->sys_nb[m] * g->sys_nb[m];
+        for (int64_t c = 0; c * 65536 < tot; c++)
+            g->zero_tasks.push_back(make_int4(m, (int)c, (int)std::min<int64_t>(65536, tot - c * 65536), 0));
+        const int nt = (g->sys_nb[m] + 31) / 32;
+        for (int bx = 0; bx < nt; bx++)
+            for (int by = 0; by <= bx; by++) g->mirror_tasks.push_back(make_int4(m, bx, by, 0));
+    }
 
     double *d_coef, *d_rc;
     float *d_coef32;
@@ -299,7 +367,7 @@ nao_status build(nao_grid *g, const nao_system_desc *d) {
     int64_t *d_scr_off;
     if ((st = upload(g, &d_coef, coef.data(), coef.size())) || (st = upload(g, &d_coef32, coef32.data(), coef32.size())) ||
         (st = upload(g, &d_inv_rk, inv_rk.data(), inv_rk.size())) ||
-        (st = upload(g, &d_rc, d->fn_cutoff, (size_t)g->n_fn)) ||
+        (st = upload(g, &d_rc, fn_cut.data(), fn_cut.size())) ||
         (st = upload(g, &d_rel_off, rel_off32.data(), rel_off32.size())) ||
         (st = upload(g, &d_rel_idx, g->rel_idx.data(), g->rel_idx.size())) ||
         (st = upload(g, &d_rfn_off, rfn_off32.data(), rfn_off32.size())) ||
@@ -312,6 +380,17 @@ nao_status build(nao_grid *g, const nao_system_desc *d) {
         (st = dev_alloc(g, &g->d_err, 4)))
         return st;
     NAO_CUDA(cudaMemset(g->d_err, 0, 4 * sizeof(int32_t)));
+    int32_t *d_sboff, *d_snb, *d_spoff;
+    if ((st = upload(g, &d_sboff, g->sys_boff.data(), g->sys_boff.size())) ||
+        (st = upload(g, &d_snb, g->sys_nb.data(), g->sys_nb.size())) ||
+        (st = upload(g, &d_spoff, g->sys_poff.data(), g->sys_poff.size())) ||
+        (st = upload(g, &g->d_sys_dw0, g->sys_dw0.data(), g->sys_dw0.size())) ||
+        (st = upload(g, &g->d_zero_tasks, g->zero_tasks.data(), g->zero_tasks.size())) ||
+        (st = upload(g, &g->d_mirror_tasks, g->mirror_tasks.data(), g->mirror_tasks.size())) ||
+        (st = dev_alloc(g, &g->d_tab, 5 * (size_t)n_sys)))
+        return st;
+    NAO_CUDA(cudaMemset(g->d_tab, 0, 5 * (size_t)n_sys * sizeof(double *)));
+    g->h_tab.assign(5 * (size_t)n_sys, nullptr);
 
     DevSystem &s = g->sys;
     s.atom_xyz = d_atoms;
@@ -332,8 +411,18 @@ nao_status build(nao_grid *g, const nao_system_desc *d) {
     s.agrp = d_agrp;
     s.agrp_off = d_agrp_off;
     s.scr_off = d_scr_off;
-    s.n_rgrid = d->n_rgrid;
-    s.r0 = d->r0;
+    s.sys.bmol = d_bmol;
+    s.sys.boff = d_sboff;
+    s.sys.nbm = d_snb;
+    s.sys.poff = d_spoff;
+    s.sys.aoff = d_aoff;
+    s.sys.H = g->d_tab;
+    s.sys.v = g->d_tab + n_sys;
+    s.sys.P = g->d_tab + 2 * n_sys;
+    s.sys.n = g->d_tab + 3 * n_sys;
+    s.sys.ne = g->d_tab + 4 * n_sys;
+    s.n_rgrid = g->n_rgrid;
+    s.r0 = g->r0;
     s.inv_delta = 1.0 / g->delta;
     s.nb = g->nb;
     for (int l = 0; l <= NAO_LMAX; l++)
@@ -412,7 +501,7 @@ nao_status split_setup(nao_grid *g) {
         int64_t used = 0;
         for (int32_t b = c.b0; b < c.b1; b++) {
             const int P = g->Pb[b], N = g->Nb[b];
-            const SplitGeom G(P, N);
+            const SplitGeom G(P, N, S);
             const int64_t need = N == 0 ? 0 : (int64_t)std::max(G.h_bytes(S), G.n_bytes(S));
             if (used + need > budget && b > cur.b0) {
                 cur.b1 = b;
@@ -429,10 +518,11 @@ nao_status split_setup(nao_grid *g) {
             if (N > 0) {
                 cur.max_rt = std::max<int32_t>(cur.max_rt, G.h_slice_tiles());
                 cur.max_qt = std::max<int32_t>(cur.max_qt, G.n_qt);
-                const int nI = (N + 127) / 128, nJ = (N + NAO_SPLIT_TN - 1) / NAO_SPLIT_TN;
+                const int TN = nao_split_tn(S);
+                const int nI = (N + 127) / 128, nJ = (N + TN - 1) / TN;
                 for (int I = 0; I < nI; I++)
                     for (int J = 0; J < nJ; J++)
-                        if (I * 128 <= J * NAO_SPLIT_TN + NAO_SPLIT_TN - 1) hw.push_back({b, I, J, 0});
+                        if (I * 128 <= J * TN + TN - 1) hw.push_back({b, I, J, 0});
                 for (int Q = 0; Q < G.n_qt; Q++)
                     for (int J = 0; J < G.n_jtN; J++) nw.push_back({b, Q, J, 0});
             }
@@ -459,79 +549,130 @@ nao_status split_setup(nao_grid *g) {
     return NAO_OK;
 }
 
-nao_status run_h_split(nao_grid *g, const double *v, uint32_t terms, double *H, cudaStream_t st) {
-    nao_status sst = split_setup(g);
-    if (sst) return sst;
-    const DevSystem &s = g->sys;
-    const int S = g->split_S;
-    NAO_CUDA(cudaMemsetAsync(H, 0, (size_t)g->nb * g->nb * sizeof(double), st));
-    for (const auto &c : g->split_chunks) {
-        NAO_CUDA(timed(g, NAO_K_EVAL_GRAD, st, [&] { return launch_eval(s, c.b0, c.b1, NAO_FP64, true, g->d_scratch, st); }));
-        NAO_CUDA(timed(g, NAO_K_SLICE, st, [&] {
-            return launch_slice_h(s, c.b0, c.b1, c.max_rt, g->d_scratch, v, terms, g->d_slices, g->d_sl_off_h, g->d_expo_h,
-                                  g->d_neg16, S, st);
-        }));
-        NAO_CUDA(timed(g, NAO_K_H_SPLIT, st, [&] {
-            return launch_h_tc(s, g->d_split_hw, c.hw0, c.hw1 - c.hw0, g->d_slices, g->d_sl_off_h, g->d_expo_h,
-                               g->d_neg16, S, H, g->d_err, st);
-        }));
-    }
-    NAO_CUDA(timed(g, NAO_K_MIRROR, st, [&] { return launch_mirror(H, g->nb, st); }));
+// This call's pointer tables (sections: 0 H, 1 v, 2 P, 3 n, 4 N_e; one entry per system),
+// copied from host memory the library owns (pageable: the source may be reused on return).
+nao_status upload_tables(nao_grid *g, int first, int count, cudaStream_t st) {
+    const size_t n = (size_t)g->n_sys;
+    NAO_CUDA(cudaMemcpyAsync(g->d_tab + first * n, g->h_tab.data() + first * n, count * n * sizeof(void *),
+                             cudaMemcpyHostToDevice, st));
     return NAO_OK;
 }
 
-nao_status run_n_split(nao_grid *g, const double *P, double *n, double *ne, cudaStream_t st) {
-    nao_status sst = split_setup(g);
-    if (sst) return sst;
-    const DevSystem &s = g->sys;
-    const int S = g->split_S;
-    NAO_CUDA(cudaMemsetAsync(n, 0, (size_t)g->n_points * sizeof(double), st));
-    for (const auto &c : g->split_chunks) {
-        NAO_CUDA(timed(g, NAO_K_EVAL_PHI, st, [&] { return launch_eval(s, c.b0, c.b1, NAO_FP64, false, g->d_scratch, st); }));
-        NAO_CUDA(timed(g, NAO_K_SLICE, st, [&] {
-            return launch_slice_n(s, c.b0, c.b1, c.max_qt, g->d_scratch, P, g->d_slices, g->d_sl_off_n, g->d_expo_q,
-                                  g->d_expo_b, S, st);
-        }));
-        NAO_CUDA(timed(g, NAO_K_N_SPLIT, st, [&] {
-            return launch_n_tc(s, g->d_split_nw, c.nw0, c.nw1 - c.nw0, g->d_slices, g->d_sl_off_n, g->d_expo_q,
-                               g->d_expo_b, g->d_scratch, S, n, g->d_err, st);
-        }));
+// Runs enqueue(stream) either directly on st, or (capture_graph) as a CUDA graph replayed on
+// the handle's own stream, ordered after st's prior work and before st's later work by events.
+// The first call with a given key captures and instantiates the graph.
+template <class F>
+nao_status run_maybe_graph(nao_grid *g, uint64_t key, cudaStream_t st, F &&enqueue) {
+    if (!g->opt.capture_graph || g->profiling) return enqueue(st);
+    if (!g->gstream) {
+        NAO_CUDA(cudaStreamCreateWithFlags(&g->gstream, cudaStreamNonBlocking));
+        NAO_CUDA(cudaEventCreateWithFlags(&g->ev_in, cudaEventDisableTiming));
+        NAO_CUDA(cudaEventCreateWithFlags(&g->ev_out, cudaEventDisableTiming));
     }
-    if (ne) {
-        NAO_CUDA(timed(g, NAO_K_REDUCE, st, [&] {
-            cudaError_t e = launch_wn_partial(s, g->d_dwork, 0, (int32_t)g->n_dwork, n, g->d_ne_part, st);
-            return e != cudaSuccess ? e : launch_reduce_sum(g->d_ne_part, g->n_dwork, ne, st);
-        }));
+    NAO_CUDA(cudaEventRecord(g->ev_in, st));
+    NAO_CUDA(cudaStreamWaitEvent(g->gstream, g->ev_in, 0));
+    auto it = g->graphs.find(key);
+    if (it == g->graphs.end()) {
+        NAO_CUDA(cudaStreamBeginCapture(g->gstream, cudaStreamCaptureModeThreadLocal));
+        const nao_status es = enqueue(g->gstream);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(g->gstream, &graph);
+        if (es != NAO_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return es;
+        }
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+        cudaGraphExec_t exec = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) return cuda_fail(ie, "cudaGraphInstantiate");
+        it = g->graphs.emplace(key, exec).first;
     }
+    NAO_CUDA(cudaGraphLaunch(it->second, g->gstream));
+    NAO_CUDA(cudaEventRecord(g->ev_out, g->gstream));
+    NAO_CUDA(cudaStreamWaitEvent(st, g->ev_out, 0));
     return NAO_OK;
 }
 
-nao_status run_h(nao_grid *g, const double *v, uint32_t terms, nao_precision prec, double *H, cudaStream_t st) {
-    if (prec == NAO_SPLIT) return run_h_split(g, v, terms, H, st);
+nao_status enqueue_h(nao_grid *g, uint32_t terms, nao_precision prec, cudaStream_t st) {
     const DevSystem &s = g->sys;
-    NAO_CUDA(cudaMemsetAsync(H, 0, (size_t)g->nb * g->nb * sizeof(double), st));
-    for (const Chunk &c : g->chunks) {
-        NAO_CUDA(timed(g, NAO_K_EVAL_GRAD, st, [&] { return launch_eval(s, c.b0, c.b1, prec, true, g->d_scratch, st); }));
-        NAO_CUDA(timed(g, prec == NAO_FP32 ? NAO_K_H_FP32 : NAO_K_H_FP64, st, [&] {
-            return launch_h_simt(s, prec, g->d_hwork + c.hw0, c.hw1 - c.hw0, g->d_scratch, v, terms, H, st);
-        }));
+    NAO_CUDA(launch_zero_h(s, g->d_zero_tasks, (int32_t)g->zero_tasks.size(), st));
+    if (prec == NAO_SPLIT) {
+        const int S = g->split_S;
+        for (const auto &c : g->split_chunks) {
+            NAO_CUDA(timed(g, NAO_K_EVAL_GRAD, st, [&] { return launch_eval(s, c.b0, c.b1, NAO_FP64, true, g->d_scratch, st); }));
+            NAO_CUDA(timed(g, NAO_K_SLICE, st, [&] {
+                return launch_slice_h(s, c.b0, c.b1, c.max_rt, g->d_scratch, terms, g->d_slices, g->d_sl_off_h,
+                                      g->d_expo_h, g->d_neg16, S, st);
+            }));
+            NAO_CUDA(timed(g, NAO_K_H_SPLIT, st, [&] {
+                return launch_h_tc(s, g->d_split_hw, c.hw0, c.hw1 - c.hw0, g->d_slices, g->d_sl_off_h, g->d_expo_h,
+                                   g->d_neg16, S, g->d_err, st);
+            }));
+        }
+    } else {
+        for (const Chunk &c : g->chunks) {
+            NAO_CUDA(timed(g, NAO_K_EVAL_GRAD, st, [&] { return launch_eval(s, c.b0, c.b1, prec, true, g->d_scratch, st); }));
+            NAO_CUDA(timed(g, prec == NAO_FP32 ? NAO_K_H_FP32 : NAO_K_H_FP64, st, [&] {
+                return launch_h_simt(s, prec, g->d_hwork + c.hw0, c.hw1 - c.hw0, g->d_scratch, terms, st);
+            }));
+        }
     }
-    NAO_CUDA(timed(g, NAO_K_MIRROR, st, [&] { return launch_mirror(H, g->nb, st); }));
+    NAO_CUDA(timed(g, NAO_K_MIRROR, st, [&] { return launch_mirror(s, g->d_mirror_tasks, (int32_t)g->mirror_tasks.size(), st); }));
     return NAO_OK;
 }
 
-nao_status run_n(nao_grid *g, const double *P, nao_precision prec, double *n, double *ne, cudaStream_t st) {
-    if (prec == NAO_SPLIT) return run_n_split(g, P, n, ne, st);
+nao_status enqueue_n(nao_grid *g, nao_precision prec, bool want_ne, cudaStream_t st) {
     const DevSystem &s = g->sys;
-    for (const Chunk &c : g->chunks) {
-        NAO_CUDA(timed(g, NAO_K_EVAL_PHI, st, [&] { return launch_eval(s, c.b0, c.b1, prec, false, g->d_scratch, st); }));
-        NAO_CUDA(timed(g, prec == NAO_FP32 ? NAO_K_N_FP32 : NAO_K_N_FP64, st, [&] {
-            return launch_density_simt(s, prec, g->d_dwork, c.dw0, c.dw1 - c.dw0, g->d_scratch, P, n, g->d_ne_part, st);
-        }));
+    if (prec == NAO_SPLIT) {
+        const int S = g->split_S;
+        NAO_CUDA(launch_zero_n(s, g->d_dwork, (int32_t)g->n_dwork, st));
+        for (const auto &c : g->split_chunks) {
+            NAO_CUDA(timed(g, NAO_K_EVAL_PHI, st, [&] { return launch_eval(s, c.b0, c.b1, NAO_FP64, false, g->d_scratch, st); }));
+            NAO_CUDA(timed(g, NAO_K_SLICE, st, [&] {
+                return launch_slice_n(s, c.b0, c.b1, c.max_qt, g->d_scratch, g->d_slices, g->d_sl_off_n, g->d_expo_q,
+                                      g->d_expo_b, S, st);
+            }));
+            NAO_CUDA(timed(g, NAO_K_N_SPLIT, st, [&] {
+                return launch_n_tc(s, g->d_split_nw, c.nw0, c.nw1 - c.nw0, g->d_slices, g->d_sl_off_n, g->d_expo_q,
+                                   g->d_expo_b, g->d_scratch, S, g->d_err, st);
+            }));
+        }
+        if (want_ne) NAO_CUDA(launch_wn_partial(s, g->d_dwork, 0, (int32_t)g->n_dwork, g->d_ne_part, st));
+    } else {
+        for (const Chunk &c : g->chunks) {
+            NAO_CUDA(timed(g, NAO_K_EVAL_PHI, st, [&] { return launch_eval(s, c.b0, c.b1, prec, false, g->d_scratch, st); }));
+            NAO_CUDA(timed(g, prec == NAO_FP32 ? NAO_K_N_FP32 : NAO_K_N_FP64, st, [&] {
+                return launch_density_simt(s, prec, g->d_dwork, c.dw0, c.dw1 - c.dw0, g->d_scratch, g->d_ne_part, st);
+            }));
+        }
     }
-    if (ne) NAO_CUDA(timed(g, NAO_K_REDUCE, st, [&] { return launch_reduce_sum(g->d_ne_part, g->n_dwork, ne, st); }));
+    if (want_ne)
+        NAO_CUDA(timed(g, NAO_K_REDUCE, st, [&] { return launch_reduce_ne(s, g->d_ne_part, g->d_sys_dw0, g->n_sys, st); }));
     return NAO_OK;
 }
+
+// H of every system from the tables' sections 0 (H) and 1 (v), already filled in g->h_tab.
+nao_status run_h(nao_grid *g, uint32_t terms, nao_precision prec, cudaStream_t st) {
+    nao_status rs;
+    if (prec == NAO_SPLIT && (rs = split_setup(g))) return rs;
+    if ((rs = upload_tables(g, 0, 2, st))) return rs;
+    const uint64_t key = (uint64_t)1 << 40 | (uint64_t)prec << 8 | terms;
+    return run_maybe_graph(g, key, st, [&](cudaStream_t s2) { return enqueue_h(g, terms, prec, s2); });
+}
+
+// n (and N_e where a table entry is set) of every system from sections 2 (P), 3 (n), 4 (N_e).
+nao_status run_n(nao_grid *g, nao_precision prec, cudaStream_t st) {
+    nao_status rs;
+    if (prec == NAO_SPLIT && (rs = split_setup(g))) return rs;
+    if ((rs = upload_tables(g, 2, 3, st))) return rs;
+    bool want_ne = false;
+    for (int m = 0; m < g->n_sys; m++) want_ne = want_ne || g->h_tab[4 * (size_t)g->n_sys + m] != nullptr;
+    const uint64_t key = (uint64_t)2 << 40 | (uint64_t)prec << 8 | (want_ne ? 1u : 0u);
+    return run_maybe_graph(g, key, st, [&](cudaStream_t s2) { return enqueue_n(g, prec, want_ne, s2); });
+}
+
+void set_tab(nao_grid *g, int section, int m, const void *p) { g->h_tab[(size_t)section * g->n_sys + m] = const_cast<void *>(p); }
 
 }  // namespace
 
@@ -543,21 +684,31 @@ nao_status nao_default_options(nao_options *o) {
     if (!o) return fail(NAO_ERR_INVALID_ARG, "opts is NULL");
     std::memset(o, 0, sizeof(*o));
     o->max_batch_points = 200;
-    o->split_slices = 10;
+    o->split_slices = 12;
     o->deterministic = 0;
     o->device = -1;
     o->scratch_bytes = 0;
+    o->capture_graph = 0;
+    o->reserved0 = 0;
     return NAO_OK;
 }
 
-nao_status nao_grid_create(const nao_system_desc *desc, const nao_options *opts, nao_grid **out) {
+static nao_status create(const nao_system_desc *descs, int32_t n_sys, const nao_options *opts, nao_grid **out) {
     if (!out) return fail(NAO_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
+    if (!descs) return fail(NAO_ERR_INVALID_ARG, "desc is NULL");
+    if (n_sys < 1) return fail(NAO_ERR_INVALID_ARG, "n_systems < 1");
     nao_options o;
     nao_default_options(&o);
     if (opts) o = *opts;
-    nao_status st = validate(desc, o);
-    if (st != NAO_OK) return st;
+    if (o.reserved0 != 0) return fail(NAO_ERR_INVALID_ARG, "options.reserved0 must be 0");
+    if (o.capture_graph != 0 && o.capture_graph != 1) return fail(NAO_ERR_INVALID_ARG, "options.capture_graph not 0/1");
+    nao_status st;
+    for (int32_t m = 0; m < n_sys; m++)
+        if ((st = validate(&descs[m], o)) != NAO_OK) {
+            if (n_sys > 1) g_last_error = "system " + std::to_string(m) + ": " + g_last_error;
+            return st;
+        }
     int dev = o.device;
     if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return fail(NAO_ERR_CUDA, "no CUDA device");
     int ndev = 0;
@@ -573,7 +724,7 @@ nao_status nao_grid_create(const nao_system_desc *desc, const nao_options *opts,
     g->opt = o;
     g->opt.device = dev;
     try {
-        st = build(g, desc);
+        st = build(g, descs, n_sys, nullptr);
     } catch (const std::bad_alloc &) {
         st = fail(NAO_ERR_OUT_OF_MEMORY, "host allocation failed");
     } catch (...) {
@@ -584,6 +735,35 @@ nao_status nao_grid_create(const nao_system_desc *desc, const nao_options *opts,
         return st;
     }
     *out = g;
+    return NAO_OK;
+}
+
+nao_status nao_grid_create(const nao_system_desc *desc, const nao_options *opts, nao_grid **out) {
+    return create(desc, 1, opts, out);
+}
+
+nao_status nao_grid_create_many(const nao_system_desc *descs, int32_t n_systems, const nao_options *opts,
+                                nao_grid **out) {
+    return create(descs, n_systems, opts, out);
+}
+
+nao_status nao_get_system(const nao_grid *g, int32_t m, int64_t *basis_offset, int64_t *n_basis, int64_t *point_offset,
+                          int64_t *n_points, int64_t *batch_begin, int64_t *batch_end) {
+    nao_status st = check_handle(g);
+    if (st) return st;
+    if (m < 0 || m >= g->n_sys) return fail(NAO_ERR_INVALID_ARG, "system index out of range");
+    if (basis_offset) *basis_offset = g->sys_boff[m];
+    if (n_basis) *n_basis = g->sys_nb[m];
+    if (point_offset) *point_offset = g->sys_poff[m];
+    if (n_points) *n_points = g->sys_np[m];
+    if (batch_begin || batch_end) {
+        // batches of system m are contiguous; their points are the system's point range
+        const int64_t p0 = g->sys_poff[m], p1 = p0 + g->sys_np[m];
+        const auto b0 = std::lower_bound(g->batch_off.begin(), g->batch_off.end(), p0) - g->batch_off.begin();
+        const auto b1 = std::lower_bound(g->batch_off.begin(), g->batch_off.end(), p1) - g->batch_off.begin();
+        if (batch_begin) *batch_begin = b0;
+        if (batch_end) *batch_end = b1;
+    }
     return NAO_OK;
 }
 
@@ -608,6 +788,8 @@ nao_status nao_get_info(const nao_grid *g, nao_grid_info *info) {
     info->device_bytes = g->dev_bytes;
     info->flops_h = g->flops_h;
     info->flops_n = g->flops_n;
+    info->n_systems = g->n_sys;
+    info->reserved0 = 0;
     return NAO_OK;
 }
 
@@ -622,27 +804,79 @@ nao_status nao_export_batches(const nao_grid *g, int64_t *batch_offsets, int64_t
     return NAO_OK;
 }
 
+static nao_status check_single(const nao_grid *g) {
+    if (g->n_sys != 1)
+        return fail(NAO_ERR_INVALID_ARG,
+                    "the handle holds " + std::to_string(g->n_sys) + " systems; use the _many entry points");
+    return NAO_OK;
+}
+
+static nao_status check_terms(uint32_t terms) {
+    if (terms == 0 || (terms & ~3u)) return fail(NAO_ERR_INVALID_ARG, "bad terms");
+    return NAO_OK;
+}
+
 nao_status nao_integrate_h(nao_grid *g, const double *v_dev, uint32_t terms, nao_precision prec, double *H_dev,
                            void *cuda_stream) {
     nao_status st = check_handle(g);
-    if (st) return st;
+    if (st || (st = check_single(g))) return st;
     if (!H_dev) return fail(NAO_ERR_INVALID_ARG, "H_dev is NULL");
-    if (terms == 0 || (terms & ~3u)) return fail(NAO_ERR_INVALID_ARG, "bad terms");
-    if ((st = check_prec(prec))) return st;
+    if ((st = check_terms(terms)) || (st = check_prec(prec))) return st;
     DeviceGuard guard(g->device);
     if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
-    return run_h(g, v_dev, terms, prec, H_dev, static_cast<cudaStream_t>(cuda_stream));
+    set_tab(g, 0, 0, H_dev);
+    set_tab(g, 1, 0, v_dev);
+    return run_h(g, terms, prec, static_cast<cudaStream_t>(cuda_stream));
+}
+
+nao_status nao_integrate_h_many(nao_grid *g, const double *const *v_dev, uint32_t terms, nao_precision prec,
+                                double *const *H_dev, void *cuda_stream) {
+    nao_status st = check_handle(g);
+    if (st) return st;
+    if (!H_dev) return fail(NAO_ERR_INVALID_ARG, "H_dev is NULL");
+    for (int m = 0; m < g->n_sys; m++)
+        if (!H_dev[m]) return fail(NAO_ERR_INVALID_ARG, "H_dev[" + std::to_string(m) + "] is NULL");
+    if ((st = check_terms(terms)) || (st = check_prec(prec))) return st;
+    DeviceGuard guard(g->device);
+    if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    for (int m = 0; m < g->n_sys; m++) {
+        set_tab(g, 0, m, H_dev[m]);
+        set_tab(g, 1, m, v_dev ? v_dev[m] : nullptr);
+    }
+    return run_h(g, terms, prec, static_cast<cudaStream_t>(cuda_stream));
 }
 
 nao_status nao_update_density(nao_grid *g, const double *P_dev, nao_precision prec, double *n_dev,
                               double *n_electrons_dev, void *cuda_stream) {
     nao_status st = check_handle(g);
-    if (st) return st;
+    if (st || (st = check_single(g))) return st;
     if (!P_dev || !n_dev) return fail(NAO_ERR_INVALID_ARG, "P_dev or n_dev is NULL");
     if ((st = check_prec(prec))) return st;
     DeviceGuard guard(g->device);
     if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
-    return run_n(g, P_dev, prec, n_dev, n_electrons_dev, static_cast<cudaStream_t>(cuda_stream));
+    set_tab(g, 2, 0, P_dev);
+    set_tab(g, 3, 0, n_dev);
+    set_tab(g, 4, 0, n_electrons_dev);
+    return run_n(g, prec, static_cast<cudaStream_t>(cuda_stream));
+}
+
+nao_status nao_update_density_many(nao_grid *g, const double *const *P_dev, nao_precision prec, double *const *n_dev,
+                                   double *const *n_electrons_dev, void *cuda_stream) {
+    nao_status st = check_handle(g);
+    if (st) return st;
+    if (!P_dev || !n_dev) return fail(NAO_ERR_INVALID_ARG, "P_dev or n_dev is NULL");
+    for (int m = 0; m < g->n_sys; m++)
+        if (!P_dev[m] || !n_dev[m])
+            return fail(NAO_ERR_INVALID_ARG, "P_dev[" + std::to_string(m) + "] or n_dev[" + std::to_string(m) + "] is NULL");
+    if ((st = check_prec(prec))) return st;
+    DeviceGuard guard(g->device);
+    if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    for (int m = 0; m < g->n_sys; m++) {
+        set_tab(g, 2, m, P_dev[m]);
+        set_tab(g, 3, m, n_dev[m]);
+        set_tab(g, 4, m, n_electrons_dev ? n_electrons_dev[m] : nullptr);
+    }
+    return run_n(g, prec, static_cast<cudaStream_t>(cuda_stream));
 }
 
 static nao_status ensure_staging(nao_grid *g) {
@@ -658,10 +892,9 @@ static nao_status ensure_staging(nao_grid *g) {
 nao_status nao_integrate_h_host(nao_grid *g, const double *v_host, uint32_t terms, nao_precision prec, double *H_host,
                                 void *cuda_stream) {
     nao_status st = check_handle(g);
-    if (st) return st;
+    if (st || (st = check_single(g))) return st;
     if (!H_host) return fail(NAO_ERR_INVALID_ARG, "H_host is NULL");
-    if (terms == 0 || (terms & ~3u)) return fail(NAO_ERR_INVALID_ARG, "bad terms");
-    if ((st = check_prec(prec))) return st;
+    if ((st = check_terms(terms)) || (st = check_prec(prec))) return st;
     DeviceGuard guard(g->device);
     if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
     if ((st = ensure_staging(g))) return st;
@@ -671,7 +904,9 @@ nao_status nao_integrate_h_host(nao_grid *g, const double *v_host, uint32_t term
         NAO_CUDA(cudaMemcpyAsync(g->d_stage_in, v_host, (size_t)g->n_points * sizeof(double), cudaMemcpyHostToDevice, s));
         v = g->d_stage_in;
     }
-    if ((st = run_h(g, v, terms, prec, g->d_stage_out, s))) return st;
+    set_tab(g, 0, 0, g->d_stage_out);
+    set_tab(g, 1, 0, v);
+    if ((st = run_h(g, terms, prec, s))) return st;
     NAO_CUDA(cudaMemcpyAsync(H_host, g->d_stage_out, (size_t)g->nb * g->nb * sizeof(double), cudaMemcpyDeviceToHost, s));
     NAO_CUDA(cudaStreamSynchronize(s));
     return NAO_OK;
@@ -680,7 +915,7 @@ nao_status nao_integrate_h_host(nao_grid *g, const double *v_host, uint32_t term
 nao_status nao_update_density_host(nao_grid *g, const double *P_host, nao_precision prec, double *n_host,
                                    double *n_electrons_host, void *cuda_stream) {
     nao_status st = check_handle(g);
-    if (st) return st;
+    if (st || (st = check_single(g))) return st;
     if (!P_host || !n_host) return fail(NAO_ERR_INVALID_ARG, "P_host or n_host is NULL");
     if ((st = check_prec(prec))) return st;
     DeviceGuard guard(g->device);
@@ -688,7 +923,10 @@ nao_status nao_update_density_host(nao_grid *g, const double *P_host, nao_precis
     if ((st = ensure_staging(g))) return st;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     NAO_CUDA(cudaMemcpyAsync(g->d_stage_in, P_host, (size_t)g->nb * g->nb * sizeof(double), cudaMemcpyHostToDevice, s));
-    if ((st = run_n(g, g->d_stage_in, prec, g->d_stage_out, n_electrons_host ? g->d_stage_ne : nullptr, s))) return st;
+    set_tab(g, 2, 0, g->d_stage_in);
+    set_tab(g, 3, 0, g->d_stage_out);
+    set_tab(g, 4, 0, n_electrons_host ? g->d_stage_ne : nullptr);
+    if ((st = run_n(g, prec, s))) return st;
     NAO_CUDA(cudaMemcpyAsync(n_host, g->d_stage_out, (size_t)g->n_points * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (n_electrons_host)
         NAO_CUDA(cudaMemcpyAsync(n_electrons_host, g->d_stage_ne, sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -94,15 +94,14 @@ struct Block {
 
 template <typename T>
 __global__ void __launch_bounds__(256) h_simt_kernel(DevSystem s, const HWork *__restrict__ work,
-                                                    const T *__restrict__ scratch, const double *__restrict__ v,
-                                                    uint32_t terms, double *__restrict__ H) {
+                                                    const T *__restrict__ scratch, uint32_t terms) {
     constexpr int KC = Cfg<T>::KC;
     constexpr int VL = KC / 4;  // elements each thread loads per row segment
     __shared__ __align__(16) T As[KC][T_];
     __shared__ __align__(16) T Bs[KC][T_];
     __shared__ T dv[NAO_MAX_BATCH], dk[NAO_MAX_BATCH];  // weights of the potential and kinetic parts
     const HWork it = work[blockIdx.x];
-    const int b = it.batch;
+    const int b = it.batch, m = s.sys.bmol[b];
     const int p0 = s.batch_off[b], P = s.batch_off[b + 1] - p0;
     const int Ppad = (P + NAO_PPAD - 1) & ~(NAO_PPAD - 1);
     const int N = s.rel_off[b + 1] - s.rel_off[b];
@@ -112,7 +111,7 @@ __global__ void __launch_bounds__(256) h_simt_kernel(DevSystem s, const HWork *_
 
     for (int q = tid; q < Ppad; q += blockDim.x) {
         const double w = q < P ? s.pw[p0 + q] : 0.0;
-        const double vv = (q < P && v) ? v[s.perm[p0 + q]] : 1.0;
+        const double vv = q < P ? v_at(s, m, p0 + q) : 1.0;
         dv[q] = T((terms & NAO_TERM_POTENTIAL) ? w * vv : 0.0);
         dk[q] = T((terms & NAO_TERM_KINETIC) ? 0.5 * w : 0.0);
     }
@@ -158,16 +157,19 @@ __global__ void __launch_bounds__(256) h_simt_kernel(DevSystem s, const HWork *_
         for (int c = 0; c < 4; c++) {
             const int j = j0 + tx * 4 + c;
             if (j >= N || (diag && j < i)) continue;
-            atomicAdd(H + gi * s.nb + rel[j], acc.value(a, c));
+            atomicAdd(h_elem(s, m, gi, rel[j]), acc.value(a, c));
         }
     }
 }
 
-// Copy the upper triangle onto the lower one through 32 x 32 shared-memory tiles.
-__global__ void mirror_kernel(double *__restrict__ H, int64_t nb) {
+// Copy the upper triangle of each system's H onto its lower one, through 32 x 32 tiles; one
+// CTA per task (system, column tile bx, row tile by) with by <= bx.
+__global__ void mirror_kernel(DevSystem s, const int4 *__restrict__ tasks) {
     __shared__ double tile[32][33];
-    const int bx = blockIdx.x, by = blockIdx.y;  // source tile (row block by, column block bx), by <= bx
-    if (by > bx) return;
+    const int4 tk = tasks[blockIdx.x];
+    const int m = tk.x, bx = tk.y, by = tk.z;
+    double *H = s.sys.H[m];
+    const int64_t nb = s.sys.nbm[m];
     const int tx = threadIdx.x, ty = threadIdx.y;
     for (int r = ty; r < 32; r += blockDim.y) {
         const int64_t row = (int64_t)by * 32 + r, col = (int64_t)bx * 32 + tx;
@@ -180,10 +182,16 @@ __global__ void mirror_kernel(double *__restrict__ H, int64_t nb) {
     }
 }
 
+// H = 0 for each task (system, first element, count).
+__global__ void __launch_bounds__(256) zero_h_kernel(DevSystem s, const int4 *__restrict__ tasks) {
+    const int4 tk = tasks[blockIdx.x];
+    double *H = s.sys.H[tk.x] + (int64_t)tk.y * 65536;
+    for (int i = threadIdx.x; i < tk.z; i += blockDim.x) H[i] = 0.0;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) density_simt_kernel(DevSystem s, const DWork *__restrict__ work, int32_t w0,
-                                                          const T *__restrict__ scratch, const double *__restrict__ Pm,
-                                                          double *__restrict__ nout, double *__restrict__ ne_part) {
+                                                          const T *__restrict__ scratch, double *__restrict__ ne_part) {
     constexpr int KC = Cfg<T>::KC;
     constexpr int RPT = (KC * T_) / 256;     // elements each thread loads per tile
     __shared__ __align__(16) T As[KC][T_];  // phi[i][q]
@@ -191,7 +199,7 @@ __global__ void __launch_bounds__(256) density_simt_kernel(DevSystem s, const DW
     __shared__ double nacc[T_];
     __shared__ double red[8];
     const DWork it = work[w0 + blockIdx.x];
-    const int b = it.batch;
+    const int b = it.batch, m = s.sys.bmol[b];
     const int p0 = s.batch_off[b], P = s.batch_off[b + 1] - p0;
     const int Ppad = (P + NAO_PPAD - 1) & ~(NAO_PPAD - 1);
     const int N = s.rel_off[b + 1] - s.rel_off[b];
@@ -223,7 +231,7 @@ __global__ void __launch_bounds__(256) density_simt_kernel(DevSystem s, const DW
                     if (i < N && j < N) {
                         int64_t gi = rel[i], gj = rel[j];
                         if (gi > gj) { const int64_t t = gi; gi = gj; gj = t; }
-                        pv = T(scale * Pm[gi * s.nb + gj]);
+                        pv = T(scale * p_elem(s, m, gi, gj));
                     }
                     Bs[lk][lc + u] = pv;
                 }
@@ -256,7 +264,7 @@ __global__ void __launch_bounds__(256) density_simt_kernel(DevSystem s, const DW
         const int q = q0 + tid;
         if (q < P) {
             const double nv = nacc[tid];
-            nout[s.perm[p0 + q]] = nv;
+            *n_at(s, m, p0 + q) = nv;
             wn = s.pw[p0 + q] * nv;
         }
     }
@@ -271,12 +279,16 @@ __global__ void __launch_bounds__(256) density_simt_kernel(DevSystem s, const DW
     }
 }
 
-// Deterministic single-CTA sum (fixed assignment and fixed tree order).
-__global__ void __launch_bounds__(1024) reduce_sum_kernel(const double *__restrict__ part, int64_t n,
-                                                         double *__restrict__ out) {
+// N_e of each system: one CTA per system sums its density work items' partial sums in a fixed
+// assignment and tree order (deterministic).
+__global__ void __launch_bounds__(1024) reduce_ne_kernel(DevSystem s, const double *__restrict__ part,
+                                                        const int32_t *__restrict__ sys_dw0) {
     __shared__ double red[32];
+    const int m = blockIdx.x;
+    double *out = s.sys.ne[m];
+    if (!out) return;
     double t = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) t += part[i];
+    for (int64_t i = sys_dw0[m] + threadIdx.x; i < sys_dw0[m + 1]; i += blockDim.x) t += part[i];
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
     __syncthreads();
@@ -287,37 +299,58 @@ __global__ void __launch_bounds__(1024) reduce_sum_kernel(const double *__restri
     }
 }
 
+// n = 0 at the points of each density work item (before accumulation by atomics).
+__global__ void __launch_bounds__(64) zero_n_kernel(DevSystem s, const DWork *__restrict__ work) {
+    const DWork it = work[blockIdx.x];
+    const int p0 = s.batch_off[it.batch], P = s.batch_off[it.batch + 1] - p0;
+    const int q = it.tp * NAO_TILE + threadIdx.x;
+    if (q < P) *n_at(s, s.sys.bmol[it.batch], p0 + q) = 0.0;
+}
+
 }  // namespace
 
 cudaError_t launch_h_simt(const DevSystem &s, nao_precision prec, const HWork *work, int32_t n_work,
-                          const double *scratch, const double *v, uint32_t terms, double *H, cudaStream_t st) {
+                          const double *scratch, uint32_t terms, cudaStream_t st) {
     if (n_work <= 0) return cudaSuccess;
     if (prec == NAO_FP32)
-        h_simt_kernel<float><<<n_work, 256, 0, st>>>(s, work, reinterpret_cast<const float *>(scratch), v, terms, H);
+        h_simt_kernel<float><<<n_work, 256, 0, st>>>(s, work, reinterpret_cast<const float *>(scratch), terms);
     else
-        h_simt_kernel<double><<<n_work, 256, 0, st>>>(s, work, scratch, v, terms, H);
+        h_simt_kernel<double><<<n_work, 256, 0, st>>>(s, work, scratch, terms);
     return cudaGetLastError();
 }
 
-cudaError_t launch_mirror(double *H, int64_t nb, cudaStream_t st) {
-    const unsigned g = (unsigned)((nb + 31) / 32);
-    if (g == 0) return cudaSuccess;
-    mirror_kernel<<<dim3(g, g), dim3(32, 8), 0, st>>>(H, nb);
+cudaError_t launch_zero_h(const DevSystem &s, const int4 *tasks, int32_t n_tasks, cudaStream_t st) {
+    if (n_tasks <= 0) return cudaSuccess;
+    zero_h_kernel<<<n_tasks, 256, 0, st>>>(s, tasks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mirror(const DevSystem &s, const int4 *tasks, int32_t n_tasks, cudaStream_t st) {
+    if (n_tasks <= 0) return cudaSuccess;
+    mirror_kernel<<<n_tasks, dim3(32, 8), 0, st>>>(s, tasks);
     return cudaGetLastError();
 }
 
 cudaError_t launch_density_simt(const DevSystem &s, nao_precision prec, const DWork *work, int32_t w0, int32_t n_work,
-                                const double *scratch, const double *P, double *n, double *ne_part, cudaStream_t st) {
+                                const double *scratch, double *ne_part, cudaStream_t st) {
     if (n_work <= 0) return cudaSuccess;
     if (prec == NAO_FP32)
-        density_simt_kernel<float><<<n_work, 256, 0, st>>>(s, work, w0, reinterpret_cast<const float *>(scratch), P, n,
+        density_simt_kernel<float><<<n_work, 256, 0, st>>>(s, work, w0, reinterpret_cast<const float *>(scratch),
                                                           ne_part);
     else
-        density_simt_kernel<double><<<n_work, 256, 0, st>>>(s, work, w0, scratch, P, n, ne_part);
+        density_simt_kernel<double><<<n_work, 256, 0, st>>>(s, work, w0, scratch, ne_part);
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_sum(const double *part, int64_t n, double *out, cudaStream_t st) {
-    reduce_sum_kernel<<<1, 1024, 0, st>>>(part, n, out);
+cudaError_t launch_reduce_ne(const DevSystem &s, const double *part, const int32_t *sys_dw0, int32_t n_sys,
+                             cudaStream_t st) {
+    if (n_sys <= 0) return cudaSuccess;
+    reduce_ne_kernel<<<n_sys, 1024, 0, st>>>(s, part, sys_dw0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_n(const DevSystem &s, const DWork *work, int32_t n_work, cudaStream_t st) {
+    if (n_work <= 0) return cudaSuccess;
+    zero_n_kernel<<<n_work, 64, 0, st>>>(s, work);
     return cudaGetLastError();
 }

@@ -27,23 +27,25 @@ __host__ __device__ constexpr double double_factorial_odd(int m) { return m <= 1
 // nnz(B): min over each batch's points of |r - R_A|^2 per atom, every operation separately
 // rounded (the host then applies r2 < rc*rc per radial function). One warp per atom.
 // ----------------------------------------------------------------------------------------
-__global__ void minr2_kernel(const double *__restrict__ atom_xyz, int n_atoms, const double *__restrict__ px,
+__global__ void minr2_kernel(const double *__restrict__ atom_xyz, const int32_t *__restrict__ bmol,
+                             const int32_t *__restrict__ aoff, int max_atoms, const double *__restrict__ px,
                              const double *__restrict__ py, const double *__restrict__ pz,
                              const int32_t *__restrict__ boff, double *__restrict__ minr2) {
-    const int b = blockIdx.x;
+    const int b = blockIdx.x, m = bmol[b];
     const int p0 = boff[b], p1 = boff[b + 1];
+    const int a0 = aoff[m], na = aoff[m + 1] - a0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int a = warp; a < n_atoms; a += nwarp) {
-        const double ax = atom_xyz[3 * a], ay = atom_xyz[3 * a + 1], az = atom_xyz[3 * a + 2];
-        double m = __longlong_as_double(0x7ff0000000000000LL);  // +inf
+    for (int a = warp; a < na; a += nwarp) {
+        const double ax = atom_xyz[3 * (a0 + a)], ay = atom_xyz[3 * (a0 + a) + 1], az = atom_xyz[3 * (a0 + a) + 2];
+        double mn = __longlong_as_double(0x7ff0000000000000LL);  // +inf
         for (int p = p0 + lane; p < p1; p += 32) {
             const double dx = __dsub_rn(px[p], ax), dy = __dsub_rn(py[p], ay), dz = __dsub_rn(pz[p], az);
             const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-            m = fmin(m, r2);
+            mn = fmin(mn, r2);
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) minr2[(size_t)b * n_atoms + a] = m;
+        for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        if (lane == 0) minr2[(size_t)b * max_atoms + a] = mn;
     }
 }
 
@@ -278,11 +280,11 @@ __global__ void __launch_bounds__(256) eval_export_kernel(DevSystem s, int32_t b
 
 }  // namespace
 
-cudaError_t launch_relevance_minr2(const double *atom_xyz, int32_t n_atoms, const double *px, const double *py,
-                                   const double *pz, const int32_t *batch_off, int64_t n_batches, double *minr2,
-                                   cudaStream_t st) {
+cudaError_t launch_relevance_minr2(const double *atom_xyz, const int32_t *bmol, const int32_t *aoff, int32_t max_atoms,
+                                   const double *px, const double *py, const double *pz, const int32_t *batch_off,
+                                   int64_t n_batches, double *minr2, cudaStream_t st) {
     if (n_batches <= 0) return cudaSuccess;
-    minr2_kernel<<<(unsigned)n_batches, 256, 0, st>>>(atom_xyz, n_atoms, px, py, pz, batch_off, minr2);
+    minr2_kernel<<<(unsigned)n_batches, 256, 0, st>>>(atom_xyz, bmol, aoff, max_atoms, px, py, pz, batch_off, minr2);
     return cudaGetLastError();
 }
 

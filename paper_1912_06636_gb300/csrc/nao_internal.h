@@ -6,6 +6,7 @@
 
 #include <string>
 #include <type_traits>
+#include <map>
 #include <vector>
 
 #include "nao.h"
@@ -14,8 +15,7 @@
 #define NAO_TILE 64          // tile edge of the SIMT contractions (basis functions and points)
 #define NAO_PPAD 16          // batch points are padded to a multiple of this in scratch
 #define NAO_MAX_BATCH 1024   // largest accepted max_batch_points
-#define NAO_SPLIT_MAX_SLICES 10  // tensor-memory budget: 10 groups x 48 FP32 columns <= 512 columns
-#define NAO_SPLIT_TN 48          // split path: MMA N (B-tile rows)
+#define NAO_SPLIT_MAX_SLICES 12  // tensor-memory budget: S groups x TN FP32 columns <= 512 columns
 #define NAO_SPLIT_MAX_PPAD 512   // split path: padded batch points (4 Ppad S < 2^14 keeps sums exact)
 
 // One radial function instance relevant to a batch: atom, radial function, position of
@@ -28,6 +28,23 @@ struct RfnEntry {
 // by l; lmax is the largest l among them.
 struct AtomGroup {
     int32_t atom, r0, nr, lmax;
+};
+
+// Systems of a handle. A handle holds one or more systems (molecules); batches never mix
+// systems and every basis index, atom and point is global (systems concatenated). The
+// per-call pointer tables (H, v, P, n, N_e) are device arrays with one entry per system,
+// written before each call's kernels.
+struct SysTables {
+    const int32_t *bmol;     // [n_batches] system of each batch
+    const int32_t *boff;     // [n_sys] first global basis index of the system
+    const int32_t *nbm;      // [n_sys] basis size of the system
+    const int32_t *poff;     // [n_sys] first global point (caller's order) of the system
+    const int32_t *aoff;     // [n_sys + 1] atoms of the system
+    double *const *H;        // [n_sys] this call's H of each system (nbm x nbm)
+    const double *const *v;  // [n_sys] this call's v of each system (NULL entry: v = 1)
+    const double *const *P;  // [n_sys] this call's P of each system
+    double *const *n;        // [n_sys] this call's n of each system
+    double *const *ne;       // [n_sys] this call's N_e of each system (NULL entry: not formed)
 };
 
 // Geometry and tables shared by every kernel (device pointers).
@@ -49,34 +66,65 @@ struct DevSystem {
     const int64_t *scr_off;   // [n_batches] element offset of the batch's block in scratch
     int32_t n_rgrid;
     double r0, inv_delta;
-    int64_t nb;
+    int64_t nb;               // total basis size over all systems
+    SysTables sys;
     double knorm[NAO_LMAX + 1][NAO_LMAX + 1];  // sqrt((2l+1)/(4pi) (l-m)!/(l+m)!) (x sqrt2 for m>0)
 };
 
+#ifdef __CUDACC__
+// Element (i, j) of the H of system m (i, j global basis indices of that system).
+__device__ __forceinline__ double *h_elem(const DevSystem &s, int m, int64_t gi, int64_t gj) {
+    const int64_t bo = s.sys.boff[m];
+    return s.sys.H[m] + (gi - bo) * (int64_t)s.sys.nbm[m] + (gj - bo);
+}
+__device__ __forceinline__ double p_elem(const DevSystem &s, int m, int64_t gi, int64_t gj) {
+    const int64_t bo = s.sys.boff[m];
+    return s.sys.P[m][(gi - bo) * (int64_t)s.sys.nbm[m] + (gj - bo)];
+}
+// v at batch-ordered point p of system m (1 when the system has no v this call).
+__device__ __forceinline__ double v_at(const DevSystem &s, int m, int p) {
+    const double *v = s.sys.v[m];
+    return v ? v[s.perm[p] - s.sys.poff[m]] : 1.0;
+}
+__device__ __forceinline__ double *n_at(const DevSystem &s, int m, int p) {
+    return s.sys.n[m] + (s.perm[p] - s.sys.poff[m]);
+}
+#endif
+
 // Geometry of one batch's operand slices on the split path (shared by host and device code).
-// H: one digit set; per (slice, K chunk of 64) a row-contiguous block of R_pad rows x 128 B
-//    (128-byte swizzle inside 8-row atoms), so a 128-row A tile and a 48-row B tile are plain
-//    byte ranges. K holds the 4 Ppad weighted columns reordered so that negative-weight
-//    columns come first, padded to a multiple of 16 (the MMA negates B on those K steps).
-// Density: A rows (points) in 128-row blocks, K = basis in chunks of 64; B rows (basis) in
-//    48-row blocks. One block = rows x 64 bf16, 128 B per row.
+// Every operand is stored row-contiguous per (slice, K chunk of 64): rows x 128 B with the
+// 128-byte swizzle inside 8-row atoms, rows rounded up to 16 only. An MMA tile (128 rows for
+// A, TN for B) is a plain byte range; the last tile of an operand is copied short and its
+// remaining shared-memory rows keep stale data, which only reaches output rows and columns
+// beyond N (or P) that the epilogues discard. B tiles are TN = nao_split_tn(S) rows.
+// H: one digit set, rows = basis functions, K = the 4 Ppad weighted columns reordered so that
+//    negative-weight columns come first, padded to a multiple of 16 (B negated on those steps).
+// Density: A rows = points, K = basis; B rows = basis (P' rows), K = basis.
+// MMA N (rows of a B tile) of the split path with S slices: each of the S slice groups holds
+// its own TN FP32 accumulator columns of the 512 tensor-memory columns.
+__host__ __device__ constexpr int nao_split_tn(int S) { return S <= 10 ? 48 : 32; }
+
 struct SplitGeom {
-    int n_kc, R_pad;             // H: K chunks, padded rows
-    int n_kcN, n_qt, n_jtN;      // density: K chunks, A 128-point blocks, B 48-row blocks
-    __host__ __device__ SplitGeom(int P, int N) {
+    int n_kc, R16;               // H: K chunks, stored rows
+    int n_kcN, P16, n_qt, n_jtN; // density: K chunks, stored A rows, 128-point tiles, TN-row B tiles
+    __host__ __device__ SplitGeom(int P, int N, int S) {
         const int Ppad = (P + NAO_PPAD - 1) / NAO_PPAD * NAO_PPAD;
         n_kc = (4 * Ppad + 16 + 63) / 64;
-        const int ra = 128 * ((N + 127) / 128), rb = NAO_SPLIT_TN * ((N + NAO_SPLIT_TN - 1) / NAO_SPLIT_TN);
-        R_pad = ra > rb ? ra : rb;
+        R16 = (N + 15) / 16 * 16;
         n_kcN = (N + 63) / 64;
+        P16 = (P + 15) / 16 * 16;
         n_qt = (P + 127) / 128;
-        n_jtN = (N + NAO_SPLIT_TN - 1) / NAO_SPLIT_TN;
+        n_jtN = (N + nao_split_tn(S) - 1) / nao_split_tn(S);
     }
-    __host__ __device__ size_t h_block(int s, int kc) const { return ((size_t)s * n_kc + kc) * (size_t)R_pad * 128; }
-    __host__ __device__ size_t h_bytes(int S) const { return (size_t)S * n_kc * (size_t)R_pad * 128; }
-    __host__ __device__ int h_slice_tiles() const { return R_pad / 64 + (R_pad % 64 ? 1 : 0); }
-    __host__ __device__ size_t n_setA(int S) const { return (size_t)S * n_kcN * n_qt * 16384; }
-    __host__ __device__ size_t n_bytes(int S) const { return n_setA(S) + (size_t)S * n_kcN * n_jtN * (NAO_SPLIT_TN * 128); }
+    __host__ __device__ size_t h_block(int s, int kc) const { return ((size_t)s * n_kc + kc) * (size_t)R16 * 128; }
+    __host__ __device__ size_t h_bytes(int S) const { return (size_t)S * n_kc * (size_t)R16 * 128; }
+    __host__ __device__ int h_slice_tiles() const { return (R16 + 63) / 64; }
+    __host__ __device__ size_t nA_block(int s, int kc) const { return ((size_t)s * n_kcN + kc) * (size_t)P16 * 128; }
+    __host__ __device__ size_t n_setA(int S) const { return (size_t)S * n_kcN * (size_t)P16 * 128; }
+    __host__ __device__ size_t nB_block(int S, int s, int kc) const {
+        return n_setA(S) + ((size_t)s * n_kcN + kc) * (size_t)R16 * 128;
+    }
+    __host__ __device__ size_t n_bytes(int S) const { return n_setA(S) + (size_t)S * n_kcN * (size_t)R16 * 128; }
 };
 
 struct HWork {  // one upper-triangular tile pair of one batch's h[B] (Eq. batch_matrix_mult)
@@ -116,6 +164,16 @@ struct nao_grid {
     double *d_scratch = nullptr;
     double *d_ne_part = nullptr;    // [n_dwork] per-tile sums of w n
     int32_t *d_err = nullptr;       // device error word
+    // systems (molecules) of the handle
+    int32_t n_sys = 1;
+    std::vector<int32_t> sys_boff, sys_nb, sys_poff, sys_np, sys_aoff;
+    std::vector<int32_t> sys_dw0;      // [n_sys + 1] density work items of each system
+    std::vector<int4> zero_tasks;      // (system, start element, count, 0) chunks of each H
+    std::vector<int4> mirror_tasks;    // (system, column tile, row tile, 0) with row <= column
+    int4 *d_zero_tasks = nullptr, *d_mirror_tasks = nullptr;
+    int32_t *d_sys_dw0 = nullptr;
+    double **d_tab = nullptr;          // device: [5][n_sys] pointer tables H, v, P, n, N_e
+    std::vector<void *> h_tab;         // host copy of the tables
     // split (tensor-core) path, set up on its first use
     struct SplitChunk {
         int32_t b0, b1;    // batches (inside one chunk of the evaluation scratch)
@@ -143,40 +201,52 @@ struct nao_grid {
     nao_profile prof{};
     // staging for the host-buffer entry points (allocated on first use)
     double *d_stage_in = nullptr, *d_stage_out = nullptr, *d_stage_ne = nullptr;
+    // CUDA graphs (options.capture_graph): one executable graph per (operation, precision,
+    // terms), replayed on the handle's own stream between two events
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    std::map<uint64_t, cudaGraphExec_t> graphs;
 };
 
 // ---- launchers (eval.cu, contract_simt.cu) ----------------------------------------------
-cudaError_t launch_relevance_minr2(const double *atom_xyz, int32_t n_atoms, const double *px, const double *py,
-                                   const double *pz, const int32_t *batch_off, int64_t n_batches, double *minr2,
-                                   cudaStream_t st);
+// minr2[b * max_atoms + a]: min over batch b's points of |r - R_A|^2 for the a-th atom of b's
+// system (atoms aoff[m] .. aoff[m+1]-1).
+cudaError_t launch_relevance_minr2(const double *atom_xyz, const int32_t *bmol, const int32_t *aoff, int32_t max_atoms,
+                                   const double *px, const double *py, const double *pz, const int32_t *batch_off,
+                                   int64_t n_batches, double *minr2, cudaStream_t st);
 cudaError_t launch_eval(const DevSystem &s, int32_t b0, int32_t b1, nao_precision prec, bool grad, double *scratch,
                         cudaStream_t st);
 cudaError_t launch_eval_one(const DevSystem &s, int32_t b, nao_precision prec, double *phi, double *grad,
                             cudaStream_t st);
 cudaError_t launch_h_simt(const DevSystem &s, nao_precision prec, const HWork *work, int32_t n_work,
-                          const double *scratch, const double *v, uint32_t terms, double *H, cudaStream_t st);
-cudaError_t launch_mirror(double *H, int64_t nb, cudaStream_t st);
+                          const double *scratch, uint32_t terms, cudaStream_t st);
+cudaError_t launch_zero_h(const DevSystem &s, const int4 *tasks, int32_t n_tasks, cudaStream_t st);
+cudaError_t launch_mirror(const DevSystem &s, const int4 *tasks, int32_t n_tasks, cudaStream_t st);
 cudaError_t launch_density_simt(const DevSystem &s, nao_precision prec, const DWork *work, int32_t w0, int32_t n_work,
-                                const double *scratch, const double *P, double *n, double *ne_part, cudaStream_t st);
-cudaError_t launch_reduce_sum(const double *part, int64_t n, double *out, cudaStream_t st);
+                                const double *scratch, double *ne_part, cudaStream_t st);
+// N_e of every system: sum of its density work items' partial sums (deterministic order)
+cudaError_t launch_reduce_ne(const DevSystem &s, const double *part, const int32_t *sys_dw0, int32_t n_sys,
+                             cudaStream_t st);
+// n = 0 at every point of the given density work items
+cudaError_t launch_zero_n(const DevSystem &s, const DWork *work, int32_t n_work, cudaStream_t st);
 
 // ---- split path (split_tc.cu) ------------------------------------------------------------
 size_t split_smem_bytes(int S);
 cudaError_t split_configure();
 cudaError_t launch_slice_h(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_rt, const double *scratch,
-                           const double *v, uint32_t terms, uint8_t *slices, const int64_t *sl_off, int32_t *expo,
-                           int32_t *neg16, int S, cudaStream_t st);
+                           uint32_t terms, uint8_t *slices, const int64_t *sl_off, int32_t *expo, int32_t *neg16, int S,
+                           cudaStream_t st);
 cudaError_t launch_h_tc(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
-                        const int64_t *sl_off, const int32_t *expo, const int32_t *neg16, int S, double *H, int32_t *err,
+                        const int64_t *sl_off, const int32_t *expo, const int32_t *neg16, int S, int32_t *err,
                         cudaStream_t st);
 cudaError_t launch_slice_n(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_qt, const double *scratch,
-                           const double *P, uint8_t *slices, const int64_t *sl_off, int32_t *expo_q, int32_t *expo_b,
-                           int S, cudaStream_t st);
+                           uint8_t *slices, const int64_t *sl_off, int32_t *expo_q, int32_t *expo_b, int S,
+                           cudaStream_t st);
 cudaError_t launch_n_tc(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
                         const int64_t *sl_off, const int32_t *expo_q, const int32_t *expo_b, const double *scratch, int S,
-                        double *n, int32_t *err, cudaStream_t st);
-cudaError_t launch_wn_partial(const DevSystem &s, const DWork *work, int32_t w0, int32_t n_work, const double *n,
-                              double *ne_part, cudaStream_t st);
+                        int32_t *err, cudaStream_t st);
+cudaError_t launch_wn_partial(const DevSystem &s, const DWork *work, int32_t w0, int32_t n_work, double *ne_part,
+                              cudaStream_t st);
 
 // Records the text nao_last_error() returns on the calling thread (api.cpp).
 void nao_set_last_error(const std::string &msg);

@@ -15,6 +15,8 @@
 //   - all calls on a device share the one array and it keeps the last call's contents:
 //     the evaluation kernel writes every entry the contraction later reads (padding
 //     included), so nothing has to be cleared; H_dev is zeroed by the call itself;
+//   - the call writes the handle's device pointer table (H, v) from host memory the handle
+//     owns, like every other call on the handle;
 //   - calls whose work overlaps on the GPU (other streams, other handles) race on the array;
 //   - the first call on a device looks up the array's device address (cudaGetSymbolAddress,
 //     with that device current); make that first call before any stream capture.
@@ -60,6 +62,7 @@ nao_status noalloc_address(int dev, double **out) {
 extern "C" nao_status nao_integrate_h_noalloc(nao_grid *g, const double *v_dev, uint32_t terms, double *H_dev,
                                               void *cuda_stream) {
     if (!g) return noalloc_fail(NAO_ERR_INVALID_ARG, "handle is NULL");
+    if (g->n_sys != 1) return noalloc_fail(NAO_ERR_INVALID_ARG, "the handle holds more than one system");
     if (!H_dev) return noalloc_fail(NAO_ERR_INVALID_ARG, "H_dev is NULL");
     if (terms == 0 || (terms & ~3u)) return noalloc_fail(NAO_ERR_INVALID_ARG, "bad terms");
     if ((uint64_t)g->scratch_elems > (uint64_t)kNoallocDoubles)
@@ -75,14 +78,23 @@ extern "C" nao_status nao_integrate_h_noalloc(nao_grid *g, const double *v_dev, 
     nao_status st = noalloc_address(g->device, &scratch);
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = cudaSuccess;
-    if (st == NAO_OK) e = cudaMemsetAsync(H_dev, 0, (size_t)g->nb * g->nb * sizeof(double), s);
+    if (st == NAO_OK) {
+        // this call's H and v pointers, in the handle's pointer table (copied from host memory
+        // the handle owns; a pageable-source copy, no allocation)
+        const size_t n = (size_t)g->n_sys;
+        g->h_tab[0] = H_dev;
+        g->h_tab[n] = const_cast<double *>(v_dev);
+        e = cudaMemcpyAsync(g->d_tab, g->h_tab.data(), 2 * n * sizeof(void *), cudaMemcpyHostToDevice, s);
+    }
+    if (st == NAO_OK && e == cudaSuccess) e = launch_zero_h(g->sys, g->d_zero_tasks, (int32_t)g->zero_tasks.size(), s);
     for (size_t c = 0; st == NAO_OK && e == cudaSuccess && c < g->chunks.size(); c++) {
         const Chunk &ch = g->chunks[c];
         e = launch_eval(g->sys, ch.b0, ch.b1, NAO_FP64, true, scratch, s);
         if (e == cudaSuccess)
-            e = launch_h_simt(g->sys, NAO_FP64, g->d_hwork + ch.hw0, ch.hw1 - ch.hw0, scratch, v_dev, terms, H_dev, s);
+            e = launch_h_simt(g->sys, NAO_FP64, g->d_hwork + ch.hw0, ch.hw1 - ch.hw0, scratch, terms, s);
     }
-    if (st == NAO_OK && e == cudaSuccess) e = launch_mirror(H_dev, g->nb, s);
+    if (st == NAO_OK && e == cudaSuccess)
+        e = launch_mirror(g->sys, g->d_mirror_tasks, (int32_t)g->mirror_tasks.size(), s);
     if (prev >= 0 && prev != g->device) cudaSetDevice(prev);
     if (st != NAO_OK) return st;
     if (e != cudaSuccess) return noalloc_fail(NAO_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));

@@ -32,6 +32,7 @@ SYMBOLS = [
     "nao_integrate_h", "nao_update_density", "nao_integrate_h_host", "nao_update_density_host",
     "nao_evaluate_batch", "nao_sync_status", "nao_status_string", "nao_last_error",
     "nao_profile_enable", "nao_profile_read", "nao_integrate_h_noalloc",
+    "nao_grid_create_many", "nao_get_system", "nao_integrate_h_many", "nao_update_density_many",
 ]
 NAO_NOALLOC_SCRATCH_BYTES = 32 << 20
 KERNELS = ["eval_grad", "eval_phi", "h_fp64", "h_fp32", "h_split", "slice", "mirror", "n_fp64", "n_fp32",
@@ -56,7 +57,8 @@ class SystemDesc(C.Structure):
 class Options(C.Structure):
     _fields_ = [
         ("max_batch_points", C.c_int32), ("split_slices", C.c_int32), ("deterministic", C.c_int32),
-        ("device", C.c_int32), ("scratch_bytes", C.c_int64),
+        ("device", C.c_int32), ("scratch_bytes", C.c_int64), ("capture_graph", C.c_int32),
+        ("reserved0", C.c_int32),
     ]
 
 
@@ -68,7 +70,7 @@ class GridInfo(C.Structure):
     _fields_ = [
         ("n_basis", C.c_int64), ("n_points", C.c_int64), ("n_batches", C.c_int64), ("rel_total", C.c_int64),
         ("max_batch_points", C.c_int32), ("max_batch_basis", C.c_int32), ("device_bytes", C.c_int64),
-        ("flops_h", C.c_int64), ("flops_n", C.c_int64),
+        ("flops_h", C.c_int64), ("flops_n", C.c_int64), ("n_systems", C.c_int32), ("reserved0", C.c_int32),
     ]
 
 
@@ -102,6 +104,10 @@ def load():
         "nao_profile_enable": ([P, I32], C.c_int),
         "nao_profile_read": ([P, P, I32], C.c_int),
         "nao_integrate_h_noalloc": ([P, P, U32, P, P], C.c_int),
+        "nao_grid_create_many": ([P, I32, P, P], C.c_int),
+        "nao_get_system": ([P, I32, P, P, P, P, P, P], C.c_int),
+        "nao_integrate_h_many": ([P, P, U32, C.c_int, P, P], C.c_int),
+        "nao_update_density_many": ([P, P, C.c_int, P, P, P], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -147,10 +153,9 @@ def nao_default_options() -> Options:
     return o
 
 
-def nao_grid_create(system, options: Options | None = None, **opts) -> C.c_void_p:
-    """Create a handle from a system (any object with the fields of nao_system_desc)."""
-    lib = load()
-    keep = {
+def _desc(system, keep: list) -> SystemDesc:
+    """nao_system_desc of a system (any object with its fields); arrays kept alive in keep."""
+    a = {
         "atom_xyz": np.ascontiguousarray(system.atom_xyz, dtype=np.float64),
         "atom_species": np.ascontiguousarray(system.atom_species, dtype=np.int32),
         "species_fn_offset": np.ascontiguousarray(system.species_fn_offset, dtype=np.int32),
@@ -160,18 +165,59 @@ def nao_grid_create(system, options: Options | None = None, **opts) -> C.c_void_
         "pt_xyz": np.ascontiguousarray(system.pt_xyz, dtype=np.float64),
         "pt_w": np.ascontiguousarray(system.pt_w, dtype=np.float64),
     }
-    d = SystemDesc(
-        int(keep["atom_xyz"].size // 3), keep["atom_xyz"].ctypes.data, keep["atom_species"].ctypes.data,
-        int(keep["species_fn_offset"].size - 1), keep["species_fn_offset"].ctypes.data, keep["fn_l"].ctypes.data,
-        keep["fn_cutoff"].ctypes.data, int(system.n_rgrid), float(system.r0), float(system.r_last),
-        keep["fn_table"].ctypes.data, int(keep["pt_w"].size), keep["pt_xyz"].ctypes.data, keep["pt_w"].ctypes.data,
+    keep.append(a)
+    return SystemDesc(
+        int(a["atom_xyz"].size // 3), a["atom_xyz"].ctypes.data, a["atom_species"].ctypes.data,
+        int(a["species_fn_offset"].size - 1), a["species_fn_offset"].ctypes.data, a["fn_l"].ctypes.data,
+        a["fn_cutoff"].ctypes.data, int(system.n_rgrid), float(system.r0), float(system.r_last),
+        a["fn_table"].ctypes.data, int(a["pt_w"].size), a["pt_xyz"].ctypes.data, a["pt_w"].ctypes.data,
     )
+
+
+def _options(options: Options | None, opts: dict) -> Options:
     o = options if options is not None else nao_default_options()
     for k, v in opts.items():
         setattr(o, k, v)
+    return o
+
+
+def nao_grid_create(system, options: Options | None = None, **opts) -> C.c_void_p:
+    """Create a handle from a system (any object with the fields of nao_system_desc)."""
+    keep: list = []
+    d = _desc(system, keep)
+    o = _options(options, opts)
     h = C.c_void_p()
-    _check(lib.nao_grid_create(C.byref(d), C.byref(o), C.byref(h)), "nao_grid_create")
+    _check(load().nao_grid_create(C.byref(d), C.byref(o), C.byref(h)), "nao_grid_create")
     return h
+
+
+def nao_grid_create_many(systems, options: Options | None = None, **opts) -> C.c_void_p:
+    """One handle over several systems that share the radial grid."""
+    keep: list = []
+    arr = (SystemDesc * len(systems))(*[_desc(s, keep) for s in systems])
+    o = _options(options, opts)
+    h = C.c_void_p()
+    _check(load().nao_grid_create_many(arr, len(systems), C.byref(o), C.byref(h)), "nao_grid_create_many")
+    return h
+
+
+def nao_get_system(h, m: int) -> dict:
+    v = [C.c_int64() for _ in range(6)]
+    _check(load().nao_get_system(h, int(m), *[C.byref(x) for x in v]), "nao_get_system")
+    keys = ("basis_offset", "n_basis", "point_offset", "n_points", "batch_begin", "batch_end")
+    return {k: int(x.value) for k, x in zip(keys, v)}
+
+
+def _ptr_array(ts, allow_none: bool):
+    """Host array of device pointers (None entries allowed where the call allows them)."""
+    if ts is None:
+        return None
+    vals = []
+    for t in ts:
+        if t is None and not allow_none:
+            raise ValueError("a required tensor is None")
+        vals.append(_dptr(t))
+    return (C.c_void_p * len(vals))(*vals)
 
 
 def nao_destroy(h) -> None:
@@ -202,6 +248,16 @@ def nao_integrate_h(h, v, terms: int, prec, H, stream=None) -> None:
 def nao_update_density(h, P, prec, n, ne=None, stream=None) -> None:
     _check(load().nao_update_density(h, _dptr(P), _prec(prec), _dptr(n), _dptr(ne), _stream(stream)),
            "nao_update_density")
+
+
+def nao_integrate_h_many(h, vs, terms: int, prec, Hs, stream=None) -> None:
+    _check(load().nao_integrate_h_many(h, _ptr_array(vs, True), int(terms), _prec(prec), _ptr_array(Hs, False),
+                                       _stream(stream)), "nao_integrate_h_many")
+
+
+def nao_update_density_many(h, Ps, prec, ns, nes=None, stream=None) -> None:
+    _check(load().nao_update_density_many(h, _ptr_array(Ps, False), _prec(prec), _ptr_array(ns, False),
+                                          _ptr_array(nes, True), _stream(stream)), "nao_update_density_many")
 
 
 def nao_integrate_h_host(h, v: np.ndarray | None, terms: int, prec, H: np.ndarray, stream=None) -> None:
@@ -258,7 +314,10 @@ class _Sizes:
 
 
 class Grid:
-    """Owns one nao_grid handle; allocates outputs as torch tensors on the handle's device."""
+    """Owns one nao_grid handle; allocates outputs as torch tensors on the handle's device.
+
+    ``system`` is one system, or a list of systems for a grouped handle (nao_grid_create_many);
+    the grouped handle's per-system calls are integrate_h_many / update_density_many."""
 
     def __init__(self, system, device: int | None = None, **opts):
         import torch
@@ -267,10 +326,16 @@ class Grid:
             device = torch.cuda.current_device()
         self.device = torch.device("cuda", device)
         with torch.cuda.device(self.device):
-            self.h = nao_grid_create(system, device=device, **opts)
+            if isinstance(system, (list, tuple)):
+                self.h = nao_grid_create_many(list(system), device=device, **opts)
+            else:
+                self.h = nao_grid_create(system, device=device, **opts)
         self.info = nao_get_info(self.h)
+        self.split_slices = int(opts.get("split_slices", nao_default_options().split_slices))
         self.nb = int(self.info.n_basis)
         self.n_points = int(self.info.n_points)
+        self.n_systems = int(self.info.n_systems)
+        self.systems = [nao_get_system(self.h, m) for m in range(self.n_systems)]
 
     def close(self):
         if getattr(self, "h", None):
@@ -309,6 +374,26 @@ class Grid:
             ne = torch.empty(1, dtype=torch.float64, device=self.device)
         nao_update_density(self.h, P, prec, n, ne, stream)
         return n, ne
+
+    def integrate_h_many(self, vs=None, terms=NAO_TERM_POTENTIAL | NAO_TERM_KINETIC, prec="fp64", Hs=None,
+                         stream=None):
+        import torch
+
+        if Hs is None:
+            Hs = [torch.empty((s["n_basis"], s["n_basis"]), dtype=torch.float64, device=self.device)
+                  for s in self.systems]
+        nao_integrate_h_many(self.h, vs, terms, prec, Hs, stream)
+        return Hs
+
+    def update_density_many(self, Ps, prec="fp64", ns=None, nes=None, stream=None, want_ne=True):
+        import torch
+
+        if ns is None:
+            ns = [torch.empty(s["n_points"], dtype=torch.float64, device=self.device) for s in self.systems]
+        if nes is None and want_ne:
+            nes = [torch.empty(1, dtype=torch.float64, device=self.device) for _ in self.systems]
+        nao_update_density_many(self.h, Ps, prec, ns, nes, stream)
+        return ns, nes
 
     def evaluate_batch(self, b: int, prec="fp64", grad=True, stream=None):
         import torch

@@ -31,7 +31,8 @@ def test_status_strings_and_defaults():
     assert nao.nao_status_string(0) == "ok"
     assert nao.nao_status_string(1) == "invalid argument"
     o = nao.nao_default_options()
-    assert o.max_batch_points == 200 and o.split_slices == 10 and o.device == -1
+    assert o.max_batch_points == 200 and o.split_slices == 12 and o.device == -1
+    assert o.capture_graph == 0 and o.reserved0 == 0
 
 
 def _bad(sys_, **opts):
@@ -60,6 +61,24 @@ def test_invalid_input_is_rejected_without_gpu():
     assert _bad(s, max_batch_points=0) == 1
     assert _bad(s, max_batch_points=5000) == 1
     assert _bad(s, split_slices=2) == 1
+    assert _bad(s, split_slices=13) == 1
+    assert _bad(s, capture_graph=2) == 1
+    assert _bad(s, reserved0=1) == 1
+
+
+def test_grouped_create_rejects_bad_input_without_gpu():
+    s = synth.config_water(n_rad=4, n_theta=2, n_phi=3)
+    bad = synth.System(**{**s.__dict__})
+    bad.fn_l = s.fn_l.copy()
+    bad.fn_l[0] = 7
+    with pytest.raises(nao.NaoError) as e:
+        nao.nao_grid_create_many([s, bad])
+    assert e.value.code == 1 and "system 1" in str(e.value)
+    lib = nao.load()
+    out = C.c_void_p(123)
+    assert lib.nao_grid_create_many(None, 2, None, C.byref(out)) == 1 and out.value is None
+    arr = (nao.SystemDesc * 1)()
+    assert lib.nao_grid_create_many(arr, 0, None, C.byref(out)) == 1
 
 
 def test_null_handle_calls_fail_cleanly():
@@ -67,6 +86,9 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.nao_destroy(None) == 0
     assert lib.nao_integrate_h(None, None, 3, 0, None, None) == 1
     assert lib.nao_update_density(None, None, 0, None, None, None) == 1
+    assert lib.nao_integrate_h_many(None, None, 3, 0, None, None) == 1
+    assert lib.nao_update_density_many(None, None, 0, None, None, None) == 1
+    assert lib.nao_get_system(None, 0, None, None, None, None, None, None) == 1
     info = nao.GridInfo()
     assert lib.nao_get_info(None, C.byref(info)) == 1
     out = C.c_void_p(123)

@@ -15,6 +15,8 @@ from tests._metrics import rel_err
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-12, "fp32": 1e-6, "split": 1e-10}
+# the split path with the library's default slices, and with the 10 slices bench.py times
+SPLIT_SLICES = {"split": None, "split10": 10}
 # sampled basis functions: several atoms (neighbours and far-apart pairs), every l
 SAMPLE_F = np.array([0, 3, 9, 18, 24, 25 * 1 + 2, 25 * 5 + 13, 25 * 8 + 21, 25 * 27 + 6, 25 * 40 + 11,
                      25 * 58 + 19, 25 * 63 + 24])
@@ -48,14 +50,20 @@ def test_partition_and_relevance_bit_exact_fullsize(diamond):
     assert np.array_equal(ro, oro) and np.array_equal(ri, ori)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "split"])
-def test_fullsize_sampled(diamond, prec):
+@pytest.mark.parametrize("case", ["fp64", "fp32", "split", "split10"])
+def test_fullsize_sampled(diamond, case):
     g, s = diamond["g"], diamond["s"]
+    prec = "split" if case.startswith("split") else case
+    own = None
+    if SPLIT_SLICES.get(case) is not None:
+        own = g = nao.Grid(s, device=0, max_batch_points=s.max_batch_points, split_slices=SPLIT_SLICES[case])
     H = g.integrate_h(cuda(diamond["v"]), prec=prec)
     n, ne = g.update_density(cuda(diamond["P"]), prec=prec)
     S = g.overlap(prec=prec)
     torch.cuda.synchronize()
     g.sync()
+    if own is not None:
+        own.close()
     Hc = H.cpu().numpy()
     assert np.array_equal(Hc, Hc.T)
     F = SAMPLE_F
@@ -66,6 +74,6 @@ def test_fullsize_sampled(diamond, prec):
     e_n = rel_err(nc[diamond["pidx"]], diamond["n_s"], diamond["D_s"])
     # tr(PS) = sum_p w_p n_p holds for the GPU's own S and n (same discrete sum)
     trPS = float(torch.sum(cuda(diamond["P"]) * S).item())
-    print(f"{prec}: e_H(sampled)={e_H:.2e} e_n(sampled)={e_n:.2e} N_e={float(ne.item()):.10f} tr(PS)={trPS:.10f}")
+    print(f"{case}: e_H(sampled)={e_H:.2e} e_n(sampled)={e_n:.2e} N_e={float(ne.item()):.10f} tr(PS)={trPS:.10f}")
     assert e_H <= TOL[prec] and e_n <= TOL[prec]
     assert abs(float(ne.item()) - trPS) <= 10 * TOL[prec] * abs(trPS)

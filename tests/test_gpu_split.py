@@ -61,23 +61,27 @@ def test_split_overlap_and_kinetic(water):
 
 def test_split_error_falls_with_slices(water):
     errs = []
-    for S in (4, 6, 8, 10):
+    for S in (4, 6, 8, 10, 11, 12):
         H, n, _ = run(water, split_slices=S)
         errs.append((rel_err(H, water["H"], water["A"]), rel_err(n, water["n"], water["D"])))
-    print("split errors by slices 4,6,8,10:", errs)
+    print("split errors by slices 4,6,8,10,11,12:", errs)
     assert errs[0][0] > errs[2][0] and errs[0][1] > errs[2][1]
-    assert errs[3][0] <= TOL and errs[3][1] <= TOL
+    for e in errs[3:]:
+        assert e[0] <= TOL and e[1] <= TOL
 
 
-@pytest.mark.parametrize("B", [1, 37, 128, 400])
-def test_split_independent_of_batch_size(water, B):
-    H, n, _ = run(water, max_batch_points=B)
+# Exact slice sums need 4 Ppad S < 2^14 (Ppad = batch points rounded up to 16): batches of up
+# to 336 points at 12 slices, 400 at 10.
+@pytest.mark.parametrize("B,S", [(1, 12), (37, 12), (128, 12), (336, 12), (400, 10)])
+def test_split_independent_of_batch_size(water, B, S):
+    H, n, _ = run(water, max_batch_points=B, split_slices=S)
     assert rel_err(H, water["H"], water["A"]) <= TOL
     assert rel_err(n, water["n"], water["D"]) <= TOL
 
 
-def test_split_rejects_batches_too_large_for_exact_sums(water):
-    with nao.Grid(water["s"], device=0, max_batch_points=1024) as g:
+@pytest.mark.parametrize("B,S", [(1024, 10), (400, 12)])
+def test_split_rejects_batches_too_large_for_exact_sums(water, B, S):
+    with nao.Grid(water["s"], device=0, max_batch_points=B, split_slices=S) as g:
         with pytest.raises(nao.NaoError) as e:
             g.integrate_h(cuda(water["v"]), prec="split")
         assert e.value.code == nao.NAO_ERR_UNSUPPORTED
