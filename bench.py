@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other precisions")
+    ap.add_argument("--serve-requests", type=int, default=16,
+                    help="requests of the serving stream (Poisson arrivals at 200/s, 3-200 atoms)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving stream")
     return ap.parse_args()
 
 
@@ -127,6 +130,35 @@ def alu_peak(kind: str):
     except Exception:
         pass
     return ({"fp64": 1.25, "fp32": 80.0}[kind], "nominal")
+
+
+SERVE_GRID = dict(n_rad=30, n_theta=8, n_phi=9)
+
+
+def serving(n_requests: int, device: int) -> dict:
+    """The request stream through the continuous-batching loop, split path then FP64 path."""
+    from paper_1912_06636_gb300 import serve, synth
+
+    stream = synth.serving_stream(n_requests, rate=200.0, seed=4, n_min=3, n_max=200)
+    t0 = time.perf_counter()
+    reqs = []
+    for rid, (t, na, seed) in enumerate(stream):
+        s = synth.random_molecule(na, seed, **SERVE_GRID)
+        reqs.append(serve.Request(rid=rid, system=s, v0=s.potential(), arrival_s=t, n_iter=20, seed=seed))
+    gen_s = time.perf_counter() - t0
+    out = {"workload": f"{n_requests} requests, Poisson arrivals at 200/s (seed 4), molecules of 3-200 atoms "
+                       f"(log-uniform; species Si/A/B), {SERVE_GRID['n_rad']}x{SERVE_GRID['n_theta'] * SERVE_GRID['n_phi']} "
+                       "points per atom, batches <= 200 points, 20 iterations each (v perturbed 1%, fresh P), "
+                       "HBM budget 150 GB, 16 slots, CUDA graphs",
+           "atoms": [int(na) for _, na, _ in stream], "points": [int(len(r.v0)) for r in reqs],
+           "generate_s": gen_s}
+    for prec in ("split", "fp64"):
+        srv = serve.Server(prec=prec, hbm_budget_bytes=150 << 30, max_active=16, device=device)
+        res = srv.run(reqs)
+        out[prec] = serve.summarize(res, srv.stats)
+    if out["split"]["p99_ms"] and out["fp64"]["p99_ms"]:
+        out["p99_speedup_vs_fp64"] = out["fp64"]["p99_ms"] / out["split"]["p99_ms"]
+    return out
 
 
 def g_split_pairs(g) -> int:
@@ -357,9 +389,14 @@ def main():
                 other[f"split_{d}_slices"] = {"unavailable": str(e)}
         line["other_precisions"] = other
 
+    if rank == 0 and world == 1 and not args.no_serve and args.serve_requests > 0:
+        g.close()
+        line["serving"] = serving(args.serve_requests, local_rank)
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(s, v_np, P_np, args.cpu_sample)
-    g.close()
+    if g.h:
+        g.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -3,6 +3,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -41,14 +43,52 @@ struct DeviceGuard {
     }
 };
 
+// One memory pool per device for every handle's device memory. Stream-ordered allocation
+// from it (cudaMallocFromPoolAsync / cudaFreeAsync on a handle's setup stream) neither waits
+// for nor stalls work that other handles have in flight on other streams, which a serving loop
+// that creates and destroys handles between other requests' launches relies on. The pool keeps
+// freed memory for reuse while handles live; it is trimmed when the device's last handle goes.
+struct PoolState {
+    std::mutex mu;
+    std::map<int, cudaMemPool_t> pool;
+    std::map<int, int> live;
+};
+PoolState &pools() {
+    static PoolState *p = new PoolState();  // never destroyed: handles may outlive static teardown
+    return *p;
+}
+
+nao_status device_pool(int dev, cudaMemPool_t *out) {
+    PoolState &P = pools();
+    std::lock_guard<std::mutex> lock(P.mu);
+    auto it = P.pool.find(dev);
+    if (it == P.pool.end()) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        NAO_CUDA(cudaMemPoolCreate(&pool, &props));
+        uint64_t keep = ~uint64_t(0);
+        NAO_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        it = P.pool.emplace(dev, pool).first;
+    }
+    *out = it->second;
+    return NAO_OK;
+}
+
 template <class T>
 nao_status dev_alloc(nao_grid *g, T **p, size_t count) {
     void *q = nullptr;
     const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
-    const cudaError_t e = cudaMalloc(&q, bytes);
+    cudaMemPool_t pool;
+    nao_status st = device_pool(g->device, &pool);
+    if (st) return st;
+    const cudaError_t e = cudaMallocFromPoolAsync(&q, bytes, pool, g->setup);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return fail(NAO_ERR_OUT_OF_MEMORY, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+        return fail(NAO_ERR_OUT_OF_MEMORY, "device allocation of " + std::to_string(bytes) + " bytes failed");
     }
     g->allocs.push_back(q);
     g->dev_bytes += (int64_t)bytes;
@@ -56,27 +96,67 @@ nao_status dev_alloc(nao_grid *g, T **p, size_t count) {
     return NAO_OK;
 }
 
+// Allocation plus an asynchronous copy on the setup stream; callers synchronise the setup
+// stream before the memory is used from another stream (and before pageable sources die).
 template <class T>
 nao_status upload(nao_grid *g, T **p, const T *src, size_t count) {
     nao_status st = dev_alloc(g, p, count);
     if (st != NAO_OK) return st;
-    if (count) NAO_CUDA(cudaMemcpy(*p, src, count * sizeof(T), cudaMemcpyHostToDevice));
+    if (count) NAO_CUDA(cudaMemcpyAsync(*p, src, count * sizeof(T), cudaMemcpyHostToDevice, g->setup));
     return NAO_OK;
 }
 
+// Frees everything once the handle's last call has completed on the device, without waiting on
+// the host for anything but this handle's own work.
 void free_grid(nao_grid *g) {
     if (!g) return;
+    if (g->setup && g->ev_last && g->used) cudaStreamWaitEvent(g->setup, g->ev_last, 0);
+    if (!g->graphs.empty() && g->ev_last && g->used) cudaEventSynchronize(g->ev_last);
+    for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
     for (auto &t : g->timed) {
         cudaEventDestroy(t.a);
         cudaEventDestroy(t.b);
     }
     for (cudaEvent_t e : g->event_pool) cudaEventDestroy(e);
-    for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
     if (g->ev_in) cudaEventDestroy(g->ev_in);
     if (g->ev_out) cudaEventDestroy(g->ev_out);
     if (g->gstream) cudaStreamDestroy(g->gstream);
-    for (void *p : g->allocs) cudaFree(p);
+    if (g->setup) {
+        for (void *p : g->allocs) cudaFreeAsync(p, g->setup);
+    }
+    bool last = false;
+    if (g->counted) {
+        PoolState &P = pools();
+        std::lock_guard<std::mutex> lock(P.mu);
+        last = --P.live[g->device] == 0;
+    }
+    if (last) {
+        // the device's last handle: return the pool's memory once these frees are done
+        cudaStreamSynchronize(g->setup);
+        cudaMemPool_t pool;
+        if (device_pool(g->device, &pool) == NAO_OK) cudaMemPoolTrimTo(pool, 0);
+    }
+    if (g->ev_last) cudaEventDestroy(g->ev_last);
+    if (g->setup) cudaStreamDestroy(g->setup);
     delete g;
+}
+
+// The handle's setup stream and last-call event (created first thing in nao_grid_create).
+nao_status init_streams(nao_grid *g) {
+    NAO_CUDA(cudaStreamCreateWithFlags(&g->setup, cudaStreamNonBlocking));
+    NAO_CUDA(cudaEventCreateWithFlags(&g->ev_last, cudaEventDisableTiming));
+    PoolState &P = pools();
+    std::lock_guard<std::mutex> lock(P.mu);
+    P.live[g->device]++;
+    g->counted = true;
+    return NAO_OK;
+}
+
+// Marks the end of a call's work on stream st.
+nao_status mark_done(nao_grid *g, cudaStream_t st) {
+    NAO_CUDA(cudaEventRecord(g->ev_last, st));
+    g->used = true;
+    return NAO_OK;
 }
 
 double factorial(int n) {
@@ -233,9 +313,12 @@ nao_status build(nao_grid *g, const nao_system_desc *descs, int32_t n_sys, const
     {
         double *d_minr2;
         if ((st = dev_alloc(g, &d_minr2, minr2.size()))) return st;
-        NAO_CUDA(launch_relevance_minr2(d_atoms, d_bmol, d_aoff, max_atoms, d_px, d_py, d_pz, d_boff, nbat, d_minr2, 0));
-        NAO_CUDA(cudaMemcpy(minr2.data(), d_minr2, minr2.size() * sizeof(double), cudaMemcpyDeviceToHost));
-        cudaFree(d_minr2);
+        NAO_CUDA(launch_relevance_minr2(d_atoms, d_bmol, d_aoff, max_atoms, d_px, d_py, d_pz, d_boff, nbat, d_minr2,
+                                        g->setup));
+        NAO_CUDA(cudaMemcpyAsync(minr2.data(), d_minr2, minr2.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                 g->setup));
+        NAO_CUDA(cudaStreamSynchronize(g->setup));
+        cudaFreeAsync(d_minr2, g->setup);
         g->allocs.pop_back();
         g->dev_bytes -= (int64_t)std::max<size_t>(minr2.size() * sizeof(double), 16);
     }
@@ -379,7 +462,7 @@ nao_status build(nao_grid *g, const nao_system_desc *descs, int32_t n_sys, const
         (st = dev_alloc(g, &g->d_ne_part, (size_t)std::max<int64_t>(g->n_dwork, 1))) ||
         (st = dev_alloc(g, &g->d_err, 4)))
         return st;
-    NAO_CUDA(cudaMemset(g->d_err, 0, 4 * sizeof(int32_t)));
+    NAO_CUDA(cudaMemsetAsync(g->d_err, 0, 4 * sizeof(int32_t), g->setup));
     int32_t *d_sboff, *d_snb, *d_spoff;
     if ((st = upload(g, &d_sboff, g->sys_boff.data(), g->sys_boff.size())) ||
         (st = upload(g, &d_snb, g->sys_nb.data(), g->sys_nb.size())) ||
@@ -389,7 +472,7 @@ nao_status build(nao_grid *g, const nao_system_desc *descs, int32_t n_sys, const
         (st = upload(g, &g->d_mirror_tasks, g->mirror_tasks.data(), g->mirror_tasks.size())) ||
         (st = dev_alloc(g, &g->d_tab, 5 * (size_t)n_sys)))
         return st;
-    NAO_CUDA(cudaMemset(g->d_tab, 0, 5 * (size_t)n_sys * sizeof(double *)));
+    NAO_CUDA(cudaMemsetAsync(g->d_tab, 0, 5 * (size_t)n_sys * sizeof(double *), g->setup));
     g->h_tab.assign(5 * (size_t)n_sys, nullptr);
 
     DevSystem &s = g->sys;
@@ -434,7 +517,7 @@ nao_status build(nao_grid *g, const nao_system_desc *descs, int32_t n_sys, const
             }
             s.knorm[l][m] = k;
         }
-    NAO_CUDA(cudaDeviceSynchronize());
+    NAO_CUDA(cudaStreamSynchronize(g->setup));
     return NAO_OK;
 }
 
@@ -544,17 +627,17 @@ nao_status split_setup(nao_grid *g) {
         (st = dev_alloc(g, &g->d_neg16, (size_t)g->n_batches)) ||
         (st = upload(g, &g->d_split_hw, hw.data(), hw.size())) || (st = upload(g, &g->d_split_nw, nw.data(), nw.size())))
         return st;
+    NAO_CUDA(cudaStreamSynchronize(g->setup));
     g->split_S = S;
     g->split_ready = true;
     return NAO_OK;
 }
 
 // This call's pointer tables (sections: 0 H, 1 v, 2 P, 3 n, 4 N_e; one entry per system),
-// copied from host memory the library owns (pageable: the source may be reused on return).
+// written on the call's stream by kernels that carry the values in their arguments.
 nao_status upload_tables(nao_grid *g, int first, int count, cudaStream_t st) {
     const size_t n = (size_t)g->n_sys;
-    NAO_CUDA(cudaMemcpyAsync(g->d_tab + first * n, g->h_tab.data() + first * n, count * n * sizeof(void *),
-                             cudaMemcpyHostToDevice, st));
+    NAO_CUDA(launch_set_pointers(g->d_tab + first * n, g->h_tab.data() + first * n, (int32_t)(count * n), st));
     return NAO_OK;
 }
 
@@ -724,7 +807,8 @@ static nao_status create(const nao_system_desc *descs, int32_t n_sys, const nao_
     g->opt = o;
     g->opt.device = dev;
     try {
-        st = build(g, descs, n_sys, nullptr);
+        st = init_streams(g);
+        if (st == NAO_OK) st = build(g, descs, n_sys, nullptr);
     } catch (const std::bad_alloc &) {
         st = fail(NAO_ERR_OUT_OF_MEMORY, "host allocation failed");
     } catch (...) {
@@ -770,7 +854,6 @@ nao_status nao_get_system(const nao_grid *g, int32_t m, int64_t *basis_offset, i
 nao_status nao_destroy(nao_grid *g) {
     if (!g) return NAO_OK;
     DeviceGuard guard(g->device);
-    cudaDeviceSynchronize();
     free_grid(g);
     return NAO_OK;
 }
@@ -826,7 +909,8 @@ nao_status nao_integrate_h(nao_grid *g, const double *v_dev, uint32_t terms, nao
     if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
     set_tab(g, 0, 0, H_dev);
     set_tab(g, 1, 0, v_dev);
-    return run_h(g, terms, prec, static_cast<cudaStream_t>(cuda_stream));
+    if ((st = run_h(g, terms, prec, static_cast<cudaStream_t>(cuda_stream)))) return st;
+    return mark_done(g, static_cast<cudaStream_t>(cuda_stream));
 }
 
 nao_status nao_integrate_h_many(nao_grid *g, const double *const *v_dev, uint32_t terms, nao_precision prec,
@@ -843,7 +927,8 @@ nao_status nao_integrate_h_many(nao_grid *g, const double *const *v_dev, uint32_
         set_tab(g, 0, m, H_dev[m]);
         set_tab(g, 1, m, v_dev ? v_dev[m] : nullptr);
     }
-    return run_h(g, terms, prec, static_cast<cudaStream_t>(cuda_stream));
+    if ((st = run_h(g, terms, prec, static_cast<cudaStream_t>(cuda_stream)))) return st;
+    return mark_done(g, static_cast<cudaStream_t>(cuda_stream));
 }
 
 nao_status nao_update_density(nao_grid *g, const double *P_dev, nao_precision prec, double *n_dev,
@@ -857,7 +942,8 @@ nao_status nao_update_density(nao_grid *g, const double *P_dev, nao_precision pr
     set_tab(g, 2, 0, P_dev);
     set_tab(g, 3, 0, n_dev);
     set_tab(g, 4, 0, n_electrons_dev);
-    return run_n(g, prec, static_cast<cudaStream_t>(cuda_stream));
+    if ((st = run_n(g, prec, static_cast<cudaStream_t>(cuda_stream)))) return st;
+    return mark_done(g, static_cast<cudaStream_t>(cuda_stream));
 }
 
 nao_status nao_update_density_many(nao_grid *g, const double *const *P_dev, nao_precision prec, double *const *n_dev,
@@ -876,7 +962,8 @@ nao_status nao_update_density_many(nao_grid *g, const double *const *P_dev, nao_
         set_tab(g, 3, m, n_dev[m]);
         set_tab(g, 4, m, n_electrons_dev ? n_electrons_dev[m] : nullptr);
     }
-    return run_n(g, prec, static_cast<cudaStream_t>(cuda_stream));
+    if ((st = run_n(g, prec, static_cast<cudaStream_t>(cuda_stream)))) return st;
+    return mark_done(g, static_cast<cudaStream_t>(cuda_stream));
 }
 
 static nao_status ensure_staging(nao_grid *g) {
@@ -886,6 +973,7 @@ static nao_status ensure_staging(nao_grid *g) {
     if ((st = dev_alloc(g, &g->d_stage_in, big)) || (st = dev_alloc(g, &g->d_stage_out, big)) ||
         (st = dev_alloc(g, &g->d_stage_ne, 1)))
         return st;
+    NAO_CUDA(cudaStreamSynchronize(g->setup));
     return NAO_OK;
 }
 
@@ -908,6 +996,7 @@ nao_status nao_integrate_h_host(nao_grid *g, const double *v_host, uint32_t term
     set_tab(g, 1, 0, v);
     if ((st = run_h(g, terms, prec, s))) return st;
     NAO_CUDA(cudaMemcpyAsync(H_host, g->d_stage_out, (size_t)g->nb * g->nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if ((st = mark_done(g, s))) return st;
     NAO_CUDA(cudaStreamSynchronize(s));
     return NAO_OK;
 }
@@ -930,6 +1019,7 @@ nao_status nao_update_density_host(nao_grid *g, const double *P_host, nao_precis
     NAO_CUDA(cudaMemcpyAsync(n_host, g->d_stage_out, (size_t)g->n_points * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (n_electrons_host)
         NAO_CUDA(cudaMemcpyAsync(n_electrons_host, g->d_stage_ne, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if ((st = mark_done(g, s))) return st;
     NAO_CUDA(cudaStreamSynchronize(s));
     return NAO_OK;
 }
@@ -945,7 +1035,7 @@ nao_status nao_evaluate_batch(nao_grid *g, int64_t batch, nao_precision prec, do
     DeviceGuard guard(g->device);
     if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
     NAO_CUDA(launch_eval_one(g->sys, (int32_t)batch, prec, phi_dev, grad_dev, static_cast<cudaStream_t>(cuda_stream)));
-    return NAO_OK;
+    return mark_done(g, static_cast<cudaStream_t>(cuda_stream));
 }
 
 nao_status nao_profile_enable(nao_grid *g, int32_t enable) {
@@ -981,9 +1071,11 @@ nao_status nao_sync_status(nao_grid *g) {
     nao_status st = check_handle(g);
     if (st) return st;
     DeviceGuard guard(g->device);
-    NAO_CUDA(cudaDeviceSynchronize());
+    // this handle's work only: its last call, then the error word on the setup stream
+    if (g->used) NAO_CUDA(cudaEventSynchronize(g->ev_last));
     int32_t err[4] = {0, 0, 0, 0};
-    NAO_CUDA(cudaMemcpy(err, g->d_err, sizeof(err), cudaMemcpyDeviceToHost));
+    NAO_CUDA(cudaMemcpyAsync(err, g->d_err, sizeof(err), cudaMemcpyDeviceToHost, g->setup));
+    NAO_CUDA(cudaStreamSynchronize(g->setup));
     if (err[0] != 0) return fail((nao_status)err[0], "device-side check failed (code " + std::to_string(err[1]) + ")");
     return NAO_OK;
 }

@@ -299,6 +299,15 @@ __global__ void __launch_bounds__(1024) reduce_ne_kernel(DevSystem s, const doub
     }
 }
 
+// Pointer-table entries passed by value in the kernel's arguments.
+constexpr int kPtrBatch = 480;
+struct PtrBatch {
+    void *p[kPtrBatch];
+};
+__global__ void set_pointers_kernel(double **__restrict__ dst, PtrBatch src, int32_t n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = static_cast<double *>(src.p[i]);
+}
+
 // n = 0 at the points of each density work item (before accumulation by atomics).
 __global__ void __launch_bounds__(64) zero_n_kernel(DevSystem s, const DWork *__restrict__ work) {
     const DWork it = work[blockIdx.x];
@@ -347,6 +356,18 @@ cudaError_t launch_reduce_ne(const DevSystem &s, const double *part, const int32
     if (n_sys <= 0) return cudaSuccess;
     reduce_ne_kernel<<<n_sys, 1024, 0, st>>>(s, part, sys_dw0);
     return cudaGetLastError();
+}
+
+cudaError_t launch_set_pointers(double **dst, void *const *src, int32_t n, cudaStream_t st) {
+    for (int32_t i0 = 0; i0 < n; i0 += kPtrBatch) {
+        const int32_t c = n - i0 < kPtrBatch ? n - i0 : kPtrBatch;
+        PtrBatch b;
+        for (int32_t i = 0; i < c; i++) b.p[i] = src[i0 + i];
+        set_pointers_kernel<<<1, 128, 0, st>>>(dst + i0, b, c);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_zero_n(const DevSystem &s, const DWork *work, int32_t n_work, cudaStream_t st) {

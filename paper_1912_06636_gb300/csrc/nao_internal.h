@@ -155,9 +155,14 @@ struct nao_grid {
     std::vector<Chunk> chunks;
     int64_t scratch_elems = 0;  // doubles
     int64_t n_hwork = 0, n_dwork = 0;
-    // device memory
+    // device memory: stream-ordered allocations from the library's per-device pool, made and
+    // freed on the handle's own setup stream (no device-wide synchronisation at create or
+    // destroy); ev_last marks the end of the handle's most recently enqueued call
     std::vector<void *> allocs;
     int64_t dev_bytes = 0;
+    cudaStream_t setup = nullptr;
+    cudaEvent_t ev_last = nullptr;
+    bool used = false, counted = false;
     DevSystem sys{};
     HWork *d_hwork = nullptr;
     DWork *d_dwork = nullptr;
@@ -227,6 +232,9 @@ cudaError_t launch_density_simt(const DevSystem &s, nao_precision prec, const DW
 // N_e of every system: sum of its density work items' partial sums (deterministic order)
 cudaError_t launch_reduce_ne(const DevSystem &s, const double *part, const int32_t *sys_dw0, int32_t n_sys,
                              cudaStream_t st);
+// dst[i] = src[i] for i < n, written by kernels whose arguments carry the pointer values (no host
+// buffer has to outlive the call)
+cudaError_t launch_set_pointers(double **dst, void *const *src, int32_t n, cudaStream_t st);
 // n = 0 at every point of the given density work items
 cudaError_t launch_zero_n(const DevSystem &s, const DWork *work, int32_t n_work, cudaStream_t st);
 

@@ -15,8 +15,8 @@
 //   - all calls on a device share the one array and it keeps the last call's contents:
 //     the evaluation kernel writes every entry the contraction later reads (padding
 //     included), so nothing has to be cleared; H_dev is zeroed by the call itself;
-//   - the call writes the handle's device pointer table (H, v) from host memory the handle
-//     owns, like every other call on the handle;
+//   - the call writes the handle's device pointer table (H, v) like every other call on the
+//     handle;
 //   - calls whose work overlaps on the GPU (other streams, other handles) race on the array;
 //   - the first call on a device looks up the array's device address (cudaGetSymbolAddress,
 //     with that device current); make that first call before any stream capture.
@@ -79,12 +79,13 @@ extern "C" nao_status nao_integrate_h_noalloc(nao_grid *g, const double *v_dev, 
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = cudaSuccess;
     if (st == NAO_OK) {
-        // this call's H and v pointers, in the handle's pointer table (copied from host memory
-        // the handle owns; a pageable-source copy, no allocation)
+        // this call's H and v pointers, into the handle's device pointer table (written by a
+        // kernel that carries the values in its arguments; no allocation)
         const size_t n = (size_t)g->n_sys;
         g->h_tab[0] = H_dev;
         g->h_tab[n] = const_cast<double *>(v_dev);
-        e = cudaMemcpyAsync(g->d_tab, g->h_tab.data(), 2 * n * sizeof(void *), cudaMemcpyHostToDevice, s);
+        e = launch_set_pointers(g->d_tab, g->h_tab.data(), 1, s);
+        if (e == cudaSuccess) e = launch_set_pointers(g->d_tab + n, g->h_tab.data() + n, 1, s);
     }
     if (st == NAO_OK && e == cudaSuccess) e = launch_zero_h(g->sys, g->d_zero_tasks, (int32_t)g->zero_tasks.size(), s);
     for (size_t c = 0; st == NAO_OK && e == cudaSuccess && c < g->chunks.size(); c++) {
@@ -95,6 +96,10 @@ extern "C" nao_status nao_integrate_h_noalloc(nao_grid *g, const double *v_dev, 
     }
     if (st == NAO_OK && e == cudaSuccess)
         e = launch_mirror(g->sys, g->d_mirror_tasks, (int32_t)g->mirror_tasks.size(), s);
+    if (st == NAO_OK && e == cudaSuccess) {
+        e = cudaEventRecord(g->ev_last, s);  // the end of this call's work, for destroy and sync
+        if (e == cudaSuccess) g->used = true;
+    }
     if (prev >= 0 && prev != g->device) cudaSetDevice(prev);
     if (st != NAO_OK) return st;
     if (e != cudaSuccess) return noalloc_fail(NAO_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));

@@ -305,6 +305,66 @@ def config_diamond64(n_rad=60, n_theta=17, n_phi=18, max_batch_points=300, cells
                        max_batch_points=max_batch_points, name=f"diamond{len(atoms)}")
 
 
+def slab_species(kind: str) -> Species:
+    """Two-species slab basis: 4s,3p,4d,1f radial functions (40 basis functions per atom), alpha
+    log-uniform in [0.1, 20]; species A (Z = 83, seed 2) and B (Z = 34, seed 3)."""
+    seed, Z = {"A": (2, 83.0), "B": (3, 34.0)}[kind]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ls = [0, 0, 0, 0, 1, 1, 1, 2, 2, 2, 2, 3]
+    return Species(ls=ls, alphas=list(_log_uniform(rng, 0.1, 20.0, len(ls))), Z=Z)
+
+
+def slab_geometry(layers: int = 15, n: int = 5, a: float = 7.8, pitch: float = 3.5):
+    """Layered slab (finite cluster): `layers` layers of an n x n triangular lattice (spacing a),
+    each layer shifted by (a/2, a/(2 sqrt 3)) from the one below (ABC stacking), layer pitch
+    `pitch`; species pattern B A B A B in every five-layer unit (species index 0 = A, 1 = B)."""
+    atoms, spec = [], []
+    pattern = [1, 0, 1, 0, 1]
+    for L in range(layers):
+        sx, sy = (L % 3) * a / 2.0, (L % 3) * a / (2.0 * math.sqrt(3.0))
+        for i in range(n):
+            for j in range(n):
+                atoms.append([i * a + j * a / 2.0 + sx, j * a * math.sqrt(3.0) / 2.0 + sy, L * pitch])
+                spec.append(pattern[L % 5])
+    return np.asarray(atoms, dtype=np.float64), np.asarray(spec, dtype=np.int32)
+
+
+def config_slab375(n_rad=80, n_theta=14, n_phi=31, max_batch_points=200, layers=15, n=5) -> System:
+    """375-atom layered slab of two species (150 A : 225 B), 15,000 basis functions, ~13M points."""
+    atoms, spec = slab_geometry(layers, n)
+    return make_system(atoms, spec, [slab_species("A"), slab_species("B")], n_rad, n_theta, n_phi,
+                       max_batch_points=max_batch_points, name=f"slab{len(atoms)}")
+
+
+def random_molecule(n_atoms: int, seed: int, n_rad=40, n_theta=10, n_phi=11, max_batch_points=200,
+                    min_dist: float = 2.0) -> System:
+    """A random molecule: atoms placed one by one, uniformly in a sphere of volume 135 n_atoms
+    bohr^3 (the atom density of silicon), rejecting any within min_dist of an earlier atom;
+    each atom's species drawn uniformly from {Si (diamond cluster), A, B (slab)}."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    radius = (3.0 * 135.0 * n_atoms / (4.0 * math.pi)) ** (1.0 / 3.0)
+    atoms = []
+    while len(atoms) < n_atoms:
+        p = rng.uniform(-radius, radius, 3)
+        if p @ p > radius * radius:
+            continue
+        if all(np.linalg.norm(p - q) >= min_dist for q in atoms):
+            atoms.append(p)
+    spec = rng.integers(0, 3, n_atoms).astype(np.int32)
+    species = [silicon_species(1), slab_species("A"), slab_species("B")]
+    return make_system(np.asarray(atoms), spec, species, n_rad, n_theta, n_phi,
+                       max_batch_points=max_batch_points, name=f"mol{n_atoms}-{seed}")
+
+
+def serving_stream(n_requests: int, rate: float = 200.0, seed: int = 4, n_min: int = 3, n_max: int = 200):
+    """Poisson arrivals at `rate` per second; molecule sizes log-uniform in [n_min, n_max] atoms.
+    Returns a list of (arrival time in s, number of atoms, molecule seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = np.cumsum(rng.exponential(1.0 / rate, n_requests))
+    sizes = np.floor(_log_uniform(rng, n_min, n_max + 1, n_requests)).astype(int)
+    return [(float(t[i]), int(min(sizes[i], n_max)), 4000 + i) for i in range(n_requests)]
+
+
 def density_matrix(sys: System, seed: int, rank: int | None = None) -> np.ndarray:
     return random_psd(sys.n_basis, seed, rank)
 
@@ -314,4 +374,6 @@ def config(k: int, **kw) -> System:
         return config_water(**kw)
     if k == 1:
         return config_diamond64(**kw)
+    if k == 2:
+        return config_slab375(**kw)
     raise ValueError(f"unknown configuration {k}")
