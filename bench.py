@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default=None, choices=[None, "fp64", "fp32", "split"])
     ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--cells", type=int, default=2,
+                    help="diamond cluster: cubic cells per edge (2 = the 64-atom workload; 1 = an 8-atom case "
+                         "for profiling captures, not a bench line)")
     ap.add_argument("--slices", type=int, default=10,
                     help="split path: slices per operand (10 meets e <= 1e-10 on this workload; the library default is 12)")
     ap.add_argument("--cpu-sample", type=int, default=200000, help="oracle sample size (points)")
@@ -161,6 +164,16 @@ def serving(n_requests: int, device: int) -> dict:
     return out
 
 
+# DRAM bytes per algorithmic FLOP_H of the dominant kernel, from one ncu capture of the diamond8
+# profiling case (dram__bytes_read.sum + dram__bytes_write.sum of one launch / that launch's
+# FLOP_H = 4.6096e9); a launch's traffic grows with tiles x K, i.e. with FLOP_H. Valid only for
+# the kernel version and slice count the capture was taken with.
+TRAFFIC_PER_FLOP_H = {
+    ("h_split", 10): ((1.033217e9 + 4.605184e6) / 4.6096304e9, "profiles/h_tc_kernel_diamond8_split.md"),
+    ("h_fp64", 0): ((359.834112e6 + 3.945472e6) / 4.6096304e9, "profiles/h_simt_kernel_diamond8_fp64.md"),
+}
+
+
 def g_split_pairs(g) -> int:
     """Slice products per contraction on the split path: S (S + 1) / 2 for S slices."""
     S = int(g.split_slices)
@@ -168,10 +181,17 @@ def g_split_pairs(g) -> int:
 
 
 # ---------------------------------------------------------------------------------------
-def make_workload(config: int, device: str):
+def workload_name(args) -> str:
+    if args.config == 1 and args.cells != 2:
+        return (f"diamond{8 * args.cells ** 3}: {8 * args.cells ** 3}-atom diamond-lattice cluster, 25 basis functions "
+                "per atom, 60x306 points per atom, batches <= 300 points (profiling case)")
+    return WORKLOAD
+
+
+def make_workload(config: int, device: str, cells: int = 2):
     from paper_1912_06636_gb300 import synth
 
-    s = synth.config(config)
+    s = synth.config(config, cells=cells) if config == 1 else synth.config(config)
     v = s.potential()
     P = synth.density_matrix(s, config)
     return s, v, P
@@ -201,7 +221,7 @@ def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
         return
-    s, v, P = make_workload(args.config, "cpu")
+    s, v, P = make_workload(args.config, "cpu", args.cells)
     times = []
     for _ in range(args.warmup + args.steps):
         cb = cpu_baseline(s, v, P, max(200, args.cpu_sample // 4))
@@ -211,7 +231,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "points/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * s.n_points / val,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": "fp64", "l2": "n/a (CPU)"},
+            "config": {"workload": workload_name(args), "precision": "fp64", "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": val, "unit": "points/s", "cores": 1, "kind": "oracle",
                              "sample": timed[0]["sample"] + " per step"},
             "e2e": {"value": val, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -238,7 +258,7 @@ def main():
     from paper_1912_06636_gb300 import nao
 
     prec = args.prec or "split"
-    s, v_np, P_np = make_workload(args.config, f"cuda:{local_rank}")
+    s, v_np, P_np = make_workload(args.config, f"cuda:{local_rank}", args.cells)
     dev = torch.device("cuda", local_rank)
     t0 = time.perf_counter()
     g = nao.Grid(s, device=local_rank, max_batch_points=s.max_batch_points, split_slices=args.slices)
@@ -312,6 +332,12 @@ def main():
                         "work": f"{pairs} slice products x algorithmic FLOPs (sum_b 4 P_b N_b (N_b+1) for H)",
                         "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}
         roofline.update({"launches": launches, "avg_launch_ms": fam_ms / max(launches, 1)})
+        tk = (fam, int(g.split_slices) if prec == "split" else 0)
+        if tk in TRAFFIC_PER_FLOP_H and launches:
+            per_flop, src = TRAFFIC_PER_FLOP_H[tk]
+            roofline["traffic"] = per_flop * info.flops_h * args.steps / launches
+            roofline["traffic_unit"] = "bytes per launch"
+            roofline["traffic_source"] = src + " (diamond8 capture scaled by FLOP_H per launch)"
     gpu_launches = int(sum(l for l, _ in prof.values()))
 
     line = {
@@ -319,7 +345,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "split": "bf16x-slices+f64"}[prec],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": prec, "parallelism": f"replicas{world}",
+        "config": {"workload": workload_name(args), "precision": prec, "parallelism": f"replicas{world}",
                    "split_slices": args.slices if prec == "split" else None,
                    "l2": f"inputs/working set larger than L2: {scratch_gb:.1f} GB of evaluated basis functions "
                          "written and re-read per step",
