@@ -606,8 +606,7 @@ nao_status split_setup(nao_grid *g) {
                 for (int I = 0; I < nI; I++)
                     for (int J = 0; J < nJ; J++)
                         if (I * 128 <= J * TN + TN - 1) hw.push_back({b, I, J, 0});
-                for (int Q = 0; Q < G.n_qt; Q++)
-                    for (int J = 0; J < G.n_jtN; J++) nw.push_back({b, Q, J, 0});
+                for (int Q = 0; Q < G.n_qt; Q++) nw.push_back({b, Q, G.n_jtN, 0});  // all J tiles in one CTA
             }
         }
         cur.b1 = c.b1;

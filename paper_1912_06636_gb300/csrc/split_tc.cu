@@ -32,49 +32,77 @@ namespace {
 
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: bounded mbarrier waits
 
-// bf16 bit pattern of a small integer (|d| <= 256 is exact).
-__device__ __forceinline__ uint32_t bf16_bits(int d) { return __float_as_uint((float)d) >> 16; }
 
-// S balanced base-64 digits of X = round(Y), |Y| < 2^(6S-1) (most significant first in
-// dig[0]), in integer arithmetic. The S-1 lower digits are taken in [-32, 31]; the top digit
-// is what remains, which the bound on |X| keeps in [-32, 32] (it must not be reduced modulo
-// 64, or a carry would be lost). For S > 10, X may need more than 64 bits; but an FP64 Y with
-// |Y| >= 2^63 is an integer m 2^k (53-bit m, k >= 11), so X = (m 2^(k mod 6)) 64^(k/6): the
-// last k/6 digits are zero and the others are those of m 2^(k mod 6) < 2^59.
-template <int S>
-__device__ __forceinline__ void digits(double Y, int (&dig)[S]) {
-    long long X;
-    int q = 0;  // trailing zero digits
-    if (S <= 10 || fabs(Y) < 9223372036854775808.0) {
-        X = __double2ll_rn(Y);
-    } else {
-        const long long bits = __double_as_longlong(Y);
-        const int k = (int)((bits >> 52) & 0x7FF) - 1075;  // Y = +-m 2^k
-        const long long m = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
-        q = k / 6;
-        X = m << (k - 6 * q);
-        if (bits < 0) X = -X;
-    }
-#pragma unroll
-    for (int s = S - 1; s >= 1; s--) {
-        if (s >= S - q) {
-            dig[s] = 0;
-        } else {
-            const int d = (int)(((X + 32) & 63LL)) - 32;
-            dig[s] = d;
-            X = (X - d) >> 6;
-        }
-    }
-    dig[0] = (int)X;
+// Digit extraction works on FP64 bit patterns with integer instructions: on this GPU the FP64
+// pipe is ~1/60 of the FP32 rate, and a double-to-int64 conversion per element would make the
+// slicing kernels FP64-bound.
+
+// |x| as an ordered integer: for non-negative doubles the bit patterns order like the values.
+__device__ __forceinline__ long long abs_bits(double x) { return __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL; }
+
+// Exponent e with max * 2^-e in [0.25, 0.5), from the bit pattern of max (abs_bits); rows whose
+// magnitude is below 2^-900 (or zero) are taken as zero (flag -10000).
+__device__ __forceinline__ int row_exponent_bits(long long mb) {
+    const int eb = (int)(mb >> 52);  // biased exponent
+    if (eb == 0) return -10000;
+    const int ex = eb - 1022;  // max = f 2^ex, f in [0.5, 1)
+    return ex < -900 ? -10000 : ex + 1;
 }
 
-// Exponent e with max * 2^-e in [0.25, 0.5); rows whose magnitude is below 2^-900 are taken
-// as zero (flag -10000).
-__device__ __forceinline__ int row_exponent(double mx) {
-    if (!(mx > 0.0)) return -10000;
-    int ex;
-    frexp(mx, &ex);
-    return ex < -900 ? -10000 : ex + 1;
+// 2^23 + u for a 23-bit unsigned u, as an exact float, minus 2^23: u as a float without a
+// conversion instruction.
+__device__ __forceinline__ float u23_to_float(uint32_t u) { return __int_as_float(0x4B000000 | (int)u) - 8388608.0f; }
+
+// S balanced base-64 digits (most significant first in dig[0]) of X = round(x 2^(6S-e)),
+// |x 2^-e| < 1/2, as exact small-integer floats. From x's bits x = +-m 2^(E-1075) (53-bit m):
+// |X| = m 2^-sh with sh = 1075 + e - 6S - E, rounded half up when sh > 0, held as a 128-bit
+// integer (hi:lo; more than 64 bits only for S > 10). |X| is cut into 18-bit chunks (three
+// digits each), exact in FP32, and the digits are peeled off from the bottom in FP32:
+// q = rint(v / 64), d = v - 64 q in [-32, 32], v <- q, the carry q (0 or 1 after a chunk's
+// three digits) joining the next chunk. The top digit keeps whatever remains, which the bound
+// on |X| keeps in [-32, 32]. The sign is applied to every digit. Subnormal x and e = -10000
+// give zeros.
+template <int S>
+__device__ __forceinline__ void digits(double x, int e, float (&dig)[S]) {
+    const long long bits = __double_as_longlong(x);
+    const int eb = (int)((bits >> 52) & 0x7FF);
+    unsigned long long lo = 0, hi = 0;
+    if (eb != 0 && e > -10000) {
+        const unsigned long long m = ((unsigned long long)bits & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+        const int sh = 1075 + e - 6 * S - eb;
+        if (sh > 0) {
+            lo = sh >= 63 ? 0ULL : (m + (1ULL << (sh - 1))) >> sh;
+        } else {
+            const int k = -sh;  // <= 6 for S <= 10, <= 18 for S = 12
+            lo = m << k;
+            hi = k > 0 ? m >> (64 - k) : 0ULL;
+        }
+    }
+    const float sgn = bits < 0 ? -1.0f : 1.0f;
+    float v = u23_to_float((uint32_t)(lo & 0x3FFFFULL));
+#pragma unroll
+    for (int s = S - 1; s >= 0; s--) {
+        const int t = S - 1 - s;  // digits already taken
+        if (t > 0 && t % 3 == 0) {
+            const int c = t / 3;  // next 18-bit chunk of |X|
+            const uint32_t u = c == 1 ? (uint32_t)((lo >> 18) & 0x3FFFFULL)
+                             : c == 2 ? (uint32_t)((lo >> 36) & 0x3FFFFULL)
+                                      : (uint32_t)(((lo >> 54) | (hi << 10)) & 0x7FFFFFULL);
+            v += u23_to_float(u);
+        }
+        if (s == 0) {
+            dig[0] = sgn * v;
+        } else {
+            const float q = fmaf(v, 0.015625f, 12582912.0f) - 12582912.0f;  // rint(v / 64)
+            dig[s] = sgn * fmaf(q, -64.0f, v);
+            v = q;
+        }
+    }
+}
+
+// bf16 bit patterns of two small integers held exactly in floats (their low halves are zero).
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+    return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
 }
 
 // 2^E as an FP64 (0 below the normal range).
@@ -149,13 +177,13 @@ __global__ void __launch_bounds__(256) slice_h_kernel(DevSystem s, int32_t b0, c
     __syncthreads();
     for (int lr = warp; lr < 64; lr += 8) {
         const int r = rt * 64 + lr;
-        double mx = 0.0;
+        long long mb = 0;
         if (r < N)
-            for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(E[(int64_t)r * K + k] * sd[k]));
+            for (int k = lane; k < K; k += 32) mb = max(mb, abs_bits(E[(int64_t)r * K + k] * sd[k]));
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
         if (lane == 0) {
-            const int e = row_exponent(mx);
+            const int e = row_exponent_bits(mb);
             ex_s[lr] = e;
             if (r < N) expo[s.rel_off[b] + r] = e;
         }
@@ -167,25 +195,24 @@ __global__ void __launch_bounds__(256) slice_h_kernel(DevSystem s, int32_t b0, c
         const int lr = u / groups, k0 = (u - lr * groups) * 8;
         const int r = rt * 64 + lr;
         if (r >= G.R16) continue;
-        const int e = ex_s[lr];
-        int dg[8][S];
-        const double scale = (r < N && e > -10000) ? pow2(6 * S - e) : 0.0;
+        const int e = r < N ? ex_s[lr] : -10000;
+        float dg[8][S];
         const double *row = E + (int64_t)(r < N ? r : 0) * K;
 #pragma unroll
         for (int h = 0; h < 8; h++) {
             const int kk = src[k0 + h];
-            const double x = (kk >= 0 && scale != 0.0) ? row[kk] * sd[kk] : 0.0;
-            digits<S>(x * scale, dg[h]);
+            const double x = (kk >= 0 && e > -10000) ? row[kk] * sd[kk] : 0.0;
+            digits<S>(x, e, dg[h]);
         }
         const int kc = k0 >> 6;
         const uint32_t off = tc::sw128_offset((uint32_t)r, (uint32_t)(k0 & 63));
 #pragma unroll
         for (int sl = 0; sl < S; sl++) {
             uint4 va;
-            va.x = bf16_bits(dg[0][sl]) | (bf16_bits(dg[1][sl]) << 16);
-            va.y = bf16_bits(dg[2][sl]) | (bf16_bits(dg[3][sl]) << 16);
-            va.z = bf16_bits(dg[4][sl]) | (bf16_bits(dg[5][sl]) << 16);
-            va.w = bf16_bits(dg[6][sl]) | (bf16_bits(dg[7][sl]) << 16);
+            va.x = pack_bf16x2(dg[0][sl], dg[1][sl]);
+            va.y = pack_bf16x2(dg[2][sl], dg[3][sl]);
+            va.z = pack_bf16x2(dg[4][sl], dg[5][sl]);
+            va.w = pack_bf16x2(dg[6][sl], dg[7][sl]);
             *reinterpret_cast<uint4 *>(base + G.h_block(sl, kc) + off) = va;
         }
     }
@@ -206,30 +233,29 @@ __global__ void __launch_bounds__(128) slice_nphi_kernel(DevSystem s, int32_t b0
     const int q = qt * 128 + threadIdx.x;
     if (N == 0 || q >= G.P16) return;
     const double *E = scratch + s.scr_off[b];  // phi[i][q], stride Ppad
-    double mx = 0.0;
+    long long mb = 0;
     if (q < P)
-        for (int i = 0; i < N; i++) mx = fmax(mx, fabs(E[(int64_t)i * Ppad + q]));
-    const int e = q < P ? row_exponent(mx) : -10000;
+        for (int i = 0; i < N; i++) mb = max(mb, abs_bits(E[(int64_t)i * Ppad + q]));
+    const int e = q < P ? row_exponent_bits(mb) : -10000;
     if (q < P) expo_q[p0 + q] = e;
-    const double scale = e > -10000 ? pow2(6 * S - e) : 0.0;
     uint8_t *base = slices + sl_off[b];
     for (int i0 = 0; i0 < G.n_kcN * 64; i0 += 8) {
-        int dg[8][S];
+        float dg[8][S];
 #pragma unroll
         for (int h = 0; h < 8; h++) {
             const int i = i0 + h;
-            const double x = (scale != 0.0 && i < N) ? E[(int64_t)i * Ppad + q] : 0.0;
-            digits<S>(x * scale, dg[h]);
+            const double x = i < N ? E[(int64_t)i * Ppad + q] : 0.0;
+            digits<S>(x, e, dg[h]);
         }
         const int kc = i0 >> 6;
         const uint32_t off = tc::sw128_offset((uint32_t)q, (uint32_t)(i0 & 63));
 #pragma unroll
         for (int sl = 0; sl < S; sl++) {
             uint4 va;
-            va.x = bf16_bits(dg[0][sl]) | (bf16_bits(dg[1][sl]) << 16);
-            va.y = bf16_bits(dg[2][sl]) | (bf16_bits(dg[3][sl]) << 16);
-            va.z = bf16_bits(dg[4][sl]) | (bf16_bits(dg[5][sl]) << 16);
-            va.w = bf16_bits(dg[6][sl]) | (bf16_bits(dg[7][sl]) << 16);
+            va.x = pack_bf16x2(dg[0][sl], dg[1][sl]);
+            va.y = pack_bf16x2(dg[2][sl], dg[3][sl]);
+            va.z = pack_bf16x2(dg[4][sl], dg[5][sl]);
+            va.w = pack_bf16x2(dg[6][sl], dg[7][sl]);
             *reinterpret_cast<uint4 *>(base + G.nA_block(sl, kc) + off) = va;
         }
     }
@@ -241,7 +267,7 @@ __global__ void __launch_bounds__(128) slice_nphi_kernel(DevSystem s, int32_t b0
 template <int S>
 __global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, uint8_t *__restrict__ slices,
                                                       const int64_t *__restrict__ sl_off, int32_t *__restrict__ expo_b) {
-    __shared__ double red[8];
+    __shared__ long long red[8];
     __shared__ int e_sh;
     const int b = b0 + blockIdx.x, m = s.sys.bmol[b];
     const int P = s.batch_off[b + 1] - s.batch_off[b];
@@ -257,36 +283,35 @@ __global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, 
         const double c = i / TN < j / TN ? 2.0 : 1.0;
         return c * p_elem(s, m, gi, gj);
     };
-    double mx = 0.0;
-    for (int u = threadIdx.x; u < N * N; u += blockDim.x) mx = fmax(mx, fabs(pval(u / N, u % N)));
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    long long mb = 0;
+    for (int u = threadIdx.x; u < N * N; u += blockDim.x) mb = max(mb, abs_bits(pval(u / N, u % N)));
+    for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mb;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double m = 0.0;
-        for (int w = 0; w < 8; w++) m = fmax(m, red[w]);
-        e_sh = row_exponent(m);
+        long long m = 0;
+        for (int w = 0; w < 8; w++) m = max(m, red[w]);
+        e_sh = row_exponent_bits(m);
         expo_b[b] = e_sh;
     }
     __syncthreads();
     const int e = e_sh;
-    const double scale = e > -10000 ? pow2(6 * S - e) : 0.0;
     uint8_t *base = slices + sl_off[b];
     const int groups = G.n_kcN * 8;  // 8-wide groups along K = i
     for (int u = threadIdx.x; u < G.R16 * groups; u += blockDim.x) {
         const int j = u / groups, i0 = (u - j * groups) * 8;
-        int dg[8][S];
+        float dg[8][S];
 #pragma unroll
-        for (int h = 0; h < 8; h++) digits<S>(pval(i0 + h, j) * scale, dg[h]);
+        for (int h = 0; h < 8; h++) digits<S>(pval(i0 + h, j), e, dg[h]);
         const int kc = i0 >> 6;
         const uint32_t off = tc::sw128_offset((uint32_t)j, (uint32_t)(i0 & 63));
 #pragma unroll
         for (int sl = 0; sl < S; sl++) {
             uint4 vb;
-            vb.x = bf16_bits(dg[0][sl]) | (bf16_bits(dg[1][sl]) << 16);
-            vb.y = bf16_bits(dg[2][sl]) | (bf16_bits(dg[3][sl]) << 16);
-            vb.z = bf16_bits(dg[4][sl]) | (bf16_bits(dg[5][sl]) << 16);
-            vb.w = bf16_bits(dg[6][sl]) | (bf16_bits(dg[7][sl]) << 16);
+            vb.x = pack_bf16x2(dg[0][sl], dg[1][sl]);
+            vb.y = pack_bf16x2(dg[2][sl], dg[3][sl]);
+            vb.z = pack_bf16x2(dg[4][sl], dg[5][sl]);
+            vb.w = pack_bf16x2(dg[6][sl], dg[7][sl]);
             *reinterpret_cast<uint4 *>(base + G.nB_block(S, sl, kc) + off) = vb;
         }
     }
@@ -302,6 +327,9 @@ __global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, 
 // columns TN (s + t) ...); commits release A buffers and B sets back to the producer through
 // "empty" mbarriers. The 16-column K steps with index < neg16 negate B (descriptor bit 14).
 // Every wait is bounded; on a timeout the CTA records NAO_ERR_TIMEOUT and skips its epilogue.
+// A CTA may run the pipeline several times (one accumulator tile after another): the ring and
+// B-set phases continue from the K chunks of the earlier runs (c0) and "done" completes once per
+// run (parity = run index).
 // ----------------------------------------------------------------------------------------
 constexpr int RING = 4;
 
@@ -318,6 +346,8 @@ struct LoopArgs {
     size_t b_s, b_kc;
     uint32_t a_bytes, b_bytes;  // <= 16 KB and TN x 128 B (the last tile of an operand is short)
     int n_kc, neg16, S;
+    int c0 = 0;     // K chunks this CTA's earlier runs of the pipeline processed
+    int round = 0;  // index of this run
 };
 
 __host__ __device__ constexpr size_t pipe_smem_bytes(int S) {
@@ -329,13 +359,13 @@ __device__ __forceinline__ void pipe_producer(Pipe &p, uint8_t *sA, uint8_t *sB,
     constexpr uint32_t B_BLOCK = TN * 128;
     const int S = L.S;
     for (int kc = 0; kc < L.n_kc; kc++) {
-        const int bb = kc & 1, ub = kc >> 1;
+        const int gk = L.c0 + kc, bb = gk & 1, ub = gk >> 1;
         if (ub >= 1 && !tc::mbar_wait(&p.emptyB[bb], (ub - 1) & 1, kWaitCycles)) { p.abort = 1; return; }
         tc::mbar_arrive_expect_tx(&p.fullB[bb], (uint32_t)S * L.b_bytes);
         for (int t = 0; t < S; t++)
             tc::bulk_g2s(sB + ((size_t)bb * S + t) * B_BLOCK, L.b0 + t * L.b_s + kc * L.b_kc, L.b_bytes, &p.fullB[bb]);
         for (int sa = 0; sa < S; sa++) {
-            const int idx = kc * S + sa, a = idx % RING, ua = idx / RING;
+            const int idx = gk * S + sa, a = idx % RING, ua = idx / RING;
             if (ua >= 1 && !tc::mbar_wait(&p.emptyA[a], (ua - 1) & 1, kWaitCycles)) { p.abort = 1; return; }
             tc::mbar_arrive_expect_tx(&p.fullA[a], L.a_bytes);
             tc::bulk_g2s(sA + (size_t)a * 16384, L.a0 + sa * L.a_s + kc * L.a_kc, L.a_bytes, &p.fullA[a]);
@@ -350,11 +380,11 @@ __device__ __forceinline__ void pipe_mma(Pipe &p, uint8_t *sA, uint8_t *sB, uint
     constexpr uint32_t idesc = tc::idesc_bf16_f32(128, TN);
     const int S = L.S;
     for (int kc = 0; kc < L.n_kc; kc++) {
-        const int bb = kc & 1, ub = kc >> 1;
+        const int gk = L.c0 + kc, bb = gk & 1, ub = gk >> 1;
         // on a timeout: flag it, and still commit "done" so the teardown waits for issued MMAs
         if (!tc::mbar_wait(&p.fullB[bb], ub & 1, kWaitCycles)) { p.abort = 1; tc::mma_commit(&p.done); return; }
         for (int sa = 0; sa < S; sa++) {
-            const int idx = kc * S + sa, a = idx % RING, ua = idx / RING;
+            const int idx = gk * S + sa, a = idx % RING, ua = idx / RING;
             if (!tc::mbar_wait(&p.fullA[a], ua & 1, kWaitCycles)) { p.abort = 1; tc::mma_commit(&p.done); return; }
             tc::fence_after_sync();
             const uint64_t ad = tc::sdesc_sw128(tc::smem_addr(sA + (size_t)a * 16384));
@@ -382,7 +412,7 @@ __device__ __forceinline__ void pipe_run(Pipe &p, uint8_t *smem, uint32_t tm, co
     else if (threadIdx.x == 32) pipe_mma<TN>(p, sA, sB, tm, L);
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (!tc::mbar_wait(&p.done, 0, kWaitCycles)) p.abort = 1;
+        if (!tc::mbar_wait(&p.done, (uint32_t)(L.round & 1), kWaitCycles)) p.abort = 1;
         if (p.abort) atomicExch(err, (int)NAO_ERR_TIMEOUT);
     }
     __syncthreads();
@@ -510,6 +540,9 @@ __global__ void __launch_bounds__(128, 1) h_tc_kernel(DevSystem s, const HWork *
     tc_teardown(tm);
 }
 
+// One CTA per (batch, 128-point tile): the TN-function tiles J = 0 .. nJ-1 one after another
+// (tensor memory holds one tile's accumulators), each epilogue adding its part of n_q in
+// registers; the CTA then stores n for its points (no atomics: one CTA owns each point).
 template <int TN>
 __global__ void __launch_bounds__(128, 1) n_tc_kernel(DevSystem s, const HWork *__restrict__ work, int32_t w0,
                                                      const uint8_t *__restrict__ slices, const int64_t *__restrict__ sl_off,
@@ -518,7 +551,7 @@ __global__ void __launch_bounds__(128, 1) n_tc_kernel(DevSystem s, const HWork *
     extern __shared__ uint8_t smem_dyn[];
     __shared__ Pipe pp;
     uint8_t *smem = align1024(smem_dyn);
-    const HWork it = work[w0 + blockIdx.x];  // batch, 128-point tile, TN-function tile
+    const HWork it = work[w0 + blockIdx.x];  // batch, 128-point tile, number of TN-function tiles
     const int b = it.batch, m = s.sys.bmol[b];
     const int p0 = s.batch_off[b], P = s.batch_off[b + 1] - p0;
     const int Ppad = (P + NAO_PPAD - 1) & ~(NAO_PPAD - 1);
@@ -527,46 +560,57 @@ __global__ void __launch_bounds__(128, 1) n_tc_kernel(DevSystem s, const HWork *
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t tm = tc_setup(pp);
     const uint8_t *base = slices + sl_off[b];
-    LoopArgs L;
-    L.a0 = base + G.nA_block(0, 0) + (size_t)it.ti * 128 * 128;
-    L.a_s = (size_t)G.n_kcN * G.P16 * 128;
-    L.a_kc = (size_t)G.P16 * 128;
-    L.b0 = base + G.nB_block(S, 0, 0) + (size_t)it.tj * TN * 128;
-    L.b_s = (size_t)G.n_kcN * G.R16 * 128;
-    L.b_kc = (size_t)G.R16 * 128;
-    L.a_bytes = (uint32_t)min(128, G.P16 - it.ti * 128) * 128u;
-    L.b_bytes = (uint32_t)min(TN, G.R16 - it.tj * TN) * 128u;
-    // P' is zero for basis functions beyond tile J, so K stops at TN (J + 1)
-    const int nk = ((it.tj + 1) * TN + 63) / 64;
-    L.n_kc = nk < G.n_kcN ? nk : G.n_kcN;
-    L.neg16 = 0;
-    L.S = S;
-    pipe_run<TN>(pp, smem, tm, L, err);
-    if (!pp.abort) {
-        const int q = it.ti * 128 + warp * 32 + lane;
-        const bool row_ok = q < P;
-        const int eq = row_ok ? expo_q[p0 + q] : -10000;
-        const int eb = expo_b[b];
-        const double *E = scratch + s.scr_off[b];
-        const uint32_t tm_row = tm + ((uint32_t)(warp * 32) << 16);
-        double part_hi = 0.0, part_lo = 0.0, part_lo2 = 0.0;
-        for (int c0 = 0; c0 < TN; c0 += 16) {
+    const int q = it.ti * 128 + warp * 32 + lane;
+    const bool row_ok = q < P;
+    const double *E = scratch + s.scr_off[b];
+    const uint32_t tm_row = tm + ((uint32_t)(warp * 32) << 16);
+    double part_hi = 0.0, part_lo = 0.0, part_lo2 = 0.0;
+    int c0 = 0;
+    for (int J = 0; J < it.tj; J++) {
+        LoopArgs L;
+        L.a0 = base + G.nA_block(0, 0) + (size_t)it.ti * 128 * 128;
+        L.a_s = (size_t)G.n_kcN * G.P16 * 128;
+        L.a_kc = (size_t)G.P16 * 128;
+        L.b0 = base + G.nB_block(S, 0, 0) + (size_t)J * TN * 128;
+        L.b_s = (size_t)G.n_kcN * G.R16 * 128;
+        L.b_kc = (size_t)G.R16 * 128;
+        L.a_bytes = (uint32_t)min(128, G.P16 - it.ti * 128) * 128u;
+        L.b_bytes = (uint32_t)min(TN, G.R16 - J * TN) * 128u;
+        // P' is zero for basis functions beyond tile J, so K stops at TN (J + 1)
+        const int nk = ((J + 1) * TN + 63) / 64;
+        L.n_kc = nk < G.n_kcN ? nk : G.n_kcN;
+        L.neg16 = 0;
+        L.S = S;
+        L.c0 = c0;
+        L.round = J;
+        if (J > 0) {  // the previous tile's accumulators have been read by every thread
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+        }
+        pipe_run<TN>(pp, smem, tm, L, err);
+        if (pp.abort) break;
+        c0 += L.n_kc;
+        for (int cc = 0; cc < TN; cc += 16) {
             Parts16 v;
-            combine16<TN>(tm_row, c0, S, v);
+            combine16<TN>(tm_row, cc, S, v);
 #pragma unroll
             for (int jj = 0; jj < 16; jj++) {
-                const int j = it.tj * TN + c0 + jj;
+                const int j = J * TN + cc + jj;
                 if (row_ok && j < N) {
                     const double f = E[(int64_t)j * Ppad + q];
                     part_hi = fma((double)v.hi[jj], f, part_hi);
                     part_lo = fma((double)v.lo[jj], f, part_lo);
-                    part_lo2 = fma((double)v.lo2[jj], f, part_lo2);
+                    if (TN != 48) part_lo2 = fma((double)v.lo2[jj], f, part_lo2);
                 }
             }
         }
-        if (row_ok && eq > -10000 && eb > -10000)
-            atomicAdd(n_at(s, m, p0 + q), fma(part_hi, pow2(eq + eb - 48),
-                                              fma(part_lo, pow2(eq + eb - 66), part_lo2 * pow2(eq + eb - 84))));
+    }
+    if (!pp.abort && row_ok) {
+        const int eq = expo_q[p0 + q], eb = expo_b[b];
+        *n_at(s, m, p0 + q) = (eq > -10000 && eb > -10000)
+                                  ? fma(part_hi, pow2(eq + eb - 48), fma(part_lo, pow2(eq + eb - 66), part_lo2 * pow2(eq + eb - 84)))
+                                  : 0.0;
     }
     tc_teardown(tm);
 }
