@@ -333,12 +333,17 @@ def main():
                         "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}
         roofline.update({"launches": launches, "avg_launch_ms": fam_ms / max(launches, 1)})
         tk = (fam, int(g.split_slices) if prec == "split" else 0)
-        if tk in TRAFFIC_PER_FLOP_H and launches:
+        all48 = prec != "split" or bool(np.all(nao.nao_get_tuning(g.h)[0][np.diff(g.batches()[2]) > 0] == 48))
+        if tk in TRAFFIC_PER_FLOP_H and launches and all48:
             per_flop, src = TRAFFIC_PER_FLOP_H[tk]
             roofline["traffic"] = per_flop * info.flops_h * args.steps / launches
             roofline["traffic_unit"] = "bytes per launch"
             roofline["traffic_source"] = src + " (diamond8 capture scaled by FLOP_H per launch)"
     gpu_launches = int(sum(l for l, _ in prof.values()))
+    tuning = None
+    if prec == "split":
+        tw, timed = nao.nao_get_tuning(g.h)
+        tuning = {"buckets_timed": timed, "batches_tile48": int(np.sum(tw == 48)), "batches_tile32": int(np.sum(tw == 32))}
 
     line = {
         "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
@@ -354,7 +359,7 @@ def main():
         "p50_ms": statistics.median(step_ms), "p99_ms": float(np.percentile(step_ms, 99)),
         "gflops_algorithmic": (info.flops_h + info.flops_n) / (total_ms / args.steps / 1e3) / 1e9,
         "create_s": create_s,
-        "roofline": roofline, "gpu_launches": gpu_launches, "clocks": clocks,
+        "roofline": roofline, "gpu_launches": gpu_launches, "clocks": clocks, "tuning": tuning,
         "kernel_ms_per_step": {k: ms / args.steps for k, (l, ms) in prof.items() if l},
     }
 

@@ -105,7 +105,10 @@ typedef struct {
                                  the graph, ordered after the caller's stream's earlier work and
                                  before its later work (events). Not used while profiling.
                                  Default 0 (plain launches on the caller's stream). */
-    int32_t reserved0;        /* must be 0 */
+    int32_t autotune;         /* 1 (default): the first NAO_SPLIT Hamiltonian call times 128x48 against
+                                 128x32 tensor-core tiles for each (N_b, P_b) bucket of the batch-size
+                                 histogram (nao_get_tuning reports the result); 0: a fixed rule (48
+                                 where S <= 10 and N_b > 32, else 32). */
 } nao_options;
 
 typedef struct {
@@ -146,17 +149,24 @@ nao_status nao_grid_create(const nao_system_desc *desc, const nao_options *opts,
  * over the union of their batches). Global numbering: basis functions, points and atoms
  * of system m follow those of systems 0..m-1; nao_get_info, nao_export_batches and
  * nao_evaluate_batch use it. descs: host array [n_systems], each as for nao_grid_create;
- * n_systems >= 1. The single-system calls (nao_integrate_h, nao_update_density and their
- * host and noalloc forms) require n_systems == 1; use the _many forms otherwise.
+ * n_systems >= 1. max_batch_points: host array [n_systems] of per-system batch sizes B
+ * (1..1024), or NULL for options.max_batch_points everywhere. The single-system calls
+ * (nao_integrate_h, nao_update_density and their host and noalloc forms) require
+ * n_systems == 1; use the _many forms otherwise.
  * Errors: as nao_grid_create; NAO_ERR_INVALID_ARG if the radial grids differ.              */
-nao_status nao_grid_create_many(const nao_system_desc *descs, int32_t n_systems, const nao_options *opts,
-                                nao_grid **out);
+nao_status nao_grid_create_many(const nao_system_desc *descs, int32_t n_systems, const int32_t *max_batch_points,
+                                const nao_options *opts, nao_grid **out);
 
 /* Basis and point ranges of system m in the global numbering: basis functions
  * basis_offset .. basis_offset+n_basis-1, points point_offset .. point_offset+n_points-1,
  * batches batch_begin .. batch_end-1. Any output pointer may be NULL.                      */
 nao_status nao_get_system(const nao_grid *g, int32_t m, int64_t *basis_offset, int64_t *n_basis,
                           int64_t *point_offset, int64_t *n_points, int64_t *batch_begin, int64_t *batch_end);
+
+/* Split-path tile width chosen for every batch (host array [n_batches]; 48 or 32, 0 before the
+ * first NAO_SPLIT call) and the number of histogram buckets the autotuner timed (-1 while
+ * tuning is pending). Either pointer may be NULL.                                            */
+nao_status nao_get_tuning(const nao_grid *g, int32_t *tile_width, int32_t *buckets_timed);
 
 /* Release the handle and all its device memory. NULL-safe. Synchronises the device work
  * the handle has enqueued before freeing.                                                */

@@ -382,6 +382,19 @@ nao_status build(nao_grid *g, const nao_system_desc *descs, int32_t n_sys, const
     for (int f = 0; f < g->n_fn; f++)
         nao_spline_coefficients(fn_tab.data() + (size_t)f * nr, nr, coef.data() + (size_t)f * (nr - 1) * 4);
     std::vector<float> coef32(coef.begin(), coef.end());
+    // Segments whose cubic is ill-conditioned (coefficient magnitudes above 4x the smaller end
+    // value, or above 4x the smaller end slope: the decaying tails of steep functions, the
+    // approach to the cutoff, extrema) lose more than a few FP32 ulps to cancellation; the FP32
+    // path evaluates them from the FP64 coefficients.
+    std::vector<uint8_t> seg64((size_t)g->n_fn * (nr - 1), 0);
+    for (size_t q = 0; q < seg64.size(); q++) {
+        const double *c = coef.data() + 4 * q;
+        const double y0 = std::fabs(c[0]), y1 = std::fabs(c[0] + c[1] + c[2] + c[3]);
+        const double d0 = std::fabs(c[1]), d1 = std::fabs(c[1] + 2.0 * c[2] + 3.0 * c[3]);
+        const double sv = std::fabs(c[0]) + std::fabs(c[1]) + std::fabs(c[2]) + std::fabs(c[3]);
+        const double sd = std::fabs(c[1]) + 2.0 * std::fabs(c[2]) + 3.0 * std::fabs(c[3]);
+        seg64[q] = (sv > 4.0 * std::min(y0, y1) || sd > 4.0 * std::min(d0, d1)) ? 1 : 0;
+    }
     std::vector<double> inv_rk((size_t)nr);
     for (int k = 0; k < nr; k++) inv_rk[(size_t)k] = 1.0 / (g->r0 * std::exp((double)k * g->delta));
 
@@ -448,7 +461,9 @@ nao_status build(nao_grid *g, const nao_system_desc *descs, int32_t n_sys, const
     AtomGroup *d_agrp;
     int32_t *d_agrp_off;
     int64_t *d_scr_off;
+    uint8_t *d_seg64;
     if ((st = upload(g, &d_coef, coef.data(), coef.size())) || (st = upload(g, &d_coef32, coef32.data(), coef32.size())) ||
+        (st = upload(g, &d_seg64, seg64.data(), seg64.size())) ||
         (st = upload(g, &d_inv_rk, inv_rk.data(), inv_rk.size())) ||
         (st = upload(g, &d_rc, fn_cut.data(), fn_cut.size())) ||
         (st = upload(g, &d_rel_off, rel_off32.data(), rel_off32.size())) ||
@@ -480,6 +495,7 @@ nao_status build(nao_grid *g, const nao_system_desc *descs, int32_t n_sys, const
     s.coef = d_coef;
     s.coef_f32 = d_coef32;
     s.inv_rk = d_inv_rk;
+    s.seg64 = d_seg64;
     s.fn_rc = d_rc;
     s.px = d_px;
     s.py = d_py;
@@ -558,8 +574,69 @@ nao_status check_prec(nao_precision p) {
     return NAO_OK;
 }
 
+// Split-path tile width of a batch before (or without) autotuning: 32 where 48 cannot hold
+// the S accumulator groups in tensor memory or where the batch has at most 32 functions.
+int default_tn(int S, int N) { return (S > 10 || N <= 32) ? 32 : 48; }
+
+// The split work lists for the current per-batch tile widths, per split chunk and width:
+// H tile pairs (batch, 128-row tile I, TN-column tile J) crossing the upper triangle, and
+// density items (batch, 128-point tile, number of TN-function tiles).
+nao_status split_lists(nao_grid *g) {
+    const int S = g->split_S;
+    std::vector<HWork> hw[2], nw[2];
+    for (auto &c : g->split_chunks) {
+        for (int k = 0; k < 2; k++) {
+            c.hw0[k] = (int32_t)hw[k].size();
+            c.nw0[k] = (int32_t)nw[k].size();
+        }
+        for (int32_t b = c.b0; b < c.b1; b++) {
+            const int P = g->Pb[b], N = g->Nb[b];
+            if (N == 0) continue;
+            const int TN = g->split_tn[b], k = TN == 48 ? 0 : 1;
+            const SplitGeom G(P, N, S, TN);
+            const int nI = (N + 127) / 128, nJ = (N + TN - 1) / TN;
+            for (int I = 0; I < nI; I++)
+                for (int J = 0; J < nJ; J++)
+                    if (I * 128 <= J * TN + TN - 1) hw[k].push_back({b, I, J, 0});
+            for (int Q = 0; Q < G.n_qt; Q++) nw[k].push_back({b, Q, G.n_jtN, 0});  // all J tiles in one CTA
+        }
+        for (int k = 0; k < 2; k++) {
+            c.hw1[k] = (int32_t)hw[k].size();
+            c.nw1[k] = (int32_t)nw[k].size();
+        }
+    }
+    // one array per list: width-48 items, then width-32 items (offsets shifted below)
+    const int64_t nh = (int64_t)(hw[0].size() + hw[1].size()), nn = (int64_t)(nw[0].size() + nw[1].size());
+    if (nh > g->cap_split_hw || nn > g->cap_split_nw)
+        return fail(NAO_ERR_INTERNAL, "split work lists exceed their planned capacity");
+    for (auto &c : g->split_chunks) {
+        c.hw0[1] += (int32_t)hw[0].size();
+        c.hw1[1] += (int32_t)hw[0].size();
+        c.nw0[1] += (int32_t)nw[0].size();
+        c.nw1[1] += (int32_t)nw[0].size();
+    }
+    hw[0].insert(hw[0].end(), hw[1].begin(), hw[1].end());
+    nw[0].insert(nw[0].end(), nw[1].begin(), nw[1].end());
+    if (!hw[0].empty())
+        NAO_CUDA(cudaMemcpyAsync(g->d_split_hw, hw[0].data(), hw[0].size() * sizeof(HWork), cudaMemcpyHostToDevice, g->setup));
+    if (!nw[0].empty())
+        NAO_CUDA(cudaMemcpyAsync(g->d_split_nw, nw[0].data(), nw[0].size() * sizeof(HWork), cudaMemcpyHostToDevice, g->setup));
+    NAO_CUDA(cudaMemcpyAsync(g->d_split_tn, g->split_tn.data(), g->split_tn.size() * sizeof(int32_t),
+                             cudaMemcpyHostToDevice, g->setup));
+    NAO_CUDA(cudaStreamSynchronize(g->setup));
+    g->n_split_hw = nh;
+    g->n_split_nw = nn;
+    // recorded graphs hold the old lists' launch ranges
+    if (!g->graphs.empty()) {
+        if (g->gstream) NAO_CUDA(cudaStreamSynchronize(g->gstream));
+        for (auto &kv : g->graphs) cudaGraphExecDestroy(kv.second);
+        g->graphs.clear();
+    }
+    return NAO_OK;
+}
+
 // Plan and allocate the split path: sub-chunks of the evaluation chunks whose slices fit the
-// slice budget, work lists of 128 x 64 tiles, per-batch slice offsets and exponent arrays.
+// slice budget, per-batch slice offsets and exponent arrays, work lists.
 nao_status split_setup(nao_grid *g) {
     if (g->split_ready) return NAO_OK;
     const int S = g->opt.split_slices;
@@ -577,10 +654,11 @@ nao_status split_setup(nao_grid *g) {
     const int64_t budget = std::max<int64_t>(g->opt.scratch_bytes > 0 ? 2 * g->opt.scratch_bytes : (int64_t(4) << 30),
                                              int64_t(1) << 20);
     std::vector<int64_t> off_h(g->n_batches, 0), off_n(g->n_batches, 0);
-    std::vector<HWork> hw, nw;
-    int64_t max_used = 0;
+    int64_t max_used = 0, cap_h = 0, cap_n = 0;
+    g->split_tn.assign(g->n_batches, 32);
     for (const Chunk &c : g->chunks) {
-        nao_grid::SplitChunk cur{c.b0, c.b0, (int32_t)hw.size(), 0, (int32_t)nw.size(), 0, 0, 0};
+        nao_grid::SplitChunk cur{};
+        cur.b0 = cur.b1 = c.b0;
         int64_t used = 0;
         for (int32_t b = c.b0; b < c.b1; b++) {
             const int P = g->Pb[b], N = g->Nb[b];
@@ -588,34 +666,36 @@ nao_status split_setup(nao_grid *g) {
             const int64_t need = N == 0 ? 0 : (int64_t)std::max(G.h_bytes(S), G.n_bytes(S));
             if (used + need > budget && b > cur.b0) {
                 cur.b1 = b;
-                cur.hw1 = (int32_t)hw.size();
-                cur.nw1 = (int32_t)nw.size();
                 g->split_chunks.push_back(cur);
-                cur = nao_grid::SplitChunk{b, b, (int32_t)hw.size(), 0, (int32_t)nw.size(), 0, 0, 0};
+                cur = nao_grid::SplitChunk{};
+                cur.b0 = cur.b1 = b;
                 used = 0;
             }
             off_h[b] = used;
             off_n[b] = used;
             used += need;
             max_used = std::max(max_used, used);
+            g->split_tn[b] = default_tn(S, N);
             if (N > 0) {
                 cur.max_rt = std::max<int32_t>(cur.max_rt, G.h_slice_tiles());
                 cur.max_qt = std::max<int32_t>(cur.max_qt, G.n_qt);
-                const int TN = nao_split_tn(S);
-                const int nI = (N + 127) / 128, nJ = (N + TN - 1) / TN;
-                for (int I = 0; I < nI; I++)
-                    for (int J = 0; J < nJ; J++)
-                        if (I * 128 <= J * TN + TN - 1) hw.push_back({b, I, J, 0});
-                for (int Q = 0; Q < G.n_qt; Q++) nw.push_back({b, Q, G.n_jtN, 0});  // all J tiles in one CTA
+                // list capacity: the larger of the two widths' item counts
+                int64_t best_h = 0;
+                for (int TN : {48, 32}) {
+                    if (TN == 48 && S > 10) continue;
+                    const int nI = (N + 127) / 128, nJ = (N + TN - 1) / TN;
+                    int64_t cnt = 0;
+                    for (int I = 0; I < nI; I++)
+                        for (int J = 0; J < nJ; J++) cnt += (I * 128 <= J * TN + TN - 1);
+                    best_h = std::max(best_h, cnt);
+                }
+                cap_h += best_h;
+                cap_n += G.n_qt;
             }
         }
         cur.b1 = c.b1;
-        cur.hw1 = (int32_t)hw.size();
-        cur.nw1 = (int32_t)nw.size();
         g->split_chunks.push_back(cur);
     }
-    g->n_split_hw = (int64_t)hw.size();
-    g->n_split_nw = (int64_t)nw.size();
     nao_status st;
     if ((st = dev_alloc(g, &g->d_slices, (size_t)std::max<int64_t>(max_used, 1024))) ||
         (st = upload(g, &g->d_sl_off_h, off_h.data(), off_h.size())) ||
@@ -624,12 +704,113 @@ nao_status split_setup(nao_grid *g) {
         (st = dev_alloc(g, &g->d_expo_q, (size_t)g->n_points)) ||
         (st = dev_alloc(g, &g->d_expo_b, (size_t)g->n_batches)) ||
         (st = dev_alloc(g, &g->d_neg16, (size_t)g->n_batches)) ||
-        (st = upload(g, &g->d_split_hw, hw.data(), hw.size())) || (st = upload(g, &g->d_split_nw, nw.data(), nw.size())))
+        (st = dev_alloc(g, &g->d_split_tn, (size_t)g->n_batches)) ||
+        (st = dev_alloc(g, &g->d_split_hw, (size_t)std::max<int64_t>(cap_h, 1))) ||
+        (st = dev_alloc(g, &g->d_split_nw, (size_t)std::max<int64_t>(cap_n, 1))))
         return st;
-    NAO_CUDA(cudaStreamSynchronize(g->setup));
+    g->cap_split_hw = cap_h;
+    g->cap_split_nw = cap_n;
     g->split_S = S;
+    g->split_tuned = S > 10 || !g->opt.autotune;  // only one width exists, or tuning is off
+    if ((st = split_lists(g))) return st;
     g->split_ready = true;
     return NAO_OK;
+}
+
+// Autotuner of the split path's tile width, driven by the batch-size histogram: batches are
+// bucketed by (basis functions N_b, points P_b); for every bucket the H contraction of the
+// bucket's batches in the first split chunks is timed with 128x48 and with 128x32 tiles (CUDA
+// events on the call's stream, the best of three runs after a warm-up, without the scatter), and
+// 32 is kept for all batches of the bucket when it is at least 3 % faster (the density uses the
+// same width). Buckets that
+// none of those chunks contains keep the default rule. Runs once per handle, inside the first
+// split Hamiltonian call (the evaluation and slicing it needs use that call's v and terms).
+int tn_bucket(int N, int P) {
+    static const int ne[] = {32, 64, 96, 128, 192, 256, 384, 512, 768};
+    static const int pe[] = {64, 128, 192, 256, 336};
+    int a = 0, c = 0;
+    while (a < 9 && N > ne[a]) a++;
+    while (c < 5 && P > pe[c]) c++;
+    return a * 6 + c;
+}
+
+nao_status split_tune(nao_grid *g, uint32_t terms, cudaStream_t st) {
+    if (g->split_tuned) return NAO_OK;
+    const int S = g->split_S;
+    const DevSystem &s = g->sys;
+    constexpr int kBuckets = 60, kChunks = 3;
+    std::vector<int> bucket(g->n_batches, -1), total(kBuckets, 0);
+    for (int64_t b = 0; b < g->n_batches; b++)
+        if (g->Nb[b] > 32) {  // N_b <= 32: one 32-wide tile is never slower than a 48-wide one
+            bucket[b] = tn_bucket(g->Nb[b], g->Pb[b]);
+            total[bucket[b]]++;
+        }
+    std::vector<int> choice(kBuckets, 0);
+    cudaEvent_t e0, e1;
+    NAO_CUDA(cudaEventCreate(&e0));
+    NAO_CUDA(cudaEventCreate(&e1));
+    nao_status rs = NAO_OK;
+    int timed = 0;
+    for (size_t ci = 0; ci < g->split_chunks.size() && (int)ci < kChunks && rs == NAO_OK; ci++) {
+        const auto &c = g->split_chunks[ci];
+        bool any = false;
+        for (int32_t b = c.b0; b < c.b1; b++) any = any || (bucket[b] >= 0 && !choice[bucket[b]]);
+        if (!any) continue;
+        cudaError_t ce = launch_eval(s, c.b0, c.b1, NAO_FP64, true, g->d_scratch, st);
+        if (ce == cudaSuccess)
+            ce = launch_slice_h(s, c.b0, c.b1, c.max_rt, g->d_scratch, terms, g->d_slices, g->d_sl_off_h, g->d_expo_h,
+                                g->d_neg16, S, st);
+        if (ce != cudaSuccess) { rs = cuda_fail(ce, "autotune evaluation"); break; }
+        for (int k = 0; k < kBuckets && rs == NAO_OK; k++) {
+            if (choice[k] || !total[k]) continue;
+            float ms[2] = {0.0f, 0.0f};
+            int64_t n_items = 0;
+            for (int w = 0; w < 2 && rs == NAO_OK; w++) {
+                const int TN = w == 0 ? 48 : 32;
+                std::vector<HWork> items;
+                for (int32_t b = c.b0; b < c.b1; b++) {
+                    if (bucket[b] != k) continue;
+                    const int N = g->Nb[b], nI = (N + 127) / 128, nJ = (N + TN - 1) / TN;
+                    for (int I = 0; I < nI; I++)
+                        for (int J = 0; J < nJ; J++)
+                            if (I * 128 <= J * TN + TN - 1) items.push_back({b, I, J, 0});
+                }
+                n_items = (int64_t)items.size();
+                if (items.empty()) break;
+                if ((int64_t)items.size() > g->cap_tune_hw) {
+                    if ((rs = dev_alloc(g, &g->d_tune_hw, items.size()))) break;
+                    g->cap_tune_hw = (int64_t)items.size();
+                }
+                ce = cudaMemcpyAsync(g->d_tune_hw, items.data(), items.size() * sizeof(HWork), cudaMemcpyHostToDevice,
+                                     g->setup);
+                if (ce == cudaSuccess) ce = cudaStreamSynchronize(g->setup);
+                ms[w] = 1e30f;
+                for (int rep = 0; rep < 4 && ce == cudaSuccess; rep++) {  // the first run warms up
+                    ce = cudaEventRecord(e0, st);
+                    if (ce == cudaSuccess)
+                        ce = launch_h_tc(s, g->d_tune_hw, 0, (int32_t)items.size(), g->d_slices, g->d_sl_off_h,
+                                         g->d_expo_h, g->d_neg16, S, TN, 0, g->d_err, st);
+                    if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
+                    if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+                    float t = 0.0f;
+                    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, e0, e1);
+                    if (rep > 0) ms[w] = std::min(ms[w], t);
+                }
+                if (ce != cudaSuccess) rs = cuda_fail(ce, "autotune timing");
+            }
+            if (rs != NAO_OK || n_items == 0) continue;
+            choice[k] = ms[1] < 0.97f * ms[0] ? 32 : 48;  // 32 only when clearly faster
+            timed++;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rs != NAO_OK) return rs;
+    for (int64_t b = 0; b < g->n_batches; b++)
+        if (bucket[b] >= 0 && choice[bucket[b]]) g->split_tn[b] = choice[bucket[b]];
+    g->tune_buckets = timed;
+    g->split_tuned = true;
+    return split_lists(g);
 }
 
 // This call's pointer tables (sections: 0 H, 1 v, 2 P, 3 n, 4 N_e; one entry per system),
@@ -687,10 +868,11 @@ nao_status enqueue_h(nao_grid *g, uint32_t terms, nao_precision prec, cudaStream
                 return launch_slice_h(s, c.b0, c.b1, c.max_rt, g->d_scratch, terms, g->d_slices, g->d_sl_off_h,
                                       g->d_expo_h, g->d_neg16, S, st);
             }));
-            NAO_CUDA(timed(g, NAO_K_H_SPLIT, st, [&] {
-                return launch_h_tc(s, g->d_split_hw, c.hw0, c.hw1 - c.hw0, g->d_slices, g->d_sl_off_h, g->d_expo_h,
-                                   g->d_neg16, S, g->d_err, st);
-            }));
+            for (int k = 0; k < 2; k++)
+                NAO_CUDA(timed(g, NAO_K_H_SPLIT, st, [&] {
+                    return launch_h_tc(s, g->d_split_hw, c.hw0[k], c.hw1[k] - c.hw0[k], g->d_slices, g->d_sl_off_h,
+                                       g->d_expo_h, g->d_neg16, S, k == 0 ? 48 : 32, 1, g->d_err, st);
+                }));
         }
     } else {
         for (const Chunk &c : g->chunks) {
@@ -713,12 +895,13 @@ nao_status enqueue_n(nao_grid *g, nao_precision prec, bool want_ne, cudaStream_t
             NAO_CUDA(timed(g, NAO_K_EVAL_PHI, st, [&] { return launch_eval(s, c.b0, c.b1, NAO_FP64, false, g->d_scratch, st); }));
             NAO_CUDA(timed(g, NAO_K_SLICE, st, [&] {
                 return launch_slice_n(s, c.b0, c.b1, c.max_qt, g->d_scratch, g->d_slices, g->d_sl_off_n, g->d_expo_q,
-                                      g->d_expo_b, S, st);
+                                      g->d_expo_b, g->d_split_tn, S, st);
             }));
-            NAO_CUDA(timed(g, NAO_K_N_SPLIT, st, [&] {
-                return launch_n_tc(s, g->d_split_nw, c.nw0, c.nw1 - c.nw0, g->d_slices, g->d_sl_off_n, g->d_expo_q,
-                                   g->d_expo_b, g->d_scratch, S, g->d_err, st);
-            }));
+            for (int k = 0; k < 2; k++)
+                NAO_CUDA(timed(g, NAO_K_N_SPLIT, st, [&] {
+                    return launch_n_tc(s, g->d_split_nw, c.nw0[k], c.nw1[k] - c.nw0[k], g->d_slices, g->d_sl_off_n,
+                                       g->d_expo_q, g->d_expo_b, g->d_scratch, S, k == 0 ? 48 : 32, g->d_err, st);
+                }));
         }
         if (want_ne) NAO_CUDA(launch_wn_partial(s, g->d_dwork, 0, (int32_t)g->n_dwork, g->d_ne_part, st));
     } else {
@@ -739,6 +922,7 @@ nao_status run_h(nao_grid *g, uint32_t terms, nao_precision prec, cudaStream_t s
     nao_status rs;
     if (prec == NAO_SPLIT && (rs = split_setup(g))) return rs;
     if ((rs = upload_tables(g, 0, 2, st))) return rs;
+    if (prec == NAO_SPLIT && (rs = split_tune(g, terms, st))) return rs;
     const uint64_t key = (uint64_t)1 << 40 | (uint64_t)prec << 8 | terms;
     return run_maybe_graph(g, key, st, [&](cudaStream_t s2) { return enqueue_h(g, terms, prec, s2); });
 }
@@ -771,11 +955,12 @@ nao_status nao_default_options(nao_options *o) {
     o->device = -1;
     o->scratch_bytes = 0;
     o->capture_graph = 0;
-    o->reserved0 = 0;
+    o->autotune = 1;
     return NAO_OK;
 }
 
-static nao_status create(const nao_system_desc *descs, int32_t n_sys, const nao_options *opts, nao_grid **out) {
+static nao_status create(const nao_system_desc *descs, int32_t n_sys, const int32_t *batch_points,
+                         const nao_options *opts, nao_grid **out) {
     if (!out) return fail(NAO_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!descs) return fail(NAO_ERR_INVALID_ARG, "desc is NULL");
@@ -783,9 +968,14 @@ static nao_status create(const nao_system_desc *descs, int32_t n_sys, const nao_
     nao_options o;
     nao_default_options(&o);
     if (opts) o = *opts;
-    if (o.reserved0 != 0) return fail(NAO_ERR_INVALID_ARG, "options.reserved0 must be 0");
+    if (o.autotune != 0 && o.autotune != 1) return fail(NAO_ERR_INVALID_ARG, "options.autotune not 0/1");
     if (o.capture_graph != 0 && o.capture_graph != 1) return fail(NAO_ERR_INVALID_ARG, "options.capture_graph not 0/1");
     nao_status st;
+    if (batch_points)
+        for (int32_t m = 0; m < n_sys; m++)
+            if (batch_points[m] < 1 || batch_points[m] > NAO_MAX_BATCH)
+                return fail(NAO_ERR_INVALID_ARG, "max_batch_points[" + std::to_string(m) + "] outside 1.." +
+                                                     std::to_string(NAO_MAX_BATCH));
     for (int32_t m = 0; m < n_sys; m++)
         if ((st = validate(&descs[m], o)) != NAO_OK) {
             if (n_sys > 1) g_last_error = "system " + std::to_string(m) + ": " + g_last_error;
@@ -807,7 +997,7 @@ static nao_status create(const nao_system_desc *descs, int32_t n_sys, const nao_
     g->opt.device = dev;
     try {
         st = init_streams(g);
-        if (st == NAO_OK) st = build(g, descs, n_sys, nullptr);
+        if (st == NAO_OK) st = build(g, descs, n_sys, batch_points);
     } catch (const std::bad_alloc &) {
         st = fail(NAO_ERR_OUT_OF_MEMORY, "host allocation failed");
     } catch (...) {
@@ -822,12 +1012,12 @@ static nao_status create(const nao_system_desc *descs, int32_t n_sys, const nao_
 }
 
 nao_status nao_grid_create(const nao_system_desc *desc, const nao_options *opts, nao_grid **out) {
-    return create(desc, 1, opts, out);
+    return create(desc, 1, nullptr, opts, out);
 }
 
-nao_status nao_grid_create_many(const nao_system_desc *descs, int32_t n_systems, const nao_options *opts,
-                                nao_grid **out) {
-    return create(descs, n_systems, opts, out);
+nao_status nao_grid_create_many(const nao_system_desc *descs, int32_t n_systems, const int32_t *max_batch_points,
+                                const nao_options *opts, nao_grid **out) {
+    return create(descs, n_systems, max_batch_points, opts, out);
 }
 
 nao_status nao_get_system(const nao_grid *g, int32_t m, int64_t *basis_offset, int64_t *n_basis, int64_t *point_offset,
@@ -895,6 +1085,17 @@ static nao_status check_single(const nao_grid *g) {
 
 static nao_status check_terms(uint32_t terms) {
     if (terms == 0 || (terms & ~3u)) return fail(NAO_ERR_INVALID_ARG, "bad terms");
+    return NAO_OK;
+}
+
+nao_status nao_get_tuning(const nao_grid *g, int32_t *tile_width, int32_t *buckets_timed) {
+    nao_status st = check_handle(g);
+    if (st) return st;
+    if (tile_width) {
+        if (g->split_ready) std::memcpy(tile_width, g->split_tn.data(), g->split_tn.size() * sizeof(int32_t));
+        else std::memset(tile_width, 0, (size_t)g->n_batches * sizeof(int32_t));
+    }
+    if (buckets_timed) *buckets_timed = g->split_tuned ? g->tune_buckets : -1;
     return NAO_OK;
 }
 

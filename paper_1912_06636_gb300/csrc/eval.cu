@@ -85,6 +85,7 @@ __device__ __noinline__ void eval_group(const DevSystem &s, const AtomGroup &ag,
     const double rr = fmax(r, s.r0);
     int k;
     T t;
+    double xk = 0.0;  // FP32 path: r / r_k - 1, for the FP64 re-evaluation of ill-conditioned segments
     if constexpr (std::is_same<T, double>::value) {
         const double sc = log(rr / s.r0) * s.inv_delta;
         k = (int)floor(sc);
@@ -96,59 +97,64 @@ __device__ __noinline__ void eval_group(const DevSystem &s, const AtomGroup &ag,
         const float sa = __logf((float)rr * (float)(1.0 / s.r0)) * (float)s.inv_delta;
         k = (int)floorf(sa);
         k = k < 0 ? 0 : (k > s.n_rgrid - 2 ? s.n_rgrid - 2 : k);
-        const double xk = fma(rr, __ldg(s.inv_rk + k), -1.0);
+        xk = fma(rr, __ldg(s.inv_rk + k), -1.0);
         t = log1pf((float)xk) * (float)s.inv_delta;
     }
     const T dr_scale = T(s.inv_delta / rr);  // dR/dr = dR/ds * inv_delta / rr
     const T u = T(1.0 / r);
-    const T x = T(dx), y = T(dy), z = T(dz), qq = T(r2);
+    const T x = T(dx), y = T(dy), z = T(dz);
+    // The solid harmonics and their gradients are computed in FP64 on both paths (type H): the
+    // recurrences cancel near the nodes of cos(m phi), sin(m phi) and P_l^m(cos theta), where
+    // FP32 (with FP32-rounded x, y, z) loses several ulps; the FP32 path rounds the results once.
+    using H = double;
+    const H xh = dx, yh = dy, zh = dz, qq = r2;
     // A_m + i B_m = (x + i y)^m
-    T A[LMAX + 1], B[LMAX + 1];
-    A[0] = T(1);
-    B[0] = T(0);
+    H A[LMAX + 1], B[LMAX + 1];
+    A[0] = H(1);
+    B[0] = H(0);
 #pragma unroll
     for (int m = 1; m <= LMAX; m++) {
-        A[m] = x * A[m - 1] - y * B[m - 1];
-        B[m] = x * B[m - 1] + y * A[m - 1];
+        A[m] = xh * A[m - 1] - yh * B[m - 1];
+        B[m] = xh * B[m - 1] + yh * A[m - 1];
     }
     // Pi_{l-1}^m (c) and Pi_{l-2}^m (p) with their z and r^2 derivatives
-    T Pc[LMAX + 1], Pcz[LMAX + 1], Pcq[LMAX + 1], Pp[LMAX + 1], Ppz[LMAX + 1], Ppq[LMAX + 1];
+    H Pc[LMAX + 1], Pcz[LMAX + 1], Pcq[LMAX + 1], Pp[LMAX + 1], Ppz[LMAX + 1], Ppq[LMAX + 1];
 #pragma unroll
-    for (int m = 0; m <= LMAX; m++) Pc[m] = Pcz[m] = Pcq[m] = Pp[m] = Ppz[m] = Ppq[m] = T(0);
+    for (int m = 0; m <= LMAX; m++) Pc[m] = Pcz[m] = Pcq[m] = Pp[m] = Ppz[m] = Ppq[m] = H(0);
     int ri = ag.r0;
     const int re = ag.r0 + ag.nr;
     T ul = T(1);  // u^l
 #pragma unroll
     for (int l = 0; l <= LMAX; l++) {
-        T S[2 * LMAX + 1], Gx[2 * LMAX + 1], Gy[2 * LMAX + 1], Gz[2 * LMAX + 1];
+        H S[2 * LMAX + 1], Gx[2 * LMAX + 1], Gy[2 * LMAX + 1], Gz[2 * LMAX + 1];
 #pragma unroll
         for (int m = 0; m <= l; m++) {
-            T p, pz, pq;
+            H p, pz, pq;
             if (m == l) {
-                p = T(double_factorial_odd(m));
-                pz = pq = T(0);
+                p = H(double_factorial_odd(m));
+                pz = pq = H(0);
             } else if (m == l - 1) {
-                p = T(2 * m + 1) * z * Pc[m];
-                pz = T(2 * m + 1) * Pc[m];
-                pq = T(0);
+                p = H(2 * m + 1) * zh * Pc[m];
+                pz = H(2 * m + 1) * Pc[m];
+                pq = H(0);
             } else {
-                const T c1 = T((double)(2 * l - 1) / (double)(l - m));
-                const T c2 = T((double)(l + m - 1) / (double)(l - m));
-                p = c1 * z * Pc[m] - c2 * qq * Pp[m];
-                pz = c1 * (Pc[m] + z * Pcz[m]) - c2 * qq * Ppz[m];
-                pq = c1 * z * Pcq[m] - c2 * (Pp[m] + qq * Ppq[m]);
+                const H c1 = H((double)(2 * l - 1) / (double)(l - m));
+                const H c2 = H((double)(l + m - 1) / (double)(l - m));
+                p = c1 * zh * Pc[m] - c2 * qq * Pp[m];
+                pz = c1 * (Pc[m] + zh * Pcz[m]) - c2 * qq * Ppz[m];
+                pq = c1 * zh * Pcq[m] - c2 * (Pp[m] + qq * Ppq[m]);
             }
             Pp[m] = Pc[m]; Ppz[m] = Pcz[m]; Ppq[m] = Pcq[m];
             Pc[m] = p; Pcz[m] = pz; Pcq[m] = pq;
-            const T dPx = T(2) * x * pq, dPy = T(2) * y * pq, dPz = pz + T(2) * z * pq;
-            const T kn = T(s.knorm[l][m]);
+            const H dPx = H(2) * xh * pq, dPy = H(2) * yh * pq, dPz = pz + H(2) * zh * pq;
+            const H kn = H(s.knorm[l][m]);
             if (m == 0) {
                 S[l] = kn * p;
                 Gx[l] = kn * dPx;
                 Gy[l] = kn * dPy;
                 Gz[l] = kn * dPz;
             } else {
-                const T fm = T(m);
+                const H fm = H(m);
                 S[l + m] = kn * p * A[m];
                 Gx[l + m] = kn * (dPx * A[m] + p * fm * A[m - 1]);
                 Gy[l + m] = kn * (dPy * A[m] - p * fm * B[m - 1]);
@@ -172,18 +178,29 @@ __device__ __noinline__ void eval_group(const DevSystem &s, const AtomGroup &ag,
                     R = fma(fma(fma(c23.y, t, c23.x), t, c01.y), t, c01.x);
                     dRds = fma(fma(3.0 * c23.y, t, 2.0 * c23.x), t, c01.y);
                 } else {
-                    const float4 c = __ldg(reinterpret_cast<const float4 *>(s.coef_f32 + ((size_t)e.fn * (s.n_rgrid - 1) + k) * 4));
-                    R = fmaf(fmaf(fmaf(c.w, t, c.z), t, c.y), t, c.x);
-                    dRds = fmaf(fmaf(3.0f * c.w, t, 2.0f * c.z), t, c.y);
+                    const size_t seg = (size_t)e.fn * (s.n_rgrid - 1) + k;
+                    if (__ldg(s.seg64 + seg)) {
+                        // ill-conditioned segment: FP64 coefficients and FP64 t
+                        const double t64 = log1p(xk) * s.inv_delta;
+                        const double2 *c = reinterpret_cast<const double2 *>(s.coef + seg * 4);
+                        const double2 c01 = __ldg(c), c23 = __ldg(c + 1);
+                        R = (float)fma(fma(fma(c23.y, t64, c23.x), t64, c01.y), t64, c01.x);
+                        dRds = (float)fma(fma(3.0 * c23.y, t64, 2.0 * c23.x), t64, c01.y);
+                    } else {
+                        const float4 c = __ldg(reinterpret_cast<const float4 *>(s.coef_f32 + seg * 4));
+                        R = fmaf(fmaf(fmaf(c.w, t, c.z), t, c.y), t, c.x);
+                        dRds = fmaf(fmaf(3.0f * c.w, t, 2.0f * c.z), t, c.y);
+                    }
                 }
                 const T g = R * ul;
                 const T gpu = (dRds * dr_scale - T(l) * R * u) * ul * u;  // g'(r) / r
 #pragma unroll
                 for (int m = 0; m < 2 * l + 1; m++) {
-                    fo[m] = OutT(g * S[m]);
-                    xo[m] = OutT(gpu * x * S[m] + g * Gx[m]);
-                    yo[m] = OutT(gpu * y * S[m] + g * Gy[m]);
-                    zo[m] = OutT(gpu * z * S[m] + g * Gz[m]);
+                    const T Sm = T(S[m]);
+                    fo[m] = OutT(g * Sm);
+                    xo[m] = OutT(gpu * x * Sm + g * T(Gx[m]));
+                    yo[m] = OutT(gpu * y * Sm + g * T(Gy[m]));
+                    zo[m] = OutT(gpu * z * Sm + g * T(Gz[m]));
                 }
             } else {
 #pragma unroll

@@ -53,6 +53,7 @@ struct DevSystem {
     const double *coef;       // [n_fn][n_rgrid-1][4] spline coefficients in t
     const float *coef_f32;    // same in FP32
     const double *inv_rk;     // [n_rgrid] 1 / r_k of the logarithmic grid
+    const uint8_t *seg64;     // [n_fn][n_rgrid-1] 1: the FP32 path evaluates this spline segment in FP64
     const double *fn_rc;      // [n_fn]
     const double *px, *py, *pz, *pw;  // points in batch order
     const int32_t *perm;      // batch order -> original index
@@ -107,14 +108,15 @@ __host__ __device__ constexpr int nao_split_tn(int S) { return S <= 10 ? 48 : 32
 struct SplitGeom {
     int n_kc, R16;               // H: K chunks, stored rows
     int n_kcN, P16, n_qt, n_jtN; // density: K chunks, stored A rows, 128-point tiles, TN-row B tiles
-    __host__ __device__ SplitGeom(int P, int N, int S) {
+    __host__ __device__ SplitGeom(int P, int N, int S, int TN = 0) {
+        if (TN == 0) TN = nao_split_tn(S);
         const int Ppad = (P + NAO_PPAD - 1) / NAO_PPAD * NAO_PPAD;
         n_kc = (4 * Ppad + 16 + 63) / 64;
         R16 = (N + 15) / 16 * 16;
         n_kcN = (N + 63) / 64;
         P16 = (P + 15) / 16 * 16;
         n_qt = (P + 127) / 128;
-        n_jtN = (N + nao_split_tn(S) - 1) / nao_split_tn(S);
+        n_jtN = (N + TN - 1) / TN;
     }
     __host__ __device__ size_t h_block(int s, int kc) const { return ((size_t)s * n_kc + kc) * (size_t)R16 * 128; }
     __host__ __device__ size_t h_bytes(int S) const { return (size_t)S * n_kc * (size_t)R16 * 128; }
@@ -182,13 +184,23 @@ struct nao_grid {
     // split (tensor-core) path, set up on its first use
     struct SplitChunk {
         int32_t b0, b1;    // batches (inside one chunk of the evaluation scratch)
-        int32_t hw0, hw1;  // items of the split H list
-        int32_t nw0, nw1;  // items of the split density list
         int32_t max_rt, max_qt;  // grid extents of the slicing kernels
+        // items of the split H and density lists: [0] tile width 48, [1] tile width 32
+        int32_t hw0[2], hw1[2];
+        int32_t nw0[2], nw1[2];
     };
     bool split_ready = false;
     int split_S = 0;
     std::vector<SplitChunk> split_chunks;
+    // tile width (MMA N) of every batch on the split path: a fixed rule until the autotuner has
+    // timed both widths per (N_b, P_b) bucket of the batch-size histogram
+    std::vector<int32_t> split_tn;
+    int32_t *d_split_tn = nullptr;
+    bool split_tuned = false;
+    int32_t tune_buckets = 0;      // buckets the autotuner timed
+    int64_t cap_split_hw = 0, cap_split_nw = 0;
+    HWork *d_tune_hw = nullptr;    // scratch work list of the autotuner
+    int64_t cap_tune_hw = 0;
     uint8_t *d_slices = nullptr;
     int64_t *d_sl_off_h = nullptr, *d_sl_off_n = nullptr;
     int32_t *d_expo_h = nullptr, *d_expo_q = nullptr, *d_expo_b = nullptr;
@@ -244,15 +256,17 @@ cudaError_t split_configure();
 cudaError_t launch_slice_h(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_rt, const double *scratch,
                            uint32_t terms, uint8_t *slices, const int64_t *sl_off, int32_t *expo, int32_t *neg16, int S,
                            cudaStream_t st);
+// tn: tile width 48 (S <= 10 only) or 32; scatter = 0 skips the H scatter (autotuner timing)
 cudaError_t launch_h_tc(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
-                        const int64_t *sl_off, const int32_t *expo, const int32_t *neg16, int S, int32_t *err,
-                        cudaStream_t st);
+                        const int64_t *sl_off, const int32_t *expo, const int32_t *neg16, int S, int tn, int scatter,
+                        int32_t *err, cudaStream_t st);
+// tn_b: per-batch tile width (the P' tiles of the density follow it)
 cudaError_t launch_slice_n(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_qt, const double *scratch,
-                           uint8_t *slices, const int64_t *sl_off, int32_t *expo_q, int32_t *expo_b, int S,
-                           cudaStream_t st);
+                           uint8_t *slices, const int64_t *sl_off, int32_t *expo_q, int32_t *expo_b,
+                           const int32_t *tn_b, int S, cudaStream_t st);
 cudaError_t launch_n_tc(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
                         const int64_t *sl_off, const int32_t *expo_q, const int32_t *expo_b, const double *scratch, int S,
-                        int32_t *err, cudaStream_t st);
+                        int tn, int32_t *err, cudaStream_t st);
 cudaError_t launch_wn_partial(const DevSystem &s, const DWork *work, int32_t w0, int32_t n_work, double *ne_part,
                               cudaStream_t st);
 

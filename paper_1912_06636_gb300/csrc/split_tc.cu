@@ -266,7 +266,8 @@ __global__ void __launch_bounds__(128) slice_nphi_kernel(DevSystem s, int32_t b0
 // digits of rows j (TN-row blocks), K = i (chunks of 64).
 template <int S>
 __global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, uint8_t *__restrict__ slices,
-                                                      const int64_t *__restrict__ sl_off, int32_t *__restrict__ expo_b) {
+                                                      const int64_t *__restrict__ sl_off, int32_t *__restrict__ expo_b,
+                                                      const int32_t *__restrict__ tn_b) {
     __shared__ long long red[8];
     __shared__ int e_sh;
     const int b = b0 + blockIdx.x, m = s.sys.bmol[b];
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, 
     if (N == 0) return;
     const SplitGeom G(P, N, S);
     const int32_t *rel = s.rel_idx + s.rel_off[b];
-    constexpr int TN = nao_split_tn(S);
+    const int TN = tn_b[b];
     auto pval = [&](int i, int j) -> double {
         if (i >= N || j >= N || i / TN > j / TN) return 0.0;
         int64_t gi = rel[i], gj = rel[j];
@@ -492,7 +493,7 @@ template <int TN>
 __global__ void __launch_bounds__(128, 1) h_tc_kernel(DevSystem s, const HWork *__restrict__ work, int32_t w0,
                                                      const uint8_t *__restrict__ slices, const int64_t *__restrict__ sl_off,
                                                      const int32_t *__restrict__ expo, const int32_t *__restrict__ neg16,
-                                                     int S, int32_t *__restrict__ err) {
+                                                     int S, int scatter, int32_t *__restrict__ err) {
     extern __shared__ uint8_t smem_dyn[];
     __shared__ Pipe pp;
     uint8_t *smem = align1024(smem_dyn);
@@ -532,7 +533,7 @@ __global__ void __launch_bounds__(128, 1) h_tc_kernel(DevSystem s, const HWork *
                 const int j = it.tj * TN + c0 + jj;
                 if (!row_ok || j >= N || j < i) continue;
                 const int ej = ex[j];
-                if (ei <= -10000 || ej <= -10000) continue;
+                if (ei <= -10000 || ej <= -10000 || !scatter) continue;
                 atomicAdd(h_elem(s, m, gi, rel[j]), recombine(v.hi[jj], v.lo[jj], v.lo2[jj], ei + ej));
             }
         }
@@ -556,7 +557,7 @@ __global__ void __launch_bounds__(128, 1) n_tc_kernel(DevSystem s, const HWork *
     const int p0 = s.batch_off[b], P = s.batch_off[b + 1] - p0;
     const int Ppad = (P + NAO_PPAD - 1) & ~(NAO_PPAD - 1);
     const int N = s.rel_off[b + 1] - s.rel_off[b];
-    const SplitGeom G(P, N, S);
+    const SplitGeom G(P, N, S, TN);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t tm = tc_setup(pp);
     const uint8_t *base = slices + sl_off[b];
@@ -675,19 +676,23 @@ cudaError_t launch_slice_h(const DevSystem &s, int32_t b0, int32_t b1, int32_t m
 }
 
 cudaError_t launch_h_tc(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
-                        const int64_t *sl_off, const int32_t *expo, const int32_t *neg16, int S, int32_t *err,
-                        cudaStream_t st) {
+                        const int64_t *sl_off, const int32_t *expo, const int32_t *neg16, int S, int tn, int scatter,
+                        int32_t *err, cudaStream_t st) {
     if (n_work <= 0) return cudaSuccess;
-    if (nao_split_tn(S) == 48)
-        h_tc_kernel<48><<<n_work, 128, split_smem_bytes(S), st>>>(s, work, w0, slices, sl_off, expo, neg16, S, err);
+    if (tn == 48 && S <= 10)
+        h_tc_kernel<48><<<n_work, 128, split_smem_bytes(S), st>>>(s, work, w0, slices, sl_off, expo, neg16, S, scatter,
+                                                                  err);
+    else if (tn == 32)
+        h_tc_kernel<32><<<n_work, 128, split_smem_bytes(S), st>>>(s, work, w0, slices, sl_off, expo, neg16, S, scatter,
+                                                                  err);
     else
-        h_tc_kernel<32><<<n_work, 128, split_smem_bytes(S), st>>>(s, work, w0, slices, sl_off, expo, neg16, S, err);
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
 cudaError_t launch_slice_n(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_qt, const double *scratch,
-                           uint8_t *slices, const int64_t *sl_off, int32_t *expo_q, int32_t *expo_b, int S,
-                           cudaStream_t st) {
+                           uint8_t *slices, const int64_t *sl_off, int32_t *expo_q, int32_t *expo_b,
+                           const int32_t *tn_b, int S, cudaStream_t st) {
     if (b1 <= b0) return cudaSuccess;
     if (max_qt > 0) {
 #define NAO_SLICE_NPHI(SS) \
@@ -697,7 +702,7 @@ cudaError_t launch_slice_n(const DevSystem &s, int32_t b0, int32_t b1, int32_t m
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-#define NAO_SLICE_NP(SS) slice_np_kernel<SS><<<b1 - b0, 256, 0, st>>>(s, b0, slices, sl_off, expo_b)
+#define NAO_SLICE_NP(SS) slice_np_kernel<SS><<<b1 - b0, 256, 0, st>>>(s, b0, slices, sl_off, expo_b, tn_b)
     NAO_SPLIT_DISPATCH(S, NAO_SLICE_NP)
 #undef NAO_SLICE_NP
     return cudaGetLastError();
@@ -705,9 +710,10 @@ cudaError_t launch_slice_n(const DevSystem &s, int32_t b0, int32_t b1, int32_t m
 
 cudaError_t launch_n_tc(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
                         const int64_t *sl_off, const int32_t *expo_q, const int32_t *expo_b, const double *scratch, int S,
-                        int32_t *err, cudaStream_t st) {
+                        int tn, int32_t *err, cudaStream_t st) {
     if (n_work <= 0) return cudaSuccess;
-    if (nao_split_tn(S) == 48)
+    if (tn != 32 && !(tn == 48 && S <= 10)) return cudaErrorInvalidValue;
+    if (tn == 48)
         n_tc_kernel<48><<<n_work, 128, split_smem_bytes(S), st>>>(s, work, w0, slices, sl_off, expo_q, expo_b, scratch,
                                                                   S, err);
     else

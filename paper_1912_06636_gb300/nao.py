@@ -33,6 +33,7 @@ SYMBOLS = [
     "nao_evaluate_batch", "nao_sync_status", "nao_status_string", "nao_last_error",
     "nao_profile_enable", "nao_profile_read", "nao_integrate_h_noalloc",
     "nao_grid_create_many", "nao_get_system", "nao_integrate_h_many", "nao_update_density_many",
+    "nao_get_tuning",
 ]
 NAO_NOALLOC_SCRATCH_BYTES = 32 << 20
 KERNELS = ["eval_grad", "eval_phi", "h_fp64", "h_fp32", "h_split", "slice", "mirror", "n_fp64", "n_fp32",
@@ -58,7 +59,7 @@ class Options(C.Structure):
     _fields_ = [
         ("max_batch_points", C.c_int32), ("split_slices", C.c_int32), ("deterministic", C.c_int32),
         ("device", C.c_int32), ("scratch_bytes", C.c_int64), ("capture_graph", C.c_int32),
-        ("reserved0", C.c_int32),
+        ("autotune", C.c_int32),
     ]
 
 
@@ -104,10 +105,11 @@ def load():
         "nao_profile_enable": ([P, I32], C.c_int),
         "nao_profile_read": ([P, P, I32], C.c_int),
         "nao_integrate_h_noalloc": ([P, P, U32, P, P], C.c_int),
-        "nao_grid_create_many": ([P, I32, P, P], C.c_int),
+        "nao_grid_create_many": ([P, I32, P, P, P], C.c_int),
         "nao_get_system": ([P, I32, P, P, P, P, P, P], C.c_int),
         "nao_integrate_h_many": ([P, P, U32, C.c_int, P, P], C.c_int),
         "nao_update_density_many": ([P, P, C.c_int, P, P, P], C.c_int),
+        "nao_get_tuning": ([P, P, P], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -191,13 +193,15 @@ def nao_grid_create(system, options: Options | None = None, **opts) -> C.c_void_
     return h
 
 
-def nao_grid_create_many(systems, options: Options | None = None, **opts) -> C.c_void_p:
-    """One handle over several systems that share the radial grid."""
+def nao_grid_create_many(systems, options: Options | None = None, batch_points=None, **opts) -> C.c_void_p:
+    """One handle over several systems that share the radial grid (optional per-system B)."""
     keep: list = []
     arr = (SystemDesc * len(systems))(*[_desc(s, keep) for s in systems])
+    bp = None if batch_points is None else np.ascontiguousarray(batch_points, dtype=np.int32)
     o = _options(options, opts)
     h = C.c_void_p()
-    _check(load().nao_grid_create_many(arr, len(systems), C.byref(o), C.byref(h)), "nao_grid_create_many")
+    _check(load().nao_grid_create_many(arr, len(systems), None if bp is None else bp.ctypes.data, C.byref(o),
+                                       C.byref(h)), "nao_grid_create_many")
     return h
 
 
@@ -206,6 +210,15 @@ def nao_get_system(h, m: int) -> dict:
     _check(load().nao_get_system(h, int(m), *[C.byref(x) for x in v]), "nao_get_system")
     keys = ("basis_offset", "n_basis", "point_offset", "n_points", "batch_begin", "batch_end")
     return {k: int(x.value) for k, x in zip(keys, v)}
+
+
+def nao_get_tuning(h):
+    """(per-batch split tile width, number of histogram buckets the autotuner timed)."""
+    info = nao_get_info(h)
+    tw = np.zeros(max(int(info.n_batches), 1), np.int32)
+    nb = C.c_int32()
+    _check(load().nao_get_tuning(h, tw.ctypes.data, C.byref(nb)), "nao_get_tuning")
+    return tw[: int(info.n_batches)], int(nb.value)
 
 
 def _ptr_array(ts, allow_none: bool):
@@ -319,7 +332,7 @@ class Grid:
     ``system`` is one system, or a list of systems for a grouped handle (nao_grid_create_many);
     the grouped handle's per-system calls are integrate_h_many / update_density_many."""
 
-    def __init__(self, system, device: int | None = None, **opts):
+    def __init__(self, system, device: int | None = None, batch_points=None, **opts):
         import torch
 
         if device is None:
@@ -327,7 +340,7 @@ class Grid:
         self.device = torch.device("cuda", device)
         with torch.cuda.device(self.device):
             if isinstance(system, (list, tuple)):
-                self.h = nao_grid_create_many(list(system), device=device, **opts)
+                self.h = nao_grid_create_many(list(system), batch_points=batch_points, device=device, **opts)
             else:
                 self.h = nao_grid_create(system, device=device, **opts)
         self.info = nao_get_info(self.h)

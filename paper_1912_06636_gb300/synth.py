@@ -356,6 +356,22 @@ def random_molecule(n_atoms: int, seed: int, n_rad=40, n_theta=10, n_phi=11, max
                        max_batch_points=max_batch_points, name=f"mol{n_atoms}-{seed}")
 
 
+def molecule_set(n_mol: int, seed: int = 3000, n_min: int = 3, n_max: int = 60, b_min: int = 20, b_max: int = 400,
+                 n_rad=60, n_theta=17, n_phi=18):
+    """Independent molecules for one grouped handle: molecule k has a size log-uniform in
+    [n_min, n_max] atoms and a batch size log-uniform in [b_min, b_max] points, both drawn
+    with seed + k (random_molecule's rules for geometry and species). Returns (systems, B)."""
+    systems, bs = [], []
+    for k in range(n_mol):
+        rng = np.random.Generator(np.random.PCG64(seed + k))
+        na = int(min(n_max, np.floor(_log_uniform(rng, n_min, n_max + 1, 1)[0])))
+        b = int(min(b_max, np.floor(_log_uniform(rng, b_min, b_max + 1, 1)[0])))
+        sysk = random_molecule(na, seed + k, n_rad, n_theta, n_phi, max_batch_points=b)
+        systems.append(sysk)
+        bs.append(b)
+    return systems, bs
+
+
 def serving_stream(n_requests: int, rate: float = 200.0, seed: int = 4, n_min: int = 3, n_max: int = 200):
     """Poisson arrivals at `rate` per second; molecule sizes log-uniform in [n_min, n_max] atoms.
     Returns a list of (arrival time in s, number of atoms, molecule seed)."""

@@ -32,7 +32,7 @@ def test_status_strings_and_defaults():
     assert nao.nao_status_string(1) == "invalid argument"
     o = nao.nao_default_options()
     assert o.max_batch_points == 200 and o.split_slices == 12 and o.device == -1
-    assert o.capture_graph == 0 and o.reserved0 == 0
+    assert o.capture_graph == 0 and o.autotune == 1
 
 
 def _bad(sys_, **opts):
@@ -63,7 +63,7 @@ def test_invalid_input_is_rejected_without_gpu():
     assert _bad(s, split_slices=2) == 1
     assert _bad(s, split_slices=13) == 1
     assert _bad(s, capture_graph=2) == 1
-    assert _bad(s, reserved0=1) == 1
+    assert _bad(s, autotune=2) == 1
 
 
 def test_grouped_create_rejects_bad_input_without_gpu():
@@ -76,9 +76,12 @@ def test_grouped_create_rejects_bad_input_without_gpu():
     assert e.value.code == 1 and "system 1" in str(e.value)
     lib = nao.load()
     out = C.c_void_p(123)
-    assert lib.nao_grid_create_many(None, 2, None, C.byref(out)) == 1 and out.value is None
+    assert lib.nao_grid_create_many(None, 2, None, None, C.byref(out)) == 1 and out.value is None
     arr = (nao.SystemDesc * 1)()
-    assert lib.nao_grid_create_many(arr, 0, None, C.byref(out)) == 1
+    assert lib.nao_grid_create_many(arr, 0, None, None, C.byref(out)) == 1
+    with pytest.raises(nao.NaoError) as e:
+        nao.nao_grid_create_many([s, s], batch_points=[200, 0])
+    assert e.value.code == 1 and "max_batch_points[1]" in str(e.value)
 
 
 def test_null_handle_calls_fail_cleanly():
@@ -89,6 +92,7 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.nao_integrate_h_many(None, None, 3, 0, None, None) == 1
     assert lib.nao_update_density_many(None, None, 0, None, None, None) == 1
     assert lib.nao_get_system(None, 0, None, None, None, None, None, None) == 1
+    assert lib.nao_get_tuning(None, None, None) == 1
     info = nao.GridInfo()
     assert lib.nao_get_info(None, C.byref(info)) == 1
     out = C.c_void_p(123)
