@@ -108,7 +108,7 @@ typedef struct {
     int32_t autotune;         /* 1 (default): the first NAO_SPLIT Hamiltonian call times 128x48 against
                                  128x32 tensor-core tiles for each (N_b, P_b) bucket of the batch-size
                                  histogram (nao_get_tuning reports the result); 0: a fixed rule (48
-                                 where S <= 10 and N_b > 32, else 32). */
+                                 where S <= 10, else 32). */
 } nao_options;
 
 typedef struct {

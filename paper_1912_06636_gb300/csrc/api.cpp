@@ -575,8 +575,9 @@ nao_status check_prec(nao_precision p) {
 }
 
 // Split-path tile width of a batch before (or without) autotuning: 32 where 48 cannot hold
-// the S accumulator groups in tensor memory or where the batch has at most 32 functions.
-int default_tn(int S, int N) { return (S > 10 || N <= 32) ? 32 : 48; }
+// the S accumulator groups in tensor memory, else 48 (every width in use costs a launch of its
+// own, so small batches stay with the majority).
+int default_tn(int S, int) { return S > 10 ? 32 : 48; }
 
 // The split work lists for the current per-batch tile widths, per split chunk and width:
 // H tile pairs (batch, 128-row tile I, TN-column tile J) crossing the upper triangle, and
@@ -719,10 +720,12 @@ nao_status split_setup(nao_grid *g) {
 
 // Autotuner of the split path's tile width, driven by the batch-size histogram: batches are
 // bucketed by (basis functions N_b, points P_b); for every bucket the H contraction of the
-// bucket's batches in the first split chunks is timed with 128x48 and with 128x32 tiles (CUDA
-// events on the call's stream, the best of three runs after a warm-up, without the scatter), and
-// 32 is kept for all batches of the bucket when it is at least 3 % faster (the density uses the
-// same width). Buckets that
+// bucket's batches in the first split chunks (repeated to fill the GPU for several waves, so
+// that the timing is the throughput of a full launch) is timed with 128x48 and with 128x32
+// tiles (CUDA events on the call's stream, the best of three runs after a warm-up, without the
+// scatter), and
+// 32 is kept for all batches of the bucket when it is at least 10 % faster (a second width
+// costs a launch of its own; the density uses the same width). Buckets that
 // none of those chunks contains keep the default rule. Runs once per handle, inside the first
 // split Hamiltonian call (the evaluation and slicing it needs use that call's v and terms).
 int tn_bucket(int N, int P) {
@@ -741,7 +744,7 @@ nao_status split_tune(nao_grid *g, uint32_t terms, cudaStream_t st) {
     constexpr int kBuckets = 60, kChunks = 3;
     std::vector<int> bucket(g->n_batches, -1), total(kBuckets, 0);
     for (int64_t b = 0; b < g->n_batches; b++)
-        if (g->Nb[b] > 32) {  // N_b <= 32: one 32-wide tile is never slower than a 48-wide one
+        if (g->Nb[b] > 0) {
             bucket[b] = tn_bucket(g->Nb[b], g->Pb[b]);
             total[bucket[b]]++;
         }
@@ -765,16 +768,27 @@ nao_status split_tune(nao_grid *g, uint32_t terms, cudaStream_t st) {
             if (choice[k] || !total[k]) continue;
             float ms[2] = {0.0f, 0.0f};
             int64_t n_items = 0;
-            for (int w = 0; w < 2 && rs == NAO_OK; w++) {
+            // the bucket's batches of this chunk, repeated so that the 48-wide launch has at
+            // least 8 CTAs per SM: the timing is throughput in a full launch, as in the real run
+            int64_t base48 = 0;
+            for (int32_t b = c.b0; b < c.b1; b++) {
+                if (bucket[b] != k) continue;
+                const int N = g->Nb[b], nI = (N + 127) / 128, nJ = (N + 47) / 48;
+                for (int I = 0; I < nI; I++)
+                    for (int J = 0; J < nJ; J++) base48 += (I * 128 <= J * 48 + 47);
+            }
+            const int64_t reps = base48 > 0 ? (8 * 152 + base48 - 1) / base48 : 0;
+            for (int w = 0; w < 2 && rs == NAO_OK && reps > 0; w++) {
                 const int TN = w == 0 ? 48 : 32;
                 std::vector<HWork> items;
-                for (int32_t b = c.b0; b < c.b1; b++) {
-                    if (bucket[b] != k) continue;
-                    const int N = g->Nb[b], nI = (N + 127) / 128, nJ = (N + TN - 1) / TN;
-                    for (int I = 0; I < nI; I++)
-                        for (int J = 0; J < nJ; J++)
-                            if (I * 128 <= J * TN + TN - 1) items.push_back({b, I, J, 0});
-                }
+                for (int64_t r = 0; r < reps; r++)
+                    for (int32_t b = c.b0; b < c.b1; b++) {
+                        if (bucket[b] != k) continue;
+                        const int N = g->Nb[b], nI = (N + 127) / 128, nJ = (N + TN - 1) / TN;
+                        for (int I = 0; I < nI; I++)
+                            for (int J = 0; J < nJ; J++)
+                                if (I * 128 <= J * TN + TN - 1) items.push_back({b, I, J, 0});
+                    }
                 n_items = (int64_t)items.size();
                 if (items.empty()) break;
                 if ((int64_t)items.size() > g->cap_tune_hw) {
@@ -799,7 +813,7 @@ nao_status split_tune(nao_grid *g, uint32_t terms, cudaStream_t st) {
                 if (ce != cudaSuccess) rs = cuda_fail(ce, "autotune timing");
             }
             if (rs != NAO_OK || n_items == 0) continue;
-            choice[k] = ms[1] < 0.97f * ms[0] ? 32 : 48;  // 32 only when clearly faster
+            choice[k] = ms[1] < 0.9f * ms[0] ? 32 : 48;  // 32 only when clearly faster (it costs a launch)
             timed++;
         }
     }
@@ -869,6 +883,7 @@ nao_status enqueue_h(nao_grid *g, uint32_t terms, nao_precision prec, cudaStream
                                       g->d_expo_h, g->d_neg16, S, st);
             }));
             for (int k = 0; k < 2; k++)
+                if (c.hw1[k] > c.hw0[k])
                 NAO_CUDA(timed(g, NAO_K_H_SPLIT, st, [&] {
                     return launch_h_tc(s, g->d_split_hw, c.hw0[k], c.hw1[k] - c.hw0[k], g->d_slices, g->d_sl_off_h,
                                        g->d_expo_h, g->d_neg16, S, k == 0 ? 48 : 32, 1, g->d_err, st);
@@ -898,6 +913,7 @@ nao_status enqueue_n(nao_grid *g, nao_precision prec, bool want_ne, cudaStream_t
                                       g->d_expo_b, g->d_split_tn, S, st);
             }));
             for (int k = 0; k < 2; k++)
+                if (c.nw1[k] > c.nw0[k])
                 NAO_CUDA(timed(g, NAO_K_N_SPLIT, st, [&] {
                     return launch_n_tc(s, g->d_split_nw, c.nw0[k], c.nw1[k] - c.nw0[k], g->d_slices, g->d_sl_off_n,
                                        g->d_expo_q, g->d_expo_b, g->d_scratch, S, k == 0 ? 48 : 32, g->d_err, st);

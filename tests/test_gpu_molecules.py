@@ -103,10 +103,10 @@ def test_ten_slice_autotuner(mols):
     Hs1, ns1, tw1, timed1, N = out[1]
     Hs0, ns0, tw0, timed0, _ = out[0]
     assert timed1 >= 1 and timed0 == 0
-    assert set(np.unique(tw1[N > 32])) <= {32, 48} and np.all(tw1[(N > 0) & (N <= 32)] == 32)
-    assert np.all(tw0[N > 32] == 48)
-    print("autotuner:", timed1, "buckets timed;", int(np.sum(tw1[N > 32] == 48)), "batches at 48,",
-          int(np.sum(tw1[N > 32] == 32)), "at 32 (of", int(np.sum(N > 32)), "with N_b > 32)")
+    assert set(np.unique(tw1[N > 0])) <= {32, 48}
+    assert np.all(tw0[N > 0] == 48)
+    print("autotuner:", timed1, "buckets timed;", int(np.sum(tw1[N > 0] == 48)), "batches at 48,",
+          int(np.sum(tw1[N > 0] == 32)), "at 32")
     for m, k in enumerate(sel):
         assert rel_err(Hs1[m], Hs0[m], refs[k]["A"]) <= 1e-14
         assert rel_err(ns1[m], ns0[m], refs[k]["D"]) <= 1e-14
