@@ -245,12 +245,13 @@ typedef enum {
     NAO_K_H_FP64,        /* FP64 h[B] contraction + scatter into H */
     NAO_K_H_FP32,        /* FP32 h[B] contraction + scatter        */
     NAO_K_H_SPLIT,       /* tensor-core slice products + scatter   */
-    NAO_K_SLICE,         /* Ozaki slicing of evaluated functions    */
+    NAO_K_SLICE,         /* Ozaki slicing for H (weighted phi, grad phi) */
     NAO_K_MIRROR,        /* upper -> lower triangle copy of H      */
     NAO_K_N_FP64,        /* FP64 density contraction               */
     NAO_K_N_FP32,        /* FP32 density contraction               */
     NAO_K_N_SPLIT,       /* tensor-core density contraction        */
     NAO_K_REDUCE,        /* electron-count reduction               */
+    NAO_K_SLICE_N,       /* Ozaki slicing for the density (phi, P') */
     NAO_K_COUNT
 } nao_kernel_id;
 

@@ -595,10 +595,7 @@ nao_status split_lists(nao_grid *g) {
             if (N == 0) continue;
             const int TN = g->split_tn[b], k = TN == 48 ? 0 : 1;
             const SplitGeom G(P, N, S, TN);
-            const int nI = (N + 127) / 128, nJ = (N + TN - 1) / TN;
-            for (int I = 0; I < nI; I++)
-                for (int J = 0; J < nJ; J++)
-                    if (I * 128 <= J * TN + TN - 1) hw[k].push_back({b, I, J, 0});
+            nao_split_h_items(b, N, TN, hw[k]);
             for (int Q = 0; Q < G.n_qt; Q++) nw[k].push_back({b, Q, G.n_jtN, 0});  // all J tiles in one CTA
         }
         for (int k = 0; k < 2; k++) {
@@ -684,11 +681,9 @@ nao_status split_setup(nao_grid *g) {
                 int64_t best_h = 0;
                 for (int TN : {48, 32}) {
                     if (TN == 48 && S > 10) continue;
-                    const int nI = (N + 127) / 128, nJ = (N + TN - 1) / TN;
-                    int64_t cnt = 0;
-                    for (int I = 0; I < nI; I++)
-                        for (int J = 0; J < nJ; J++) cnt += (I * 128 <= J * TN + TN - 1);
-                    best_h = std::max(best_h, cnt);
+                    std::vector<HWork> tmp;
+                    nao_split_h_items(b, N, TN, tmp);
+                    best_h = std::max(best_h, (int64_t)tmp.size());
                 }
                 cap_h += best_h;
                 cap_n += G.n_qt;
@@ -773,22 +768,17 @@ nao_status split_tune(nao_grid *g, uint32_t terms, cudaStream_t st) {
             int64_t base48 = 0;
             for (int32_t b = c.b0; b < c.b1; b++) {
                 if (bucket[b] != k) continue;
-                const int N = g->Nb[b], nI = (N + 127) / 128, nJ = (N + 47) / 48;
-                for (int I = 0; I < nI; I++)
-                    for (int J = 0; J < nJ; J++) base48 += (I * 128 <= J * 48 + 47);
+                std::vector<HWork> tmp;
+                nao_split_h_items(b, g->Nb[b], 48, tmp);
+                base48 += (int64_t)tmp.size() * NAO_SPLIT_CLUSTER;  // CTAs
             }
             const int64_t reps = base48 > 0 ? (8 * 152 + base48 - 1) / base48 : 0;
             for (int w = 0; w < 2 && rs == NAO_OK && reps > 0; w++) {
                 const int TN = w == 0 ? 48 : 32;
                 std::vector<HWork> items;
                 for (int64_t r = 0; r < reps; r++)
-                    for (int32_t b = c.b0; b < c.b1; b++) {
-                        if (bucket[b] != k) continue;
-                        const int N = g->Nb[b], nI = (N + 127) / 128, nJ = (N + TN - 1) / TN;
-                        for (int I = 0; I < nI; I++)
-                            for (int J = 0; J < nJ; J++)
-                                if (I * 128 <= J * TN + TN - 1) items.push_back({b, I, J, 0});
-                    }
+                    for (int32_t b = c.b0; b < c.b1; b++)
+                        if (bucket[b] == k) nao_split_h_items(b, g->Nb[b], TN, items);
                 n_items = (int64_t)items.size();
                 if (items.empty()) break;
                 if ((int64_t)items.size() > g->cap_tune_hw) {
@@ -908,7 +898,7 @@ nao_status enqueue_n(nao_grid *g, nao_precision prec, bool want_ne, cudaStream_t
         NAO_CUDA(launch_zero_n(s, g->d_dwork, (int32_t)g->n_dwork, st));
         for (const auto &c : g->split_chunks) {
             NAO_CUDA(timed(g, NAO_K_EVAL_PHI, st, [&] { return launch_eval(s, c.b0, c.b1, NAO_FP64, false, g->d_scratch, st); }));
-            NAO_CUDA(timed(g, NAO_K_SLICE, st, [&] {
+            NAO_CUDA(timed(g, NAO_K_SLICE_N, st, [&] {
                 return launch_slice_n(s, c.b0, c.b1, c.max_qt, g->d_scratch, g->d_slices, g->d_sl_off_n, g->d_expo_q,
                                       g->d_expo_b, g->d_split_tn, S, st);
             }));

@@ -30,7 +30,7 @@
 
 namespace {
 
-constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: bounded mbarrier waits
+constexpr long long kWaitCycles = 400000000LL;  // ~0.2 s at 2 GHz: bounded mbarrier waits
 
 
 // Digit extraction works on FP64 bit patterns with integer instructions: on this GPU the FP64
@@ -324,8 +324,8 @@ __global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, 
 // Producer (warp 0, one lane): for each K chunk, the S B slices into B set kc % 2, then the
 // S A slices one by one into the ring, each copy a single bulk (TMA) transfer completing on a
 // "full" mbarrier. MMA issuer (warp 1, one lane): for each A slice s, the pairs (s, t) with
-// s + t < S, four 128xTNx16 tcgen05.mma each into accumulator group s + t (tensor-memory
-// columns TN (s + t) ...); commits release A buffers and B sets back to the producer through
+// s + t < S as one 128 x TN(S-s) x 16 tcgen05.mma per K step (two where TN(S-s) > 256) into
+// accumulator groups s .. S-1 (tensor-memory columns TN s ...); commits release A buffers and B sets back to the producer through
 // "empty" mbarriers. The 16-column K steps with index < neg16 negate B (descriptor bit 14).
 // Every wait is bounded; on a timeout the CTA records NAO_ERR_TIMEOUT and skips its epilogue.
 // A CTA may run the pipeline several times (one accumulator tile after another): the ring and
@@ -349,14 +349,19 @@ struct LoopArgs {
     int n_kc, neg16, S;
     int c0 = 0;     // K chunks this CTA's earlier runs of the pipeline processed
     int round = 0;  // index of this run
+    int mma = 1;    // 0: consume the operands without issuing MMAs (a cluster CTA without a tile)
 };
 
 __host__ __device__ constexpr size_t pipe_smem_bytes(int S) {
     return (size_t)RING * 16384 + 2 * (size_t)S * nao_split_tn(S) * 128 + 1024;
 }
 
-template <int TN>
-__device__ __forceinline__ void pipe_producer(Pipe &p, uint8_t *sA, uint8_t *sB, const LoopArgs &L) {
+// CL > 1: the CTAs of a cluster share the A operand. Every CTA arms its own "full" barrier; the
+// cluster's first CTA issues one multicast copy of each A tile into all of them; "empty" barriers
+// count the MMA completions of all CL CTAs (multicast commits), so the first CTA reuses a ring
+// slot only when every CTA has consumed it.
+template <int TN, int CL = 1>
+__device__ __forceinline__ void pipe_producer(Pipe &p, uint8_t *sA, uint8_t *sB, const LoopArgs &L, uint32_t rank) {
     constexpr uint32_t B_BLOCK = TN * 128;
     const int S = L.S;
     for (int kc = 0; kc < L.n_kc; kc++) {
@@ -369,16 +374,19 @@ __device__ __forceinline__ void pipe_producer(Pipe &p, uint8_t *sA, uint8_t *sB,
             const int idx = gk * S + sa, a = idx % RING, ua = idx / RING;
             if (ua >= 1 && !tc::mbar_wait(&p.emptyA[a], (ua - 1) & 1, kWaitCycles)) { p.abort = 1; return; }
             tc::mbar_arrive_expect_tx(&p.fullA[a], L.a_bytes);
-            tc::bulk_g2s(sA + (size_t)a * 16384, L.a0 + sa * L.a_s + kc * L.a_kc, L.a_bytes, &p.fullA[a]);
+            if (CL == 1)
+                tc::bulk_g2s(sA + (size_t)a * 16384, L.a0 + sa * L.a_s + kc * L.a_kc, L.a_bytes, &p.fullA[a]);
+            else if (rank == 0)
+                tc::bulk_g2s_multicast(sA + (size_t)a * 16384, L.a0 + sa * L.a_s + kc * L.a_kc, L.a_bytes, &p.fullA[a],
+                                       (uint16_t)((1u << CL) - 1));
         }
         if (*(volatile int *)&p.abort) return;
     }
 }
 
-template <int TN>
+template <int TN, int CL = 1>
 __device__ __forceinline__ void pipe_mma(Pipe &p, uint8_t *sA, uint8_t *sB, uint32_t tm, const LoopArgs &L) {
     constexpr uint32_t B_BLOCK = TN * 128;
-    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, TN);
     const int S = L.S;
     for (int kc = 0; kc < L.n_kc; kc++) {
         const int gk = L.c0 + kc, bb = gk & 1, ub = gk >> 1;
@@ -389,16 +397,25 @@ __device__ __forceinline__ void pipe_mma(Pipe &p, uint8_t *sA, uint8_t *sB, uint
             if (!tc::mbar_wait(&p.fullA[a], ua & 1, kWaitCycles)) { p.abort = 1; tc::mma_commit(&p.done); return; }
             tc::fence_after_sync();
             const uint64_t ad = tc::sdesc_sw128(tc::smem_addr(sA + (size_t)a * 16384));
-            for (int tb = 0; sa + tb < S; tb++) {
-                const uint64_t bd = tc::sdesc_sw128(tc::smem_addr(sB + ((size_t)bb * S + tb) * B_BLOCK));
-                const uint32_t dt = tm + (uint32_t)((sa + tb) * TN);
+            // The B slices t = 0 .. S-1-sa are consecutive TN-row tiles of the B set, one
+            // (S-sa) TN-row operand, and their groups sa + t are consecutive TN-column blocks of
+            // tensor memory: one MMA per 16-column K step covers all pairs (sa, t), split at the
+            // MMA's largest N of 256.
+            const int ncols = TN * (S - sa);
+            const uint8_t *bset = sB + (size_t)bb * S * B_BLOCK;
+            for (int n0 = 0; L.mma && n0 < ncols; n0 += 256) {
+                const int nn = ncols - n0 < 256 ? ncols - n0 : 256;
+                const uint32_t idesc = tc::idesc_bf16_f32(128, nn);
+                const uint64_t bd = tc::sdesc_sw128(tc::smem_addr(bset + (size_t)n0 * 128));
+                const uint32_t dt = tm + (uint32_t)(sa * TN + n0);
 #pragma unroll
                 for (int ks = 0; ks < 4; ks++) {
                     const uint32_t id = (kc * 4 + ks < L.neg16) ? (idesc | (1u << 14)) : idesc;
                     tc::mma_bf16(dt, ad + 2 * ks, bd + 2 * ks, id, (kc | sa | ks) ? 1u : 0u);
                 }
             }
-            tc::mma_commit(&p.emptyA[a]);
+            if (CL == 1) tc::mma_commit(&p.emptyA[a]);
+            else tc::mma_commit_multicast(&p.emptyA[a], (uint16_t)((1u << CL) - 1));
         }
         tc::mma_commit(&p.emptyB[bb]);
     }
@@ -406,11 +423,12 @@ __device__ __forceinline__ void pipe_mma(Pipe &p, uint8_t *sA, uint8_t *sB, uint
 }
 
 // Runs the pipeline; on return (all threads) the accumulators are complete unless p.abort.
-template <int TN>
-__device__ __forceinline__ void pipe_run(Pipe &p, uint8_t *smem, uint32_t tm, const LoopArgs &L, int32_t *err) {
+template <int TN, int CL = 1>
+__device__ __forceinline__ void pipe_run(Pipe &p, uint8_t *smem, uint32_t tm, const LoopArgs &L, int32_t *err,
+                                         uint32_t rank = 0) {
     uint8_t *sA = smem, *sB = smem + (size_t)RING * 16384;
-    if (threadIdx.x == 0) pipe_producer<TN>(p, sA, sB, L);
-    else if (threadIdx.x == 32) pipe_mma<TN>(p, sA, sB, tm, L);
+    if (threadIdx.x == 0) pipe_producer<TN, CL>(p, sA, sB, L, rank);
+    else if (threadIdx.x == 32) pipe_mma<TN, CL>(p, sA, sB, tm, L);
     __syncthreads();
     if (threadIdx.x == 0) {
         if (!tc::mbar_wait(&p.done, (uint32_t)(L.round & 1), kWaitCycles)) p.abort = 1;
@@ -457,12 +475,13 @@ __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
     return reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
 }
 
+template <int CL = 1>
 __device__ __forceinline__ uint32_t tc_setup(Pipe &p) {
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         for (int i = 0; i < RING; i++) {
             tc::mbar_init(&p.fullA[i], 1);
-            tc::mbar_init(&p.emptyA[i], 1);
+            tc::mbar_init(&p.emptyA[i], CL);
         }
         for (int i = 0; i < 2; i++) {
             tc::mbar_init(&p.fullB[i], 1);
@@ -480,6 +499,7 @@ __device__ __forceinline__ uint32_t tc_setup(Pipe &p) {
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
+    if (CL > 1) tc::cluster_sync();  // every CTA's barriers exist before any multicast or remote arrive
     return p.tmem;
 }
 
@@ -489,35 +509,47 @@ __device__ __forceinline__ void tc_teardown(uint32_t tm) {
     if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(tm, 512);
 }
 
-template <int TN>
-__global__ void __launch_bounds__(128, 1) h_tc_kernel(DevSystem s, const HWork *__restrict__ work, int32_t w0,
-                                                     const uint8_t *__restrict__ slices, const int64_t *__restrict__ sl_off,
-                                                     const int32_t *__restrict__ expo, const int32_t *__restrict__ neg16,
-                                                     int S, int scatter, int32_t *__restrict__ err) {
+// One cluster of CL CTAs per work item (batch, 128-row tile I, first TN-column tile J0): CTA r
+// takes tile J0 + r (if it exists; otherwise it only takes part in the shared A loads). The A
+// operand (rows of tile I) is loaded once per cluster and multicast to every CTA.
+template <int TN, int CL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(128, 1)
+    h_tc_kernel(DevSystem s, const HWork *__restrict__ work, int32_t w0, const uint8_t *__restrict__ slices,
+                const int64_t *__restrict__ sl_off, const int32_t *__restrict__ expo,
+                const int32_t *__restrict__ neg16, int S, int scatter, int32_t *__restrict__ err) {
     extern __shared__ uint8_t smem_dyn[];
     __shared__ Pipe pp;
     uint8_t *smem = align1024(smem_dyn);
-    const HWork it = work[w0 + blockIdx.x];  // batch, 128-row tile, TN-column tile
+    const uint32_t rank = CL > 1 ? tc::cluster_rank() : 0;
+    const HWork it = work[w0 + blockIdx.x / CL];  // batch, 128-row tile, first TN-column tile
     const int b = it.batch, m = s.sys.bmol[b];
     const int P = s.batch_off[b + 1] - s.batch_off[b];
     const int N = s.rel_off[b + 1] - s.rel_off[b];
     const SplitGeom G(P, N, S);
+    const int nJ = (N + TN - 1) / TN;
+    const int J = it.tj + (int)rank;
+    const bool has_tile = J < nJ;
+    const int Jb = has_tile ? J : it.tj;  // a CTA without a tile still reads a valid B
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t tm = tc_setup(pp);
+    const uint32_t tm = tc_setup<CL>(pp);
     const uint8_t *base = slices + sl_off[b];
     const size_t blk = (size_t)G.R16 * 128;
     LoopArgs L;
     L.a0 = base + (size_t)it.ti * 128 * 128;
-    L.b0 = base + (size_t)it.tj * TN * 128;
+    L.b0 = base + (size_t)Jb * TN * 128;
     L.a_s = L.b_s = (size_t)G.n_kc * blk;
     L.a_kc = L.b_kc = blk;
     L.a_bytes = (uint32_t)min(128, G.R16 - it.ti * 128) * 128u;
-    L.b_bytes = (uint32_t)min(TN, G.R16 - it.tj * TN) * 128u;
+    L.b_bytes = (uint32_t)min(TN, G.R16 - Jb * TN) * 128u;
     L.n_kc = G.n_kc;
     L.neg16 = neg16[b];
     L.S = S;
-    pipe_run<TN>(pp, smem, tm, L, err);
-    if (!pp.abort) {
+    L.mma = has_tile ? 1 : 0;
+    // after a timeout anywhere in this launch, the remaining CTAs skip their work quickly
+    if (threadIdx.x == 0 && *(volatile int32_t *)err != 0) pp.abort = 1;
+    __syncthreads();
+    if (!pp.abort) pipe_run<TN, CL>(pp, smem, tm, L, err, rank);
+    if (!pp.abort && has_tile) {
         const int i = it.ti * 128 + warp * 32 + lane;
         const bool row_ok = i < N;
         const int32_t *rel = s.rel_idx + s.rel_off[b];
@@ -530,7 +562,7 @@ __global__ void __launch_bounds__(128, 1) h_tc_kernel(DevSystem s, const HWork *
             combine16<TN>(tm_row, c0, S, v);
 #pragma unroll
             for (int jj = 0; jj < 16; jj++) {
-                const int j = it.tj * TN + c0 + jj;
+                const int j = J * TN + c0 + jj;
                 if (!row_ok || j >= N || j < i) continue;
                 const int ej = ex[j];
                 if (ei <= -10000 || ej <= -10000 || !scatter) continue;
@@ -539,6 +571,7 @@ __global__ void __launch_bounds__(128, 1) h_tc_kernel(DevSystem s, const HWork *
         }
     }
     tc_teardown(tm);
+    if (CL > 1) tc::cluster_sync();  // no CTA leaves while a multicast or a remote arrive may target it
 }
 
 // One CTA per (batch, 128-point tile): the TN-function tiles J = 0 .. nJ-1 one after another
@@ -567,7 +600,9 @@ __global__ void __launch_bounds__(128, 1) n_tc_kernel(DevSystem s, const HWork *
     const uint32_t tm_row = tm + ((uint32_t)(warp * 32) << 16);
     double part_hi = 0.0, part_lo = 0.0, part_lo2 = 0.0;
     int c0 = 0;
-    for (int J = 0; J < it.tj; J++) {
+    if (threadIdx.x == 0 && *(volatile int32_t *)err != 0) pp.abort = 1;  // a timeout earlier in this launch
+    __syncthreads();
+    for (int J = 0; J < it.tj && !pp.abort; J++) {
         LoopArgs L;
         L.a0 = base + G.nA_block(0, 0) + (size_t)it.ti * 128 * 128;
         L.a_s = (size_t)G.n_kcN * G.P16 * 128;
@@ -642,8 +677,8 @@ size_t split_smem_bytes(int S) { return pipe_smem_bytes(S); }
 cudaError_t split_configure() {
     size_t bytes = 0;
     for (int S = 4; S <= NAO_SPLIT_MAX_SLICES; S++) bytes = split_smem_bytes(S) > bytes ? split_smem_bytes(S) : bytes;
-    const void *fns[4] = {(const void *)h_tc_kernel<48>, (const void *)h_tc_kernel<32>, (const void *)n_tc_kernel<48>,
-                          (const void *)n_tc_kernel<32>};
+    const void *fns[4] = {(const void *)h_tc_kernel<48, NAO_SPLIT_CLUSTER>, (const void *)h_tc_kernel<32, NAO_SPLIT_CLUSTER>,
+                          (const void *)n_tc_kernel<48>, (const void *)n_tc_kernel<32>};
     for (const void *f : fns) {
         const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (e != cudaSuccess) return e;
@@ -679,12 +714,13 @@ cudaError_t launch_h_tc(const DevSystem &s, const HWork *work, int32_t w0, int32
                         const int64_t *sl_off, const int32_t *expo, const int32_t *neg16, int S, int tn, int scatter,
                         int32_t *err, cudaStream_t st) {
     if (n_work <= 0) return cudaSuccess;
+    constexpr int CL = NAO_SPLIT_CLUSTER;
     if (tn == 48 && S <= 10)
-        h_tc_kernel<48><<<n_work, 128, split_smem_bytes(S), st>>>(s, work, w0, slices, sl_off, expo, neg16, S, scatter,
-                                                                  err);
+        h_tc_kernel<48, CL><<<n_work * CL, 128, split_smem_bytes(S), st>>>(s, work, w0, slices, sl_off, expo, neg16, S,
+                                                                           scatter, err);
     else if (tn == 32)
-        h_tc_kernel<32><<<n_work, 128, split_smem_bytes(S), st>>>(s, work, w0, slices, sl_off, expo, neg16, S, scatter,
-                                                                  err);
+        h_tc_kernel<32, CL><<<n_work * CL, 128, split_smem_bytes(S), st>>>(s, work, w0, slices, sl_off, expo, neg16, S,
+                                                                           scatter, err);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

@@ -36,8 +36,8 @@ SYMBOLS = [
     "nao_get_tuning",
 ]
 NAO_NOALLOC_SCRATCH_BYTES = 32 << 20
-KERNELS = ["eval_grad", "eval_phi", "h_fp64", "h_fp32", "h_split", "slice", "mirror", "n_fp64", "n_fp32",
-           "n_split", "reduce"]
+KERNELS = ["eval_grad", "eval_phi", "h_fp64", "h_fp32", "h_split", "slice_h", "mirror", "n_fp64", "n_fp32",
+           "n_split", "reduce", "slice_n"]
 
 
 class NaoError(RuntimeError):
@@ -64,7 +64,7 @@ class Options(C.Structure):
 
 
 class Profile(C.Structure):
-    _fields_ = [("launches", C.c_int64 * 11), ("ms", C.c_double * 11)]
+    _fields_ = [("launches", C.c_int64 * 12), ("ms", C.c_double * 12)]
 
 
 class GridInfo(C.Structure):
