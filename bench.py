@@ -164,12 +164,13 @@ def serving(n_requests: int, device: int) -> dict:
     return out
 
 
-# DRAM bytes per algorithmic FLOP_H of the dominant kernel, from one ncu capture of the diamond8
-# profiling case (dram__bytes_read.sum + dram__bytes_write.sum of one launch / that launch's
-# FLOP_H = 4.6096e9); a launch's traffic grows with tiles x K, i.e. with FLOP_H. Valid only for
-# the kernel version and slice count the capture was taken with.
+# DRAM bytes per algorithmic FLOP_H of the dominant kernel, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum over the captured launches / their FLOP_H): the
+# split H contraction on the full 64-atom workload (both tile widths, 2 timed steps), the FP64
+# contraction on the 8-atom profiling case (a launch's traffic grows with tiles x K, i.e. with
+# FLOP_H). Valid only for the kernel version and slice count the capture was taken with.
 TRAFFIC_PER_FLOP_H = {
-    ("h_split", 10): ((1.033217e9 + 4.605184e6) / 4.6096304e9, "profiles/h_tc_kernel_diamond8_split.md"),
+    ("h_split", 10): (24.612e9 / (2 * 9.1321260e10), "profiles/traffic_diamond64_split.md"),
     ("h_fp64", 0): ((359.834112e6 + 3.945472e6) / 4.6096304e9, "profiles/h_simt_kernel_diamond8_fp64.md"),
 }
 
@@ -289,10 +290,12 @@ def main():
         torch.distributed.barrier()
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.nvtx.range_push("timed")  # profilers can select the timed steps by this range
     for k in range(args.steps):
         evs[k][0].record(stream)
         step()
         evs[k][1].record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -333,12 +336,11 @@ def main():
                         "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}
         roofline.update({"launches": launches, "avg_launch_ms": fam_ms / max(launches, 1)})
         tk = (fam, int(g.split_slices) if prec == "split" else 0)
-        all48 = prec != "split" or bool(np.all(nao.nao_get_tuning(g.h)[0][np.diff(g.batches()[2]) > 0] == 48))
-        if tk in TRAFFIC_PER_FLOP_H and launches and all48:
+        if tk in TRAFFIC_PER_FLOP_H and launches:
             per_flop, src = TRAFFIC_PER_FLOP_H[tk]
             roofline["traffic"] = per_flop * info.flops_h * args.steps / launches
             roofline["traffic_unit"] = "bytes per launch"
-            roofline["traffic_source"] = src + " (diamond8 capture scaled by FLOP_H per launch)"
+            roofline["traffic_source"] = src + " (bytes per FLOP_H x this run's FLOP_H per launch)"
     gpu_launches = int(sum(l for l, _ in prof.values()))
     tuning = None
     if prec == "split":
