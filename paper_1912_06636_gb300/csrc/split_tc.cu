@@ -40,6 +40,11 @@ constexpr long long kWaitCycles = 400000000LL;  // ~0.2 s at 2 GHz: bounded mbar
 // |x| as an ordered integer: for non-negative doubles the bit patterns order like the values.
 __device__ __forceinline__ long long abs_bits(double x) { return __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL; }
 
+// The significand of the FP64 with bit pattern xb, in [1, 2), truncated to FP32.
+__device__ __forceinline__ float significand_f(long long xb) {
+    return __int_as_float(0x3F800000 | (int)((xb >> 29) & 0x7FFFFF));
+}
+
 // Exponent e with max * 2^-e in [0.25, 0.5), from the bit pattern of max (abs_bits); rows whose
 // magnitude is below 2^-900 (or zero) are taken as zero (flag -10000).
 __device__ __forceinline__ int row_exponent_bits(long long mb) {
@@ -124,6 +129,8 @@ __global__ void __launch_bounds__(256) slice_h_kernel(DevSystem s, int32_t b0, c
                                                      const int64_t *__restrict__ sl_off, int32_t *__restrict__ expo,
                                                      int32_t *__restrict__ neg16) {
     __shared__ double sd[4 * NAO_SPLIT_MAX_PPAD];
+    __shared__ int sd_eb[4 * NAO_SPLIT_MAX_PPAD];    // biased exponent of sd (0: zero weight)
+    __shared__ float sd_m[4 * NAO_SPLIT_MAX_PPAD];   // significand of sd in [1, 2), truncated
     __shared__ short src[4 * NAO_SPLIT_MAX_PPAD + 64];
     __shared__ unsigned char negf[4 * NAO_SPLIT_MAX_PPAD];
     __shared__ int wsum[8];
@@ -143,6 +150,9 @@ __global__ void __launch_bounds__(256) slice_h_kernel(DevSystem s, int32_t b0, c
         if (c == 0) d = (terms & NAO_TERM_POTENTIAL) && q < P ? w * v_at(s, m, p0 + q) : 0.0;
         else d = (terms & NAO_TERM_KINETIC) ? 0.5 * w : 0.0;
         sd[k] = sqrt(fabs(d));
+        const long long sb = __double_as_longlong(sd[k]);
+        sd_eb[k] = (int)((sb >> 52) & 0x7FF);
+        sd_m[k] = significand_f(sb);
         negf[k] = d < 0.0 ? 1 : 0;
     }
     for (int k = threadIdx.x; k < Kp; k += blockDim.x) src[k] = -1;
@@ -177,13 +187,23 @@ __global__ void __launch_bounds__(256) slice_h_kernel(DevSystem s, int32_t b0, c
     __syncthreads();
     for (int lr = warp; lr < 64; lr += 8) {
         const int r = rt * 64 + lr;
-        long long mb = 0;
+        // the binade of max_k |E_rk sd_k| without FP64 products: the product's biased exponent is
+        // eb(E) + eb(sd) - 1023, plus 1 when the significands' product reaches 2 (taken as reached
+        // from 2 - 2^-20 on, since both significands are truncated to FP32: e may then be one
+        // too large, costing one bit, but never too small)
+        int mk = 0;
         if (r < N)
-            for (int k = lane; k < K; k += 32) mb = max(mb, abs_bits(E[(int64_t)r * K + k] * sd[k]));
+            for (int k = lane; k < K; k += 32) {
+                const long long xb = __double_as_longlong(E[(int64_t)r * K + k]);
+                const int ebx = (int)((xb >> 52) & 0x7FF), ebs = sd_eb[k];
+                if (ebx == 0 || ebs == 0) continue;
+                const int carry = significand_f(xb) * sd_m[k] >= 1.999998f ? 1 : 0;
+                mk = max(mk, ebx + ebs + carry);
+            }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+        for (int o = 16; o > 0; o >>= 1) mk = max(mk, __shfl_xor_sync(0xffffffffu, mk, o));
         if (lane == 0) {
-            const int e = row_exponent_bits(mb);
+            const int e = mk - 1023 > 0 ? row_exponent_bits((long long)(mk - 1023) << 52) : -10000;
             ex_s[lr] = e;
             if (r < N) expo[s.rel_off[b] + r] = e;
         }
@@ -281,8 +301,11 @@ __global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, 
         if (i >= N || j >= N || i / TN > j / TN) return 0.0;
         int64_t gi = rel[i], gj = rel[j];
         if (gi > gj) { const int64_t t = gi; gi = gj; gj = t; }
-        const double c = i / TN < j / TN ? 2.0 : 1.0;
-        return c * p_elem(s, m, gi, gj);
+        const double pv = p_elem(s, m, gi, gj);
+        // c_IJ = 2 off the diagonal tiles: exact, as one more in the exponent field (zero and
+        // subnormal values, which give no digits, are left as they are)
+        const long long pb = __double_as_longlong(pv);
+        return (i / TN < j / TN && ((pb >> 52) & 0x7FF) != 0) ? __longlong_as_double(pb + (1LL << 52)) : pv;
     };
     long long mb = 0;
     for (int u = threadIdx.x; u < N * N; u += blockDim.x) mb = max(mb, abs_bits(pval(u / N, u % N)));
