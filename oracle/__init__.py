@@ -74,6 +74,8 @@ def _load():
         lib.or_hamiltonian_block.restype = C.c_int
         lib.or_density.argtypes = [P, I64, P, P, P, P, P, P, P]
         lib.or_density.restype = C.c_int
+        lib.or_density_gradient.argtypes = [P, I64, P, P, P, P, P]
+        lib.or_density_gradient.restype = C.c_int
         lib.or_bruteforce.argtypes = [P, I64, P, P, P, P, P, P, P]
         lib.or_bruteforce.restype = C.c_int
         lib.or_partition.argtypes = [I64, P, I64, P, P]
@@ -202,6 +204,18 @@ class Oracle:
                                  C.byref(self.pole_count))
         _check(st, "density")
         return n, D, (Ne.value if w is not None else None)
+
+    def density_gradient(self, pts, P):
+        """grad n at each point ([n, 3]) and the magnitude sums 2 sum_ij |d_c phi_i P_ij phi_j| ([n, 3])."""
+        pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+        P = np.ascontiguousarray(P, dtype=np.float64)
+        assert P.shape == (self.nb, self.nb)
+        g = np.zeros((pts.shape[0], 3))
+        Dg = np.zeros((pts.shape[0], 3))
+        st = self.lib.or_density_gradient(self.sp, pts.shape[0], _ptr(pts), _ptr(P), _ptr(g), _ptr(Dg),
+                                          C.byref(self.pole_count))
+        _check(st, "density_gradient")
+        return g, Dg
 
     def bruteforce(self, pts, w, v, P):
         pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)

@@ -418,6 +418,40 @@ int or_density(const or_sys *S, int64_t n_pts, const double *pts, const double *
     return status;
 }
 
+/* Gradient of the density (Sec. 2, the density gradients needed by GGA functionals, "straightforward
+ * extensions of Eq. Density"): differentiating n = sum_ij phi_i P_ij phi_j gives
+ *     grad n = sum_ij P_ij (grad phi_i phi_j + phi_i grad phi_j) = 2 sum_ij grad phi_i P_ij phi_j
+ * for symmetric P. g[3p + c] is component c at point p; Dg[3p + c] = 2 sum_ij |d_c phi_i P_ij phi_j|
+ * (the sum of the term magnitudes, the error denominator). Compensated sums.                 */
+int or_density_gradient(const or_sys *S, int64_t n_pts, const double *pts, const double *P, double *g,
+                        double *Dg, int64_t *pole_count) {
+    int64_t nb = or_n_basis(S);
+    int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nb ? nb : 1));
+    double *phi = (double *)malloc(sizeof(double) * (size_t)(nb ? nb : 1));
+    double *grad = (double *)malloc(sizeof(double) * 3 * (size_t)(nb ? nb : 1));
+    if (!idx || !phi || !grad) { free(idx); free(phi); free(grad); return -1; }
+    int status = 0;
+    for (int64_t p = 0; p < n_pts; p++) {
+        int64_t cnt = point_basis(S, pts + 3 * p, idx, phi, grad, pole_count, 0);
+        if (cnt < 0) { status = (int)cnt; break; }
+        for (int c = 0; c < 3; c++) {
+            double s = 0.0, e = 0.0, ds = 0.0, de = 0.0;
+            for (int64_t a = 0; a < cnt; a++) {
+                const double *row = P + (size_t)idx[a] * (size_t)nb;
+                for (int64_t b = 0; b < cnt; b++) {
+                    double t = 2.0 * grad[3 * a + c] * row[idx[b]] * phi[b];
+                    neu_add(&s, &e, t);
+                    neu_add(&ds, &de, fabs(t));
+                }
+            }
+            g[3 * p + c] = s + e;
+            if (Dg) Dg[3 * p + c] = ds + de;
+        }
+    }
+    free(idx); free(phi); free(grad);
+    return status;
+}
+
 /* Brute force for tiny inputs: phi for every basis function at every point (zeros
  * included) and a triple loop over p, i, j, with no batching and no relevance pruning.   */
 int or_bruteforce(const or_sys *S, int64_t n_pts, const double *pts, const double *w, const double *v,

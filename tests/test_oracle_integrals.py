@@ -211,3 +211,39 @@ def test_block_equals_full(small_molecule):
     F = np.array([0, 3, 7, 12, 19])
     Hb, Ab = o.hamiltonian_block(F, s.pt_xyz, s.pt_w, v)
     assert np.all(np.abs(Hb - H[np.ix_(F, F)]) <= 1e-15 * Ab + 1e-300)
+
+
+def test_density_gradient_matches_finite_differences(small_molecule):
+    """grad n = 2 sum_ij grad phi_i P_ij phi_j against central differences of n itself."""
+    s, o = small_molecule
+    P = synth.density_matrix(s, 3)
+    rng = np.random.Generator(np.random.PCG64(17))
+    pts = s.pt_xyz[rng.choice(s.n_points, 60, replace=False)]
+    g, Dg = o.density_gradient(pts, P)
+    h = 1e-4
+    for c in range(3):
+        e = np.zeros(3)
+        e[c] = h
+        npl, _, _ = o.density(pts + e, P)
+        nmi, _, _ = o.density(pts - e, P)
+        fd = (npl - nmi) / (2 * h)
+        assert np.all(np.abs(g[:, c] - fd) <= 1e-6 * Dg[:, c] + 1e-12), c
+
+
+def test_density_gradient_single_s_function():
+    """One s function R = N exp(-a r^2) (a large enough that the cutoff smoothing is below 1e-15)
+    and P = [[p]]: n = p R^2 / 4 pi, grad n = 2 p R R' r_hat / 4 pi with R' = -2 a r R."""
+    a, p = 2.0, 0.7
+    sp = synth.Species(ls=[0], alphas=[a], Z=1.0)
+    s = synth.make_system([[0.0, 0.0, 0.0]], [0], [sp], n_rad=8, n_theta=4, n_phi=5, n_rgrid=4000)
+    o = Oracle(s)
+    rng = np.random.Generator(np.random.PCG64(3))
+    pts = rng.normal(size=(40, 3)) * 0.8
+    g, _ = o.density_gradient(pts, np.array([[p]]))
+    r = np.linalg.norm(pts, axis=1)
+    N = synth.gaussian_norm(0, a)
+    R = N * np.exp(-a * r * r)
+    exact = (2 * p * R * (-2 * a * r * R) / (4 * np.pi))[:, None] * pts / r[:, None]
+    # the spline reproduces the Gaussian to ~1e-6 relative in its far tail (r ~ 2.7 here)
+    assert np.all(np.abs(g - exact) <= 1e-6 * np.abs(exact) + 1e-10 * np.abs(exact).max())
+    assert np.all(np.abs(g - exact)[r < 1.5] <= 1e-8 * np.abs(exact)[r < 1.5])
