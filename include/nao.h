@@ -216,6 +216,21 @@ nao_status nao_integrate_h_many(nao_grid *g, const double *const *v_dev, uint32_
 nao_status nao_update_density_many(nao_grid *g, const double *const *P_dev, nao_precision prec,
                                    double *const *n_dev, double *const *n_electrons_dev, void *cuda_stream);
 
+/* Density and its gradient (Sec. 2: the density gradients GGA functionals need, "straightforward
+ * extensions of Eq. Density"; Sec. "Density and Density Derivatives"):
+ *     grad n(r_p) = 2 sum_ij grad phi_i(r_p) P_ij phi_j(r_p)   (P symmetric),
+ * computed with n from one product T = Phi P over all of P (no tile-pair symmetry), so one call
+ * costs about twice nao_update_density plus the gradient evaluation. grad_dev: device
+ * [3 * n_points], component-major (d/dx for every point, then d/dy, then d/dz), original point
+ * order; n_dev and n_electrons_dev as nao_update_density. NAO_FP64 and NAO_FP32 only
+ * (NAO_SPLIT: NAO_ERR_UNSUPPORTED). The _many form: host arrays of per-system device pointers
+ * as nao_update_density_many, grad_dev[m] of 3 * n_points(m) entries.                       */
+nao_status nao_update_density_gradient(nao_grid *g, const double *P_dev, nao_precision prec, double *n_dev,
+                                       double *grad_dev, double *n_electrons_dev, void *cuda_stream);
+nao_status nao_update_density_gradient_many(nao_grid *g, const double *const *P_dev, nao_precision prec,
+                                            double *const *n_dev, double *const *grad_dev,
+                                            double *const *n_electrons_dev, void *cuda_stream);
+
 /* The same two operations with HOST buffers: the library copies the inputs to the device,
  * runs the operation on the given stream, copies the results back and synchronises the
  * stream before returning. Host buffers may be pageable or pinned (pinned is faster).

@@ -485,10 +485,11 @@ nao_status build(nao_grid *g, const nao_system_desc *descs, int32_t n_sys, const
         (st = upload(g, &g->d_sys_dw0, g->sys_dw0.data(), g->sys_dw0.size())) ||
         (st = upload(g, &g->d_zero_tasks, g->zero_tasks.data(), g->zero_tasks.size())) ||
         (st = upload(g, &g->d_mirror_tasks, g->mirror_tasks.data(), g->mirror_tasks.size())) ||
-        (st = dev_alloc(g, &g->d_tab, 5 * (size_t)n_sys)))
+        (st = upload(g, &g->d_sys_np, g->sys_np.data(), g->sys_np.size())) ||
+        (st = dev_alloc(g, &g->d_tab, 6 * (size_t)n_sys)))
         return st;
-    NAO_CUDA(cudaMemsetAsync(g->d_tab, 0, 5 * (size_t)n_sys * sizeof(double *), g->setup));
-    g->h_tab.assign(5 * (size_t)n_sys, nullptr);
+    NAO_CUDA(cudaMemsetAsync(g->d_tab, 0, 6 * (size_t)n_sys * sizeof(double *), g->setup));
+    g->h_tab.assign(6 * (size_t)n_sys, nullptr);
 
     DevSystem &s = g->sys;
     s.atom_xyz = d_atoms;
@@ -520,6 +521,8 @@ nao_status build(nao_grid *g, const nao_system_desc *descs, int32_t n_sys, const
     s.sys.P = g->d_tab + 2 * n_sys;
     s.sys.n = g->d_tab + 3 * n_sys;
     s.sys.ne = g->d_tab + 4 * n_sys;
+    s.sys.gn = g->d_tab + 5 * n_sys;
+    s.sys.np = g->d_sys_np;
     s.n_rgrid = g->n_rgrid;
     s.r0 = g->r0;
     s.inv_delta = 1.0 / g->delta;
@@ -891,7 +894,7 @@ nao_status enqueue_h(nao_grid *g, uint32_t terms, nao_precision prec, cudaStream
     return NAO_OK;
 }
 
-nao_status enqueue_n(nao_grid *g, nao_precision prec, bool want_ne, cudaStream_t st) {
+nao_status enqueue_n(nao_grid *g, nao_precision prec, bool want_ne, bool grad, cudaStream_t st) {
     const DevSystem &s = g->sys;
     if (prec == NAO_SPLIT) {
         const int S = g->split_S;
@@ -912,9 +915,11 @@ nao_status enqueue_n(nao_grid *g, nao_precision prec, bool want_ne, cudaStream_t
         if (want_ne) NAO_CUDA(launch_wn_partial(s, g->d_dwork, 0, (int32_t)g->n_dwork, g->d_ne_part, st));
     } else {
         for (const Chunk &c : g->chunks) {
-            NAO_CUDA(timed(g, NAO_K_EVAL_PHI, st, [&] { return launch_eval(s, c.b0, c.b1, prec, false, g->d_scratch, st); }));
+            NAO_CUDA(timed(g, grad ? NAO_K_EVAL_GRAD : NAO_K_EVAL_PHI, st,
+                           [&] { return launch_eval(s, c.b0, c.b1, prec, grad, g->d_scratch, st); }));
             NAO_CUDA(timed(g, prec == NAO_FP32 ? NAO_K_N_FP32 : NAO_K_N_FP64, st, [&] {
-                return launch_density_simt(s, prec, g->d_dwork, c.dw0, c.dw1 - c.dw0, g->d_scratch, g->d_ne_part, st);
+                return launch_density_simt(s, prec, g->d_dwork, c.dw0, c.dw1 - c.dw0, g->d_scratch, g->d_ne_part, grad,
+                                           st);
             }));
         }
     }
@@ -933,15 +938,17 @@ nao_status run_h(nao_grid *g, uint32_t terms, nao_precision prec, cudaStream_t s
     return run_maybe_graph(g, key, st, [&](cudaStream_t s2) { return enqueue_h(g, terms, prec, s2); });
 }
 
-// n (and N_e where a table entry is set) of every system from sections 2 (P), 3 (n), 4 (N_e).
-nao_status run_n(nao_grid *g, nao_precision prec, cudaStream_t st) {
+// n (and N_e where a table entry is set, grad n when asked for) of every system from sections
+// 2 (P), 3 (n), 4 (N_e), 5 (grad n).
+nao_status run_n(nao_grid *g, nao_precision prec, cudaStream_t st, bool grad = false) {
     nao_status rs;
+    if (prec == NAO_SPLIT && grad) return fail(NAO_ERR_UNSUPPORTED, "the density gradient runs on NAO_FP64 and NAO_FP32");
     if (prec == NAO_SPLIT && (rs = split_setup(g))) return rs;
-    if ((rs = upload_tables(g, 2, 3, st))) return rs;
+    if ((rs = upload_tables(g, 2, grad ? 4 : 3, st))) return rs;
     bool want_ne = false;
     for (int m = 0; m < g->n_sys; m++) want_ne = want_ne || g->h_tab[4 * (size_t)g->n_sys + m] != nullptr;
-    const uint64_t key = (uint64_t)2 << 40 | (uint64_t)prec << 8 | (want_ne ? 1u : 0u);
-    return run_maybe_graph(g, key, st, [&](cudaStream_t s2) { return enqueue_n(g, prec, want_ne, s2); });
+    const uint64_t key = (uint64_t)2 << 40 | (uint64_t)prec << 8 | (want_ne ? 1u : 0u) | (grad ? 2u : 0u);
+    return run_maybe_graph(g, key, st, [&](cudaStream_t s2) { return enqueue_n(g, prec, want_ne, grad, s2); });
 }
 
 void set_tab(nao_grid *g, int section, int m, const void *p) { g->h_tab[(size_t)section * g->n_sys + m] = const_cast<void *>(p); }
@@ -1170,6 +1177,36 @@ nao_status nao_update_density_many(nao_grid *g, const double *const *P_dev, nao_
     }
     if ((st = run_n(g, prec, static_cast<cudaStream_t>(cuda_stream)))) return st;
     return mark_done(g, static_cast<cudaStream_t>(cuda_stream));
+}
+
+nao_status nao_update_density_gradient_many(nao_grid *g, const double *const *P_dev, nao_precision prec,
+                                            double *const *n_dev, double *const *grad_dev,
+                                            double *const *n_electrons_dev, void *cuda_stream) {
+    nao_status st = check_handle(g);
+    if (st) return st;
+    if (!P_dev || !n_dev || !grad_dev) return fail(NAO_ERR_INVALID_ARG, "P_dev, n_dev or grad_dev is NULL");
+    for (int m = 0; m < g->n_sys; m++)
+        if (!P_dev[m] || !n_dev[m] || !grad_dev[m])
+            return fail(NAO_ERR_INVALID_ARG, "P_dev, n_dev or grad_dev entry " + std::to_string(m) + " is NULL");
+    if ((st = check_prec(prec))) return st;
+    DeviceGuard guard(g->device);
+    if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    for (int m = 0; m < g->n_sys; m++) {
+        set_tab(g, 2, m, P_dev[m]);
+        set_tab(g, 3, m, n_dev[m]);
+        set_tab(g, 4, m, n_electrons_dev ? n_electrons_dev[m] : nullptr);
+        set_tab(g, 5, m, grad_dev[m]);
+    }
+    if ((st = run_n(g, prec, static_cast<cudaStream_t>(cuda_stream), true))) return st;
+    return mark_done(g, static_cast<cudaStream_t>(cuda_stream));
+}
+
+nao_status nao_update_density_gradient(nao_grid *g, const double *P_dev, nao_precision prec, double *n_dev,
+                                       double *grad_dev, double *n_electrons_dev, void *cuda_stream) {
+    nao_status st = check_handle(g);
+    if (st || (st = check_single(g))) return st;
+    double *const ne[1] = {n_electrons_dev};
+    return nao_update_density_gradient_many(g, &P_dev, prec, &n_dev, &grad_dev, ne, cuda_stream);
 }
 
 static nao_status ensure_staging(nao_grid *g) {

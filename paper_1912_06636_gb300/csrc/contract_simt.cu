@@ -189,7 +189,10 @@ __global__ void __launch_bounds__(256) zero_h_kernel(DevSystem s, const int4 *__
     for (int i = threadIdx.x; i < tk.z; i += blockDim.x) H[i] = 0.0;
 }
 
-template <typename T>
+// GRADN: the density gradient too (Sec. 2; grad n = 2 sum_ij grad phi_i P_ij phi_j): with
+// T_qj = sum_i phi_qi P_ij over all of P (no tile-pair symmetry), n_q = sum_j T_qj phi_qj and
+// grad n_q = 2 sum_j T_qj grad phi_qj; the scratch rows then hold [phi | d/dx | d/dy | d/dz].
+template <typename T, bool GRADN>
 __global__ void __launch_bounds__(256) density_simt_kernel(DevSystem s, const DWork *__restrict__ work, int32_t w0,
                                                           const T *__restrict__ scratch, double *__restrict__ ne_part) {
     constexpr int KC = Cfg<T>::KC;
@@ -197,6 +200,7 @@ __global__ void __launch_bounds__(256) density_simt_kernel(DevSystem s, const DW
     __shared__ __align__(16) T As[KC][T_];  // phi[i][q]
     __shared__ __align__(16) T Bs[KC][T_];  // c_IJ P[rel_i][rel_j]
     __shared__ double nacc[T_];
+    __shared__ double gacc[GRADN ? 3 : 1][T_];
     __shared__ double red[8];
     const DWork it = work[w0 + blockIdx.x];
     const int b = it.batch, m = s.sys.bmol[b];
@@ -204,25 +208,29 @@ __global__ void __launch_bounds__(256) density_simt_kernel(DevSystem s, const DW
     const int Ppad = (P + NAO_PPAD - 1) & ~(NAO_PPAD - 1);
     const int N = s.rel_off[b + 1] - s.rel_off[b];
     const int q0 = it.tp * T_;
-    const T *E = scratch + s.scr_off[b];  // phi only: row stride Ppad
+    const T *E = scratch + s.scr_off[b];  // row stride Ppad (phi only) or 4 Ppad (GRADN)
+    const int64_t ld = GRADN ? 4 * (int64_t)Ppad : (int64_t)Ppad;
     const int32_t *rel = s.rel_idx + s.rel_off[b];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int nt = (N + T_ - 1) / T_;
-    if (tid < T_) nacc[tid] = 0.0;
+    if (tid < T_) {
+        nacc[tid] = 0.0;
+        if (GRADN) gacc[0][tid] = gacc[GRADN ? 1 : 0][tid] = gacc[GRADN ? 2 : 0][tid] = 0.0;
+    }
 
     // loader mapping: row lk of the chunk, RPT consecutive columns starting at lc
     const int lk = tid / (T_ / RPT), lc = (tid % (T_ / RPT)) * RPT;
     for (int tj = 0; tj < nt; tj++) {
         Block<T> acc;
         acc.zero();
-        for (int ti = 0; ti <= tj; ti++) {
-            const double scale = ti < tj ? 2.0 : 1.0;
+        for (int ti = 0; ti < (GRADN ? nt : tj + 1); ti++) {
+            const double scale = (!GRADN && ti < tj) ? 2.0 : 1.0;
             for (int k0 = 0; k0 < T_; k0 += KC) {
                 const int i = ti * T_ + k0 + lk;
                 T fv[RPT];
 #pragma unroll
                 for (int u = 0; u < RPT; u++) fv[u] = T(0);
-                if (i < N && q0 + lc < Ppad) load_vec(E + (int64_t)i * Ppad + q0 + lc, fv);
+                if (i < N && q0 + lc < Ppad) load_vec(E + (int64_t)i * ld + q0 + lc, fv);
 #pragma unroll
                 for (int u = 0; u < RPT; u++) {
                     As[lk][lc + u] = fv[u];
@@ -245,16 +253,30 @@ __global__ void __launch_bounds__(256) density_simt_kernel(DevSystem s, const DW
 #pragma unroll
         for (int a = 0; a < 4; a++) {
             const int q = q0 + ty * 4 + a;
-            double part = 0.0;
+            double part = 0.0, gp[3] = {0.0, 0.0, 0.0};
 #pragma unroll
             for (int c = 0; c < 4; c++) {
                 const int j = tj * T_ + tx * 4 + c;
-                const double f = (j < N && q < Ppad) ? (double)E[(int64_t)j * Ppad + q] : 0.0;
-                part += acc.value(a, c) * f;
+                const bool ok = j < N && q < Ppad;
+                const double tv = acc.value(a, c);
+                part += tv * (ok ? (double)E[(int64_t)j * ld + q] : 0.0);
+                if (GRADN)
+#pragma unroll
+                    for (int d = 0; d < 3; d++) gp[d] += tv * (ok ? (double)E[(int64_t)j * ld + (d + 1) * Ppad + q] : 0.0);
             }
 #pragma unroll
-            for (int o = 8; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-            if (tx == 0) nacc[ty * 4 + a] += part;
+            for (int o = 8; o > 0; o >>= 1) {
+                part += __shfl_xor_sync(0xffffffffu, part, o);
+                if (GRADN)
+#pragma unroll
+                    for (int d = 0; d < 3; d++) gp[d] += __shfl_xor_sync(0xffffffffu, gp[d], o);
+            }
+            if (tx == 0) {
+                nacc[ty * 4 + a] += part;
+                if (GRADN)
+#pragma unroll
+                    for (int d = 0; d < 3; d++) gacc[d][ty * 4 + a] += 2.0 * gp[d];
+            }
         }
         __syncthreads();
     }
@@ -265,6 +287,9 @@ __global__ void __launch_bounds__(256) density_simt_kernel(DevSystem s, const DW
         if (q < P) {
             const double nv = nacc[tid];
             *n_at(s, m, p0 + q) = nv;
+            if (GRADN)
+#pragma unroll
+                for (int d = 0; d < 3; d++) *gn_at(s, m, p0 + q, d) = gacc[d][tid];
             wn = s.pw[p0 + q] * nv;
         }
     }
@@ -341,13 +366,13 @@ cudaError_t launch_mirror(const DevSystem &s, const int4 *tasks, int32_t n_tasks
 }
 
 cudaError_t launch_density_simt(const DevSystem &s, nao_precision prec, const DWork *work, int32_t w0, int32_t n_work,
-                                const double *scratch, double *ne_part, cudaStream_t st) {
+                                const double *scratch, double *ne_part, bool grad, cudaStream_t st) {
     if (n_work <= 0) return cudaSuccess;
-    if (prec == NAO_FP32)
-        density_simt_kernel<float><<<n_work, 256, 0, st>>>(s, work, w0, reinterpret_cast<const float *>(scratch),
-                                                          ne_part);
-    else
-        density_simt_kernel<double><<<n_work, 256, 0, st>>>(s, work, w0, scratch, ne_part);
+    const float *sf = reinterpret_cast<const float *>(scratch);
+    if (prec == NAO_FP32 && grad) density_simt_kernel<float, true><<<n_work, 256, 0, st>>>(s, work, w0, sf, ne_part);
+    else if (prec == NAO_FP32) density_simt_kernel<float, false><<<n_work, 256, 0, st>>>(s, work, w0, sf, ne_part);
+    else if (grad) density_simt_kernel<double, true><<<n_work, 256, 0, st>>>(s, work, w0, scratch, ne_part);
+    else density_simt_kernel<double, false><<<n_work, 256, 0, st>>>(s, work, w0, scratch, ne_part);
     return cudaGetLastError();
 }
 

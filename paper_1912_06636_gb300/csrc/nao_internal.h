@@ -46,6 +46,8 @@ struct SysTables {
     const double *const *P;  // [n_sys] this call's P of each system
     double *const *n;        // [n_sys] this call's n of each system
     double *const *ne;       // [n_sys] this call's N_e of each system (NULL entry: not formed)
+    double *const *gn;       // [n_sys] this call's grad n of each system ([3][np], component-major)
+    const int32_t *np;       // [n_sys] points of the system
 };
 
 // Geometry and tables shared by every kernel (device pointers).
@@ -90,6 +92,10 @@ __device__ __forceinline__ double v_at(const DevSystem &s, int m, int p) {
 }
 __device__ __forceinline__ double *n_at(const DevSystem &s, int m, int p) {
     return s.sys.n[m] + (s.perm[p] - s.sys.poff[m]);
+}
+// component c of grad n at batch-ordered point p of system m
+__device__ __forceinline__ double *gn_at(const DevSystem &s, int m, int p, int c) {
+    return s.sys.gn[m] + (int64_t)c * s.sys.np[m] + (s.perm[p] - s.sys.poff[m]);
 }
 #endif
 
@@ -188,8 +194,8 @@ struct nao_grid {
     std::vector<int4> zero_tasks;      // (system, start element, count, 0) chunks of each H
     std::vector<int4> mirror_tasks;    // (system, column tile, row tile, 0) with row <= column
     int4 *d_zero_tasks = nullptr, *d_mirror_tasks = nullptr;
-    int32_t *d_sys_dw0 = nullptr;
-    double **d_tab = nullptr;          // device: [5][n_sys] pointer tables H, v, P, n, N_e
+    int32_t *d_sys_dw0 = nullptr, *d_sys_np = nullptr;
+    double **d_tab = nullptr;          // device: [6][n_sys] pointer tables H, v, P, n, N_e, grad n
     std::vector<void *> h_tab;         // host copy of the tables
     // split (tensor-core) path, set up on its first use
     struct SplitChunk {
@@ -249,8 +255,10 @@ cudaError_t launch_h_simt(const DevSystem &s, nao_precision prec, const HWork *w
                           const double *scratch, uint32_t terms, cudaStream_t st);
 cudaError_t launch_zero_h(const DevSystem &s, const int4 *tasks, int32_t n_tasks, cudaStream_t st);
 cudaError_t launch_mirror(const DevSystem &s, const int4 *tasks, int32_t n_tasks, cudaStream_t st);
+// grad: also grad n = 2 sum_j T_qj grad phi_jq with T = Phi P over all of P (the scratch then holds
+// phi and grad phi, rows of 4 Ppad)
 cudaError_t launch_density_simt(const DevSystem &s, nao_precision prec, const DWork *work, int32_t w0, int32_t n_work,
-                                const double *scratch, double *ne_part, cudaStream_t st);
+                                const double *scratch, double *ne_part, bool grad, cudaStream_t st);
 // N_e of every system: sum of its density work items' partial sums (deterministic order)
 cudaError_t launch_reduce_ne(const DevSystem &s, const double *part, const int32_t *sys_dw0, int32_t n_sys,
                              cudaStream_t st);

@@ -33,7 +33,7 @@ SYMBOLS = [
     "nao_evaluate_batch", "nao_sync_status", "nao_status_string", "nao_last_error",
     "nao_profile_enable", "nao_profile_read", "nao_integrate_h_noalloc",
     "nao_grid_create_many", "nao_get_system", "nao_integrate_h_many", "nao_update_density_many",
-    "nao_get_tuning",
+    "nao_get_tuning", "nao_update_density_gradient", "nao_update_density_gradient_many",
 ]
 NAO_NOALLOC_SCRATCH_BYTES = 32 << 20
 KERNELS = ["eval_grad", "eval_phi", "h_fp64", "h_fp32", "h_split", "slice_h", "mirror", "n_fp64", "n_fp32",
@@ -110,6 +110,8 @@ def load():
         "nao_integrate_h_many": ([P, P, U32, C.c_int, P, P], C.c_int),
         "nao_update_density_many": ([P, P, C.c_int, P, P, P], C.c_int),
         "nao_get_tuning": ([P, P, P], C.c_int),
+        "nao_update_density_gradient": ([P, P, C.c_int, P, P, P, P], C.c_int),
+        "nao_update_density_gradient_many": ([P, P, C.c_int, P, P, P, P], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -273,6 +275,17 @@ def nao_update_density_many(h, Ps, prec, ns, nes=None, stream=None) -> None:
                                           _ptr_array(nes, True), _stream(stream)), "nao_update_density_many")
 
 
+def nao_update_density_gradient(h, P, prec, n, grad, ne=None, stream=None) -> None:
+    _check(load().nao_update_density_gradient(h, _dptr(P), _prec(prec), _dptr(n), _dptr(grad), _dptr(ne),
+                                              _stream(stream)), "nao_update_density_gradient")
+
+
+def nao_update_density_gradient_many(h, Ps, prec, ns, grads, nes=None, stream=None) -> None:
+    _check(load().nao_update_density_gradient_many(h, _ptr_array(Ps, False), _prec(prec), _ptr_array(ns, False),
+                                                   _ptr_array(grads, False), _ptr_array(nes, True), _stream(stream)),
+           "nao_update_density_gradient_many")
+
+
 def nao_integrate_h_host(h, v: np.ndarray | None, terms: int, prec, H: np.ndarray, stream=None) -> None:
     vp = None if v is None else np.ascontiguousarray(v, dtype=np.float64).ctypes.data
     assert H.dtype == np.float64 and H.flags.c_contiguous
@@ -407,6 +420,28 @@ class Grid:
             nes = [torch.empty(1, dtype=torch.float64, device=self.device) for _ in self.systems]
         nao_update_density_many(self.h, Ps, prec, ns, nes, stream)
         return ns, nes
+
+    def density_gradient(self, P, prec="fp64", n=None, grad=None, ne=None, stream=None, want_ne=True):
+        """n, grad n ([3, n_points]) and N_e of a single-system handle."""
+        import torch
+
+        if n is None:
+            n = torch.empty(self.n_points, dtype=torch.float64, device=self.device)
+        if grad is None:
+            grad = torch.empty((3, self.n_points), dtype=torch.float64, device=self.device)
+        if ne is None and want_ne:
+            ne = torch.empty(1, dtype=torch.float64, device=self.device)
+        nao_update_density_gradient(self.h, P, prec, n, grad, ne, stream)
+        return n, grad, ne
+
+    def density_gradient_many(self, Ps, prec="fp64", stream=None):
+        import torch
+
+        ns = [torch.empty(s["n_points"], dtype=torch.float64, device=self.device) for s in self.systems]
+        gs = [torch.empty((3, s["n_points"]), dtype=torch.float64, device=self.device) for s in self.systems]
+        nes = [torch.empty(1, dtype=torch.float64, device=self.device) for _ in self.systems]
+        nao_update_density_gradient_many(self.h, Ps, prec, ns, gs, nes, stream)
+        return ns, gs, nes
 
     def evaluate_batch(self, b: int, prec="fp64", grad=True, stream=None):
         import torch
