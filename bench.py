@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=16,
                     help="requests of the serving stream (Poisson arrivals at 200/s, 3-200 atoms)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving stream")
+    ap.add_argument("--grouped-molecules", type=int, default=128,
+                    help="molecules of the grouped-launch comparison (0 skips it)")
     return ap.parse_args()
 
 
@@ -173,6 +175,66 @@ TRAFFIC_PER_FLOP_H = {
     ("h_split", 10): (24.612e9 / (2 * 9.1321260e10), "profiles/traffic_diamond64_split.md"),
     ("h_fp64", 0): ((359.834112e6 + 3.945472e6) / 4.6096304e9, "profiles/h_simt_kernel_diamond8_fp64.md"),
 }
+
+
+GROUP_GRID = dict(n_rad=30, n_theta=8, n_phi=9)
+
+
+def grouped(n_mol: int, device: int, steps: int = 3) -> dict:
+    """Many molecules: one grouped handle (one launch per kernel for all of them, CUDA graphs)
+    against one handle per molecule, the same H + n step on one stream, split path."""
+    import torch
+
+    from paper_1912_06636_gb300 import nao, synth
+
+    t0 = time.perf_counter()
+    systems, bs = synth.molecule_set(n_mol, seed=3000, n_min=3, n_max=60, b_min=20, b_max=336, **GROUP_GRID)
+    dev = torch.device("cuda", device)
+    vs = [torch.from_numpy(s.potential()).to(dev) for s in systems]
+    Ps = [torch.from_numpy(synth.density_matrix(s, 3000 + k)).to(dev) for k, s in enumerate(systems)]
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"{n_mol} molecules of 3-60 atoms (log-uniform, seed 3000; species Si/A/B), "
+                       f"{GROUP_GRID['n_rad']}x{GROUP_GRID['n_theta'] * GROUP_GRID['n_phi']} points per atom, "
+                       "batch sizes log-uniform in [20, 336]; one step = H + n of every molecule, split path "
+                       "(12 slices)",
+           "points": int(sum(s.n_points for s in systems)), "generate_s": gen_s}
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps
+
+    g = nao.Grid(systems, device=device, batch_points=bs, capture_graph=1)
+    Hs = [torch.empty((s["n_basis"], s["n_basis"]), dtype=torch.float64, device=dev) for s in g.systems]
+    ns = [torch.empty(s["n_points"], dtype=torch.float64, device=dev) for s in g.systems]
+    nes = [torch.empty(1, dtype=torch.float64, device=dev) for _ in g.systems]
+    ms_g = timed(lambda: (g.integrate_h_many(vs, prec="split", Hs=Hs, stream=stream),
+                          g.update_density_many(Ps, prec="split", ns=ns, nes=nes, stream=stream)))
+    g.sync()
+    g.close()
+    singles = [nao.Grid(s, device=device, max_batch_points=b) for s, b in zip(systems, bs)]
+
+    def one_by_one():
+        for k, h in enumerate(singles):
+            h.integrate_h(vs[k], prec="split", H=Hs[k], stream=stream)
+            h.update_density(Ps[k], prec="split", n=ns[k], ne=nes[k], stream=stream)
+
+    ms_s = timed(one_by_one)
+    for h in singles:
+        h.sync()
+        h.close()
+    pts = out["points"]
+    out.update({"grouped_ms_per_step": ms_g, "grouped_points_per_s": pts / (ms_g / 1e3),
+                "per_molecule_ms_per_step": ms_s, "per_molecule_points_per_s": pts / (ms_s / 1e3),
+                "speedup_grouped": ms_s / ms_g})
+    return out
 
 
 def g_split_pairs(g) -> int:
@@ -479,6 +541,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_serve and args.serve_requests > 0:
         g.close()
         line["serving"] = serving(args.serve_requests, local_rank)
+    if rank == 0 and world == 1 and args.grouped_molecules > 0:
+        if g.h:
+            g.close()
+        line["grouped"] = grouped(args.grouped_molecules, local_rank)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(s, v_np, P_np, args.cpu_sample)

@@ -898,18 +898,20 @@ nao_status enqueue_n(nao_grid *g, nao_precision prec, bool want_ne, bool grad, c
     const DevSystem &s = g->sys;
     if (prec == NAO_SPLIT) {
         const int S = g->split_S;
-        NAO_CUDA(launch_zero_n(s, g->d_dwork, (int32_t)g->n_dwork, st));
+        NAO_CUDA(launch_zero_n(s, g->d_dwork, (int32_t)g->n_dwork, grad, st));
         for (const auto &c : g->split_chunks) {
-            NAO_CUDA(timed(g, NAO_K_EVAL_PHI, st, [&] { return launch_eval(s, c.b0, c.b1, NAO_FP64, false, g->d_scratch, st); }));
+            NAO_CUDA(timed(g, grad ? NAO_K_EVAL_GRAD : NAO_K_EVAL_PHI, st,
+                           [&] { return launch_eval(s, c.b0, c.b1, NAO_FP64, grad, g->d_scratch, st); }));
             NAO_CUDA(timed(g, NAO_K_SLICE_N, st, [&] {
                 return launch_slice_n(s, c.b0, c.b1, c.max_qt, g->d_scratch, g->d_slices, g->d_sl_off_n, g->d_expo_q,
-                                      g->d_expo_b, g->d_split_tn, S, st);
+                                      g->d_expo_b, g->d_split_tn, S, grad, st);
             }));
             for (int k = 0; k < 2; k++)
                 if (c.nw1[k] > c.nw0[k])
                 NAO_CUDA(timed(g, NAO_K_N_SPLIT, st, [&] {
                     return launch_n_tc(s, g->d_split_nw, c.nw0[k], c.nw1[k] - c.nw0[k], g->d_slices, g->d_sl_off_n,
-                                       g->d_expo_q, g->d_expo_b, g->d_scratch, S, k == 0 ? 48 : 32, g->d_err, st);
+                                       g->d_expo_q, g->d_expo_b, g->d_scratch, S, k == 0 ? 48 : 32, grad, g->d_err,
+                                       st);
                 }));
         }
         if (want_ne) NAO_CUDA(launch_wn_partial(s, g->d_dwork, 0, (int32_t)g->n_dwork, g->d_ne_part, st));
@@ -942,7 +944,6 @@ nao_status run_h(nao_grid *g, uint32_t terms, nao_precision prec, cudaStream_t s
 // 2 (P), 3 (n), 4 (N_e), 5 (grad n).
 nao_status run_n(nao_grid *g, nao_precision prec, cudaStream_t st, bool grad = false) {
     nao_status rs;
-    if (prec == NAO_SPLIT && grad) return fail(NAO_ERR_UNSUPPORTED, "the density gradient runs on NAO_FP64 and NAO_FP32");
     if (prec == NAO_SPLIT && (rs = split_setup(g))) return rs;
     if ((rs = upload_tables(g, 2, grad ? 4 : 3, st))) return rs;
     bool want_ne = false;

@@ -333,12 +333,17 @@ __global__ void set_pointers_kernel(double **__restrict__ dst, PtrBatch src, int
     for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = static_cast<double *>(src.p[i]);
 }
 
-// n = 0 at the points of each density work item (before accumulation by atomics).
-__global__ void __launch_bounds__(64) zero_n_kernel(DevSystem s, const DWork *__restrict__ work) {
+// n = 0 (and grad n = 0) at the points of each density work item: the tensor-core density
+// writes only the points of batches that have basis functions.
+__global__ void __launch_bounds__(64) zero_n_kernel(DevSystem s, const DWork *__restrict__ work, int grad) {
     const DWork it = work[blockIdx.x];
     const int p0 = s.batch_off[it.batch], P = s.batch_off[it.batch + 1] - p0;
     const int q = it.tp * NAO_TILE + threadIdx.x;
-    if (q < P) *n_at(s, s.sys.bmol[it.batch], p0 + q) = 0.0;
+    if (q >= P) return;
+    const int m = s.sys.bmol[it.batch];
+    *n_at(s, m, p0 + q) = 0.0;
+    if (grad)
+        for (int d = 0; d < 3; d++) *gn_at(s, m, p0 + q, d) = 0.0;
 }
 
 }  // namespace
@@ -395,8 +400,8 @@ cudaError_t launch_set_pointers(double **dst, void *const *src, int32_t n, cudaS
     return cudaSuccess;
 }
 
-cudaError_t launch_zero_n(const DevSystem &s, const DWork *work, int32_t n_work, cudaStream_t st) {
+cudaError_t launch_zero_n(const DevSystem &s, const DWork *work, int32_t n_work, bool grad, cudaStream_t st) {
     if (n_work <= 0) return cudaSuccess;
-    zero_n_kernel<<<n_work, 64, 0, st>>>(s, work);
+    zero_n_kernel<<<n_work, 64, 0, st>>>(s, work, grad ? 1 : 0);
     return cudaGetLastError();
 }

@@ -266,7 +266,7 @@ cudaError_t launch_reduce_ne(const DevSystem &s, const double *part, const int32
 // buffer has to outlive the call)
 cudaError_t launch_set_pointers(double **dst, void *const *src, int32_t n, cudaStream_t st);
 // n = 0 at every point of the given density work items
-cudaError_t launch_zero_n(const DevSystem &s, const DWork *work, int32_t n_work, cudaStream_t st);
+cudaError_t launch_zero_n(const DevSystem &s, const DWork *work, int32_t n_work, bool grad, cudaStream_t st);
 
 // ---- split path (split_tc.cu) ------------------------------------------------------------
 size_t split_smem_bytes(int S);
@@ -280,13 +280,14 @@ cudaError_t launch_slice_h(const DevSystem &s, int32_t b0, int32_t b1, int32_t m
 cudaError_t launch_h_tc(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
                         const int64_t *sl_off, const int32_t *expo, const int32_t *neg16, int S, int tn, int scatter,
                         int32_t *err, cudaStream_t st);
-// tn_b: per-batch tile width (the P' tiles of the density follow it)
+// tn_b: per-batch tile width (the P' tiles of the density follow it). grad: the scratch rows hold
+// [phi | grad phi] (4 Ppad) and P' = P over all tiles (density gradient)
 cudaError_t launch_slice_n(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_qt, const double *scratch,
                            uint8_t *slices, const int64_t *sl_off, int32_t *expo_q, int32_t *expo_b,
-                           const int32_t *tn_b, int S, cudaStream_t st);
+                           const int32_t *tn_b, int S, bool grad, cudaStream_t st);
 cudaError_t launch_n_tc(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
                         const int64_t *sl_off, const int32_t *expo_q, const int32_t *expo_b, const double *scratch, int S,
-                        int tn, int32_t *err, cudaStream_t st);
+                        int tn, bool grad, int32_t *err, cudaStream_t st);
 cudaError_t launch_wn_partial(const DevSystem &s, const DWork *work, int32_t w0, int32_t n_work, double *ne_part,
                               cudaStream_t st);
 

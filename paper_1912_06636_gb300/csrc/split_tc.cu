@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(256) slice_h_kernel(DevSystem s, int32_t b0, c
 template <int S>
 __global__ void __launch_bounds__(128) slice_nphi_kernel(DevSystem s, int32_t b0, const double *__restrict__ scratch,
                                                         uint8_t *__restrict__ slices, const int64_t *__restrict__ sl_off,
-                                                        int32_t *__restrict__ expo_q) {
+                                                        int32_t *__restrict__ expo_q, int ld_mult) {
     const int b = b0 + blockIdx.x, qt = blockIdx.y;
     const int p0 = s.batch_off[b], P = s.batch_off[b + 1] - p0;
     const int Ppad = (P + NAO_PPAD - 1) & ~(NAO_PPAD - 1);
@@ -252,10 +252,11 @@ __global__ void __launch_bounds__(128) slice_nphi_kernel(DevSystem s, int32_t b0
     const SplitGeom G(P, N, S);
     const int q = qt * 128 + threadIdx.x;
     if (N == 0 || q >= G.P16) return;
-    const double *E = scratch + s.scr_off[b];  // phi[i][q], stride Ppad
+    const double *E = scratch + s.scr_off[b];  // phi[i][q], row stride ld_mult Ppad (4: rows also hold grad phi)
+    const int64_t ld = (int64_t)ld_mult * Ppad;
     long long mb = 0;
     if (q < P)
-        for (int i = 0; i < N; i++) mb = max(mb, abs_bits(E[(int64_t)i * Ppad + q]));
+        for (int i = 0; i < N; i++) mb = max(mb, abs_bits(E[(int64_t)i * ld + q]));
     const int e = q < P ? row_exponent_bits(mb) : -10000;
     if (q < P) expo_q[p0 + q] = e;
     uint8_t *base = slices + sl_off[b];
@@ -264,7 +265,7 @@ __global__ void __launch_bounds__(128) slice_nphi_kernel(DevSystem s, int32_t b0
 #pragma unroll
         for (int h = 0; h < 8; h++) {
             const int i = i0 + h;
-            const double x = i < N ? E[(int64_t)i * Ppad + q] : 0.0;
+            const double x = i < N ? E[(int64_t)i * ld + q] : 0.0;
             digits<S>(x, e, dg[h]);
         }
         const int kc = i0 >> 6;
@@ -287,7 +288,7 @@ __global__ void __launch_bounds__(128) slice_nphi_kernel(DevSystem s, int32_t b0
 template <int S>
 __global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, uint8_t *__restrict__ slices,
                                                       const int64_t *__restrict__ sl_off, int32_t *__restrict__ expo_b,
-                                                      const int32_t *__restrict__ tn_b) {
+                                                      const int32_t *__restrict__ tn_b, int full) {
     __shared__ long long red[8];
     __shared__ int e_sh;
     const int b = b0 + blockIdx.x, m = s.sys.bmol[b];
@@ -298,14 +299,14 @@ __global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, 
     const int32_t *rel = s.rel_idx + s.rel_off[b];
     const int TN = tn_b[b];
     auto pval = [&](int i, int j) -> double {
-        if (i >= N || j >= N || i / TN > j / TN) return 0.0;
+        if (i >= N || j >= N || (!full && i / TN > j / TN)) return 0.0;
         int64_t gi = rel[i], gj = rel[j];
         if (gi > gj) { const int64_t t = gi; gi = gj; gj = t; }
         const double pv = p_elem(s, m, gi, gj);
         // c_IJ = 2 off the diagonal tiles: exact, as one more in the exponent field (zero and
         // subnormal values, which give no digits, are left as they are)
         const long long pb = __double_as_longlong(pv);
-        return (i / TN < j / TN && ((pb >> 52) & 0x7FF) != 0) ? __longlong_as_double(pb + (1LL << 52)) : pv;
+        return (!full && i / TN < j / TN && ((pb >> 52) & 0x7FF) != 0) ? __longlong_as_double(pb + (1LL << 52)) : pv;
     };
     long long mb = 0;
     for (int u = threadIdx.x; u < N * N; u += blockDim.x) mb = max(mb, abs_bits(pval(u / N, u % N)));
@@ -600,7 +601,9 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(128, 1)
 // One CTA per (batch, 128-point tile): the TN-function tiles J = 0 .. nJ-1 one after another
 // (tensor memory holds one tile's accumulators), each epilogue adding its part of n_q in
 // registers; the CTA then stores n for its points (no atomics: one CTA owns each point).
-template <int TN>
+// GRADN (density gradient, Sec. 2): T = Phi P over all of P (P' = P, K = every function), and the
+// epilogue also forms grad n_q = 2 sum_j T_qj grad phi_qj from the rows [phi | grad phi] of 4 Ppad.
+template <int TN, bool GRADN>
 __global__ void __launch_bounds__(128, 1) n_tc_kernel(DevSystem s, const HWork *__restrict__ work, int32_t w0,
                                                      const uint8_t *__restrict__ slices, const int64_t *__restrict__ sl_off,
                                                      const int32_t *__restrict__ expo_q, const int32_t *__restrict__ expo_b,
@@ -620,8 +623,10 @@ __global__ void __launch_bounds__(128, 1) n_tc_kernel(DevSystem s, const HWork *
     const int q = it.ti * 128 + warp * 32 + lane;
     const bool row_ok = q < P;
     const double *E = scratch + s.scr_off[b];
+    const int64_t ld = GRADN ? 4 * (int64_t)Ppad : (int64_t)Ppad;
     const uint32_t tm_row = tm + ((uint32_t)(warp * 32) << 16);
     double part_hi = 0.0, part_lo = 0.0, part_lo2 = 0.0;
+    double gr_hi[3] = {0.0, 0.0, 0.0}, gr_lo[3] = {0.0, 0.0, 0.0}, gr_lo2[3] = {0.0, 0.0, 0.0};
     int c0 = 0;
     if (threadIdx.x == 0 && *(volatile int32_t *)err != 0) pp.abort = 1;  // a timeout earlier in this launch
     __syncthreads();
@@ -635,8 +640,8 @@ __global__ void __launch_bounds__(128, 1) n_tc_kernel(DevSystem s, const HWork *
         L.b_kc = (size_t)G.R16 * 128;
         L.a_bytes = (uint32_t)min(128, G.P16 - it.ti * 128) * 128u;
         L.b_bytes = (uint32_t)min(TN, G.R16 - J * TN) * 128u;
-        // P' is zero for basis functions beyond tile J, so K stops at TN (J + 1)
-        const int nk = ((J + 1) * TN + 63) / 64;
+        // P' is zero for basis functions beyond tile J, so K stops at TN (J + 1) (all of K for GRADN)
+        const int nk = GRADN ? G.n_kcN : ((J + 1) * TN + 63) / 64;
         L.n_kc = nk < G.n_kcN ? nk : G.n_kcN;
         L.neg16 = 0;
         L.S = S;
@@ -657,19 +662,32 @@ __global__ void __launch_bounds__(128, 1) n_tc_kernel(DevSystem s, const HWork *
             for (int jj = 0; jj < 16; jj++) {
                 const int j = J * TN + cc + jj;
                 if (row_ok && j < N) {
-                    const double f = E[(int64_t)j * Ppad + q];
-                    part_hi = fma((double)v.hi[jj], f, part_hi);
-                    part_lo = fma((double)v.lo[jj], f, part_lo);
-                    if (TN != 48) part_lo2 = fma((double)v.lo2[jj], f, part_lo2);
+                    const double f = E[(int64_t)j * ld + q];
+                    const double th = (double)v.hi[jj], tl = (double)v.lo[jj], tl2 = TN != 48 ? (double)v.lo2[jj] : 0.0;
+                    part_hi = fma(th, f, part_hi);
+                    part_lo = fma(tl, f, part_lo);
+                    if (TN != 48) part_lo2 = fma(tl2, f, part_lo2);
+                    if (GRADN)
+#pragma unroll
+                        for (int d = 0; d < 3; d++) {
+                            const double gf = E[(int64_t)j * ld + (d + 1) * Ppad + q];
+                            gr_hi[d] = fma(th, gf, gr_hi[d]);
+                            gr_lo[d] = fma(tl, gf, gr_lo[d]);
+                            if (TN != 48) gr_lo2[d] = fma(tl2, gf, gr_lo2[d]);
+                        }
                 }
             }
         }
     }
     if (!pp.abort && row_ok) {
         const int eq = expo_q[p0 + q], eb = expo_b[b];
-        *n_at(s, m, p0 + q) = (eq > -10000 && eb > -10000)
-                                  ? fma(part_hi, pow2(eq + eb - 48), fma(part_lo, pow2(eq + eb - 66), part_lo2 * pow2(eq + eb - 84)))
-                                  : 0.0;
+        const bool live = eq > -10000 && eb > -10000;
+        const double s48 = pow2(eq + eb - 48), s66 = pow2(eq + eb - 66), s84 = pow2(eq + eb - 84);
+        *n_at(s, m, p0 + q) = live ? fma(part_hi, s48, fma(part_lo, s66, part_lo2 * s84)) : 0.0;
+        if (GRADN)
+#pragma unroll
+            for (int d = 0; d < 3; d++)
+                *gn_at(s, m, p0 + q, d) = live ? 2.0 * fma(gr_hi[d], s48, fma(gr_lo[d], s66, gr_lo2[d] * s84)) : 0.0;
     }
     tc_teardown(tm);
 }
@@ -700,8 +718,9 @@ size_t split_smem_bytes(int S) { return pipe_smem_bytes(S); }
 cudaError_t split_configure() {
     size_t bytes = 0;
     for (int S = 4; S <= NAO_SPLIT_MAX_SLICES; S++) bytes = split_smem_bytes(S) > bytes ? split_smem_bytes(S) : bytes;
-    const void *fns[4] = {(const void *)h_tc_kernel<48, NAO_SPLIT_CLUSTER>, (const void *)h_tc_kernel<32, NAO_SPLIT_CLUSTER>,
-                          (const void *)n_tc_kernel<48>, (const void *)n_tc_kernel<32>};
+    const void *fns[6] = {(const void *)h_tc_kernel<48, NAO_SPLIT_CLUSTER>, (const void *)h_tc_kernel<32, NAO_SPLIT_CLUSTER>,
+                          (const void *)n_tc_kernel<48, false>, (const void *)n_tc_kernel<32, false>,
+                          (const void *)n_tc_kernel<48, true>, (const void *)n_tc_kernel<32, true>};
     for (const void *f : fns) {
         const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (e != cudaSuccess) return e;
@@ -751,17 +770,18 @@ cudaError_t launch_h_tc(const DevSystem &s, const HWork *work, int32_t w0, int32
 
 cudaError_t launch_slice_n(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_qt, const double *scratch,
                            uint8_t *slices, const int64_t *sl_off, int32_t *expo_q, int32_t *expo_b,
-                           const int32_t *tn_b, int S, cudaStream_t st) {
+                           const int32_t *tn_b, int S, bool grad, cudaStream_t st) {
     if (b1 <= b0) return cudaSuccess;
     if (max_qt > 0) {
 #define NAO_SLICE_NPHI(SS) \
-    slice_nphi_kernel<SS><<<dim3(b1 - b0, max_qt), 128, 0, st>>>(s, b0, scratch, slices, sl_off, expo_q)
+    slice_nphi_kernel<SS><<<dim3(b1 - b0, max_qt), 128, 0, st>>>(s, b0, scratch, slices, sl_off, expo_q, grad ? 4 : 1)
         NAO_SPLIT_DISPATCH(S, NAO_SLICE_NPHI)
 #undef NAO_SLICE_NPHI
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-#define NAO_SLICE_NP(SS) slice_np_kernel<SS><<<b1 - b0, 256, 0, st>>>(s, b0, slices, sl_off, expo_b, tn_b)
+#define NAO_SLICE_NP(SS) \
+    slice_np_kernel<SS><<<b1 - b0, 256, 0, st>>>(s, b0, slices, sl_off, expo_b, tn_b, grad ? 1 : 0)
     NAO_SPLIT_DISPATCH(S, NAO_SLICE_NP)
 #undef NAO_SLICE_NP
     return cudaGetLastError();
@@ -769,15 +789,17 @@ cudaError_t launch_slice_n(const DevSystem &s, int32_t b0, int32_t b1, int32_t m
 
 cudaError_t launch_n_tc(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
                         const int64_t *sl_off, const int32_t *expo_q, const int32_t *expo_b, const double *scratch, int S,
-                        int tn, int32_t *err, cudaStream_t st) {
+                        int tn, bool grad, int32_t *err, cudaStream_t st) {
     if (n_work <= 0) return cudaSuccess;
     if (tn != 32 && !(tn == 48 && S <= 10)) return cudaErrorInvalidValue;
-    if (tn == 48)
-        n_tc_kernel<48><<<n_work, 128, split_smem_bytes(S), st>>>(s, work, w0, slices, sl_off, expo_q, expo_b, scratch,
-                                                                  S, err);
-    else
-        n_tc_kernel<32><<<n_work, 128, split_smem_bytes(S), st>>>(s, work, w0, slices, sl_off, expo_q, expo_b, scratch,
-                                                                  S, err);
+    const size_t sm = split_smem_bytes(S);
+#define NAO_N_TC(TNV, G) \
+    n_tc_kernel<TNV, G><<<n_work, 128, sm, st>>>(s, work, w0, slices, sl_off, expo_q, expo_b, scratch, S, err)
+    if (tn == 48 && grad) NAO_N_TC(48, true);
+    else if (tn == 48) NAO_N_TC(48, false);
+    else if (grad) NAO_N_TC(32, true);
+    else NAO_N_TC(32, false);
+#undef NAO_N_TC
     return cudaGetLastError();
 }
 
