@@ -171,3 +171,21 @@ def test_graph_replay_matches_plain_launches(prec):
     finally:
         plain.close()
         graph.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "split"])
+def test_every_output_element_is_written(group, prec):
+    """H (both triangles) and n at every point, also points of batches without basis
+    functions, are written by each call: outputs pre-filled with NaN come back finite."""
+    g, refs = group["g"], group["refs"]
+    Hs = [torch.full((s["n_basis"], s["n_basis"]), float("nan"), dtype=torch.float64, device="cuda") for s in g.systems]
+    ns = [torch.full((s["n_points"],), float("nan"), dtype=torch.float64, device="cuda") for s in g.systems]
+    nes = [torch.full((1,), float("nan"), dtype=torch.float64, device="cuda") for _ in g.systems]
+    g.integrate_h_many([cuda(r["v"]) for r in refs], prec=prec, Hs=Hs)
+    g.update_density_many([cuda(r["P"]) for r in refs], prec=prec, ns=ns, nes=nes)
+    torch.cuda.synchronize()
+    g.sync()
+    bo, _, ro, _ = g.batches()
+    assert np.any(np.diff(ro) == 0)  # there are batches without functions
+    for m in range(len(refs)):
+        assert torch.isfinite(Hs[m]).all() and torch.isfinite(ns[m]).all() and torch.isfinite(nes[m]).all()
