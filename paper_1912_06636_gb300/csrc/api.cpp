@@ -773,7 +773,7 @@ nao_status split_tune(nao_grid *g, uint32_t terms, cudaStream_t st) {
                 if (bucket[b] != k) continue;
                 std::vector<HWork> tmp;
                 nao_split_h_items(b, g->Nb[b], 48, tmp);
-                base48 += (int64_t)tmp.size() * NAO_SPLIT_CLUSTER;  // CTAs
+                base48 += (int64_t)tmp.size();
             }
             const int64_t reps = base48 > 0 ? (8 * 152 + base48 - 1) / base48 : 0;
             for (int w = 0; w < 2 && rs == NAO_OK && reps > 0; w++) {

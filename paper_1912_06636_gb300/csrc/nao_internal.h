@@ -16,7 +16,6 @@
 #define NAO_PPAD 16          // batch points are padded to a multiple of this in scratch
 #define NAO_MAX_BATCH 1024   // largest accepted max_batch_points
 #define NAO_SPLIT_MAX_SLICES 12  // tensor-memory budget: S groups x TN FP32 columns <= 512 columns
-#define NAO_SPLIT_CLUSTER 1      // split H: CTAs per cluster sharing (multicast) the A operand
 #define NAO_SPLIT_MAX_PPAD 512   // split path: padded batch points (4 Ppad S < 2^14 keeps sums exact)
 
 // One radial function instance relevant to a batch: atom, radial function, position of
@@ -141,12 +140,11 @@ struct HWork {  // one upper-triangular tile pair of one batch's h[B] (Eq. batch
 };
 
 // Split H work items of one batch with N functions for tile width TN: per 128-row tile I, the
-// TN-column tiles J >= floor(128 I / TN) (those reaching the upper triangle), in groups of
-// NAO_SPLIT_CLUSTER consecutive tiles, one item (batch, I, first J) per group.
+// TN-column tiles J >= floor(128 I / TN) (those reaching the upper triangle).
 inline void nao_split_h_items(int32_t b, int N, int TN, std::vector<HWork> &out) {
     const int nI = (N + 127) / 128, nJ = (N + TN - 1) / TN;
     for (int I = 0; I < nI; I++)
-        for (int J = (I * 128) / TN; J < nJ; J += NAO_SPLIT_CLUSTER) out.push_back({b, I, J, 0});
+        for (int J = (I * 128) / TN; J < nJ; J++) out.push_back({b, I, J, 0});
 }
 struct DWork {  // one tile of points of one batch for the density
     int32_t batch, tp;
@@ -275,8 +273,8 @@ cudaError_t launch_slice_h(const DevSystem &s, int32_t b0, int32_t b1, int32_t m
                            uint32_t terms, uint8_t *slices, const int64_t *sl_off, int32_t *expo, int32_t *neg16, int S,
                            cudaStream_t st);
 // tn: tile width 48 (S <= 10 only) or 32; scatter = 0 skips the H scatter (autotuner timing).
-// work: items (batch, I, J0), each taken by a cluster of NAO_SPLIT_CLUSTER CTAs (tiles J0, J0+1, ...;
-// see nao_split_h_items)
+// work: items (batch, 128-row tile I, TN-column tile J) of nao_split_h_items; a persistent kernel
+// (one CTA per SM) walks them
 cudaError_t launch_h_tc(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
                         const int64_t *sl_off, const int32_t *expo, const int32_t *neg16, int S, int tn, int scatter,
                         int32_t *err, cudaStream_t st);

@@ -373,19 +373,14 @@ struct LoopArgs {
     int n_kc, neg16, S;
     int c0 = 0;     // K chunks this CTA's earlier runs of the pipeline processed
     int round = 0;  // index of this run
-    int mma = 1;    // 0: consume the operands without issuing MMAs (a cluster CTA without a tile)
 };
 
 __host__ __device__ constexpr size_t pipe_smem_bytes(int S) {
     return (size_t)RING * 16384 + 2 * (size_t)S * nao_split_tn(S) * 128 + 1024;
 }
 
-// CL > 1: the CTAs of a cluster share the A operand. Every CTA arms its own "full" barrier; the
-// cluster's first CTA issues one multicast copy of each A tile into all of them; "empty" barriers
-// count the MMA completions of all CL CTAs (multicast commits), so the first CTA reuses a ring
-// slot only when every CTA has consumed it.
-template <int TN, int CL = 1>
-__device__ __forceinline__ void pipe_producer(Pipe &p, uint8_t *sA, uint8_t *sB, const LoopArgs &L, uint32_t rank) {
+template <int TN>
+__device__ __forceinline__ void pipe_producer(Pipe &p, uint8_t *sA, uint8_t *sB, const LoopArgs &L) {
     constexpr uint32_t B_BLOCK = TN * 128;
     const int S = L.S;
     for (int kc = 0; kc < L.n_kc; kc++) {
@@ -398,17 +393,13 @@ __device__ __forceinline__ void pipe_producer(Pipe &p, uint8_t *sA, uint8_t *sB,
             const int idx = gk * S + sa, a = idx % RING, ua = idx / RING;
             if (ua >= 1 && !tc::mbar_wait(&p.emptyA[a], (ua - 1) & 1, kWaitCycles)) { p.abort = 1; return; }
             tc::mbar_arrive_expect_tx(&p.fullA[a], L.a_bytes);
-            if (CL == 1)
-                tc::bulk_g2s(sA + (size_t)a * 16384, L.a0 + sa * L.a_s + kc * L.a_kc, L.a_bytes, &p.fullA[a]);
-            else if (rank == 0)
-                tc::bulk_g2s_multicast(sA + (size_t)a * 16384, L.a0 + sa * L.a_s + kc * L.a_kc, L.a_bytes, &p.fullA[a],
-                                       (uint16_t)((1u << CL) - 1));
+            tc::bulk_g2s(sA + (size_t)a * 16384, L.a0 + sa * L.a_s + kc * L.a_kc, L.a_bytes, &p.fullA[a]);
         }
         if (*(volatile int *)&p.abort) return;
     }
 }
 
-template <int TN, int CL = 1>
+template <int TN>
 __device__ __forceinline__ void pipe_mma(Pipe &p, uint8_t *sA, uint8_t *sB, uint32_t tm, const LoopArgs &L) {
     constexpr uint32_t B_BLOCK = TN * 128;
     const int S = L.S;
@@ -427,7 +418,7 @@ __device__ __forceinline__ void pipe_mma(Pipe &p, uint8_t *sA, uint8_t *sB, uint
             // MMA's largest N of 256.
             const int ncols = TN * (S - sa);
             const uint8_t *bset = sB + (size_t)bb * S * B_BLOCK;
-            for (int n0 = 0; L.mma && n0 < ncols; n0 += 256) {
+            for (int n0 = 0; n0 < ncols; n0 += 256) {
                 const int nn = ncols - n0 < 256 ? ncols - n0 : 256;
                 const uint32_t idesc = tc::idesc_bf16_f32(128, nn);
                 const uint64_t bd = tc::sdesc_sw128(tc::smem_addr(bset + (size_t)n0 * 128));
@@ -438,8 +429,7 @@ __device__ __forceinline__ void pipe_mma(Pipe &p, uint8_t *sA, uint8_t *sB, uint
                     tc::mma_bf16(dt, ad + 2 * ks, bd + 2 * ks, id, (kc | sa | ks) ? 1u : 0u);
                 }
             }
-            if (CL == 1) tc::mma_commit(&p.emptyA[a]);
-            else tc::mma_commit_multicast(&p.emptyA[a], (uint16_t)((1u << CL) - 1));
+            tc::mma_commit(&p.emptyA[a]);
         }
         tc::mma_commit(&p.emptyB[bb]);
     }
@@ -447,12 +437,11 @@ __device__ __forceinline__ void pipe_mma(Pipe &p, uint8_t *sA, uint8_t *sB, uint
 }
 
 // Runs the pipeline; on return (all threads) the accumulators are complete unless p.abort.
-template <int TN, int CL = 1>
-__device__ __forceinline__ void pipe_run(Pipe &p, uint8_t *smem, uint32_t tm, const LoopArgs &L, int32_t *err,
-                                         uint32_t rank = 0) {
+template <int TN>
+__device__ __forceinline__ void pipe_run(Pipe &p, uint8_t *smem, uint32_t tm, const LoopArgs &L, int32_t *err) {
     uint8_t *sA = smem, *sB = smem + (size_t)RING * 16384;
-    if (threadIdx.x == 0) pipe_producer<TN, CL>(p, sA, sB, L, rank);
-    else if (threadIdx.x == 32) pipe_mma<TN, CL>(p, sA, sB, tm, L);
+    if (threadIdx.x == 0) pipe_producer<TN>(p, sA, sB, L);
+    else if (threadIdx.x == 32) pipe_mma<TN>(p, sA, sB, tm, L);
     __syncthreads();
     if (threadIdx.x == 0) {
         if (!tc::mbar_wait(&p.done, (uint32_t)(L.round & 1), kWaitCycles)) p.abort = 1;
@@ -499,13 +488,12 @@ __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
     return reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
 }
 
-template <int CL = 1>
 __device__ __forceinline__ uint32_t tc_setup(Pipe &p) {
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         for (int i = 0; i < RING; i++) {
             tc::mbar_init(&p.fullA[i], 1);
-            tc::mbar_init(&p.emptyA[i], CL);
+            tc::mbar_init(&p.emptyA[i], 1);
         }
         for (int i = 0; i < 2; i++) {
             tc::mbar_init(&p.fullB[i], 1);
@@ -523,7 +511,6 @@ __device__ __forceinline__ uint32_t tc_setup(Pipe &p) {
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (CL > 1) tc::cluster_sync();  // every CTA's barriers exist before any multicast or remote arrive
     return p.tmem;
 }
 
@@ -533,69 +520,196 @@ __device__ __forceinline__ void tc_teardown(uint32_t tm) {
     if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(tm, 512);
 }
 
-// One cluster of CL CTAs per work item (batch, 128-row tile I, first TN-column tile J0): CTA r
-// takes tile J0 + r (if it exists; otherwise it only takes part in the shared A loads). The A
-// operand (rows of tile I) is loaded once per cluster and multicast to every CTA.
-template <int TN, int CL>
-__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(128, 1)
-    h_tc_kernel(DevSystem s, const HWork *__restrict__ work, int32_t w0, const uint8_t *__restrict__ slices,
+// Persistent, warp-specialised H contraction: one CTA per SM walks the work items w =
+// blockIdx.x, blockIdx.x + gridDim.x, ... Warp 4 (lane 0) loads the operands into the A ring and
+// the two B sets, its phases continuing over all items; warp 5 (lane 0) issues the MMAs of one
+// item after the other into the single accumulator set; warps 0-3 (128 threads, one accumulator
+// row each) read an item's accumulators into registers, hand tensor memory back to the MMA warp
+// ("acc_empty") and then scatter into H while the next item's MMAs run, so the scatter, the
+// tensor-memory reads and the next item's first loads overlap the MMAs.
+struct PPipe {
+    uint64_t fullA[RING], emptyA[RING], fullB[2], emptyB[2];
+    uint64_t acc_full, acc_empty, fin;
+    uint32_t tmem;
+    int abort;
+};
+
+struct HItem {  // geometry of one H work item
+    const uint8_t *a0, *b0;
+    size_t blk;
+    uint32_t a_bytes, b_bytes;
+    int n_kc, neg16, b, m, N, ti, tj;
+};
+
+template <int TN>
+__device__ __forceinline__ HItem h_item(const DevSystem &s, const HWork *work, int32_t w, const uint8_t *slices,
+                                        const int64_t *sl_off, const int32_t *neg16, int S) {
+    HItem h;
+    const HWork it = work[w];
+    h.b = it.batch;
+    h.ti = it.ti;
+    h.tj = it.tj;
+    h.m = s.sys.bmol[h.b];
+    const int P = s.batch_off[h.b + 1] - s.batch_off[h.b];
+    h.N = s.rel_off[h.b + 1] - s.rel_off[h.b];
+    const SplitGeom G(P, h.N, S);
+    const uint8_t *base = slices + sl_off[h.b];
+    h.blk = (size_t)G.R16 * 128;
+    h.a0 = base + (size_t)it.ti * 128 * 128;
+    h.b0 = base + (size_t)it.tj * TN * 128;
+    h.a_bytes = (uint32_t)min(128, G.R16 - it.ti * 128) * 128u;
+    h.b_bytes = (uint32_t)min(TN, G.R16 - it.tj * TN) * 128u;
+    h.n_kc = G.n_kc;
+    h.neg16 = neg16[h.b];
+    return h;
+}
+
+template <int TN>
+__global__ void __launch_bounds__(192, 1)
+    h_tc_kernel(DevSystem s, const HWork *__restrict__ work, int32_t w0, int32_t n_work, const uint8_t *__restrict__ slices,
                 const int64_t *__restrict__ sl_off, const int32_t *__restrict__ expo,
                 const int32_t *__restrict__ neg16, int S, int scatter, int32_t *__restrict__ err) {
+    constexpr uint32_t B_BLOCK = TN * 128;
     extern __shared__ uint8_t smem_dyn[];
-    __shared__ Pipe pp;
+    __shared__ PPipe pp;
     uint8_t *smem = align1024(smem_dyn);
-    const uint32_t rank = CL > 1 ? tc::cluster_rank() : 0;
-    const HWork it = work[w0 + blockIdx.x / CL];  // batch, 128-row tile, first TN-column tile
-    const int b = it.batch, m = s.sys.bmol[b];
-    const int P = s.batch_off[b + 1] - s.batch_off[b];
-    const int N = s.rel_off[b + 1] - s.rel_off[b];
-    const SplitGeom G(P, N, S);
-    const int nJ = (N + TN - 1) / TN;
-    const int J = it.tj + (int)rank;
-    const bool has_tile = J < nJ;
-    const int Jb = has_tile ? J : it.tj;  // a CTA without a tile still reads a valid B
+    uint8_t *sA = smem, *sB = smem + (size_t)RING * 16384;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t tm = tc_setup<CL>(pp);
-    const uint8_t *base = slices + sl_off[b];
-    const size_t blk = (size_t)G.R16 * 128;
-    LoopArgs L;
-    L.a0 = base + (size_t)it.ti * 128 * 128;
-    L.b0 = base + (size_t)Jb * TN * 128;
-    L.a_s = L.b_s = (size_t)G.n_kc * blk;
-    L.a_kc = L.b_kc = blk;
-    L.a_bytes = (uint32_t)min(128, G.R16 - it.ti * 128) * 128u;
-    L.b_bytes = (uint32_t)min(TN, G.R16 - Jb * TN) * 128u;
-    L.n_kc = G.n_kc;
-    L.neg16 = neg16[b];
-    L.S = S;
-    L.mma = has_tile ? 1 : 0;
-    // after a timeout anywhere in this launch, the remaining CTAs skip their work quickly
-    if (threadIdx.x == 0 && *(volatile int32_t *)err != 0) pp.abort = 1;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < RING; i++) {
+            tc::mbar_init(&pp.fullA[i], 1);
+            tc::mbar_init(&pp.emptyA[i], 1);
+        }
+        for (int i = 0; i < 2; i++) {
+            tc::mbar_init(&pp.fullB[i], 1);
+            tc::mbar_init(&pp.emptyB[i], 1);
+        }
+        tc::mbar_init(&pp.acc_full, 1);
+        tc::mbar_init(&pp.acc_empty, 4);  // one arrival per accumulator-reading warp
+        tc::mbar_init(&pp.fin, 1);
+        tc::fence_mbar_init();
+        pp.abort = *(volatile int32_t *)err != 0 ? 1 : 0;  // a timeout earlier in this launch
+    }
+    __syncwarp();
+    if (warp == 0) {
+        tc::tmem_alloc(&pp.tmem, 512);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
     __syncthreads();
-    if (!pp.abort) pipe_run<TN, CL>(pp, smem, tm, L, err, rank);
-    if (!pp.abort && has_tile) {
-        const int i = it.ti * 128 + warp * 32 + lane;
-        const bool row_ok = i < N;
-        const int32_t *rel = s.rel_idx + s.rel_off[b];
-        const int32_t *ex = expo + s.rel_off[b];
-        const int ei = row_ok ? ex[i] : -10000;
-        const int64_t gi = row_ok ? rel[i] : 0;
-        const uint32_t tm_row = tm + ((uint32_t)(warp * 32) << 16);
-        for (int c0 = 0; c0 < TN; c0 += 16) {
-            Parts16 v;
-            combine16<TN>(tm_row, c0, S, v);
+    tc::fence_after_sync();
+    const uint32_t tm = pp.tmem;
+    volatile int *abort = &pp.abort;
+
+    if (warp == 4) {
+        // ---- producer ----
+        if (lane == 0) {
+            int gk = 0;
+            for (int w = blockIdx.x; w < n_work && !*abort; w += gridDim.x) {
+                const HItem h = h_item<TN>(s, work, w0 + w, slices, sl_off, neg16, S);
+                for (int kc = 0; kc < h.n_kc; kc++, gk++) {
+                    const int bb = gk & 1, ub = gk >> 1;
+                    if (ub >= 1 && !tc::mbar_wait(&pp.emptyB[bb], (ub - 1) & 1, kWaitCycles)) { *abort = 1; break; }
+                    tc::mbar_arrive_expect_tx(&pp.fullB[bb], (uint32_t)S * h.b_bytes);
+                    for (int t = 0; t < S; t++)
+                        tc::bulk_g2s(sB + ((size_t)bb * S + t) * B_BLOCK, h.b0 + ((size_t)t * h.n_kc + kc) * h.blk,
+                                     h.b_bytes, &pp.fullB[bb]);
+                    for (int sa = 0; sa < S; sa++) {
+                        const int idx = gk * S + sa, a = idx % RING, ua = idx / RING;
+                        if (ua >= 1 && !tc::mbar_wait(&pp.emptyA[a], (ua - 1) & 1, kWaitCycles)) { *abort = 1; break; }
+                        tc::mbar_arrive_expect_tx(&pp.fullA[a], h.a_bytes);
+                        tc::bulk_g2s(sA + (size_t)a * 16384, h.a0 + ((size_t)sa * h.n_kc + kc) * h.blk, h.a_bytes,
+                                     &pp.fullA[a]);
+                    }
+                    if (*abort) break;
+                }
+            }
+        }
+    } else if (warp == 5) {
+        // ---- MMA issuer ----
+        if (lane == 0) {
+            int gk = 0, t = 0;
+            for (int w = blockIdx.x; w < n_work && !*abort; w += gridDim.x, t++) {
+                const HItem h = h_item<TN>(s, work, w0 + w, slices, sl_off, neg16, S);
+                // the accumulators of the previous item have been read
+                if (t >= 1 && !tc::mbar_wait(&pp.acc_empty, (t - 1) & 1, kWaitCycles)) { *abort = 1; break; }
+                tc::fence_after_sync();
+                for (int kc = 0; kc < h.n_kc && !*abort; kc++, gk++) {
+                    const int bb = gk & 1, ub = gk >> 1;
+                    if (!tc::mbar_wait(&pp.fullB[bb], ub & 1, kWaitCycles)) { *abort = 1; break; }
+                    const uint8_t *bset = sB + (size_t)bb * S * B_BLOCK;
+                    for (int sa = 0; sa < S; sa++) {
+                        const int idx = gk * S + sa, a = idx % RING, ua = idx / RING;
+                        if (!tc::mbar_wait(&pp.fullA[a], ua & 1, kWaitCycles)) { *abort = 1; break; }
+                        tc::fence_after_sync();
+                        const uint64_t ad = tc::sdesc_sw128(tc::smem_addr(sA + (size_t)a * 16384));
+                        // pairs (sa, t = 0 .. S-1-sa): one MMA per 16-column K step (two above N = 256)
+                        const int ncols = TN * (S - sa);
+                        for (int n0 = 0; n0 < ncols; n0 += 256) {
+                            const int nn = ncols - n0 < 256 ? ncols - n0 : 256;
+                            const uint32_t idesc = tc::idesc_bf16_f32(128, nn);
+                            const uint64_t bd = tc::sdesc_sw128(tc::smem_addr(bset + (size_t)n0 * 128));
+                            const uint32_t dt = tm + (uint32_t)(sa * TN + n0);
 #pragma unroll
-            for (int jj = 0; jj < 16; jj++) {
-                const int j = J * TN + c0 + jj;
-                if (!row_ok || j >= N || j < i) continue;
-                const int ej = ex[j];
-                if (ei <= -10000 || ej <= -10000 || !scatter) continue;
-                atomicAdd(h_elem(s, m, gi, rel[j]), recombine(v.hi[jj], v.lo[jj], v.lo2[jj], ei + ej));
+                            for (int ks = 0; ks < 4; ks++) {
+                                const uint32_t id = (kc * 4 + ks < h.neg16) ? (idesc | (1u << 14)) : idesc;
+                                tc::mma_bf16(dt, ad + 2 * ks, bd + 2 * ks, id, (kc | sa | ks) ? 1u : 0u);
+                            }
+                        }
+                        tc::mma_commit(&pp.emptyA[a]);
+                    }
+                    tc::mma_commit(&pp.emptyB[bb]);
+                }
+                if (*abort) break;
+                tc::mma_commit(&pp.acc_full);  // this item's accumulators are complete
+            }
+            // every issued MMA has completed before tensor memory is released
+            tc::mma_commit(&pp.fin);
+            if (!tc::mbar_wait(&pp.fin, 0, kWaitCycles)) *abort = 1;
+        }
+    } else {
+        // ---- accumulator readers and scatter (warps 0-3) ----
+        int t = 0;
+        const uint32_t tm_row = tm + ((uint32_t)(warp * 32) << 16);
+        for (int w = blockIdx.x; w < n_work; w += gridDim.x, t++) {
+            const HItem h = h_item<TN>(s, work, w0 + w, slices, sl_off, neg16, S);
+            if (*abort || !tc::mbar_wait(&pp.acc_full, t & 1, kWaitCycles)) { *abort = 1; break; }
+            tc::fence_after_sync();
+            const int i = h.ti * 128 + warp * 32 + lane;
+            const bool row_ok = i < h.N;
+            const int32_t *rel = s.rel_idx + s.rel_off[h.b];
+            const int32_t *ex = expo + s.rel_off[h.b];
+            const int ei = row_ok ? ex[i] : -10000;
+            double val[TN];
+#pragma unroll
+            for (int c0 = 0; c0 < TN; c0 += 16) {
+                Parts16 v;
+                combine16<TN>(tm_row, c0, S, v);
+#pragma unroll
+                for (int jj = 0; jj < 16; jj++) {
+                    const int j = h.tj * TN + c0 + jj;
+                    const int ej = (row_ok && j < h.N) ? ex[j] : -10000;
+                    val[c0 + jj] = (ei > -10000 && ej > -10000) ? recombine(v.hi[jj], v.lo[jj], v.lo2[jj], ei + ej) : 0.0;
+                }
+            }
+            // tensor memory is free for the next item
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&pp.acc_empty);
+            if (scatter && row_ok) {
+                const int64_t gi = rel[i];
+#pragma unroll
+                for (int jj = 0; jj < TN; jj++) {
+                    const int j = h.tj * TN + jj;
+                    if (j < h.N && j >= i) atomicAdd(h_elem(s, h.m, gi, rel[j]), val[jj]);
+                }
             }
         }
     }
-    tc_teardown(tm);
-    if (CL > 1) tc::cluster_sync();  // no CTA leaves while a multicast or a remote arrive may target it
+    if (*abort && threadIdx.x == 0) atomicExch(err, (int)NAO_ERR_TIMEOUT);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tm, 512);
 }
 
 // One CTA per (batch, 128-point tile): the TN-function tiles J = 0 .. nJ-1 one after another
@@ -718,7 +832,7 @@ size_t split_smem_bytes(int S) { return pipe_smem_bytes(S); }
 cudaError_t split_configure() {
     size_t bytes = 0;
     for (int S = 4; S <= NAO_SPLIT_MAX_SLICES; S++) bytes = split_smem_bytes(S) > bytes ? split_smem_bytes(S) : bytes;
-    const void *fns[6] = {(const void *)h_tc_kernel<48, NAO_SPLIT_CLUSTER>, (const void *)h_tc_kernel<32, NAO_SPLIT_CLUSTER>,
+    const void *fns[6] = {(const void *)h_tc_kernel<48>, (const void *)h_tc_kernel<32>,
                           (const void *)n_tc_kernel<48, false>, (const void *)n_tc_kernel<32, false>,
                           (const void *)n_tc_kernel<48, true>, (const void *)n_tc_kernel<32, true>};
     for (const void *f : fns) {
@@ -756,13 +870,19 @@ cudaError_t launch_h_tc(const DevSystem &s, const HWork *work, int32_t w0, int32
                         const int64_t *sl_off, const int32_t *expo, const int32_t *neg16, int S, int tn, int scatter,
                         int32_t *err, cudaStream_t st) {
     if (n_work <= 0) return cudaSuccess;
-    constexpr int CL = NAO_SPLIT_CLUSTER;
+    static int n_sm = 0;
+    if (n_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 1;
+    }
+    const int grid = n_work < n_sm ? n_work : n_sm;  // persistent: one CTA per SM
     if (tn == 48 && S <= 10)
-        h_tc_kernel<48, CL><<<n_work * CL, 128, split_smem_bytes(S), st>>>(s, work, w0, slices, sl_off, expo, neg16, S,
-                                                                           scatter, err);
+        h_tc_kernel<48><<<grid, 192, split_smem_bytes(S), st>>>(s, work, w0, n_work, slices, sl_off, expo, neg16, S,
+                                                               scatter, err);
     else if (tn == 32)
-        h_tc_kernel<32, CL><<<n_work * CL, 128, split_smem_bytes(S), st>>>(s, work, w0, slices, sl_off, expo, neg16, S,
-                                                                           scatter, err);
+        h_tc_kernel<32><<<grid, 192, split_smem_bytes(S), st>>>(s, work, w0, n_work, slices, sl_off, expo, neg16, S,
+                                                               scatter, err);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
