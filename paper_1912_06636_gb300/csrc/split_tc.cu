@@ -829,6 +829,15 @@ __global__ void __launch_bounds__(256) wn_partial_kernel(DevSystem s, const DWor
 
 size_t split_smem_bytes(int S) { return pipe_smem_bytes(S); }
 
+// SMs of the current device (the persistent kernels' grid size).
+static int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        n <= 0)
+        return 1;
+    return n;
+}
+
 cudaError_t split_configure() {
     size_t bytes = 0;
     for (int S = 4; S <= NAO_SPLIT_MAX_SLICES; S++) bytes = split_smem_bytes(S) > bytes ? split_smem_bytes(S) : bytes;
@@ -870,13 +879,7 @@ cudaError_t launch_h_tc(const DevSystem &s, const HWork *work, int32_t w0, int32
                         const int64_t *sl_off, const int32_t *expo, const int32_t *neg16, int S, int tn, int scatter,
                         int32_t *err, cudaStream_t st) {
     if (n_work <= 0) return cudaSuccess;
-    static int n_sm = 0;
-    if (n_sm == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 1;
-    }
-    const int grid = n_work < n_sm ? n_work : n_sm;  // persistent: one CTA per SM
+    const int grid = n_work < sm_count() ? n_work : sm_count();  // persistent: one CTA per SM
     if (tn == 48 && S <= 10)
         h_tc_kernel<48><<<grid, 192, split_smem_bytes(S), st>>>(s, work, w0, n_work, slices, sl_off, expo, neg16, S,
                                                                scatter, err);
