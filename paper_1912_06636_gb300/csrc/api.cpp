@@ -726,11 +726,13 @@ nao_status split_setup(nao_grid *g) {
 // costs a launch of its own; the density uses the same width). Buckets that
 // none of those chunks contains keep the default rule. Runs once per handle, inside the first
 // split Hamiltonian call (the evaluation and slicing it needs use that call's v and terms).
+// N_b classes: steps of 16 up to 512 (the padding of the last 48- or 32-wide tile depends on N_b
+// modulo the width), then steps of 128; P_b classes: 64, 128, 192, 256, 336, more.
+constexpr int kTnBuckets = (32 + 5) * 6;
 int tn_bucket(int N, int P) {
-    static const int ne[] = {32, 64, 96, 128, 192, 256, 384, 512, 768};
     static const int pe[] = {64, 128, 192, 256, 336};
-    int a = 0, c = 0;
-    while (a < 9 && N > ne[a]) a++;
+    const int a = N <= 512 ? (N + 15) / 16 - 1 : (N <= 1024 ? 32 + (N - 513) / 128 : 36);
+    int c = 0;
     while (c < 5 && P > pe[c]) c++;
     return a * 6 + c;
 }
@@ -739,7 +741,7 @@ nao_status split_tune(nao_grid *g, uint32_t terms, cudaStream_t st) {
     if (g->split_tuned) return NAO_OK;
     const int S = g->split_S;
     const DevSystem &s = g->sys;
-    constexpr int kBuckets = 60, kChunks = 3;
+    constexpr int kBuckets = kTnBuckets, kChunks = 3;
     std::vector<int> bucket(g->n_batches, -1), total(kBuckets, 0);
     for (int64_t b = 0; b < g->n_batches; b++)
         if (g->Nb[b] > 0) {
