@@ -124,7 +124,7 @@ __device__ __forceinline__ double pow2(int E) {
 // multiple of 16, then the rest, so that B = A and the sign is applied per 16-column K step.
 // ----------------------------------------------------------------------------------------
 template <int S>
-__global__ void __launch_bounds__(256) slice_h_kernel(DevSystem s, int32_t b0, const double *__restrict__ scratch,
+__global__ void __launch_bounds__(256, 5) slice_h_kernel(DevSystem s, int32_t b0, const double *__restrict__ scratch,
                                                      uint32_t terms, uint8_t *__restrict__ slices,
                                                      const int64_t *__restrict__ sl_off, int32_t *__restrict__ expo,
                                                      int32_t *__restrict__ neg16) {
@@ -134,7 +134,6 @@ __global__ void __launch_bounds__(256) slice_h_kernel(DevSystem s, int32_t b0, c
     __shared__ short src[4 * NAO_SPLIT_MAX_PPAD + 64];
     __shared__ unsigned char negf[4 * NAO_SPLIT_MAX_PPAD];
     __shared__ int wsum[8];
-    __shared__ int ex_s[64];
     const int b = b0 + blockIdx.x, rt = blockIdx.y, m = s.sys.bmol[b];
     const int p0 = s.batch_off[b], P = s.batch_off[b + 1] - p0;
     const int Ppad = (P + NAO_PPAD - 1) & ~(NAO_PPAD - 1);
@@ -185,8 +184,13 @@ __global__ void __launch_bounds__(256) slice_h_kernel(DevSystem s, int32_t b0, c
     }
     if (rt == 0 && threadIdx.x == 0) neg16[b] = negpad / 16;
     __syncthreads();
+    // one warp per row: the row's exponent, then its digits, so that the second read of the row
+    // follows the first within microseconds and is served from cache
+    uint8_t *base = slices + sl_off[b];
     for (int lr = warp; lr < 64; lr += 8) {
         const int r = rt * 64 + lr;
+        if (r >= G.R16) break;
+        const double *row = E + (int64_t)(r < N ? r : 0) * K;
         // the binade of max_k |E_rk sd_k| without FP64 products: the product's biased exponent is
         // eb(E) + eb(sd) - 1023, plus 1 when the significands' product reaches 2 (taken as reached
         // from 2 - 2^-20 on, since both significands are truncated to FP32: e may then be one
@@ -194,7 +198,7 @@ __global__ void __launch_bounds__(256) slice_h_kernel(DevSystem s, int32_t b0, c
         int mk = 0;
         if (r < N)
             for (int k = lane; k < K; k += 32) {
-                const long long xb = __double_as_longlong(E[(int64_t)r * K + k]);
+                const long long xb = __double_as_longlong(row[k]);
                 const int ebx = (int)((xb >> 52) & 0x7FF), ebs = sd_eb[k];
                 if (ebx == 0 || ebs == 0) continue;
                 const int carry = significand_f(xb) * sd_m[k] >= 1.999998f ? 1 : 0;
@@ -202,38 +206,22 @@ __global__ void __launch_bounds__(256) slice_h_kernel(DevSystem s, int32_t b0, c
             }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mk = max(mk, __shfl_xor_sync(0xffffffffu, mk, o));
-        if (lane == 0) {
-            const int e = mk - 1023 > 0 ? row_exponent_bits((long long)(mk - 1023) << 52) : -10000;
-            ex_s[lr] = e;
-            if (r < N) expo[s.rel_off[b] + r] = e;
-        }
-    }
-    __syncthreads();
-    uint8_t *base = slices + sl_off[b];
-    const int groups = Kp / 8;
-    for (int u = threadIdx.x; u < 64 * groups; u += blockDim.x) {
-        const int lr = u / groups, k0 = (u - lr * groups) * 8;
-        const int r = rt * 64 + lr;
-        if (r >= G.R16) continue;
-        const int e = r < N ? ex_s[lr] : -10000;
-        float dg[8][S];
-        const double *row = E + (int64_t)(r < N ? r : 0) * K;
+        const int e = (r < N && mk - 1023 > 0) ? row_exponent_bits((long long)(mk - 1023) << 52) : -10000;
+        if (lane == 0 && r < N) expo[s.rel_off[b] + r] = e;
+        // two consecutive K columns per lane: a warp writes one 128-byte row segment per slice
+        for (int kc = 0; kc < G.n_kc; kc++) {
+            const int k0 = 64 * kc + 2 * lane;
+            float dg[2][S];
 #pragma unroll
-        for (int h = 0; h < 8; h++) {
-            const int kk = src[k0 + h];
-            const double x = (kk >= 0 && e > -10000) ? row[kk] * sd[kk] : 0.0;
-            digits<S>(x, e, dg[h]);
-        }
-        const int kc = k0 >> 6;
-        const uint32_t off = tc::sw128_offset((uint32_t)r, (uint32_t)(k0 & 63));
+            for (int h = 0; h < 2; h++) {
+                const int kk = src[k0 + h];
+                const double x = (kk >= 0 && e > -10000) ? row[kk] * sd[kk] : 0.0;
+                digits<S>(x, e, dg[h]);
+            }
+            const uint32_t off = tc::sw128_offset((uint32_t)r, (uint32_t)(2 * lane));
 #pragma unroll
-        for (int sl = 0; sl < S; sl++) {
-            uint4 va;
-            va.x = pack_bf16x2(dg[0][sl], dg[1][sl]);
-            va.y = pack_bf16x2(dg[2][sl], dg[3][sl]);
-            va.z = pack_bf16x2(dg[4][sl], dg[5][sl]);
-            va.w = pack_bf16x2(dg[6][sl], dg[7][sl]);
-            *reinterpret_cast<uint4 *>(base + G.h_block(sl, kc) + off) = va;
+            for (int sl = 0; sl < S; sl++)
+                *reinterpret_cast<uint32_t *>(base + G.h_block(sl, kc) + off) = pack_bf16x2(dg[0][sl], dg[1][sl]);
         }
     }
 }
