@@ -902,11 +902,12 @@ nao_status enqueue_n(nao_grid *g, nao_precision prec, bool want_ne, bool grad, c
         const int S = g->split_S;
         NAO_CUDA(launch_zero_n(s, g->d_dwork, (int32_t)g->n_dwork, grad, st));
         for (const auto &c : g->split_chunks) {
-            NAO_CUDA(timed(g, grad ? NAO_K_EVAL_GRAD : NAO_K_EVAL_PHI, st,
-                           [&] { return launch_eval(s, c.b0, c.b1, NAO_FP64, grad, g->d_scratch, st); }));
+            NAO_CUDA(timed(g, grad ? NAO_K_EVAL_GRAD : NAO_K_EVAL_PHI, st, [&] {
+                return launch_eval_split(s, c.b0, c.b1, grad, g->d_scratch, g->d_expo_q, 128 * c.max_qt, st);
+            }));
             NAO_CUDA(timed(g, NAO_K_SLICE_N, st, [&] {
-                return launch_slice_n(s, c.b0, c.b1, c.max_qt, g->d_scratch, g->d_slices, g->d_sl_off_n, g->d_expo_q,
-                                      g->d_expo_b, g->d_split_tn, S, grad, st);
+                return launch_slice_n(s, c.b0, c.b1, c.max_qt, c.max_rt, g->d_scratch, g->d_slices, g->d_sl_off_n,
+                                      g->d_expo_q, g->d_expo_b, g->d_split_tn, S, grad, st);
             }));
             for (int k = 0; k < 2; k++)
                 if (c.nw1[k] > c.nw0[k])

@@ -17,6 +17,7 @@
 #include <type_traits>
 
 #include "nao_internal.h"
+#include "split_bits.h"
 
 namespace {
 
@@ -58,6 +59,13 @@ struct EvalOut {
     int32_t qmax; // points written per row (q >= P_b is written as 0)
 };
 
+// Split path (EXPO = 1): per point, the largest biased exponent of phi over the basis, reduced
+// while the values are produced (the density slicing's point exponents) into red[q], shared
+// memory of the batch's CTA.
+struct ExpoIn {
+    int *red;
+};
+
 // Distance below which the FP32 path evaluates in FP64 (bohr).
 constexpr double kNearNucleus = 0.1;
 
@@ -78,9 +86,9 @@ __device__ __forceinline__ void store_rows(const EvalOut<OutT> &o, int pos, int 
 // All relevant radial functions of one atom at one point, in arithmetic T. Distance, square
 // root, logarithm, reciprocals and the solid-harmonic recurrence are shared by the atom's
 // radial functions, which are visited in increasing l.
-template <int LMAX, typename T, bool GRAD, typename OutT>
+template <int LMAX, typename T, bool GRAD, typename OutT, int EXPO>
 __device__ __noinline__ void eval_group(const DevSystem &s, const AtomGroup &ag, double dx, double dy, double dz,
-                                           double r2, double r, const EvalOut<OutT> &o, int q) {
+                                           double r2, double r, const EvalOut<OutT> &o, int q, ExpoIn xi) {
     // radial coordinate: segment k and t in [0, 1)
     const double rr = fmax(r, s.r0);
     int k;
@@ -123,6 +131,7 @@ __device__ __noinline__ void eval_group(const DevSystem &s, const AtomGroup &ag,
     for (int m = 0; m <= LMAX; m++) Pc[m] = Pcz[m] = Pcq[m] = Pp[m] = Ppz[m] = Ppq[m] = H(0);
     int ri = ag.r0;
     const int re = ag.r0 + ag.nr;
+    int pt_eb = 0;  // EXPO 1: largest biased exponent of phi at this point
     T ul = T(1);  // u^l
 #pragma unroll
     for (int l = 0; l <= LMAX; l++) {
@@ -206,27 +215,39 @@ __device__ __noinline__ void eval_group(const DevSystem &s, const AtomGroup &ag,
 #pragma unroll
                 for (int m = 0; m < 2 * l + 1; m++) fo[m] = xo[m] = yo[m] = zo[m] = OutT(0);
             }
+            if constexpr (EXPO == 1) {
+#pragma unroll
+                for (int m = 0; m < 2 * l + 1; m++)
+                    pt_eb = max(pt_eb, split_bits::biased_exponent(__double_as_longlong(double(fo[m]))));
+            }
             store_rows(o, e.pos, 2 * l + 1, q, fo, xo, yo, zo, GRAD);
         }
         ul *= u;
     }
+    if constexpr (EXPO == 1) {
+        if (pt_eb > 0) atomicMax(xi.red + q, pt_eb);
+    }
 }
 
-template <int LMAX, bool GRAD, typename T, typename OutT>
+template <int LMAX, bool GRAD, typename T, int EXPO, typename OutT>
 __device__ __forceinline__ void eval_group_dispatch(const DevSystem &s, const AtomGroup &ag, double dx, double dy,
-                                                    double dz, double r2, double r, const EvalOut<OutT> &o, int q) {
-    if (std::is_same<T, double>::value || r < kNearNucleus)
-        eval_group<LMAX, double, GRAD, OutT>(s, ag, dx, dy, dz, r2, r, o, q);
+                                                    double dz, double r2, double r, const EvalOut<OutT> &o, int q,
+                                                    const ExpoIn &xi) {
+    if constexpr (EXPO != 0 || std::is_same<T, double>::value)
+        eval_group<LMAX, double, GRAD, OutT, EXPO>(s, ag, dx, dy, dz, r2, r, o, q, xi);
+    else if (r < kNearNucleus)
+        eval_group<LMAX, double, GRAD, OutT, 0>(s, ag, dx, dy, dz, r2, r, o, q, xi);
     else
-        eval_group<LMAX, float, GRAD, OutT>(s, ag, dx, dy, dz, r2, r, o, q);
+        eval_group<LMAX, float, GRAD, OutT, 0>(s, ag, dx, dy, dz, r2, r, o, q, xi);
 }
 
-template <bool GRAD, typename T, typename OutT>
-__device__ __forceinline__ void eval_batch(const DevSystem &s, int b, const EvalOut<OutT> &o) {
+template <bool GRAD, typename T, int EXPO, typename OutT>
+__device__ __forceinline__ void eval_batch(const DevSystem &s, int b, const EvalOut<OutT> &o, int *red = nullptr) {
     const int p0 = s.batch_off[b], P = s.batch_off[b + 1] - p0;
     const int g0 = s.agrp_off[b], ng = s.agrp_off[b + 1] - g0;
     const int qmax = o.qmax;
     const int total = ng * qmax;
+    const ExpoIn xi{red};
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const int gl = idx / qmax, q = idx - gl * qmax;
         const AtomGroup ag = s.agrp[g0 + gl];
@@ -247,24 +268,19 @@ __device__ __forceinline__ void eval_batch(const DevSystem &s, int b, const Eval
         const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
         const double r = __dsqrt_rn(r2);
         switch (ag.lmax) {
-            case 0: eval_group_dispatch<0, GRAD, T>(s, ag, dx, dy, dz, r2, r, o, q); break;
-            case 1: eval_group_dispatch<1, GRAD, T>(s, ag, dx, dy, dz, r2, r, o, q); break;
-            case 2: eval_group_dispatch<2, GRAD, T>(s, ag, dx, dy, dz, r2, r, o, q); break;
-            case 3: eval_group_dispatch<3, GRAD, T>(s, ag, dx, dy, dz, r2, r, o, q); break;
-            case 4: eval_group_dispatch<4, GRAD, T>(s, ag, dx, dy, dz, r2, r, o, q); break;
-            case 5: eval_group_dispatch<5, GRAD, T>(s, ag, dx, dy, dz, r2, r, o, q); break;
-            default: eval_group_dispatch<6, GRAD, T>(s, ag, dx, dy, dz, r2, r, o, q); break;
+            case 0: eval_group_dispatch<0, GRAD, T, EXPO>(s, ag, dx, dy, dz, r2, r, o, q, xi); break;
+            case 1: eval_group_dispatch<1, GRAD, T, EXPO>(s, ag, dx, dy, dz, r2, r, o, q, xi); break;
+            case 2: eval_group_dispatch<2, GRAD, T, EXPO>(s, ag, dx, dy, dz, r2, r, o, q, xi); break;
+            case 3: eval_group_dispatch<3, GRAD, T, EXPO>(s, ag, dx, dy, dz, r2, r, o, q, xi); break;
+            case 4: eval_group_dispatch<4, GRAD, T, EXPO>(s, ag, dx, dy, dz, r2, r, o, q, xi); break;
+            case 5: eval_group_dispatch<5, GRAD, T, EXPO>(s, ag, dx, dy, dz, r2, r, o, q, xi); break;
+            default: eval_group_dispatch<6, GRAD, T, EXPO>(s, ag, dx, dy, dz, r2, r, o, q, xi); break;
         }
     }
 }
 
-// One CTA per batch; the batch's block of scratch holds, per reduced-basis row j,
-// [phi | d/dx | d/dy | d/dz] over Ppad points each (GRAD) or phi alone, in type T.
 template <bool GRAD, typename T>
-__global__ void __launch_bounds__(256) eval_chunk_kernel(DevSystem s, int32_t b0, T *scratch) {
-    const int b = b0 + blockIdx.x;
-    const int P = s.batch_off[b + 1] - s.batch_off[b];
-    const int Ppad = (P + NAO_PPAD - 1) & ~(NAO_PPAD - 1);
+__device__ __forceinline__ EvalOut<T> batch_out(const DevSystem &s, int b, int Ppad, T *scratch) {
     EvalOut<T> o;
     o.phi = scratch + s.scr_off[b];
     o.qmax = Ppad;
@@ -278,7 +294,34 @@ __global__ void __launch_bounds__(256) eval_chunk_kernel(DevSystem s, int32_t b0
         o.grad = nullptr;
         o.grad_cs = o.grad_rs = 0;
     }
-    eval_batch<GRAD, T>(s, b, o);
+    return o;
+}
+
+// One CTA per batch; the batch's block of scratch holds, per reduced-basis row j,
+// [phi | d/dx | d/dy | d/dz] over Ppad points each (GRAD) or phi alone, in type T.
+template <bool GRAD, typename T>
+__global__ void __launch_bounds__(256) eval_chunk_kernel(DevSystem s, int32_t b0, T *scratch) {
+    const int b = b0 + blockIdx.x;
+    const int P = s.batch_off[b + 1] - s.batch_off[b];
+    const int Ppad = (P + NAO_PPAD - 1) & ~(NAO_PPAD - 1);
+    eval_batch<GRAD, T, 0>(s, b, batch_out<GRAD, T>(s, b, Ppad, scratch));
+}
+
+// The density's evaluation on the split path (FP64): as eval_chunk_kernel, and the point
+// exponents of the slicing: expo[batch_off[b] + q] = the exponent of point q, from the binade of
+// max_i |phi_iq| (split_bits::exponent_of_binade). Dynamic shared memory: n_red >= P_b ints.
+template <bool GRAD>
+__global__ void __launch_bounds__(256) eval_split_kernel(DevSystem s, int32_t b0, double *scratch, int32_t *expo,
+                                                         int n_red) {
+    extern __shared__ int red_sh[];
+    const int b = b0 + blockIdx.x;
+    const int p0 = s.batch_off[b], P = s.batch_off[b + 1] - p0;
+    const int Ppad = (P + NAO_PPAD - 1) & ~(NAO_PPAD - 1);
+    for (int i = threadIdx.x; i < n_red; i += blockDim.x) red_sh[i] = 0;
+    __syncthreads();
+    eval_batch<GRAD, double, 1>(s, b, batch_out<GRAD, double>(s, b, Ppad, scratch), red_sh);
+    __syncthreads();
+    for (int q = threadIdx.x; q < P; q += blockDim.x) expo[p0 + q] = split_bits::exponent_of_binade(red_sh[q]);
 }
 
 template <bool GRAD, typename T>
@@ -292,7 +335,7 @@ __global__ void __launch_bounds__(256) eval_export_kernel(DevSystem s, int32_t b
     o.grad_cs = (int64_t)N * P;
     o.grad_rs = P;
     o.qmax = P;
-    eval_batch<GRAD, T>(s, b, o);
+    eval_batch<GRAD, T, 0>(s, b, o);
 }
 
 }  // namespace
@@ -316,6 +359,15 @@ cudaError_t launch_eval(const DevSystem &s, int32_t b0, int32_t b1, nao_precisio
         if (grad) eval_chunk_kernel<true, double><<<b1 - b0, 256, 0, st>>>(s, b0, scratch);
         else eval_chunk_kernel<false, double><<<b1 - b0, 256, 0, st>>>(s, b0, scratch);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eval_split(const DevSystem &s, int32_t b0, int32_t b1, bool grad, double *scratch, int32_t *expo,
+                              int32_t n_red, cudaStream_t st) {
+    if (b1 <= b0) return cudaSuccess;
+    const size_t smem = (size_t)n_red * 4;
+    if (grad) eval_split_kernel<true><<<b1 - b0, 256, smem, st>>>(s, b0, scratch, expo, n_red);
+    else eval_split_kernel<false><<<b1 - b0, 256, smem, st>>>(s, b0, scratch, expo, n_red);
     return cudaGetLastError();
 }
 

@@ -247,6 +247,10 @@ cudaError_t launch_relevance_minr2(const double *atom_xyz, const int32_t *bmol, 
                                    int64_t n_batches, double *minr2, cudaStream_t st);
 cudaError_t launch_eval(const DevSystem &s, int32_t b0, int32_t b1, nao_precision prec, bool grad, double *scratch,
                         cudaStream_t st);
+// Split path, the density's evaluation (FP64 values; phi, with grad phi when grad) and the
+// point exponents of the slicing into expo (by batch-ordered point; n_red >= P_b).
+cudaError_t launch_eval_split(const DevSystem &s, int32_t b0, int32_t b1, bool grad, double *scratch, int32_t *expo,
+                              int32_t n_red, cudaStream_t st);
 cudaError_t launch_eval_one(const DevSystem &s, int32_t b, nao_precision prec, double *phi, double *grad,
                             cudaStream_t st);
 cudaError_t launch_h_simt(const DevSystem &s, nao_precision prec, const HWork *work, int32_t n_work,
@@ -280,9 +284,9 @@ cudaError_t launch_h_tc(const DevSystem &s, const HWork *work, int32_t w0, int32
                         int32_t *err, cudaStream_t st);
 // tn_b: per-batch tile width (the P' tiles of the density follow it). grad: the scratch rows hold
 // [phi | grad phi] (4 Ppad) and P' = P over all tiles (density gradient)
-cudaError_t launch_slice_n(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_qt, const double *scratch,
-                           uint8_t *slices, const int64_t *sl_off, int32_t *expo_q, int32_t *expo_b,
-                           const int32_t *tn_b, int S, bool grad, cudaStream_t st);
+cudaError_t launch_slice_n(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_qt, int32_t max_rt,
+                           const double *scratch, uint8_t *slices, const int64_t *sl_off, const int32_t *expo_q,
+                           int32_t *expo_b, const int32_t *tn_b, int S, bool grad, cudaStream_t st);
 cudaError_t launch_n_tc(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
                         const int64_t *sl_off, const int32_t *expo_q, const int32_t *expo_b, const double *scratch, int S,
                         int tn, bool grad, int32_t *err, cudaStream_t st);

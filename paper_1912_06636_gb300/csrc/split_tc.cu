@@ -26,6 +26,7 @@
 #include <cmath>
 
 #include "nao_internal.h"
+#include "split_bits.h"
 #include "tc_ptx.h"
 
 namespace {
@@ -36,23 +37,8 @@ constexpr long long kWaitCycles = 400000000LL;  // ~0.2 s at 2 GHz: bounded mbar
 // Digit extraction works on FP64 bit patterns with integer instructions: on this GPU the FP64
 // pipe is ~1/60 of the FP32 rate, and a double-to-int64 conversion per element would make the
 // slicing kernels FP64-bound.
-
-// |x| as an ordered integer: for non-negative doubles the bit patterns order like the values.
-__device__ __forceinline__ long long abs_bits(double x) { return __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL; }
-
-// The significand of the FP64 with bit pattern xb, in [1, 2), truncated to FP32.
-__device__ __forceinline__ float significand_f(long long xb) {
-    return __int_as_float(0x3F800000 | (int)((xb >> 29) & 0x7FFFFF));
-}
-
-// Exponent e with max * 2^-e in [0.25, 0.5), from the bit pattern of max (abs_bits); rows whose
-// magnitude is below 2^-900 (or zero) are taken as zero (flag -10000).
-__device__ __forceinline__ int row_exponent_bits(long long mb) {
-    const int eb = (int)(mb >> 52);  // biased exponent
-    if (eb == 0) return -10000;
-    const int ex = eb - 1022;  // max = f 2^ex, f in [0.5, 1)
-    return ex < -900 ? -10000 : ex + 1;
-}
+using split_bits::abs_bits;
+using split_bits::row_exponent_bits;
 
 // 2^23 + u for a 23-bit unsigned u, as an exact float, minus 2^23: u as a float without a
 // conversion instruction.
@@ -122,12 +108,15 @@ __device__ __forceinline__ double pow2(int E) {
 // Hamiltonian slicing: one CTA per (batch, 64-row tile of basis functions). Columns are
 // reordered: the negative-weight ones (v < 0 on the potential part) first, padded to a
 // multiple of 16, then the rest, so that B = A and the sign is applied per 16-column K step.
+// One warp per row: the row's exponent (a pass over the row), then its digits (a second pass,
+// served from L2: the slices are written with evict-first stores so that they do not push the
+// rows out).
 // ----------------------------------------------------------------------------------------
 template <int S>
 __global__ void __launch_bounds__(256, 5) slice_h_kernel(DevSystem s, int32_t b0, const double *__restrict__ scratch,
-                                                     uint32_t terms, uint8_t *__restrict__ slices,
-                                                     const int64_t *__restrict__ sl_off, int32_t *__restrict__ expo,
-                                                     int32_t *__restrict__ neg16) {
+                                                        uint32_t terms, uint8_t *__restrict__ slices,
+                                                        const int64_t *__restrict__ sl_off, int32_t *__restrict__ expo,
+                                                        int32_t *__restrict__ neg16) {
     __shared__ double sd[4 * NAO_SPLIT_MAX_PPAD];
     __shared__ int sd_eb[4 * NAO_SPLIT_MAX_PPAD];    // biased exponent of sd (0: zero weight)
     __shared__ float sd_m[4 * NAO_SPLIT_MAX_PPAD];   // significand of sd in [1, 2), truncated
@@ -144,14 +133,11 @@ __global__ void __launch_bounds__(256, 5) slice_h_kernel(DevSystem s, int32_t b0
     const double *E = scratch + s.scr_off[b];
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         const int c = k / Ppad, q = k - c * Ppad;
-        const double w = q < P ? s.pw[p0 + q] : 0.0;
-        double d;
-        if (c == 0) d = (terms & NAO_TERM_POTENTIAL) && q < P ? w * v_at(s, m, p0 + q) : 0.0;
-        else d = (terms & NAO_TERM_KINETIC) ? 0.5 * w : 0.0;
-        sd[k] = sqrt(fabs(d));
+        const double d = q < P ? split_bits::h_column_weight(s, m, p0 + q, c, terms) : 0.0;
+        sd[k] = split_bits::h_column_scale(d);
         const long long sb = __double_as_longlong(sd[k]);
-        sd_eb[k] = (int)((sb >> 52) & 0x7FF);
-        sd_m[k] = significand_f(sb);
+        sd_eb[k] = split_bits::biased_exponent(sb);
+        sd_m[k] = split_bits::significand_f(sb);
         negf[k] = d < 0.0 ? 1 : 0;
     }
     for (int k = threadIdx.x; k < Kp; k += blockDim.x) src[k] = -1;
@@ -184,29 +170,16 @@ __global__ void __launch_bounds__(256, 5) slice_h_kernel(DevSystem s, int32_t b0
     }
     if (rt == 0 && threadIdx.x == 0) neg16[b] = negpad / 16;
     __syncthreads();
-    // one warp per row: the row's exponent, then its digits, so that the second read of the row
-    // follows the first within microseconds and is served from cache
     uint8_t *base = slices + sl_off[b];
     for (int lr = warp; lr < 64; lr += 8) {
         const int r = rt * 64 + lr;
         if (r >= G.R16) break;
         const double *row = E + (int64_t)(r < N ? r : 0) * K;
-        // the binade of max_k |E_rk sd_k| without FP64 products: the product's biased exponent is
-        // eb(E) + eb(sd) - 1023, plus 1 when the significands' product reaches 2 (taken as reached
-        // from 2 - 2^-20 on, since both significands are truncated to FP32: e may then be one
-        // too large, costing one bit, but never too small)
         int mk = 0;
         if (r < N)
-            for (int k = lane; k < K; k += 32) {
-                const long long xb = __double_as_longlong(row[k]);
-                const int ebx = (int)((xb >> 52) & 0x7FF), ebs = sd_eb[k];
-                if (ebx == 0 || ebs == 0) continue;
-                const int carry = significand_f(xb) * sd_m[k] >= 1.999998f ? 1 : 0;
-                mk = max(mk, ebx + ebs + carry);
-            }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mk = max(mk, __shfl_xor_sync(0xffffffffu, mk, o));
-        const int e = (r < N && mk - 1023 > 0) ? row_exponent_bits((long long)(mk - 1023) << 52) : -10000;
+            for (int k = lane; k < K; k += 32) mk = max(mk, split_bits::h_row_key(row[k], sd_eb[k], sd_m[k]));
+        mk = __reduce_max_sync(0xffffffffu, mk);
+        const int e = r < N ? split_bits::h_row_exponent(mk) : -10000;
         if (lane == 0 && r < N) expo[s.rel_off[b] + r] = e;
         // two consecutive K columns per lane: a warp writes one 128-byte row segment per slice
         for (int kc = 0; kc < G.n_kc; kc++) {
@@ -215,117 +188,146 @@ __global__ void __launch_bounds__(256, 5) slice_h_kernel(DevSystem s, int32_t b0
 #pragma unroll
             for (int h = 0; h < 2; h++) {
                 const int kk = src[k0 + h];
-                const double x = (kk >= 0 && e > -10000) ? row[kk] * sd[kk] : 0.0;
+                const double x = (kk >= 0 && e > -10000) ? __ldcs(row + kk) * sd[kk] : 0.0;
                 digits<S>(x, e, dg[h]);
             }
             const uint32_t off = tc::sw128_offset((uint32_t)r, (uint32_t)(2 * lane));
 #pragma unroll
             for (int sl = 0; sl < S; sl++)
-                *reinterpret_cast<uint32_t *>(base + G.h_block(sl, kc) + off) = pack_bf16x2(dg[0][sl], dg[1][sl]);
+                __stcs(reinterpret_cast<unsigned int *>(base + G.h_block(sl, kc) + off), pack_bf16x2(dg[0][sl], dg[1][sl]));
         }
     }
 }
 
 // ----------------------------------------------------------------------------------------
-// Density slicing. Phi^T: one CTA (128 threads, one point each) per (batch, 128-point tile).
+// Density slicing.
+// Phi^T: one CTA (8 warps) per (batch, 32-point tile), the point exponents from the
+// evaluation. Per 64-function K chunk the CTA stages phi[i][q] (64 x 32, read along the points)
+// in shared memory and each warp writes its points' rows along K (two functions per lane, one
+// 128-byte row segment per slice). CTAs with blockIdx.y = 0 instead reduce the batch's
+// exponent of P' (the upper-triangle tile pairs, read along rows of P).
 // ----------------------------------------------------------------------------------------
+__device__ __forceinline__ int tile_of(int i, int TN) { return i / TN; }
+
 template <int S>
-__global__ void __launch_bounds__(128) slice_nphi_kernel(DevSystem s, int32_t b0, const double *__restrict__ scratch,
+__global__ void __launch_bounds__(256) slice_nphi_kernel(DevSystem s, int32_t b0, const double *__restrict__ scratch,
                                                         uint8_t *__restrict__ slices, const int64_t *__restrict__ sl_off,
-                                                        int32_t *__restrict__ expo_q, int ld_mult) {
-    const int b = b0 + blockIdx.x, qt = blockIdx.y;
+                                                        const int32_t *__restrict__ expo_q, int32_t *__restrict__ expo_b,
+                                                        const int32_t *__restrict__ tn_b, int ld_mult, int full) {
+    __shared__ double t[32][65];
+    __shared__ int red[8];
+    const int b = b0 + blockIdx.x;
     const int p0 = s.batch_off[b], P = s.batch_off[b + 1] - p0;
     const int Ppad = (P + NAO_PPAD - 1) & ~(NAO_PPAD - 1);
     const int N = s.rel_off[b + 1] - s.rel_off[b];
+    if (N == 0) return;
     const SplitGeom G(P, N, S);
-    const int q = qt * 128 + threadIdx.x;
-    if (N == 0 || q >= G.P16) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (blockIdx.y == 0) {
+        // max |P'_ij| over i <= j (P' is P on the diagonal tiles, 2 P off them, 0 below unless
+        // full): the exponent field of |P| plus one off the diagonal tiles
+        const int m = s.sys.bmol[b], TN = tn_b[b];
+        const int32_t *rel = s.rel_idx + s.rel_off[b];
+        int mk = 0;
+        for (int i = warp; i < N; i += 8) {
+            const int64_t gi = rel[i];
+            for (int j = (full ? 0 : i) + lane; j < N; j += 32) {
+                const int64_t gj = rel[j];
+                const int eb = split_bits::biased_exponent(abs_bits(gi <= gj ? p_elem(s, m, gi, gj) : p_elem(s, m, gj, gi)));
+                if (eb != 0) mk = max(mk, eb + ((!full && tile_of(i, TN) < tile_of(j, TN)) ? 1 : 0));
+            }
+        }
+        mk = __reduce_max_sync(0xffffffffu, mk);
+        if (lane == 0) red[warp] = mk;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < 8; w++) mk = max(mk, red[w]);
+            expo_b[b] = split_bits::exponent_of_binade(mk);
+        }
+        return;
+    }
+    const int q0 = (blockIdx.y - 1) * 32;
+    if (q0 >= G.P16) return;
     const double *E = scratch + s.scr_off[b];  // phi[i][q], row stride ld_mult Ppad (4: rows also hold grad phi)
     const int64_t ld = (int64_t)ld_mult * Ppad;
-    long long mb = 0;
-    if (q < P)
-        for (int i = 0; i < N; i++) mb = max(mb, abs_bits(E[(int64_t)i * ld + q]));
-    const int e = q < P ? row_exponent_bits(mb) : -10000;
-    if (q < P) expo_q[p0 + q] = e;
+    const bool qin = q0 + lane < P;
+    int eq[4];
+#pragma unroll
+    for (int h = 0; h < 4; h++) {
+        const int q = q0 + warp * 4 + h;
+        eq[h] = q < P ? expo_q[p0 + q] : -10000;
+    }
     uint8_t *base = slices + sl_off[b];
-    for (int i0 = 0; i0 < G.n_kcN * 64; i0 += 8) {
-        float dg[8][S];
+    for (int kc = 0; kc < G.n_kcN; kc++) {
 #pragma unroll
         for (int h = 0; h < 8; h++) {
-            const int i = i0 + h;
-            const double x = i < N ? E[(int64_t)i * ld + q] : 0.0;
-            digits<S>(x, e, dg[h]);
+            const int i = kc * 64 + warp + 8 * h;
+            t[lane][warp + 8 * h] = (i < N && qin) ? E[(int64_t)i * ld + q0 + lane] : 0.0;
         }
-        const int kc = i0 >> 6;
-        const uint32_t off = tc::sw128_offset((uint32_t)q, (uint32_t)(i0 & 63));
+        __syncthreads();
 #pragma unroll
-        for (int sl = 0; sl < S; sl++) {
-            uint4 va;
-            va.x = pack_bf16x2(dg[0][sl], dg[1][sl]);
-            va.y = pack_bf16x2(dg[2][sl], dg[3][sl]);
-            va.z = pack_bf16x2(dg[4][sl], dg[5][sl]);
-            va.w = pack_bf16x2(dg[6][sl], dg[7][sl]);
-            *reinterpret_cast<uint4 *>(base + G.nA_block(sl, kc) + off) = va;
+        for (int h = 0; h < 4; h++) {
+            const int ql = warp * 4 + h, q = q0 + ql;
+            if (q >= G.P16) break;
+            float dg[2][S];
+            digits<S>(t[ql][2 * lane], eq[h], dg[0]);
+            digits<S>(t[ql][2 * lane + 1], eq[h], dg[1]);
+            const uint32_t off = tc::sw128_offset((uint32_t)q, (uint32_t)(2 * lane));
+#pragma unroll
+            for (int sl = 0; sl < S; sl++)
+                *reinterpret_cast<uint32_t *>(base + G.nA_block(sl, kc) + off) = pack_bf16x2(dg[0][sl], dg[1][sl]);
         }
+        __syncthreads();
     }
 }
 
 // P'_ij = c_IJ P[rel_i][rel_j] over TN-function tiles I = i/TN <= J = j/TN (c_II = 1,
-// c_IJ = 2), read from P's upper triangle. One CTA per batch: a per-batch exponent, then the
-// digits of rows j (TN-row blocks), K = i (chunks of 64).
+// c_IJ = 2; every (i, j) with c = 1 when full), read from P's upper triangle, with the batch's
+// exponent from slice_nphi_kernel. One CTA per (batch, 16 rows j), one warp per row, two
+// functions i per lane (one 128-byte row segment per slice).
 template <int S>
 __global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, uint8_t *__restrict__ slices,
-                                                      const int64_t *__restrict__ sl_off, int32_t *__restrict__ expo_b,
+                                                      const int64_t *__restrict__ sl_off,
+                                                      const int32_t *__restrict__ expo_b,
                                                       const int32_t *__restrict__ tn_b, int full) {
-    __shared__ long long red[8];
-    __shared__ int e_sh;
     const int b = b0 + blockIdx.x, m = s.sys.bmol[b];
     const int P = s.batch_off[b + 1] - s.batch_off[b];
     const int N = s.rel_off[b + 1] - s.rel_off[b];
     if (N == 0) return;
     const SplitGeom G(P, N, S);
+    const int j0 = blockIdx.y * 16;
+    if (j0 >= G.R16) return;
     const int32_t *rel = s.rel_idx + s.rel_off[b];
-    const int TN = tn_b[b];
-    auto pval = [&](int i, int j) -> double {
-        if (i >= N || j >= N || (!full && i / TN > j / TN)) return 0.0;
-        int64_t gi = rel[i], gj = rel[j];
-        if (gi > gj) { const int64_t t = gi; gi = gj; gj = t; }
-        const double pv = p_elem(s, m, gi, gj);
-        // c_IJ = 2 off the diagonal tiles: exact, as one more in the exponent field (zero and
-        // subnormal values, which give no digits, are left as they are)
-        const long long pb = __double_as_longlong(pv);
-        return (!full && i / TN < j / TN && ((pb >> 52) & 0x7FF) != 0) ? __longlong_as_double(pb + (1LL << 52)) : pv;
-    };
-    long long mb = 0;
-    for (int u = threadIdx.x; u < N * N; u += blockDim.x) mb = max(mb, abs_bits(pval(u / N, u % N)));
-    for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mb;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long m = 0;
-        for (int w = 0; w < 8; w++) m = max(m, red[w]);
-        e_sh = row_exponent_bits(m);
-        expo_b[b] = e_sh;
-    }
-    __syncthreads();
-    const int e = e_sh;
+    const int TN = tn_b[b], e = expo_b[b];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint8_t *base = slices + sl_off[b];
-    const int groups = G.n_kcN * 8;  // 8-wide groups along K = i
-    for (int u = threadIdx.x; u < G.R16 * groups; u += blockDim.x) {
-        const int j = u / groups, i0 = (u - j * groups) * 8;
-        float dg[8][S];
+#pragma unroll 1
+    for (int h = 0; h < 2; h++) {
+        const int j = j0 + warp * 2 + h;  // < R16: R16 is a multiple of 16
+        const bool jin = j < N;
+        const int64_t gj = jin ? rel[j] : 0;
+        const int tj = tile_of(j, TN);
+        for (int kc = 0; kc < G.n_kcN; kc++) {
+            float dg[2][S];
 #pragma unroll
-        for (int h = 0; h < 8; h++) digits<S>(pval(i0 + h, j), e, dg[h]);
-        const int kc = i0 >> 6;
-        const uint32_t off = tc::sw128_offset((uint32_t)j, (uint32_t)(i0 & 63));
+            for (int hh = 0; hh < 2; hh++) {
+                const int i = 64 * kc + 2 * lane + hh;
+                double x = 0.0;
+                if (jin && i < N && (full || tile_of(i, TN) <= tj)) {
+                    const int64_t gi = rel[i];
+                    x = gi <= gj ? p_elem(s, m, gi, gj) : p_elem(s, m, gj, gi);
+                    // c_IJ = 2 off the diagonal tiles: exact, as one more in the exponent field
+                    // (zero and subnormal values, which give no digits, are left as they are)
+                    const long long pb = __double_as_longlong(x);
+                    if (!full && tile_of(i, TN) < tj && split_bits::biased_exponent(pb) != 0)
+                        x = __longlong_as_double(pb + (1LL << 52));
+                }
+                digits<S>(x, e, dg[hh]);
+            }
+            const uint32_t off = tc::sw128_offset((uint32_t)j, (uint32_t)(2 * lane));
 #pragma unroll
-        for (int sl = 0; sl < S; sl++) {
-            uint4 vb;
-            vb.x = pack_bf16x2(dg[0][sl], dg[1][sl]);
-            vb.y = pack_bf16x2(dg[2][sl], dg[3][sl]);
-            vb.z = pack_bf16x2(dg[4][sl], dg[5][sl]);
-            vb.w = pack_bf16x2(dg[6][sl], dg[7][sl]);
-            *reinterpret_cast<uint4 *>(base + G.nB_block(S, sl, kc) + off) = vb;
+            for (int sl = 0; sl < S; sl++)
+                *reinterpret_cast<uint32_t *>(base + G.nB_block(S, sl, kc) + off) = pack_bf16x2(dg[0][sl], dg[1][sl]);
         }
     }
 }
@@ -879,20 +881,21 @@ cudaError_t launch_h_tc(const DevSystem &s, const HWork *work, int32_t w0, int32
     return cudaGetLastError();
 }
 
-cudaError_t launch_slice_n(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_qt, const double *scratch,
-                           uint8_t *slices, const int64_t *sl_off, int32_t *expo_q, int32_t *expo_b,
-                           const int32_t *tn_b, int S, bool grad, cudaStream_t st) {
+cudaError_t launch_slice_n(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_qt, int32_t max_rt,
+                           const double *scratch, uint8_t *slices, const int64_t *sl_off, const int32_t *expo_q,
+                           int32_t *expo_b, const int32_t *tn_b, int S, bool grad, cudaStream_t st) {
     if (b1 <= b0) return cudaSuccess;
-    if (max_qt > 0) {
-#define NAO_SLICE_NPHI(SS) \
-    slice_nphi_kernel<SS><<<dim3(b1 - b0, max_qt), 128, 0, st>>>(s, b0, scratch, slices, sl_off, expo_q, grad ? 4 : 1)
-        NAO_SPLIT_DISPATCH(S, NAO_SLICE_NPHI)
+    // y = 0: the exponent of P'; y >= 1: 32-point tiles (128 max_qt >= P16)
+#define NAO_SLICE_NPHI(SS)                                                                                   \
+    slice_nphi_kernel<SS><<<dim3(b1 - b0, 4 * max_qt + 1), 256, 0, st>>>(s, b0, scratch, slices, sl_off, expo_q, \
+                                                                         expo_b, tn_b, grad ? 4 : 1, grad ? 1 : 0)
+    NAO_SPLIT_DISPATCH(S, NAO_SLICE_NPHI)
 #undef NAO_SLICE_NPHI
-    }
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || max_rt <= 0) return e;
+    // 16 rows per CTA (64 max_rt >= R16)
 #define NAO_SLICE_NP(SS) \
-    slice_np_kernel<SS><<<b1 - b0, 256, 0, st>>>(s, b0, slices, sl_off, expo_b, tn_b, grad ? 1 : 0)
+    slice_np_kernel<SS><<<dim3(b1 - b0, 4 * max_rt), 256, 0, st>>>(s, b0, slices, sl_off, expo_b, tn_b, grad ? 1 : 0)
     NAO_SPLIT_DISPATCH(S, NAO_SLICE_NP)
 #undef NAO_SLICE_NP
     return cudaGetLastError();
