@@ -601,7 +601,13 @@ nao_status split_lists(nao_grid *g) {
             nao_split_h_items(b, N, TN, hw[k]);
             for (int Q = 0; Q < G.n_qt; Q++) nw[k].push_back({b, Q, G.n_jtN, 0});  // all J tiles in one CTA
         }
+        // the persistent contraction kernels take items round-robin: heaviest first (H: longest
+        // K; density: most function tiles), so that every CTA gets a similar share
         for (int k = 0; k < 2; k++) {
+            std::stable_sort(hw[k].begin() + c.hw0[k], hw[k].end(),
+                             [&](const HWork &x, const HWork &y) { return g->Pb[x.batch] > g->Pb[y.batch]; });
+            std::stable_sort(nw[k].begin() + c.nw0[k], nw[k].end(),
+                             [](const HWork &x, const HWork &y) { return x.tj > y.tj; });
             c.hw1[k] = (int32_t)hw[k].size();
             c.nw1[k] = (int32_t)nw[k].size();
         }

@@ -333,112 +333,21 @@ __global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, 
 }
 
 // ----------------------------------------------------------------------------------------
-// Slice-product pipeline. Shared memory: a ring of 4 A-tile buffers (128 rows x 64 bf16,
-// 16 KB, one slice of one K chunk each) and two sets of S B-tile buffers (TN rows, TN x 128 B).
-// Producer (warp 0, one lane): for each K chunk, the S B slices into B set kc % 2, then the
-// S A slices one by one into the ring, each copy a single bulk (TMA) transfer completing on a
-// "full" mbarrier. MMA issuer (warp 1, one lane): for each A slice s, the pairs (s, t) with
-// s + t < S as one 128 x TN(S-s) x 16 tcgen05.mma per K step (two where TN(S-s) > 256) into
-// accumulator groups s .. S-1 (tensor-memory columns TN s ...); commits release A buffers and B sets back to the producer through
-// "empty" mbarriers. The 16-column K steps with index < neg16 negate B (descriptor bit 14).
-// Every wait is bounded; on a timeout the CTA records NAO_ERR_TIMEOUT and skips its epilogue.
-// A CTA may run the pipeline several times (one accumulator tile after another): the ring and
-// B-set phases continue from the K chunks of the earlier runs (c0) and "done" completes once per
-// run (parity = run index).
+// Slice-product pipeline of the persistent contraction kernels. Shared memory: a ring of 4
+// A-tile buffers (128 rows x 64 bf16, 16 KB, one slice of one K chunk each) and two sets of S
+// B-tile buffers (TN rows, TN x 128 B). Producer (one lane): for each K chunk, the S B slices
+// into B set kc % 2, then the S A slices one by one into the ring, each copy a single bulk
+// (TMA) transfer completing on a "full" mbarrier. MMA issuer (one lane): for each A slice s,
+// the pairs (s, t) with s + t < S as one 128 x TN(S-s) x 16 tcgen05.mma per K step (two where
+// TN(S-s) > 256) into accumulator groups s .. S-1 (tensor-memory columns TN s ...); commits
+// release A buffers and B sets back to the producer through "empty" mbarriers. The phases of
+// the ring and of the B sets continue over all the accumulations a CTA runs. Every wait is
+// bounded; on a timeout the CTA records NAO_ERR_TIMEOUT and skips the rest of its work.
 // ----------------------------------------------------------------------------------------
 constexpr int RING = 4;
 
-struct Pipe {
-    uint64_t fullA[RING], emptyA[RING], fullB[2], emptyB[2], done;
-    uint32_t tmem;
-    int abort;
-};
-
-struct LoopArgs {
-    const uint8_t *a0;  // A tile (slice s, chunk kc) at a0 + s a_s + kc a_kc, a_bytes long
-    size_t a_s, a_kc;
-    const uint8_t *b0;  // B tile (slice t, chunk kc) at b0 + t b_s + kc b_kc, b_bytes long
-    size_t b_s, b_kc;
-    uint32_t a_bytes, b_bytes;  // <= 16 KB and TN x 128 B (the last tile of an operand is short)
-    int n_kc, neg16, S;
-    int c0 = 0;     // K chunks this CTA's earlier runs of the pipeline processed
-    int round = 0;  // index of this run
-};
-
 __host__ __device__ constexpr size_t pipe_smem_bytes(int S) {
     return (size_t)RING * 16384 + 2 * (size_t)S * nao_split_tn(S) * 128 + 1024;
-}
-
-template <int TN>
-__device__ __forceinline__ void pipe_producer(Pipe &p, uint8_t *sA, uint8_t *sB, const LoopArgs &L) {
-    constexpr uint32_t B_BLOCK = TN * 128;
-    const int S = L.S;
-    for (int kc = 0; kc < L.n_kc; kc++) {
-        const int gk = L.c0 + kc, bb = gk & 1, ub = gk >> 1;
-        if (ub >= 1 && !tc::mbar_wait(&p.emptyB[bb], (ub - 1) & 1, kWaitCycles)) { p.abort = 1; return; }
-        tc::mbar_arrive_expect_tx(&p.fullB[bb], (uint32_t)S * L.b_bytes);
-        for (int t = 0; t < S; t++)
-            tc::bulk_g2s(sB + ((size_t)bb * S + t) * B_BLOCK, L.b0 + t * L.b_s + kc * L.b_kc, L.b_bytes, &p.fullB[bb]);
-        for (int sa = 0; sa < S; sa++) {
-            const int idx = gk * S + sa, a = idx % RING, ua = idx / RING;
-            if (ua >= 1 && !tc::mbar_wait(&p.emptyA[a], (ua - 1) & 1, kWaitCycles)) { p.abort = 1; return; }
-            tc::mbar_arrive_expect_tx(&p.fullA[a], L.a_bytes);
-            tc::bulk_g2s(sA + (size_t)a * 16384, L.a0 + sa * L.a_s + kc * L.a_kc, L.a_bytes, &p.fullA[a]);
-        }
-        if (*(volatile int *)&p.abort) return;
-    }
-}
-
-template <int TN>
-__device__ __forceinline__ void pipe_mma(Pipe &p, uint8_t *sA, uint8_t *sB, uint32_t tm, const LoopArgs &L) {
-    constexpr uint32_t B_BLOCK = TN * 128;
-    const int S = L.S;
-    for (int kc = 0; kc < L.n_kc; kc++) {
-        const int gk = L.c0 + kc, bb = gk & 1, ub = gk >> 1;
-        // on a timeout: flag it, and still commit "done" so the teardown waits for issued MMAs
-        if (!tc::mbar_wait(&p.fullB[bb], ub & 1, kWaitCycles)) { p.abort = 1; tc::mma_commit(&p.done); return; }
-        for (int sa = 0; sa < S; sa++) {
-            const int idx = gk * S + sa, a = idx % RING, ua = idx / RING;
-            if (!tc::mbar_wait(&p.fullA[a], ua & 1, kWaitCycles)) { p.abort = 1; tc::mma_commit(&p.done); return; }
-            tc::fence_after_sync();
-            const uint64_t ad = tc::sdesc_sw128(tc::smem_addr(sA + (size_t)a * 16384));
-            // The B slices t = 0 .. S-1-sa are consecutive TN-row tiles of the B set, one
-            // (S-sa) TN-row operand, and their groups sa + t are consecutive TN-column blocks of
-            // tensor memory: one MMA per 16-column K step covers all pairs (sa, t), split at the
-            // MMA's largest N of 256.
-            const int ncols = TN * (S - sa);
-            const uint8_t *bset = sB + (size_t)bb * S * B_BLOCK;
-            for (int n0 = 0; n0 < ncols; n0 += 256) {
-                const int nn = ncols - n0 < 256 ? ncols - n0 : 256;
-                const uint32_t idesc = tc::idesc_bf16_f32(128, nn);
-                const uint64_t bd = tc::sdesc_sw128(tc::smem_addr(bset + (size_t)n0 * 128));
-                const uint32_t dt = tm + (uint32_t)(sa * TN + n0);
-#pragma unroll
-                for (int ks = 0; ks < 4; ks++) {
-                    const uint32_t id = (kc * 4 + ks < L.neg16) ? (idesc | (1u << 14)) : idesc;
-                    tc::mma_bf16(dt, ad + 2 * ks, bd + 2 * ks, id, (kc | sa | ks) ? 1u : 0u);
-                }
-            }
-            tc::mma_commit(&p.emptyA[a]);
-        }
-        tc::mma_commit(&p.emptyB[bb]);
-    }
-    tc::mma_commit(&p.done);
-}
-
-// Runs the pipeline; on return (all threads) the accumulators are complete unless p.abort.
-template <int TN>
-__device__ __forceinline__ void pipe_run(Pipe &p, uint8_t *smem, uint32_t tm, const LoopArgs &L, int32_t *err) {
-    uint8_t *sA = smem, *sB = smem + (size_t)RING * 16384;
-    if (threadIdx.x == 0) pipe_producer<TN>(p, sA, sB, L);
-    else if (threadIdx.x == 32) pipe_mma<TN>(p, sA, sB, tm, L);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (!tc::mbar_wait(&p.done, (uint32_t)(L.round & 1), kWaitCycles)) p.abort = 1;
-        if (p.abort) atomicExch(err, (int)NAO_ERR_TIMEOUT);
-    }
-    __syncthreads();
-    tc::fence_after_sync();
 }
 
 // Integer recombination of the S group accumulators for 16 columns of this thread's row:
@@ -476,38 +385,6 @@ __device__ __forceinline__ double recombine(long long hi, long long lo, long lon
 
 __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
     return reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
-}
-
-__device__ __forceinline__ uint32_t tc_setup(Pipe &p) {
-    const int warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < RING; i++) {
-            tc::mbar_init(&p.fullA[i], 1);
-            tc::mbar_init(&p.emptyA[i], 1);
-        }
-        for (int i = 0; i < 2; i++) {
-            tc::mbar_init(&p.fullB[i], 1);
-            tc::mbar_init(&p.emptyB[i], 1);
-        }
-        tc::mbar_init(&p.done, 1);
-        tc::fence_mbar_init();
-        p.abort = 0;
-    }
-    __syncwarp();
-    if (warp == 0) {
-        tc::tmem_alloc(&p.tmem, 512);
-        tc::tmem_relinquish();
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    return p.tmem;
-}
-
-__device__ __forceinline__ void tc_teardown(uint32_t tm) {
-    tc::fence_before_sync();
-    __syncthreads();
-    if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(tm, 512);
 }
 
 // Persistent, warp-specialised H contraction: one CTA per SM walks the work items w =
@@ -702,98 +579,229 @@ __global__ void __launch_bounds__(192, 1)
     if (warp == 0) tc::tmem_dealloc(tm, 512);
 }
 
-// One CTA per (batch, 128-point tile): the TN-function tiles J = 0 .. nJ-1 one after another
-// (tensor memory holds one tile's accumulators), each epilogue adding its part of n_q in
-// registers; the CTA then stores n for its points (no atomics: one CTA owns each point).
-// GRADN (density gradient, Sec. 2): T = Phi P over all of P (P' = P, K = every function), and the
-// epilogue also forms grad n_q = 2 sum_j T_qj grad phi_qj from the rows [phi | grad phi] of 4 Ppad.
+// Density contraction, persistent and warp-specialised as h_tc_kernel: one CTA per SM walks
+// the work items (batch, 128-point tile, nJ TN-function tiles) w = blockIdx.x, blockIdx.x +
+// gridDim.x, ...; each item is nJ accumulations T_qJ = Phi_q P'_J (K = the functions up to
+// tile J, where P' is nonzero), one after another through the single accumulator set. Warps
+// 0-3 (one point each) read tile J's accumulators, hand tensor memory back and then add
+// sum_j T_qj phi_qj to the point's n in registers while tile J+1's MMAs run; after the last
+// tile they store n (no atomics: one item owns each point).
+// GRADN (density gradient, Sec. 2): P' = P over all of K, and the epilogue also forms
+// grad n_q = 2 sum_j T_qj grad phi_qj from the rows [phi | grad phi] of 4 Ppad.
+struct NItem {  // geometry of one density work item
+    const uint8_t *a0, *b0;  // A: slice 0, chunk 0 of the point tile; B: slice 0, chunk 0, tile 0
+    size_t a_s, a_kc, b_s, b_kc;
+    uint32_t a_bytes;
+    int nJ, n_kcN, R16, b, m, p0, P, Ppad, N, ti;
+};
+
+template <int TN>
+__device__ __forceinline__ NItem n_item(const DevSystem &s, const HWork *work, int32_t w, const uint8_t *slices,
+                                        const int64_t *sl_off, int S) {
+    NItem h;
+    const HWork it = work[w];  // batch, 128-point tile, number of TN-function tiles
+    h.b = it.batch;
+    h.ti = it.ti;
+    h.nJ = it.tj;
+    h.m = s.sys.bmol[h.b];
+    h.p0 = s.batch_off[h.b];
+    h.P = s.batch_off[h.b + 1] - h.p0;
+    h.Ppad = (h.P + NAO_PPAD - 1) & ~(NAO_PPAD - 1);
+    h.N = s.rel_off[h.b + 1] - s.rel_off[h.b];
+    const SplitGeom G(h.P, h.N, S, TN);
+    const uint8_t *base = slices + sl_off[h.b];
+    h.a0 = base + G.nA_block(0, 0) + (size_t)it.ti * 128 * 128;
+    h.a_s = (size_t)G.n_kcN * G.P16 * 128;
+    h.a_kc = (size_t)G.P16 * 128;
+    h.b0 = base + G.nB_block(S, 0, 0);
+    h.b_s = (size_t)G.n_kcN * G.R16 * 128;
+    h.b_kc = (size_t)G.R16 * 128;
+    h.a_bytes = (uint32_t)min(128, G.P16 - it.ti * 128) * 128u;
+    h.n_kcN = G.n_kcN;
+    h.R16 = G.R16;
+    return h;
+}
+
+// K chunks of tile J: P' is zero for basis functions beyond tile J, so K stops at TN (J + 1)
+// (all of K for GRADN)
 template <int TN, bool GRADN>
-__global__ void __launch_bounds__(128, 1) n_tc_kernel(DevSystem s, const HWork *__restrict__ work, int32_t w0,
-                                                     const uint8_t *__restrict__ slices, const int64_t *__restrict__ sl_off,
-                                                     const int32_t *__restrict__ expo_q, const int32_t *__restrict__ expo_b,
-                                                     const double *__restrict__ scratch, int S, int32_t *__restrict__ err) {
+__device__ __forceinline__ int n_item_kc(const NItem &h, int J) {
+    const int nk = GRADN ? h.n_kcN : ((J + 1) * TN + 63) / 64;
+    return nk < h.n_kcN ? nk : h.n_kcN;
+}
+
+template <int TN, bool GRADN>
+__global__ void __launch_bounds__(192, 1)
+    n_tc_kernel(DevSystem s, const HWork *__restrict__ work, int32_t w0, int32_t n_work, const uint8_t *__restrict__ slices,
+                const int64_t *__restrict__ sl_off, const int32_t *__restrict__ expo_q,
+                const int32_t *__restrict__ expo_b, const double *__restrict__ scratch, int S,
+                int32_t *__restrict__ err) {
+    constexpr uint32_t B_BLOCK = TN * 128;
     extern __shared__ uint8_t smem_dyn[];
-    __shared__ Pipe pp;
+    __shared__ PPipe pp;
     uint8_t *smem = align1024(smem_dyn);
-    const HWork it = work[w0 + blockIdx.x];  // batch, 128-point tile, number of TN-function tiles
-    const int b = it.batch, m = s.sys.bmol[b];
-    const int p0 = s.batch_off[b], P = s.batch_off[b + 1] - p0;
-    const int Ppad = (P + NAO_PPAD - 1) & ~(NAO_PPAD - 1);
-    const int N = s.rel_off[b + 1] - s.rel_off[b];
-    const SplitGeom G(P, N, S, TN);
+    uint8_t *sA = smem, *sB = smem + (size_t)RING * 16384;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t tm = tc_setup(pp);
-    const uint8_t *base = slices + sl_off[b];
-    const int q = it.ti * 128 + warp * 32 + lane;
-    const bool row_ok = q < P;
-    const double *E = scratch + s.scr_off[b];
-    const int64_t ld = GRADN ? 4 * (int64_t)Ppad : (int64_t)Ppad;
-    const uint32_t tm_row = tm + ((uint32_t)(warp * 32) << 16);
-    double part_hi = 0.0, part_lo = 0.0, part_lo2 = 0.0;
-    double gr_hi[3] = {0.0, 0.0, 0.0}, gr_lo[3] = {0.0, 0.0, 0.0}, gr_lo2[3] = {0.0, 0.0, 0.0};
-    int c0 = 0;
-    if (threadIdx.x == 0 && *(volatile int32_t *)err != 0) pp.abort = 1;  // a timeout earlier in this launch
-    __syncthreads();
-    for (int J = 0; J < it.tj && !pp.abort; J++) {
-        LoopArgs L;
-        L.a0 = base + G.nA_block(0, 0) + (size_t)it.ti * 128 * 128;
-        L.a_s = (size_t)G.n_kcN * G.P16 * 128;
-        L.a_kc = (size_t)G.P16 * 128;
-        L.b0 = base + G.nB_block(S, 0, 0) + (size_t)J * TN * 128;
-        L.b_s = (size_t)G.n_kcN * G.R16 * 128;
-        L.b_kc = (size_t)G.R16 * 128;
-        L.a_bytes = (uint32_t)min(128, G.P16 - it.ti * 128) * 128u;
-        L.b_bytes = (uint32_t)min(TN, G.R16 - J * TN) * 128u;
-        // P' is zero for basis functions beyond tile J, so K stops at TN (J + 1) (all of K for GRADN)
-        const int nk = GRADN ? G.n_kcN : ((J + 1) * TN + 63) / 64;
-        L.n_kc = nk < G.n_kcN ? nk : G.n_kcN;
-        L.neg16 = 0;
-        L.S = S;
-        L.c0 = c0;
-        L.round = J;
-        if (J > 0) {  // the previous tile's accumulators have been read by every thread
-            tc::fence_before_sync();
-            __syncthreads();
-            tc::fence_after_sync();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < RING; i++) {
+            tc::mbar_init(&pp.fullA[i], 1);
+            tc::mbar_init(&pp.emptyA[i], 1);
         }
-        pipe_run<TN>(pp, smem, tm, L, err);
-        if (pp.abort) break;
-        c0 += L.n_kc;
-        for (int cc = 0; cc < TN; cc += 16) {
-            Parts16 v;
-            combine16<TN>(tm_row, cc, S, v);
-#pragma unroll
-            for (int jj = 0; jj < 16; jj++) {
-                const int j = J * TN + cc + jj;
-                if (row_ok && j < N) {
-                    const double f = E[(int64_t)j * ld + q];
-                    const double th = (double)v.hi[jj], tl = (double)v.lo[jj], tl2 = TN != 48 ? (double)v.lo2[jj] : 0.0;
-                    part_hi = fma(th, f, part_hi);
-                    part_lo = fma(tl, f, part_lo);
-                    if (TN != 48) part_lo2 = fma(tl2, f, part_lo2);
-                    if (GRADN)
-#pragma unroll
-                        for (int d = 0; d < 3; d++) {
-                            const double gf = E[(int64_t)j * ld + (d + 1) * Ppad + q];
-                            gr_hi[d] = fma(th, gf, gr_hi[d]);
-                            gr_lo[d] = fma(tl, gf, gr_lo[d]);
-                            if (TN != 48) gr_lo2[d] = fma(tl2, gf, gr_lo2[d]);
+        for (int i = 0; i < 2; i++) {
+            tc::mbar_init(&pp.fullB[i], 1);
+            tc::mbar_init(&pp.emptyB[i], 1);
+        }
+        tc::mbar_init(&pp.acc_full, 1);
+        tc::mbar_init(&pp.acc_empty, 4);  // one arrival per accumulator-reading warp
+        tc::mbar_init(&pp.fin, 1);
+        tc::fence_mbar_init();
+        pp.abort = *(volatile int32_t *)err != 0 ? 1 : 0;  // a timeout earlier in this launch
+    }
+    __syncwarp();
+    if (warp == 0) {
+        tc::tmem_alloc(&pp.tmem, 512);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tm = pp.tmem;
+    volatile int *abort = &pp.abort;
+
+    if (warp == 4) {
+        // ---- producer ----
+        if (lane == 0) {
+            int gk = 0;
+            for (int w = blockIdx.x; w < n_work && !*abort; w += gridDim.x) {
+                const NItem h = n_item<TN>(s, work, w0 + w, slices, sl_off, S);
+                for (int J = 0; J < h.nJ && !*abort; J++) {
+                    const int nk = n_item_kc<TN, GRADN>(h, J);
+                    const uint8_t *bJ = h.b0 + (size_t)J * TN * 128;
+                    const uint32_t b_bytes = (uint32_t)min(TN, h.R16 - J * TN) * 128u;
+                    for (int kc = 0; kc < nk; kc++, gk++) {
+                        const int bb = gk & 1, ub = gk >> 1;
+                        if (ub >= 1 && !tc::mbar_wait(&pp.emptyB[bb], (ub - 1) & 1, kWaitCycles)) { *abort = 1; break; }
+                        tc::mbar_arrive_expect_tx(&pp.fullB[bb], (uint32_t)S * b_bytes);
+                        for (int t = 0; t < S; t++)
+                            tc::bulk_g2s(sB + ((size_t)bb * S + t) * B_BLOCK, bJ + t * h.b_s + kc * h.b_kc, b_bytes,
+                                         &pp.fullB[bb]);
+                        for (int sa = 0; sa < S; sa++) {
+                            const int idx = gk * S + sa, a = idx % RING, ua = idx / RING;
+                            if (ua >= 1 && !tc::mbar_wait(&pp.emptyA[a], (ua - 1) & 1, kWaitCycles)) { *abort = 1; break; }
+                            tc::mbar_arrive_expect_tx(&pp.fullA[a], h.a_bytes);
+                            tc::bulk_g2s(sA + (size_t)a * 16384, h.a0 + sa * h.a_s + kc * h.a_kc, h.a_bytes, &pp.fullA[a]);
                         }
+                        if (*abort) break;
+                    }
                 }
             }
         }
-    }
-    if (!pp.abort && row_ok) {
-        const int eq = expo_q[p0 + q], eb = expo_b[b];
-        const bool live = eq > -10000 && eb > -10000;
-        const double s48 = pow2(eq + eb - 48), s66 = pow2(eq + eb - 66), s84 = pow2(eq + eb - 84);
-        *n_at(s, m, p0 + q) = live ? fma(part_hi, s48, fma(part_lo, s66, part_lo2 * s84)) : 0.0;
-        if (GRADN)
+    } else if (warp == 5) {
+        // ---- MMA issuer ----
+        if (lane == 0) {
+            int gk = 0, t = 0;
+            for (int w = blockIdx.x; w < n_work && !*abort; w += gridDim.x) {
+                const NItem h = n_item<TN>(s, work, w0 + w, slices, sl_off, S);
+                for (int J = 0; J < h.nJ && !*abort; J++, t++) {
+                    const int nk = n_item_kc<TN, GRADN>(h, J);
+                    // the accumulators of the previous tile have been read
+                    if (t >= 1 && !tc::mbar_wait(&pp.acc_empty, (t - 1) & 1, kWaitCycles)) { *abort = 1; break; }
+                    tc::fence_after_sync();
+                    for (int kc = 0; kc < nk && !*abort; kc++, gk++) {
+                        const int bb = gk & 1, ub = gk >> 1;
+                        if (!tc::mbar_wait(&pp.fullB[bb], ub & 1, kWaitCycles)) { *abort = 1; break; }
+                        const uint8_t *bset = sB + (size_t)bb * S * B_BLOCK;
+                        for (int sa = 0; sa < S; sa++) {
+                            const int idx = gk * S + sa, a = idx % RING, ua = idx / RING;
+                            if (!tc::mbar_wait(&pp.fullA[a], ua & 1, kWaitCycles)) { *abort = 1; break; }
+                            tc::fence_after_sync();
+                            const uint64_t ad = tc::sdesc_sw128(tc::smem_addr(sA + (size_t)a * 16384));
+                            // pairs (sa, t = 0 .. S-1-sa): one MMA per 16-column K step (two above N = 256)
+                            const int ncols = TN * (S - sa);
+                            for (int n0 = 0; n0 < ncols; n0 += 256) {
+                                const int nn = ncols - n0 < 256 ? ncols - n0 : 256;
+                                const uint32_t idesc = tc::idesc_bf16_f32(128, nn);
+                                const uint64_t bd = tc::sdesc_sw128(tc::smem_addr(bset + (size_t)n0 * 128));
+                                const uint32_t dt = tm + (uint32_t)(sa * TN + n0);
 #pragma unroll
-            for (int d = 0; d < 3; d++)
-                *gn_at(s, m, p0 + q, d) = live ? 2.0 * fma(gr_hi[d], s48, fma(gr_lo[d], s66, gr_lo2[d] * s84)) : 0.0;
+                                for (int ks = 0; ks < 4; ks++)
+                                    tc::mma_bf16(dt, ad + 2 * ks, bd + 2 * ks, idesc, (kc | sa | ks) ? 1u : 0u);
+                            }
+                            tc::mma_commit(&pp.emptyA[a]);
+                        }
+                        tc::mma_commit(&pp.emptyB[bb]);
+                    }
+                    if (*abort) break;
+                    tc::mma_commit(&pp.acc_full);  // tile J's accumulators are complete
+                }
+            }
+            // every issued MMA has completed before tensor memory is released
+            tc::mma_commit(&pp.fin);
+            if (!tc::mbar_wait(&pp.fin, 0, kWaitCycles)) *abort = 1;
+        }
+    } else {
+        // ---- accumulator readers and the n epilogue (warps 0-3) ----
+        int t = 0;
+        const uint32_t tm_row = tm + ((uint32_t)(warp * 32) << 16);
+        for (int w = blockIdx.x; w < n_work && !*abort; w += gridDim.x) {
+            const NItem h = n_item<TN>(s, work, w0 + w, slices, sl_off, S);
+            const int q = h.ti * 128 + warp * 32 + lane;
+            const bool row_ok = q < h.P;
+            const double *E = scratch + s.scr_off[h.b];
+            const int64_t ld = GRADN ? 4 * (int64_t)h.Ppad : (int64_t)h.Ppad;
+            // sum_j T_qj phi_qj (and grad phi) in units of 2^(e_q + e_b) 64^-8. Each T_qj is
+            // rounded once to FP64 (hi + lo 64^-3 + lo2 64^-6: relative error 2^-53, so the sum's
+            // error stays below 2^-53 sum_j |T_qj phi_qj| <= 2^-53 sum_ij |phi_qi P_ij phi_qj|):
+            // two conversions and one FMA per element (48 wide), then one FMA per product.
+            double part = 0.0, gpart[3] = {0.0, 0.0, 0.0};
+            for (int J = 0; J < h.nJ; J++, t++) {
+                if (*abort || !tc::mbar_wait(&pp.acc_full, t & 1, kWaitCycles)) { *abort = 1; break; }
+                tc::fence_after_sync();
+                double val[TN];
+#pragma unroll
+                for (int c0 = 0; c0 < TN; c0 += 16) {
+                    Parts16 v;
+                    combine16<TN>(tm_row, c0, S, v);
+#pragma unroll
+                    for (int jj = 0; jj < 16; jj++) {
+                        const double th = fma((double)v.lo[jj], 0x1p-18, (double)v.hi[jj]);
+                        val[c0 + jj] = TN == 48 ? th : fma((double)v.lo2[jj], 0x1p-36, th);
+                    }
+                }
+                // tensor memory is free for the next tile
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&pp.acc_empty);
+                if (row_ok) {
+                    const int jn = min(TN, h.N - J * TN);
+                    const double *f = E + (int64_t)J * TN * ld + q;
+#pragma unroll
+                    for (int jj = 0; jj < TN; jj++) {
+                        if (jj < jn) {
+                            part = fma(val[jj], f[jj * ld], part);
+                            if (GRADN)
+#pragma unroll
+                                for (int d = 0; d < 3; d++) gpart[d] = fma(val[jj], f[jj * ld + (d + 1) * h.Ppad], gpart[d]);
+                        }
+                    }
+                }
+            }
+            if (*abort) break;
+            if (row_ok) {
+                const int eq = expo_q[h.p0 + q], eb = expo_b[h.b];
+                const bool live = eq > -10000 && eb > -10000;
+                const double sc = pow2(eq + eb - 48);
+                *n_at(s, h.m, h.p0 + q) = live ? part * sc : 0.0;
+                if (GRADN)
+#pragma unroll
+                    for (int d = 0; d < 3; d++) *gn_at(s, h.m, h.p0 + q, d) = live ? 2.0 * gpart[d] * sc : 0.0;
+            }
+        }
     }
-    tc_teardown(tm);
+    if (*abort && threadIdx.x == 0) atomicExch(err, (int)NAO_ERR_TIMEOUT);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tm, 512);
 }
 
 // sum over each density tile of 64 points of w n (then the deterministic final reduction)
@@ -907,8 +915,9 @@ cudaError_t launch_n_tc(const DevSystem &s, const HWork *work, int32_t w0, int32
     if (n_work <= 0) return cudaSuccess;
     if (tn != 32 && !(tn == 48 && S <= 10)) return cudaErrorInvalidValue;
     const size_t sm = split_smem_bytes(S);
+    const int grid = n_work < sm_count() ? n_work : sm_count();  // persistent: one CTA per SM
 #define NAO_N_TC(TNV, G) \
-    n_tc_kernel<TNV, G><<<n_work, 128, sm, st>>>(s, work, w0, slices, sl_off, expo_q, expo_b, scratch, S, err)
+    n_tc_kernel<TNV, G><<<grid, 192, sm, st>>>(s, work, w0, n_work, slices, sl_off, expo_q, expo_b, scratch, S, err)
     if (tn == 48 && grad) NAO_N_TC(48, true);
     else if (tn == 48) NAO_N_TC(48, false);
     else if (grad) NAO_N_TC(32, true);
