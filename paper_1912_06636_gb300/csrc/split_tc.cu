@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, 
 }
 
 // ----------------------------------------------------------------------------------------
-// Slice-product pipeline of the persistent contraction kernels. Shared memory: a ring of 4
+// Slice-product pipeline of the persistent contraction kernels. Shared memory: a ring of 6
 // A-tile buffers (128 rows x 64 bf16, 16 KB, one slice of one K chunk each) and two sets of S
 // B-tile buffers (TN rows, TN x 128 B). Producer (one lane): for each K chunk, the S B slices
 // into B set kc % 2, then the S A slices one by one into the ring, each copy a single bulk
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, 
 // the ring and of the B sets continue over all the accumulations a CTA runs. Every wait is
 // bounded; on a timeout the CTA records NAO_ERR_TIMEOUT and skips the rest of its work.
 // ----------------------------------------------------------------------------------------
-constexpr int RING = 4;
+constexpr int RING = 6;
 
 __host__ __device__ constexpr size_t pipe_smem_bytes(int S) {
     return (size_t)RING * 16384 + 2 * (size_t)S * nao_split_tn(S) * 128 + 1024;
