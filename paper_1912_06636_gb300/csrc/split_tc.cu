@@ -24,6 +24,7 @@
 // tiles I <= J with c_II = 1, c_IJ = 2, else 0) so that T_qj = sum_i phi_qi P'_ij and
 // n_q = sum_j T_qj phi_qj; one per-batch exponent is used for P'.
 #include <cmath>
+#include <type_traits>
 
 #include "nao_internal.h"
 #include "split_bits.h"
@@ -749,23 +750,29 @@ __global__ void __launch_bounds__(192, 1)
             const bool row_ok = q < h.P;
             const double *E = scratch + s.scr_off[h.b];
             const int64_t ld = GRADN ? 4 * (int64_t)h.Ppad : (int64_t)h.Ppad;
-            // sum_j T_qj phi_qj (and grad phi) in units of 2^(e_q + e_b) 64^-8. Each T_qj is
-            // rounded once to FP64 (hi + lo 64^-3 + lo2 64^-6: relative error 2^-53, so the sum's
-            // error stays below 2^-53 sum_j |T_qj phi_qj| <= 2^-53 sum_ij |phi_qi P_ij phi_qj|):
-            // two conversions and one FMA per element (48 wide), then one FMA per product.
+            // sum_j T_qj phi_qj (and grad phi) in units of 2^(e_q + e_b - 50). Width 48 (S <= 10):
+            // each T_qj as one 64-bit integer in those units, 4 hi + round(lo / 2^16) (|4 hi| <
+            // 2^62.03), rounded by at most 2^-1 unit, the order of the split's own truncation (the
+            // dropped groups g >= S reach K (S + 1) 2^(e_q + e_b - 6S - 2)); then one conversion
+            // and one FMA per product. Width 32 (S = 11, 12, whose truncation is far smaller): T_qj
+            // rounded to FP64 relative to itself, 4 hi + lo 2^-16 + lo2 2^-34.
             double part = 0.0, gpart[3] = {0.0, 0.0, 0.0};
             for (int J = 0; J < h.nJ; J++, t++) {
                 if (*abort || !tc::mbar_wait(&pp.acc_full, t & 1, kWaitCycles)) { *abort = 1; break; }
                 tc::fence_after_sync();
-                double val[TN];
+                using Val = typename std::conditional<TN == 48, long long, double>::type;
+                Val val[TN];
 #pragma unroll
                 for (int c0 = 0; c0 < TN; c0 += 16) {
                     Parts16 v;
                     combine16<TN>(tm_row, c0, S, v);
 #pragma unroll
                     for (int jj = 0; jj < 16; jj++) {
-                        const double th = fma((double)v.lo[jj], 0x1p-18, (double)v.hi[jj]);
-                        val[c0 + jj] = TN == 48 ? th : fma((double)v.lo2[jj], 0x1p-36, th);
+                        if constexpr (TN == 48)
+                            val[c0 + jj] = (v.hi[jj] << 2) + ((v.lo[jj] + (1LL << 15)) >> 16);
+                        else
+                            val[c0 + jj] = fma((double)v.lo2[jj], 0x1p-34,
+                                               fma((double)v.lo[jj], 0x1p-16, 4.0 * (double)v.hi[jj]));
                     }
                 }
                 // tensor memory is free for the next tile
@@ -773,15 +780,22 @@ __global__ void __launch_bounds__(192, 1)
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&pp.acc_empty);
                 if (row_ok) {
+                    // the next tile's rows of phi towards L2 while this tile's products run
+                    if (J + 1 < h.nJ) {
+                        const double *fn = E + (int64_t)(J + 1) * TN * ld + q;
+                        const int jn1 = min(TN, h.N - (J + 1) * TN);
+                        for (int jj = 0; jj < jn1; jj++) asm volatile("prefetch.global.L2 [%0];" ::"l"(fn + jj * ld));
+                    }
                     const int jn = min(TN, h.N - J * TN);
                     const double *f = E + (int64_t)J * TN * ld + q;
 #pragma unroll
                     for (int jj = 0; jj < TN; jj++) {
                         if (jj < jn) {
-                            part = fma(val[jj], f[jj * ld], part);
+                            const double vj = (double)val[jj];
+                            part = fma(vj, f[jj * ld], part);
                             if (GRADN)
 #pragma unroll
-                                for (int d = 0; d < 3; d++) gpart[d] = fma(val[jj], f[jj * ld + (d + 1) * h.Ppad], gpart[d]);
+                                for (int d = 0; d < 3; d++) gpart[d] = fma(vj, f[jj * ld + (d + 1) * h.Ppad], gpart[d]);
                         }
                     }
                 }
@@ -790,7 +804,7 @@ __global__ void __launch_bounds__(192, 1)
             if (row_ok) {
                 const int eq = expo_q[h.p0 + q], eb = expo_b[h.b];
                 const bool live = eq > -10000 && eb > -10000;
-                const double sc = pow2(eq + eb - 48);
+                const double sc = pow2(eq + eb - 50);
                 *n_at(s, h.m, h.p0 + q) = live ? part * sc : 0.0;
                 if (GRADN)
 #pragma unroll
