@@ -526,6 +526,7 @@ nao_status build(nao_grid *g, const nao_system_desc *descs, int32_t n_sys, const
     s.n_rgrid = g->n_rgrid;
     s.r0 = g->r0;
     s.inv_delta = 1.0 / g->delta;
+    s.step_m1 = std::expm1(g->delta);
     s.nb = g->nb;
     for (int l = 0; l <= NAO_LMAX; l++)
         for (int m = 0; m <= NAO_LMAX; m++) {

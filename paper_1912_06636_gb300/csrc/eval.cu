@@ -21,6 +21,27 @@
 
 namespace {
 
+// log(1 + x) for the radial coordinate, x = r / r_k - 1, normally in [0, b), b = exp(Delta) - 1
+// of the logarithmic grid. For |x| <= b <= 0.031 (grids with Delta <= 0.03) the Taylor series
+// x - x^2/2 + x^3/3 - ... to x^12/12 (the first omitted term is below 2^-53 |x|), evaluated by
+// Horner's rule; otherwise (coarser grids, r beyond the last knot) log1p.
+__device__ __forceinline__ double log1p_small(double x, double b) {
+    if (b > 0.031 || fabs(x) > b) return log1p(x);
+    double p = -1.0 / 12.0;
+    p = fma(p, x, 1.0 / 11.0);
+    p = fma(p, x, -1.0 / 10.0);
+    p = fma(p, x, 1.0 / 9.0);
+    p = fma(p, x, -1.0 / 8.0);
+    p = fma(p, x, 1.0 / 7.0);
+    p = fma(p, x, -1.0 / 6.0);
+    p = fma(p, x, 1.0 / 5.0);
+    p = fma(p, x, -1.0 / 4.0);
+    p = fma(p, x, 1.0 / 3.0);
+    p = fma(p, x, -0.5);
+    p = fma(p, x, 1.0);
+    return p * x;
+}
+
 // (2m-1)!!
 __host__ __device__ constexpr double double_factorial_odd(int m) { return m <= 1 ? 1.0 : (2 * m - 1) * double_factorial_odd(m - 1); }
 
@@ -95,10 +116,21 @@ __device__ __noinline__ void eval_group(const DevSystem &s, const AtomGroup &ag,
     T t;
     double xk = 0.0;  // FP32 path: r / r_k - 1, for the FP64 re-evaluation of ill-conditioned segments
     if constexpr (std::is_same<T, double>::value) {
-        const double sc = log(rr / s.r0) * s.inv_delta;
-        k = (int)floor(sc);
+        // segment k from an FP32 logarithm, moved by one where it disagrees with the FP64 knots
+        // (r_k <= r < r_{k+1} as rr / r_k - 1 in [0, exp(Delta) - 1)), then
+        // t = ln(r / r_k) / Delta = log1p(rr / r_k - 1) / Delta
+        const float sa = __logf((float)rr * (float)__ldg(s.inv_rk)) * (float)s.inv_delta;
+        k = (int)floorf(sa);
         k = k < 0 ? 0 : (k > s.n_rgrid - 2 ? s.n_rgrid - 2 : k);
-        t = sc - (double)k;
+        double xr = fma(rr, __ldg(s.inv_rk + k), -1.0);
+        if (xr < 0.0 && k > 0) {
+            k--;
+            xr = fma(rr, __ldg(s.inv_rk + k), -1.0);
+        } else if (xr >= s.step_m1 && k < s.n_rgrid - 2) {
+            k++;
+            xr = fma(rr, __ldg(s.inv_rk + k), -1.0);
+        }
+        t = log1p_small(xr, s.step_m1) * s.inv_delta;
     } else {
         // FP32 segment, refined as ln(r / r_k)/Delta = log1p(r * (1/r_k) - 1)/Delta with one FP64
         // FMA: t keeps ~1e-7 although a plain FP32 ln(r/r0) carries ~1e-6.
@@ -108,8 +140,9 @@ __device__ __noinline__ void eval_group(const DevSystem &s, const AtomGroup &ag,
         xk = fma(rr, __ldg(s.inv_rk + k), -1.0);
         t = log1pf((float)xk) * (float)s.inv_delta;
     }
-    const T dr_scale = T(s.inv_delta / rr);  // dR/dr = dR/ds * inv_delta / rr
-    const T u = T(1.0 / r);
+    const double ur = 1.0 / r;
+    const T dr_scale = T(s.inv_delta * (r < s.r0 ? __ldg(s.inv_rk) : ur));  // dR/dr = dR/ds * inv_delta / rr
+    const T u = T(ur);
     const T x = T(dx), y = T(dy), z = T(dz);
     // The solid harmonics and their gradients are computed in FP64 on both paths (type H): the
     // recurrences cancel near the nodes of cos(m phi), sin(m phi) and P_l^m(cos theta), where

@@ -69,6 +69,7 @@ struct DevSystem {
     const int64_t *scr_off;   // [n_batches] element offset of the batch's block in scratch
     int32_t n_rgrid;
     double r0, inv_delta;
+    double step_m1;           // exp(Delta) - 1: r_{k+1} / r_k - 1 of the logarithmic grid
     int64_t nb;               // total basis size over all systems
     SysTables sys;
     double knorm[NAO_LMAX + 1][NAO_LMAX + 1];  // sqrt((2l+1)/(4pi) (l-m)!/(l+m)!) (x sqrt2 for m>0)
