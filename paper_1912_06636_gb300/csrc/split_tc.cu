@@ -41,10 +41,6 @@ constexpr long long kWaitCycles = 400000000LL;  // ~0.2 s at 2 GHz: bounded mbar
 using split_bits::abs_bits;
 using split_bits::row_exponent_bits;
 
-// 2^23 + u for a 23-bit unsigned u, as an exact float, minus 2^23: u as a float without a
-// conversion instruction.
-__device__ __forceinline__ float u23_to_float(uint32_t u) { return __int_as_float(0x4B000000 | (int)u) - 8388608.0f; }
-
 // S balanced base-64 digits (most significant first in dig[0]) of X = round(x 2^(6S-e)),
 // |x 2^-e| < 1/2, as exact small-integer floats. From x's bits x = +-m 2^(E-1075) (53-bit m):
 // |X| = m 2^-sh with sh = 1075 + e - 6S - E, rounded half up when sh > 0, held as a 128-bit
@@ -52,13 +48,15 @@ __device__ __forceinline__ float u23_to_float(uint32_t u) { return __int_as_floa
 // digits each), exact in FP32, and the digits are peeled off from the bottom in FP32:
 // q = rint(v / 64), d = v - 64 q in [-32, 32], v <- q, the carry q (0 or 1 after a chunk's
 // three digits) joining the next chunk. The top digit keeps whatever remains, which the bound
-// on |X| keeps in [-32, 32]. The sign is applied to every digit. Subnormal x and e = -10000
-// give zeros.
+// on |X| keeps in [-32, 32]. Subnormal x and e = -10000 give zeros.
+// |X| = round(|x| 2^(6S-e)) as a 128-bit integer (hi:lo) from the bits of x, and the sign of x.
 template <int S>
-__device__ __forceinline__ void digits(double x, int e, float (&dig)[S]) {
+__device__ __forceinline__ void digit_integer(double x, int e, unsigned long long &lo, unsigned long long &hi,
+                                              float &sgn) {
     const long long bits = __double_as_longlong(x);
     const int eb = (int)((bits >> 52) & 0x7FF);
-    unsigned long long lo = 0, hi = 0;
+    lo = 0;
+    hi = 0;
     if (eb != 0 && e > -10000) {
         const unsigned long long m = ((unsigned long long)bits & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
         const int sh = 1075 + e - 6 * S - eb;
@@ -70,23 +68,46 @@ __device__ __forceinline__ void digits(double x, int e, float (&dig)[S]) {
             hi = k > 0 ? m >> (64 - k) : 0ULL;
         }
     }
-    const float sgn = bits < 0 ? -1.0f : 1.0f;
-    float v = u23_to_float((uint32_t)(lo & 0x3FFFFULL));
+    sgn = bits < 0 ? -1.0f : 1.0f;
+}
+
+// Chunk c (c = 0, 1, 2: 18 bits; c = 3: the 23 bits from bit 54) of |X| = (hi:lo).
+__device__ __forceinline__ uint32_t digit_chunk(unsigned long long lo, unsigned long long hi, int c) {
+    return c == 0 ? (uint32_t)(lo & 0x3FFFFULL)
+         : c == 1 ? (uint32_t)((lo >> 18) & 0x3FFFFULL)
+         : c == 2 ? (uint32_t)((lo >> 36) & 0x3FFFFULL)
+                  : (uint32_t)(((lo >> 54) | (hi << 10)) & 0x7FFFFFULL);
+}
+
+// The S digits of two values x0, x1 at once (.x and .y of dig[s]) with packed FP32x2 arithmetic.
+// The sign is carried in the running value: v starts as sgn |X| mod 2^18 (sgn (2^23 + u) - sgn 2^23,
+// one packed FMA, exact), every later chunk enters as + sgn u 2^(18c) at its digit position, and
+// the peeling q = rint(v / 64), d = v - 64 q works on signed v as well: rint is odd-symmetric, so
+// the digits are those of |X| times the sign.
+template <int S>
+__device__ __forceinline__ void digits2(double x0, double x1, int e, float2 (&dig)[S]) {
+    unsigned long long lo0, hi0, lo1, hi1;
+    float s0, s1;
+    digit_integer<S>(x0, e, lo0, hi0, s0);
+    digit_integer<S>(x1, e, lo1, hi1, s1);
+    const float2 sgn = make_float2(s0, s1), nb = make_float2(-8388608.0f * s0, -8388608.0f * s1);
+    const float2 inv64 = make_float2(0.015625f, 0.015625f), big = make_float2(12582912.0f, 12582912.0f);
+    const float2 nbig = make_float2(-12582912.0f, -12582912.0f), m64 = make_float2(-64.0f, -64.0f);
+    auto chunk = [&](int c) {  // sgn u, u < 2^23, exactly
+        const float2 u = make_float2(__int_as_float(0x4B000000 | (int)digit_chunk(lo0, hi0, c)),
+                                     __int_as_float(0x4B000000 | (int)digit_chunk(lo1, hi1, c)));
+        return __ffma2_rn(sgn, u, nb);
+    };
+    float2 v = chunk(0);
 #pragma unroll
     for (int s = S - 1; s >= 0; s--) {
         const int t = S - 1 - s;  // digits already taken
-        if (t > 0 && t % 3 == 0) {
-            const int c = t / 3;  // next 18-bit chunk of |X|
-            const uint32_t u = c == 1 ? (uint32_t)((lo >> 18) & 0x3FFFFULL)
-                             : c == 2 ? (uint32_t)((lo >> 36) & 0x3FFFFULL)
-                                      : (uint32_t)(((lo >> 54) | (hi << 10)) & 0x7FFFFFULL);
-            v += u23_to_float(u);
-        }
+        if (t > 0 && t % 3 == 0) v = __fadd2_rn(v, chunk(t / 3));
         if (s == 0) {
-            dig[0] = sgn * v;
+            dig[0] = v;
         } else {
-            const float q = fmaf(v, 0.015625f, 12582912.0f) - 12582912.0f;  // rint(v / 64)
-            dig[s] = sgn * fmaf(q, -64.0f, v);
+            const float2 q = __fadd2_rn(__ffma2_rn(v, inv64, big), nbig);  // rint(v / 64)
+            dig[s] = __ffma2_rn(q, m64, v);
             v = q;
         }
     }
@@ -114,7 +135,7 @@ __device__ __forceinline__ double pow2(int E) {
 // rows out).
 // ----------------------------------------------------------------------------------------
 template <int S>
-__global__ void __launch_bounds__(256, 5) slice_h_kernel(DevSystem s, int32_t b0, const double *__restrict__ scratch,
+__global__ void __launch_bounds__(256, S <= 10 ? 5 : 4) slice_h_kernel(DevSystem s, int32_t b0, const double *__restrict__ scratch,
                                                         uint32_t terms, uint8_t *__restrict__ slices,
                                                         const int64_t *__restrict__ sl_off, int32_t *__restrict__ expo,
                                                         int32_t *__restrict__ neg16) {
@@ -185,17 +206,15 @@ __global__ void __launch_bounds__(256, 5) slice_h_kernel(DevSystem s, int32_t b0
         // two consecutive K columns per lane: a warp writes one 128-byte row segment per slice
         for (int kc = 0; kc < G.n_kc; kc++) {
             const int k0 = 64 * kc + 2 * lane;
-            float dg[2][S];
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int kk = src[k0 + h];
-                const double x = (kk >= 0 && e > -10000) ? __ldcs(row + kk) * sd[kk] : 0.0;
-                digits<S>(x, e, dg[h]);
-            }
+            const int k0a = src[k0], k0b = src[k0 + 1];
+            const double xa = (k0a >= 0 && e > -10000) ? __ldcs(row + k0a) * sd[k0a] : 0.0;
+            const double xb = (k0b >= 0 && e > -10000) ? __ldcs(row + k0b) * sd[k0b] : 0.0;
+            float2 dg[S];
+            digits2<S>(xa, xb, e, dg);
             const uint32_t off = tc::sw128_offset((uint32_t)r, (uint32_t)(2 * lane));
 #pragma unroll
             for (int sl = 0; sl < S; sl++)
-                __stcs(reinterpret_cast<unsigned int *>(base + G.h_block(sl, kc) + off), pack_bf16x2(dg[0][sl], dg[1][sl]));
+                __stcs(reinterpret_cast<unsigned int *>(base + G.h_block(sl, kc) + off), pack_bf16x2(dg[sl].x, dg[sl].y));
         }
     }
 }
@@ -270,13 +289,12 @@ __global__ void __launch_bounds__(256) slice_nphi_kernel(DevSystem s, int32_t b0
         for (int h = 0; h < 4; h++) {
             const int ql = warp * 4 + h, q = q0 + ql;
             if (q >= G.P16) break;
-            float dg[2][S];
-            digits<S>(t[ql][2 * lane], eq[h], dg[0]);
-            digits<S>(t[ql][2 * lane + 1], eq[h], dg[1]);
+            float2 dg[S];
+            digits2<S>(t[ql][2 * lane], t[ql][2 * lane + 1], eq[h], dg);
             const uint32_t off = tc::sw128_offset((uint32_t)q, (uint32_t)(2 * lane));
 #pragma unroll
             for (int sl = 0; sl < S; sl++)
-                *reinterpret_cast<uint32_t *>(base + G.nA_block(sl, kc) + off) = pack_bf16x2(dg[0][sl], dg[1][sl]);
+                *reinterpret_cast<uint32_t *>(base + G.nA_block(sl, kc) + off) = pack_bf16x2(dg[sl].x, dg[sl].y);
         }
         __syncthreads();
     }
@@ -309,7 +327,7 @@ __global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, 
         const int64_t gj = jin ? rel[j] : 0;
         const int tj = tile_of(j, TN);
         for (int kc = 0; kc < G.n_kcN; kc++) {
-            float dg[2][S];
+            double xp[2];
 #pragma unroll
             for (int hh = 0; hh < 2; hh++) {
                 const int i = 64 * kc + 2 * lane + hh;
@@ -323,12 +341,14 @@ __global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, 
                     if (!full && tile_of(i, TN) < tj && split_bits::biased_exponent(pb) != 0)
                         x = __longlong_as_double(pb + (1LL << 52));
                 }
-                digits<S>(x, e, dg[hh]);
+                xp[hh] = x;
             }
+            float2 dg[S];
+            digits2<S>(xp[0], xp[1], e, dg);
             const uint32_t off = tc::sw128_offset((uint32_t)j, (uint32_t)(2 * lane));
 #pragma unroll
             for (int sl = 0; sl < S; sl++)
-                *reinterpret_cast<uint32_t *>(base + G.nB_block(S, sl, kc) + off) = pack_bf16x2(dg[0][sl], dg[1][sl]);
+                *reinterpret_cast<uint32_t *>(base + G.nB_block(S, sl, kc) + off) = pack_bf16x2(dg[sl].x, dg[sl].y);
         }
     }
 }
