@@ -568,6 +568,9 @@ __global__ void __launch_bounds__(192, 1)
             const int32_t *rel = s.rel_idx + s.rel_off[h.b];
             const int32_t *ex = expo + s.rel_off[h.b];
             const int ei = row_ok ? ex[i] : -10000;
+            // Width 48 (S <= 10, no lo2): h_ij as one 64-bit integer, exact as hi 2^18 + lo where
+            // |hi| < 2^44, else 4 hi + round(lo / 2^16) (|4 hi| >= 2^46: relative error <= 2^-47);
+            // one conversion and one product per element. Width 32: the three parts in FP64.
             double val[TN];
 #pragma unroll
             for (int c0 = 0; c0 < TN; c0 += 16) {
@@ -577,7 +580,15 @@ __global__ void __launch_bounds__(192, 1)
                 for (int jj = 0; jj < 16; jj++) {
                     const int j = h.tj * TN + c0 + jj;
                     const int ej = (row_ok && j < h.N) ? ex[j] : -10000;
-                    val[c0 + jj] = (ei > -10000 && ej > -10000) ? recombine(v.hi[jj], v.lo[jj], v.lo2[jj], ei + ej) : 0.0;
+                    const bool live = ei > -10000 && ej > -10000;
+                    if constexpr (TN == 48) {
+                        const long long hi = v.hi[jj], lo = v.lo[jj];
+                        const bool small = hi > -(1LL << 44) && hi < (1LL << 44);
+                        const long long X = small ? (hi << 18) + lo : (hi << 2) + ((lo + (1LL << 15)) >> 16);
+                        val[c0 + jj] = live ? (double)X * pow2(ei + ej - (small ? 66 : 50)) : 0.0;
+                    } else {
+                        val[c0 + jj] = live ? recombine(v.hi[jj], v.lo[jj], v.lo2[jj], ei + ej) : 0.0;
+                    }
                 }
             }
             // tensor memory is free for the next item
