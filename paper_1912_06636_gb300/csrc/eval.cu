@@ -150,15 +150,26 @@ __device__ __noinline__ void eval_group(const DevSystem &s, const AtomGroup &ag,
     using H = double;
     const H xh = dx, yh = dy, zh = dz, qq = r2;
     // A_m + i B_m = (x + i y)^m
+    // (A_0, B_0) = (1, 0) and (A_1, B_1) = (x, y) exactly. Terms that vanish for every point
+    // (a derivative of a constant or of a polynomial without that variable, a factor B_0) are
+    // left out rather than multiplied by zero, which IEEE arithmetic would not let the compiler
+    // drop: the flags below are compile-time constants once the loops over l and m unroll.
     H A[LMAX + 1], B[LMAX + 1];
     A[0] = H(1);
     B[0] = H(0);
 #pragma unroll
     for (int m = 1; m <= LMAX; m++) {
-        A[m] = xh * A[m - 1] - yh * B[m - 1];
-        B[m] = xh * B[m - 1] + yh * A[m - 1];
+        if (m == 1) {
+            A[1] = xh;
+            B[1] = yh;
+        } else {
+            A[m] = xh * A[m - 1] - yh * B[m - 1];
+            B[m] = xh * B[m - 1] + yh * A[m - 1];
+        }
     }
-    // Pi_{l-1}^m (c) and Pi_{l-2}^m (p) with their z and r^2 derivatives
+    // Pi_{l-1}^m (c) and Pi_{l-2}^m (p) with their z and r^2 derivatives. Pi_l^m is a
+    // polynomial in z of degree l - m and in r^2 of degree floor((l - m) / 2): its z-derivative
+    // vanishes for l = m, its r^2-derivative for l - m < 2.
     H Pc[LMAX + 1], Pcz[LMAX + 1], Pcq[LMAX + 1], Pp[LMAX + 1], Ppz[LMAX + 1], Ppq[LMAX + 1];
 #pragma unroll
     for (int m = 0; m <= LMAX; m++) Pc[m] = Pcz[m] = Pcq[m] = Pp[m] = Ppz[m] = Ppq[m] = H(0);
@@ -169,44 +180,57 @@ __device__ __noinline__ void eval_group(const DevSystem &s, const AtomGroup &ag,
 #pragma unroll
     for (int l = 0; l <= LMAX; l++) {
         H S[2 * LMAX + 1], Gx[2 * LMAX + 1], Gy[2 * LMAX + 1], Gz[2 * LMAX + 1];
+        bool zx[2 * LMAX + 1], zy[2 * LMAX + 1], zz[2 * LMAX + 1];  // gradient component is 0
 #pragma unroll
         for (int m = 0; m <= l; m++) {
-            H p, pz, pq;
+            H p, pz = H(0), pq = H(0);
+            const bool zpz = (m == l), zpq = (l - m < 2);
             if (m == l) {
                 p = H(double_factorial_odd(m));
-                pz = pq = H(0);
             } else if (m == l - 1) {
                 p = H(2 * m + 1) * zh * Pc[m];
                 pz = H(2 * m + 1) * Pc[m];
-                pq = H(0);
             } else {
                 const H c1 = H((double)(2 * l - 1) / (double)(l - m));
                 const H c2 = H((double)(l + m - 1) / (double)(l - m));
                 p = c1 * zh * Pc[m] - c2 * qq * Pp[m];
-                pz = c1 * (Pc[m] + zh * Pcz[m]) - c2 * qq * Ppz[m];
-                pq = c1 * zh * Pcq[m] - c2 * (Pp[m] + qq * Ppq[m]);
+                pz = c1 * (Pc[m] + zh * Pcz[m]);
+                if (l - 2 != m) pz = pz - c2 * qq * Ppz[m];          // Pi_{l-2}^m depends on z
+                const H pq_p = (l - 2 - m >= 2) ? Pp[m] + qq * Ppq[m] : Pp[m];
+                pq = (l - 1 - m >= 2) ? c1 * zh * Pcq[m] - c2 * pq_p : -(c2 * pq_p);
             }
             Pp[m] = Pc[m]; Ppz[m] = Pcz[m]; Ppq[m] = Pcq[m];
             Pc[m] = p; Pcz[m] = pz; Pcq[m] = pq;
-            const H dPx = H(2) * xh * pq, dPy = H(2) * yh * pq, dPz = pz + H(2) * zh * pq;
+            const H dPx = zpq ? H(0) : H(2) * xh * pq, dPy = zpq ? H(0) : H(2) * yh * pq;
+            const H dPz = zpq ? pz : pz + H(2) * zh * pq;
+            const bool zdz = zpz && zpq;
             const H kn = H(s.knorm[l][m]);
             if (m == 0) {
                 S[l] = kn * p;
-                Gx[l] = kn * dPx;
-                Gy[l] = kn * dPy;
-                Gz[l] = kn * dPz;
+                Gx[l] = zpq ? H(0) : kn * dPx;
+                Gy[l] = zpq ? H(0) : kn * dPy;
+                Gz[l] = zdz ? H(0) : kn * dPz;
+                zx[l] = zy[l] = zpq;
+                zz[l] = zdz;
             } else {
                 const H fm = H(m);
+                const H pfm = p * fm;
                 S[l + m] = kn * p * A[m];
-                Gx[l + m] = kn * (dPx * A[m] + p * fm * A[m - 1]);
-                Gy[l + m] = kn * (dPy * A[m] - p * fm * B[m - 1]);
-                Gz[l + m] = kn * dPz * A[m];
+                Gx[l + m] = zpq ? kn * (pfm * A[m - 1]) : kn * (dPx * A[m] + pfm * A[m - 1]);
+                Gy[l + m] = m == 1 ? (zpq ? H(0) : kn * (dPy * A[m])) : (zpq ? kn * -(pfm * B[m - 1]) : kn * (dPy * A[m] - pfm * B[m - 1]));
+                Gz[l + m] = zdz ? H(0) : kn * dPz * A[m];
                 S[l - m] = kn * p * B[m];
-                Gx[l - m] = kn * (dPx * B[m] + p * fm * B[m - 1]);
-                Gy[l - m] = kn * (dPy * B[m] + p * fm * A[m - 1]);
-                Gz[l - m] = kn * dPz * B[m];
+                Gx[l - m] = m == 1 ? (zpq ? H(0) : kn * (dPx * B[m])) : (zpq ? kn * (pfm * B[m - 1]) : kn * (dPx * B[m] + pfm * B[m - 1]));
+                Gy[l - m] = zpq ? kn * (pfm * A[m - 1]) : kn * (dPy * B[m] + pfm * A[m - 1]);
+                Gz[l - m] = zdz ? H(0) : kn * dPz * B[m];
+                zx[l + m] = false;
+                zy[l + m] = (m == 1 && zpq);
+                zz[l + m] = zz[l - m] = zdz;
+                zx[l - m] = (m == 1 && zpq);
+                zy[l - m] = false;
             }
         }
+        const T ulu = ul * u;  // u^(l+1)
         // the atom's radial functions of this l
         for (; ri < re; ri++) {
             const RfnEntry e = s.rfn[ri];
@@ -235,14 +259,16 @@ __device__ __noinline__ void eval_group(const DevSystem &s, const AtomGroup &ag,
                     }
                 }
                 const T g = R * ul;
-                const T gpu = (dRds * dr_scale - T(l) * R * u) * ul * u;  // g'(r) / r
+                // g'(r) / r = (dR/dr - l R / r) u^l / r
+                const T gpu = (l == 0 ? dRds * dr_scale : dRds * dr_scale - T(l) * R * u) * ulu;
+                const T gx = gpu * x, gy = gpu * y, gz = gpu * z;
 #pragma unroll
                 for (int m = 0; m < 2 * l + 1; m++) {
                     const T Sm = T(S[m]);
                     fo[m] = OutT(g * Sm);
-                    xo[m] = OutT(gpu * x * Sm + g * T(Gx[m]));
-                    yo[m] = OutT(gpu * y * Sm + g * T(Gy[m]));
-                    zo[m] = OutT(gpu * z * Sm + g * T(Gz[m]));
+                    xo[m] = OutT(zx[m] ? gx * Sm : gx * Sm + g * T(Gx[m]));
+                    yo[m] = OutT(zy[m] ? gy * Sm : gy * Sm + g * T(Gy[m]));
+                    zo[m] = OutT(zz[m] ? gz * Sm : gz * Sm + g * T(Gz[m]));
                 }
             } else {
 #pragma unroll
