@@ -109,7 +109,8 @@ __device__ __forceinline__ void store_rows(const EvalOut<OutT> &o, int pos, int 
 // radial functions, which are visited in increasing l.
 template <int LMAX, typename T, bool GRAD, typename OutT, int EXPO>
 __device__ __noinline__ void eval_group(const DevSystem &s, const AtomGroup &ag, double dx, double dy, double dz,
-                                           double r2, double r, const EvalOut<OutT> &o, int q, ExpoIn xi) {
+                                           double r2, double r, double ur, const EvalOut<OutT> &o, int q,
+                                           ExpoIn xi) {
     // radial coordinate: segment k and t in [0, 1)
     const double rr = fmax(r, s.r0);
     int k;
@@ -140,7 +141,6 @@ __device__ __noinline__ void eval_group(const DevSystem &s, const AtomGroup &ag,
         xk = fma(rr, __ldg(s.inv_rk + k), -1.0);
         t = log1pf((float)xk) * (float)s.inv_delta;
     }
-    const double ur = 1.0 / r;
     const T dr_scale = T(s.inv_delta * (r < s.r0 ? __ldg(s.inv_rk) : ur));  // dR/dr = dR/ds * inv_delta / rr
     const T u = T(ur);
     const T x = T(dx), y = T(dy), z = T(dz);
@@ -241,8 +241,10 @@ __device__ __noinline__ void eval_group(const DevSystem &s, const AtomGroup &ag,
                 if constexpr (std::is_same<T, double>::value) {
                     const double2 *c = reinterpret_cast<const double2 *>(s.coef + ((size_t)e.fn * (s.n_rgrid - 1) + k) * 4);
                     const double2 c01 = __ldg(c), c23 = __ldg(c + 1);
-                    R = fma(fma(fma(c23.y, t, c23.x), t, c01.y), t, c01.x);
-                    dRds = fma(fma(3.0 * c23.y, t, 2.0 * c23.x), t, c01.y);
+                    // R = c0 + t (c1 + t a), dR/dt = c1 + t (2 a + c3 t), a = c2 + c3 t
+                    const double a = fma(c23.y, t, c23.x);
+                    R = fma(fma(a, t, c01.y), t, c01.x);
+                    dRds = fma(fma(c23.y, t, a + a), t, c01.y);
                 } else {
                     const size_t seg = (size_t)e.fn * (s.n_rgrid - 1) + k;
                     if (__ldg(s.seg64 + seg)) {
@@ -290,14 +292,14 @@ __device__ __noinline__ void eval_group(const DevSystem &s, const AtomGroup &ag,
 
 template <int LMAX, bool GRAD, typename T, int EXPO, typename OutT>
 __device__ __forceinline__ void eval_group_dispatch(const DevSystem &s, const AtomGroup &ag, double dx, double dy,
-                                                    double dz, double r2, double r, const EvalOut<OutT> &o, int q,
+                                                    double dz, double r2, double r, double ur, const EvalOut<OutT> &o, int q,
                                                     const ExpoIn &xi) {
     if constexpr (EXPO != 0 || std::is_same<T, double>::value)
-        eval_group<LMAX, double, GRAD, OutT, EXPO>(s, ag, dx, dy, dz, r2, r, o, q, xi);
+        eval_group<LMAX, double, GRAD, OutT, EXPO>(s, ag, dx, dy, dz, r2, r, ur, o, q, xi);
     else if (r < kNearNucleus)
-        eval_group<LMAX, double, GRAD, OutT, 0>(s, ag, dx, dy, dz, r2, r, o, q, xi);
+        eval_group<LMAX, double, GRAD, OutT, 0>(s, ag, dx, dy, dz, r2, r, ur, o, q, xi);
     else
-        eval_group<LMAX, float, GRAD, OutT, 0>(s, ag, dx, dy, dz, r2, r, o, q, xi);
+        eval_group<LMAX, float, GRAD, OutT, 0>(s, ag, dx, dy, dz, r2, r, ur, o, q, xi);
 }
 
 template <bool GRAD, typename T, int EXPO, typename OutT>
@@ -325,15 +327,18 @@ __device__ __forceinline__ void eval_batch(const DevSystem &s, int b, const Eval
         const double dy = __dsub_rn(s.py[p], s.atom_xyz[3 * ag.atom + 1]);
         const double dz = __dsub_rn(s.pz[p], s.atom_xyz[3 * ag.atom + 2]);
         const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-        const double r = __dsqrt_rn(r2);
+        // 1/r from the library's reciprocal square root (about one ulp) and r = r^2 (1/r): one
+        // FP64 function instead of a square root and a division
+        const double ur = rsqrt(r2);
+        const double r = r2 > 0.0 ? r2 * ur : 0.0;
         switch (ag.lmax) {
-            case 0: eval_group_dispatch<0, GRAD, T, EXPO>(s, ag, dx, dy, dz, r2, r, o, q, xi); break;
-            case 1: eval_group_dispatch<1, GRAD, T, EXPO>(s, ag, dx, dy, dz, r2, r, o, q, xi); break;
-            case 2: eval_group_dispatch<2, GRAD, T, EXPO>(s, ag, dx, dy, dz, r2, r, o, q, xi); break;
-            case 3: eval_group_dispatch<3, GRAD, T, EXPO>(s, ag, dx, dy, dz, r2, r, o, q, xi); break;
-            case 4: eval_group_dispatch<4, GRAD, T, EXPO>(s, ag, dx, dy, dz, r2, r, o, q, xi); break;
-            case 5: eval_group_dispatch<5, GRAD, T, EXPO>(s, ag, dx, dy, dz, r2, r, o, q, xi); break;
-            default: eval_group_dispatch<6, GRAD, T, EXPO>(s, ag, dx, dy, dz, r2, r, o, q, xi); break;
+            case 0: eval_group_dispatch<0, GRAD, T, EXPO>(s, ag, dx, dy, dz, r2, r, ur, o, q, xi); break;
+            case 1: eval_group_dispatch<1, GRAD, T, EXPO>(s, ag, dx, dy, dz, r2, r, ur, o, q, xi); break;
+            case 2: eval_group_dispatch<2, GRAD, T, EXPO>(s, ag, dx, dy, dz, r2, r, ur, o, q, xi); break;
+            case 3: eval_group_dispatch<3, GRAD, T, EXPO>(s, ag, dx, dy, dz, r2, r, ur, o, q, xi); break;
+            case 4: eval_group_dispatch<4, GRAD, T, EXPO>(s, ag, dx, dy, dz, r2, r, ur, o, q, xi); break;
+            case 5: eval_group_dispatch<5, GRAD, T, EXPO>(s, ag, dx, dy, dz, r2, r, ur, o, q, xi); break;
+            default: eval_group_dispatch<6, GRAD, T, EXPO>(s, ag, dx, dy, dz, r2, r, ur, o, q, xi); break;
         }
     }
 }
