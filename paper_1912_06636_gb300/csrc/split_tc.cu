@@ -495,7 +495,20 @@ __global__ void __launch_bounds__(192, 1)
             int gk = 0;
             for (int w = blockIdx.x; w < n_work && !*abort; w += gridDim.x) {
                 const HItem h = h_item<TN>(s, work, w0 + w, slices, sl_off, neg16, S);
+                const bool more = w + (int)gridDim.x < n_work;
+                HItem hn = h;
+                if (more) hn = h_item<TN>(s, work, w0 + w + gridDim.x, slices, sl_off, neg16, S);
                 for (int kc = 0; kc < h.n_kc; kc++, gk++) {
+                    // the next K chunk's slices (or the next item's first) towards L2, so that the
+                    // ring's copies come from L2
+                    if (kc + 1 < h.n_kc || more) {
+                        const HItem &hp = kc + 1 < h.n_kc ? h : hn;
+                        const int kp = kc + 1 < h.n_kc ? kc + 1 : 0;
+                        for (int t = 0; t < S; t++) {
+                            tc::bulk_prefetch_l2(hp.b0 + ((size_t)t * hp.n_kc + kp) * hp.blk, hp.b_bytes);
+                            tc::bulk_prefetch_l2(hp.a0 + ((size_t)t * hp.n_kc + kp) * hp.blk, hp.a_bytes);
+                        }
+                    }
                     const int bb = gk & 1, ub = gk >> 1;
                     if (ub >= 1 && !tc::mbar_wait(&pp.emptyB[bb], (ub - 1) & 1, kWaitCycles)) { *abort = 1; break; }
                     tc::mbar_arrive_expect_tx(&pp.fullB[bb], (uint32_t)S * h.b_bytes);
@@ -570,24 +583,26 @@ __global__ void __launch_bounds__(192, 1)
             const int ei = row_ok ? ex[i] : -10000;
             // Width 48 (S <= 10, no lo2): h_ij as one 64-bit integer, exact as hi 2^18 + lo where
             // |hi| < 2^44, else 4 hi + round(lo / 2^16) (|4 hi| >= 2^46: relative error <= 2^-47);
-            // one conversion and one product per element. Width 32: the three parts in FP64.
-            double val[TN];
+            // the integers are formed before tensor memory is handed back, the conversion and the
+            // product by 2^(e_i + e_j - 66 or - 50) after. Width 32: the three parts in FP64.
+            using Val = typename std::conditional<TN == 48, long long, double>::type;
+            Val val[TN];
+            uint64_t small_mask = 0;
 #pragma unroll
             for (int c0 = 0; c0 < TN; c0 += 16) {
                 Parts16 v;
                 combine16<TN>(tm_row, c0, S, v);
 #pragma unroll
                 for (int jj = 0; jj < 16; jj++) {
-                    const int j = h.tj * TN + c0 + jj;
-                    const int ej = (row_ok && j < h.N) ? ex[j] : -10000;
-                    const bool live = ei > -10000 && ej > -10000;
                     if constexpr (TN == 48) {
                         const long long hi = v.hi[jj], lo = v.lo[jj];
                         const bool small = hi > -(1LL << 44) && hi < (1LL << 44);
-                        const long long X = small ? (hi << 18) + lo : (hi << 2) + ((lo + (1LL << 15)) >> 16);
-                        val[c0 + jj] = live ? (double)X * pow2(ei + ej - (small ? 66 : 50)) : 0.0;
+                        val[c0 + jj] = small ? (hi << 18) + lo : (hi << 2) + ((lo + (1LL << 15)) >> 16);
+                        small_mask |= (uint64_t)small << (c0 + jj);
                     } else {
-                        val[c0 + jj] = live ? recombine(v.hi[jj], v.lo[jj], v.lo2[jj], ei + ej) : 0.0;
+                        const int j = h.tj * TN + c0 + jj;
+                        const int ej = (row_ok && j < h.N) ? ex[j] : -10000;
+                        val[c0 + jj] = (ei > -10000 && ej > -10000) ? recombine(v.hi[jj], v.lo[jj], v.lo2[jj], ei + ej) : 0.0;
                     }
                 }
             }
@@ -600,7 +615,18 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
                 for (int jj = 0; jj < TN; jj++) {
                     const int j = h.tj * TN + jj;
-                    if (j < h.N && j >= i) atomicAdd(h_elem(s, h.m, gi, rel[j]), val[jj]);
+                    if (j < h.N && j >= i) {
+                        double x;
+                        if constexpr (TN == 48) {
+                            const int ej = ex[j];
+                            x = (ei > -10000 && ej > -10000)
+                                    ? (double)val[jj] * pow2(ei + ej - (((small_mask >> jj) & 1) ? 66 : 50))
+                                    : 0.0;
+                        } else {
+                            x = val[jj];
+                        }
+                        atomicAdd(h_elem(s, h.m, gi, rel[j]), x);
+                    }
                 }
             }
         }
@@ -711,6 +737,19 @@ __global__ void __launch_bounds__(192, 1)
                     const uint8_t *bJ = h.b0 + (size_t)J * TN * 128;
                     const uint32_t b_bytes = (uint32_t)min(TN, h.R16 - J * TN) * 128u;
                     for (int kc = 0; kc < nk; kc++, gk++) {
+                        // the next K chunk of this tile (or the next tile's first) towards L2
+                        {
+                            const bool same = kc + 1 < nk;
+                            const int Jp = same ? J : J + 1, kp = same ? kc + 1 : 0;
+                            if (Jp < h.nJ) {
+                                const uint8_t *bp = h.b0 + (size_t)Jp * TN * 128;
+                                const uint32_t bpb = (uint32_t)min(TN, h.R16 - Jp * TN) * 128u;
+                                for (int t = 0; t < S; t++) {
+                                    tc::bulk_prefetch_l2(bp + t * h.b_s + kp * h.b_kc, bpb);
+                                    tc::bulk_prefetch_l2(h.a0 + t * h.a_s + kp * h.a_kc, h.a_bytes);
+                                }
+                            }
+                        }
                         const int bb = gk & 1, ub = gk >> 1;
                         if (ub >= 1 && !tc::mbar_wait(&pp.emptyB[bb], (ub - 1) & 1, kWaitCycles)) { *abort = 1; break; }
                         tc::mbar_arrive_expect_tx(&pp.fullB[bb], (uint32_t)S * b_bytes);

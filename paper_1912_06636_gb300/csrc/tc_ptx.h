@@ -49,6 +49,11 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  : "memory");
 }
 
+// Prefetch of a global range into L2 (no shared memory, no completion): both 16-byte aligned.
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // ---- tensor memory -------------------------------------------------------------------------
 // Whole-warp operations. ncols is a power of two >= 32; the base address is written to smem.
 __device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
