@@ -149,6 +149,7 @@ __device__ __noinline__ void eval_group(const DevSystem &s, const AtomGroup &ag,
     // FP32 (with FP32-rounded x, y, z) loses several ulps; the FP32 path rounds the results once.
     using H = double;
     const H xh = dx, yh = dy, zh = dz, qq = r2;
+    const H x2 = xh + xh, y2 = yh + yh, z2 = zh + zh;
     // A_m + i B_m = (x + i y)^m
     // (A_0, B_0) = (1, 0) and (A_1, B_1) = (x, y) exactly. Terms that vanish for every point
     // (a derivative of a constant or of a polynomial without that variable, a factor B_0) are
@@ -201,28 +202,30 @@ __device__ __noinline__ void eval_group(const DevSystem &s, const AtomGroup &ag,
             }
             Pp[m] = Pc[m]; Ppz[m] = Pcz[m]; Ppq[m] = Pcq[m];
             Pc[m] = p; Pcz[m] = pz; Pcq[m] = pq;
-            const H dPx = zpq ? H(0) : H(2) * xh * pq, dPy = zpq ? H(0) : H(2) * yh * pq;
-            const H dPz = zpq ? pz : pz + H(2) * zh * pq;
-            const bool zdz = zpz && zpq;
+            // K_lm folded into p and its derivatives once: kp = K p, kd = K grad(Pi)
             const H kn = H(s.knorm[l][m]);
+            const H kp = kn * p;
+            const H kpq = zpq ? H(0) : kn * pq;
+            const H kdx = zpq ? H(0) : x2 * kpq, kdy = zpq ? H(0) : y2 * kpq;
+            const H kdz = zpz ? (zpq ? H(0) : z2 * kpq) : (zpq ? kn * pz : fma(z2, kpq, kn * pz));
+            const bool zdz = zpz && zpq;
             if (m == 0) {
-                S[l] = kn * p;
-                Gx[l] = zpq ? H(0) : kn * dPx;
-                Gy[l] = zpq ? H(0) : kn * dPy;
-                Gz[l] = zdz ? H(0) : kn * dPz;
+                S[l] = kp;
+                Gx[l] = kdx;
+                Gy[l] = kdy;
+                Gz[l] = kdz;
                 zx[l] = zy[l] = zpq;
                 zz[l] = zdz;
             } else {
-                const H fm = H(m);
-                const H pfm = p * fm;
-                S[l + m] = kn * p * A[m];
-                Gx[l + m] = zpq ? kn * (pfm * A[m - 1]) : kn * (dPx * A[m] + pfm * A[m - 1]);
-                Gy[l + m] = m == 1 ? (zpq ? H(0) : kn * (dPy * A[m])) : (zpq ? kn * -(pfm * B[m - 1]) : kn * (dPy * A[m] - pfm * B[m - 1]));
-                Gz[l + m] = zdz ? H(0) : kn * dPz * A[m];
-                S[l - m] = kn * p * B[m];
-                Gx[l - m] = m == 1 ? (zpq ? H(0) : kn * (dPx * B[m])) : (zpq ? kn * (pfm * B[m - 1]) : kn * (dPx * B[m] + pfm * B[m - 1]));
-                Gy[l - m] = zpq ? kn * (pfm * A[m - 1]) : kn * (dPy * B[m] + pfm * A[m - 1]);
-                Gz[l - m] = zdz ? H(0) : kn * dPz * B[m];
+                const H kpf = kp * H(m);
+                S[l + m] = kp * A[m];
+                Gx[l + m] = zpq ? kpf * A[m - 1] : fma(kdx, A[m], kpf * A[m - 1]);
+                Gy[l + m] = m == 1 ? (zpq ? H(0) : kdy * A[m]) : (zpq ? -(kpf * B[m - 1]) : fma(kdy, A[m], -(kpf * B[m - 1])));
+                Gz[l + m] = zdz ? H(0) : kdz * A[m];
+                S[l - m] = kp * B[m];
+                Gx[l - m] = m == 1 ? (zpq ? H(0) : kdx * B[m]) : (zpq ? kpf * B[m - 1] : fma(kdx, B[m], kpf * B[m - 1]));
+                Gy[l - m] = zpq ? kpf * A[m - 1] : fma(kdy, B[m], kpf * A[m - 1]);
+                Gz[l - m] = zdz ? H(0) : kdz * B[m];
                 zx[l + m] = false;
                 zy[l + m] = (m == 1 && zpq);
                 zz[l + m] = zz[l - m] = zdz;
@@ -230,7 +233,9 @@ __device__ __noinline__ void eval_group(const DevSystem &s, const AtomGroup &ag,
                 zy[l - m] = false;
             }
         }
-        const T ulu = ul * u;  // u^(l+1)
+        const T ulu = ul * u;                      // u^(l+1)
+        const T a_dr = dr_scale * ulu;              // dR/ds -> g'(r)/r
+        const T a_r = T(l) * u * ulu;               // R -> the l R / r part of g'(r)/r
         // the atom's radial functions of this l
         for (; ri < re; ri++) {
             const RfnEntry e = s.rfn[ri];
@@ -262,7 +267,7 @@ __device__ __noinline__ void eval_group(const DevSystem &s, const AtomGroup &ag,
                 }
                 const T g = R * ul;
                 // g'(r) / r = (dR/dr - l R / r) u^l / r
-                const T gpu = (l == 0 ? dRds * dr_scale : dRds * dr_scale - T(l) * R * u) * ulu;
+                const T gpu = l == 0 ? dRds * a_dr : fma(dRds, a_dr, -(R * a_r));
                 const T gx = gpu * x, gy = gpu * y, gz = gpu * z;
 #pragma unroll
                 for (int m = 0; m < 2 * l + 1; m++) {
