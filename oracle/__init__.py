@@ -76,6 +76,14 @@ def _load():
         lib.or_density.restype = C.c_int
         lib.or_density_gradient.argtypes = [P, I64, P, P, P, P, P]
         lib.or_density_gradient.restype = C.c_int
+        lib.or_radial2.argtypes = [P, I32, D, P, P, P]
+        lib.or_radial2.restype = None
+        lib.or_solid.argtypes = [I32, D, D, D, P, P, P]
+        lib.or_solid.restype = C.c_int
+        lib.or_eval_dense2.argtypes = [P, I64, P, P, P, P]
+        lib.or_eval_dense2.restype = C.c_int
+        lib.or_density_hessian.argtypes = [P, I64, P, P, P, P]
+        lib.or_density_hessian.restype = C.c_int
         lib.or_bruteforce.argtypes = [P, I64, P, P, P, P, P, P, P]
         lib.or_bruteforce.restype = C.c_int
         lib.or_partition.argtypes = [I64, P, I64, P, P]
@@ -148,6 +156,25 @@ class Oracle:
         self.lib.or_radial(self.sp, int(f), float(r), C.byref(R), C.byref(dR))
         return R.value, dR.value
 
+    def radial2(self, f: int, r: float):
+        """R_f(r), dR/dr, d^2R/dr^2."""
+        R, dR, d2R = C.c_double(), C.c_double(), C.c_double()
+        self.lib.or_radial2(self.sp, int(f), float(r), C.byref(R), C.byref(dR), C.byref(d2R))
+        return R.value, dR.value, d2R.value
+
+    @staticmethod
+    def solid(l: int, x: float, y: float, z: float):
+        """Real solid harmonics S_lm = r^l Y_lm (m = -l..l) from their monomial expansion, with
+        gradients [2l+1, 3] and Hessians [2l+1, 6] (xx, xy, xz, yy, yz, zz)."""
+        lib = _load()
+        S = np.zeros(2 * l + 1)
+        G = np.zeros((2 * l + 1, 3))
+        Hs = np.zeros((2 * l + 1, 6))
+        st = lib.or_solid(int(l), float(x), float(y), float(z), S.ctypes.data, G.ctypes.data, Hs.ctypes.data)
+        if st != 0:
+            raise OracleError(f"solid: status {st}")
+        return S, G, Hs
+
     @staticmethod
     def ylm(l: int, x: float, y: float, z: float) -> np.ndarray:
         lib = _load()
@@ -164,6 +191,16 @@ class Oracle:
         grad = np.zeros((n, self.nb, 3))
         _check(self.lib.or_eval_dense(self.sp, n, _ptr(pts), _ptr(phi), _ptr(grad), C.byref(self.pole_count)), "eval")
         return phi, grad
+
+    def eval_dense2(self, pts: np.ndarray):
+        """phi [n, nb], grad [n, nb, 3] and Hessian [n, nb, 6] through the Cartesian form."""
+        pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+        n = pts.shape[0]
+        phi = np.zeros((n, self.nb))
+        grad = np.zeros((n, self.nb, 3))
+        hess = np.zeros((n, self.nb, 6))
+        _check(self.lib.or_eval_dense2(self.sp, n, _ptr(pts), _ptr(phi), _ptr(grad), _ptr(hess)), "eval2")
+        return phi, grad, hess
 
     # -- integrals ------------------------------------------------------------------------
     def hamiltonian(self, pts, w, v=None, terms=TERM_POTENTIAL | TERM_KINETIC):
@@ -216,6 +253,18 @@ class Oracle:
                                           C.byref(self.pole_count))
         _check(st, "density_gradient")
         return g, Dg
+
+    def density_hessian(self, pts, P):
+        """The density Hessian at each point ([n, 6]: xx, xy, xz, yy, yz, zz) and the magnitude sums
+        of its four terms ([n, 6])."""
+        pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+        P = np.ascontiguousarray(P, dtype=np.float64)
+        assert P.shape == (self.nb, self.nb)
+        h = np.zeros((pts.shape[0], 6))
+        Dh = np.zeros((pts.shape[0], 6))
+        _check(self.lib.or_density_hessian(self.sp, pts.shape[0], _ptr(pts), _ptr(P), _ptr(h), _ptr(Dh)),
+               "density_hessian")
+        return h, Dh
 
     def bruteforce(self, pts, w, v, P):
         pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)

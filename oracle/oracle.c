@@ -17,6 +17,12 @@
  *     summed point by point over the basis functions that are non-zero at p;
  *   - the density as the plain definition (Eq. Density): n_p = sum_ij phi_i P_ij phi_j;
  *   - the electron count N_e = sum_p w_p n_p;
+ *   - the density gradient and Hessian (Sec. 2: the derivatives of Eq. Density needed by GGA
+ *     functionals and by forces and stresses), the Hessian from second derivatives of the basis
+ *     functions written in Cartesian form, phi = g(r) S_lm(x, y, z) with g = R / r^l and the real
+ *     solid harmonic S_lm = r^l Y_lm expanded into monomials by the closed formula of Helgaker,
+ *     Jorgensen, Olsen, "Molecular Electronic-Structure Theory" (2000), Eq. 6.4.48 (Racah
+ *     normalisation there, times sqrt((2l+1)/(4 pi)) here);
  *   - the batch partition (Sec. 3.3.1, grid-adapted cut planes) and the per-batch reduced
  *     basis sets nnz(B) (Sec. 3.3.2), both under the integer rules stated at each function.
  * Cross-point sums use Neumaier's compensated summation (Neumaier 1974).
@@ -119,6 +125,27 @@ void or_radial(const or_sys *S, int32_t f, double r, double *R, double *dR) {
     *dR = dv / (rr * delta);
 }
 
+/* R_f(r) with dR_f/dr and d^2R_f/dr^2 (same conventions as or_radial). With s = ln(r/r0)/Delta,
+ * ds/dr = 1/(r Delta) and d^2s/dr^2 = -1/(r^2 Delta), so R'' = v_ss / (r Delta)^2 - v_s / (r^2 Delta);
+ * the spline's second derivative in s is the linear interpolation of M between the knots.     */
+void or_radial2(const or_sys *S, int32_t f, double r, double *R, double *dR, double *d2R) {
+    if (r >= S->fn_cutoff[f]) { *R = 0.0; *dR = 0.0; *d2R = 0.0; return; }
+    double delta = log(S->r_last / S->r0) / (double)(S->n_rgrid - 1);
+    double rr = r < S->r0 ? S->r0 : r;
+    double s = log(rr / S->r0) / delta;
+    const double *y = S->fn_table + (size_t)f * S->n_rgrid, *M = S->spline_M + (size_t)f * S->n_rgrid;
+    double v, dv;
+    spline_eval(y, M, S->n_rgrid, s, &v, &dv);
+    int32_t k = (int32_t)floor(s);
+    if (k < 0) k = 0;
+    if (k > S->n_rgrid - 2) k = S->n_rgrid - 2;
+    double t = s - (double)k;
+    double vss = (1.0 - t) * M[k] + t * M[k + 1];
+    *R = v;
+    *dR = dv / (rr * delta);
+    *d2R = vss / ((rr * delta) * (rr * delta)) - dv / (rr * rr * delta);
+}
+
 /* ------------------------------------------------------------------------------------ */
 /* real spherical harmonics through spherical coordinates                               */
 /* ------------------------------------------------------------------------------------ */
@@ -177,6 +204,87 @@ int or_ylm(int32_t l, double x, double y, double z, double *Y) {
     if (r == 0.0) return -2;
     double dt[2 * OR_LMAX + 1], dp[2 * OR_LMAX + 1];
     ylm_sph(l, acos(z / r), atan2(y, x), Y, dt, dp);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* real solid harmonics as polynomials (for second derivatives)                          */
+/* ------------------------------------------------------------------------------------ */
+static double binom(int n, int k) { return (k < 0 || k > n) ? 0.0 : factorial(n) / (factorial(k) * factorial(n - k)); }
+
+typedef struct {
+    int n;
+    double c[64];
+    int e[64][3];  /* exponents of x, y, z */
+} or_poly;
+
+/* S_lm(x, y, z) = r^l Y_lm as a sum of monomials (Helgaker et al. Eq. 6.4.48):
+ *   S = sqrt((2l+1)/(4 pi)) N_lm sum_t sum_u sum_v C_tuv x^(2t+|m|-2(u+v)) y^(2(u+v)) z^(l-2t-|m|),
+ *   C_tuv = (-1)^(t+v-v_m) 4^-t binom(l,t) binom(l-t,|m|+t) binom(t,u) binom(|m|,2v),
+ *   N_lm = sqrt(2 (l+|m|)! (l-|m|)! / 2^delta_m0) / (2^|m| l!),
+ * t = 0..floor((l-|m|)/2), u = 0..t, 2v = 0, 2, .. <= |m| (m >= 0, v_m = 0) or 1, 3, .. <= |m|
+ * (m < 0, v_m = 1/2). Index w = 2v below.                                                    */
+static void solid_poly(int l, int m, or_poly *P) {
+    int am = m < 0 ? -m : m;
+    double N = sqrt(2.0 * factorial(l + am) * factorial(l - am) / (m == 0 ? 2.0 : 1.0)) / (pow(2.0, am) * factorial(l));
+    double norm = sqrt((2.0 * l + 1.0) / (4.0 * M_PI)) * N;
+    P->n = 0;
+    for (int t = 0; t <= (l - am) / 2; t++)
+        for (int u = 0; u <= t; u++)
+            for (int w = (m < 0 ? 1 : 0); w <= am; w += 2) {
+                int sgn_exp = t + (m < 0 ? (w - 1) / 2 : w / 2);
+                double C = ((sgn_exp & 1) ? -1.0 : 1.0) * pow(0.25, t) * binom(l, t) * binom(l - t, am + t) * binom(t, u) *
+                           binom(am, w);
+                P->c[P->n] = norm * C;
+                P->e[P->n][0] = 2 * t + am - 2 * u - w;
+                P->e[P->n][1] = 2 * u + w;
+                P->e[P->n][2] = l - 2 * t - am;
+                P->n++;
+            }
+}
+
+static double ipow(double x, int k) { double r = 1.0; for (int i = 0; i < k; i++) r *= x; return r; }
+
+/* value, gradient [3] and Hessian [6] (xx, xy, xz, yy, yz, zz) of a polynomial at (x, y, z) */
+static void poly_eval2(const or_poly *P, const double q[3], double *v, double g[3], double h[6]) {
+    *v = 0.0;
+    for (int c = 0; c < 3; c++) g[c] = 0.0;
+    for (int c = 0; c < 6; c++) h[c] = 0.0;
+    static const int hp[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    for (int i = 0; i < P->n; i++) {
+        const int *e = P->e[i];
+        double f[3], d1[3], d2[3];
+        for (int c = 0; c < 3; c++) {
+            f[c] = ipow(q[c], e[c]);
+            d1[c] = e[c] >= 1 ? (double)e[c] * ipow(q[c], e[c] - 1) : 0.0;
+            d2[c] = e[c] >= 2 ? (double)(e[c] * (e[c] - 1)) * ipow(q[c], e[c] - 2) : 0.0;
+        }
+        *v += P->c[i] * f[0] * f[1] * f[2];
+        g[0] += P->c[i] * d1[0] * f[1] * f[2];
+        g[1] += P->c[i] * f[0] * d1[1] * f[2];
+        g[2] += P->c[i] * f[0] * f[1] * d1[2];
+        for (int k = 0; k < 6; k++) {
+            int a = hp[k][0], b = hp[k][1];
+            double prod = P->c[i];
+            for (int c = 0; c < 3; c++) {
+                int order = (c == a) + (c == b);
+                prod *= order == 0 ? f[c] : order == 1 ? d1[c] : d2[c];
+            }
+            h[k] += prod;
+        }
+    }
+}
+
+/* Public helper for the tests: S_lm (m=-l..l) with gradients [2l+1][3] and Hessians [2l+1][6]
+ * at (x, y, z). */
+int or_solid(int32_t l, double x, double y, double z, double *S, double *G, double *Hs) {
+    if (l < 0 || l > OR_LMAX) return -1;
+    double q[3] = {x, y, z};
+    for (int m = -l; m <= l; m++) {
+        or_poly P;
+        solid_poly(l, m, &P);
+        poly_eval2(&P, q, S + (l + m), G + 3 * (l + m), Hs + 6 * (l + m));
+    }
     return 0;
 }
 
@@ -449,6 +557,122 @@ int or_density_gradient(const or_sys *S, int64_t n_pts, const double *pts, const
         }
     }
     free(idx); free(phi); free(grad);
+    return status;
+}
+
+/* All basis functions non-zero at p with phi, gradient [3] and Hessian [6] (xx, xy, xz, yy, yz,
+ * zz), in ascending basis order, in Cartesian form: with x = p - R_A, r = |x|, phi = g S_lm,
+ * g = R / r^l,
+ *   d_a phi     = g' (x_a / r) S + g d_a S,
+ *   d_a d_b phi = g'' (x_a x_b / r^2) S + g' (delta_ab / r - x_a x_b / r^3) S
+ *                 + (g' / r)(x_b d_a S + x_a d_b S) + g d_a d_b S,
+ *   g' = R' / r^l - l R / r^(l+1),  g'' = R'' / r^l - 2 l R' / r^(l+1) + l (l+1) R / r^(l+2).
+ * When all is set, every basis function is listed (zeros beyond the cutoff). Returns the count,
+ * or -2 for a point on a nucleus.                                                              */
+static int64_t point_basis2(const or_sys *S, const double p[3], int64_t *idx, double *phi, double *grad,
+                            double *hess, int all) {
+    static const int hp[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    int64_t cnt = 0, base = 0;
+    for (int32_t a = 0; a < S->n_atoms; a++) {
+        int32_t sp = S->atom_species[a];
+        double x[3] = {p[0] - S->atom_xyz[3 * a + 0], p[1] - S->atom_xyz[3 * a + 1], p[2] - S->atom_xyz[3 * a + 2]};
+        double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        for (int32_t f = S->species_fn_offset[sp]; f < S->species_fn_offset[sp + 1]; f++) {
+            int l = S->fn_l[f];
+            int nm = 2 * l + 1;
+            if (!(r < S->fn_cutoff[f])) {
+                if (all)
+                    for (int m = 0; m < nm; m++) {
+                        idx[cnt] = base + m; phi[cnt] = 0.0;
+                        for (int c = 0; c < 3; c++) grad[3 * cnt + c] = 0.0;
+                        for (int c = 0; c < 6; c++) hess[6 * cnt + c] = 0.0;
+                        cnt++;
+                    }
+                base += nm;
+                continue;
+            }
+            if (r == 0.0) return -2;
+            double R, dR, d2R;
+            or_radial2(S, f, r, &R, &dR, &d2R);
+            double rl = ipow(r, l);
+            double g = R / rl;
+            double g1 = dR / rl - (double)l * R / (rl * r);
+            double g2 = d2R / rl - 2.0 * (double)l * dR / (rl * r) + (double)(l * (l + 1)) * R / (rl * r * r);
+            for (int m = -l; m <= l; m++) {
+                or_poly P;
+                solid_poly(l, m, &P);
+                double Sv, Sg[3], Sh[6];
+                poly_eval2(&P, x, &Sv, Sg, Sh);
+                idx[cnt] = base + (m + l);
+                phi[cnt] = g * Sv;
+                for (int c = 0; c < 3; c++) grad[3 * cnt + c] = g1 * (x[c] / r) * Sv + g * Sg[c];
+                for (int k = 0; k < 6; k++) {
+                    int ia = hp[k][0], ib = hp[k][1];
+                    double dab = ia == ib ? 1.0 : 0.0;
+                    hess[6 * cnt + k] = g2 * (x[ia] * x[ib] / (r * r)) * Sv + g1 * (dab / r - x[ia] * x[ib] / (r * r * r)) * Sv +
+                                        (g1 / r) * (x[ib] * Sg[ia] + x[ia] * Sg[ib]) + g * Sh[k];
+                }
+                cnt++;
+            }
+            base += nm;
+        }
+    }
+    return cnt;
+}
+
+/* Dense phi [n_pts][nb], grad [n_pts][nb][3] and Hessian [n_pts][nb][6] through the Cartesian
+ * form (point_basis2). */
+int or_eval_dense2(const or_sys *S, int64_t n_pts, const double *pts, double *phi, double *grad, double *hess) {
+    int64_t nb = or_n_basis(S);
+    int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nb > 0 ? nb : 1));
+    if (!idx) return -1;
+    for (int64_t p = 0; p < n_pts; p++) {
+        int64_t c = point_basis2(S, pts + 3 * p, idx, phi + p * nb, grad + 3 * p * nb, hess + 6 * p * nb, 1);
+        if (c < 0) { free(idx); return (int)c; }
+    }
+    free(idx);
+    return 0;
+}
+
+/* Hessian of the density (Sec. 2: needed for forces and stresses; six components, each a
+ * "straightforward extension" of Eq. Density). Differentiating n = sum_ij phi_i P_ij phi_j twice:
+ *   d_a d_b n = sum_ij P_ij (d_a d_b phi_i phi_j + d_a phi_i d_b phi_j + d_b phi_i d_a phi_j
+ *                            + phi_i d_a d_b phi_j),
+ * h[6p + k] for k = xx, xy, xz, yy, yz, zz; Dh = the sum of the four terms' magnitudes.
+ * Compensated sums.                                                                          */
+int or_density_hessian(const or_sys *S, int64_t n_pts, const double *pts, const double *P, double *h, double *Dh) {
+    static const int hp[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    int64_t nb = or_n_basis(S);
+    size_t nn = (size_t)(nb ? nb : 1);
+    int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * nn);
+    double *phi = (double *)malloc(sizeof(double) * nn);
+    double *grad = (double *)malloc(sizeof(double) * 3 * nn);
+    double *hs = (double *)malloc(sizeof(double) * 6 * nn);
+    if (!idx || !phi || !grad || !hs) { free(idx); free(phi); free(grad); free(hs); return -1; }
+    int status = 0;
+    for (int64_t p = 0; p < n_pts; p++) {
+        int64_t cnt = point_basis2(S, pts + 3 * p, idx, phi, grad, hs, 0);
+        if (cnt < 0) { status = (int)cnt; break; }
+        for (int k = 0; k < 6; k++) {
+            int ia = hp[k][0], ib = hp[k][1];
+            double sv = 0.0, se = 0.0, dv = 0.0, de = 0.0;
+            for (int64_t a = 0; a < cnt; a++) {
+                const double *row = P + (size_t)idx[a] * (size_t)nb;
+                for (int64_t b = 0; b < cnt; b++) {
+                    double pij = row[idx[b]];
+                    double t[4] = {pij * hs[6 * a + k] * phi[b], pij * grad[3 * a + ia] * grad[3 * b + ib],
+                                   pij * grad[3 * a + ib] * grad[3 * b + ia], pij * phi[a] * hs[6 * b + k]};
+                    for (int u = 0; u < 4; u++) {
+                        neu_add(&sv, &se, t[u]);
+                        neu_add(&dv, &de, fabs(t[u]));
+                    }
+                }
+            }
+            h[6 * p + k] = sv + se;
+            if (Dh) Dh[6 * p + k] = dv + de;
+        }
+    }
+    free(idx); free(phi); free(grad); free(hs);
     return status;
 }
 
