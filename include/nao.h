@@ -222,14 +222,28 @@ nao_status nao_update_density_many(nao_grid *g, const double *const *P_dev, nao_
  * computed with n from one product T = Phi P over all of P (no tile-pair symmetry), so one call
  * costs about twice nao_update_density plus the gradient evaluation. grad_dev: device
  * [3 * n_points], component-major (d/dx for every point, then d/dy, then d/dz), original point
- * order; n_dev and n_electrons_dev as nao_update_density. NAO_FP64 and NAO_FP32 only
- * (NAO_SPLIT: NAO_ERR_UNSUPPORTED). The _many form: host arrays of per-system device pointers
- * as nao_update_density_many, grad_dev[m] of 3 * n_points(m) entries.                       */
+ * order; n_dev and n_electrons_dev as nao_update_density. All three precisions (NAO_SPLIT
+ * takes P' = P over all of K and the gradient rows of the evaluated block in its epilogue).
+ * The _many form: host arrays of per-system device pointers as nao_update_density_many,
+ * grad_dev[m] of 3 * n_points(m) entries.                                                      */
 nao_status nao_update_density_gradient(nao_grid *g, const double *P_dev, nao_precision prec, double *n_dev,
                                        double *grad_dev, double *n_electrons_dev, void *cuda_stream);
 nao_status nao_update_density_gradient_many(nao_grid *g, const double *const *P_dev, nao_precision prec,
                                             double *const *n_dev, double *const *grad_dev,
                                             double *const *n_electrons_dev, void *cuda_stream);
+
+/* Density, gradient and Hessian (Sec. 2: the Hessian of the density, six components, needed for
+ * forces and stresses):
+ *     d_a d_b n(r_p) = 2 sum_ij P_ij (phi_i d_a d_b phi_j + d_a phi_i d_b phi_j)   (P symmetric),
+ * from the basis functions' second derivatives and the four products Phi P, (d_a Phi) P over all
+ * of P, in FP64. hess_dev: device [6 * n_points], component-major in the order xx, xy, xz, yy,
+ * yz, zz, original point order; n_dev, grad_dev and n_electrons_dev as
+ * nao_update_density_gradient. Single-system handles only (grouped: NAO_ERR_INVALID_ARG);
+ * NAO_FP64 only (NAO_FP32, NAO_SPLIT: NAO_ERR_UNSUPPORTED). A batch whose 10-row evaluation
+ * (N_b x 10 Ppad FP64) exceeds the evaluation scratch returns NAO_ERR_UNSUPPORTED (raise
+ * scratch_bytes).                                                                              */
+nao_status nao_update_density_hessian(nao_grid *g, const double *P_dev, nao_precision prec, double *n_dev,
+                                      double *grad_dev, double *hess_dev, double *n_electrons_dev, void *cuda_stream);
 
 /* The same two operations with HOST buffers: the library copies the inputs to the device,
  * runs the operation on the given stream, copies the results back and synchronises the

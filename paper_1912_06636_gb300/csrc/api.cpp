@@ -964,6 +964,48 @@ nao_status run_n(nao_grid *g, nao_precision prec, cudaStream_t st, bool grad = f
 
 void set_tab(nao_grid *g, int section, int m, const void *p) { g->h_tab[(size_t)section * g->n_sys + m] = const_cast<void *>(p); }
 
+// Density Hessian plan: runs of batches whose evaluation in the 10-row layout (phi, grad phi,
+// six second derivatives: N_b x 10 Ppad FP64 per batch) fits the evaluation scratch, their
+// density work items (64-point tiles, consecutive per batch) and the per-batch offsets.
+nao_status hess_plan(nao_grid *g) {
+    if (!g->hess_chunks.empty()) return NAO_OK;
+    const int64_t nbat = g->n_batches;
+    std::vector<int64_t> off((size_t)std::max<int64_t>(nbat, 1), 0);
+    int64_t used = 0, dw = 0;
+    nao_grid::HessChunk cur{0, 0, 0, 0};
+    for (int64_t b = 0; b < nbat; b++) {
+        const int64_t Ppad = (g->Pb[b] + NAO_PPAD - 1) / NAO_PPAD * NAO_PPAD;
+        const int64_t e = (int64_t)g->Nb[b] * 10 * Ppad;
+        if (e > g->scratch_elems)
+            return fail(NAO_ERR_UNSUPPORTED, "density Hessian: batch " + std::to_string(b) +
+                                                 " needs more evaluation scratch than the handle has (raise scratch_bytes)");
+        if (used + e > g->scratch_elems && b > cur.b0) {
+            cur.b1 = (int32_t)b;
+            cur.dw1 = (int32_t)dw;
+            g->hess_chunks.push_back(cur);
+            cur = nao_grid::HessChunk{(int32_t)b, 0, (int32_t)dw, 0};
+            used = 0;
+        }
+        off[(size_t)b] = used;
+        used += e;
+        dw += (g->Pb[b] + NAO_TILE - 1) / NAO_TILE;
+    }
+    cur.b1 = (int32_t)nbat;
+    cur.dw1 = (int32_t)dw;
+    g->hess_chunks.push_back(cur);
+    if (dw != g->n_dwork) {
+        g->hess_chunks.clear();
+        return fail(NAO_ERR_INTERNAL, "density Hessian: work items do not match the density tiles");
+    }
+    nao_status st = upload(g, &g->d_hess_off, off.data(), off.size());
+    if (st) {
+        g->hess_chunks.clear();
+        return st;
+    }
+    NAO_CUDA(cudaStreamSynchronize(g->setup));
+    return NAO_OK;
+}
+
 }  // namespace
 
 void nao_set_last_error(const std::string &msg) { g_last_error = msg; }
@@ -1218,6 +1260,33 @@ nao_status nao_update_density_gradient(nao_grid *g, const double *P_dev, nao_pre
     if (st || (st = check_single(g))) return st;
     double *const ne[1] = {n_electrons_dev};
     return nao_update_density_gradient_many(g, &P_dev, prec, &n_dev, &grad_dev, ne, cuda_stream);
+}
+
+nao_status nao_update_density_hessian(nao_grid *g, const double *P_dev, nao_precision prec, double *n_dev,
+                                      double *grad_dev, double *hess_dev, double *n_electrons_dev, void *cuda_stream) {
+    nao_status st = check_handle(g);
+    if (st || (st = check_single(g))) return st;
+    if (!P_dev || !n_dev || !grad_dev || !hess_dev)
+        return fail(NAO_ERR_INVALID_ARG, "P_dev, n_dev, grad_dev or hess_dev is NULL");
+    if ((st = check_prec(prec))) return st;
+    if (prec != NAO_FP64) return fail(NAO_ERR_UNSUPPORTED, "the density Hessian is built on the FP64 path only");
+    DeviceGuard guard(g->device);
+    if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    if ((st = hess_plan(g))) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    set_tab(g, 2, 0, P_dev);
+    set_tab(g, 3, 0, n_dev);
+    set_tab(g, 4, 0, n_electrons_dev);
+    set_tab(g, 5, 0, grad_dev);
+    if ((st = upload_tables(g, 2, 4, s))) return st;
+    const DevSystem &sys = g->sys;
+    for (const auto &c : g->hess_chunks) {
+        NAO_CUDA(launch_eval_hess(sys, c.b0, c.b1, g->d_scratch, g->d_hess_off, s));
+        NAO_CUDA(launch_density_hess(sys, g->d_dwork, c.dw0, c.dw1 - c.dw0, g->d_scratch, g->d_hess_off, hess_dev,
+                                     g->d_ne_part, s));
+    }
+    if (n_electrons_dev) NAO_CUDA(launch_reduce_ne(sys, g->d_ne_part, g->d_sys_dw0, g->n_sys, s));
+    return mark_done(g, s);
 }
 
 static nao_status ensure_staging(nao_grid *g) {

@@ -207,6 +207,13 @@ struct nao_grid {
     bool split_ready = false;
     int split_S = 0;
     std::vector<SplitChunk> split_chunks;
+    // density Hessian (FP64): chunks of batches whose 10-row evaluation fits the scratch, with
+    // their density work ranges, and the per-batch scratch offsets of that layout
+    struct HessChunk {
+        int32_t b0, b1, dw0, dw1;
+    };
+    std::vector<HessChunk> hess_chunks;
+    int64_t *d_hess_off = nullptr;
     // tile width (MMA N) of every batch on the split path: a fixed rule until the autotuner has
     // timed both widths per (N_b, P_b) bucket of the batch-size histogram
     std::vector<int32_t> split_tn;
@@ -252,6 +259,13 @@ cudaError_t launch_eval(const DevSystem &s, int32_t b0, int32_t b1, nao_precisio
 // point exponents of the slicing into expo (by batch-ordered point; n_red >= P_b).
 cudaError_t launch_eval_split(const DevSystem &s, int32_t b0, int32_t b1, bool grad, double *scratch, int32_t *expo,
                               int32_t n_red, cudaStream_t st);
+// Density Hessian (FP64): evaluation of phi, grad phi and the six second derivatives (10 rows
+// of Ppad per function at scratch + hoff[b]) and the contraction (n, grad n into the pointer
+// tables' sections 3 and 5, the Hessian component-major into hess, per-tile w n into ne_part).
+cudaError_t launch_eval_hess(const DevSystem &s, int32_t b0, int32_t b1, double *scratch, const int64_t *hoff,
+                             cudaStream_t st);
+cudaError_t launch_density_hess(const DevSystem &s, const DWork *work, int32_t w0, int32_t n_work, const double *scratch,
+                                const int64_t *hoff, double *hess, double *ne_part, cudaStream_t st);
 cudaError_t launch_eval_one(const DevSystem &s, int32_t b, nao_precision prec, double *phi, double *grad,
                             cudaStream_t st);
 cudaError_t launch_h_simt(const DevSystem &s, nao_precision prec, const HWork *work, int32_t n_work,

@@ -34,6 +34,7 @@ SYMBOLS = [
     "nao_profile_enable", "nao_profile_read", "nao_integrate_h_noalloc",
     "nao_grid_create_many", "nao_get_system", "nao_integrate_h_many", "nao_update_density_many",
     "nao_get_tuning", "nao_update_density_gradient", "nao_update_density_gradient_many",
+    "nao_update_density_hessian",
 ]
 NAO_NOALLOC_SCRATCH_BYTES = 32 << 20
 KERNELS = ["eval_grad", "eval_phi", "h_fp64", "h_fp32", "h_split", "slice_h", "mirror", "n_fp64", "n_fp32",
@@ -111,6 +112,7 @@ def load():
         "nao_update_density_many": ([P, P, C.c_int, P, P, P], C.c_int),
         "nao_get_tuning": ([P, P, P], C.c_int),
         "nao_update_density_gradient": ([P, P, C.c_int, P, P, P, P], C.c_int),
+        "nao_update_density_hessian": ([P, P, C.c_int, P, P, P, P, P], C.c_int),
         "nao_update_density_gradient_many": ([P, P, C.c_int, P, P, P, P], C.c_int),
     }
     for name, (args, res) in sig.items():
@@ -280,6 +282,11 @@ def nao_update_density_gradient(h, P, prec, n, grad, ne=None, stream=None) -> No
                                               _stream(stream)), "nao_update_density_gradient")
 
 
+def nao_update_density_hessian(h, P, prec, n, grad, hess, ne=None, stream=None) -> None:
+    _check(load().nao_update_density_hessian(h, _dptr(P), _prec(prec), _dptr(n), _dptr(grad), _dptr(hess), _dptr(ne),
+                                             _stream(stream)), "nao_update_density_hessian")
+
+
 def nao_update_density_gradient_many(h, Ps, prec, ns, grads, nes=None, stream=None) -> None:
     _check(load().nao_update_density_gradient_many(h, _ptr_array(Ps, False), _prec(prec), _ptr_array(ns, False),
                                                    _ptr_array(grads, False), _ptr_array(nes, True), _stream(stream)),
@@ -433,6 +440,22 @@ class Grid:
             ne = torch.empty(1, dtype=torch.float64, device=self.device)
         nao_update_density_gradient(self.h, P, prec, n, grad, ne, stream)
         return n, grad, ne
+
+    def density_hessian(self, P, prec="fp64", n=None, grad=None, hess=None, ne=None, stream=None, want_ne=True):
+        """n, grad n ([3, n_points]), the density Hessian ([6, n_points]: xx, xy, xz, yy, yz, zz)
+        and N_e of a single-system handle (FP64)."""
+        import torch
+
+        if n is None:
+            n = torch.empty(self.n_points, dtype=torch.float64, device=self.device)
+        if grad is None:
+            grad = torch.empty((3, self.n_points), dtype=torch.float64, device=self.device)
+        if hess is None:
+            hess = torch.empty((6, self.n_points), dtype=torch.float64, device=self.device)
+        if ne is None and want_ne:
+            ne = torch.empty(1, dtype=torch.float64, device=self.device)
+        nao_update_density_hessian(self.h, P, prec, n, grad, hess, ne, stream)
+        return n, grad, hess, ne
 
     def density_gradient_many(self, Ps, prec="fp64", stream=None):
         import torch
