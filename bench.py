@@ -537,6 +537,30 @@ def main():
             except nao.NaoError as e:
                 other[f"split_{d}_slices"] = {"unavailable": str(e)}
         line["other_precisions"] = other
+        # density derivatives (Sec. 2) on the same workload: the gradient (split and FP64) and the
+        # Hessian (FP64), one untimed and one timed call each
+        deriv = {}
+        gbuf = torch.empty((3, g.n_points), dtype=torch.float64, device=dev)
+        hbuf = torch.empty((6, g.n_points), dtype=torch.float64, device=dev)
+        calls = {
+            "gradient_split": lambda: g.density_gradient(P, prec="split", n=n, grad=gbuf, ne=ne, stream=stream),
+            "gradient_fp64": lambda: g.density_gradient(P, prec="fp64", n=n, grad=gbuf, ne=ne, stream=stream),
+            "hessian_fp64": lambda: g.density_hessian(P, prec="fp64", n=n, grad=gbuf, hess=hbuf, ne=ne, stream=stream),
+        }
+        for name, call in calls.items():
+            try:
+                call()
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                call()
+                b.record(stream)
+                torch.cuda.synchronize()
+                g.sync()
+                deriv[name] = {"ms": a.elapsed_time(b), "points_per_s": g.n_points / (a.elapsed_time(b) / 1e3)}
+            except nao.NaoError as e:
+                deriv[name] = {"unavailable": str(e)}
+        line["density_derivatives"] = deriv
 
     if rank == 0 and world == 1 and not args.no_serve and args.serve_requests > 0:
         g.close()
