@@ -70,6 +70,8 @@ def _load():
         lib.or_eval_dense.restype = C.c_int
         lib.or_hamiltonian.argtypes = [P, I64, P, P, P, C.c_uint32, P, P, P]
         lib.or_hamiltonian.restype = C.c_int
+        lib.or_hamiltonian_tau.argtypes = [P, I64, P, P, P, P, C.c_uint32, P, P, P]
+        lib.or_hamiltonian_tau.restype = C.c_int
         lib.or_hamiltonian_block.argtypes = [P, I64, P, P, P, C.c_uint32, I32, P, P, P, P]
         lib.or_hamiltonian_block.restype = C.c_int
         lib.or_density.argtypes = [P, I64, P, P, P, P, P, P, P]
@@ -113,6 +115,7 @@ def _check(st, what):
 
 TERM_POTENTIAL = 1
 TERM_KINETIC = 2
+TERM_TAU = 4  # meta-GGA: w vtau 1/2 grad phi_i . grad phi_j
 
 
 class Oracle:
@@ -212,6 +215,19 @@ class Oracle:
         st = self.lib.or_hamiltonian(self.sp, pts.shape[0], _ptr(pts), _ptr(w), _ptr(v), int(terms), _ptr(H), _ptr(A),
                                      C.byref(self.pole_count))
         _check(st, "hamiltonian")
+        return H, A
+
+    def hamiltonian_tau(self, pts, w, v, vtau, terms=TERM_POTENTIAL | TERM_KINETIC | TERM_TAU):
+        """H with the meta-GGA term w vtau 1/2 grad phi_i . grad phi_j (terms bit 4)."""
+        pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        v = None if v is None else np.ascontiguousarray(v, dtype=np.float64)
+        vtau = np.ascontiguousarray(vtau, dtype=np.float64)
+        H = np.zeros((self.nb, self.nb))
+        A = np.zeros((self.nb, self.nb))
+        st = self.lib.or_hamiltonian_tau(self.sp, pts.shape[0], _ptr(pts), _ptr(w), _ptr(v), _ptr(vtau), int(terms),
+                                         _ptr(H), _ptr(A), C.byref(self.pole_count))
+        _check(st, "hamiltonian_tau")
         return H, A
 
     def hamiltonian_block(self, F, pts, w, v=None, terms=TERM_POTENTIAL | TERM_KINETIC):

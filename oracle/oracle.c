@@ -375,8 +375,20 @@ int or_eval_dense(const or_sys *S, int64_t n_pts, const double *pts, double *phi
 /* H [nb*nb] (full, both triangles formed independently) and the error denominator
  * A_ij = sum_p w_p [ |phi_i v phi_j| + 1/2 |grad phi_i . grad phi_j| ].
  * terms: bit 0 = potential term (v == NULL means v = 1), bit 1 = kinetic term.           */
+int or_hamiltonian_tau(const or_sys *S, int64_t n_pts, const double *pts, const double *w, const double *v,
+                       const double *vtau, uint32_t terms, double *H, double *A, int64_t *pole_count);
+
 int or_hamiltonian(const or_sys *S, int64_t n_pts, const double *pts, const double *w, const double *v,
                    uint32_t terms, double *H, double *A, int64_t *pole_count) {
+    return or_hamiltonian_tau(S, n_pts, pts, w, v, NULL, terms & 3u, H, A, pole_count);
+}
+
+/* With the meta-GGA kinetic-energy-density term (Sec. 3.4: the tau-dependent part of the
+ * exchange-correlation potential, an extra weighted gradient product): terms bit 4 adds
+ *     w_p vtau_p 1/2 grad phi_i . grad phi_j
+ * to each point's contribution (vtau required then).                                      */
+int or_hamiltonian_tau(const or_sys *S, int64_t n_pts, const double *pts, const double *w, const double *v,
+                       const double *vtau, uint32_t terms, double *H, double *A, int64_t *pole_count) {
     int64_t nb = or_n_basis(S);
     size_t nn = (size_t)nb * (size_t)nb;
     double *Hc = (double *)calloc(nn ? nn : 1, sizeof(double));
@@ -387,7 +399,7 @@ int or_hamiltonian(const or_sys *S, int64_t n_pts, const double *pts, const doub
     if (!Hc || !Ac || !idx || !phi || !grad) { free(Hc); free(Ac); free(idx); free(phi); free(grad); return -1; }
     memset(H, 0, nn * sizeof(double));
     memset(A, 0, nn * sizeof(double));
-    int pot = (terms & 1u) != 0, kin = (terms & 2u) != 0;
+    int pot = (terms & 1u) != 0, kin = (terms & 2u) != 0, tau = (terms & 4u) != 0 && vtau != NULL;
     int status = 0;
     for (int64_t p = 0; p < n_pts; p++) {
         int64_t cnt = point_basis(S, pts + 3 * p, idx, phi, grad, pole_count, 0);
@@ -399,9 +411,10 @@ int or_hamiltonian(const or_sys *S, int64_t n_pts, const double *pts, const doub
                 double tv = pot ? wp * (phi[a] * vp * phi[b]) : 0.0;
                 double gg = grad[3 * a] * grad[3 * b] + grad[3 * a + 1] * grad[3 * b + 1] + grad[3 * a + 2] * grad[3 * b + 2];
                 double tk = kin ? wp * 0.5 * gg : 0.0;
+                double tt = tau ? wp * vtau[p] * 0.5 * gg : 0.0;
                 size_t e = row + (size_t)idx[b];
-                neu_add(&H[e], &Hc[e], tv + tk);
-                neu_add(&A[e], &Ac[e], fabs(tv) + fabs(tk));
+                neu_add(&H[e], &Hc[e], tv + tk + tt);
+                neu_add(&A[e], &Ac[e], fabs(tv) + fabs(tk) + fabs(tt));
             }
         }
     }

@@ -486,10 +486,10 @@ nao_status build(nao_grid *g, const nao_system_desc *descs, int32_t n_sys, const
         (st = upload(g, &g->d_zero_tasks, g->zero_tasks.data(), g->zero_tasks.size())) ||
         (st = upload(g, &g->d_mirror_tasks, g->mirror_tasks.data(), g->mirror_tasks.size())) ||
         (st = upload(g, &g->d_sys_np, g->sys_np.data(), g->sys_np.size())) ||
-        (st = dev_alloc(g, &g->d_tab, 6 * (size_t)n_sys)))
+        (st = dev_alloc(g, &g->d_tab, 7 * (size_t)n_sys)))
         return st;
-    NAO_CUDA(cudaMemsetAsync(g->d_tab, 0, 6 * (size_t)n_sys * sizeof(double *), g->setup));
-    g->h_tab.assign(6 * (size_t)n_sys, nullptr);
+    NAO_CUDA(cudaMemsetAsync(g->d_tab, 0, 7 * (size_t)n_sys * sizeof(double *), g->setup));
+    g->h_tab.assign(7 * (size_t)n_sys, nullptr);
 
     DevSystem &s = g->sys;
     s.atom_xyz = d_atoms;
@@ -522,6 +522,7 @@ nao_status build(nao_grid *g, const nao_system_desc *descs, int32_t n_sys, const
     s.sys.n = g->d_tab + 3 * n_sys;
     s.sys.ne = g->d_tab + 4 * n_sys;
     s.sys.gn = g->d_tab + 5 * n_sys;
+    s.sys.vt = g->d_tab + 6 * n_sys;
     s.sys.np = g->d_sys_np;
     s.n_rgrid = g->n_rgrid;
     s.r0 = g->r0;

@@ -46,6 +46,7 @@ struct SysTables {
     double *const *n;        // [n_sys] this call's n of each system
     double *const *ne;       // [n_sys] this call's N_e of each system (NULL entry: not formed)
     double *const *gn;       // [n_sys] this call's grad n of each system ([3][np], component-major)
+    const double *const *vt; // [n_sys] this call's v_tau of each system (NULL entry: no tau term)
     const int32_t *np;       // [n_sys] points of the system
 };
 
@@ -89,6 +90,11 @@ __device__ __forceinline__ double p_elem(const DevSystem &s, int m, int64_t gi, 
 __device__ __forceinline__ double v_at(const DevSystem &s, int m, int p) {
     const double *v = s.sys.v[m];
     return v ? v[s.perm[p] - s.sys.poff[m]] : 1.0;
+}
+// v_tau at batch-ordered point p of system m (0 when the system has no v_tau this call).
+__device__ __forceinline__ double vt_at(const DevSystem &s, int m, int p) {
+    const double *vt = s.sys.vt[m];
+    return vt ? vt[s.perm[p] - s.sys.poff[m]] : 0.0;
 }
 __device__ __forceinline__ double *n_at(const DevSystem &s, int m, int p) {
     return s.sys.n[m] + (s.perm[p] - s.sys.poff[m]);

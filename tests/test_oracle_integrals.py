@@ -247,3 +247,26 @@ def test_density_gradient_single_s_function():
     # the spline reproduces the Gaussian to ~1e-6 relative in its far tail (r ~ 2.7 here)
     assert np.all(np.abs(g - exact) <= 1e-6 * np.abs(exact) + 1e-10 * np.abs(exact).max())
     assert np.all(np.abs(g - exact)[r < 1.5] <= 1e-8 * np.abs(exact)[r < 1.5])
+
+
+def test_tau_term_pins(small_molecule):
+    """The meta-GGA term w vtau 1/2 grad phi_i . grad phi_j: vtau = 1 gives the kinetic term,
+    it is linear in vtau and adds to the other terms, and its magnitude sum is its own."""
+    from oracle import TERM_TAU
+
+    s, o = small_molecule
+    rng = np.random.Generator(np.random.PCG64(23))
+    ones = np.ones(s.n_points)
+    Hk, Ak = o.hamiltonian(s.pt_xyz, s.pt_w, None, TERM_KINETIC)
+    Ht, At = o.hamiltonian_tau(s.pt_xyz, s.pt_w, None, ones, TERM_TAU)
+    assert np.allclose(Ht, Hk, rtol=0, atol=1e-14 * np.abs(Ak).max())
+    a, b = rng.uniform(-1, 1, s.n_points), rng.uniform(-1, 1, s.n_points)
+    Ha, _ = o.hamiltonian_tau(s.pt_xyz, s.pt_w, None, a, TERM_TAU)
+    Hb, _ = o.hamiltonian_tau(s.pt_xyz, s.pt_w, None, b, TERM_TAU)
+    Hab, Aab = o.hamiltonian_tau(s.pt_xyz, s.pt_w, None, 2 * a - 3 * b, TERM_TAU)
+    assert np.allclose(Hab, 2 * Ha - 3 * Hb, rtol=0, atol=1e-13 * np.abs(Aab).max())
+    v = s.potential()
+    Hall, _ = o.hamiltonian_tau(s.pt_xyz, s.pt_w, v, a, TERM_POTENTIAL | TERM_KINETIC | TERM_TAU)
+    Hpk, _ = o.hamiltonian(s.pt_xyz, s.pt_w, v)
+    assert np.allclose(Hall, Hpk + Ha, rtol=0, atol=1e-13 * np.abs(Hall).max())
+    assert np.allclose(Ha, Ha.T, rtol=0, atol=1e-14 * np.abs(Ha).max())
