@@ -63,7 +63,7 @@ typedef enum { NAO_FP64 = 0, NAO_FP32 = 1, NAO_SPLIT = 2 } nao_precision;
 /* Terms of nao_integrate_h. The overlap s_ij (Eq. OverlapNoPeriodic) is
  * NAO_TERM_POTENTIAL with v_dev == NULL (v = 1): the paper integrates it with the same
  * code as h (Sec. 3.2.1).                                                                */
-enum { NAO_TERM_POTENTIAL = 1u, NAO_TERM_KINETIC = 2u };
+enum { NAO_TERM_POTENTIAL = 1u, NAO_TERM_KINETIC = 2u, NAO_TERM_TAU = 4u /* nao_integrate_h_tau only */ };
 
 /* The system, exactly as the paper states the problem (Sec. 3.2.1, Sec. 3.3):
  * atoms with species; per species a list of radial functions (angular momentum l and a
@@ -192,6 +192,17 @@ nao_status nao_export_batches(const nao_grid *g, int64_t *batch_offsets, int64_t
  * NAO_ERR_UNSUPPORTED (precision not built for this device).                               */
 nao_status nao_integrate_h(nao_grid *g, const double *v_dev, uint32_t terms, nao_precision prec,
                            double *H_dev, void *cuda_stream);
+
+/* The same with the meta-GGA term (the part of the exchange-correlation potential that depends on
+ * the kinetic-energy density tau, Sec. 3.4's "extra weighted" gradient product): with
+ * NAO_TERM_TAU in terms, H_dev additionally receives sum_p w_p v_tau,p 1/2 grad phi_i . grad phi_j.
+ * It enters as a weight on the three gradient columns (w (kappa + v_tau) / 2, kappa = 1 with
+ * NAO_TERM_KINETIC), so it costs no extra contraction. vtau_dev: device [n_points], original
+ * point order; required (non-NULL) with NAO_TERM_TAU. terms: a non-empty subset of
+ * NAO_TERM_POTENTIAL | NAO_TERM_KINETIC | NAO_TERM_TAU. All three precisions; single-system
+ * handles (grouped: NAO_ERR_INVALID_ARG). Other arguments and errors as nao_integrate_h.    */
+nao_status nao_integrate_h_tau(nao_grid *g, const double *v_dev, const double *vtau_dev, uint32_t terms,
+                               nao_precision prec, double *H_dev, void *cuda_stream);
 
 /* Density update (Eq. Density, Sec. 3.3.5): n_dev[p] = sum_ij phi_i(r_p) P_ij phi_j(r_p)
  * for every point p (original order; 0 for points in batches without basis functions),

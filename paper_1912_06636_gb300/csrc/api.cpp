@@ -946,6 +946,7 @@ nao_status run_h(nao_grid *g, uint32_t terms, nao_precision prec, cudaStream_t s
     nao_status rs;
     if (prec == NAO_SPLIT && (rs = split_setup(g))) return rs;
     if ((rs = upload_tables(g, 0, 2, st))) return rs;
+    if ((terms & NAO_TERM_TAU) && (rs = upload_tables(g, 6, 1, st))) return rs;
     if (prec == NAO_SPLIT && (rs = split_tune(g, terms, st))) return rs;
     const uint64_t key = (uint64_t)1 << 40 | (uint64_t)prec << 8 | terms;
     return run_maybe_graph(g, key, st, [&](cudaStream_t s2) { return enqueue_h(g, terms, prec, s2); });
@@ -1179,6 +1180,23 @@ nao_status nao_integrate_h(nao_grid *g, const double *v_dev, uint32_t terms, nao
     if ((st = run_h(g, terms, prec, static_cast<cudaStream_t>(cuda_stream)))) return st;
     return mark_done(g, static_cast<cudaStream_t>(cuda_stream));
 }
+nao_status nao_integrate_h_tau(nao_grid *g, const double *v_dev, const double *vtau_dev, uint32_t terms,
+                               nao_precision prec, double *H_dev, void *cuda_stream) {
+    nao_status st = check_handle(g);
+    if (st || (st = check_single(g))) return st;
+    if (!H_dev) return fail(NAO_ERR_INVALID_ARG, "H_dev is NULL");
+    if (terms == 0 || (terms & ~7u)) return fail(NAO_ERR_INVALID_ARG, "bad terms");
+    if ((terms & NAO_TERM_TAU) && !vtau_dev) return fail(NAO_ERR_INVALID_ARG, "NAO_TERM_TAU needs vtau_dev");
+    if ((st = check_prec(prec))) return st;
+    DeviceGuard guard(g->device);
+    if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    set_tab(g, 0, 0, H_dev);
+    set_tab(g, 1, 0, v_dev);
+    set_tab(g, 6, 0, (terms & NAO_TERM_TAU) ? vtau_dev : nullptr);
+    if ((st = run_h(g, terms, prec, static_cast<cudaStream_t>(cuda_stream)))) return st;
+    return mark_done(g, static_cast<cudaStream_t>(cuda_stream));
+}
+
 
 nao_status nao_integrate_h_many(nao_grid *g, const double *const *v_dev, uint32_t terms, nao_precision prec,
                                 double *const *H_dev, void *cuda_stream) {

@@ -113,7 +113,8 @@ __global__ void __launch_bounds__(256) h_simt_kernel(DevSystem s, const HWork *_
         const double w = q < P ? s.pw[p0 + q] : 0.0;
         const double vv = q < P ? v_at(s, m, p0 + q) : 1.0;
         dv[q] = T((terms & NAO_TERM_POTENTIAL) ? w * vv : 0.0);
-        dk[q] = T((terms & NAO_TERM_KINETIC) ? 0.5 * w : 0.0);
+        const double kin = (terms & NAO_TERM_KINETIC) ? 1.0 : 0.0;
+        dk[q] = T(0.5 * w * ((terms & NAO_TERM_TAU) && q < P ? kin + vt_at(s, m, p0 + q) : kin));
     }
 
     const int i0 = it.ti * T_, j0 = it.tj * T_;

@@ -34,11 +34,14 @@ __device__ __forceinline__ int exponent_of_binade(int eb) {
 __device__ __forceinline__ int row_exponent_bits(long long mb) { return exponent_of_binade((int)(mb >> 52)); }
 
 // d_k of the Hamiltonian's column k = (component c, batch-ordered point p): w v on the potential
-// part (c = 0), w / 2 on the three gradient parts (Eq. H_decomp), 0 for a term that is off; the
-// column's scale is sqrt|d_k|.
+// part (c = 0), w (kappa + v_tau) / 2 on the three gradient parts (Eq. H_decomp; kappa = 1 with
+// the kinetic term, v_tau with the meta-GGA term), 0 for a term that is off; the column's scale
+// is sqrt|d_k|.
 __device__ __forceinline__ double h_column_weight(const DevSystem &s, int m, int p, int c, uint32_t terms) {
     const double w = s.pw[p];
-    return c == 0 ? ((terms & NAO_TERM_POTENTIAL) ? w * v_at(s, m, p) : 0.0) : ((terms & NAO_TERM_KINETIC) ? 0.5 * w : 0.0);
+    if (c == 0) return (terms & NAO_TERM_POTENTIAL) ? w * v_at(s, m, p) : 0.0;
+    const double kin = (terms & NAO_TERM_KINETIC) ? 1.0 : 0.0;
+    return 0.5 * w * ((terms & NAO_TERM_TAU) ? kin + vt_at(s, m, p) : kin);
 }
 __device__ __forceinline__ double h_column_scale(double d) { return sqrt(fabs(d)); }
 

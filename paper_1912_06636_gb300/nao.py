@@ -18,7 +18,7 @@ _LIB_PATH = Path(__file__).resolve().parent / "lib" / "libnao.so"
 _lib = None
 
 NAO_FP64, NAO_FP32, NAO_SPLIT = 0, 1, 2
-NAO_TERM_POTENTIAL, NAO_TERM_KINETIC = 1, 2
+NAO_TERM_POTENTIAL, NAO_TERM_KINETIC, NAO_TERM_TAU = 1, 2, 4
 NAO_OK, NAO_ERR_INVALID_ARG, NAO_ERR_OUT_OF_MEMORY, NAO_ERR_CUDA = 0, 1, 2, 3
 NAO_ERR_TIMEOUT, NAO_ERR_INTERNAL, NAO_ERR_UNSUPPORTED = 4, 5, 6
 PRECISIONS = {"fp64": NAO_FP64, "fp32": NAO_FP32, "split": NAO_SPLIT}
@@ -34,7 +34,7 @@ SYMBOLS = [
     "nao_profile_enable", "nao_profile_read", "nao_integrate_h_noalloc",
     "nao_grid_create_many", "nao_get_system", "nao_integrate_h_many", "nao_update_density_many",
     "nao_get_tuning", "nao_update_density_gradient", "nao_update_density_gradient_many",
-    "nao_update_density_hessian",
+    "nao_update_density_hessian", "nao_integrate_h_tau",
 ]
 NAO_NOALLOC_SCRATCH_BYTES = 32 << 20
 KERNELS = ["eval_grad", "eval_phi", "h_fp64", "h_fp32", "h_split", "slice_h", "mirror", "n_fp64", "n_fp32",
@@ -113,6 +113,7 @@ def load():
         "nao_get_tuning": ([P, P, P], C.c_int),
         "nao_update_density_gradient": ([P, P, C.c_int, P, P, P, P], C.c_int),
         "nao_update_density_hessian": ([P, P, C.c_int, P, P, P, P, P], C.c_int),
+        "nao_integrate_h_tau": ([P, P, P, C.c_uint32, C.c_int, P, P], C.c_int),
         "nao_update_density_gradient_many": ([P, P, C.c_int, P, P, P, P], C.c_int),
     }
     for name, (args, res) in sig.items():
@@ -262,6 +263,11 @@ def nao_integrate_h(h, v, terms: int, prec, H, stream=None) -> None:
     _check(load().nao_integrate_h(h, _dptr(v), int(terms), _prec(prec), _dptr(H), _stream(stream)), "nao_integrate_h")
 
 
+def nao_integrate_h_tau(h, v, vtau, terms: int, prec, H, stream=None) -> None:
+    _check(load().nao_integrate_h_tau(h, _dptr(v), _dptr(vtau), int(terms), _prec(prec), _dptr(H), _stream(stream)),
+           "nao_integrate_h_tau")
+
+
 def nao_update_density(h, P, prec, n, ne=None, stream=None) -> None:
     _check(load().nao_update_density(h, _dptr(P), _prec(prec), _dptr(n), _dptr(ne), _stream(stream)),
            "nao_update_density")
@@ -393,6 +399,16 @@ class Grid:
         if H is None:
             H = torch.empty((self.nb, self.nb), dtype=torch.float64, device=self.device)
         nao_integrate_h(self.h, v, terms, prec, H, stream)
+        return H
+
+    def integrate_h_tau(self, v, vtau, terms=NAO_TERM_POTENTIAL | NAO_TERM_KINETIC | NAO_TERM_TAU, prec="fp64", H=None,
+                        stream=None):
+        """H with the meta-GGA term sum_p w_p vtau_p 1/2 grad phi_i . grad phi_j (single system)."""
+        import torch
+
+        if H is None:
+            H = torch.empty((self.nb, self.nb), dtype=torch.float64, device=self.device)
+        nao_integrate_h_tau(self.h, v, vtau, terms, prec, H, stream)
         return H
 
     def overlap(self, prec="fp64", S=None, stream=None):
