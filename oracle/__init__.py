@@ -86,6 +86,10 @@ def _load():
         lib.or_eval_dense2.restype = C.c_int
         lib.or_density_hessian.argtypes = [P, I64, P, P, P, P]
         lib.or_density_hessian.restype = C.c_int
+        lib.or_pulay_matrices.argtypes = [P, I64, P, P, P, P, P, P, P]
+        lib.or_pulay_matrices.restype = C.c_int
+        lib.or_pulay_forces.argtypes = [P, I64, P, P, P, P, P, P]
+        lib.or_pulay_forces.restype = C.c_int
         lib.or_bruteforce.argtypes = [P, I64, P, P, P, P, P, P, P]
         lib.or_bruteforce.restype = C.c_int
         lib.or_partition.argtypes = [I64, P, I64, P, P]
@@ -281,6 +285,29 @@ class Oracle:
         _check(self.lib.or_density_hessian(self.sp, pts.shape[0], _ptr(pts), _ptr(P), _ptr(h), _ptr(Dh)),
                "density_hessian")
         return h, Dh
+
+    def pulay_matrices(self, pts, w, v=None):
+        """M [3, nb, nb] (sum_p w d_c phi_i (-1/2 lap + v) phi_j), S [3, nb, nb] (sum_p w d_c phi_i phi_j)
+        and their magnitude sums."""
+        pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        v = None if v is None else np.ascontiguousarray(v, dtype=np.float64)
+        M = np.zeros((3, self.nb, self.nb)); S = np.zeros((3, self.nb, self.nb))
+        AM = np.zeros((3, self.nb, self.nb)); AS = np.zeros((3, self.nb, self.nb))
+        _check(self.lib.or_pulay_matrices(self.sp, pts.shape[0], _ptr(pts), _ptr(w), _ptr(v), _ptr(M), _ptr(S), _ptr(AM),
+                                          _ptr(AS)), "pulay_matrices")
+        return M, S, AM, AS
+
+    def pulay_forces(self, pts, w, v, nmat, qmat):
+        """Local Pulay forces [n_atoms, 3] point by point from their definition."""
+        pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        v = None if v is None else np.ascontiguousarray(v, dtype=np.float64)
+        nmat = np.ascontiguousarray(nmat, dtype=np.float64); qmat = np.ascontiguousarray(qmat, dtype=np.float64)
+        F = np.zeros((int(self._keep["atom_xyz"].shape[0]), 3))
+        _check(self.lib.or_pulay_forces(self.sp, pts.shape[0], _ptr(pts), _ptr(w), _ptr(v), _ptr(nmat), _ptr(qmat),
+                                        _ptr(F)), "pulay_forces")
+        return F
 
     def bruteforce(self, pts, w, v, P):
         pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)

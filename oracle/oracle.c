@@ -689,6 +689,108 @@ int or_density_hessian(const or_sys *S, int64_t n_pts, const double *pts, const 
     return status;
 }
 
+/* Local Pulay force terms (Sec. 2, Eq. for F^{P,local}: -2 sum_ij int [grad_at phi_i] n_ij h_KS phi_j
+ * + 2 sum_ij int [grad_at phi_i] q_ij phi_j, with q the energy-weighted density matrix). The
+ * library assembles matrix elements with basis-function indices first ("initially assembling
+ * matrix elements", Sec. "Density and Density Derivatives"):
+ *     M^c_ij = sum_p w_p d_c phi_i (h phi_j),  h phi_j = -1/2 lap phi_j + v phi_j,
+ *     S^c_ij = sum_p w_p d_c phi_i phi_j                       (c = x, y, z),
+ * M[c nb^2 + i nb + j]; AM, AS the sums of the term magnitudes (may be NULL). The Laplacian is
+ * the trace of the Cartesian basis Hessian (point_basis2). Compensated sums.                   */
+int or_pulay_matrices(const or_sys *S, int64_t n_pts, const double *pts, const double *w, const double *v,
+                      double *M, double *Sm, double *AM, double *AS) {
+    int64_t nb = or_n_basis(S);
+    size_t nn = (size_t)nb * (size_t)nb, n1 = (size_t)(nb ? nb : 1);
+    double *cM = (double *)calloc(3 * (nn ? nn : 1), sizeof(double));
+    double *cS = (double *)calloc(3 * (nn ? nn : 1), sizeof(double));
+    double *cAM = (double *)calloc(3 * (nn ? nn : 1), sizeof(double));
+    double *cAS = (double *)calloc(3 * (nn ? nn : 1), sizeof(double));
+    int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * n1);
+    double *phi = (double *)malloc(sizeof(double) * n1);
+    double *grad = (double *)malloc(sizeof(double) * 3 * n1);
+    double *hs = (double *)malloc(sizeof(double) * 6 * n1);
+    double *hphi = (double *)malloc(sizeof(double) * n1);
+    double *dummyM = AM ? AM : cAM, *dummyS = AS ? AS : cAS;
+    int status = 0;
+    if (!cM || !cS || !cAM || !cAS || !idx || !phi || !grad || !hs || !hphi) { status = -1; goto done; }
+    memset(M, 0, 3 * nn * sizeof(double));
+    memset(Sm, 0, 3 * nn * sizeof(double));
+    if (AM) memset(AM, 0, 3 * nn * sizeof(double));
+    if (AS) memset(AS, 0, 3 * nn * sizeof(double));
+    for (int64_t p = 0; p < n_pts; p++) {
+        int64_t cnt = point_basis2(S, pts + 3 * p, idx, phi, grad, hs, 0);
+        if (cnt < 0) { status = (int)cnt; break; }
+        double wp = w[p], vp = v ? v[p] : 1.0;
+        for (int64_t b = 0; b < cnt; b++) hphi[b] = -0.5 * (hs[6 * b + 0] + hs[6 * b + 3] + hs[6 * b + 5]) + vp * phi[b];
+        for (int c = 0; c < 3; c++)
+            for (int64_t a = 0; a < cnt; a++) {
+                size_t row = (size_t)c * nn + (size_t)idx[a] * (size_t)nb;
+                for (int64_t b = 0; b < cnt; b++) {
+                    size_t e = row + (size_t)idx[b];
+                    double tm = wp * (grad[3 * a + c] * hphi[b]);
+                    double ts = wp * (grad[3 * a + c] * phi[b]);
+                    neu_add(&M[e], &cM[e], tm);
+                    neu_add(&Sm[e], &cS[e], ts);
+                    if (AM) AM[e] += fabs(tm);
+                    if (AS) AS[e] += fabs(ts);
+                }
+            }
+    }
+    for (size_t e = 0; e < 3 * nn; e++) { M[e] += cM[e]; Sm[e] += cS[e]; }
+    (void)dummyM; (void)dummyS;
+done:
+    free(cM); free(cS); free(cAM); free(cAS); free(idx); free(phi); free(grad); free(hs); free(hphi);
+    return status;
+}
+
+/* The local Pulay forces point by point from their definition (no matrix elements):
+ *   F_at = -2 sum_ij sum_p w_p [d/dR_at phi_i] n_ij (h phi_j) + 2 sum_ij sum_p w_p [d/dR_at phi_i] q_ij phi_j,
+ * d/dR_at phi_i = -grad phi_i for a function on atom at (0 otherwise); F[3 at + c].          */
+int or_pulay_forces(const or_sys *S, int64_t n_pts, const double *pts, const double *w, const double *v,
+                    const double *nmat, const double *qmat, double *F) {
+    int64_t nb = or_n_basis(S);
+    size_t n1 = (size_t)(nb ? nb : 1);
+    int32_t *atom_of = (int32_t *)malloc(sizeof(int32_t) * n1);
+    int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * n1);
+    double *phi = (double *)malloc(sizeof(double) * n1);
+    double *grad = (double *)malloc(sizeof(double) * 3 * n1);
+    double *hs = (double *)malloc(sizeof(double) * 6 * n1);
+    double *hphi = (double *)malloc(sizeof(double) * n1);
+    double *acc = (double *)calloc(3 * (size_t)(S->n_atoms ? S->n_atoms : 1), sizeof(double));
+    double *cacc = (double *)calloc(3 * (size_t)(S->n_atoms ? S->n_atoms : 1), sizeof(double));
+    int status = 0;
+    if (!atom_of || !idx || !phi || !grad || !hs || !hphi || !acc || !cacc) { status = -1; goto done2; }
+    {
+        int64_t k = 0;
+        for (int32_t a = 0; a < S->n_atoms; a++) {
+            int32_t sp = S->atom_species[a];
+            for (int32_t f = S->species_fn_offset[sp]; f < S->species_fn_offset[sp + 1]; f++)
+                for (int m = 0; m < 2 * S->fn_l[f] + 1; m++) atom_of[k++] = a;
+        }
+    }
+    for (int64_t p = 0; p < n_pts; p++) {
+        int64_t cnt = point_basis2(S, pts + 3 * p, idx, phi, grad, hs, 0);
+        if (cnt < 0) { status = (int)cnt; break; }
+        double wp = w[p], vp = v ? v[p] : 1.0;
+        for (int64_t b = 0; b < cnt; b++) hphi[b] = -0.5 * (hs[6 * b + 0] + hs[6 * b + 3] + hs[6 * b + 5]) + vp * phi[b];
+        for (int64_t a = 0; a < cnt; a++) {
+            const double *nr = nmat + (size_t)idx[a] * (size_t)nb, *qr = qmat + (size_t)idx[a] * (size_t)nb;
+            int32_t at = atom_of[idx[a]];
+            for (int c = 0; c < 3; c++) {
+                double dRphi = -grad[3 * a + c];
+                for (int64_t b = 0; b < cnt; b++) {
+                    double t = -2.0 * wp * dRphi * nr[idx[b]] * hphi[b] + 2.0 * wp * dRphi * qr[idx[b]] * phi[b];
+                    neu_add(&acc[3 * at + c], &cacc[3 * at + c], t);
+                }
+            }
+        }
+    }
+    for (int32_t a = 0; a < 3 * S->n_atoms; a++) F[a] = acc[a] + cacc[a];
+done2:
+    free(atom_of); free(idx); free(phi); free(grad); free(hs); free(hphi); free(acc); free(cacc);
+    return status;
+}
+
 /* Brute force for tiny inputs: phi for every basis function at every point (zeros
  * included) and a triple loop over p, i, j, with no batching and no relevance pruning.   */
 int or_bruteforce(const or_sys *S, int64_t n_pts, const double *pts, const double *w, const double *v,

@@ -147,3 +147,59 @@ def test_density_hessian_differences_and_rank_one(water):
     ddu = np.einsum("pik,i->pk", hess, cvec)
     want = np.stack([2 * du[:, a] * du[:, b] + 2 * u * ddu[:, k] for k, (a, b) in enumerate(PAIRS)], axis=1)
     assert np.allclose(H1, want, rtol=0, atol=1e-12 * np.abs(want).max())
+
+
+def _atom_of(s):
+    out = []
+    for A, sp in enumerate(s.atom_species):
+        for f in range(s.species_fn_offset[sp], s.species_fn_offset[sp + 1]):
+            out += [A] * (2 * int(s.fn_l[f]) + 1)
+    return np.array(out)
+
+
+def _moved(s, A, c, d):
+    import copy
+
+    s2 = copy.copy(s)
+    ax = np.array(s.atom_xyz, dtype=float).copy()
+    ax[A, c] += d
+    s2.atom_xyz = ax
+    return Oracle(s2)
+
+
+def test_pulay_forces_routes_and_fixed_grid_derivatives(water):
+    """Local Pulay forces (Sec. 2): the matrix-element route 2 sum_{i in at} sum_j (n_ij M^c_ij - q_ij S^c_ij)
+    equals the point-by-point definition; with the grid held fixed, the q part is exactly
+    +d/dR tr(q S(R)) and the potential part (difference of two potentials, the kinetic part
+    cancels) exactly -d/dR tr(n H_pot(R)), checked by central differences."""
+    s, o = water
+    rng = np.random.Generator(np.random.PCG64(12))
+    v = s.potential()
+    P = synth.density_matrix(s, 3)
+    X = rng.normal(size=(o.nb, o.nb))
+    Q = (X + X.T) / 10
+    M, S, _, _ = o.pulay_matrices(s.pt_xyz, s.pt_w, v)
+    F = o.pulay_forces(s.pt_xyz, s.pt_w, v, P, Q)
+    at = _atom_of(s)
+    F2 = np.zeros_like(F)
+    for c in range(3):
+        r = 2 * ((P * M[c]).sum(1) - (Q * S[c]).sum(1))
+        for A in range(len(s.atom_species)):
+            F2[A, c] = r[at == A].sum()
+    assert np.allclose(F2, F, rtol=0, atol=1e-13 * np.abs(F).max())
+    h = 1e-5
+    zero = np.zeros_like(P)
+    Fq = o.pulay_forces(s.pt_xyz, s.pt_w, v, zero, Q)
+    v2 = v * 0.5 + 0.3
+    Fv = o.pulay_forces(s.pt_xyz, s.pt_w, v, P, zero) - o.pulay_forces(s.pt_xyz, s.pt_w, v2, P, zero)
+    for A in range(len(s.atom_species)):
+        for c in range(3):
+            op, om = _moved(s, A, c, h), _moved(s, A, c, -h)
+            Sp, _ = op.overlap(s.pt_xyz, s.pt_w)
+            Sm, _ = om.overlap(s.pt_xyz, s.pt_w)
+            dq = ((Q * Sp).sum() - (Q * Sm).sum()) / (2 * h)
+            assert abs(Fq[A, c] - dq) <= 1e-6 * (abs(dq) + np.abs(Fq).max() * 1e-3), (A, c)
+            Hp = op.hamiltonian(s.pt_xyz, s.pt_w, v, 1)[0] - op.hamiltonian(s.pt_xyz, s.pt_w, v2, 1)[0]
+            Hm = om.hamiltonian(s.pt_xyz, s.pt_w, v, 1)[0] - om.hamiltonian(s.pt_xyz, s.pt_w, v2, 1)[0]
+            dv = -((P * Hp).sum() - (P * Hm).sum()) / (2 * h)
+            assert abs(Fv[A, c] - dv) <= 1e-6 * (abs(dv) + np.abs(Fv).max() * 1e-3), (A, c)
