@@ -256,6 +256,22 @@ nao_status nao_update_density_gradient_many(nao_grid *g, const double *const *P_
 nao_status nao_update_density_hessian(nao_grid *g, const double *P_dev, nao_precision prec, double *n_dev,
                                       double *grad_dev, double *hess_dev, double *n_electrons_dev, void *cuda_stream);
 
+/* Local Pulay force terms (Sec. 2: F^{P,local}_at = -2 sum_ij int [grad_at phi_i] n_ij h_KS phi_j
+ * + 2 sum_ij int [grad_at phi_i] q_ij phi_j, q the energy-weighted density matrix), assembled from
+ * matrix elements with basis-function indices as the paper describes for forces:
+ *     M_dev[c*nb*nb + i*nb + j] = sum_p w_p d_c phi_i(r_p) (-1/2 lap + v_p) phi_j(r_p),
+ *     S_dev[c*nb*nb + i*nb + j] = sum_p w_p d_c phi_i(r_p) phi_j(r_p),        c = x, y, z,
+ * (not symmetric; both overwritten) from the basis functions' second derivatives, in FP64.
+ * v_dev: device [n_points] original order, or NULL for v = 1. Single-system handles; NAO_FP64
+ * only (others: NAO_ERR_UNSUPPORTED); scratch rules as nao_update_density_hessian.
+ * nao_pulay_forces: F_dev[3*a + c] = 2 sum_{i on atom a} sum_j (n_ij M^c_ij - q_ij S^c_ij)
+ * (grad_at phi_i = -grad phi_i for a function on atom a), n_dev and q_dev device [nb*nb]
+ * row-major, F_dev device [3*n_atoms], overwritten.                                            */
+nao_status nao_pulay_matrices(nao_grid *g, const double *v_dev, nao_precision prec, double *M_dev, double *S_dev,
+                              void *cuda_stream);
+nao_status nao_pulay_forces(nao_grid *g, const double *n_dev, const double *q_dev, const double *M_dev,
+                            const double *S_dev, double *F_dev, void *cuda_stream);
+
 /* The same two operations with HOST buffers: the library copies the inputs to the device,
  * runs the operation on the given stream, copies the results back and synchronises the
  * stream before returning. Host buffers may be pageable or pinned (pinned is faster).

@@ -262,6 +262,7 @@ nao_status build(nao_grid *g, const nao_system_desc *descs, int32_t n_sys, const
     g->n_fn = fn_base;
     g->nb = atom_basis.back();
     if (g->nb >= (int64_t(1) << 31)) return fail(NAO_ERR_INVALID_ARG, "too many basis functions");
+    g->atom_basis.assign(atom_basis.begin(), atom_basis.end());
     const int64_t n = (int64_t)wts.size();
     g->n_points = n;
 
@@ -1008,6 +1009,32 @@ nao_status hess_plan(nao_grid *g) {
     return NAO_OK;
 }
 
+// Local Pulay terms plan (after hess_plan): every 64 x 64 tile pair of every batch, in the order of
+// the Hessian chunks, and the atoms' basis offsets on the device.
+nao_status pulay_plan(nao_grid *g) {
+    if (g->d_pulay_work) return NAO_OK;
+    nao_status st;
+    if ((st = hess_plan(g))) return st;
+    std::vector<HWork> items;
+    g->pulay_w0.assign(1, 0);
+    for (const auto &c : g->hess_chunks) {
+        for (int32_t b = c.b0; b < c.b1; b++) {
+            const int nt = (g->Nb[b] + NAO_TILE - 1) / NAO_TILE;
+            for (int I = 0; I < nt; I++)
+                for (int J = 0; J < nt; J++) items.push_back({b, I, J, 0});
+        }
+        g->pulay_w0.push_back((int32_t)items.size());
+    }
+    if (items.empty()) items.push_back({0, 0, 0, 0});  // keeps the device array non-empty
+    if ((st = upload(g, &g->d_pulay_work, items.data(), items.size())) ||
+        (st = upload(g, &g->d_atom_basis, g->atom_basis.data(), g->atom_basis.size()))) {
+        g->d_pulay_work = nullptr;
+        return st;
+    }
+    NAO_CUDA(cudaStreamSynchronize(g->setup));
+    return NAO_OK;
+}
+
 }  // namespace
 
 void nao_set_last_error(const std::string &msg) { g_last_error = msg; }
@@ -1305,6 +1332,45 @@ nao_status nao_update_density_hessian(nao_grid *g, const double *P_dev, nao_prec
                                      g->d_ne_part, s));
     }
     if (n_electrons_dev) NAO_CUDA(launch_reduce_ne(sys, g->d_ne_part, g->d_sys_dw0, g->n_sys, s));
+    return mark_done(g, s);
+}
+
+nao_status nao_pulay_matrices(nao_grid *g, const double *v_dev, nao_precision prec, double *M_dev, double *S_dev,
+                              void *cuda_stream) {
+    nao_status st = check_handle(g);
+    if (st || (st = check_single(g))) return st;
+    if (!M_dev || !S_dev) return fail(NAO_ERR_INVALID_ARG, "M_dev or S_dev is NULL");
+    if ((st = check_prec(prec))) return st;
+    if (prec != NAO_FP64) return fail(NAO_ERR_UNSUPPORTED, "the Pulay matrix elements are built on the FP64 path only");
+    DeviceGuard guard(g->device);
+    if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    if ((st = pulay_plan(g))) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    set_tab(g, 1, 0, v_dev);
+    if ((st = upload_tables(g, 1, 1, s))) return st;
+    const size_t bytes = 3 * (size_t)g->nb * (size_t)g->nb * sizeof(double);
+    NAO_CUDA(cudaMemsetAsync(M_dev, 0, bytes, s));
+    NAO_CUDA(cudaMemsetAsync(S_dev, 0, bytes, s));
+    const DevSystem &sys = g->sys;
+    for (size_t k = 0; k < g->hess_chunks.size(); k++) {
+        const auto &c = g->hess_chunks[k];
+        NAO_CUDA(launch_eval_hess(sys, c.b0, c.b1, g->d_scratch, g->d_hess_off, s));
+        NAO_CUDA(launch_pulay(sys, g->d_pulay_work, g->pulay_w0[k], g->pulay_w0[k + 1] - g->pulay_w0[k], g->d_scratch,
+                              g->d_hess_off, M_dev, S_dev, g->nb, s));
+    }
+    return mark_done(g, s);
+}
+
+nao_status nao_pulay_forces(nao_grid *g, const double *n_dev, const double *q_dev, const double *M_dev,
+                            const double *S_dev, double *F_dev, void *cuda_stream) {
+    nao_status st = check_handle(g);
+    if (st || (st = check_single(g))) return st;
+    if (!n_dev || !q_dev || !M_dev || !S_dev || !F_dev) return fail(NAO_ERR_INVALID_ARG, "a buffer is NULL");
+    DeviceGuard guard(g->device);
+    if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    if ((st = pulay_plan(g))) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    NAO_CUDA(launch_pulay_forces(n_dev, q_dev, M_dev, S_dev, g->d_atom_basis, g->n_atoms, g->nb, F_dev, s));
     return mark_done(g, s);
 }
 

@@ -220,6 +220,11 @@ struct nao_grid {
     };
     std::vector<HessChunk> hess_chunks;
     int64_t *d_hess_off = nullptr;
+    // local Pulay force terms: every 64 x 64 tile pair of every batch, per Hessian chunk
+    std::vector<int64_t> atom_basis;         // [n_atoms + 1] first global basis index of each atom
+    std::vector<int32_t> pulay_w0;           // [hess_chunks + 1] work ranges
+    HWork *d_pulay_work = nullptr;
+    int64_t *d_atom_basis = nullptr;
     // tile width (MMA N) of every batch on the split path: a fixed rule until the autotuner has
     // timed both widths per (N_b, P_b) bucket of the batch-size histogram
     std::vector<int32_t> split_tn;
@@ -272,6 +277,14 @@ cudaError_t launch_eval_hess(const DevSystem &s, int32_t b0, int32_t b1, double 
                              cudaStream_t st);
 cudaError_t launch_density_hess(const DevSystem &s, const DWork *work, int32_t w0, int32_t n_work, const double *scratch,
                                 const int64_t *hoff, double *hess, double *ne_part, cudaStream_t st);
+// Local Pulay force terms (FP64): M^c += sum_q w d_c phi_i (-1/2 lap + v) phi_j and S^c += sum_q w
+// d_c phi_i phi_j over the full tile pairs of work items (batch, I, J) from the 10-row evaluation,
+// into M and S ([3][nb][nb], single system); and F[3 a + c] = 2 sum_{i on a} sum_j (n_ij M^c_ij -
+// q_ij S^c_ij).
+cudaError_t launch_pulay(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const double *scratch,
+                         const int64_t *hoff, double *M, double *S, int64_t nb, cudaStream_t st);
+cudaError_t launch_pulay_forces(const double *nmat, const double *qmat, const double *M, const double *S,
+                                const int64_t *atom_basis, int32_t n_atoms, int64_t nb, double *F, cudaStream_t st);
 cudaError_t launch_eval_one(const DevSystem &s, int32_t b, nao_precision prec, double *phi, double *grad,
                             cudaStream_t st);
 cudaError_t launch_h_simt(const DevSystem &s, nao_precision prec, const HWork *work, int32_t n_work,

@@ -34,7 +34,7 @@ SYMBOLS = [
     "nao_profile_enable", "nao_profile_read", "nao_integrate_h_noalloc",
     "nao_grid_create_many", "nao_get_system", "nao_integrate_h_many", "nao_update_density_many",
     "nao_get_tuning", "nao_update_density_gradient", "nao_update_density_gradient_many",
-    "nao_update_density_hessian", "nao_integrate_h_tau",
+    "nao_update_density_hessian", "nao_integrate_h_tau", "nao_pulay_matrices", "nao_pulay_forces",
 ]
 NAO_NOALLOC_SCRATCH_BYTES = 32 << 20
 KERNELS = ["eval_grad", "eval_phi", "h_fp64", "h_fp32", "h_split", "slice_h", "mirror", "n_fp64", "n_fp32",
@@ -114,6 +114,8 @@ def load():
         "nao_update_density_gradient": ([P, P, C.c_int, P, P, P, P], C.c_int),
         "nao_update_density_hessian": ([P, P, C.c_int, P, P, P, P, P], C.c_int),
         "nao_integrate_h_tau": ([P, P, P, C.c_uint32, C.c_int, P, P], C.c_int),
+        "nao_pulay_matrices": ([P, P, C.c_int, P, P, P], C.c_int),
+        "nao_pulay_forces": ([P, P, P, P, P, P, P], C.c_int),
         "nao_update_density_gradient_many": ([P, P, C.c_int, P, P, P, P], C.c_int),
     }
     for name, (args, res) in sig.items():
@@ -268,6 +270,16 @@ def nao_integrate_h_tau(h, v, vtau, terms: int, prec, H, stream=None) -> None:
            "nao_integrate_h_tau")
 
 
+def nao_pulay_matrices(h, v, prec, M, S, stream=None) -> None:
+    _check(load().nao_pulay_matrices(h, _dptr(v), _prec(prec), _dptr(M), _dptr(S), _stream(stream)),
+           "nao_pulay_matrices")
+
+
+def nao_pulay_forces(h, n, q, M, S, F, stream=None) -> None:
+    _check(load().nao_pulay_forces(h, _dptr(n), _dptr(q), _dptr(M), _dptr(S), _dptr(F), _stream(stream)),
+           "nao_pulay_forces")
+
+
 def nao_update_density(h, P, prec, n, ne=None, stream=None) -> None:
     _check(load().nao_update_density(h, _dptr(P), _prec(prec), _dptr(n), _dptr(ne), _stream(stream)),
            "nao_update_density")
@@ -375,6 +387,8 @@ class Grid:
         self.n_points = int(self.info.n_points)
         self.n_systems = int(self.info.n_systems)
         self.systems = [nao_get_system(self.h, m) for m in range(self.n_systems)]
+        sys_list = list(system) if isinstance(system, (list, tuple)) else [system]
+        self.n_atoms = sum(len(np.asarray(sy.atom_xyz).reshape(-1, 3)) for sy in sys_list)
 
     def close(self):
         if getattr(self, "h", None):
@@ -410,6 +424,26 @@ class Grid:
             H = torch.empty((self.nb, self.nb), dtype=torch.float64, device=self.device)
         nao_integrate_h_tau(self.h, v, vtau, terms, prec, H, stream)
         return H
+
+    def pulay_matrices(self, v=None, prec="fp64", M=None, S=None, stream=None):
+        """M [3, nb, nb] = sum_p w d_c phi_i (-1/2 lap + v) phi_j and S [3, nb, nb] = sum_p w d_c phi_i phi_j."""
+        import torch
+
+        if M is None:
+            M = torch.empty((3, self.nb, self.nb), dtype=torch.float64, device=self.device)
+        if S is None:
+            S = torch.empty((3, self.nb, self.nb), dtype=torch.float64, device=self.device)
+        nao_pulay_matrices(self.h, v, prec, M, S, stream)
+        return M, S
+
+    def pulay_forces(self, n, q, M, S, F=None, stream=None):
+        """Local Pulay forces [n_atoms, 3] from the matrix elements and the (energy-weighted) density matrices."""
+        import torch
+
+        if F is None:
+            F = torch.empty((self.n_atoms, 3), dtype=torch.float64, device=self.device)
+        nao_pulay_forces(self.h, n, q, M, S, F, stream)
+        return F
 
     def overlap(self, prec="fp64", S=None, stream=None):
         return self.integrate_h(None, NAO_TERM_POTENTIAL, prec, S, stream)
