@@ -537,15 +537,21 @@ def main():
             except nao.NaoError as e:
                 other[f"split_{d}_slices"] = {"unavailable": str(e)}
         line["other_precisions"] = other
-        # density derivatives (Sec. 2) on the same workload: the gradient (split and FP64) and the
-        # Hessian (FP64), one untimed and one timed call each
+        # the extensions on the same workload, one untimed and one timed call each: the density
+        # gradient (split, FP64) and Hessian (FP64), H with the meta-GGA term (split), the local
+        # Pulay matrix elements (FP64)
         deriv = {}
         gbuf = torch.empty((3, g.n_points), dtype=torch.float64, device=dev)
         hbuf = torch.empty((6, g.n_points), dtype=torch.float64, device=dev)
+        vtau = torch.full((g.n_points,), 0.25, dtype=torch.float64, device=dev)
+        mbuf = torch.empty((3, g.nb, g.nb), dtype=torch.float64, device=dev)
+        sbuf = torch.empty((3, g.nb, g.nb), dtype=torch.float64, device=dev)
         calls = {
             "gradient_split": lambda: g.density_gradient(P, prec="split", n=n, grad=gbuf, ne=ne, stream=stream),
             "gradient_fp64": lambda: g.density_gradient(P, prec="fp64", n=n, grad=gbuf, ne=ne, stream=stream),
             "hessian_fp64": lambda: g.density_hessian(P, prec="fp64", n=n, grad=gbuf, hess=hbuf, ne=ne, stream=stream),
+            "h_with_tau_split": lambda: g.integrate_h_tau(v, vtau, prec="split", H=H, stream=stream),
+            "pulay_matrices_fp64": lambda: g.pulay_matrices(v, prec="fp64", M=mbuf, S=sbuf, stream=stream),
         }
         for name, call in calls.items():
             try:
@@ -560,7 +566,7 @@ def main():
                 deriv[name] = {"ms": a.elapsed_time(b), "points_per_s": g.n_points / (a.elapsed_time(b) / 1e3)}
             except nao.NaoError as e:
                 deriv[name] = {"unavailable": str(e)}
-        line["density_derivatives"] = deriv
+        line["extensions"] = deriv
 
     if rank == 0 and world == 1 and not args.no_serve and args.serve_requests > 0:
         g.close()
