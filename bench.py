@@ -172,7 +172,7 @@ def serving(n_requests: int, device: int) -> dict:
 # contraction on the 8-atom profiling case (a launch's traffic grows with tiles x K, i.e. with
 # FLOP_H). Valid only for the kernel version and slice count the capture was taken with.
 TRAFFIC_PER_FLOP_H = {
-    ("h_split", 10): (24.957e9 / (2 * 9.1321260e10), "profiles/traffic_diamond64_split.md"),
+    ("h_split", 10): (24.984e9 / (2 * 9.1321260e10), "profiles/traffic_diamond64_split.md"),
     ("h_fp64", 0): ((359.834112e6 + 3.945472e6) / 4.6096304e9, "profiles/h_simt_kernel_diamond8_fp64.md"),
 }
 
