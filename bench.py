@@ -372,7 +372,7 @@ def main():
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     __graft_entry__.build()
-    from paper_1912_06636_gb300 import nao
+    from paper_1912_06636_gb300 import nao, replicas
 
     prec = args.prec or "split"
     s, v_np, P_np = make_workload(args.config, f"cuda:{local_rank}", args.cells)
@@ -421,11 +421,8 @@ def main():
     g.sync()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = evs[0][0].elapsed_time(evs[-1][1])
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps * g.n_points / (total_ms / 1e3)
+    # all ranks' points over the slowest rank's time (replicas: no data-path collective)
+    value, total_ms, _ = replicas.aggregate(args.steps * g.n_points, total_ms, dev)
     bo, _, ro, _ = g.batches()
     Pb, Nb = np.diff(bo), np.diff(ro)
     Ppad = (Pb + 15) // 16 * 16
