@@ -33,7 +33,7 @@ def _worker(rank, world, port, units, ms, out):
 def test_aggregate_two_ranks():
     world = 2
     units, ms = [1000.0, 3000.0], [250.0, 400.0]
-    with mp.Manager() as man:
+    with mp.get_context("spawn").Manager() as man:
         out = man.dict()
         mp.spawn(_worker, args=(world, _free_port(), units, ms, out), nprocs=world, join=True)
         res = dict(out)
