@@ -30,9 +30,6 @@ __device__ __forceinline__ int exponent_of_binade(int eb) {
     return ex < -900 ? -10000 : ex + 1;
 }
 
-// The same from the bit pattern of max (abs_bits).
-__device__ __forceinline__ int row_exponent_bits(long long mb) { return exponent_of_binade((int)(mb >> 52)); }
-
 // d_k of the Hamiltonian's column k = (component c, batch-ordered point p): w v on the potential
 // part (c = 0), w (kappa + v_tau) / 2 on the three gradient parts (Eq. H_decomp; kappa = 1 with
 // the kinetic term, v_tau with the meta-GGA term), 0 for a term that is off; the column's scale

@@ -39,7 +39,6 @@ constexpr long long kWaitCycles = 400000000LL;  // ~0.2 s at 2 GHz: bounded mbar
 // pipe is ~1/60 of the FP32 rate, and a double-to-int64 conversion per element would make the
 // slicing kernels FP64-bound.
 using split_bits::abs_bits;
-using split_bits::row_exponent_bits;
 
 // S balanced base-64 digits (most significant first in dig[0]) of X = round(x 2^(6S-e)),
 // |x 2^-e| < 1/2, as exact small-integer floats. From x's bits x = +-m 2^(E-1075) (53-bit m):
