@@ -90,6 +90,8 @@ def _load():
         lib.or_pulay_matrices.restype = C.c_int
         lib.or_pulay_forces.argtypes = [P, I64, P, P, P, P, P, P]
         lib.or_pulay_forces.restype = C.c_int
+        lib.or_periodic_h.argtypes = [P, P, I32, I64, P, P, P, P, C.c_uint32, P, P]
+        lib.or_periodic_h.restype = C.c_int
         lib.or_bruteforce.argtypes = [P, I64, P, P, P, P, P, P, P]
         lib.or_bruteforce.restype = C.c_int
         lib.or_partition.argtypes = [I64, P, I64, P, P]
@@ -308,6 +310,20 @@ class Oracle:
         _check(self.lib.or_pulay_forces(self.sp, pts.shape[0], _ptr(pts), _ptr(w), _ptr(v), _ptr(nmat), _ptr(qmat),
                                         _ptr(F)), "pulay_forces")
         return F
+
+    def periodic_h(self, lattice, nrange, pts, w, k, v=None, terms=TERM_POTENTIAL | TERM_KINETIC):
+        """h(k) [nb, nb] complex of the unit cell described by this oracle's system (Bloch basis
+        summed over the translations |n_c| <= nrange) and the magnitude sums [nb, nb]."""
+        lattice = np.ascontiguousarray(lattice, dtype=np.float64).reshape(3, 3)
+        pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        v = None if v is None else np.ascontiguousarray(v, dtype=np.float64)
+        k = np.ascontiguousarray(k, dtype=np.float64).reshape(3)
+        H = np.zeros((self.nb, self.nb, 2))
+        A = np.zeros((self.nb, self.nb))
+        _check(self.lib.or_periodic_h(self.sp, _ptr(lattice), int(nrange), pts.shape[0], _ptr(pts), _ptr(w), _ptr(v),
+                                      _ptr(k), int(terms), _ptr(H), _ptr(A)), "periodic_h")
+        return H[..., 0] + 1j * H[..., 1], A
 
     def bruteforce(self, pts, w, v, P):
         pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)

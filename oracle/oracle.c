@@ -791,6 +791,79 @@ done2:
     return status;
 }
 
+/* Periodic Hamiltonian at crystal momentum k (Eq. HamPeriodic with the Bloch basis of
+ * Eq. Bloch-basis, chi_ik(r) = sum_T e^{i k.T} phi_i(r - T)), directly from its definition: at
+ * every point r of the unit cell the Bloch functions and their gradients are summed over the
+ * lattice translations T = n1 a1 + n2 a2 + n3 a3, |n_c| <= nrange, then
+ *     h_ij(k) = sum_p w_p [ conj(chi_i) v chi_j (POTENTIAL) + 1/2 conj(grad chi_i) . grad chi_j (KINETIC) ]
+ * over the unit cell's points. S describes the unit cell's atoms and basis; lattice = rows a1, a2,
+ * a3. Hk[2 (i nb + j)] = (re, im); Ak the sums of the term magnitudes (may be NULL).           */
+int or_periodic_h(const or_sys *S, const double *lattice, int32_t nrange, int64_t n_pts, const double *pts,
+                  const double *w, const double *v, const double *k, uint32_t terms, double *Hk, double *Ak) {
+    int64_t nb = or_n_basis(S);
+    size_t n1 = (size_t)(nb ? nb : 1);
+    int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * n1);
+    double *phi = (double *)malloc(sizeof(double) * n1), *grad = (double *)malloc(sizeof(double) * 3 * n1);
+    double *cr = (double *)malloc(sizeof(double) * n1), *ci = (double *)malloc(sizeof(double) * n1);
+    double *gr = (double *)malloc(sizeof(double) * 3 * n1), *gi = (double *)malloc(sizeof(double) * 3 * n1);
+    double *cH = (double *)calloc(2 * n1 * n1, sizeof(double));
+    int64_t pole = 0;
+    int status = 0;
+    int pot = (terms & 1u) != 0, kin = (terms & 2u) != 0;
+    if (!idx || !phi || !grad || !cr || !ci || !gr || !gi || !cH) { status = -1; goto done3; }
+    memset(Hk, 0, 2 * (size_t)nb * (size_t)nb * sizeof(double));
+    if (Ak) memset(Ak, 0, (size_t)nb * (size_t)nb * sizeof(double));
+    for (int64_t p = 0; p < n_pts; p++) {
+        for (int64_t a = 0; a < nb; a++) { cr[a] = ci[a] = 0.0; gr[3 * a] = gr[3 * a + 1] = gr[3 * a + 2] = 0.0; gi[3 * a] = gi[3 * a + 1] = gi[3 * a + 2] = 0.0; }
+        for (int n0 = -nrange; n0 <= nrange; n0++)
+            for (int n1_ = -nrange; n1_ <= nrange; n1_++)
+                for (int n2 = -nrange; n2 <= nrange; n2++) {
+                    double T[3];
+                    for (int c = 0; c < 3; c++) T[c] = n0 * lattice[c] + n1_ * lattice[3 + c] + n2 * lattice[6 + c];
+                    double q[3] = {pts[3 * p] - T[0], pts[3 * p + 1] - T[1], pts[3 * p + 2] - T[2]};
+                    int64_t cnt = point_basis(S, q, idx, phi, grad, &pole, 0);
+                    if (cnt < 0) { status = (int)cnt; goto done3; }
+                    double ph = k[0] * T[0] + k[1] * T[1] + k[2] * T[2];
+                    double c_ = cos(ph), s_ = sin(ph);
+                    for (int64_t a = 0; a < cnt; a++) {
+                        int64_t i = idx[a];
+                        cr[i] += c_ * phi[a];
+                        ci[i] += s_ * phi[a];
+                        for (int c = 0; c < 3; c++) { gr[3 * i + c] += c_ * grad[3 * a + c]; gi[3 * i + c] += s_ * grad[3 * a + c]; }
+                    }
+                }
+        double wp = w[p], vp = v ? v[p] : 1.0;
+        for (int64_t i = 0; i < nb; i++)
+            for (int64_t j = 0; j < nb; j++) {
+                /* conj(x_i) y_j = (xr - i xi)(yr + i yi) */
+                double tr = 0.0, ti = 0.0, ta = 0.0;
+                if (pot) {
+                    double re = cr[i] * cr[j] + ci[i] * ci[j], im = cr[i] * ci[j] - ci[i] * cr[j];
+                    tr += wp * vp * re; ti += wp * vp * im;
+                    ta += fabs(wp * vp) * sqrt(cr[i] * cr[i] + ci[i] * ci[i]) * sqrt(cr[j] * cr[j] + ci[j] * ci[j]);
+                }
+                if (kin) {
+                    double re = 0.0, im = 0.0, mag = 0.0;
+                    for (int c = 0; c < 3; c++) {
+                        re += gr[3 * i + c] * gr[3 * j + c] + gi[3 * i + c] * gi[3 * j + c];
+                        im += gr[3 * i + c] * gi[3 * j + c] - gi[3 * i + c] * gr[3 * j + c];
+                        mag += sqrt(gr[3 * i + c] * gr[3 * i + c] + gi[3 * i + c] * gi[3 * i + c]) *
+                               sqrt(gr[3 * j + c] * gr[3 * j + c] + gi[3 * j + c] * gi[3 * j + c]);
+                    }
+                    tr += 0.5 * wp * re; ti += 0.5 * wp * im; ta += 0.5 * fabs(wp) * mag;
+                }
+                size_t e = (size_t)i * (size_t)nb + (size_t)j;
+                neu_add(&Hk[2 * e], &cH[2 * e], tr);
+                neu_add(&Hk[2 * e + 1], &cH[2 * e + 1], ti);
+                if (Ak) Ak[e] += ta;
+            }
+    }
+    for (size_t e = 0; e < 2 * (size_t)nb * (size_t)nb; e++) Hk[e] += cH[e];
+done3:
+    free(idx); free(phi); free(grad); free(cr); free(ci); free(gr); free(gi); free(cH);
+    return status;
+}
+
 /* Brute force for tiny inputs: phi for every basis function at every point (zeros
  * included) and a triple loop over p, i, j, with no batching and no relevance pruning.   */
 int or_bruteforce(const or_sys *S, int64_t n_pts, const double *pts, const double *w, const double *v,

@@ -410,3 +410,49 @@ def config(k: int, **kw) -> System:
     if k == 2:
         return config_slab375(**kw)
     raise ValueError(f"unknown configuration {k}")
+
+
+# ---------------------------------------------------------------------------------------
+# Periodic cells (Eq. HamPeriodic): the unit cell's atoms and a uniform grid of its points.
+# ---------------------------------------------------------------------------------------
+def periodic_cell(lattice, frac_positions, species_of_atom, species: list, n_grid=12,
+                  n_rgrid: int = NRGRID_DEFAULT, r0: float = R0_DEFAULT, r_last: float = RLAST_DEFAULT,
+                  max_batch_points: int = 200) -> System:
+    """Unit cell with lattice rows a1, a2, a3 (bohr) and atoms at fractional positions. The grid is
+    the periodic trapezoid rule of the cell, fractional coordinates (i + 1/2) / n on each axis
+    (n_grid: one n, or one per axis), weight V / (n1 n2 n3) (exact for trigonometric polynomials of degree < n_grid, so spectrally
+    accurate for smooth periodic integrands); meta["lattice"] holds the lattice."""
+    A = np.asarray(lattice, dtype=np.float64).reshape(3, 3)
+    fr = np.asarray(frac_positions, dtype=np.float64).reshape(-1, 3)
+    atoms = fr @ A
+    sys0 = make_system(atoms, species_of_atom, species, n_rad=1, n_theta=1, n_phi=1, n_rgrid=n_rgrid, r0=r0,
+                       r_last=r_last, max_batch_points=max_batch_points, name="periodic-cell")
+    ng = (n_grid,) * 3 if np.isscalar(n_grid) else tuple(int(x) for x in n_grid)
+    u = [(np.arange(n) + 0.5) / n for n in ng]
+    f = np.stack(np.meshgrid(*u, indexing="ij"), axis=-1).reshape(-1, 3)
+    sys0.pt_xyz = np.ascontiguousarray(f @ A)
+    sys0.pt_w = np.full(f.shape[0], abs(np.linalg.det(A)) / float(np.prod(ng)))
+    sys0.meta["lattice"] = A
+    return sys0
+
+
+def periodic_potential(sys0: System, pts=None) -> np.ndarray:
+    """A smooth lattice-periodic potential: v = -1 + 0.3 cos(2 pi f1) + 0.2 sin(2 pi f2) + 0.1 cos(2 pi (f1 + f3))
+    with f the fractional coordinates of the points."""
+    A = sys0.meta["lattice"]
+    f = np.asarray(sys0.pt_xyz if pts is None else pts) @ np.linalg.inv(A)
+    t = 2 * np.pi * f
+    return -1.0 + 0.3 * np.cos(t[:, 0]) + 0.2 * np.sin(t[:, 1]) + 0.1 * np.cos(t[:, 0] + t[:, 2])
+
+
+def image_system(sys0: System, img_xyz, img_atom) -> System:
+    """The unit cell's grid with the periodic images of its atoms as the atoms (the real-space
+    system whose Hamiltonian is h^uc): img_atom[k] is the unit-cell atom of image k."""
+    import copy
+
+    s = copy.copy(sys0)
+    s.atom_xyz = np.ascontiguousarray(np.asarray(img_xyz, dtype=np.float64).reshape(-1, 3))
+    s.atom_species = np.ascontiguousarray(np.asarray(sys0.atom_species)[np.asarray(img_atom)], dtype=np.int32)
+    s.Z = np.asarray(sys0.Z)[np.asarray(img_atom)]
+    s.name = sys0.name + "-images"
+    return s

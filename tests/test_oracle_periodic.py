@@ -1,0 +1,68 @@
+"""Pins for the oracle's periodic Hamiltonian h(k) (Eq. HamPeriodic with the Bloch basis of
+Eq. Bloch-basis), computed point by point from the Bloch functions:
+  * h(k) is Hermitian, h(-k) = conj(h(k)), and h(k + G) = h(k) for reciprocal vectors G
+    (e^{i G.T} = 1): a wrong translation or phase argument fails these;
+  * the translation sum has converged (one more shell of cells changes nothing);
+  * supercell identity: with a lattice-periodic potential and matching grids, the generalised
+    spectrum of a cell doubled along a1 at k = 0 is the union of the unit cell's spectra at k = 0
+    and k = b1 / 2 (Bloch's theorem), which fixes the Bloch sum, its normalisation per cell and
+    the overlap together.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from oracle import TERM_POTENTIAL, Oracle
+from paper_1912_06636_gb300 import synth
+
+LAT = np.diag([6.0, 6.5, 7.0]) + np.array([[0, 0, 0], [0.8, 0, 0], [0, 0.5, 0]])
+SPECIES = [synth.Species(ls=[0, 1], alphas=[1.0, 0.8], rc=4.0, Z=1.0),
+           synth.Species(ls=[0, 0, 1, 2], alphas=[2.0, 0.7, 1.1, 0.9], rc=4.5, Z=2.0)]
+FRAC = [[0.11, 0.23, 0.31], [0.57, 0.61, 0.72]]
+
+
+@pytest.fixture(scope="module")
+def cell():
+    s = synth.periodic_cell(LAT, FRAC, [0, 1], SPECIES, n_grid=10)
+    return s, Oracle(s)
+
+
+def test_hermitian_time_reversal_and_reciprocal_shift(cell):
+    s, o = cell
+    v = synth.periodic_potential(s)
+    B = 2 * np.pi * np.linalg.inv(LAT).T
+    k = np.array([0.31, -0.17, 0.12])
+    H, A = o.periodic_h(LAT, 2, s.pt_xyz, s.pt_w, k, v)
+    scale = np.abs(A).max()
+    assert np.abs(H).max() > 1e-3 * scale
+    assert np.allclose(H, H.conj().T, rtol=0, atol=1e-15 * scale)
+    Hm, _ = o.periodic_h(LAT, 2, s.pt_xyz, s.pt_w, -k, v)
+    assert np.allclose(Hm, H.conj(), rtol=0, atol=1e-15 * scale)
+    for G in (B[0], B[1] - B[2], 2 * B[2]):
+        HG, _ = o.periodic_h(LAT, 2, s.pt_xyz, s.pt_w, k + G, v)
+        assert np.allclose(HG, H, rtol=0, atol=1e-13 * scale)
+    H3, _ = o.periodic_h(LAT, 3, s.pt_xyz, s.pt_w, k, v)
+    assert np.allclose(H3, H, rtol=0, atol=1e-15 * scale)
+
+
+def test_supercell_spectrum_is_union_of_k_spectra():
+    n = (6, 6, 6)
+    s = synth.periodic_cell(LAT, FRAC, [0, 1], SPECIES, n_grid=n)
+    o = Oracle(s)
+    Lsc = LAT.copy()
+    Lsc[0] *= 2
+    frac_sc = [[f[0] / 2, f[1], f[2]] for f in FRAC] + [[(f[0] + 1) / 2, f[1], f[2]] for f in FRAC]
+    ssc = synth.periodic_cell(Lsc, frac_sc, [0, 1, 0, 1], SPECIES, n_grid=(2 * n[0], n[1], n[2]))
+    osc = Oracle(ssc)
+    B = 2 * np.pi * np.linalg.inv(LAT).T
+    ev = []
+    for k in (np.zeros(3), B[0] / 2):
+        h, _ = o.periodic_h(LAT, 2, s.pt_xyz, s.pt_w, k, synth.periodic_potential(s))
+        sm, _ = o.periodic_h(LAT, 2, s.pt_xyz, s.pt_w, k, None, TERM_POTENTIAL)
+        ev.append(sla.eigh(h, sm, eigvals_only=True))
+    hsc, _ = osc.periodic_h(Lsc, 2, ssc.pt_xyz, ssc.pt_w, np.zeros(3), synth.periodic_potential(s, ssc.pt_xyz))
+    ssm, _ = osc.periodic_h(Lsc, 2, ssc.pt_xyz, ssc.pt_w, np.zeros(3), None, TERM_POTENTIAL)
+    esc = sla.eigh(hsc, ssm, eigvals_only=True)
+    want = np.sort(np.concatenate(ev))
+    assert esc.shape == want.shape
+    assert np.allclose(np.sort(esc), want, rtol=0, atol=1e-10 * np.abs(want).max())
