@@ -272,6 +272,37 @@ nao_status nao_pulay_matrices(nao_grid *g, const double *v_dev, nao_precision pr
 nao_status nao_pulay_forces(nao_grid *g, const double *n_dev, const double *q_dev, const double *M_dev,
                             const double *S_dev, double *F_dev, void *cuda_stream);
 
+/* Periodic systems (Eq. HamPeriodic, Eq. RealSpaceHamPeriodic, Eq. Bloch-basis). The real-space
+ * matrix h^uc over the N_rs functions that can be non-zero in the unit cell is integrated by the
+ * same code as a finite system: a handle whose atoms are the periodic images of the cell's atoms
+ * and whose points are the unit cell's points (nao_integrate_h gives h^uc, NAO_TERM_POTENTIAL with
+ * v = 1 gives s^uc).
+ * nao_periodic_images (host): the images R_A + n1 a1 + n2 a2 + n3 a3 of the atoms atom_xyz
+ * [n_atoms*3] whose fractional coordinates lie within `reach` (bohr; the largest cutoff radius)
+ * of the cell [0, 1)^3 along every lattice direction (a superset of the images whose functions
+ * reach the cell; the handle's relevance step drops the rest), the atoms themselves (n = 0) first.
+ * lattice: host [9], rows a1, a2, a3. Outputs (host, caller-allocated, max_images entries):
+ * img_xyz [3*n], img_atom [n] (the unit-cell atom), img_cell [3*n] (n1, n2, n3); *n_images = n.
+ * n > max_images: NAO_ERR_INVALID_ARG with *n_images set (call again with room).
+ * nao_periodic_basis_map (host): for the image system's basis (image atom -> radial function -> m),
+ * fn_map[r] = the unit-cell basis index and fn_image[r] = the image of each of its N_rs functions;
+ * *n_rs = N_rs (> max_rs: NAO_ERR_INVALID_ARG with *n_rs set).
+ * nao_bloch_sum (GPU): hk_dev[2*((q*nb + i)*nb + j) + {0, 1}] = (re, im) of
+ *     h_ij(k_q) = sum_{r -> i, s -> j} h_uc[r*n_rs + s] e^{i k_q . (T_s - T_r)},  T = img_cell A,
+ * for the n_k points k_dev [n_k*3] (cartesian, 1/bohr): Eq. Bloch-basis inserted into
+ * Eq. HamPeriodic. h_uc_dev [n_rs*n_rs], fn_map_dev/fn_image_dev [n_rs], img_cell_dev [3*n_images]
+ * on the device; lattice on the host; hk_dev overwritten. FP64 atomics (one per element and k).
+ * Errors: NAO_ERR_INVALID_ARG, NAO_ERR_CUDA.                                                      */
+nao_status nao_periodic_images(const double *atom_xyz, int32_t n_atoms, const double *lattice, double reach,
+                               int32_t max_images, double *img_xyz, int32_t *img_atom, int32_t *img_cell,
+                               int32_t *n_images);
+nao_status nao_periodic_basis_map(const int32_t *atom_species, int32_t n_atoms, const int32_t *species_fn_offset,
+                                  int32_t n_species, const int32_t *fn_l, const int32_t *img_atom, int32_t n_images,
+                                  int64_t max_rs, int32_t *fn_map, int32_t *fn_image, int64_t *n_rs);
+nao_status nao_bloch_sum(const double *h_uc_dev, int64_t n_rs, const int32_t *fn_map_dev, const int32_t *fn_image_dev,
+                         const int32_t *img_cell_dev, const double *lattice, const double *k_dev, int32_t n_k, int64_t nb,
+                         double *hk_dev, void *cuda_stream);
+
 /* The same two operations with HOST buffers: the library copies the inputs to the device,
  * runs the operation on the given stream, copies the results back and synchronises the
  * stream before returning. Host buffers may be pageable or pinned (pinned is faster).

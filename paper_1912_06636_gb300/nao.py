@@ -35,6 +35,7 @@ SYMBOLS = [
     "nao_grid_create_many", "nao_get_system", "nao_integrate_h_many", "nao_update_density_many",
     "nao_get_tuning", "nao_update_density_gradient", "nao_update_density_gradient_many",
     "nao_update_density_hessian", "nao_integrate_h_tau", "nao_pulay_matrices", "nao_pulay_forces",
+    "nao_periodic_images", "nao_periodic_basis_map", "nao_bloch_sum",
 ]
 NAO_NOALLOC_SCRATCH_BYTES = 32 << 20
 KERNELS = ["eval_grad", "eval_phi", "h_fp64", "h_fp32", "h_split", "slice_h", "mirror", "n_fp64", "n_fp32",
@@ -117,6 +118,9 @@ def load():
         "nao_pulay_matrices": ([P, P, C.c_int, P, P, P], C.c_int),
         "nao_pulay_forces": ([P, P, P, P, P, P, P], C.c_int),
         "nao_update_density_gradient_many": ([P, P, C.c_int, P, P, P, P], C.c_int),
+        "nao_periodic_images": ([P, I32, P, C.c_double, I32, P, P, P, P], C.c_int),
+        "nao_periodic_basis_map": ([P, I32, P, I32, P, P, I32, I64, P, P, P], C.c_int),
+        "nao_bloch_sum": ([P, I64, P, P, P, P, P, I32, I64, P, P], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -278,6 +282,55 @@ def nao_pulay_matrices(h, v, prec, M, S, stream=None) -> None:
 def nao_pulay_forces(h, n, q, M, S, F, stream=None) -> None:
     _check(load().nao_pulay_forces(h, _dptr(n), _dptr(q), _dptr(M), _dptr(S), _dptr(F), _stream(stream)),
            "nao_pulay_forces")
+
+
+def nao_periodic_images(atom_xyz, lattice, reach: float):
+    """Periodic images of the cell's atoms that can reach the cell (host): (xyz [n, 3], unit-cell
+    atom [n], cell [n, 3]), the atoms themselves first."""
+    lib = load()
+    x = np.ascontiguousarray(atom_xyz, dtype=np.float64).reshape(-1, 3)
+    A = np.ascontiguousarray(lattice, dtype=np.float64).reshape(9)
+    n = C.c_int32(0)
+    lib.nao_periodic_images(x.ctypes.data, x.shape[0], A.ctypes.data, float(reach), 0, None, None, None, C.byref(n))
+    xyz = np.zeros((max(n.value, 1), 3))
+    atom = np.zeros(max(n.value, 1), dtype=np.int32)
+    cell = np.zeros((max(n.value, 1), 3), dtype=np.int32)
+    _check(lib.nao_periodic_images(x.ctypes.data, x.shape[0], A.ctypes.data, float(reach), n.value, xyz.ctypes.data,
+                                   atom.ctypes.data, cell.ctypes.data, C.byref(n)), "nao_periodic_images")
+    return xyz[:n.value], atom[:n.value], cell[:n.value]
+
+
+def nao_periodic_basis_map(system, img_atom):
+    """(fn_map, fn_image) of the image system's N_rs functions (host int32 arrays)."""
+    lib = load()
+    sp = np.ascontiguousarray(system.atom_species, dtype=np.int32)
+    off = np.ascontiguousarray(system.species_fn_offset, dtype=np.int32)
+    fl = np.ascontiguousarray(system.fn_l, dtype=np.int32)
+    ia = np.ascontiguousarray(img_atom, dtype=np.int32)
+    n = C.c_int64(0)
+    lib.nao_periodic_basis_map(sp.ctypes.data, len(sp), off.ctypes.data, len(off) - 1, fl.ctypes.data, ia.ctypes.data,
+                               len(ia), 0, None, None, C.byref(n))
+    fm = np.zeros(max(n.value, 1), dtype=np.int32)
+    fi = np.zeros(max(n.value, 1), dtype=np.int32)
+    _check(lib.nao_periodic_basis_map(sp.ctypes.data, len(sp), off.ctypes.data, len(off) - 1, fl.ctypes.data,
+                                      ia.ctypes.data, len(ia), n.value, fm.ctypes.data, fi.ctypes.data, C.byref(n)),
+           "nao_periodic_basis_map")
+    return fm[:n.value], fi[:n.value]
+
+
+def nao_bloch_sum(h_uc, fn_map, fn_image, img_cell, lattice, kpts, nb: int, stream=None):
+    """h(k) [n_k, nb, nb] complex from h^uc [n_rs, n_rs] (CUDA tensors; the index arrays int32)."""
+    import torch
+
+    A = np.ascontiguousarray(lattice, dtype=np.float64).reshape(9)
+    k = kpts.contiguous()
+    hk = torch.empty((k.shape[0], nb, nb, 2), dtype=torch.float64, device=h_uc.device)
+    for t in (fn_map, fn_image, img_cell):
+        if not t.is_cuda or t.dtype != torch.int32 or not t.is_contiguous():
+            raise ValueError("index arrays must be contiguous int32 CUDA tensors")
+    _check(load().nao_bloch_sum(_dptr(h_uc), h_uc.shape[0], fn_map.data_ptr(), fn_image.data_ptr(), img_cell.data_ptr(),
+                                A.ctypes.data, _dptr(k), k.shape[0], int(nb), _dptr(hk), _stream(stream)), "nao_bloch_sum")
+    return torch.view_as_complex(hk)
 
 
 def nao_update_density(h, P, prec, n, ne=None, stream=None) -> None:

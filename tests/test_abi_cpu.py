@@ -99,6 +99,7 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.nao_integrate_h_tau(None, None, None, 7, 0, None, None) == 1
     assert lib.nao_pulay_matrices(None, None, 0, None, None, None) == 1
     assert lib.nao_pulay_forces(None, None, None, None, None, None, None) == 1
+    assert lib.nao_bloch_sum(None, 0, None, None, None, None, None, 0, 0, None, None) == 1
     info = nao.GridInfo()
     assert lib.nao_get_info(None, C.byref(info)) == 1
     out = C.c_void_p(123)
