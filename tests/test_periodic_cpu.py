@@ -59,3 +59,17 @@ def test_basis_map_and_buffer_sizes():
     n = C.c_int32(0)
     assert lib.nao_periodic_images(x.ctypes.data, s.n_atoms, A.ctypes.data, 4.5, 1, None, None, None, C.byref(n)) != 0
     assert n.value == len(atom)
+
+
+def test_periodic_grid_is_the_trapezoid_rule_of_the_cell():
+    """Weights sum to the cell volume; a lattice-periodic trigonometric polynomial of degree below
+    the grid size integrates to its exact mean times the volume (here: the constant term)."""
+    s = synth.periodic_cell(LAT, FRAC, [0, 1], SPECIES, n_grid=(8, 9, 10))
+    V = abs(np.linalg.det(LAT))
+    assert np.isclose(s.pt_w.sum(), V, rtol=1e-14)
+    f = s.pt_xyz @ np.linalg.inv(LAT)
+    t = 2 * np.pi * f
+    g = 0.7 + np.cos(3 * t[:, 0]) * np.sin(2 * t[:, 1]) + np.cos(t[:, 0] - 4 * t[:, 2]) + np.sin(5 * t[:, 1])
+    assert abs(np.dot(s.pt_w, g) - 0.7 * V) <= 1e-12 * V
+    v = synth.periodic_potential(s)
+    assert abs(np.dot(s.pt_w, v) - (-1.0) * V) <= 1e-12 * V
