@@ -6,7 +6,9 @@ and shares no code with the CUDA library. See ``oracle.c`` for what each functio
 and which equation of the paper it follows.
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests in
-``tests/test_oracle_*.py`` (closed forms, library routines, invariants, brute force).
+``tests/test_oracle_*.py`` (closed forms, library routines, invariants, brute force), and
+``tests/test_mutants_oracle.py`` checks that those pins catch plausible mistakes planted in copies
+of ``oracle.c``.
 """
 from __future__ import annotations
 
@@ -53,10 +55,13 @@ class _Sys(C.Structure):
 
 
 def _load():
+    """Load the oracle library: liboracle.so built from oracle.c, or the prebuilt library that
+    the environment variable NAO_ORACLE_LIB names (the mutation tests load copies of oracle.c
+    with one planted mistake each this way)."""
     global _lib
     if _lib is None:
-        build()
-        lib = C.CDLL(str(_LIB))
+        override = os.environ.get("NAO_ORACLE_LIB")
+        lib = C.CDLL(override if override else str(build()))
         P, I64, I32, D = C.c_void_p, C.c_int64, C.c_int32, C.c_double
         lib.or_spline_M.argtypes = [P, I32, P]
         lib.or_spline_M.restype = C.c_int

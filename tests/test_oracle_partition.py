@@ -62,6 +62,29 @@ def test_points_inside_a_batch_are_ordered_along_an_axis():
         assert any(np.all(np.diff(q[:, c]) >= 0) for c in range(3))
 
 
+def test_partition_left_part_is_rounded_down():
+    """Worked by hand from the rule. Five points on a line, B = 2: k = 3, the left part holds
+    floor(5 * 1 / 3) = 1 point; the remaining four give k = 2 and floor(4 * 1 / 2) = 2. With 201
+    points and B = 200 the cut is floor(201 / 2) = 100."""
+    x = np.array([3.0, 0.0, 4.0, 1.0, 2.0])
+    pts = np.stack([x, np.zeros(5), np.zeros(5)], 1)
+    off, perm = Oracle.partition(pts, 2)
+    assert off.tolist() == [0, 1, 3, 5]
+    assert perm.tolist() == [1, 3, 4, 0, 2]
+    line = np.stack([np.arange(201.0), np.zeros(201), np.zeros(201)], 1)
+    off, perm = Oracle.partition(line, 200)
+    assert off.tolist() == [0, 100, 201] and perm.tolist() == list(range(201))
+
+
+def test_equal_coordinates_keep_index_order():
+    """Worked by hand from the rule: equal coordinates along the cut axis are ordered by point
+    index. The x extent (1) is the largest, so the cut is along x; the sorted order is
+    (x=0: points 1, 3), (x=1: points 0, 2)."""
+    pts = np.array([[1.0, 0.0, 0.0], [0.0, 0.1, 0.0], [1.0, 0.2, 0.0], [0.0, 0.3, 0.0]])
+    off, perm = Oracle.partition(pts, 2)
+    assert off.tolist() == [0, 2, 4] and perm.tolist() == [1, 3, 0, 2]
+
+
 def _brute_relevance(sys, pts, off, perm):
     rel_off, rel = [0], []
     for b in range(len(off) - 1):

@@ -15,7 +15,18 @@ import scipy.linalg as sla
 from oracle import TERM_POTENTIAL, Oracle
 from paper_1912_06636_gb300 import synth
 
-LAT = np.diag([6.0, 6.5, 7.0]) + np.array([[0, 0, 0], [0.8, 0, 0], [0, 0.5, 0]])
+
+
+def _rotation(axis, angle):
+    """Rotation matrix about a unit axis (Rodrigues' formula)."""
+    u = np.asarray(axis, dtype=np.float64) / np.linalg.norm(axis)
+    K = np.array([[0, -u[2], u[1]], [u[2], 0, -u[0]], [-u[1], u[0], 0]])
+    return np.eye(3) + np.sin(angle) * K + (1 - np.cos(angle)) * (K @ K)
+
+
+# a skewed cell turned so that no lattice vector lies along a coordinate axis: a mistake that
+# mirrors one Cartesian component of the translations then maps no lattice vector onto another
+LAT = (np.diag([6.0, 6.5, 7.0]) + np.array([[0, 0, 0], [0.8, 0, 0], [0, 0.5, 0]])) @ _rotation([0.3, -0.5, 0.8], 0.7).T
 SPECIES = [synth.Species(ls=[0, 1], alphas=[1.0, 0.8], rc=4.0, Z=1.0),
            synth.Species(ls=[0, 0, 1, 2], alphas=[2.0, 0.7, 1.1, 0.9], rc=4.5, Z=2.0)]
 FRAC = [[0.11, 0.23, 0.31], [0.57, 0.61, 0.72]]
@@ -66,3 +77,31 @@ def test_supercell_spectrum_is_union_of_k_spectra():
     want = np.sort(np.concatenate(ev))
     assert esc.shape == want.shape
     assert np.allclose(np.sort(esc), want, rtol=0, atol=1e-10 * np.abs(want).max())
+
+
+def test_bloch_sum_of_the_image_system_hamiltonian(cell):
+    """Eq. Bloch-basis inserted into Eq. HamPeriodic by hand: with chi_i = sum_T e^{i k.T}
+    phi_i(r - T),
+        h_ij(k) = sum_{T, T'} e^{-i k.T} e^{i k.T'} H^img_{(i, T), (j, T')},
+    where H^img is the finite-system Hamiltonian (pinned by the closed forms) of the atoms'
+    images R_A + T over the same translations, on the cell's points. This fixes the phase
+    convention, the conjugate on the left and both terms' factors of the point-by-point route."""
+    s, o = cell
+    v = synth.periodic_potential(s)
+    r = np.arange(-2, 3)
+    cells = np.stack(np.meshgrid(r, r, r, indexing="ij"), -1).reshape(-1, 3)
+    T = cells @ LAT
+    n_atoms = len(s.atom_species)
+    img_xyz = (s.atom_xyz[None, :, :] + T[:, None, :]).reshape(-1, 3)
+    img_atom = np.tile(np.arange(n_atoms), len(T))
+    si = synth.image_system(s, img_xyz, img_atom)
+    Hi, _ = Oracle(si).hamiltonian(s.pt_xyz, s.pt_w, v)
+    nc, nb = len(T), o.nb
+    Hi = Hi.reshape(nc, nb, nc, nb)  # images cell by cell, each with the unit cell's basis order
+    B = 2 * np.pi * np.linalg.inv(LAT).T
+    for k in (np.zeros(3), np.array([0.31, -0.17, 0.12]), 0.5 * B[1] + 0.25 * B[2]):
+        ph = np.exp(1j * (T @ k))
+        want = np.einsum("a,aibj,b->ij", ph.conj(), Hi, ph)
+        H, A = o.periodic_h(LAT, 2, s.pt_xyz, s.pt_w, k, v)
+        assert np.abs(H.imag).max() > 1e-5 * np.abs(A).max() or not k.any()  # not real by accident
+        assert np.allclose(H, want, rtol=0, atol=1e-13 * np.abs(A).max())
