@@ -182,6 +182,20 @@ nao_status nao_get_info(const nao_grid *g, nao_grid_info *info);
 nao_status nao_export_batches(const nao_grid *g, int64_t *batch_offsets, int64_t *point_perm,
                               int64_t *rel_offsets, int32_t *rel_idx);
 
+/* Host-only set-up steps, without a handle or a GPU (the same code nao_grid_create runs).
+ * nao_partition_points (Sec. 3.3.1): the batch-partition rule above applied to pt_xyz
+ * [n_points*3] (host) with B = max_batch_points (>= 1). Outputs (host, caller-allocated):
+ * batch_offsets [n_batches+1], point_perm [n_points] as nao_export_batches; *n_batches =
+ * ceil(n_points/B). More batches than max_batches: NAO_ERR_INVALID_ARG with *n_batches set
+ * (call again with room). Non-finite coordinates: NAO_ERR_INVALID_ARG.
+ * nao_radial_spline (Sec. 2, the radial functions' cubic splines): the natural cubic spline in
+ * the index coordinate s = ln(r/r0)/Delta through (k, fn_table[k]), k = 0..n_rgrid-1 (>= 4),
+ * as coef [(n_rgrid-1)*4] (host): on segment k, R = c0 + c1 t + c2 t^2 + c3 t^3 with t = s - k,
+ * c = coef + 4k. Non-finite table entries: NAO_ERR_INVALID_ARG.                              */
+nao_status nao_partition_points(const double *pt_xyz, int64_t n_points, int64_t max_batch_points, int64_t max_batches,
+                                int64_t *batch_offsets, int64_t *point_perm, int64_t *n_batches);
+nao_status nao_radial_spline(const double *fn_table, int32_t n_rgrid, double *coef);
+
 /* Hamiltonian integration (Eq. H_int_aims; Eqs. H_decomp, H_contrib_batch,
  * batch_matrix_mult): H_dev[i*nb+j] = sum_p w_p [ phi_i v_p phi_j (if POTENTIAL)
  *                                              + 1/2 grad phi_i . grad phi_j (if KINETIC) ].
@@ -292,6 +306,8 @@ nao_status nao_pulay_forces(nao_grid *g, const double *n_dev, const double *q_de
  * for the n_k points k_dev [n_k*3] (cartesian, 1/bohr): Eq. Bloch-basis inserted into
  * Eq. HamPeriodic. h_uc_dev [n_rs*n_rs], fn_map_dev/fn_image_dev [n_rs], img_cell_dev [3*n_images]
  * on the device; lattice on the host; hk_dev overwritten. FP64 atomics (one per element and k).
+ * The maps are read on the device unchecked: every fn_map entry must lie in [0, nb) and every
+ * fn_image entry in [0, n_images), as nao_periodic_basis_map writes them.
  * Errors: NAO_ERR_INVALID_ARG, NAO_ERR_CUDA.                                                      */
 nao_status nao_periodic_images(const double *atom_xyz, int32_t n_atoms, const double *lattice, double reach,
                                int32_t max_images, double *img_xyz, int32_t *img_atom, int32_t *img_cell,

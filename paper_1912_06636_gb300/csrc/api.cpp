@@ -1171,6 +1171,35 @@ nao_status nao_export_batches(const nao_grid *g, int64_t *batch_offsets, int64_t
     return NAO_OK;
 }
 
+nao_status nao_partition_points(const double *pt_xyz, int64_t n_points, int64_t max_batch_points, int64_t max_batches,
+                                int64_t *batch_offsets, int64_t *point_perm, int64_t *n_batches) {
+    if (!pt_xyz || !n_batches || n_points < 1 || max_batch_points < 1 || max_batches < 0)
+        return fail(NAO_ERR_INVALID_ARG, "nao_partition_points: bad argument");
+    for (int64_t k = 0; k < 3 * n_points; k++)
+        if (!std::isfinite(pt_xyz[k])) return fail(NAO_ERR_INVALID_ARG, "nao_partition_points: non-finite coordinate");
+    std::vector<int64_t> off, perm;
+    try {
+        *n_batches = nao_partition(n_points, pt_xyz, max_batch_points, off, perm);
+    } catch (const std::bad_alloc &) {
+        return fail(NAO_ERR_OUT_OF_MEMORY, "nao_partition_points: host memory");
+    }
+    if (*n_batches > max_batches)
+        return fail(NAO_ERR_INVALID_ARG, "nao_partition_points: " + std::to_string(*n_batches) +
+                                             " batches exceed max_batches (n_batches holds the count)");
+    if (!batch_offsets || !point_perm) return fail(NAO_ERR_INVALID_ARG, "nao_partition_points: NULL output");
+    std::memcpy(batch_offsets, off.data(), off.size() * sizeof(int64_t));
+    std::memcpy(point_perm, perm.data(), perm.size() * sizeof(int64_t));
+    return NAO_OK;
+}
+
+nao_status nao_radial_spline(const double *fn_table, int32_t n_rgrid, double *coef) {
+    if (!fn_table || !coef || n_rgrid < 4) return fail(NAO_ERR_INVALID_ARG, "nao_radial_spline: bad argument");
+    for (int32_t k = 0; k < n_rgrid; k++)
+        if (!std::isfinite(fn_table[k])) return fail(NAO_ERR_INVALID_ARG, "nao_radial_spline: non-finite table entry");
+    nao_spline_coefficients(fn_table, n_rgrid, coef);
+    return NAO_OK;
+}
+
 static nao_status check_single(const nao_grid *g) {
     if (g->n_sys != 1)
         return fail(NAO_ERR_INVALID_ARG,

@@ -35,7 +35,8 @@ SYMBOLS = [
     "nao_grid_create_many", "nao_get_system", "nao_integrate_h_many", "nao_update_density_many",
     "nao_get_tuning", "nao_update_density_gradient", "nao_update_density_gradient_many",
     "nao_update_density_hessian", "nao_integrate_h_tau", "nao_pulay_matrices", "nao_pulay_forces",
-    "nao_periodic_images", "nao_periodic_basis_map", "nao_bloch_sum",
+    "nao_periodic_images", "nao_periodic_basis_map", "nao_bloch_sum", "nao_partition_points",
+    "nao_radial_spline",
 ]
 NAO_NOALLOC_SCRATCH_BYTES = 32 << 20
 KERNELS = ["eval_grad", "eval_phi", "h_fp64", "h_fp32", "h_split", "slice_h", "mirror", "n_fp64", "n_fp32",
@@ -121,6 +122,8 @@ def load():
         "nao_periodic_images": ([P, I32, P, C.c_double, I32, P, P, P, P], C.c_int),
         "nao_periodic_basis_map": ([P, I32, P, I32, P, P, I32, I64, P, P, P], C.c_int),
         "nao_bloch_sum": ([P, I64, P, P, P, P, P, I32, I64, P, P], C.c_int),
+        "nao_partition_points": ([P, I64, I64, I64, P, P, P], C.c_int),
+        "nao_radial_spline": ([P, I32, P], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -282,6 +285,31 @@ def nao_pulay_matrices(h, v, prec, M, S, stream=None) -> None:
 def nao_pulay_forces(h, n, q, M, S, F, stream=None) -> None:
     _check(load().nao_pulay_forces(h, _dptr(n), _dptr(q), _dptr(M), _dptr(S), _dptr(F), _stream(stream)),
            "nao_pulay_forces")
+
+
+def nao_partition_points(pt_xyz, max_batch_points: int):
+    """The batch partition of the points (host, no GPU): (batch_offsets [n_batches + 1],
+    point_perm [n_points]), int64."""
+    lib = load()
+    x = np.ascontiguousarray(pt_xyz, dtype=np.float64).reshape(-1, 3)
+    n = x.shape[0]
+    B = int(max_batch_points)
+    max_b = -(-n // B) if B > 0 else 0
+    off = np.zeros(max_b + 1, np.int64)
+    perm = np.zeros(max(n, 1), np.int64)
+    nbat = C.c_int64(0)
+    _check(lib.nao_partition_points(x.ctypes.data, n, B, max_b, off.ctypes.data, perm.ctypes.data, C.byref(nbat)),
+           "nao_partition_points")
+    return off[: nbat.value + 1], perm[:n]
+
+
+def nao_radial_spline(fn_table):
+    """Cubic coefficients [(n_rgrid - 1), 4] of the natural spline through one radial table (host)."""
+    lib = load()
+    y = np.ascontiguousarray(fn_table, dtype=np.float64).reshape(-1)
+    coef = np.zeros((max(y.size - 1, 1), 4))
+    _check(lib.nao_radial_spline(y.ctypes.data, y.size, coef.ctypes.data), "nao_radial_spline")
+    return coef
 
 
 def nao_periodic_images(atom_xyz, lattice, reach: float):
