@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=16,
                     help="requests of the serving stream (Poisson arrivals at 200/s, 3-200 atoms)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving stream")
+    ap.add_argument("--no-periodic", action="store_true", help="skip the periodic-silicon measurement")
     ap.add_argument("--grouped-molecules", type=int, default=128,
                     help="molecules of the grouped-launch comparison (0 skips it)")
     return ap.parse_args()
@@ -234,6 +235,60 @@ def grouped(n_mol: int, device: int, steps: int = 3) -> dict:
     out.update({"grouped_ms_per_step": ms_g, "grouped_points_per_s": pts / (ms_g / 1e3),
                 "per_molecule_ms_per_step": ms_s, "per_molecule_points_per_s": pts / (ms_s / 1e3),
                 "speedup_grouped": ms_s / ms_g})
+    return out
+
+
+def periodic(device: int, n_grid: int = 48, n_k: int = 4, steps: int = 3) -> dict:
+    """Periodic silicon: the conventional diamond cell (10.26 bohr, 8 atoms, the diamond64 basis),
+    its periodic images as the atoms of a finite system on the cell's points. h^uc and s^uc on the
+    split path, then h(k) and s(k) by the Bloch sum on an n_k^3 k mesh."""
+    import numpy as np
+    import torch
+
+    from paper_1912_06636_gb300 import nao, synth
+
+    a = 10.26
+    base = [[0, 0, 0], [0, 0.5, 0.5], [0.5, 0, 0.5], [0.5, 0.5, 0]]
+    frac = base + [[x + 0.25 for x in f] for f in base]
+    lat = np.eye(3) * a
+    s = synth.periodic_cell(lat, frac, [0] * 8, [synth.silicon_species(1)], n_grid=n_grid, max_batch_points=300)
+    xyz, atom, cell = nao.nao_periodic_images(s.atom_xyz, lat, float(np.max(s.fn_cutoff)))
+    simg = synth.image_system(s, xyz, atom)
+    fm, fi = nao.nao_periodic_basis_map(s, atom)
+    u = (np.arange(n_k) + 0.5) / n_k - 0.5
+    kf = np.stack(np.meshgrid(u, u, u, indexing="ij"), -1).reshape(-1, 3)
+    dev = torch.device("cuda", device)
+    kpts = torch.from_numpy(kf @ (2 * np.pi * np.linalg.inv(lat).T)).to(dev)
+    fm_d, fi_d = torch.from_numpy(fm).to(dev), torch.from_numpy(fi).to(dev)
+    cell_d = torch.from_numpy(np.ascontiguousarray(cell, dtype=np.int32)).to(dev)
+    v = torch.from_numpy(synth.periodic_potential(s)).to(dev)
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"periodic Si, conventional diamond cell 10.26 bohr, 8 atoms x 25 basis functions, "
+                       f"{len(atom)} images (N_rs = {len(fm)}), {n_grid}^3 = {s.n_points} cell points "
+                       f"(periodic trapezoid rule), batches <= 300 points, {n_k}^3 = {len(kf)} k points; "
+                       "h^uc and s^uc split (10 slices)"}
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / steps
+
+    with nao.Grid(simg, device=device, max_batch_points=300, split_slices=10) as g:
+        H = torch.empty((g.nb, g.nb), dtype=torch.float64, device=dev)
+        S = torch.empty((g.nb, g.nb), dtype=torch.float64, device=dev)
+        hk = torch.empty((len(kf), s.n_basis, s.n_basis, 2), dtype=torch.float64, device=dev)
+        ms_h = timed(lambda: g.integrate_h(v, prec="split", H=H, stream=stream))
+        ms_s = timed(lambda: g.overlap(prec="split", S=S, stream=stream))
+        ms_k = timed(lambda: nao.nao_bloch_sum(H, fm_d, fi_d, cell_d, lat, kpts, s.n_basis, stream=stream, out=hk))
+        g.sync()
+    out.update({"h_uc_ms": ms_h, "h_uc_points_per_s": s.n_points / (ms_h / 1e3), "s_uc_ms": ms_s,
+                "bloch_sum_ms": ms_k, "k_points_per_s": len(kf) / (ms_k / 1e3)})
     return out
 
 
@@ -572,6 +627,14 @@ def main():
         if g.h:
             g.close()
         line["grouped"] = grouped(args.grouped_molecules, local_rank)
+
+    if rank == 0 and world == 1 and not args.no_periodic:
+        if g.h:
+            g.close()
+        try:
+            line["periodic"] = periodic(local_rank)
+        except nao.NaoError as e:
+            line["periodic"] = {"unavailable": str(e)}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(s, v_np, P_np, args.cpu_sample)

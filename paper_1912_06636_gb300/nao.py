@@ -346,13 +346,16 @@ def nao_periodic_basis_map(system, img_atom):
     return fm[:n.value], fi[:n.value]
 
 
-def nao_bloch_sum(h_uc, fn_map, fn_image, img_cell, lattice, kpts, nb: int, stream=None):
-    """h(k) [n_k, nb, nb] complex from h^uc [n_rs, n_rs] (CUDA tensors; the index arrays int32)."""
+def nao_bloch_sum(h_uc, fn_map, fn_image, img_cell, lattice, kpts, nb: int, stream=None, out=None):
+    """h(k) [n_k, nb, nb] complex from h^uc [n_rs, n_rs] (CUDA tensors; the index arrays int32).
+    out: optional FP64 CUDA tensor [n_k, nb, nb, 2] to write into."""
     import torch
 
     A = np.ascontiguousarray(lattice, dtype=np.float64).reshape(9)
     k = kpts.contiguous()
-    hk = torch.empty((k.shape[0], nb, nb, 2), dtype=torch.float64, device=h_uc.device)
+    hk = out if out is not None else torch.empty((k.shape[0], nb, nb, 2), dtype=torch.float64, device=h_uc.device)
+    if hk.dtype != torch.float64 or tuple(hk.shape) != (k.shape[0], nb, nb, 2) or not hk.is_contiguous():
+        raise ValueError("out must be a contiguous float64 tensor [n_k, nb, nb, 2]")
     for t in (fn_map, fn_image, img_cell):
         if not t.is_cuda or t.dtype != torch.int32 or not t.is_contiguous():
             raise ValueError("index arrays must be contiguous int32 CUDA tensors")
