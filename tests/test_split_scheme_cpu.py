@@ -1,0 +1,80 @@
+"""The split-precision scheme's accuracy from its arithmetic alone (CPU, no GPU): an emulation in
+numpy of the Ozaki splitting (Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59, 2012) as the
+split path applies it to the Hamiltonian contraction h = E^T D E of each batch (Eq.
+batch_matrix_mult): every row of F = E sqrt|D| is scaled by a power of two 2^-e with
+max |x 2^-e| in [1/4, 1/2), cut into S balanced base-64 digits (|d| <= 32, exact in bf16), and the
+slice products D_s D_t^T are summed exactly for s + t < S (the pairs with s + t >= S carry a
+weight below 64^-S and are dropped); negative weights flip the sign of the B operand's columns.
+
+The emulation takes the oracle's basis functions, so it checks the scheme and the tolerance the
+split path is held to, not the kernels (the GPU tests do that): the error against the FP64
+product falls about 64^2 per two slices, and 10 slices meet the 1e-10 bar on the water molecule
+(with the metric of tests/_metrics.py)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_1912_06636_gb300 import synth
+from tests._metrics import rel_err
+
+
+def _split_product(F, sign, S):
+    """Emulated sum over s + t < S of (digits_s of F)(sign * digits_t of F)^T, scaled back."""
+    mx = np.abs(F).max(axis=1)
+    e = np.array([math.frexp(m)[1] + 1 if m > 0 else 0 for m in mx], dtype=np.int64)  # m 2^-e in [1/4, 1/2)
+    r = F * np.exp2(-e.astype(np.float64))[:, None]
+    digits = []
+    for _ in range(S):
+        t = r * 64.0
+        d = np.rint(t)  # balanced digit, |d| <= 32
+        digits.append(d)
+        r = t - d
+    acc = np.zeros((F.shape[0], F.shape[0]))
+    for s in range(S):
+        for t in range(S - s):
+            # exact: |d| <= 32 and K < 2^33, so every integer sum is below 2^53
+            acc += (digits[s] @ (digits[t] * sign[None, :]).T) * 2.0 ** (-6 * (s + t + 2))
+    return acc * np.exp2((e[:, None] + e[None, :]).astype(np.float64))
+
+
+@pytest.fixture(scope="module")
+def water_batches():
+    s = synth.config_water()
+    o = Oracle(s)
+    v = s.potential()
+    off, perm = Oracle.partition(s.pt_xyz, 200)
+    ro, ri = o.relevance(s.pt_xyz, off, perm)
+    out = []
+    for b in range(len(off) - 1):
+        rel = ri[ro[b]:ro[b + 1]]
+        if len(rel) == 0:
+            continue
+        idx = perm[off[b]:off[b + 1]]
+        phi, grad = o.eval_dense(s.pt_xyz[idx])
+        E = np.concatenate([phi[:, rel].T] + [grad[:, rel, c].T for c in range(3)], axis=1)
+        w = s.pt_w[idx]
+        d = np.concatenate([w * v[idx], 0.5 * w, 0.5 * w, 0.5 * w])
+        out.append((rel, E, d))
+    return s.n_basis, out
+
+
+def test_split_error_per_slice_count(water_batches):
+    nb, batches = water_batches
+    ref, A = np.zeros((nb, nb)), np.zeros((nb, nb))
+    emu = {S: np.zeros((nb, nb)) for S in (4, 6, 8, 10)}
+    for rel, E, d in batches:
+        ix = np.ix_(rel, rel)
+        ref[ix] += (E * d[None, :]) @ E.T
+        A[ix] += np.abs(E * d[None, :]) @ np.abs(E).T
+        F = E * np.sqrt(np.abs(d))[None, :]
+        sign = np.where(d < 0, -1.0, 1.0)
+        for S in emu:
+            emu[S][ix] += _split_product(F, sign, S)
+    err = {S: rel_err(emu[S], ref, A) for S in emu}
+    print({S: f"{e:.2e}" for S, e in err.items()})
+    assert err[4] > 1e-8  # the test is not vacuous
+    for S in (4, 6):
+        assert err[S] / max(err[S + 2], 1e-300) > 500.0  # about 64^2 per two slices
+    assert err[10] <= 1e-10
