@@ -6,10 +6,13 @@ max |x 2^-e| in [1/4, 1/2), cut into S balanced base-64 digits (|d| <= 32, exact
 slice products D_s D_t^T are summed exactly for s + t < S (the pairs with s + t >= S carry a
 weight below 64^-S and are dropped); negative weights flip the sign of the B operand's columns.
 
+The density's T = Phi P is split the same way with one exponent per point (row of Phi) and
+one per batch (its block of P).
+
 The emulation takes the oracle's basis functions, so it checks the scheme and the tolerance the
 split path is held to, not the kernels (the GPU tests do that): the error against the FP64
-product falls about 64^2 per two slices, and 10 slices meet the 1e-10 bar on the water molecule
-(with the metric of tests/_metrics.py)."""
+results falls about 64^2 per two slices, and 10 slices meet the 1e-10 bar for H and n on the
+water molecule (with the metric of tests/_metrics.py)."""
 import math
 
 import numpy as np
@@ -77,4 +80,62 @@ def test_split_error_per_slice_count(water_batches):
     assert err[4] > 1e-8  # the test is not vacuous
     for S in (4, 6):
         assert err[S] / max(err[S + 2], 1e-300) > 500.0  # about 64^2 per two slices
+    assert err[10] <= 1e-10
+
+
+def _split_matmul(X, ex, Y, ey, S):
+    """Emulated split product X Y with per-row exponents ex of X and one exponent ey for all of Y
+    (the density's T = Phi P: exponents per point and per batch)."""
+    def digits(M, scale):
+        r = M * scale
+        out = []
+        for _ in range(S):
+            t = r * 64.0
+            d = np.rint(t)
+            out.append(d)
+            r = t - d
+        return out
+
+    dx = digits(X, np.exp2(-ex.astype(np.float64))[:, None])
+    dy = digits(Y, 2.0 ** -ey)
+    acc = np.zeros((X.shape[0], Y.shape[1]))
+    for s in range(S):
+        for t in range(S - s):
+            acc += (dx[s] @ dy[t]) * 2.0 ** (-6 * (s + t + 2))
+    return acc * np.exp2(ex.astype(np.float64))[:, None] * 2.0 ** ey
+
+
+def _exponent(m):
+    return math.frexp(m)[1] + 1 if m > 0 else 0
+
+
+def test_split_density_error_per_slice_count():
+    """The density n_q = sum_j T_qj phi_qj with T = Phi P split (Eq. Density), P of the water
+    molecule (seed 0): the error against the oracle falls about 64^2 per two slices and 10
+    slices meet 1e-10 with the metric of tests/_metrics.py."""
+    s = synth.config_water()
+    o = Oracle(s)
+    P = synth.density_matrix(s, 0)
+    nref, D, _ = o.density(s.pt_xyz, P, s.pt_w)
+    off, perm = Oracle.partition(s.pt_xyz, 200)
+    ro, ri = o.relevance(s.pt_xyz, off, perm)
+    emu = {S: np.zeros(s.n_points) for S in (4, 6, 8, 10)}
+    for b in range(len(off) - 1):
+        rel = ri[ro[b]:ro[b + 1]]
+        if len(rel) == 0:
+            continue
+        idx = perm[off[b]:off[b + 1]]
+        phi, _ = o.eval_dense(s.pt_xyz[idx])
+        Phi = phi[:, rel]
+        Pb = P[np.ix_(rel, rel)]
+        ex = np.array([_exponent(m) for m in np.abs(Phi).max(axis=1)], dtype=np.int64)
+        ey = _exponent(np.abs(Pb).max())
+        for S in emu:
+            T = _split_matmul(Phi, ex, Pb, ey, S)
+            emu[S][idx] = np.sum(T * Phi, axis=1)
+    err = {S: rel_err(emu[S], nref, D) for S in emu}
+    print({S: f"{e:.2e}" for S, e in err.items()})
+    assert err[4] > 1e-8
+    for S in (4, 6):
+        assert err[S] / max(err[S + 2], 1e-300) > 500.0
     assert err[10] <= 1e-10
