@@ -128,6 +128,16 @@ MUTANTS = [
      "pij * grad[3 * a + ib] * grad[3 * b + ia], pij * phi[a] * hs[6 * b + k]}",
      "0.0 * grad[3 * a + ib] * grad[3 * b + ia], pij * phi[a] * hs[6 * b + k]}",
      "test_density_hessian_differences_and_rank_one"),
+    # error denominators (the scale of every parity bar)
+    ("H magnitude sum drops the kinetic term",
+     "neu_add(&A[e], &Ac[e], fabs(tv) + fabs(tk) + fabs(tt));", "neu_add(&A[e], &Ac[e], fabs(tv) + fabs(tt));",
+     "test_error_denominators"),
+    ("density magnitude sum takes signed terms",
+     "neu_add(&ds, &dc, fabs(t));", "neu_add(&ds, &dc, t);",
+     "test_error_denominators"),
+    ("gradient magnitude sum takes signed terms",
+     "neu_add(&ds, &de, fabs(t));", "neu_add(&ds, &de, t);",
+     "test_error_denominators"),
     # local Pulay terms
     ("Pulay force: sign of the q term",
      "+ 2.0 * wp * dRphi * qr[idx[b]] * phi[b];", "- 2.0 * wp * dRphi * qr[idx[b]] * phi[b];",

@@ -129,6 +129,36 @@ def test_symmetry_trace_and_positivity(small_molecule):
     assert np.all(n >= -1e-15 * D)
 
 
+def test_error_denominators(small_molecule):
+    """The magnitude sums that scale every parity bar, from their definitions: A_ij =
+    sum_p w_p (|phi_i v phi_j| + 1/2 |grad phi_i . grad phi_j|) is the sum of its two terms' sums,
+    bounds |H|, and equals the plain sum on the diagonal of a term whose summands are all
+    non-negative (w >= 0); for a rank-one P = c c^T, D_p = (sum_i |c_i phi_i|)^2 and the
+    gradient's 2 sum_ij |d phi_i P_ij phi_j| = 2 (sum_i |c_i d phi_i|)(sum_j |c_j phi_j|)."""
+    s, o = small_molecule
+    assert np.all(s.pt_w >= 0)
+    v = s.potential()
+    H, A = o.hamiltonian(s.pt_xyz, s.pt_w, v)
+    Hp, Ap = o.hamiltonian(s.pt_xyz, s.pt_w, v, TERM_POTENTIAL)
+    T, At = o.hamiltonian(s.pt_xyz, s.pt_w, None, TERM_KINETIC)
+    S, As = o.overlap(s.pt_xyz, s.pt_w)
+    assert np.allclose(A, Ap + At, rtol=1e-14, atol=0)
+    assert np.all(np.abs(H) <= A * (1 + 1e-14))
+    assert np.allclose(np.diag(At), np.diag(T), rtol=1e-14, atol=0)
+    assert np.allclose(np.diag(As), np.diag(S), rtol=1e-14, atol=0)
+    assert np.max(np.abs(As - np.abs(S))) > 1e-3 * As.max()  # off-diagonal sign changes count
+    rng = np.random.Generator(np.random.PCG64(11))
+    c = rng.standard_normal(o.nb)
+    pts = s.pt_xyz[::7]
+    phi, grad = o.eval_dense(pts)
+    n, D, _ = o.density(pts, np.outer(c, c))
+    assert np.allclose(n, (phi @ c) ** 2, rtol=1e-12, atol=1e-14 * D.max())
+    assert np.allclose(D, (np.abs(phi) @ np.abs(c)) ** 2, rtol=1e-13, atol=0)
+    g, Dg = o.density_gradient(pts, np.outer(c, c))
+    want = 2 * (np.abs(grad) * np.abs(c)[None, :, None]).sum(axis=1) * (np.abs(phi) @ np.abs(c))[:, None]
+    assert np.allclose(Dg, want, rtol=1e-13, atol=0)
+
+
 def test_linearity_and_terms(small_molecule):
     s, o = small_molecule
     v = s.potential()
