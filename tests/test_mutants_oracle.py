@@ -138,6 +138,9 @@ MUTANTS = [
     ("gradient magnitude sum takes signed terms",
      "neu_add(&ds, &de, fabs(t));", "neu_add(&ds, &de, t);",
      "test_error_denominators"),
+    ("density Hessian magnitude sum takes signed terms",
+     "neu_add(&dv, &de, fabs(t[u]));", "neu_add(&dv, &de, t[u]);",
+     "test_density_hessian_differences_and_rank_one"),
     # local Pulay terms
     ("Pulay force: sign of the q term",
      "+ 2.0 * wp * dRphi * qr[idx[b]] * phi[b];", "- 2.0 * wp * dRphi * qr[idx[b]] * phi[b];",
@@ -166,6 +169,9 @@ MUTANTS = [
     ("Bloch phase e^{-ik.T} for e^{ik.T}",
      "double ph = k[0] * T[0] + k[1] * T[1] + k[2] * T[2];", "double ph = -(k[0] * T[0] + k[1] * T[1] + k[2] * T[2]);",
      "test_bloch_sum_of_the_image_system_hamiltonian"),
+    ("periodic kinetic magnitude sum loses its 1/2",
+     "ta += 0.5 * fabs(wp) * mag;", "ta += fabs(wp) * mag;",
+     "test_periodic_error_denominators"),
     # partition and relevance (Sec. 3.3.1, 3.3.2)
     ("tie between equal extents goes to y",
      "if (ext[1] > ext[ax]) ax = 1;", "if (ext[1] >= ext[ax]) ax = 1;",

@@ -141,12 +141,19 @@ def test_density_hessian_differences_and_rank_one(water):
     # rank one: n = (c . phi)^2
     cvec = rng.normal(size=o.nb)
     phi, grad, hess = o.eval_dense2(pts)
-    H1, _ = o.density_hessian(pts, np.outer(cvec, cvec))
+    H1, Dh1 = o.density_hessian(pts, np.outer(cvec, cvec))
     u = phi @ cvec
     du = np.einsum("pic,i->pc", grad, cvec)
     ddu = np.einsum("pik,i->pk", hess, cvec)
     want = np.stack([2 * du[:, a] * du[:, b] + 2 * u * ddu[:, k] for k, (a, b) in enumerate(PAIRS)], axis=1)
     assert np.allclose(H1, want, rtol=0, atol=1e-12 * np.abs(want).max())
+    # and its magnitude sums: 2 (sum |c d_a d_b phi|)(sum |c phi|) + 2 (sum |c d_a phi|)(sum |c d_b phi|)
+    ac = np.abs(cvec)
+    U = np.abs(phi) @ ac
+    dU = np.einsum("pic,i->pc", np.abs(grad), ac)
+    ddU = np.einsum("pik,i->pk", np.abs(hess), ac)
+    wantD = np.stack([2 * ddU[:, k] * U + 2 * dU[:, a] * dU[:, b] for k, (a, b) in enumerate(PAIRS)], axis=1)
+    assert np.allclose(Dh1, wantD, rtol=1e-13, atol=0)
 
 
 def _atom_of(s):

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 import scipy.linalg as sla
 
-from oracle import TERM_POTENTIAL, Oracle
+from oracle import TERM_KINETIC, TERM_POTENTIAL, Oracle
 from paper_1912_06636_gb300 import synth
 
 
@@ -105,3 +105,18 @@ def test_bloch_sum_of_the_image_system_hamiltonian(cell):
         H, A = o.periodic_h(LAT, 2, s.pt_xyz, s.pt_w, k, v)
         assert np.abs(H.imag).max() > 1e-5 * np.abs(A).max() or not k.any()  # not real by accident
         assert np.allclose(H, want, rtol=0, atol=1e-13 * np.abs(A).max())
+
+
+def test_periodic_error_denominators(cell):
+    """A_ij(k) = sum_p w_p (|v| |chi_i| |chi_j| + 1/2 sum_c |d_c chi_i| |d_c chi_j|) bounds |h(k)|
+    and equals the diagonal of s(k) and of the kinetic h(k), whose diagonal terms are all
+    non-negative."""
+    s, o = cell
+    k = np.array([0.31, -0.17, 0.12])
+    Sk, As = o.periodic_h(LAT, 2, s.pt_xyz, s.pt_w, k, None, TERM_POTENTIAL)
+    Tk, At = o.periodic_h(LAT, 2, s.pt_xyz, s.pt_w, k, None, TERM_KINETIC)
+    Hk, A = o.periodic_h(LAT, 2, s.pt_xyz, s.pt_w, k, synth.periodic_potential(s))
+    assert np.allclose(np.diag(As), np.diag(Sk).real, rtol=1e-13, atol=0)
+    assert np.allclose(np.diag(At), np.diag(Tk).real, rtol=1e-13, atol=0)
+    assert np.all(np.abs(Hk) <= A * (1 + 1e-13))
+    assert np.all(np.abs(Sk) <= As * (1 + 1e-13))
