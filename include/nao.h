@@ -188,7 +188,8 @@ nao_status nao_export_batches(const nao_grid *g, int64_t *batch_offsets, int64_t
  * batch_offsets [n_batches+1], point_perm [n_points] as nao_export_batches; *n_batches =
  * ceil(n_points/B). More batches than max_batches: NAO_ERR_INVALID_ARG with *n_batches set
  * (call again with room). Non-finite coordinates: NAO_ERR_INVALID_ARG.
- * nao_radial_spline (Sec. 2, the radial functions' cubic splines): the natural cubic spline in
+ * nao_radial_spline (Sec. 3.2.1, the NAO radial functions, represented as cubic splines through
+ * their tables as in nao_grid_create): the natural cubic spline in
  * the index coordinate s = ln(r/r0)/Delta through (k, fn_table[k]), k = 0..n_rgrid-1 (>= 4),
  * as coef [(n_rgrid-1)*4] (host): on segment k, R = c0 + c1 t + c2 t^2 + c3 t^3 with t = s - k,
  * c = coef + 4k. Non-finite table entries: NAO_ERR_INVALID_ARG.                              */

@@ -1,6 +1,6 @@
 """The library's host set-up steps against the oracle, on the CPU (no GPU, no handle):
 the batch partition (Sec. 3.3.1) bit-exact, and the natural cubic spline of the radial tables
-(Sec. 2) to rounding. nao_grid_create runs the same host code, so these parity checks cover it
+(Sec. 3.2.1) to rounding. nao_grid_create runs the same host code, so these parity checks cover it
 without a GPU; the GPU tests check the same partition again through nao_export_batches."""
 import math
 

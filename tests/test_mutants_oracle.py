@@ -26,7 +26,7 @@ PINS = sorted(str(p.relative_to(ROOT)) for p in (ROOT / "tests").glob("test_orac
 
 # (name, text in oracle.c (must occur once), replacement, a pin test that must fail)
 MUTANTS = [
-    # radial splines (Sec. 2: cubic splines of the tabulated radial functions)
+    # radial splines (Sec. 3.2.1: cubic splines of the tabulated radial functions)
     ("spline system right-hand side halved",
      "double rhs = 6.0 * (", "double rhs = 3.0 * (",
      "test_spline_matches_scipy_natural_spline"),
