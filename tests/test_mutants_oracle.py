@@ -111,6 +111,16 @@ MUTANTS = [
     ("H element added to the wrong column",
      "size_t e = row + (size_t)idx[b];\n                neu_add(&H[e]", "size_t e = row + (size_t)idx[a];\n                neu_add(&H[e]",
      "test_two_centre_gaussian_product"),
+    ("block Hamiltonian: kinetic factor 1/2 dropped",
+     "double tk = kin ? wp * 0.5 * gg : 0.0;\n                size_t e = (size_t)a * (size_t)nF",
+     "double tk = kin ? wp * gg : 0.0;\n                size_t e = (size_t)a * (size_t)nF",
+     "test_block_equals_full"),
+    ("brute force: kinetic factor 1/2 dropped",
+     "0.5 * (gi[3 * i] * gi[3 * j]", "1.0 * (gi[3 * i] * gi[3 * j]",
+     "test_bruteforce_equals_pointwise_definition"),
+    ("Cartesian g' sign of the l R / r^(l+1) term",
+     "double g1 = dR / rl - (double)l * R / (rl * r);", "double g1 = dR / rl + (double)l * R / (rl * r);",
+     "test_cartesian_basis_equals_spherical"),
     ("tau term factor 1/2 dropped",
      "double tt = tau ? wp * vtau[p] * 0.5 * gg : 0.0;", "double tt = tau ? wp * vtau[p] * gg : 0.0;",
      "test_tau_term_pins"),
