@@ -292,6 +292,22 @@ def periodic(device: int, n_grid: int = 48, n_k: int = 4, steps: int = 3) -> dic
     return out
 
 
+def h_tile_area(n_basis, k_cols, tile_width, tile_rows: int = 128):
+    """Issued and useful MMA area (rows x columns x K) of the split H contraction: per batch, the
+    tile_rows x tile_width tiles that reach the upper triangle (i <= j) of its N x N block, against
+    the triangle's own N (N + 1) / 2 elements (the part FLOP_H counts), both times the batch's K."""
+    issued = useful = 0
+    for n, k, tn in zip(n_basis, k_cols, tile_width):
+        n, k, tn = int(n), int(k), int(tn)
+        if n <= 0 or tn <= 0:
+            continue
+        useful += k * n * (n + 1) // 2
+        for i0 in range(0, n, tile_rows):
+            j_first = (i0 // tn) * tn  # the first column tile that reaches i0 <= j
+            issued += k * tile_rows * tn * len(range(j_first, n, tn))
+    return issued, useful
+
+
 def g_split_pairs(g) -> int:
     """Slice products per contraction on the split path: S (S + 1) / 2 for S slices."""
     S = int(g.split_slices)
@@ -514,6 +530,13 @@ def main():
     if prec == "split":
         tw, timed = nao.nao_get_tuning(g.h)
         tuning = {"buckets_timed": timed, "batches_tile48": int(np.sum(tw == 48)), "batches_tile32": int(np.sum(tw == 32))}
+        if roofline is not None and fam == "h_split":
+            try:  # the share of the issued MMA area that is the work FLOP_H counts
+                issued, useful = h_tile_area(Nb, 4 * Ppad, tw)
+                roofline["useful_area_frac"] = useful / issued
+                roofline["issued_tflops"] = roofline["achieved"] * issued / useful
+            except Exception as e:  # reported, never fatal
+                roofline["useful_area_frac"] = f"unavailable: {type(e).__name__}: {e}"
 
     line = {
         "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,

@@ -31,3 +31,26 @@ def test_reference_arm_json_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_h_tile_area_against_brute_force():
+    """The issued/useful MMA area that bench.py reports for the split H contraction: closed form
+    against a cell-by-cell count of the 128 x TN tiles that reach the upper triangle."""
+    sys.path.insert(0, str(ROOT))
+    import numpy as np
+
+    import bench
+
+    rng = np.random.Generator(np.random.PCG64(8))
+    n = rng.integers(0, 400, 40)
+    k = 4 * rng.integers(1, 20, 40) * 16
+    tw = rng.choice([32, 48], 40)
+    issued = useful = 0
+    for nb, kk, tn in zip(n, k, tw):
+        for i0 in range(0, nb, 128):
+            for j0 in range(0, nb, tn):
+                cells = [(i, j) for i in range(i0, i0 + 128) for j in range(j0, j0 + tn)]
+                if any(i <= j and i < nb and j < nb for i, j in cells):
+                    issued += 128 * tn * kk
+                    useful += kk * sum(1 for i, j in cells if i <= j and j < nb)
+    assert bench.h_tile_area(n, k, tw) == (issued, useful)
