@@ -162,6 +162,56 @@ def _stream(stream) -> int | None:
     return getattr(stream, "cuda_stream", stream)
 
 
+def _count(t) -> int:
+    return int(t.numel()) if hasattr(t, "numel") else int(np.size(t))
+
+
+def _need(t, n: int, what: str) -> None:
+    """A caller's buffer (tensor or array; None is checked by the library) must hold n elements:
+    the C ABI cannot see the size of a device buffer, so the binding checks it before the call."""
+    if t is not None and _count(t) < n:
+        raise ValueError(f"{what}: needs {n} elements, the buffer holds {_count(t)}")
+
+
+# sizes of each live handle (fixed at create; dropped by nao_destroy, so a later handle at the
+# same address is looked up afresh)
+_HANDLE_SIZES: dict = {}
+
+
+def _handle_sizes(h):
+    """(n_basis, n_points, [(n_basis_m, n_points_m) per system]) of a handle."""
+    key = getattr(h, "value", h)
+    got = _HANDLE_SIZES.get(key)
+    if got is None:
+        info = nao_get_info(h)
+        per = []
+        for m in range(int(info.n_systems)):
+            sysm = nao_get_system(h, m)
+            per.append((sysm["n_basis"], sysm["n_points"]))
+        got = (int(info.n_basis), int(info.n_points), per)
+        if key is not None:
+            _HANDLE_SIZES[key] = got
+    return got
+
+
+def _sizes(h):
+    """(n_basis, n_points) of a handle (for a grouped handle, the totals)."""
+    nb, npts, _ = _handle_sizes(h)
+    return nb, npts
+
+
+def _need_each(h, ts, per_system, what: str) -> None:
+    """Per-system buffers of a grouped call: one entry per system (the library reads that many
+    pointers), ts[m] holding per_system(n_basis_m, n_points_m) elements."""
+    if ts is None:
+        return
+    per = _handle_sizes(h)[2]
+    if len(ts) != len(per):
+        raise ValueError(f"{what}: {len(per)} entries required (one per system), got {len(ts)}")
+    for m, (t, (nb_m, np_m)) in enumerate(zip(ts, per)):
+        _need(t, per_system(nb_m, np_m), f"{what}[{m}]")
+
+
 # ---- C-named functions --------------------------------------------------------------------
 def nao_default_options() -> Options:
     o = Options()
@@ -248,6 +298,7 @@ def _ptr_array(ts, allow_none: bool):
 
 
 def nao_destroy(h) -> None:
+    _HANDLE_SIZES.pop(getattr(h, "value", h), None)
     _check(load().nao_destroy(h), "nao_destroy")
 
 
@@ -269,20 +320,34 @@ def nao_export_batches(h):
 
 
 def nao_integrate_h(h, v, terms: int, prec, H, stream=None) -> None:
+    nb, npts = _sizes(h)
+    _need(v, npts, "v")
+    _need(H, nb * nb, "H")
     _check(load().nao_integrate_h(h, _dptr(v), int(terms), _prec(prec), _dptr(H), _stream(stream)), "nao_integrate_h")
 
 
 def nao_integrate_h_tau(h, v, vtau, terms: int, prec, H, stream=None) -> None:
+    nb, npts = _sizes(h)
+    _need(v, npts, "v")
+    _need(vtau, npts, "vtau")
+    _need(H, nb * nb, "H")
     _check(load().nao_integrate_h_tau(h, _dptr(v), _dptr(vtau), int(terms), _prec(prec), _dptr(H), _stream(stream)),
            "nao_integrate_h_tau")
 
 
 def nao_pulay_matrices(h, v, prec, M, S, stream=None) -> None:
+    nb, npts = _sizes(h)
+    _need(v, npts, "v")
+    _need(M, 3 * nb * nb, "M")
+    _need(S, 3 * nb * nb, "S")
     _check(load().nao_pulay_matrices(h, _dptr(v), _prec(prec), _dptr(M), _dptr(S), _stream(stream)),
            "nao_pulay_matrices")
 
 
 def nao_pulay_forces(h, n, q, M, S, F, stream=None) -> None:
+    nb, _ = _sizes(h)
+    for t, k, what in ((n, 1, "n"), (q, 1, "q"), (M, 3, "M"), (S, 3, "S")):
+        _need(t, k * nb * nb, what)
     _check(load().nao_pulay_forces(h, _dptr(n), _dptr(q), _dptr(M), _dptr(S), _dptr(F), _stream(stream)),
            "nao_pulay_forces")
 
@@ -359,51 +424,89 @@ def nao_bloch_sum(h_uc, fn_map, fn_image, img_cell, lattice, kpts, nb: int, stre
     for t in (fn_map, fn_image, img_cell):
         if not t.is_cuda or t.dtype != torch.int32 or not t.is_contiguous():
             raise ValueError("index arrays must be contiguous int32 CUDA tensors")
+    n_rs = int(h_uc.shape[0])
+    if h_uc.dim() != 2 or int(h_uc.shape[1]) != n_rs:
+        raise ValueError("h_uc must be a square [n_rs, n_rs] tensor")
+    _need(fn_map, n_rs, "fn_map")
+    _need(fn_image, n_rs, "fn_image")
+    if k.dim() != 2 or int(k.shape[1]) != 3:
+        raise ValueError("kpts must be [n_k, 3]")
     _check(load().nao_bloch_sum(_dptr(h_uc), h_uc.shape[0], fn_map.data_ptr(), fn_image.data_ptr(), img_cell.data_ptr(),
                                 A.ctypes.data, _dptr(k), k.shape[0], int(nb), _dptr(hk), _stream(stream)), "nao_bloch_sum")
     return torch.view_as_complex(hk)
 
 
 def nao_update_density(h, P, prec, n, ne=None, stream=None) -> None:
+    nb, npts = _sizes(h)
+    _need(P, nb * nb, "P")
+    _need(n, npts, "n")
+    _need(ne, 1, "ne")
     _check(load().nao_update_density(h, _dptr(P), _prec(prec), _dptr(n), _dptr(ne), _stream(stream)),
            "nao_update_density")
 
 
 def nao_integrate_h_many(h, vs, terms: int, prec, Hs, stream=None) -> None:
+    _need_each(h, vs, lambda nb, npts: npts, "vs")
+    _need_each(h, Hs, lambda nb, npts: nb * nb, "Hs")
     _check(load().nao_integrate_h_many(h, _ptr_array(vs, True), int(terms), _prec(prec), _ptr_array(Hs, False),
                                        _stream(stream)), "nao_integrate_h_many")
 
 
 def nao_update_density_many(h, Ps, prec, ns, nes=None, stream=None) -> None:
+    _need_each(h, Ps, lambda nb, npts: nb * nb, "Ps")
+    _need_each(h, ns, lambda nb, npts: npts, "ns")
+    _need_each(h, nes, lambda nb, npts: 1, "nes")
     _check(load().nao_update_density_many(h, _ptr_array(Ps, False), _prec(prec), _ptr_array(ns, False),
                                           _ptr_array(nes, True), _stream(stream)), "nao_update_density_many")
 
 
 def nao_update_density_gradient(h, P, prec, n, grad, ne=None, stream=None) -> None:
+    nb, npts = _sizes(h)
+    _need(P, nb * nb, "P")
+    _need(n, npts, "n")
+    _need(grad, 3 * npts, "grad")
+    _need(ne, 1, "ne")
     _check(load().nao_update_density_gradient(h, _dptr(P), _prec(prec), _dptr(n), _dptr(grad), _dptr(ne),
                                               _stream(stream)), "nao_update_density_gradient")
 
 
 def nao_update_density_hessian(h, P, prec, n, grad, hess, ne=None, stream=None) -> None:
+    nb, npts = _sizes(h)
+    _need(P, nb * nb, "P")
+    _need(n, npts, "n")
+    _need(grad, 3 * npts, "grad")
+    _need(hess, 6 * npts, "hess")
+    _need(ne, 1, "ne")
     _check(load().nao_update_density_hessian(h, _dptr(P), _prec(prec), _dptr(n), _dptr(grad), _dptr(hess), _dptr(ne),
                                              _stream(stream)), "nao_update_density_hessian")
 
 
 def nao_update_density_gradient_many(h, Ps, prec, ns, grads, nes=None, stream=None) -> None:
+    _need_each(h, Ps, lambda nb, npts: nb * nb, "Ps")
+    _need_each(h, ns, lambda nb, npts: npts, "ns")
+    _need_each(h, grads, lambda nb, npts: 3 * npts, "grads")
+    _need_each(h, nes, lambda nb, npts: 1, "nes")
     _check(load().nao_update_density_gradient_many(h, _ptr_array(Ps, False), _prec(prec), _ptr_array(ns, False),
                                                    _ptr_array(grads, False), _ptr_array(nes, True), _stream(stream)),
            "nao_update_density_gradient_many")
 
 
 def nao_integrate_h_host(h, v: np.ndarray | None, terms: int, prec, H: np.ndarray, stream=None) -> None:
-    vp = None if v is None else np.ascontiguousarray(v, dtype=np.float64).ctypes.data
+    nb, npts = _sizes(h)
+    v = None if v is None else np.ascontiguousarray(v, dtype=np.float64)
+    _need(v, npts, "v")
+    _need(H, nb * nb, "H")
+    vp = None if v is None else v.ctypes.data
     assert H.dtype == np.float64 and H.flags.c_contiguous
     _check(load().nao_integrate_h_host(h, vp, int(terms), _prec(prec), H.ctypes.data, _stream(stream)),
            "nao_integrate_h_host")
 
 
 def nao_update_density_host(h, P: np.ndarray, prec, n: np.ndarray, stream=None) -> float:
+    nb, npts = _sizes(h)
     P = np.ascontiguousarray(P, dtype=np.float64)
+    _need(P, nb * nb, "P")
+    _need(n, npts, "n")
     assert n.dtype == np.float64 and n.flags.c_contiguous
     ne = C.c_double(0.0)
     _check(load().nao_update_density_host(h, P.ctypes.data, _prec(prec), n.ctypes.data, C.byref(ne), _stream(stream)),
@@ -422,6 +525,9 @@ def nao_sync_status(h) -> None:
 
 def nao_integrate_h_noalloc(h, v, terms: int, H, stream=None) -> None:
     """FP64 Hamiltonian with the library's fixed device scratch (no allocation of any kind)."""
+    nb, npts = _sizes(h)
+    _need(v, npts, "v")
+    _need(H, nb * nb, "H")
     _check(load().nao_integrate_h_noalloc(h, _dptr(v), int(terms), _dptr(H), _stream(stream)),
            "nao_integrate_h_noalloc")
 
