@@ -152,6 +152,9 @@ MUTANTS = [
      "neu_add(&dv, &de, fabs(t[u]));", "neu_add(&dv, &de, t[u]);",
      "test_density_hessian_differences_and_rank_one"),
     # local Pulay terms
+    ("Pulay magnitude sums take signed terms",
+     "if (AM) AM[e] += fabs(tm);", "if (AM) AM[e] += tm;",
+     "test_pulay_forces_routes_and_fixed_grid_derivatives"),
     ("Pulay force: sign of the q term",
      "+ 2.0 * wp * dRphi * qr[idx[b]] * phi[b];", "- 2.0 * wp * dRphi * qr[idx[b]] * phi[b];",
      "test_pulay_forces_routes_and_fixed_grid_derivatives"),

@@ -185,7 +185,10 @@ def test_pulay_forces_routes_and_fixed_grid_derivatives(water):
     P = synth.density_matrix(s, 3)
     X = rng.normal(size=(o.nb, o.nb))
     Q = (X + X.T) / 10
-    M, S, _, _ = o.pulay_matrices(s.pt_xyz, s.pt_w, v)
+    M, S, AM, AS = o.pulay_matrices(s.pt_xyz, s.pt_w, v)
+    # the magnitude sums bound the matrices and exceed them where signs cancel
+    assert np.all(np.abs(M) <= AM * (1 + 1e-14)) and np.all(np.abs(S) <= AS * (1 + 1e-14))
+    assert np.max(AM - np.abs(M)) > 1e-3 * AM.max() and np.max(AS - np.abs(S)) > 1e-3 * AS.max()
     F = o.pulay_forces(s.pt_xyz, s.pt_w, v, P, Q)
     at = _atom_of(s)
     F2 = np.zeros_like(F)
