@@ -3,15 +3,18 @@
 
 One step = nao_integrate_h (evaluate phi, grad phi per batch; h[B] contraction; scatter into
 H; mirror) followed by nao_update_density (evaluate phi; density contraction; N_e) over the
-whole grid of the 64-atom diamond-lattice cluster (1600 basis functions, 1,175,040 points,
-batches of <= 300 points), inputs resident in device memory. Prints one JSON line.
+whole grid, inputs resident in device memory. The default workload is the 375-atom
+two-species slab (15,000 basis functions, 80 x 434 points per atom = 13,020,000 points,
+batches <= 200 points; the stand-in for the paper's Bi2Se3 slab of Sec. 4), on the split
+path at the slice count whose accuracy the full-size parity test checks on the same input.
+``--config 1`` times the 64-atom diamond-lattice cluster instead. Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec split|fp64|fp32] [--impl ours|reference]
 
 Under torchrun (N > 1) every rank runs an independent replica of the workload on its own
 GPU (the path has no exchange step on one handle); the line reports all ranks' points
-divided by the slowest rank's time. ``--impl reference`` times the FP64 CPU oracle on a
-bounded sample of the same workload instead.
+divided by the slowest rank's time. ``--impl reference`` times the FP64 CPU oracle on
+bounded samples of the same workload instead.
 """
 from __future__ import annotations
 
@@ -29,8 +32,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Hamiltonian integration + density update pts/s, split-prec vs FP64; p99 latency"
-WORKLOAD = ("diamond64: 64-atom diamond-lattice cluster (cubic cell 10.26 bohr), 1600 basis functions "
-            "(2s2p2d1f per atom), 60x306 points per atom = 1,175,040 points, batches <= 300 points")
+WORKLOADS = {
+    1: ("diamond64: 64-atom diamond-lattice cluster (cubic cell 10.26 bohr), 1600 basis functions "
+        "(2s2p2d1f per atom), 60x306 points per atom = 1,175,040 points, batches <= 300 points"),
+    2: ("slab375: 375-atom layered slab of two species (150 A : 225 B, 15 layers of 5x5, a = 7.8 bohr, "
+        "pitch 3.5 bohr), 15,000 basis functions (4s3p4d1f per atom), 80x434 points per atom = "
+        "13,020,000 points, batches <= 200 points"),
+}
+# split slices timed per workload: the count whose e <= 1e-10 the full-size parity tests check
+# on the same input (tests/test_gpu_slab.py, tests/test_gpu_fullsize.py)
+BENCH_SLICES = {1: 10, 2: 11}
 
 
 def parse():
@@ -40,13 +51,20 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default=None, choices=[None, "fp64", "fp32", "split"])
-    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--config", type=int, default=2, choices=[0, 1, 2],
+                    help="workload: 2 = slab375 (default), 1 = diamond64, 0 = the 3-atom molecule")
     ap.add_argument("--cells", type=int, default=2,
                     help="diamond cluster: cubic cells per edge (2 = the 64-atom workload; 1 = an 8-atom case "
                          "for profiling captures, not a bench line)")
-    ap.add_argument("--slices", type=int, default=10,
-                    help="split path: slices per operand (10 meets e <= 1e-10 on this workload; the library default is 12)")
-    ap.add_argument("--cpu-sample", type=int, default=200000, help="oracle sample size (points)")
+    ap.add_argument("--slab-layers", type=int, default=15,
+                    help="slab: layers (15 = the 375-atom workload; fewer = a profiling case, not a bench line)")
+    ap.add_argument("--scratch-mb", type=int, default=0,
+                    help="evaluation scratch of the handle in MiB (0: the library default; the split slices get twice this)")
+    ap.add_argument("--slices", type=int, default=None,
+                    help="split path: slices per operand (default: the count the full-size parity test checks "
+                         "on the workload; the library default is 12)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target single-thread CPU time of the oracle baseline's sample (its size is calibrated)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other precisions")
@@ -173,8 +191,8 @@ def serving(n_requests: int, device: int) -> dict:
 # contraction on the 8-atom profiling case (a launch's traffic grows with tiles x K, i.e. with
 # FLOP_H). Valid only for the kernel version and slice count the capture was taken with.
 TRAFFIC_PER_FLOP_H = {
-    ("h_split", 10): (24.984e9 / (2 * 9.1321260e10), "profiles/traffic_diamond64_split.md"),
-    ("h_fp64", 0): ((359.834112e6 + 3.945472e6) / 4.6096304e9, "profiles/h_simt_kernel_diamond8_fp64.md"),
+    (1, "h_split", 10): (24.984e9 / (2 * 9.1321260e10), "profiles/traffic_diamond64_split.md"),
+    (1, "h_fp64", 0): ((359.834112e6 + 3.945472e6) / 4.6096304e9, "profiles/h_simt_kernel_diamond8_fp64.md"),
 }
 
 
@@ -189,7 +207,7 @@ def grouped(n_mol: int, device: int, steps: int = 3) -> dict:
     from paper_1912_06636_gb300 import nao, synth
 
     t0 = time.perf_counter()
-    systems, bs = synth.molecule_set(n_mol, seed=3000, n_min=3, n_max=60, b_min=20, b_max=336, **GROUP_GRID)
+    systems, bs = synth.molecule_set(n_mol, seed=3000, n_min=3, n_max=60, b_min=20, b_max=400, **GROUP_GRID)
     dev = torch.device("cuda", device)
     vs = [torch.from_numpy(s.potential()).to(dev) for s in systems]
     Ps = [torch.from_numpy(synth.density_matrix(s, 3000 + k)).to(dev) for k, s in enumerate(systems)]
@@ -197,7 +215,7 @@ def grouped(n_mol: int, device: int, steps: int = 3) -> dict:
     stream = torch.cuda.current_stream()
     out = {"workload": f"{n_mol} molecules of 3-60 atoms (log-uniform, seed 3000; species Si/A/B), "
                        f"{GROUP_GRID['n_rad']}x{GROUP_GRID['n_theta'] * GROUP_GRID['n_phi']} points per atom, "
-                       "batch sizes log-uniform in [20, 336]; one step = H + n of every molecule, split path "
+                       "batch sizes log-uniform in [20, 400]; one step = H + n of every molecule, split path "
                        "(12 slices)",
            "points": int(sum(s.n_points for s in systems)), "generate_s": gen_s}
 
@@ -321,36 +339,61 @@ def workload_name(args) -> str:
     if args.config == 1 and args.cells != 2:
         return (f"diamond{8 * args.cells ** 3}: {8 * args.cells ** 3}-atom diamond-lattice cluster, 25 basis functions "
                 "per atom, 60x306 points per atom, batches <= 300 points (profiling case)")
-    return WORKLOAD
+    if args.config == 2 and args.slab_layers != 15:
+        return (f"slab{25 * args.slab_layers}: {args.slab_layers} layers of the slab (5x5 per layer), 40 basis functions "
+                "per atom, 80x434 points per atom, batches <= 200 points (profiling case)")
+    return WORKLOADS[args.config]
 
 
-def make_workload(config: int, device: str, cells: int = 2):
+def bench_slices(args) -> int:
+    return args.slices if args.slices is not None else BENCH_SLICES.get(args.config, 12)
+
+
+def make_workload(config: int, device: str, cells: int = 2, layers: int = 15):
     from paper_1912_06636_gb300 import synth
 
-    s = synth.config(config, cells=cells) if config == 1 else synth.config(config)
+    kw = {1: {"cells": cells}, 2: {"layers": layers}}.get(config, {})
+    s = synth.config(config, **kw)
     v = s.potential()
-    P = synth.density_matrix(s, config)
+    # the slab's P is X X^T / 64 with X nb x 64 (a dense 15000 x 15000 product would dominate the set-up)
+    P = synth.density_matrix(s, config, rank=64 if config == 2 else None)
     return s, v, P
+
+
+def _sample(s, n, seed):
+    import numpy as np
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.sort(rng.choice(s.n_points, size=min(int(n), s.n_points), replace=False))
+
+
+def _oracle_rate(s, v, P, idx):
+    """Single-thread oracle on the points idx: (points/s, seconds of H, seconds of n)."""
+    import oracle
+
+    o = oracle.Oracle(s)
+    t0 = time.perf_counter()
+    o.hamiltonian(s.pt_xyz[idx], s.pt_w[idx], v[idx])
+    t1 = time.perf_counter()
+    o.density(s.pt_xyz[idx], P, s.pt_w[idx])
+    t2 = time.perf_counter()
+    return len(idx) / (t2 - t0), t1 - t0, t2 - t1
+
+
+def calibrate_sample(s, v, P, seconds: float, seed: int = 12344) -> int:
+    """Points of a sample that the single-thread oracle finishes in about `seconds` (from a
+    2,000-point trial run)."""
+    rate, _, _ = _oracle_rate(s, v, P, _sample(s, 2000, seed))
+    return int(max(1000, min(s.n_points, rate * seconds)))
 
 
 def cpu_baseline(s, v, P, n_sample: int, seed: int = 12345):
     """The FP64 oracle as it stands, on a seeded sample of the workload's points (1 thread)."""
-    import numpy as np
-
-    import oracle
-
-    rng = np.random.Generator(np.random.PCG64(seed))
-    idx = np.sort(rng.choice(s.n_points, size=min(n_sample, s.n_points), replace=False))
-    pts, w, vv = s.pt_xyz[idx], s.pt_w[idx], v[idx]
-    o = oracle.Oracle(s)
-    t0 = time.perf_counter()
-    o.hamiltonian(pts, w, vv)
-    t1 = time.perf_counter()
-    o.density(pts, P, w)
-    t2 = time.perf_counter()
-    return {"value": len(idx) / (t2 - t0), "unit": "points/s", "cores": 1, "kind": "oracle",
+    idx = _sample(s, n_sample, seed)
+    rate, th, tn = _oracle_rate(s, v, P, idx)
+    return {"value": rate, "unit": "points/s", "cores": 1, "kind": "oracle",
             "sample": f"{len(idx)} seeded points of the workload (H over those points, then n on them): "
-                      f"H {t1 - t0:.1f} s + n {t2 - t1:.1f} s"}
+                      f"H {th:.1f} s + n {tn:.1f} s"}
 
 
 def _oracle_chunk(job):
@@ -381,8 +424,7 @@ def cpu_baseline_all_cores(s, v, P, n_sample: int, seed: int = 12345, ex=None):
     import numpy as np
 
     procs = os.cpu_count() or 1
-    rng = np.random.Generator(np.random.PCG64(seed))
-    idx = np.sort(rng.choice(s.n_points, size=min(n_sample, s.n_points), replace=False))
+    idx = _sample(s, n_sample, seed)
     parts = np.array_split(idx, procs)
     jobs = [(dataclasses.replace(s, pt_xyz=s.pt_xyz[p], pt_w=s.pt_w[p]), v[p], P) for p in parts]
     own = ex is None
@@ -403,13 +445,14 @@ def cpu_baseline_all_cores(s, v, P, n_sample: int, seed: int = 12345, ex=None):
 
 def run_reference(args):
     """The oracle as it stands, on every host core (one process per core), on seeded samples of
-    the workload: each step is one sample (H then n)."""
+    the workload: each step is one sample (H then n), sized from a single-thread trial so that
+    a step takes about --cpu-seconds / 3 of wall time on all cores."""
     rank, _, world = dist_env()
     if rank != 0:
         return
-    s, v, P = make_workload(args.config, "cpu", args.cells)
+    s, v, P = make_workload(args.config, "cpu", args.cells, args.slab_layers)
     procs = os.cpu_count() or 1
-    n_sample = max(200 * procs, args.cpu_sample)
+    n_sample = max(200 * procs, calibrate_sample(s, v, P, procs * args.cpu_seconds / 3.0))
     times = []
     with _oracle_pool(procs) as ex:
         for k in range(args.warmup + args.steps):
@@ -418,6 +461,8 @@ def run_reference(args):
     val = statistics.mean(t["value"] for t in timed)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "points/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * s.n_points / val,
+            "ms_per_step_kind": (f"extrapolated: the whole grid ({s.n_points} points) at the rate measured on "
+                                 f"{n_sample}-point samples (each step times one sample)"),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(args), "precision": "fp64", "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": val, "unit": "points/s", "cores": procs, "kind": "oracle",
@@ -446,10 +491,12 @@ def main():
     from paper_1912_06636_gb300 import nao, replicas
 
     prec = args.prec or "split"
-    s, v_np, P_np = make_workload(args.config, f"cuda:{local_rank}", args.cells)
+    s, v_np, P_np = make_workload(args.config, f"cuda:{local_rank}", args.cells, args.slab_layers)
     dev = torch.device("cuda", local_rank)
     t0 = time.perf_counter()
-    g = nao.Grid(s, device=local_rank, max_batch_points=s.max_batch_points, split_slices=args.slices)
+    slices = bench_slices(args)
+    extra = {"scratch_bytes": args.scratch_mb << 20} if args.scratch_mb > 0 else {}
+    g = nao.Grid(s, device=local_rank, max_batch_points=s.max_batch_points, split_slices=slices, **extra)
     torch.cuda.synchronize()
     create_s = time.perf_counter() - t0
     info = g.info
@@ -513,13 +560,15 @@ def main():
             roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                         "traffic": None, "kernel": fam, "peak_source": peak_src}
         else:
-            pk = measured_peaks().get("bf16_tflops_sustained", 1719.5)
+            mp = measured_peaks()
+            pk, pk_s = mp.get("bf16_tflops", 1900.0), mp.get("bf16_tflops_sustained", 1700.0)
+            src_pk = "MEASURED_PEAKS.json bf16_tflops (burst; of measured)" if "bf16_tflops" in mp else "fallback 1.9 PFLOP/s"
             roofline = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
                         "traffic": None, "kernel": fam,
                         "work": f"{pairs} slice products x algorithmic FLOPs (sum_b 4 P_b N_b (N_b+1) for H)",
-                        "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}
+                        "peak_source": src_pk, "frac_of_sustained": achieved / pk_s}
         roofline.update({"launches": launches, "avg_launch_ms": fam_ms / max(launches, 1)})
-        tk = (fam, int(g.split_slices) if prec == "split" else 0)
+        tk = (args.config, fam, int(g.split_slices) if prec == "split" else 0)
         if tk in TRAFFIC_PER_FLOP_H and launches:
             per_flop, src = TRAFFIC_PER_FLOP_H[tk]
             roofline["traffic"] = per_flop * info.flops_h * args.steps / launches
@@ -544,7 +593,7 @@ def main():
         "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "split": "bf16x-slices+f64"}[prec],
         "data": "synthetic",
         "config": {"workload": workload_name(args), "precision": prec, "parallelism": f"replicas{world}",
-                   "split_slices": args.slices if prec == "split" else None,
+                   "split_slices": slices if prec == "split" else None,
                    "l2": f"inputs/working set larger than L2: {scratch_gb:.1f} GB of evaluated basis functions "
                          "written and re-read per step",
                    "n_points": g.n_points, "n_basis": g.nb, "n_batches": int(info.n_batches),
@@ -593,7 +642,7 @@ def main():
                 other[p] = {"unavailable": str(e)}
         # the split path at the library's default slice count
         d = nao.nao_default_options().split_slices
-        if d != args.slices:
+        if d != slices:
             try:
                 g2 = nao.Grid(s, device=local_rank, max_batch_points=s.max_batch_points)
                 g2.integrate_h(v, prec="split", H=H, stream=stream)
@@ -660,9 +709,10 @@ def main():
             line["periodic"] = {"unavailable": str(e)}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(s, v_np, P_np, args.cpu_sample)
+        n1 = calibrate_sample(s, v_np, P_np, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(s, v_np, P_np, n1)
         try:
-            line["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores(s, v_np, P_np, 8 * args.cpu_sample)
+            line["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores(s, v_np, P_np, (os.cpu_count() or 1) * n1)
         except Exception as e:  # the single-thread figure stands on its own
             line["cpu_baseline"]["all_cores"] = {"unavailable": f"{type(e).__name__}: {e}"}
     if g.h:

@@ -122,7 +122,7 @@ typedef struct {
     int64_t flops_h;          /* algorithmic FLOPs of one nao_integrate_h: sum_b 4 P_b N_b (N_b+1) */
     int64_t flops_n;          /* algorithmic FLOPs of one nao_update_density: sum_b 2 P_b N_b^2 + 2 P_b N_b */
     int32_t n_systems;        /* systems of the handle (1 for nao_grid_create) */
-    int32_t reserved0;
+    int32_t n_atoms;          /* atoms of the handle (all systems); F of nao_pulay_forces is 3 x this */
 } nao_grid_info;
 
 /* Fill *opts with the defaults above. */
@@ -307,9 +307,11 @@ nao_status nao_pulay_forces(nao_grid *g, const double *n_dev, const double *q_de
  * for the n_k points k_dev [n_k*3] (cartesian, 1/bohr): Eq. Bloch-basis inserted into
  * Eq. HamPeriodic. h_uc_dev [n_rs*n_rs], fn_map_dev/fn_image_dev [n_rs], img_cell_dev [3*n_images]
  * on the device; lattice on the host; hk_dev overwritten. FP64 atomics (one per element and k).
- * The maps are read on the device unchecked: every fn_map entry must lie in [0, nb) and every
- * fn_image entry in [0, n_images), as nao_periodic_basis_map writes them.
- * Errors: NAO_ERR_INVALID_ARG, NAO_ERR_CUDA.                                                      */
+ * Every fn_map entry must lie in [0, nb) and every fn_image entry in [0, n_images), as
+ * nao_periodic_basis_map writes them; the maps live on the device, so the kernel checks them
+ * itself: an h^uc element with an out-of-range entry is skipped (nothing outside hk_dev and
+ * img_cell_dev is touched) and counted into *err_dev, a device int32 the call zeroes first
+ * (err_dev may be NULL: no count). Errors: NAO_ERR_INVALID_ARG, NAO_ERR_CUDA.                     */
 nao_status nao_periodic_images(const double *atom_xyz, int32_t n_atoms, const double *lattice, double reach,
                                int32_t max_images, double *img_xyz, int32_t *img_atom, int32_t *img_cell,
                                int32_t *n_images);
@@ -317,8 +319,8 @@ nao_status nao_periodic_basis_map(const int32_t *atom_species, int32_t n_atoms, 
                                   int32_t n_species, const int32_t *fn_l, const int32_t *img_atom, int32_t n_images,
                                   int64_t max_rs, int32_t *fn_map, int32_t *fn_image, int64_t *n_rs);
 nao_status nao_bloch_sum(const double *h_uc_dev, int64_t n_rs, const int32_t *fn_map_dev, const int32_t *fn_image_dev,
-                         const int32_t *img_cell_dev, const double *lattice, const double *k_dev, int32_t n_k, int64_t nb,
-                         double *hk_dev, void *cuda_stream);
+                         const int32_t *img_cell_dev, int32_t n_images, const double *lattice, const double *k_dev,
+                         int32_t n_k, int64_t nb, double *hk_dev, int32_t *err_dev, void *cuda_stream);
 
 /* The same two operations with HOST buffers: the library copies the inputs to the device,
  * runs the operation on the given stream, copies the results back and synchronises the
@@ -382,14 +384,36 @@ nao_status nao_profile_read(nao_grid *g, nao_profile *out, int32_t reset);
  *     it needs clearing: every entry read is first written by the same call). Calls whose
  *     work overlaps on the GPU (other streams or handles) race on it.
  *   - The first call on a device looks up the array's device address; make that first call
- *     before any stream capture.
+ *     before any stream capture. The address is kept for the rest of the process: after a
+ *     cudaDeviceReset (or any teardown of the device's primary context) the library's module
+ *     is loaded again and the array may move, so this entry point must not be used on that
+ *     device again in the same process.
  * Arguments and errors as nao_integrate_h (no precision argument: FP64).                    */
 #define NAO_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
 nao_status nao_integrate_h_noalloc(nao_grid *g, const double *v_dev, uint32_t terms, double *H_dev,
                                    void *cuda_stream);
 
-/* Wait for the handle's enqueued work and report a device-side failure, if any. */
+/* Wait for the handle's enqueued work and report a device-side failure, if any: a bounded
+ * device wait that gave up (NAO_ERR_TIMEOUT; its kernel skipped the rest of its work, so that
+ * call's results are incomplete). The failure is reported once: the handle's error word is
+ * cleared, and later calls run normally.                                                    */
 nao_status nao_sync_status(nao_grid *g);
+
+/* Failure handling without a GPU fault (the paper has no counterpart; test support).
+ * nao_fault_inject: makes the n-th device allocation ("alloc:<n>"), host<->device copy
+ * ("copy:<n>") or kernel launch ("launch:<n>") that the library attempts after this call fail
+ * once, as if the CUDA call had failed (nothing is allocated, copied or launched for it). The
+ * entry point that hits it returns NAO_ERR_OUT_OF_MEMORY (allocation) or NAO_ERR_CUDA with a
+ * message that starts "injected failure"; a create leaves *out NULL, a call on a handle leaves the
+ * handle usable and destroyable (its outputs of that call are undefined). Process-wide; NULL or ""
+ * clears a pending injection; the environment variable NAO_FAULT_INJECT sets the same the first
+ * time the library needs it. Errors: NAO_ERR_INVALID_ARG (malformed spec).
+ * nao_check_wait_timeout: enqueues one bounded device wait (the mbarrier wait of the tensor-core
+ * pipelines) on a barrier that nothing completes; after max_cycles SM cycles (1..2^34) it gives
+ * up and records NAO_ERR_TIMEOUT in the handle's error word, as a stuck pipeline would, for
+ * nao_sync_status to report. Nothing else is touched.                                          */
+nao_status nao_fault_inject(const char *spec);
+nao_status nao_check_wait_timeout(nao_grid *g, int64_t max_cycles, void *cuda_stream);
 
 /* Static text for a status code. */
 const char *nao_status_string(nao_status s);

@@ -2,6 +2,7 @@
 // per-call dispatch of the evaluation and contraction kernels onto the caller's stream.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -19,7 +20,67 @@ nao_status fail(nao_status s, const std::string &msg) {
     return s;
 }
 
+// ---- host-side fault injection ------------------------------------------------------------
+// Tests how every entry point unwinds from a failed CUDA call without faulting a GPU: the n-th
+// device allocation, host<->device copy or kernel launch counted from the setting fails, once,
+// as if the CUDA call had returned an error (nothing is allocated, copied or launched for it).
+// Set from the environment variable NAO_FAULT_INJECT ("alloc:<n>", "copy:<n>", "launch:<n>") when
+// the library first needs it, or at run time by nao_fault_inject.
+enum FaultKind { FAULT_NONE = 0, FAULT_ALLOC, FAULT_COPY, FAULT_LAUNCH };
+struct FaultState {
+    std::mutex mu;
+    int kind = FAULT_NONE;
+    int64_t n = 0, seen = 0;
+};
+thread_local bool g_fault_fired = false;  // the failure being reported was injected
+
+bool parse_fault(const char *spec, int *kind, int64_t *n) {
+    *kind = FAULT_NONE;
+    *n = 0;
+    if (!spec || !*spec) return true;
+    const char *colon = std::strchr(spec, ':');
+    if (!colon) return false;
+    const std::string k(spec, colon - spec);
+    char *end = nullptr;
+    const long long v = std::strtoll(colon + 1, &end, 10);
+    if (end == colon + 1 || *end != '\0' || v < 1) return false;
+    if (k == "alloc") *kind = FAULT_ALLOC;
+    else if (k == "copy") *kind = FAULT_COPY;
+    else if (k == "launch") *kind = FAULT_LAUNCH;
+    else return false;
+    *n = v;
+    return true;
+}
+
+FaultState &faults() {
+    static FaultState *f = [] {
+        FaultState *st = new FaultState();  // never destroyed: used until the process exits
+        int kind;
+        int64_t n;
+        if (parse_fault(std::getenv("NAO_FAULT_INJECT"), &kind, &n)) {
+            st->kind = kind;
+            st->n = n;
+        }
+        return st;
+    }();
+    return *f;
+}
+
+// True (once) when this operation of the given kind is the one chosen to fail.
+bool fault_fires(int kind) {
+    FaultState &F = faults();
+    std::lock_guard<std::mutex> lock(F.mu);
+    if (F.kind != kind || ++F.seen < F.n) return false;
+    F.kind = FAULT_NONE;
+    g_fault_fired = true;
+    return true;
+}
+
 nao_status cuda_fail(cudaError_t e, const char *what) {
+    if (g_fault_fired) {
+        g_fault_fired = false;
+        return fail(NAO_ERR_CUDA, std::string("injected failure: ") + what);
+    }
     return fail(NAO_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
@@ -28,6 +89,12 @@ nao_status cuda_fail(cudaError_t e, const char *what) {
         cudaError_t e_ = (expr);                           \
         if (e_ != cudaSuccess) return cuda_fail(e_, #expr); \
     } while (0)
+
+// cudaMemcpyAsync, or the injected failure of a copy.
+cudaError_t copy_async(void *dst, const void *src, size_t bytes, cudaMemcpyKind kind, cudaStream_t st) {
+    if (fault_fires(FAULT_COPY)) return cudaErrorInvalidValue;
+    return cudaMemcpyAsync(dst, src, bytes, kind, st);
+}
 
 // Makes g's device current for the lifetime of the guard and restores the caller's.
 struct DeviceGuard {
@@ -85,6 +152,10 @@ nao_status dev_alloc(nao_grid *g, T **p, size_t count) {
     cudaMemPool_t pool;
     nao_status st = device_pool(g->device, &pool);
     if (st) return st;
+    if (fault_fires(FAULT_ALLOC)) {
+        g_fault_fired = false;
+        return fail(NAO_ERR_OUT_OF_MEMORY, "injected failure: device allocation of " + std::to_string(bytes) + " bytes");
+    }
     const cudaError_t e = cudaMallocFromPoolAsync(&q, bytes, pool, g->setup);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -102,7 +173,7 @@ template <class T>
 nao_status upload(nao_grid *g, T **p, const T *src, size_t count) {
     nao_status st = dev_alloc(g, p, count);
     if (st != NAO_OK) return st;
-    if (count) NAO_CUDA(cudaMemcpyAsync(*p, src, count * sizeof(T), cudaMemcpyHostToDevice, g->setup));
+    if (count) NAO_CUDA(copy_async(*p, src, count * sizeof(T), cudaMemcpyHostToDevice, g->setup));
     return NAO_OK;
 }
 
@@ -158,6 +229,22 @@ nao_status mark_done(nao_grid *g, cudaStream_t st) {
     g->used = true;
     return NAO_OK;
 }
+
+// Also marks the end of a call's work when the call returns early, after a failure part-way
+// through its launches: the kernels it did enqueue are then still covered by ev_last, which
+// destroy and nao_sync_status wait for before anything is freed or read. The failure's message
+// is kept.
+struct CallEnd {
+    nao_grid *g;
+    cudaStream_t st;
+    CallEnd(nao_grid *g_, cudaStream_t s) : g(g_), st(s) {}
+    ~CallEnd() {
+        const std::string msg = g_last_error;
+        if (cudaEventRecord(g->ev_last, st) == cudaSuccess) g->used = true;
+        else cudaGetLastError();
+        g_last_error = msg;
+    }
+};
 
 double factorial(int n) {
     double f = 1.0;
@@ -316,7 +403,7 @@ nao_status build(nao_grid *g, const nao_system_desc *descs, int32_t n_sys, const
         if ((st = dev_alloc(g, &d_minr2, minr2.size()))) return st;
         NAO_CUDA(launch_relevance_minr2(d_atoms, d_bmol, d_aoff, max_atoms, d_px, d_py, d_pz, d_boff, nbat, d_minr2,
                                         g->setup));
-        NAO_CUDA(cudaMemcpyAsync(minr2.data(), d_minr2, minr2.size() * sizeof(double), cudaMemcpyDeviceToHost,
+        NAO_CUDA(copy_async(minr2.data(), d_minr2, minr2.size() * sizeof(double), cudaMemcpyDeviceToHost,
                                  g->setup));
         NAO_CUDA(cudaStreamSynchronize(g->setup));
         cudaFreeAsync(d_minr2, g->setup);
@@ -560,6 +647,7 @@ cudaEvent_t take_event(nao_grid *g) {
 // Runs one launcher; when profiling, brackets it with events on the stream.
 template <class F>
 cudaError_t timed(nao_grid *g, int kid, cudaStream_t st, F &&launch) {
+    if (fault_fires(FAULT_LAUNCH)) return cudaErrorLaunchFailure;
     if (!g->profiling) return launch();
     cudaEvent_t a = take_event(g), b = take_event(g);
     if (!a || !b) return launch();
@@ -601,14 +689,21 @@ nao_status split_lists(nao_grid *g) {
             if (N == 0) continue;
             const int TN = g->split_tn[b], k = TN == 48 ? 0 : 1;
             const SplitGeom G(P, N, S, TN);
-            nao_split_h_items(b, N, TN, hw[k]);
+            nao_split_h_items(b, P, N, TN, S, hw[k]);
             for (int Q = 0; Q < G.n_qt; Q++) nw[k].push_back({b, Q, G.n_jtN, 0});  // all J tiles in one CTA
         }
         // the persistent contraction kernels take items round-robin: heaviest first (H: longest
-        // K; density: most function tiles), so that every CTA gets a similar share
+        // K, i.e. most K chunks in the item's segment; density: most function tiles), so that
+        // every CTA gets a similar share
+        auto item_kc = [&](const HWork &x) {
+            const SplitGeom G(g->Pb[x.batch], g->Nb[x.batch], S);
+            int kc0, kc1;
+            nao_split_h_seg_range(G.n_kc, nao_split_h_nseg(g->Pb[x.batch], S), x.pad, S, kc0, kc1);
+            return kc1 - kc0;
+        };
         for (int k = 0; k < 2; k++) {
             std::stable_sort(hw[k].begin() + c.hw0[k], hw[k].end(),
-                             [&](const HWork &x, const HWork &y) { return g->Pb[x.batch] > g->Pb[y.batch]; });
+                             [&](const HWork &x, const HWork &y) { return item_kc(x) > item_kc(y); });
             std::stable_sort(nw[k].begin() + c.nw0[k], nw[k].end(),
                              [](const HWork &x, const HWork &y) { return x.tj > y.tj; });
             c.hw1[k] = (int32_t)hw[k].size();
@@ -628,10 +723,10 @@ nao_status split_lists(nao_grid *g) {
     hw[0].insert(hw[0].end(), hw[1].begin(), hw[1].end());
     nw[0].insert(nw[0].end(), nw[1].begin(), nw[1].end());
     if (!hw[0].empty())
-        NAO_CUDA(cudaMemcpyAsync(g->d_split_hw, hw[0].data(), hw[0].size() * sizeof(HWork), cudaMemcpyHostToDevice, g->setup));
+        NAO_CUDA(copy_async(g->d_split_hw, hw[0].data(), hw[0].size() * sizeof(HWork), cudaMemcpyHostToDevice, g->setup));
     if (!nw[0].empty())
-        NAO_CUDA(cudaMemcpyAsync(g->d_split_nw, nw[0].data(), nw[0].size() * sizeof(HWork), cudaMemcpyHostToDevice, g->setup));
-    NAO_CUDA(cudaMemcpyAsync(g->d_split_tn, g->split_tn.data(), g->split_tn.size() * sizeof(int32_t),
+        NAO_CUDA(copy_async(g->d_split_nw, nw[0].data(), nw[0].size() * sizeof(HWork), cudaMemcpyHostToDevice, g->setup));
+    NAO_CUDA(copy_async(g->d_split_tn, g->split_tn.data(), g->split_tn.size() * sizeof(int32_t),
                              cudaMemcpyHostToDevice, g->setup));
     NAO_CUDA(cudaStreamSynchronize(g->setup));
     g->n_split_hw = nh;
@@ -655,12 +750,18 @@ nao_status split_setup(nao_grid *g) {
     for (int64_t b = 0; b < g->n_batches; b++) {
         const int64_t Ppad = (g->Pb[b] + NAO_PPAD - 1) / NAO_PPAD * NAO_PPAD;
         const int64_t N64 = (g->Nb[b] + 63) / 64 * 64;
-        // every slice-group sum must stay below 2^24: K (g+1) 2^10 with g + 1 <= S
-        if (Ppad > NAO_SPLIT_MAX_PPAD || 4 * Ppad * S >= 16384 || N64 * S >= 16384)
-            return fail(NAO_ERR_UNSUPPORTED, "batch too large for exact slice sums (points " + std::to_string(g->Pb[b]) +
-                                                 ", basis " + std::to_string(g->Nb[b]) + ", slices " + std::to_string(S) + ")");
+        // every slice-group sum must stay below 2^24: K (g+1) 2^10 with g + 1 <= S. The H
+        // contraction (K = 4 Ppad) splits K into segments where needed; the density's K is the
+        // batch's basis (N rounded up to 64), one accumulation per function tile
+        if (Ppad > NAO_SPLIT_MAX_PPAD)
+            return fail(NAO_ERR_UNSUPPORTED, "batch too large for the split path (points " + std::to_string(g->Pb[b]) +
+                                                 ", at most " + std::to_string(NAO_SPLIT_MAX_PPAD) + ")");
+        if (N64 * S >= 16384)
+            return fail(NAO_ERR_UNSUPPORTED, "batch too large for exact slice sums (basis " + std::to_string(g->Nb[b]) +
+                                                 ", slices " + std::to_string(S) + ")");
     }
     NAO_CUDA(split_configure());
+    g->split_chunks.clear();  // a failed earlier set-up may have planned part of them
     const int64_t budget = std::max<int64_t>(g->opt.scratch_bytes > 0 ? 2 * g->opt.scratch_bytes : (int64_t(4) << 30),
                                              int64_t(1) << 20);
     std::vector<int64_t> off_h(g->n_batches, 0), off_n(g->n_batches, 0);
@@ -694,7 +795,7 @@ nao_status split_setup(nao_grid *g) {
                 for (int TN : {48, 32}) {
                     if (TN == 48 && S > 10) continue;
                     std::vector<HWork> tmp;
-                    nao_split_h_items(b, N, TN, tmp);
+                    nao_split_h_items(b, P, N, TN, S, tmp);
                     best_h = std::max(best_h, (int64_t)tmp.size());
                 }
                 cap_h += best_h;
@@ -783,7 +884,7 @@ nao_status split_tune(nao_grid *g, uint32_t terms, cudaStream_t st) {
             for (int32_t b = c.b0; b < c.b1; b++) {
                 if (bucket[b] != k) continue;
                 std::vector<HWork> tmp;
-                nao_split_h_items(b, g->Nb[b], 48, tmp);
+                nao_split_h_items(b, g->Pb[b], g->Nb[b], 48, S, tmp);
                 base48 += (int64_t)tmp.size();
             }
             const int64_t reps = base48 > 0 ? (8 * 152 + base48 - 1) / base48 : 0;
@@ -792,14 +893,14 @@ nao_status split_tune(nao_grid *g, uint32_t terms, cudaStream_t st) {
                 std::vector<HWork> items;
                 for (int64_t r = 0; r < reps; r++)
                     for (int32_t b = c.b0; b < c.b1; b++)
-                        if (bucket[b] == k) nao_split_h_items(b, g->Nb[b], TN, items);
+                        if (bucket[b] == k) nao_split_h_items(b, g->Pb[b], g->Nb[b], TN, S, items);
                 n_items = (int64_t)items.size();
                 if (items.empty()) break;
                 if ((int64_t)items.size() > g->cap_tune_hw) {
                     if ((rs = dev_alloc(g, &g->d_tune_hw, items.size()))) break;
                     g->cap_tune_hw = (int64_t)items.size();
                 }
-                ce = cudaMemcpyAsync(g->d_tune_hw, items.data(), items.size() * sizeof(HWork), cudaMemcpyHostToDevice,
+                ce = copy_async(g->d_tune_hw, items.data(), items.size() * sizeof(HWork), cudaMemcpyHostToDevice,
                                      g->setup);
                 if (ce == cudaSuccess) ce = cudaStreamSynchronize(g->setup);
                 ms[w] = 1e30f;
@@ -835,6 +936,7 @@ nao_status split_tune(nao_grid *g, uint32_t terms, cudaStream_t st) {
 // written on the call's stream by kernels that carry the values in their arguments.
 nao_status upload_tables(nao_grid *g, int first, int count, cudaStream_t st) {
     const size_t n = (size_t)g->n_sys;
+    if (fault_fires(FAULT_LAUNCH)) return cuda_fail(cudaErrorLaunchFailure, "launch_set_pointers");
     NAO_CUDA(launch_set_pointers(g->d_tab + first * n, g->h_tab.data() + first * n, (int32_t)(count * n), st));
     return NAO_OK;
 }
@@ -1156,7 +1258,7 @@ nao_status nao_get_info(const nao_grid *g, nao_grid_info *info) {
     info->flops_h = g->flops_h;
     info->flops_n = g->flops_n;
     info->n_systems = g->n_sys;
-    info->reserved0 = 0;
+    info->n_atoms = g->n_atoms;
     return NAO_OK;
 }
 
@@ -1231,6 +1333,7 @@ nao_status nao_integrate_h(nao_grid *g, const double *v_dev, uint32_t terms, nao
     if ((st = check_terms(terms)) || (st = check_prec(prec))) return st;
     DeviceGuard guard(g->device);
     if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    CallEnd call_end(g, static_cast<cudaStream_t>(cuda_stream));
     set_tab(g, 0, 0, H_dev);
     set_tab(g, 1, 0, v_dev);
     if ((st = run_h(g, terms, prec, static_cast<cudaStream_t>(cuda_stream)))) return st;
@@ -1246,6 +1349,7 @@ nao_status nao_integrate_h_tau(nao_grid *g, const double *v_dev, const double *v
     if ((st = check_prec(prec))) return st;
     DeviceGuard guard(g->device);
     if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    CallEnd call_end(g, static_cast<cudaStream_t>(cuda_stream));
     set_tab(g, 0, 0, H_dev);
     set_tab(g, 1, 0, v_dev);
     set_tab(g, 6, 0, (terms & NAO_TERM_TAU) ? vtau_dev : nullptr);
@@ -1264,6 +1368,7 @@ nao_status nao_integrate_h_many(nao_grid *g, const double *const *v_dev, uint32_
     if ((st = check_terms(terms)) || (st = check_prec(prec))) return st;
     DeviceGuard guard(g->device);
     if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    CallEnd call_end(g, static_cast<cudaStream_t>(cuda_stream));
     for (int m = 0; m < g->n_sys; m++) {
         set_tab(g, 0, m, H_dev[m]);
         set_tab(g, 1, m, v_dev ? v_dev[m] : nullptr);
@@ -1280,6 +1385,7 @@ nao_status nao_update_density(nao_grid *g, const double *P_dev, nao_precision pr
     if ((st = check_prec(prec))) return st;
     DeviceGuard guard(g->device);
     if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    CallEnd call_end(g, static_cast<cudaStream_t>(cuda_stream));
     set_tab(g, 2, 0, P_dev);
     set_tab(g, 3, 0, n_dev);
     set_tab(g, 4, 0, n_electrons_dev);
@@ -1298,6 +1404,7 @@ nao_status nao_update_density_many(nao_grid *g, const double *const *P_dev, nao_
     if ((st = check_prec(prec))) return st;
     DeviceGuard guard(g->device);
     if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    CallEnd call_end(g, static_cast<cudaStream_t>(cuda_stream));
     for (int m = 0; m < g->n_sys; m++) {
         set_tab(g, 2, m, P_dev[m]);
         set_tab(g, 3, m, n_dev[m]);
@@ -1319,6 +1426,7 @@ nao_status nao_update_density_gradient_many(nao_grid *g, const double *const *P_
     if ((st = check_prec(prec))) return st;
     DeviceGuard guard(g->device);
     if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    CallEnd call_end(g, static_cast<cudaStream_t>(cuda_stream));
     for (int m = 0; m < g->n_sys; m++) {
         set_tab(g, 2, m, P_dev[m]);
         set_tab(g, 3, m, n_dev[m]);
@@ -1347,6 +1455,7 @@ nao_status nao_update_density_hessian(nao_grid *g, const double *P_dev, nao_prec
     if (prec != NAO_FP64) return fail(NAO_ERR_UNSUPPORTED, "the density Hessian is built on the FP64 path only");
     DeviceGuard guard(g->device);
     if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    CallEnd call_end(g, static_cast<cudaStream_t>(cuda_stream));
     if ((st = hess_plan(g))) return st;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     set_tab(g, 2, 0, P_dev);
@@ -1373,6 +1482,7 @@ nao_status nao_pulay_matrices(nao_grid *g, const double *v_dev, nao_precision pr
     if (prec != NAO_FP64) return fail(NAO_ERR_UNSUPPORTED, "the Pulay matrix elements are built on the FP64 path only");
     DeviceGuard guard(g->device);
     if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    CallEnd call_end(g, static_cast<cudaStream_t>(cuda_stream));
     if ((st = pulay_plan(g))) return st;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     set_tab(g, 1, 0, v_dev);
@@ -1397,6 +1507,7 @@ nao_status nao_pulay_forces(nao_grid *g, const double *n_dev, const double *q_de
     if (!n_dev || !q_dev || !M_dev || !S_dev || !F_dev) return fail(NAO_ERR_INVALID_ARG, "a buffer is NULL");
     DeviceGuard guard(g->device);
     if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    CallEnd call_end(g, static_cast<cudaStream_t>(cuda_stream));
     if ((st = pulay_plan(g))) return st;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     NAO_CUDA(launch_pulay_forces(n_dev, q_dev, M_dev, S_dev, g->d_atom_basis, g->n_atoms, g->nb, F_dev, s));
@@ -1404,7 +1515,7 @@ nao_status nao_pulay_forces(nao_grid *g, const double *n_dev, const double *q_de
 }
 
 static nao_status ensure_staging(nao_grid *g) {
-    if (g->d_stage_in) return NAO_OK;
+    if (g->d_stage_in && g->d_stage_out && g->d_stage_ne) return NAO_OK;
     const size_t big = (size_t)std::max<int64_t>(g->nb * g->nb, g->n_points);
     nao_status st;
     if ((st = dev_alloc(g, &g->d_stage_in, big)) || (st = dev_alloc(g, &g->d_stage_out, big)) ||
@@ -1422,17 +1533,18 @@ nao_status nao_integrate_h_host(nao_grid *g, const double *v_host, uint32_t term
     if ((st = check_terms(terms)) || (st = check_prec(prec))) return st;
     DeviceGuard guard(g->device);
     if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    CallEnd call_end(g, static_cast<cudaStream_t>(cuda_stream));
     if ((st = ensure_staging(g))) return st;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const double *v = nullptr;
     if (v_host) {
-        NAO_CUDA(cudaMemcpyAsync(g->d_stage_in, v_host, (size_t)g->n_points * sizeof(double), cudaMemcpyHostToDevice, s));
+        NAO_CUDA(copy_async(g->d_stage_in, v_host, (size_t)g->n_points * sizeof(double), cudaMemcpyHostToDevice, s));
         v = g->d_stage_in;
     }
     set_tab(g, 0, 0, g->d_stage_out);
     set_tab(g, 1, 0, v);
     if ((st = run_h(g, terms, prec, s))) return st;
-    NAO_CUDA(cudaMemcpyAsync(H_host, g->d_stage_out, (size_t)g->nb * g->nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+    NAO_CUDA(copy_async(H_host, g->d_stage_out, (size_t)g->nb * g->nb * sizeof(double), cudaMemcpyDeviceToHost, s));
     if ((st = mark_done(g, s))) return st;
     NAO_CUDA(cudaStreamSynchronize(s));
     return NAO_OK;
@@ -1446,16 +1558,17 @@ nao_status nao_update_density_host(nao_grid *g, const double *P_host, nao_precis
     if ((st = check_prec(prec))) return st;
     DeviceGuard guard(g->device);
     if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    CallEnd call_end(g, static_cast<cudaStream_t>(cuda_stream));
     if ((st = ensure_staging(g))) return st;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    NAO_CUDA(cudaMemcpyAsync(g->d_stage_in, P_host, (size_t)g->nb * g->nb * sizeof(double), cudaMemcpyHostToDevice, s));
+    NAO_CUDA(copy_async(g->d_stage_in, P_host, (size_t)g->nb * g->nb * sizeof(double), cudaMemcpyHostToDevice, s));
     set_tab(g, 2, 0, g->d_stage_in);
     set_tab(g, 3, 0, g->d_stage_out);
     set_tab(g, 4, 0, n_electrons_host ? g->d_stage_ne : nullptr);
     if ((st = run_n(g, prec, s))) return st;
-    NAO_CUDA(cudaMemcpyAsync(n_host, g->d_stage_out, (size_t)g->n_points * sizeof(double), cudaMemcpyDeviceToHost, s));
+    NAO_CUDA(copy_async(n_host, g->d_stage_out, (size_t)g->n_points * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (n_electrons_host)
-        NAO_CUDA(cudaMemcpyAsync(n_electrons_host, g->d_stage_ne, sizeof(double), cudaMemcpyDeviceToHost, s));
+        NAO_CUDA(copy_async(n_electrons_host, g->d_stage_ne, sizeof(double), cudaMemcpyDeviceToHost, s));
     if ((st = mark_done(g, s))) return st;
     NAO_CUDA(cudaStreamSynchronize(s));
     return NAO_OK;
@@ -1471,6 +1584,7 @@ nao_status nao_evaluate_batch(nao_grid *g, int64_t batch, nao_precision prec, do
     if ((st = check_prec(prec))) return st;
     DeviceGuard guard(g->device);
     if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    CallEnd call_end(g, static_cast<cudaStream_t>(cuda_stream));
     NAO_CUDA(launch_eval_one(g->sys, (int32_t)batch, prec, phi_dev, grad_dev, static_cast<cudaStream_t>(cuda_stream)));
     return mark_done(g, static_cast<cudaStream_t>(cuda_stream));
 }
@@ -1511,10 +1625,39 @@ nao_status nao_sync_status(nao_grid *g) {
     // this handle's work only: its last call, then the error word on the setup stream
     if (g->used) NAO_CUDA(cudaEventSynchronize(g->ev_last));
     int32_t err[4] = {0, 0, 0, 0};
-    NAO_CUDA(cudaMemcpyAsync(err, g->d_err, sizeof(err), cudaMemcpyDeviceToHost, g->setup));
+    NAO_CUDA(copy_async(err, g->d_err, sizeof(err), cudaMemcpyDeviceToHost, g->setup));
     NAO_CUDA(cudaStreamSynchronize(g->setup));
-    if (err[0] != 0) return fail((nao_status)err[0], "device-side check failed (code " + std::to_string(err[1]) + ")");
+    if (err[0] != 0) {
+        // reported once: the word is cleared so that the handle's later calls run again
+        NAO_CUDA(cudaMemsetAsync(g->d_err, 0, sizeof(err), g->setup));
+        NAO_CUDA(cudaStreamSynchronize(g->setup));
+        return fail((nao_status)err[0], "device-side check failed (code " + std::to_string(err[1]) + ")");
+    }
     return NAO_OK;
+}
+
+nao_status nao_fault_inject(const char *spec) {
+    int kind;
+    int64_t n;
+    if (!parse_fault(spec, &kind, &n))
+        return fail(NAO_ERR_INVALID_ARG, "fault spec must be alloc:<n>, copy:<n> or launch:<n> (n >= 1)");
+    FaultState &F = faults();
+    std::lock_guard<std::mutex> lock(F.mu);
+    F.kind = kind;
+    F.n = n;
+    F.seen = 0;
+    return NAO_OK;
+}
+
+nao_status nao_check_wait_timeout(nao_grid *g, int64_t max_cycles, void *cuda_stream) {
+    nao_status st = check_handle(g);
+    if (st) return st;
+    if (max_cycles < 1 || max_cycles > (int64_t(1) << 34)) return fail(NAO_ERR_INVALID_ARG, "max_cycles outside 1..2^34");
+    DeviceGuard guard(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    CallEnd call_end(g, s);
+    NAO_CUDA(launch_wait_timeout_probe(max_cycles, g->d_err, s));
+    return mark_done(g, s);
 }
 
 const char *nao_status_string(nao_status s) {

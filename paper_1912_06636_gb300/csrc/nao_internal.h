@@ -16,7 +16,7 @@
 #define NAO_PPAD 16          // batch points are padded to a multiple of this in scratch
 #define NAO_MAX_BATCH 1024   // largest accepted max_batch_points
 #define NAO_SPLIT_MAX_SLICES 12  // tensor-memory budget: S groups x TN FP32 columns <= 512 columns
-#define NAO_SPLIT_MAX_PPAD 512   // split path: padded batch points (4 Ppad S < 2^14 keeps sums exact)
+#define NAO_SPLIT_MAX_PPAD 512   // split path: padded batch points (the slicers' shared-memory column tables)
 
 // One radial function instance relevant to a batch: atom, radial function, position of
 // its m = -l entry in the batch's reduced basis, l.
@@ -143,15 +143,42 @@ struct SplitGeom {
 };
 
 struct HWork {  // one upper-triangular tile pair of one batch's h[B] (Eq. batch_matrix_mult)
-    int32_t batch, ti, tj, pad;
+    int32_t batch, ti, tj, pad;  // split H items: pad = the K segment (below)
 };
 
-// Split H work items of one batch with N functions for tile width TN: per 128-row tile I, the
-// TN-column tiles J >= floor(128 I / TN) (those reaching the upper triangle).
-inline void nao_split_h_items(int32_t b, int N, int TN, std::vector<HWork> &out) {
-    const int nI = (N + 127) / 128, nJ = (N + TN - 1) / TN;
+// K segments of the split H contraction. A slice-order group's FP32 accumulator sums K products
+// of at most 2^10 for each of its g + 1 <= S slice pairs; it stays an exact integer while
+// K (g + 1) 2^10 < 2^24, i.e. K S < 2^14. A batch whose 4 Ppad weighted columns meet that bound
+// is one accumulation; a larger batch is accumulated in segments of nao_split_kc_seg(S) chunks
+// of 64 columns (64 kc_seg S < 2^14), each recombined and scattered into H on its own (H is a
+// sum over K, so the segments' FP64 partial sums simply add; Eq. H_decomp).
+__host__ __device__ constexpr int nao_split_kc_seg(int S) { return 255 / S; }
+__host__ __device__ inline int nao_split_h_nseg(int P, int S) {
+    const int Ppad = (P + NAO_PPAD - 1) / NAO_PPAD * NAO_PPAD;
+    if (4 * Ppad * S < 16384) return 1;
+    const int n_kc = (4 * Ppad + 16 + 63) / 64, kcs = nao_split_kc_seg(S);
+    return (n_kc + kcs - 1) / kcs;
+}
+// K chunks [kc0, kc1) of segment seg of a batch with n_kc chunks.
+__host__ __device__ inline void nao_split_h_seg_range(int n_kc, int nseg, int seg, int S, int &kc0, int &kc1) {
+    if (nseg <= 1) {
+        kc0 = 0;
+        kc1 = n_kc;
+        return;
+    }
+    const int kcs = nao_split_kc_seg(S);
+    kc0 = seg * kcs;
+    kc1 = kc0 + kcs < n_kc ? kc0 + kcs : n_kc;
+}
+
+// Split H work items of one batch (P points, N functions) for tile width TN and S slices: per
+// 128-row tile I, the TN-column tiles J >= floor(128 I / TN) (those reaching the upper
+// triangle), once per K segment.
+inline void nao_split_h_items(int32_t b, int P, int N, int TN, int S, std::vector<HWork> &out) {
+    const int nI = (N + 127) / 128, nJ = (N + TN - 1) / TN, nseg = nao_split_h_nseg(P, S);
     for (int I = 0; I < nI; I++)
-        for (int J = (I * 128) / TN; J < nJ; J++) out.push_back({b, I, J, 0});
+        for (int J = (I * 128) / TN; J < nJ; J++)
+            for (int q = 0; q < nseg; q++) out.push_back({b, I, J, q});
 }
 struct DWork {  // one tile of points of one batch for the density
     int32_t batch, tp;
@@ -324,6 +351,9 @@ cudaError_t launch_slice_n(const DevSystem &s, int32_t b0, int32_t b1, int32_t m
 cudaError_t launch_n_tc(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
                         const int64_t *sl_off, const int32_t *expo_q, const int32_t *expo_b, const double *scratch, int S,
                         int tn, bool grad, int32_t *err, cudaStream_t st);
+// One bounded mbarrier wait that nothing completes (the wait of the tensor-core pipelines): it gives
+// up after max_cycles SM cycles and records NAO_ERR_TIMEOUT in err[0] (code 1 in err[1]).
+cudaError_t launch_wait_timeout_probe(long long max_cycles, int32_t *err, cudaStream_t st);
 cudaError_t launch_wn_partial(const DevSystem &s, const DWork *work, int32_t w0, int32_t n_work, double *ne_part,
                               cudaStream_t st);
 

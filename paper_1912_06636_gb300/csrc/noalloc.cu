@@ -19,7 +19,9 @@
 //     handle;
 //   - calls whose work overlaps on the GPU (other streams, other handles) race on the array;
 //   - the first call on a device looks up the array's device address (cudaGetSymbolAddress,
-//     with that device current); make that first call before any stream capture.
+//     with that device current); make that first call before any stream capture. The address
+//     is cached for the life of the process: a device reset (or a new primary context) can move
+//     the array, after which this entry point must not be called on that device again.
 #include <mutex>
 #include <string>
 

@@ -22,17 +22,26 @@ struct Lattice {
 
 // One thread per element (i', j') of h^uc for one k point (blockIdx.y); both the real and the
 // imaginary part of e^{i k.(T_j' - T_i')} h^uc_{i'j'} are added into h(k)[fn(i')][fn(j')].
+// The maps come from the caller: an element whose fn_map entry lies outside [0, nb) or whose
+// fn_image entry lies outside [0, n_images) is skipped and counted in *err (when err is given),
+// so that no map value can move a read or an atomic outside its array.
 __global__ void __launch_bounds__(256) bloch_kernel(const double *__restrict__ huc, int64_t n_rs,
                                                    const int32_t *__restrict__ fn_map,
                                                    const int32_t *__restrict__ fn_image,
-                                                   const int32_t *__restrict__ img_cell, Lattice L,
-                                                   const double *__restrict__ kpts, int64_t nb, double *__restrict__ hk) {
+                                                   const int32_t *__restrict__ img_cell, int32_t n_images, Lattice L,
+                                                   const double *__restrict__ kpts, int64_t nb, double *__restrict__ hk,
+                                                   int32_t *__restrict__ err) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_rs * n_rs) return;
     const double hv = huc[e];
     if (hv == 0.0) return;
     const int64_t i = e / n_rs, j = e - i * n_rs;
-    const int32_t *ci = img_cell + 3 * (int64_t)fn_image[i], *cj = img_cell + 3 * (int64_t)fn_image[j];
+    const int32_t mi = fn_map[i], mj = fn_map[j], ti = fn_image[i], tj = fn_image[j];
+    if (mi < 0 || mi >= nb || mj < 0 || mj >= nb || ti < 0 || ti >= n_images || tj < 0 || tj >= n_images) {
+        if (err && blockIdx.y == 0) atomicAdd(err, 1);
+        return;
+    }
+    const int32_t *ci = img_cell + 3 * (int64_t)ti, *cj = img_cell + 3 * (int64_t)tj;
     const double *k = kpts + 3 * (int64_t)blockIdx.y;
     double ph = 0.0;
 #pragma unroll
@@ -43,7 +52,7 @@ __global__ void __launch_bounds__(256) bloch_kernel(const double *__restrict__ h
     }
     double sn, cs;
     sincos(ph, &sn, &cs);
-    double *out = hk + 2 * (((int64_t)blockIdx.y * nb + fn_map[i]) * nb + fn_map[j]);
+    double *out = hk + 2 * (((int64_t)blockIdx.y * nb + mi) * nb + mj);
     atomicAdd(out, cs * hv);
     atomicAdd(out + 1, sn * hv);
 }
@@ -166,20 +175,21 @@ nao_status nao_periodic_basis_map(const int32_t *atom_species, int32_t n_atoms, 
 }
 
 nao_status nao_bloch_sum(const double *h_uc_dev, int64_t n_rs, const int32_t *fn_map_dev, const int32_t *fn_image_dev,
-                         const int32_t *img_cell_dev, const double *lattice, const double *k_dev, int32_t n_k, int64_t nb,
-                         double *hk_dev, void *cuda_stream) {
+                         const int32_t *img_cell_dev, int32_t n_images, const double *lattice, const double *k_dev,
+                         int32_t n_k, int64_t nb, double *hk_dev, int32_t *err_dev, void *cuda_stream) {
     if (!h_uc_dev || !fn_map_dev || !fn_image_dev || !img_cell_dev || !lattice || !k_dev || !hk_dev || n_rs <= 0 ||
-        n_k <= 0 || nb <= 0 || n_k > 65535)
+        n_k <= 0 || nb <= 0 || n_k > 65535 || n_images <= 0)
         return bad(NAO_ERR_INVALID_ARG, "nao_bloch_sum: bad argument");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     Lattice L;
     for (int c = 0; c < 9; c++) L.a[c] = lattice[c];
     cudaError_t e = cudaMemsetAsync(hk_dev, 0, 2 * (size_t)n_k * (size_t)nb * (size_t)nb * sizeof(double), st);
+    if (e == cudaSuccess && err_dev) e = cudaMemsetAsync(err_dev, 0, sizeof(int32_t), st);
     const int64_t blocks = (n_rs * n_rs + 255) / 256;
     if (e == cudaSuccess && blocks > 0x7FFFFFFF) return bad(NAO_ERR_INVALID_ARG, "nao_bloch_sum: h^uc too large");
     if (e == cudaSuccess) {
-        bloch_kernel<<<dim3((unsigned)blocks, (unsigned)n_k), 256, 0, st>>>(h_uc_dev, n_rs, fn_map_dev, fn_image_dev,
-                                                                           img_cell_dev, L, k_dev, nb, hk_dev);
+        bloch_kernel<<<dim3((unsigned)blocks, (unsigned)n_k), 256, 0, st>>>(
+            h_uc_dev, n_rs, fn_map_dev, fn_image_dev, img_cell_dev, n_images, L, k_dev, nb, hk_dev, err_dev);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return bad(NAO_ERR_CUDA, std::string("nao_bloch_sum: ") + cudaGetErrorString(e));

@@ -425,7 +425,7 @@ struct HItem {  // geometry of one H work item
     const uint8_t *a0, *b0;
     size_t blk;
     uint32_t a_bytes, b_bytes;
-    int n_kc, neg16, b, m, N, ti, tj;
+    int n_kc, kc0, kc1, neg16, b, m, N, ti, tj;  // K chunks [kc0, kc1) of the item's segment
 };
 
 template <int TN>
@@ -447,6 +447,7 @@ __device__ __forceinline__ HItem h_item(const DevSystem &s, const HWork *work, i
     h.a_bytes = (uint32_t)min(128, G.R16 - it.ti * 128) * 128u;
     h.b_bytes = (uint32_t)min(TN, G.R16 - it.tj * TN) * 128u;
     h.n_kc = G.n_kc;
+    nao_split_h_seg_range(G.n_kc, nao_split_h_nseg(P, S), it.pad, S, h.kc0, h.kc1);
     h.neg16 = neg16[h.b];
     return h;
 }
@@ -497,12 +498,12 @@ __global__ void __launch_bounds__(192, 1)
                 const bool more = w + (int)gridDim.x < n_work;
                 HItem hn = h;
                 if (more) hn = h_item<TN>(s, work, w0 + w + gridDim.x, slices, sl_off, neg16, S);
-                for (int kc = 0; kc < h.n_kc; kc++, gk++) {
+                for (int kc = h.kc0; kc < h.kc1; kc++, gk++) {
                     // the next K chunk's slices (or the next item's first) towards L2, so that the
                     // ring's copies come from L2
-                    if (kc + 1 < h.n_kc || more) {
-                        const HItem &hp = kc + 1 < h.n_kc ? h : hn;
-                        const int kp = kc + 1 < h.n_kc ? kc + 1 : 0;
+                    if (kc + 1 < h.kc1 || more) {
+                        const HItem &hp = kc + 1 < h.kc1 ? h : hn;
+                        const int kp = kc + 1 < h.kc1 ? kc + 1 : hn.kc0;
                         for (int t = 0; t < S; t++) {
                             tc::bulk_prefetch_l2(hp.b0 + ((size_t)t * hp.n_kc + kp) * hp.blk, hp.b_bytes);
                             tc::bulk_prefetch_l2(hp.a0 + ((size_t)t * hp.n_kc + kp) * hp.blk, hp.a_bytes);
@@ -534,10 +535,11 @@ __global__ void __launch_bounds__(192, 1)
                 // the accumulators of the previous item have been read
                 if (t >= 1 && !tc::mbar_wait(&pp.acc_empty, (t - 1) & 1, kWaitCycles)) { *abort = 1; break; }
                 tc::fence_after_sync();
-                for (int kc = 0; kc < h.n_kc && !*abort; kc++, gk++) {
+                for (int kc = h.kc0; kc < h.kc1 && !*abort; kc++, gk++) {
                     const int bb = gk & 1, ub = gk >> 1;
                     if (!tc::mbar_wait(&pp.fullB[bb], ub & 1, kWaitCycles)) { *abort = 1; break; }
                     const uint8_t *bset = sB + (size_t)bb * S * B_BLOCK;
+                    const int first = kc == h.kc0 ? 0 : 1;  // the segment's first chunk overwrites the accumulators
                     for (int sa = 0; sa < S; sa++) {
                         const int idx = gk * S + sa, a = idx % RING, ua = idx / RING;
                         if (!tc::mbar_wait(&pp.fullA[a], ua & 1, kWaitCycles)) { *abort = 1; break; }
@@ -553,7 +555,7 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
                             for (int ks = 0; ks < 4; ks++) {
                                 const uint32_t id = (kc * 4 + ks < h.neg16) ? (idesc | (1u << 14)) : idesc;
-                                tc::mma_bf16(dt, ad + 2 * ks, bd + 2 * ks, id, (kc | sa | ks) ? 1u : 0u);
+                                tc::mma_bf16(dt, ad + 2 * ks, bd + 2 * ks, id, (first | sa | ks) ? 1u : 0u);
                             }
                         }
                         tc::mma_commit(&pp.emptyA[a]);
@@ -906,9 +908,27 @@ __global__ void __launch_bounds__(256) wn_partial_kernel(DevSystem s, const DWor
     }
 }
 
+// The timeout path of the bounded waits, exercised without a stuck pipeline: one thread waits on
+// an mbarrier that expects one arrival which never comes (no copy or MMA is in flight, so giving
+// up leaves nothing behind), then records the timeout the way the contraction kernels do.
+__global__ void wait_timeout_probe_kernel(long long max_cycles, int32_t *__restrict__ err) {
+    __shared__ uint64_t bar;
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+    if (!tc::mbar_wait(&bar, 0, max_cycles)) {
+        atomicExch(err + 1, 1);
+        atomicExch(err, (int)NAO_ERR_TIMEOUT);
+    }
+}
+
 }  // namespace
 
 size_t split_smem_bytes(int S) { return pipe_smem_bytes(S); }
+
+cudaError_t launch_wait_timeout_probe(long long max_cycles, int32_t *err, cudaStream_t st) {
+    wait_timeout_probe_kernel<<<1, 1, 0, st>>>(max_cycles, err);
+    return cudaGetLastError();
+}
 
 // SMs of the current device (the persistent kernels' grid size).
 static int sm_count() {

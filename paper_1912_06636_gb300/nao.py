@@ -36,7 +36,7 @@ SYMBOLS = [
     "nao_get_tuning", "nao_update_density_gradient", "nao_update_density_gradient_many",
     "nao_update_density_hessian", "nao_integrate_h_tau", "nao_pulay_matrices", "nao_pulay_forces",
     "nao_periodic_images", "nao_periodic_basis_map", "nao_bloch_sum", "nao_partition_points",
-    "nao_radial_spline",
+    "nao_radial_spline", "nao_fault_inject", "nao_check_wait_timeout",
 ]
 NAO_NOALLOC_SCRATCH_BYTES = 32 << 20
 KERNELS = ["eval_grad", "eval_phi", "h_fp64", "h_fp32", "h_split", "slice_h", "mirror", "n_fp64", "n_fp32",
@@ -74,7 +74,7 @@ class GridInfo(C.Structure):
     _fields_ = [
         ("n_basis", C.c_int64), ("n_points", C.c_int64), ("n_batches", C.c_int64), ("rel_total", C.c_int64),
         ("max_batch_points", C.c_int32), ("max_batch_basis", C.c_int32), ("device_bytes", C.c_int64),
-        ("flops_h", C.c_int64), ("flops_n", C.c_int64), ("n_systems", C.c_int32), ("reserved0", C.c_int32),
+        ("flops_h", C.c_int64), ("flops_n", C.c_int64), ("n_systems", C.c_int32), ("n_atoms", C.c_int32),
     ]
 
 
@@ -121,9 +121,11 @@ def load():
         "nao_update_density_gradient_many": ([P, P, C.c_int, P, P, P, P], C.c_int),
         "nao_periodic_images": ([P, I32, P, C.c_double, I32, P, P, P, P], C.c_int),
         "nao_periodic_basis_map": ([P, I32, P, I32, P, P, I32, I64, P, P, P], C.c_int),
-        "nao_bloch_sum": ([P, I64, P, P, P, P, P, I32, I64, P, P], C.c_int),
+        "nao_bloch_sum": ([P, I64, P, P, P, I32, P, P, I32, I64, P, P, P], C.c_int),
         "nao_partition_points": ([P, I64, I64, I64, P, P, P], C.c_int),
         "nao_radial_spline": ([P, I32, P], C.c_int),
+        "nao_fault_inject": ([C.c_char_p], C.c_int),
+        "nao_check_wait_timeout": ([P, I64, P], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -173,30 +175,28 @@ def _need(t, n: int, what: str) -> None:
         raise ValueError(f"{what}: needs {n} elements, the buffer holds {_count(t)}")
 
 
-# sizes of each live handle (fixed at create; dropped by nao_destroy, so a later handle at the
-# same address is looked up afresh)
-_HANDLE_SIZES: dict = {}
-
-
 def _handle_sizes(h):
-    """(n_basis, n_points, [(n_basis_m, n_points_m) per system]) of a handle."""
-    key = getattr(h, "value", h)
-    got = _HANDLE_SIZES.get(key)
+    """(n_basis, n_points, [(n_basis_m, n_points_m) per system], n_atoms) of a handle, queried from
+    the library (host-side queries) and kept on the handle object itself when it can hold them, so
+    that no size outlives its handle."""
+    got = getattr(h, "_nao_sizes", None)
     if got is None:
         info = nao_get_info(h)
         per = []
         for m in range(int(info.n_systems)):
             sysm = nao_get_system(h, m)
             per.append((sysm["n_basis"], sysm["n_points"]))
-        got = (int(info.n_basis), int(info.n_points), per)
-        if key is not None:
-            _HANDLE_SIZES[key] = got
+        got = (int(info.n_basis), int(info.n_points), per, int(info.n_atoms))
+        try:
+            h._nao_sizes = got
+        except AttributeError:  # a plain integer address: queried again on every call
+            pass
     return got
 
 
 def _sizes(h):
     """(n_basis, n_points) of a handle (for a grouped handle, the totals)."""
-    nb, npts, _ = _handle_sizes(h)
+    nb, npts, _, _ = _handle_sizes(h)
     return nb, npts
 
 
@@ -298,7 +298,8 @@ def _ptr_array(ts, allow_none: bool):
 
 
 def nao_destroy(h) -> None:
-    _HANDLE_SIZES.pop(getattr(h, "value", h), None)
+    if getattr(h, "_nao_sizes", None) is not None:
+        h._nao_sizes = None
     _check(load().nao_destroy(h), "nao_destroy")
 
 
@@ -345,11 +346,24 @@ def nao_pulay_matrices(h, v, prec, M, S, stream=None) -> None:
 
 
 def nao_pulay_forces(h, n, q, M, S, F, stream=None) -> None:
-    nb, _ = _sizes(h)
+    nb, _, _, n_atoms = _handle_sizes(h)
     for t, k, what in ((n, 1, "n"), (q, 1, "q"), (M, 3, "M"), (S, 3, "S")):
         _need(t, k * nb * nb, what)
+    _need(F, 3 * n_atoms, "F")
     _check(load().nao_pulay_forces(h, _dptr(n), _dptr(q), _dptr(M), _dptr(S), _dptr(F), _stream(stream)),
            "nao_pulay_forces")
+
+
+def nao_fault_inject(spec: str | None) -> None:
+    """Make the n-th device allocation, copy or launch of the library fail once ("alloc:<n>",
+    "copy:<n>", "launch:<n>"); None or "" clears it (host-side; no GPU fault is involved)."""
+    _check(load().nao_fault_inject(None if spec is None else spec.encode()), "nao_fault_inject")
+
+
+def nao_check_wait_timeout(h, max_cycles: int, stream=None) -> None:
+    """Enqueue one bounded device wait that runs out after max_cycles SM cycles and records
+    NAO_ERR_TIMEOUT for nao_sync_status to report."""
+    _check(load().nao_check_wait_timeout(h, int(max_cycles), _stream(stream)), "nao_check_wait_timeout")
 
 
 def nao_partition_points(pt_xyz, max_batch_points: int):
@@ -411,9 +425,25 @@ def nao_periodic_basis_map(system, img_atom):
     return fm[:n.value], fi[:n.value]
 
 
-def nao_bloch_sum(h_uc, fn_map, fn_image, img_cell, lattice, kpts, nb: int, stream=None, out=None):
+def check_bloch_maps(fn_map, fn_image, img_cell, nb: int) -> int:
+    """The Bloch sum's index arrays against the sizes they index (tensors on any device; a
+    device tensor costs one synchronising read of its extremes): every fn_map entry in [0, nb),
+    every fn_image entry in [0, n_images) with n_images = img_cell's length / 3. Returns n_images."""
+    if img_cell.numel() % 3 != 0 or img_cell.numel() == 0:
+        raise ValueError("img_cell must hold 3 integers per image")
+    n_images = int(img_cell.numel() // 3)
+    if fn_map.numel() and (int(fn_map.min()) < 0 or int(fn_map.max()) >= nb):
+        raise ValueError(f"fn_map entries must lie in [0, {nb})")
+    if fn_image.numel() and (int(fn_image.min()) < 0 or int(fn_image.max()) >= n_images):
+        raise ValueError(f"fn_image entries must lie in [0, {n_images})")
+    return n_images
+
+
+def nao_bloch_sum(h_uc, fn_map, fn_image, img_cell, lattice, kpts, nb: int, stream=None, out=None, err=None):
     """h(k) [n_k, nb, nb] complex from h^uc [n_rs, n_rs] (CUDA tensors; the index arrays int32).
-    out: optional FP64 CUDA tensor [n_k, nb, nb, 2] to write into."""
+    out: optional FP64 CUDA tensor [n_k, nb, nb, 2] to write into. err: optional int32 CUDA
+    tensor of one element that receives the kernel's count of skipped out-of-range map entries
+    (0 after a valid call; the maps are also checked here before the call)."""
     import torch
 
     A = np.ascontiguousarray(lattice, dtype=np.float64).reshape(9)
@@ -431,8 +461,12 @@ def nao_bloch_sum(h_uc, fn_map, fn_image, img_cell, lattice, kpts, nb: int, stre
     _need(fn_image, n_rs, "fn_image")
     if k.dim() != 2 or int(k.shape[1]) != 3:
         raise ValueError("kpts must be [n_k, 3]")
+    n_images = check_bloch_maps(fn_map[:n_rs], fn_image[:n_rs], img_cell, int(nb))
+    if err is not None and (not err.is_cuda or err.dtype != torch.int32 or err.numel() < 1):
+        raise ValueError("err must be an int32 CUDA tensor of at least one element")
     _check(load().nao_bloch_sum(_dptr(h_uc), h_uc.shape[0], fn_map.data_ptr(), fn_image.data_ptr(), img_cell.data_ptr(),
-                                A.ctypes.data, _dptr(k), k.shape[0], int(nb), _dptr(hk), _stream(stream)), "nao_bloch_sum")
+                                n_images, A.ctypes.data, _dptr(k), k.shape[0], int(nb), _dptr(hk),
+                                None if err is None else err.data_ptr(), _stream(stream)), "nao_bloch_sum")
     return torch.view_as_complex(hk)
 
 

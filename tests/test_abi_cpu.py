@@ -99,8 +99,19 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.nao_integrate_h_tau(None, None, None, 7, 0, None, None) == 1
     assert lib.nao_pulay_matrices(None, None, 0, None, None, None) == 1
     assert lib.nao_pulay_forces(None, None, None, None, None, None, None) == 1
-    assert lib.nao_bloch_sum(None, 0, None, None, None, None, None, 0, 0, None, None) == 1
+    assert lib.nao_bloch_sum(None, 0, None, None, None, 0, None, None, 0, 0, None, None, None) == 1
     info = nao.GridInfo()
     assert lib.nao_get_info(None, C.byref(info)) == 1
     out = C.c_void_p(123)
     assert lib.nao_grid_create(None, None, C.byref(out)) == 1 and out.value is None
+
+
+def test_fault_injection_spec_is_checked_without_gpu():
+    """nao_fault_inject accepts alloc/copy/launch:<n>, n >= 1, and clears with "" or None."""
+    for good in ("alloc:1", "copy:17", "launch:3", "", None):
+        nao.nao_fault_inject(good)
+    for bad in ("alloc", "alloc:0", "launch:-2", "copy:x", "free:3", "alloc:3junk", ":4"):
+        with pytest.raises(nao.NaoError) as e:
+            nao.nao_fault_inject(bad)
+        assert e.value.code == nao.NAO_ERR_INVALID_ARG
+    nao.nao_fault_inject(None)

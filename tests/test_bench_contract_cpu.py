@@ -11,7 +11,7 @@ ROOT = Path(__file__).resolve().parents[1]
 
 def test_reference_arm_json_line():
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "1", "--config", "0",
-                        "--cpu-sample", "800"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+                        "--cpu-seconds", "0.5"], cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
     assert len(lines) == 1
@@ -25,6 +25,7 @@ def test_reference_arm_json_line():
         assert key in d, key
     assert d["value"] > 0 and d["unit"] == "points/s" and d["steps"] == 2 and d["warmup"] == 1
     assert d["higher_is_better"] is True and d["dtype"] == "f64" and d["data"] == "synthetic"
+    assert d["ms_per_step_kind"].startswith("extrapolated")
     assert "workload" in d["config"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]

@@ -10,13 +10,13 @@ torch = pytest.importorskip("torch")
 
 from paper_1912_06636_gb300 import nao
 
-NB, NP = 7, 11
+NB, NP, NA = 7, 11, 2
 SYSTEMS = [(3, 5), (4, 6)]  # (n_basis, n_points) of a grouped handle's systems
 
 
 class _Info:
-    def __init__(self, nb, npts, n_sys):
-        self.n_basis, self.n_points, self.n_systems = nb, npts, n_sys
+    def __init__(self, nb, npts, n_sys, n_atoms=NA):
+        self.n_basis, self.n_points, self.n_systems, self.n_atoms = nb, npts, n_sys, n_atoms
 
 
 class _AcceptAll:
@@ -61,6 +61,7 @@ def test_single_system_calls(fake):
                 lambda: nao.nao_update_density_hessian(h, z(NB, NB), "fp64", z(NP), z(3, NP), z(5, NP), None, s),
                 lambda: nao.nao_pulay_matrices(h, None, "fp64", z(3, NB, NB), z(2, NB, NB), s),
                 lambda: nao.nao_pulay_forces(h, z(NB, NB), z(NB, NB), z(3, NB, NB), z(3, NB, NB - 1), z(6), s),
+                lambda: nao.nao_pulay_forces(h, z(NB, NB), z(NB, NB), z(3, NB, NB), z(3, NB, NB), z(3 * NA - 1), s),
                 lambda: nao.nao_integrate_h_noalloc(h, z(NP), 3, z(NB), s)):
         with pytest.raises(ValueError):
             bad()
@@ -69,7 +70,7 @@ def test_single_system_calls(fake):
     nao.nao_update_density_gradient(h, z(NB, NB), "split", z(NP), z(3, NP), z(1), s)
     nao.nao_update_density_hessian(h, z(NB, NB), "fp64", z(NP), z(3, NP), z(6, NP), z(1), s)
     nao.nao_pulay_matrices(h, z(NP), "fp64", z(3, NB, NB), z(3, NB, NB), s)
-    nao.nao_pulay_forces(h, z(NB, NB), z(NB, NB), z(3, NB, NB), z(3, NB, NB), z(6), s)
+    nao.nao_pulay_forces(h, z(NB, NB), z(NB, NB), z(3, NB, NB), z(3, NB, NB), z(3 * NA), s)
     nao.nao_integrate_h_noalloc(h, z(NP), 3, z(NB, NB), s)
 
 

@@ -52,8 +52,7 @@ def test_density_gradient_water(water, prec):
 
 @pytest.mark.parametrize("prec", ["fp64", "split"])
 def test_density_gradient_grouped(prec):
-    systems, bs = synth.molecule_set(6, seed=3100, n_min=3, n_max=10, b_min=20, b_max=300, n_rad=14, n_theta=5, n_phi=6)
-    bs = [min(b, 336) for b in bs]
+    systems, bs = synth.molecule_set(6, seed=3100, n_min=3, n_max=10, b_min=20, b_max=400, n_rad=14, n_theta=5, n_phi=6)
     Ps = [synth.density_matrix(s, 40 + k) for k, s in enumerate(systems)]
     with nao.Grid(systems, device=0, batch_points=bs) as g:
         ns = [torch.full((st["n_points"],), float("nan"), dtype=torch.float64, device="cuda") for st in g.systems]

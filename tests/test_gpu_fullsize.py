@@ -1,25 +1,25 @@
-"""Full-size parity on the benchmark workload (64-atom diamond-lattice cluster, 1600 basis
-functions, 1,175,040 points, batches <= 300 points) in the launch configuration bench.py
-times: partition and reduced bases bit-exact; H on a sampled block of basis functions and n
-on sampled points against the oracle, which computes them one by one; plus properties that
-hold at any size (symmetry, exact zeros, tr(PS) = sum_p w_p n_p)."""
+"""Full-size parity on the 64-atom diamond-lattice cluster (1600 basis functions, 1,175,040
+points, batches <= 300 points), in the launch configuration bench.py times for it: partition
+and reduced bases bit-exact; every element of H and n at every point against the oracle
+(tests/_oracle_par.py spreads it over the host's cores), at every precision and at the split
+slice counts the library defaults to and bench.py times; plus properties that hold at any size
+(symmetry, exact zeros, tr(PS) = sum_p w_p n_p)."""
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
+import bench
 import oracle
 from paper_1912_06636_gb300 import nao, synth
-from tests._metrics import rel_err
+from tests import _oracle_par
+from tests._metrics import raw_rel_err, rel_err
 
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-12, "fp32": 1e-6, "split": 1e-10}
-# the split path with the library's default slices, and with the 10 slices bench.py times
-SPLIT_SLICES = {"split": None, "split10": 10}
-# sampled basis functions: several atoms (neighbours and far-apart pairs), every l
-SAMPLE_F = np.array([0, 3, 9, 18, 24, 25 * 1 + 2, 25 * 5 + 13, 25 * 8 + 21, 25 * 27 + 6, 25 * 40 + 11,
-                     25 * 58 + 19, 25 * 63 + 24])
+# the split path at the library's default slice count and at the count bench.py times here
+SPLIT_CASES = sorted({12, bench.BENCH_SLICES[1]})
 
 
 def cuda(a):
@@ -31,18 +31,16 @@ def diamond():
     s = synth.config(1)
     v = s.potential()
     P = synth.density_matrix(s, 1)
-    o = oracle.Oracle(s)
-    Hb, Ab = o.hamiltonian_block(SAMPLE_F, s.pt_xyz, s.pt_w, v)
-    rng = np.random.Generator(np.random.PCG64(77))
-    pidx = np.sort(rng.choice(s.n_points, 3000, replace=False))
-    n_s, D_s, _ = o.density(s.pt_xyz[pidx], P)
+    H_ref, A = _oracle_par.hamiltonian(s, s.pt_xyz, s.pt_w, v)
+    n_ref, D = _oracle_par.density(s, s.pt_xyz, P)
     g = nao.Grid(s, device=0, max_batch_points=s.max_batch_points)
-    yield dict(s=s, v=v, P=P, o=o, Hb=Hb, Ab=Ab, pidx=pidx, n_s=n_s, D_s=D_s, g=g)
+    yield dict(s=s, v=v, P=P, H=H_ref, A=A, n=n_ref, D=D, g=g)
     g.close()
 
 
 def test_partition_and_relevance_bit_exact_fullsize(diamond):
-    s, o, g = diamond["s"], diamond["o"], diamond["g"]
+    s, g = diamond["s"], diamond["g"]
+    o = oracle.Oracle(s)
     bo, pp, ro, ri = g.batches()
     obo, opp = oracle.Oracle.partition(s.pt_xyz, s.max_batch_points)
     assert np.array_equal(bo, obo) and np.array_equal(pp, opp)
@@ -50,13 +48,13 @@ def test_partition_and_relevance_bit_exact_fullsize(diamond):
     assert np.array_equal(ro, oro) and np.array_equal(ri, ori)
 
 
-@pytest.mark.parametrize("case", ["fp64", "fp32", "split", "split10"])
-def test_fullsize_sampled(diamond, case):
+@pytest.mark.parametrize("case", ["fp64", "fp32"] + [f"split{S}" for S in SPLIT_CASES])
+def test_fullsize_every_element(diamond, case):
     g, s = diamond["g"], diamond["s"]
     prec = "split" if case.startswith("split") else case
     own = None
-    if SPLIT_SLICES.get(case) is not None:
-        own = g = nao.Grid(s, device=0, max_batch_points=s.max_batch_points, split_slices=SPLIT_SLICES[case])
+    if prec == "split":
+        own = g = nao.Grid(s, device=0, max_batch_points=s.max_batch_points, split_slices=int(case[5:]))
     H = g.integrate_h(cuda(diamond["v"]), prec=prec)
     n, ne = g.update_density(cuda(diamond["P"]), prec=prec)
     S = g.overlap(prec=prec)
@@ -66,14 +64,13 @@ def test_fullsize_sampled(diamond, case):
         own.close()
     Hc = H.cpu().numpy()
     assert np.array_equal(Hc, Hc.T)
-    F = SAMPLE_F
-    e_H = rel_err(Hc[np.ix_(F, F)], diamond["Hb"], diamond["Ab"])
-    zero = diamond["Ab"] == 0
-    assert np.all(Hc[np.ix_(F, F)][zero] == 0.0)
+    e_H = rel_err(Hc, diamond["H"], diamond["A"])
+    assert np.all(Hc[diamond["A"] == 0] == 0.0)  # no pair of functions that never overlap picks up a value
     nc = n.cpu().numpy()
-    e_n = rel_err(nc[diamond["pidx"]], diamond["n_s"], diamond["D_s"])
+    e_n = rel_err(nc, diamond["n"], diamond["D"])
     # tr(PS) = sum_p w_p n_p holds for the GPU's own S and n (same discrete sum)
     trPS = float(torch.sum(cuda(diamond["P"]) * S).item())
-    print(f"{case}: e_H(sampled)={e_H:.2e} e_n(sampled)={e_n:.2e} N_e={float(ne.item()):.10f} tr(PS)={trPS:.10f}")
+    print(f"{case}: e_H={e_H:.2e} (raw {raw_rel_err(Hc, diamond['H'], diamond['A']):.2e}) over all "
+          f"{Hc.size} elements, e_n={e_n:.2e} over all {nc.size} points, N_e={float(ne.item()):.10f} tr(PS)={trPS:.10f}")
     assert e_H <= TOL[prec] and e_n <= TOL[prec]
     assert abs(float(ne.item()) - trPS) <= 10 * TOL[prec] * abs(trPS)

@@ -4,8 +4,8 @@ kernel): every molecule's H, n and N_e against the oracle at each precision's ba
 FP32 1e-6, split 1e-10; tests/_metrics.py).
 
 Sizes are reduced so that the oracle finishes in seconds: 32 molecules of 3-16 atoms on a
-16 x 42 points-per-atom grid, batch sizes log-uniform in [20, 336] (336 keeps the 12-slice
-split sums exact).
+16 x 42 points-per-atom grid, batch sizes log-uniform in [20, 400] as the batching
+configuration states (the split path accumulates batches above 336 points in K segments).
 """
 import numpy as np
 import pytest
@@ -23,7 +23,7 @@ TOL = {"fp64": 1e-12, "fp32": 1e-6, "split": 1e-10}
 
 @pytest.fixture(scope="module")
 def mols():
-    systems, bs = synth.molecule_set(32, seed=3000, n_min=3, n_max=16, b_min=20, b_max=336,
+    systems, bs = synth.molecule_set(32, seed=3000, n_min=3, n_max=16, b_min=20, b_max=400,
                                      n_rad=16, n_theta=6, n_phi=7)
     refs = []
     for k, s in enumerate(systems):

@@ -48,7 +48,9 @@ def test_bloch_hamiltonian_and_overlap(cell, prec):
         assert g.nb == len(cell["fm"])
         Huc = g.integrate_h(torch.from_numpy(cell["v"]).to(dev), prec=prec)
         Suc = g.overlap(prec=prec)
-        Hk = nao.nao_bloch_sum(Huc, fm, fi, ci, LAT, k, s.n_basis).cpu().numpy()
+        err = torch.full((1,), -1, dtype=torch.int32, device=dev)
+        Hk = nao.nao_bloch_sum(Huc, fm, fi, ci, LAT, k, s.n_basis, err=err).cpu().numpy()
+        assert int(err.item()) == 0  # no map entry was skipped
         Sk = nao.nao_bloch_sum(Suc, fm, fi, ci, LAT, k, s.n_basis).cpu().numpy()
         torch.cuda.synchronize()
         g.sync()

@@ -34,21 +34,36 @@ def reqs():
     return _requests()
 
 
-def _close(a, b, tol):
-    scale = max(float(np.max(np.abs(b))), 1e-300)
-    return float(np.max(np.abs(a - b))) <= tol * scale
+def _last_inputs(q):
+    """v and P of a request's last iteration, regenerated the way the server draws them."""
+    dev = torch.device("cuda", 0)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(q.seed) * 1_000_003 + q.n_iter - 1)
+    u = torch.rand(len(q.v0), generator=gen, dtype=torch.float64, device=dev)
+    X = torch.randn((q.system.n_basis, 16), generator=gen, dtype=torch.float64, device=dev)
+    v = (torch.from_numpy(q.v0).to(dev) * (u * 0.02 + 0.99)).cpu().numpy()
+    P = (X @ X.t() / 16.0).cpu().numpy()
+    return v, P
 
 
 @pytest.mark.parametrize("prec", ["fp64", "split"])
 def test_alone_equals_mix(reqs, prec):
+    """Element by element, in the measure of every other parity test: |H_mix - H_alone| against
+    the magnitude sums A of the oracle's H, |n_mix - n_alone| against D (tests/_metrics.py)."""
     mix_server = serve.Server(prec=prec, max_active=4, keep_results=True)
     mix = mix_server.run(reqs)
     assert [r.rid for r in mix] == list(range(len(reqs)))
     assert mix_server.stats["peak_active"] >= 2  # requests did overlap
     for q, m in zip(reqs, mix):
         alone = serve.Server(prec=prec, max_active=1, keep_results=True).run([q])[0]
-        assert _close(m.H, alone.H, TOL[prec]), q.rid
-        assert _close(m.n, alone.n, TOL[prec]), q.rid
+        v, P = _last_inputs(q)
+        o = oracle.Oracle(q.system)
+        H_ref, A = o.hamiltonian(q.system.pt_xyz, q.system.pt_w, v)
+        n_ref, D, _ = o.density(q.system.pt_xyz, P)
+        assert rel_err(m.H, alone.H, A) <= TOL[prec], q.rid
+        assert rel_err(m.n, alone.n, D) <= TOL[prec], q.rid
+        # and both against the oracle
+        assert rel_err(m.H, H_ref, A) <= TOL[prec] and rel_err(alone.n, n_ref, D) <= TOL[prec], q.rid
         assert np.allclose(m.n_electrons, alone.n_electrons, rtol=TOL[prec], atol=0.0)
         assert np.all(m.n_electrons > 0)
 
@@ -74,13 +89,7 @@ def test_staggered_arrivals_and_oracle(reqs):
     # the last iteration of request 1 against the oracle, with v and P regenerated the same way
     q, r = qs[1], res[1]
     s = q.system
-    dev = torch.device("cuda", 0)
-    gen = torch.Generator(device=dev)
-    gen.manual_seed(int(q.seed) * 1_000_003 + q.n_iter - 1)
-    u = torch.rand(len(q.v0), generator=gen, dtype=torch.float64, device=dev)
-    X = torch.randn((s.n_basis, 16), generator=gen, dtype=torch.float64, device=dev)
-    v = (torch.from_numpy(q.v0).to(dev) * (u * 0.02 + 0.99)).cpu().numpy()
-    P = (X @ X.t() / 16.0).cpu().numpy()
+    v, P = _last_inputs(q)
     o = oracle.Oracle(s)
     H, A = o.hamiltonian(s.pt_xyz, s.pt_w, v)
     n, D, ne = o.density(s.pt_xyz, P, s.pt_w)

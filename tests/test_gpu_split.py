@@ -70,17 +70,33 @@ def test_split_error_falls_with_slices(water):
         assert e[0] <= TOL and e[1] <= TOL
 
 
-# Exact slice sums need 4 Ppad S < 2^14 (Ppad = batch points rounded up to 16): batches of up
-# to 336 points at 12 slices, 400 at 10.
-@pytest.mark.parametrize("B,S", [(1, 12), (37, 12), (128, 12), (336, 12), (400, 10)])
+# Exact slice sums need K S < 2^14 per accumulation: the H contraction (K = 4 Ppad, Ppad = batch
+# points rounded up to 16) accumulates batches of more than 336 points at 12 slices (400 at 10)
+# in K segments; (1024, 12) gives 4.3 segments' worth of K on the one-atom grid below.
+@pytest.mark.parametrize("B,S", [(1, 12), (37, 12), (128, 12), (336, 12), (337, 12), (400, 12), (400, 10),
+                                 (512, 12), (512, 4), (401, 10)])
 def test_split_independent_of_batch_size(water, B, S):
     H, n, _ = run(water, max_batch_points=B, split_slices=S)
     assert rel_err(H, water["H"], water["A"]) <= TOL
     assert rel_err(n, water["n"], water["D"]) <= TOL
 
 
-@pytest.mark.parametrize("B,S", [(1024, 10), (400, 12)])
-def test_split_rejects_batches_too_large_for_exact_sums(water, B, S):
+def test_split_segments_cover_every_k_chunk():
+    """Batch sizes that put the segment boundary at every position of a chunk: one atom, so
+    every batch has the same functions and H over the whole grid must not depend on B."""
+    s = synth.make_system([[0.0, 0.0, 0.0]], [0], [synth.Species(ls=[0, 1, 2], alphas=[1.2, 0.7, 0.9], Z=2.0)],
+                          n_rad=40, n_theta=8, n_phi=9)
+    o = oracle.Oracle(s)
+    v = s.potential()
+    H_ref, A = o.hamiltonian(s.pt_xyz, s.pt_w, v)
+    for B in (321, 352, 368, 384, 448, 496, 512):
+        with nao.Grid(s, device=0, max_batch_points=B, split_slices=12) as g:
+            H = g.integrate_h(cuda(v), prec="split").cpu().numpy()
+        assert rel_err(H, H_ref, A) <= TOL, B
+
+
+@pytest.mark.parametrize("B,S", [(1024, 10), (600, 12)])
+def test_split_rejects_batches_beyond_512_points(water, B, S):
     with nao.Grid(water["s"], device=0, max_batch_points=B, split_slices=S) as g:
         with pytest.raises(nao.NaoError) as e:
             g.integrate_h(cuda(water["v"]), prec="split")

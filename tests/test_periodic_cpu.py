@@ -73,3 +73,19 @@ def test_periodic_grid_is_the_trapezoid_rule_of_the_cell():
     assert abs(np.dot(s.pt_w, g) - 0.7 * V) <= 1e-12 * V
     v = synth.periodic_potential(s)
     assert abs(np.dot(s.pt_w, v) - (-1.0) * V) <= 1e-12 * V
+
+
+def test_bloch_map_checks():
+    """The binding rejects maps that would index outside h(k) or the image table (the kernel
+    also skips and counts such entries, so that they can never move a device access)."""
+    import pytest
+
+    torch = pytest.importorskip("torch")
+    i32 = lambda a: torch.tensor(a, dtype=torch.int32)
+    cell = i32([0, 0, 0, 1, 0, 0])  # two images
+    assert nao.check_bloch_maps(i32([0, 1, 2]), i32([0, 1, 1]), cell, 3) == 2
+    for fm, fi, c in ((i32([0, 3, 2]), i32([0, 1, 1]), cell), (i32([-1, 1, 2]), i32([0, 1, 1]), cell),
+                      (i32([0, 1, 2]), i32([0, 2, 1]), cell), (i32([0, 1, 2]), i32([0, -1, 1]), cell),
+                      (i32([0, 1, 2]), i32([0, 1, 1]), i32([0, 0, 0, 1]))):
+        with pytest.raises(ValueError):
+            nao.check_bloch_maps(fm, fi, c, 3)
