@@ -98,7 +98,9 @@ typedef struct {
     int32_t deterministic;    /* reserved; results are already run-to-run reproducible up to
                                  the order of FP64 atomic additions into H */
     int32_t device;           /* CUDA device ordinal; -1 = the calling thread's current device */
-    int64_t scratch_bytes;    /* device scratch for evaluated basis functions; 0 = library default */
+    int64_t scratch_bytes;    /* device scratch for evaluated basis functions; 0 = library default (8 GiB;
+                                 the split path's slices take three times this). Memory is taken only
+                                 up to what the batches need; smaller values mean more, smaller launches */
     int32_t capture_graph;    /* 1: the first call of each (operation, precision, terms) records
                                  its kernel launches as a CUDA graph on a stream the handle
                                  owns; later calls upload that call's pointer tables and replay

@@ -15,6 +15,13 @@ namespace {
 
 thread_local std::string g_last_error;
 
+// Evaluation scratch when options.scratch_bytes is 0: 8 GiB (the split slices get three times as
+// much). Each evaluation chunk is one launch of every kernel, so larger chunks mean fewer
+// launches and fewer partly filled tails; memory is only taken up to what the handle's batches
+// need.
+constexpr int64_t kDefaultScratch = int64_t(8) << 30;
+
+
 nao_status fail(nao_status s, const std::string &msg) {
     g_last_error = msg;
     return s;
@@ -490,7 +497,7 @@ nao_status build(nao_grid *g, const nao_system_desc *descs, int32_t n_sys, const
     std::vector<HWork> hw;
     std::vector<DWork> dw;
     std::vector<int64_t> scr_off(nbat, 0);
-    int64_t budget = (g->opt.scratch_bytes > 0 ? g->opt.scratch_bytes : (int64_t(2) << 30)) / (int64_t)sizeof(double);
+    int64_t budget = (g->opt.scratch_bytes > 0 ? g->opt.scratch_bytes : kDefaultScratch) / (int64_t)sizeof(double);
     int64_t need_max = 0, need_total = 0;
     for (int64_t b = 0; b < nbat; b++) {
         const int64_t Ppad = (g->Pb[b] + NAO_PPAD - 1) / NAO_PPAD * NAO_PPAD;
@@ -762,8 +769,10 @@ nao_status split_setup(nao_grid *g) {
     }
     NAO_CUDA(split_configure());
     g->split_chunks.clear();  // a failed earlier set-up may have planned part of them
-    const int64_t budget = std::max<int64_t>(g->opt.scratch_bytes > 0 ? 2 * g->opt.scratch_bytes : (int64_t(4) << 30),
-                                             int64_t(1) << 20);
+    // slices take S x 2 bytes per evaluated FP64 value (8 bytes): three times the evaluation
+    // budget holds one evaluation chunk's slices at up to 12 slices
+    const int64_t budget =
+        std::max<int64_t>(3 * (g->opt.scratch_bytes > 0 ? g->opt.scratch_bytes : kDefaultScratch), int64_t(1) << 20);
     std::vector<int64_t> off_h(g->n_batches, 0), off_n(g->n_batches, 0);
     int64_t max_used = 0, cap_h = 0, cap_n = 0;
     g->split_tn.assign(g->n_batches, 32);

@@ -353,8 +353,8 @@ __global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, 
 }
 
 // ----------------------------------------------------------------------------------------
-// Slice-product pipeline of the persistent contraction kernels. Shared memory: a ring of 6
-// A-tile buffers (128 rows x 64 bf16, 16 KB, one slice of one K chunk each) and two sets of S
+// Slice-product pipeline of the persistent contraction kernels. Shared memory: a ring of
+// ring_slots(S) A-tile buffers (128 rows x 64 bf16, 16 KB, one slice of one K chunk each) and two sets of S
 // B-tile buffers (TN rows, TN x 128 B). Producer (one lane): for each K chunk, the S B slices
 // into B set kc % 2, then the S A slices one by one into the ring, each copy a single bulk
 // (TMA) transfer completing on a "full" mbarrier. MMA issuer (one lane): for each A slice s,
@@ -364,11 +364,25 @@ __global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, 
 // the ring and of the B sets continue over all the accumulations a CTA runs. Every wait is
 // bounded; on a timeout the CTA records NAO_ERR_TIMEOUT and skips the rest of its work.
 // ----------------------------------------------------------------------------------------
-constexpr int RING = 6;
+constexpr int kMaxRing = 8;
+constexpr size_t kSmemOptin = 232448;  // shared memory a CTA may opt into on this GPU (227 KB)
+constexpr size_t kStaticSmem = 2048;   // room for the CTA's static shared memory (the PPipe barriers)
+
+// A-ring slots: as many 16 KB A tiles as fit beside the two B sets (S tiles of TN rows each),
+// at most kMaxRing: 8 for S = 11, 12 (TN = 32), 6 for S = 10 (TN = 48). A deeper ring lets the
+// producer's copies run further ahead of the MMAs that wait for them.
+__host__ __device__ constexpr int ring_slots(int S) {
+    return (int)((kSmemOptin - kStaticSmem - 1024 - 2 * (size_t)S * nao_split_tn(S) * 128) / 16384) < kMaxRing
+               ? (int)((kSmemOptin - kStaticSmem - 1024 - 2 * (size_t)S * nao_split_tn(S) * 128) / 16384)
+               : kMaxRing;
+}
 
 __host__ __device__ constexpr size_t pipe_smem_bytes(int S) {
-    return (size_t)RING * 16384 + 2 * (size_t)S * nao_split_tn(S) * 128 + 1024;
+    return (size_t)ring_slots(S) * 16384 + 2 * (size_t)S * nao_split_tn(S) * 128 + 1024;
 }
+static_assert(ring_slots(12) >= 4 && ring_slots(10) >= 4 && ring_slots(4) >= 4, "A ring too shallow");
+static_assert(pipe_smem_bytes(12) + kStaticSmem <= kSmemOptin && pipe_smem_bytes(10) + kStaticSmem <= kSmemOptin,
+              "split pipeline exceeds shared memory");
 
 // Integer recombination of the S group accumulators for 16 columns of this thread's row:
 // value = hi 64^-8 + lo 64^-11 + lo2 64^-14 (in units of 2^(e_i + e_j)) with
@@ -382,25 +396,28 @@ template <int TN>
 __device__ __forceinline__ void combine16(uint32_t tm_row, int c0, int S, Parts16 &v) {
 #pragma unroll
     for (int jj = 0; jj < 16; jj++) v.hi[jj] = v.lo[jj] = v.lo2[jj] = 0;
-    for (int g = 0; g < S; g++) {
-        uint32_t r[16];
-        tc::tmem_ld16(tm_row + (uint32_t)(g * TN + c0), r);
-        tc::tmem_ld_wait();
-        const int part = g <= 6 ? 0 : (TN == 48 || g <= 9 ? 1 : 2);  // TN = 48: S <= 10, no lo2
-        const long long w = 1LL << (6 * (part == 0 ? 6 - g : (part == 1 ? 9 - g : 12 - g)));
+    // three groups' loads in flight per wait
+    for (int g0 = 0; g0 < S; g0 += 3) {
+        uint32_t r[3][16];
 #pragma unroll
-        for (int jj = 0; jj < 16; jj++) {
-            const long long m = (long long)__float2int_rn(__uint_as_float(r[jj]));
-            if (part == 0) v.hi[jj] += m * w;
-            else if (part == 1) v.lo[jj] += m * w;
-            else v.lo2[jj] += m * w;
+        for (int d = 0; d < 3; d++)
+            if (g0 + d < S) tc::tmem_ld16(tm_row + (uint32_t)((g0 + d) * TN + c0), r[d]);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const int g = g0 + d;
+            if (g >= S) break;
+            const int part = g <= 6 ? 0 : (TN == 48 || g <= 9 ? 1 : 2);  // TN = 48: S <= 10, no lo2
+            const long long w = 1LL << (6 * (part == 0 ? 6 - g : (part == 1 ? 9 - g : 12 - g)));
+#pragma unroll
+            for (int jj = 0; jj < 16; jj++) {
+                const long long m = (long long)__float2int_rn(__uint_as_float(r[d][jj]));
+                if (part == 0) v.hi[jj] += m * w;
+                else if (part == 1) v.lo[jj] += m * w;
+                else v.lo2[jj] += m * w;
+            }
         }
     }
-}
-
-// 2^(e_i + e_j) (hi 64^-8 + lo 64^-11 + lo2 64^-14)
-__device__ __forceinline__ double recombine(long long hi, long long lo, long long lo2, int eij) {
-    return fma((double)hi, pow2(eij - 48), fma((double)lo, pow2(eij - 66), (double)lo2 * pow2(eij - 84)));
 }
 
 __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
@@ -415,7 +432,7 @@ __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
 // ("acc_empty") and then scatter into H while the next item's MMAs run, so the scatter, the
 // tensor-memory reads and the next item's first loads overlap the MMAs.
 struct PPipe {
-    uint64_t fullA[RING], emptyA[RING], fullB[2], emptyB[2];
+    uint64_t fullA[kMaxRing], emptyA[kMaxRing], fullB[2], emptyB[2];
     uint64_t acc_full, acc_empty, fin;
     uint32_t tmem;
     int abort;
@@ -461,6 +478,7 @@ __global__ void __launch_bounds__(192, 1)
     extern __shared__ uint8_t smem_dyn[];
     __shared__ PPipe pp;
     uint8_t *smem = align1024(smem_dyn);
+    const int RING = ring_slots(S);
     uint8_t *sA = smem, *sB = smem + (size_t)RING * 16384;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -582,12 +600,13 @@ __global__ void __launch_bounds__(192, 1)
             const int32_t *rel = s.rel_idx + s.rel_off[h.b];
             const int32_t *ex = expo + s.rel_off[h.b];
             const int ei = row_ok ? ex[i] : -10000;
-            // Width 48 (S <= 10, no lo2): h_ij as one 64-bit integer, exact as hi 2^18 + lo where
-            // |hi| < 2^44, else 4 hi + round(lo / 2^16) (|4 hi| >= 2^46: relative error <= 2^-47);
-            // the integers are formed before tensor memory is handed back, the conversion and the
-            // product by 2^(e_i + e_j - 66 or - 50) after. Width 32: the three parts in FP64.
-            using Val = typename std::conditional<TN == 48, long long, double>::type;
-            Val val[TN];
+            // h_ij as one 64-bit integer, exact as hi 2^18 + lo' where |hi| < 2^44, else
+            // 4 hi + round(lo' / 2^16) (|4 hi| >= 2^46: relative error <= 2^-47), with lo' = lo +
+            // round(lo2 / 2^18): the groups g >= 10 that only S = 11, 12 have are folded into lo at
+            // a cost of at most half a unit of lo, 2^-67 of 2^(e_i + e_j), far below the split's own
+            // truncation. The integers are formed before tensor memory is handed back, the
+            // conversion and the product by 2^(e_i + e_j - 66 or - 50) after.
+            long long val[TN];
             uint64_t small_mask = 0;
 #pragma unroll
             for (int c0 = 0; c0 < TN; c0 += 16) {
@@ -595,16 +614,10 @@ __global__ void __launch_bounds__(192, 1)
                 combine16<TN>(tm_row, c0, S, v);
 #pragma unroll
                 for (int jj = 0; jj < 16; jj++) {
-                    if constexpr (TN == 48) {
-                        const long long hi = v.hi[jj], lo = v.lo[jj];
-                        const bool small = hi > -(1LL << 44) && hi < (1LL << 44);
-                        val[c0 + jj] = small ? (hi << 18) + lo : (hi << 2) + ((lo + (1LL << 15)) >> 16);
-                        small_mask |= (uint64_t)small << (c0 + jj);
-                    } else {
-                        const int j = h.tj * TN + c0 + jj;
-                        const int ej = (row_ok && j < h.N) ? ex[j] : -10000;
-                        val[c0 + jj] = (ei > -10000 && ej > -10000) ? recombine(v.hi[jj], v.lo[jj], v.lo2[jj], ei + ej) : 0.0;
-                    }
+                    const long long hi = v.hi[jj], lo = v.lo[jj] + ((v.lo2[jj] + (1LL << 17)) >> 18);
+                    const bool small = hi > -(1LL << 44) && hi < (1LL << 44);
+                    val[c0 + jj] = small ? (hi << 18) + lo : (hi << 2) + ((lo + (1LL << 15)) >> 16);
+                    small_mask |= (uint64_t)small << (c0 + jj);
                 }
             }
             // tensor memory is free for the next item
@@ -617,15 +630,10 @@ __global__ void __launch_bounds__(192, 1)
                 for (int jj = 0; jj < TN; jj++) {
                     const int j = h.tj * TN + jj;
                     if (j < h.N && j >= i) {
-                        double x;
-                        if constexpr (TN == 48) {
-                            const int ej = ex[j];
-                            x = (ei > -10000 && ej > -10000)
-                                    ? (double)val[jj] * pow2(ei + ej - (((small_mask >> jj) & 1) ? 66 : 50))
-                                    : 0.0;
-                        } else {
-                            x = val[jj];
-                        }
+                        const int ej = ex[j];
+                        const double x = (ei > -10000 && ej > -10000)
+                                             ? (double)val[jj] * pow2(ei + ej - (((small_mask >> jj) & 1) ? 66 : 50))
+                                             : 0.0;
                         atomicAdd(h_elem(s, h.m, gi, rel[j]), x);
                     }
                 }
@@ -699,6 +707,7 @@ __global__ void __launch_bounds__(192, 1)
     extern __shared__ uint8_t smem_dyn[];
     __shared__ PPipe pp;
     uint8_t *smem = align1024(smem_dyn);
+    const int RING = ring_slots(S);
     uint8_t *sA = smem, *sB = smem + (size_t)RING * 16384;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {

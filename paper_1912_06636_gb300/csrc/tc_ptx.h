@@ -31,8 +31,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: gives up after ~max_cycles SM clock cycles and returns false.
+// Bounded wait: gives up after ~max_cycles SM clock cycles and returns false. The clock is
+// read only once the first try has failed (most waits of a running pipeline succeed at once).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long max_cycles) {
+    if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (clock64() - t0 > max_cycles) return false;

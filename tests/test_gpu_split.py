@@ -74,7 +74,7 @@ def test_split_error_falls_with_slices(water):
 # points rounded up to 16) accumulates batches of more than 336 points at 12 slices (400 at 10)
 # in K segments; (1024, 12) gives 4.3 segments' worth of K on the one-atom grid below.
 @pytest.mark.parametrize("B,S", [(1, 12), (37, 12), (128, 12), (336, 12), (337, 12), (400, 12), (400, 10),
-                                 (512, 12), (512, 4), (401, 10)])
+                                 (512, 12), (512, 10), (401, 10)])
 def test_split_independent_of_batch_size(water, B, S):
     H, n, _ = run(water, max_batch_points=B, split_slices=S)
     assert rel_err(H, water["H"], water["A"]) <= TOL
