@@ -68,12 +68,15 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other precisions")
-    ap.add_argument("--serve-requests", type=int, default=16,
+    ap.add_argument("--serve-requests", type=int, default=120,
                     help="requests of the serving stream (Poisson arrivals at 200/s, 3-200 atoms)")
+    ap.add_argument("--serve-fp64-requests", type=int, default=24,
+                    help="the first requests of the same stream run again on the FP64 path")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving stream")
     ap.add_argument("--no-periodic", action="store_true", help="skip the periodic-silicon measurement")
     ap.add_argument("--grouped-molecules", type=int, default=128,
-                    help="molecules of the grouped-launch comparison (0 skips it)")
+                    help="molecules of the batching configuration on their species' grids (0 skips it; "
+                         "the stated configuration is 1024)")
     return ap.parse_args()
 
 
@@ -159,8 +162,9 @@ def alu_peak(kind: str):
 SERVE_GRID = dict(n_rad=30, n_theta=8, n_phi=9)
 
 
-def serving(n_requests: int, device: int) -> dict:
-    """The request stream through the continuous-batching loop, split path then FP64 path."""
+def serving(n_requests: int, device: int, fp64_requests: int) -> dict:
+    """The request stream through the continuous-batching loop: every request on the split path,
+    then the first fp64_requests of the same stream (same arrival times) on the FP64 path."""
     from paper_1912_06636_gb300 import serve, synth
 
     stream = synth.serving_stream(n_requests, rate=200.0, seed=4, n_min=3, n_max=200)
@@ -168,20 +172,36 @@ def serving(n_requests: int, device: int) -> dict:
     reqs = []
     for rid, (t, na, seed) in enumerate(stream):
         s = synth.random_molecule(na, seed, **SERVE_GRID)
-        reqs.append(serve.Request(rid=rid, system=s, v0=s.potential(), arrival_s=t, n_iter=20, seed=seed))
+        reqs.append(serve.Request(rid=rid, system=s, v0=s.potential(on_device=True), arrival_s=t, n_iter=20, seed=seed))
     gen_s = time.perf_counter() - t0
     out = {"workload": f"{n_requests} requests, Poisson arrivals at 200/s (seed 4), molecules of 3-200 atoms "
                        f"(log-uniform; species Si/A/B), {SERVE_GRID['n_rad']}x{SERVE_GRID['n_theta'] * SERVE_GRID['n_phi']} "
                        "points per atom, batches <= 200 points, 20 iterations each (v perturbed 1%, fresh P), "
-                       "HBM budget 150 GB, 16 slots, CUDA graphs",
-           "atoms": [int(na) for _, na, _ in stream], "points": [int(len(r.v0)) for r in reqs],
-           "generate_s": gen_s}
-    for prec in ("split", "fp64"):
+                       f"HBM budget 150 GB, 16 slots, CUDA graphs; FP64 on the first {min(fp64_requests, n_requests)} "
+                       "requests of the same stream",
+           "atoms_mean": float(sum(na for _, na, _ in stream) / max(len(stream), 1)),
+           "points_total": int(sum(len(r.v0) for r in reqs)), "generate_s": gen_s}
+    for prec, rs in (("split", reqs), ("fp64", reqs[:fp64_requests])):
+        if not rs:
+            continue
         srv = serve.Server(prec=prec, hbm_budget_bytes=150 << 30, max_active=16, device=device)
-        res = srv.run(reqs)
-        out[prec] = serve.summarize(res, srv.stats)
-    if out["split"]["p99_ms"] and out["fp64"]["p99_ms"]:
-        out["p99_speedup_vs_fp64"] = out["fp64"]["p99_ms"] / out["split"]["p99_ms"]
+        res = srv.run(rs)
+        sm = serve.summarize(res, srv.stats)
+        # the rate the server sustains while requests wait: requests over the busy period
+        busy = max(r.done_s for r in res) - min(r.admitted_s for r in res)
+        sm["sustainable_requests_per_s"] = len(res) / busy if busy > 0 else None
+        sm["arrival_rate_per_s"] = 200.0
+        out[prec] = sm
+    if "fp64" in out:
+        # the same requests on both paths: the prefix the FP64 run served
+        k = out["fp64"]["requests"]
+        split_prefix = serve.Server(prec="split", hbm_budget_bytes=150 << 30, max_active=16, device=device)
+        res = split_prefix.run(reqs[:k])
+        pre = serve.summarize(res, split_prefix.stats)
+        out["split_on_fp64_prefix"] = {"requests": k, "p50_ms": pre["p50_ms"], "p99_ms": pre["p99_ms"],
+                                       "makespan_s": pre["makespan_s"]}
+        if pre["p99_ms"] and out["fp64"]["p99_ms"]:
+            out["p99_speedup_vs_fp64"] = out["fp64"]["p99_ms"] / pre["p99_ms"]
     return out
 
 
@@ -196,63 +216,80 @@ TRAFFIC_PER_FLOP_H = {
 }
 
 
-GROUP_GRID = dict(n_rad=30, n_theta=8, n_phi=9)
-
-
-def grouped(n_mol: int, device: int, steps: int = 3) -> dict:
-    """Many molecules: one grouped handle (one launch per kernel for all of them, CUDA graphs)
-    against one handle per molecule, the same H + n step on one stream, split path."""
+def grouped(n_mol: int, device: int, steps: int = 3, per_molecule_max: int = 256) -> dict:
+    """Many molecules (the batching configuration): molecules of 3-60 atoms on their species'
+    grids with batch sizes log-uniform in [20, 400], in one grouped handle (one launch per kernel
+    for all of them, CUDA graphs), the H + n step timed on the split path (library default
+    slices) and on the FP64 path; against one handle per molecule when there are at most
+    per_molecule_max of them (creating a thousand handles would dominate the run)."""
+    import numpy as np
     import torch
 
     from paper_1912_06636_gb300 import nao, synth
 
     t0 = time.perf_counter()
-    systems, bs = synth.molecule_set(n_mol, seed=3000, n_min=3, n_max=60, b_min=20, b_max=400, **GROUP_GRID)
+    systems, bs = synth.molecule_set(n_mol, seed=3000, n_min=3, n_max=60, b_min=20, b_max=400, species_grids=True)
     dev = torch.device("cuda", device)
-    vs = [torch.from_numpy(s.potential()).to(dev) for s in systems]
-    Ps = [torch.from_numpy(synth.density_matrix(s, 3000 + k)).to(dev) for k, s in enumerate(systems)]
+    vs = [torch.from_numpy(s.potential(on_device=True)).to(dev) for s in systems]
+    Ps = [torch.from_numpy(synth.density_matrix(s, 3000 + k, rank=64)).to(dev) for k, s in enumerate(systems)]
     gen_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
-    out = {"workload": f"{n_mol} molecules of 3-60 atoms (log-uniform, seed 3000; species Si/A/B), "
-                       f"{GROUP_GRID['n_rad']}x{GROUP_GRID['n_theta'] * GROUP_GRID['n_phi']} points per atom, "
-                       "batch sizes log-uniform in [20, 400]; one step = H + n of every molecule, split path "
-                       "(12 slices)",
-           "points": int(sum(s.n_points for s in systems)), "generate_s": gen_s}
+    atoms = [s.n_atoms for s in systems]
+    out = {"workload": f"{n_mol} molecules of 3-60 atoms (log-uniform, seed 3000; species Si/A/B, each atom on its "
+                       "species' grid: Si 60x306, A/B 80x434 points), batch sizes log-uniform in [20, 400]; one step "
+                       "= H + n of every molecule; P = X X^T / 64 (rank 64)",
+           "molecules": n_mol, "atoms": int(sum(atoms)), "points": int(sum(s.n_points for s in systems)),
+           "generate_s": gen_s}
 
-    def timed(fn):
+    def timed(fn, k=steps):
         fn()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for _ in range(steps):
+        for _ in range(k):
             fn()
         b.record(stream)
         torch.cuda.synchronize()
-        return a.elapsed_time(b) / steps
+        return a.elapsed_time(b) / k
 
+    t0 = time.perf_counter()
     g = nao.Grid(systems, device=device, batch_points=bs, capture_graph=1)
-    Hs = [torch.empty((s["n_basis"], s["n_basis"]), dtype=torch.float64, device=dev) for s in g.systems]
-    ns = [torch.empty(s["n_points"], dtype=torch.float64, device=dev) for s in g.systems]
+    torch.cuda.synchronize()
+    out["create_s"] = time.perf_counter() - t0
+    bo, _, ro, _ = g.batches()
+    Pb, Nb = np.diff(bo), np.diff(ro)
+    out["batches"] = {"count": int(len(Pb)), "points_min": int(Pb.min()), "points_max": int(Pb.max()),
+                      "points_mean": float(Pb.mean()), "basis_min": int(Nb.min()), "basis_max": int(Nb.max()),
+                      "basis_mean": float(Nb.mean()), "basis_pct": [int(x) for x in np.percentile(Nb, [5, 50, 95])]}
+    Hs = [torch.empty((m["n_basis"], m["n_basis"]), dtype=torch.float64, device=dev) for m in g.systems]
+    ns = [torch.empty(m["n_points"], dtype=torch.float64, device=dev) for m in g.systems]
     nes = [torch.empty(1, dtype=torch.float64, device=dev) for _ in g.systems]
-    ms_g = timed(lambda: (g.integrate_h_many(vs, prec="split", Hs=Hs, stream=stream),
-                          g.update_density_many(Ps, prec="split", ns=ns, nes=nes, stream=stream)))
+    for prec in ("split", "fp64"):
+        ms = timed(lambda: (g.integrate_h_many(vs, prec=prec, Hs=Hs, stream=stream),
+                            g.update_density_many(Ps, prec=prec, ns=ns, nes=nes, stream=stream)),
+                   k=steps if prec == "split" else 1)
+        out[f"grouped_{prec}_ms_per_step"] = ms
+        out[f"grouped_{prec}_points_per_s"] = out["points"] / (ms / 1e3)
+    tw, tuned = nao.nao_get_tuning(g.h)
+    out["tuning"] = {"buckets_timed": int(tuned), "tile_widths": sorted(set(int(x) for x in tw[Nb > 0]))}
+    out["gflops_algorithmic_split"] = (g.info.flops_h + g.info.flops_n) / (out["grouped_split_ms_per_step"] / 1e3) / 1e9
+    out["speedup_split_vs_fp64"] = out["grouped_fp64_ms_per_step"] / out["grouped_split_ms_per_step"]
     g.sync()
     g.close()
-    singles = [nao.Grid(s, device=device, max_batch_points=b) for s, b in zip(systems, bs)]
+    if n_mol <= per_molecule_max:
+        singles = [nao.Grid(s, device=device, max_batch_points=b) for s, b in zip(systems, bs)]
 
-    def one_by_one():
-        for k, h in enumerate(singles):
-            h.integrate_h(vs[k], prec="split", H=Hs[k], stream=stream)
-            h.update_density(Ps[k], prec="split", n=ns[k], ne=nes[k], stream=stream)
+        def one_by_one():
+            for k, h in enumerate(singles):
+                h.integrate_h(vs[k], prec="split", H=Hs[k], stream=stream)
+                h.update_density(Ps[k], prec="split", n=ns[k], ne=nes[k], stream=stream)
 
-    ms_s = timed(one_by_one)
-    for h in singles:
-        h.sync()
-        h.close()
-    pts = out["points"]
-    out.update({"grouped_ms_per_step": ms_g, "grouped_points_per_s": pts / (ms_g / 1e3),
-                "per_molecule_ms_per_step": ms_s, "per_molecule_points_per_s": pts / (ms_s / 1e3),
-                "speedup_grouped": ms_s / ms_g})
+        ms_s = timed(one_by_one)
+        for h in singles:
+            h.sync()
+            h.close()
+        out.update({"per_molecule_split_ms_per_step": ms_s,
+                    "speedup_grouped": ms_s / out["grouped_split_ms_per_step"]})
     return out
 
 
@@ -694,7 +731,7 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_serve and args.serve_requests > 0:
         g.close()
-        line["serving"] = serving(args.serve_requests, local_rank)
+        line["serving"] = serving(args.serve_requests, local_rank, args.serve_fp64_requests)
     if rank == 0 and world == 1 and args.grouped_molecules > 0:
         if g.h:
             g.close()

@@ -95,8 +95,18 @@ typedef struct {
                                  slice (measured e_H on an 8-atom cell with 20 radial shells:
                                  1.6e-9 at 10, 4.6e-11 at 11, 8.6e-13 at 12 slices). 4..10 slices
                                  run 128x48 tensor-core tiles, 11..12 slices 128x32 tiles. */
-    int32_t deterministic;    /* reserved; results are already run-to-run reproducible up to
-                                 the order of FP64 atomic additions into H */
+    int32_t deterministic;    /* 0 (default): the batches' contributions to H are FP64 atomic
+                                 additions, whose order (and so H's last bits) varies from run to
+                                 run. 1: every contribution is added exactly as a 128-bit
+                                 fixed-point integer (resolution 2^-90, contributions below 2^37)
+                                 and H is converted once at the end, so H is bitwise the same
+                                 from run to run on every precision path (each contribution is
+                                 rounded to 2^-90, the exact sum converted with a relative error
+                                 below 2^-52); costs 16 bytes of device memory per H
+                                 element of every system, taken at create, and two integer atomics
+                                 per contribution. n, grad n, the Hessian and N_e have no atomics
+                                 and are reproducible either way; the Pulay matrices and the Bloch
+                                 sum keep FP64 atomics. */
     int32_t device;           /* CUDA device ordinal; -1 = the calling thread's current device */
     int64_t scratch_bytes;    /* device scratch for evaluated basis functions; 0 = library default (8 GiB;
                                  the split path's slices take three times this). Memory is taken only

@@ -48,7 +48,7 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> Path:
             if log.strip():
                 print(f"--- {s.name}\n{log}")
     tmp = str(LIB) + ".tmp"
-    cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *map(str, objs)]
+    cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *map(str, objs), "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

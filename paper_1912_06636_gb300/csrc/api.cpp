@@ -1,6 +1,7 @@
 // C ABI of libnao (see include/nao.h): validation, set-up of a grid handle, and the
 // per-call dispatch of the evaluation and contraction kernels onto the caller's stream.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -8,6 +9,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 
 #include "nao_internal.h"
 
@@ -360,20 +362,51 @@ nao_status build(nao_grid *g, const nao_system_desc *descs, int32_t n_sys, const
     const int64_t n = (int64_t)wts.size();
     g->n_points = n;
 
-    // Sec. 3.3.1: batches, system by system
+    // Sec. 3.3.1: batches, system by system. The systems' partitions are independent, so they
+    // run on host threads (each system on one thread, systems handed out in order of size);
+    // the result is the same as in sequence.
     std::vector<int32_t> bmol;
     g->batch_off.assign(1, 0);
     g->perm.clear();
     for (int m = 0; m < n_sys; m++) {
-        std::vector<int64_t> off, perm;
         const int B = batch_points ? batch_points[m] : g->opt.max_batch_points;
         if (B < 1 || B > NAO_MAX_BATCH) return fail(NAO_ERR_INVALID_ARG, "batch size outside 1..1024");
-        nao_partition(descs[m].n_points, descs[m].pt_xyz, B, off, perm);
+    }
+    std::vector<std::vector<int64_t>> offs(n_sys), perms(n_sys);
+    {
+        std::vector<int32_t> order(n_sys);
+        for (int m = 0; m < n_sys; m++) order[m] = m;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int32_t a, int32_t b) { return descs[a].n_points > descs[b].n_points; });
+        std::atomic<int32_t> next{0};
+        auto work = [&]() {
+            for (int32_t k; (k = next.fetch_add(1)) < n_sys;) {
+                const int m = order[k];
+                nao_partition(descs[m].n_points, descs[m].pt_xyz, batch_points ? batch_points[m] : g->opt.max_batch_points,
+                              offs[m], perms[m]);
+            }
+        };
+        int64_t total_pts = 0;
+        for (int m = 0; m < n_sys; m++) total_pts += descs[m].n_points;
+        const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+        const int nthr = (int)std::min<int64_t>({(int64_t)hw, (int64_t)n_sys, 1 + total_pts / 200000});
+        std::vector<std::thread> pool;
+        try {
+            for (int t = 1; t < nthr; t++) pool.emplace_back(work);
+        } catch (...) {  // no more threads: the calling thread does the rest
+        }
+        work();
+        for (auto &th : pool) th.join();
+    }
+    for (int m = 0; m < n_sys; m++) {
+        const std::vector<int64_t> &off = offs[m];
         for (size_t k = 1; k < off.size(); k++) {
             g->batch_off.push_back(g->sys_poff[m] + off[k]);
             bmol.push_back(m);
         }
-        for (int64_t p : perm) g->perm.push_back(g->sys_poff[m] + p);
+        for (int64_t p : perms[m]) g->perm.push_back(g->sys_poff[m] + p);
+        std::vector<int64_t>().swap(offs[m]);
+        std::vector<int64_t>().swap(perms[m]);
     }
     g->n_batches = (int64_t)bmol.size();
     const int64_t nbat = g->n_batches;
@@ -581,10 +614,21 @@ nao_status build(nao_grid *g, const nao_system_desc *descs, int32_t n_sys, const
         (st = upload(g, &g->d_zero_tasks, g->zero_tasks.data(), g->zero_tasks.size())) ||
         (st = upload(g, &g->d_mirror_tasks, g->mirror_tasks.data(), g->mirror_tasks.size())) ||
         (st = upload(g, &g->d_sys_np, g->sys_np.data(), g->sys_np.size())) ||
-        (st = dev_alloc(g, &g->d_tab, 7 * (size_t)n_sys)))
+        (st = dev_alloc(g, &g->d_tab, 8 * (size_t)n_sys)))
         return st;
-    NAO_CUDA(cudaMemsetAsync(g->d_tab, 0, 7 * (size_t)n_sys * sizeof(double *), g->setup));
-    g->h_tab.assign(7 * (size_t)n_sys, nullptr);
+    NAO_CUDA(cudaMemsetAsync(g->d_tab, 0, 8 * (size_t)n_sys * sizeof(double *), g->setup));
+    g->h_tab.assign(8 * (size_t)n_sys, nullptr);
+    if (g->opt.deterministic) {
+        // section 7: each system's fixed-point H accumulators (2 words per element), fixed for the
+        // handle's life
+        for (int m = 0; m < n_sys; m++) {
+            unsigned long long *acc = nullptr;
+            if ((st = dev_alloc(g, &acc, 2 * (size_t)g->sys_nb[m] * (size_t)g->sys_nb[m]))) return st;
+            g->h_tab[7 * (size_t)n_sys + m] = acc;
+        }
+        NAO_CUDA(copy_async(g->d_tab + 7 * (size_t)n_sys, g->h_tab.data() + 7 * (size_t)n_sys,
+                            (size_t)n_sys * sizeof(void *), cudaMemcpyHostToDevice, g->setup));
+    }
 
     DevSystem &s = g->sys;
     s.atom_xyz = d_atoms;
@@ -618,6 +662,7 @@ nao_status build(nao_grid *g, const nao_system_desc *descs, int32_t n_sys, const
     s.sys.ne = g->d_tab + 4 * n_sys;
     s.sys.gn = g->d_tab + 5 * n_sys;
     s.sys.vt = g->d_tab + 6 * n_sys;
+    s.sys.Hacc = reinterpret_cast<unsigned long long *const *>(g->d_tab + 7 * n_sys);
     s.sys.np = g->d_sys_np;
     s.n_rgrid = g->n_rgrid;
     s.r0 = g->r0;
@@ -1176,6 +1221,7 @@ static nao_status create(const nao_system_desc *descs, int32_t n_sys, const int3
     if (opts) o = *opts;
     if (o.autotune != 0 && o.autotune != 1) return fail(NAO_ERR_INVALID_ARG, "options.autotune not 0/1");
     if (o.capture_graph != 0 && o.capture_graph != 1) return fail(NAO_ERR_INVALID_ARG, "options.capture_graph not 0/1");
+    if (o.deterministic != 0 && o.deterministic != 1) return fail(NAO_ERR_INVALID_ARG, "options.deterministic not 0/1");
     nao_status st;
     if (batch_points)
         for (int32_t m = 0; m < n_sys; m++)

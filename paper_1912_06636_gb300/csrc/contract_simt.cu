@@ -158,23 +158,37 @@ __global__ void __launch_bounds__(256) h_simt_kernel(DevSystem s, const HWork *_
         for (int c = 0; c < 4; c++) {
             const int j = j0 + tx * 4 + c;
             if (j >= N || (diag && j < i)) continue;
-            atomicAdd(h_elem(s, m, gi, rel[j]), acc.value(a, c));
+            h_add(s, m, gi, rel[j], acc.value(a, c));
         }
     }
 }
 
 // Copy the upper triangle of each system's H onto its lower one, through 32 x 32 tiles; one
 // CTA per task (system, column tile bx, row tile by) with by <= bx.
+// In the deterministic mode the upper triangle comes from the fixed-point accumulators, converted
+// once here (and written to both triangles).
 __global__ void mirror_kernel(DevSystem s, const int4 *__restrict__ tasks) {
     __shared__ double tile[32][33];
     const int4 tk = tasks[blockIdx.x];
     const int m = tk.x, bx = tk.y, by = tk.z;
     double *H = s.sys.H[m];
+    const unsigned long long *acc = s.sys.Hacc[m];
     const int64_t nb = s.sys.nbm[m];
     const int tx = threadIdx.x, ty = threadIdx.y;
     for (int r = ty; r < 32; r += blockDim.y) {
         const int64_t row = (int64_t)by * 32 + r, col = (int64_t)bx * 32 + tx;
-        tile[r][tx] = (row < nb && col < nb) ? H[row * nb + col] : 0.0;
+        double h = 0.0;
+        if (row < nb && col < nb) {
+            if (acc) {
+                if (row <= col) {
+                    h = det_value(acc + 2 * (row * nb + col));
+                    H[row * nb + col] = h;
+                }
+            } else {
+                h = H[row * nb + col];
+            }
+        }
+        tile[r][tx] = h;
     }
     __syncthreads();
     for (int r = ty; r < 32; r += blockDim.y) {
@@ -183,9 +197,16 @@ __global__ void mirror_kernel(DevSystem s, const int4 *__restrict__ tasks) {
     }
 }
 
-// H = 0 for each task (system, first element, count).
+// H = 0 for each task (system, first element, count); in the deterministic mode its fixed-point
+// accumulators instead (H itself is then written whole by the mirror pass).
 __global__ void __launch_bounds__(256) zero_h_kernel(DevSystem s, const int4 *__restrict__ tasks) {
     const int4 tk = tasks[blockIdx.x];
+    unsigned long long *acc = s.sys.Hacc[tk.x];
+    if (acc) {
+        acc += 2 * ((int64_t)tk.y * 65536);
+        for (int i = threadIdx.x; i < 2 * tk.z; i += blockDim.x) acc[i] = 0ULL;
+        return;
+    }
     double *H = s.sys.H[tk.x] + (int64_t)tk.y * 65536;
     for (int i = threadIdx.x; i < tk.z; i += blockDim.x) H[i] = 0.0;
 }

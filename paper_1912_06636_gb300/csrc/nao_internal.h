@@ -47,6 +47,8 @@ struct SysTables {
     double *const *ne;       // [n_sys] this call's N_e of each system (NULL entry: not formed)
     double *const *gn;       // [n_sys] this call's grad n of each system ([3][np], component-major)
     const double *const *vt; // [n_sys] this call's v_tau of each system (NULL entry: no tau term)
+    unsigned long long *const *Hacc;  // [n_sys] deterministic mode: the system's H as 128-bit fixed-point
+                                      // integers (lo, hi per element); NULL entries: FP64 atomics into H
     const int32_t *np;       // [n_sys] points of the system
 };
 
@@ -81,6 +83,41 @@ struct DevSystem {
 __device__ __forceinline__ double *h_elem(const DevSystem &s, int m, int64_t gi, int64_t gj) {
     const int64_t bo = s.sys.boff[m];
     return s.sys.H[m] + (gi - bo) * (int64_t)s.sys.nbm[m] + (gj - bo);
+}
+
+// Deterministic accumulation: x is added as the 128-bit two's-complement integer X = round(x 2^90)
+// (|x| < 2^37), low word first; a wrap of the unsigned low word carries one into the high word.
+// Integer addition is associative, so the final (hi, lo) of an element, and the FP64 value the
+// mirror pass makes of it, do not depend on the order of the additions.
+constexpr int NAO_DET_FRAC = 90;
+__device__ __forceinline__ void det_add(unsigned long long *acc, double x) {
+    const double y = x * 0x1p26;  // x 2^(90 - 64), exact
+    const double f = floor(y);
+    long long hi = (long long)f;
+    const double fr = rint((y - f) * 0x1p64);  // the fraction in units of 2^-90: [0, 2^64]
+    unsigned long long lo;
+    if (fr >= 0x1p64) {
+        lo = 0ULL;
+        hi += 1;
+    } else {
+        lo = (unsigned long long)fr;
+    }
+    const unsigned long long old = atomicAdd(acc, lo);
+    atomicAdd(acc + 1, (unsigned long long)hi + (old + lo < old ? 1ULL : 0ULL));
+}
+__device__ __forceinline__ double det_value(const unsigned long long *acc) {
+    return fma((double)(long long)acc[1], 0x1p-26, (double)acc[0] * 0x1p-90);
+}
+
+// H_ij += x for system m: an FP64 atomic, or the deterministic fixed-point addition.
+__device__ __forceinline__ void h_add(const DevSystem &s, int m, int64_t gi, int64_t gj, double x) {
+    unsigned long long *acc = s.sys.Hacc[m];
+    if (acc) {
+        const int64_t bo = s.sys.boff[m];
+        det_add(acc + 2 * ((gi - bo) * (int64_t)s.sys.nbm[m] + (gj - bo)), x);
+    } else {
+        atomicAdd(h_elem(s, m, gi, gj), x);
+    }
 }
 __device__ __forceinline__ double p_elem(const DevSystem &s, int m, int64_t gi, int64_t gj) {
     const int64_t bo = s.sys.boff[m];

@@ -634,7 +634,7 @@ __global__ void __launch_bounds__(192, 1)
                         const double x = (ei > -10000 && ej > -10000)
                                              ? (double)val[jj] * pow2(ei + ej - (((small_mask >> jj) & 1) ? 66 : 50))
                                              : 0.0;
-                        atomicAdd(h_elem(s, h.m, gi, rel[j]), x);
+                        h_add(s, h.m, gi, rel[j], x);
                     }
                 }
             }

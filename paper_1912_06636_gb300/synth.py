@@ -150,12 +150,13 @@ def build_grid(atoms: np.ndarray, n_rad, n_theta, n_phi, rm: float = 1.0):
     return np.ascontiguousarray(pts), wts * wb
 
 
-def model_potential(pts: np.ndarray, atoms: np.ndarray, Z: np.ndarray) -> np.ndarray:
+def model_potential(pts: np.ndarray, atoms: np.ndarray, Z: np.ndarray, on_device: bool = False) -> np.ndarray:
     """v(r) = sum_A [ -Z_A erf(r_A)/r_A + 0.3 exp(-r_A^2) ], with erf(r)/r -> 2/sqrt(pi) at r = 0.
 
-    Inputs of more than 2M points are generated with torch on a CUDA device when one is
-    present (input generation only; the caller passes the same array to every consumer)."""
-    if pts.shape[0] > 2_000_000:
+    Inputs of more than 2M points (or any input, with on_device) are generated with torch on a
+    CUDA device when one is present (input generation only; the caller passes the same array to
+    every consumer)."""
+    if pts.shape[0] > 2_000_000 or on_device:
         import torch
 
         if torch.cuda.is_available():
@@ -233,8 +234,8 @@ class System:
         ]
         return int(sum(per_species[s] for s in self.atom_species))
 
-    def potential(self) -> np.ndarray:
-        return model_potential(self.pt_xyz, self.atom_xyz, self.Z)
+    def potential(self, on_device: bool = False) -> np.ndarray:
+        return model_potential(self.pt_xyz, self.atom_xyz, self.Z, on_device)
 
 
 def make_system(
@@ -353,11 +354,18 @@ def config_slab375(n_rad=80, n_theta=14, n_phi=31, max_batch_points=200, layers=
                        max_batch_points=max_batch_points, name=f"slab{len(atoms)}")
 
 
+# Per-atom grids of the species in their own configurations: Si as in the diamond cluster
+# (60 shells x 17 x 18 directions), A and B as in the slab (80 shells x 14 x 31).
+SPECIES_GRIDS = {"n_rad": (60, 80, 80), "n_theta": (17, 14, 14), "n_phi": (18, 31, 31)}
+
+
 def random_molecule(n_atoms: int, seed: int, n_rad=40, n_theta=10, n_phi=11, max_batch_points=200,
-                    min_dist: float = 2.0) -> System:
+                    min_dist: float = 2.0, species_grids: bool = False) -> System:
     """A random molecule: atoms placed one by one, uniformly in a sphere of volume 135 n_atoms
     bohr^3 (the atom density of silicon), rejecting any within min_dist of an earlier atom;
-    each atom's species drawn uniformly from {Si (diamond cluster), A, B (slab)}."""
+    each atom's species drawn uniformly from {Si (diamond cluster), A, B (slab)}. With
+    species_grids, every atom gets its species' grid (SPECIES_GRIDS) instead of n_rad x
+    (n_theta x n_phi)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     radius = (3.0 * 135.0 * n_atoms / (4.0 * math.pi)) ** (1.0 / 3.0)
     atoms = []
@@ -369,21 +377,23 @@ def random_molecule(n_atoms: int, seed: int, n_rad=40, n_theta=10, n_phi=11, max
             atoms.append(p)
     spec = rng.integers(0, 3, n_atoms).astype(np.int32)
     species = [silicon_species(1), slab_species("A"), slab_species("B")]
+    if species_grids:
+        n_rad, n_theta, n_phi = (np.asarray(SPECIES_GRIDS[k])[spec] for k in ("n_rad", "n_theta", "n_phi"))
     return make_system(np.asarray(atoms), spec, species, n_rad, n_theta, n_phi,
                        max_batch_points=max_batch_points, name=f"mol{n_atoms}-{seed}")
 
 
 def molecule_set(n_mol: int, seed: int = 3000, n_min: int = 3, n_max: int = 60, b_min: int = 20, b_max: int = 400,
-                 n_rad=60, n_theta=17, n_phi=18):
+                 n_rad=60, n_theta=17, n_phi=18, species_grids: bool = False):
     """Independent molecules for one grouped handle: molecule k has a size log-uniform in
     [n_min, n_max] atoms and a batch size log-uniform in [b_min, b_max] points, both drawn
-    with seed + k (random_molecule's rules for geometry and species). Returns (systems, B)."""
+    with seed + k (random_molecule's rules for geometry, species and grids). Returns (systems, B)."""
     systems, bs = [], []
     for k in range(n_mol):
         rng = np.random.Generator(np.random.PCG64(seed + k))
         na = int(min(n_max, np.floor(_log_uniform(rng, n_min, n_max + 1, 1)[0])))
         b = int(min(b_max, np.floor(_log_uniform(rng, b_min, b_max + 1, 1)[0])))
-        sysk = random_molecule(na, seed + k, n_rad, n_theta, n_phi, max_batch_points=b)
+        sysk = random_molecule(na, seed + k, n_rad, n_theta, n_phi, max_batch_points=b, species_grids=species_grids)
         systems.append(sysk)
         bs.append(b)
     return systems, bs
