@@ -830,29 +830,26 @@ __global__ void __launch_bounds__(192, 1)
             const bool row_ok = q < h.P;
             const double *E = scratch + s.scr_off[h.b];
             const int64_t ld = GRADN ? 4 * (int64_t)h.Ppad : (int64_t)h.Ppad;
-            // sum_j T_qj phi_qj (and grad phi) in units of 2^(e_q + e_b - 50). Width 48 (S <= 10):
-            // each T_qj as one 64-bit integer in those units, 4 hi + round(lo / 2^16) (|4 hi| <
-            // 2^62.03), rounded by at most 2^-1 unit, the order of the split's own truncation (the
-            // dropped groups g >= S reach K (S + 1) 2^(e_q + e_b - 6S - 2)); then one conversion
-            // and one FMA per product. Width 32 (S = 11, 12, whose truncation is far smaller): T_qj
-            // rounded to FP64 relative to itself, 4 hi + lo 2^-16 + lo2 2^-34.
+            // sum_j T_qj phi_qj (and grad phi) in units of 2^(e_q + e_b - 50): each T_qj as one
+            // 64-bit integer in those units, 4 hi + round(lo' / 2^16) (|4 hi| < 2^62.03; lo' = lo +
+            // round(lo2 / 2^18) folds the groups g >= 10 of S = 11, 12), rounded by at most 2^-1
+            // unit: the order of the split's truncation at S = 10 (the dropped groups g >= S reach
+            // K (S + 1) 2^(e_q + e_b - 6S - 2)) and below the FP64 evaluation's rounding in n. Then
+            // one conversion and one FMA per product, all integer work done before tensor memory is
+            // handed back (no FP64 arithmetic on that path).
             double part = 0.0, gpart[3] = {0.0, 0.0, 0.0};
             for (int J = 0; J < h.nJ; J++, t++) {
                 if (*abort || !tc::mbar_wait(&pp.acc_full, t & 1, kWaitCycles)) { *abort = 1; break; }
                 tc::fence_after_sync();
-                using Val = typename std::conditional<TN == 48, long long, double>::type;
-                Val val[TN];
+                long long val[TN];
 #pragma unroll
                 for (int c0 = 0; c0 < TN; c0 += 16) {
                     Parts16 v;
                     combine16<TN>(tm_row, c0, S, v);
 #pragma unroll
                     for (int jj = 0; jj < 16; jj++) {
-                        if constexpr (TN == 48)
-                            val[c0 + jj] = (v.hi[jj] << 2) + ((v.lo[jj] + (1LL << 15)) >> 16);
-                        else
-                            val[c0 + jj] = fma((double)v.lo2[jj], 0x1p-34,
-                                               fma((double)v.lo[jj], 0x1p-16, 4.0 * (double)v.hi[jj]));
+                        const long long lo = v.lo[jj] + ((v.lo2[jj] + (1LL << 17)) >> 18);  // lo2: S = 11, 12
+                        val[c0 + jj] = (v.hi[jj] << 2) + ((lo + (1LL << 15)) >> 16);
                     }
                 }
                 // tensor memory is free for the next tile

@@ -85,8 +85,11 @@ def test_twelve_slices_have_one_tile_width(mols):
 
 def test_ten_slice_autotuner(mols):
     """With 10 slices both widths exist: the autotuner times them per histogram bucket; the
-    tuned run and the fixed rule give the same H and n up to the order of the FP64 additions
-    (every element's slice sums are exact integers whatever the tile)."""
+    tuned run and the fixed rule give the same H up to the order of the FP64 additions (every
+    element's slice sums are exact integers whatever the tile) and the same n up to the rounding
+    of each T element to a 64-bit integer in units of 2^(e_q + e_b - 50), whose grouping into
+    tiles follows the width (at most 1e-13 of the magnitude sums D; the bar against the oracle is
+    1e-10)."""
     systems, bs, refs = mols["systems"], mols["bs"], mols["refs"]
     sel = list(range(len(systems)))
     kw = dict(device=0, batch_points=[bs[k] for k in sel], split_slices=10)
@@ -109,7 +112,7 @@ def test_ten_slice_autotuner(mols):
           int(np.sum(tw1[N > 0] == 32)), "at 32")
     for m, k in enumerate(sel):
         assert rel_err(Hs1[m], Hs0[m], refs[k]["A"]) <= 1e-14
-        assert rel_err(ns1[m], ns0[m], refs[k]["D"]) <= 1e-14
+        assert rel_err(ns1[m], ns0[m], refs[k]["D"]) <= 1e-13
 
 
 def test_graphs_recorded_before_tuning_are_replaced(mols):
