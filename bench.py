@@ -42,6 +42,13 @@ WORKLOADS = {
 # split slices timed per workload: the count whose e <= 1e-10 the full-size parity tests check
 # on the same input (tests/test_gpu_slab.py, tests/test_gpu_fullsize.py)
 BENCH_SLICES = {1: 11, 2: 11}
+# digit format timed per workload (bf16: base-64 digits, kind::f16; e4m3: base-32 digits,
+# kind::f8f6f4) and the slice counts of each format that the parity tests check
+BENCH_DIGITS = {1: "e4m3", 2: "e4m3"}
+BENCH_SLICES_E4M3 = {1: 14, 2: 14}
+# the split setting of the grouped and serving blocks (the molecule tests check it)
+BENCH_SPLIT_OPTS = {"split_slices": 14, "split_digits": 1}
+BENCH_SERVE_OPTS = {"split_slices": 14, "split_digits": 1}
 
 
 def parse():
@@ -60,6 +67,8 @@ def parse():
                     help="slab: layers (15 = the 375-atom workload; fewer = a profiling case, not a bench line)")
     ap.add_argument("--scratch-mb", type=int, default=0,
                     help="evaluation scratch of the handle in MiB (0: the library default; the split slices get twice this)")
+    ap.add_argument("--digits", default=None, choices=[None, "bf16", "e4m3"],
+                    help="split path digit format (default: the one the workload is benched with)")
     ap.add_argument("--slices", type=int, default=None,
                     help="split path: slices per operand (default: the count the full-size parity test checks "
                          "on the workload; the library default is 12)")
@@ -184,7 +193,7 @@ def serving(n_requests: int, device: int, fp64_requests: int) -> dict:
     for prec, rs in (("split", reqs), ("fp64", reqs[:fp64_requests])):
         if not rs:
             continue
-        srv = serve.Server(prec=prec, hbm_budget_bytes=150 << 30, max_active=16, device=device)
+        srv = serve.Server(prec=prec, hbm_budget_bytes=150 << 30, max_active=16, device=device, **BENCH_SERVE_OPTS)
         res = srv.run(rs)
         sm = serve.summarize(res, srv.stats)
         # the rate the server sustains while requests wait: requests over the busy period
@@ -195,7 +204,8 @@ def serving(n_requests: int, device: int, fp64_requests: int) -> dict:
     if "fp64" in out:
         # the same requests on both paths: the prefix the FP64 run served
         k = out["fp64"]["requests"]
-        split_prefix = serve.Server(prec="split", hbm_budget_bytes=150 << 30, max_active=16, device=device)
+        split_prefix = serve.Server(prec="split", hbm_budget_bytes=150 << 30, max_active=16, device=device,
+                                    **BENCH_SERVE_OPTS)
         res = split_prefix.run(reqs[:k])
         pre = serve.summarize(res, split_prefix.stats)
         out["split_on_fp64_prefix"] = {"requests": k, "p50_ms": pre["p50_ms"], "p99_ms": pre["p99_ms"],
@@ -253,7 +263,7 @@ def grouped(n_mol: int, device: int, steps: int = 3, per_molecule_max: int = 256
         return a.elapsed_time(b) / k
 
     t0 = time.perf_counter()
-    g = nao.Grid(systems, device=device, batch_points=bs, capture_graph=1)
+    g = nao.Grid(systems, device=device, batch_points=bs, capture_graph=1, **BENCH_SPLIT_OPTS)
     torch.cuda.synchronize()
     out["create_s"] = time.perf_counter() - t0
     bo, _, ro, _ = g.batches()
@@ -277,7 +287,7 @@ def grouped(n_mol: int, device: int, steps: int = 3, per_molecule_max: int = 256
     g.sync()
     g.close()
     if n_mol <= per_molecule_max:
-        singles = [nao.Grid(s, device=device, max_batch_points=b) for s, b in zip(systems, bs)]
+        singles = [nao.Grid(s, device=device, max_batch_points=b, **BENCH_SPLIT_OPTS) for s, b in zip(systems, bs)]
 
         def one_by_one():
             for k, h in enumerate(singles):
@@ -382,8 +392,16 @@ def workload_name(args) -> str:
     return WORKLOADS[args.config]
 
 
+def bench_digits(args) -> str:
+    return args.digits if args.digits is not None else BENCH_DIGITS.get(args.config, "bf16")
+
+
 def bench_slices(args) -> int:
-    return args.slices if args.slices is not None else BENCH_SLICES.get(args.config, 12)
+    if args.slices is not None:
+        return args.slices
+    if bench_digits(args) == "e4m3":
+        return BENCH_SLICES_E4M3.get(args.config, 14)
+    return BENCH_SLICES.get(args.config, 12)
 
 
 def make_workload(config: int, device: str, cells: int = 2, layers: int = 15):
@@ -531,8 +549,9 @@ def main():
     s, v_np, P_np = make_workload(args.config, f"cuda:{local_rank}", args.cells, args.slab_layers)
     dev = torch.device("cuda", local_rank)
     t0 = time.perf_counter()
-    slices = bench_slices(args)
+    slices, digits = bench_slices(args), bench_digits(args)
     extra = {"scratch_bytes": args.scratch_mb << 20} if args.scratch_mb > 0 else {}
+    extra["split_digits"] = 1 if digits == "e4m3" else 0
     g = nao.Grid(s, device=local_rank, max_batch_points=s.max_batch_points, split_slices=slices, **extra)
     torch.cuda.synchronize()
     create_s = time.perf_counter() - t0
@@ -600,6 +619,9 @@ def main():
             mp = measured_peaks()
             pk, pk_s = mp.get("bf16_tflops", 1900.0), mp.get("bf16_tflops_sustained", 1700.0)
             src_pk = "MEASURED_PEAKS.json bf16_tflops (burst; of measured)" if "bf16_tflops" in mp else "fallback 1.9 PFLOP/s"
+            if digits == "e4m3":  # e4m3 MMAs: the measured bf16 peak times the nominal fp8/bf16 ratio (4.5 / 2.25)
+                pk, pk_s = 2.0 * pk, 2.0 * pk_s
+                src_pk += " x 2 (nominal fp8 / bf16 dense ratio: the e4m3 peak)"
             roofline = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
                         "traffic": None, "kernel": fam,
                         "work": f"{pairs} slice products x algorithmic FLOPs (sum_b 4 P_b N_b (N_b+1) for H)",
@@ -627,10 +649,12 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "split": "bf16x-slices+f64"}[prec],
+        "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32", "split": f"{digits}x-slices+f64"}[prec],
         "data": "synthetic",
         "config": {"workload": workload_name(args), "precision": prec, "parallelism": f"replicas{world}",
                    "split_slices": slices if prec == "split" else None,
+                   "split_digits": digits if prec == "split" else None,
                    "l2": f"inputs/working set larger than L2: {scratch_gb:.1f} GB of evaluated basis functions "
                          "written and re-read per step",
                    "n_points": g.n_points, "n_basis": g.nb, "n_batches": int(info.n_batches),
@@ -677,9 +701,28 @@ def main():
                     line["speedup_vs_fp64"] = value / other[p]["points_per_s"]
             except nao.NaoError as e:
                 other[p] = {"unavailable": str(e)}
+        # the split path with the other digit format, at the slice count its parity tests check
+        od = "e4m3" if digits == "bf16" else "bf16"
+        os_ = BENCH_SLICES_E4M3.get(args.config, 14) if od == "e4m3" else BENCH_SLICES.get(args.config, 11)
+        try:
+            g3 = nao.Grid(s, device=local_rank, max_batch_points=s.max_batch_points, split_slices=os_,
+                          split_digits=1 if od == "e4m3" else 0)
+            for rep in range(2):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                g3.integrate_h(v, prec="split", H=H, stream=stream)
+                g3.update_density(P, prec="split", n=n, ne=ne, stream=stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+            g3.sync()
+            other[f"split_{od}_{os_}_slices"] = {"points_per_s": g.n_points / (a.elapsed_time(b) / 1e3),
+                                                  "ms_per_step": a.elapsed_time(b)}
+            g3.close()
+        except nao.NaoError as e:
+            other[f"split_{od}_{os_}_slices"] = {"unavailable": str(e)}
         # the split path at the library's default slice count
         d = nao.nao_default_options().split_slices
-        if d != slices:
+        if d != slices or digits != "bf16":
             try:
                 g2 = nao.Grid(s, device=local_rank, max_batch_points=s.max_batch_points)
                 g2.integrate_h(v, prec="split", H=H, stream=stream)

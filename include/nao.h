@@ -90,11 +90,13 @@ typedef struct {
 
 typedef struct {
     int32_t max_batch_points; /* target batch size B (Sec. 3.3.1; the paper uses 200 on GPUs); default 200 */
-    int32_t split_slices;     /* slices per operand on the NAO_SPLIT path, 4..12; default 12. Each
-                                 slice adds 6 bits: the error of an element falls about 64x per
-                                 slice (measured e_H on an 8-atom cell with 20 radial shells:
-                                 1.6e-9 at 10, 4.6e-11 at 11, 8.6e-13 at 12 slices). 4..10 slices
-                                 run 128x48 tensor-core tiles, 11..12 slices 128x32 tiles. */
+    int32_t split_slices;     /* slices per operand on the NAO_SPLIT path: 4..12 with bf16 digits
+                                 (default 12), 4..16 with e4m3 digits (split_digits). Each bf16
+                                 slice adds 6 bits and each e4m3 slice 5: the error of an element
+                                 falls about 64x (32x) per slice (measured e_H on an 8-atom cell
+                                 with 20 radial shells: 1.6e-9 at 10, 4.6e-11 at 11, 8.6e-13 at 12
+                                 bf16 slices). bf16 with 4..10 slices runs 128x48 tensor-core
+                                 tiles, otherwise 128x32. */
     int32_t deterministic;    /* 0 (default): the batches' contributions to H are FP64 atomic
                                  additions, whose order (and so H's last bits) varies from run to
                                  run. 1: every contribution is added exactly as a 128-bit
@@ -121,6 +123,11 @@ typedef struct {
                                  128x32 tensor-core tiles for each (N_b, P_b) bucket of the batch-size
                                  histogram (nao_get_tuning reports the result); 0: a fixed rule (48
                                  where S <= 10, else 32). */
+    int32_t split_digits;     /* digit format of the NAO_SPLIT path: 0 (default) balanced base-64
+                                 digits stored as bf16 (kind::f16 MMAs); 1 balanced base-32 digits
+                                 stored as e4m3 (every integer |d| <= 16 is exact in e4m3;
+                                 kind::f8f6f4 MMAs at twice the bf16 rate, half the bytes per
+                                 digit). 14 e4m3 slices carry 70 bits, 11 bf16 slices 66. */
 } nao_options;
 
 typedef struct {

@@ -274,8 +274,13 @@ nao_status validate(const nao_system_desc *d, const nao_options &o) {
         return fail(NAO_ERR_INVALID_ARG, "bad points");
     if (o.max_batch_points < 1 || o.max_batch_points > NAO_MAX_BATCH)
         return fail(NAO_ERR_INVALID_ARG, "max_batch_points must be in 1.." + std::to_string(NAO_MAX_BATCH));
-    if (o.split_slices < 4 || o.split_slices > NAO_SPLIT_MAX_SLICES)
-        return fail(NAO_ERR_INVALID_ARG, "split_slices must be in 4.." + std::to_string(NAO_SPLIT_MAX_SLICES));
+    if (o.split_digits != NAO_DIGITS_BF16 && o.split_digits != NAO_DIGITS_E4M3)
+        return fail(NAO_ERR_INVALID_ARG, "split_digits must be 0 (bf16) or 1 (e4m3)");
+    if (o.split_digits == NAO_DIGITS_BF16 && (o.split_slices < 4 || o.split_slices > NAO_SPLIT_MAX_SLICES))
+        return fail(NAO_ERR_INVALID_ARG, "split_slices must be in 4.." + std::to_string(NAO_SPLIT_MAX_SLICES) + " with bf16 digits");
+    if (o.split_digits == NAO_DIGITS_E4M3 && (o.split_slices < 8 || o.split_slices > NAO_SPLIT_MAX_SLICES_E4M3))
+        return fail(NAO_ERR_INVALID_ARG,
+                    "split_slices must be in 8.." + std::to_string(NAO_SPLIT_MAX_SLICES_E4M3) + " with e4m3 digits");
     if (d->species_fn_offset[0] != 0) return fail(NAO_ERR_INVALID_ARG, "species_fn_offset[0] != 0");
     for (int s = 0; s < d->n_species; s++)
         if (d->species_fn_offset[s + 1] < d->species_fn_offset[s])
@@ -723,13 +728,13 @@ nao_status check_prec(nao_precision p) {
 // Split-path tile width of a batch before (or without) autotuning: 32 where 48 cannot hold
 // the S accumulator groups in tensor memory, else 48 (every width in use costs a launch of its
 // own, so small batches stay with the majority).
-int default_tn(int S, int) { return S > 10 ? 32 : 48; }
+int default_tn(int S, int F) { return nao_split_tn(S, F); }
 
 // The split work lists for the current per-batch tile widths, per split chunk and width:
 // H tile pairs (batch, 128-row tile I, TN-column tile J) crossing the upper triangle, and
 // density items (batch, 128-point tile, number of TN-function tiles).
 nao_status split_lists(nao_grid *g) {
-    const int S = g->split_S;
+    const int S = g->split_S, F = g->split_F;
     std::vector<HWork> hw[2], nw[2];
     for (auto &c : g->split_chunks) {
         for (int k = 0; k < 2; k++) {
@@ -740,17 +745,17 @@ nao_status split_lists(nao_grid *g) {
             const int P = g->Pb[b], N = g->Nb[b];
             if (N == 0) continue;
             const int TN = g->split_tn[b], k = TN == 48 ? 0 : 1;
-            const SplitGeom G(P, N, S, TN);
-            nao_split_h_items(b, P, N, TN, S, hw[k]);
+            const SplitGeom G(P, N, S, TN, F);
+            nao_split_h_items(b, P, N, TN, S, hw[k], F);
             for (int Q = 0; Q < G.n_qt; Q++) nw[k].push_back({b, Q, G.n_jtN, 0});  // all J tiles in one CTA
         }
         // the persistent contraction kernels take items round-robin: heaviest first (H: longest
         // K, i.e. most K chunks in the item's segment; density: most function tiles), so that
         // every CTA gets a similar share
         auto item_kc = [&](const HWork &x) {
-            const SplitGeom G(g->Pb[x.batch], g->Nb[x.batch], S);
+            const SplitGeom G(g->Pb[x.batch], g->Nb[x.batch], S, 0, F);
             int kc0, kc1;
-            nao_split_h_seg_range(G.n_kc, nao_split_h_nseg(g->Pb[x.batch], S), x.pad, S, kc0, kc1);
+            nao_split_h_seg_range(G.n_kc, nao_split_h_nseg(g->Pb[x.batch], S, F), x.pad, S, kc0, kc1, F);
             return kc1 - kc0;
         };
         for (int k = 0; k < 2; k++) {
@@ -796,26 +801,27 @@ nao_status split_lists(nao_grid *g) {
 // slice budget, per-batch slice offsets and exponent arrays, work lists.
 nao_status split_setup(nao_grid *g) {
     if (g->split_ready) return NAO_OK;
-    const int S = g->opt.split_slices;
-    if (S > NAO_SPLIT_MAX_SLICES)
-        return fail(NAO_ERR_UNSUPPORTED, "split path supports at most " + std::to_string(NAO_SPLIT_MAX_SLICES) + " slices");
+    const int S = g->opt.split_slices, F = g->opt.split_digits;
+    if (S > (F == NAO_DIGITS_E4M3 ? NAO_SPLIT_MAX_SLICES_E4M3 : NAO_SPLIT_MAX_SLICES))
+        return fail(NAO_ERR_UNSUPPORTED, "too many slices for the split path's tensor memory");
+    const int C = nao_chunk_cols(F);
     for (int64_t b = 0; b < g->n_batches; b++) {
         const int64_t Ppad = (g->Pb[b] + NAO_PPAD - 1) / NAO_PPAD * NAO_PPAD;
-        const int64_t N64 = (g->Nb[b] + 63) / 64 * 64;
-        // every slice-group sum must stay below 2^24: K (g+1) 2^10 with g + 1 <= S. The H
+        const int64_t N64 = (g->Nb[b] + C - 1) / C * C;
+        // every slice-group sum must stay below 2^24: K S 2^(2 bits - 2) < 2^24. The H
         // contraction (K = 4 Ppad) splits K into segments where needed; the density's K is the
-        // batch's basis (N rounded up to 64), one accumulation per function tile
+        // batch's basis (N rounded up to a K chunk), one accumulation per function tile
         if (Ppad > NAO_SPLIT_MAX_PPAD)
             return fail(NAO_ERR_UNSUPPORTED, "batch too large for the split path (points " + std::to_string(g->Pb[b]) +
                                                  ", at most " + std::to_string(NAO_SPLIT_MAX_PPAD) + ")");
-        if (N64 * S >= 16384)
+        if (N64 * S >= nao_exact_ks(F))
             return fail(NAO_ERR_UNSUPPORTED, "batch too large for exact slice sums (basis " + std::to_string(g->Nb[b]) +
                                                  ", slices " + std::to_string(S) + ")");
     }
     NAO_CUDA(split_configure());
     g->split_chunks.clear();  // a failed earlier set-up may have planned part of them
-    // slices take S x 2 bytes per evaluated FP64 value (8 bytes): three times the evaluation
-    // budget holds one evaluation chunk's slices at up to 12 slices
+    // slices take S x 2 (bf16) or S (e4m3) bytes per evaluated FP64 value (8 bytes): three times
+    // the evaluation budget holds one evaluation chunk's slices at up to 12 bf16 or 16 e4m3 slices
     const int64_t budget =
         std::max<int64_t>(3 * (g->opt.scratch_bytes > 0 ? g->opt.scratch_bytes : kDefaultScratch), int64_t(1) << 20);
     std::vector<int64_t> off_h(g->n_batches, 0), off_n(g->n_batches, 0);
@@ -827,7 +833,7 @@ nao_status split_setup(nao_grid *g) {
         int64_t used = 0;
         for (int32_t b = c.b0; b < c.b1; b++) {
             const int P = g->Pb[b], N = g->Nb[b];
-            const SplitGeom G(P, N, S);
+            const SplitGeom G(P, N, S, 0, F);
             const int64_t need = N == 0 ? 0 : (int64_t)std::max(G.h_bytes(S), G.n_bytes(S));
             if (used + need > budget && b > cur.b0) {
                 cur.b1 = b;
@@ -840,16 +846,16 @@ nao_status split_setup(nao_grid *g) {
             off_n[b] = used;
             used += need;
             max_used = std::max(max_used, used);
-            g->split_tn[b] = default_tn(S, N);
+            g->split_tn[b] = default_tn(S, F);
             if (N > 0) {
                 cur.max_rt = std::max<int32_t>(cur.max_rt, G.h_slice_tiles());
                 cur.max_qt = std::max<int32_t>(cur.max_qt, G.n_qt);
                 // list capacity: the larger of the two widths' item counts
                 int64_t best_h = 0;
                 for (int TN : {48, 32}) {
-                    if (TN == 48 && S > 10) continue;
+                    if (TN == 48 && nao_split_tn(S, F) != 48) continue;
                     std::vector<HWork> tmp;
-                    nao_split_h_items(b, P, N, TN, S, tmp);
+                    nao_split_h_items(b, P, N, TN, S, tmp, F);
                     best_h = std::max(best_h, (int64_t)tmp.size());
                 }
                 cap_h += best_h;
@@ -874,7 +880,8 @@ nao_status split_setup(nao_grid *g) {
     g->cap_split_hw = cap_h;
     g->cap_split_nw = cap_n;
     g->split_S = S;
-    g->split_tuned = S > 10 || !g->opt.autotune;  // only one width exists, or tuning is off
+    g->split_F = F;
+    g->split_tuned = nao_split_tn(S, F) != 48 || !g->opt.autotune;  // only one width exists, or tuning is off
     if ((st = split_lists(g))) return st;
     g->split_ready = true;
     return NAO_OK;
@@ -926,7 +933,7 @@ nao_status split_tune(nao_grid *g, uint32_t terms, cudaStream_t st) {
         cudaError_t ce = launch_eval(s, c.b0, c.b1, NAO_FP64, true, g->d_scratch, st);
         if (ce == cudaSuccess)
             ce = launch_slice_h(s, c.b0, c.b1, c.max_rt, g->d_scratch, terms, g->d_slices, g->d_sl_off_h, g->d_expo_h,
-                                g->d_neg16, S, st);
+                                g->d_neg16, S, g->split_F, st);
         if (ce != cudaSuccess) { rs = cuda_fail(ce, "autotune evaluation"); break; }
         for (int k = 0; k < kBuckets && rs == NAO_OK; k++) {
             if (choice[k] || !total[k]) continue;
@@ -962,7 +969,7 @@ nao_status split_tune(nao_grid *g, uint32_t terms, cudaStream_t st) {
                     ce = cudaEventRecord(e0, st);
                     if (ce == cudaSuccess)
                         ce = launch_h_tc(s, g->d_tune_hw, 0, (int32_t)items.size(), g->d_slices, g->d_sl_off_h,
-                                         g->d_expo_h, g->d_neg16, S, TN, 0, g->d_err, st);
+                                         g->d_expo_h, g->d_neg16, S, g->split_F, TN, 0, g->d_err, st);
                     if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
                     if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
                     float t = 0.0f;
@@ -1040,13 +1047,13 @@ nao_status enqueue_h(nao_grid *g, uint32_t terms, nao_precision prec, cudaStream
             NAO_CUDA(timed(g, NAO_K_EVAL_GRAD, st, [&] { return launch_eval(s, c.b0, c.b1, NAO_FP64, true, g->d_scratch, st); }));
             NAO_CUDA(timed(g, NAO_K_SLICE, st, [&] {
                 return launch_slice_h(s, c.b0, c.b1, c.max_rt, g->d_scratch, terms, g->d_slices, g->d_sl_off_h,
-                                      g->d_expo_h, g->d_neg16, S, st);
+                                      g->d_expo_h, g->d_neg16, S, g->split_F, st);
             }));
             for (int k = 0; k < 2; k++)
                 if (c.hw1[k] > c.hw0[k])
                 NAO_CUDA(timed(g, NAO_K_H_SPLIT, st, [&] {
                     return launch_h_tc(s, g->d_split_hw, c.hw0[k], c.hw1[k] - c.hw0[k], g->d_slices, g->d_sl_off_h,
-                                       g->d_expo_h, g->d_neg16, S, k == 0 ? 48 : 32, 1, g->d_err, st);
+                                       g->d_expo_h, g->d_neg16, S, g->split_F, k == 0 ? 48 : 32, 1, g->d_err, st);
                 }));
         }
     } else {
@@ -1072,13 +1079,13 @@ nao_status enqueue_n(nao_grid *g, nao_precision prec, bool want_ne, bool grad, c
             }));
             NAO_CUDA(timed(g, NAO_K_SLICE_N, st, [&] {
                 return launch_slice_n(s, c.b0, c.b1, c.max_qt, c.max_rt, g->d_scratch, g->d_slices, g->d_sl_off_n,
-                                      g->d_expo_q, g->d_expo_b, g->d_split_tn, S, grad, st);
+                                      g->d_expo_q, g->d_expo_b, g->d_split_tn, S, g->split_F, grad, st);
             }));
             for (int k = 0; k < 2; k++)
                 if (c.nw1[k] > c.nw0[k])
                 NAO_CUDA(timed(g, NAO_K_N_SPLIT, st, [&] {
                     return launch_n_tc(s, g->d_split_nw, c.nw0[k], c.nw1[k] - c.nw0[k], g->d_slices, g->d_sl_off_n,
-                                       g->d_expo_q, g->d_expo_b, g->d_scratch, S, k == 0 ? 48 : 32, grad, g->d_err,
+                                       g->d_expo_q, g->d_expo_b, g->d_scratch, S, g->split_F, k == 0 ? 48 : 32, grad, g->d_err,
                                        st);
                 }));
         }
@@ -1207,6 +1214,7 @@ nao_status nao_default_options(nao_options *o) {
     o->scratch_bytes = 0;
     o->capture_graph = 0;
     o->autotune = 1;
+    o->split_digits = NAO_DIGITS_BF16;
     return NAO_OK;
 }
 

@@ -15,7 +15,8 @@
 #define NAO_TILE 64          // tile edge of the SIMT contractions (basis functions and points)
 #define NAO_PPAD 16          // batch points are padded to a multiple of this in scratch
 #define NAO_MAX_BATCH 1024   // largest accepted max_batch_points
-#define NAO_SPLIT_MAX_SLICES 12  // tensor-memory budget: S groups x TN FP32 columns <= 512 columns
+#define NAO_SPLIT_MAX_SLICES 12  // bf16 digits: S groups x TN FP32 columns <= 512 tensor-memory columns
+#define NAO_SPLIT_MAX_SLICES_E4M3 16  // e4m3 digits (TN = 32): 16 x 32 = 512 columns
 #define NAO_SPLIT_MAX_PPAD 512   // split path: padded batch points (the slicers' shared-memory column tables)
 
 // One radial function instance relevant to a batch: atom, radial function, position of
@@ -142,28 +143,47 @@ __device__ __forceinline__ double *gn_at(const DevSystem &s, int m, int p, int c
 }
 #endif
 
+// Digit formats of the split path (options.split_digits):
+//   NAO_DIGITS_BF16: balanced base-64 digits, |d| <= 32, stored as bf16, tcgen05 kind::f16 MMAs
+//                    with K = 16 per instruction;
+//   NAO_DIGITS_E4M3: balanced base-32 digits, |d| <= 16 (every such integer is exact in e4m3),
+//                    stored as e4m3 bytes, kind::f8f6f4 MMAs with K = 32 at twice the bf16 rate.
+// Either way a 128-byte operand row holds one K chunk (64 bf16 or 128 e4m3 columns) and an MMA
+// K step is 32 bytes, so the shared-memory descriptors, the 128-byte swizzle and the four K
+// steps per chunk are the same; a digit product is at most 2^(2 bits - 2) (2^10 or 2^8).
+#define NAO_DIGITS_BF16 0
+#define NAO_DIGITS_E4M3 1
+__host__ __device__ constexpr int nao_digit_bits(int F) { return F == NAO_DIGITS_E4M3 ? 5 : 6; }
+__host__ __device__ constexpr int nao_chunk_cols(int F) { return F == NAO_DIGITS_E4M3 ? 128 : 64; }
+__host__ __device__ constexpr int nao_kstep_cols(int F) { return F == NAO_DIGITS_E4M3 ? 32 : 16; }
+// Largest K of one exact accumulation of S slice groups: K S 2^(2 bits - 2) < 2^24.
+__host__ __device__ constexpr int nao_exact_ks(int F) { return F == NAO_DIGITS_E4M3 ? 65536 : 16384; }
+
 // Geometry of one batch's operand slices on the split path (shared by host and device code).
-// Every operand is stored row-contiguous per (slice, K chunk of 64): rows x 128 B with the
-// 128-byte swizzle inside 8-row atoms, rows rounded up to 16 only. An MMA tile (128 rows for
-// A, TN for B) is a plain byte range; the last tile of an operand is copied short and its
-// remaining shared-memory rows keep stale data, which only reaches output rows and columns
-// beyond N (or P) that the epilogues discard. B tiles are TN = nao_split_tn(S) rows.
+// Every operand is stored row-contiguous per (slice, K chunk): rows x 128 B with the 128-byte
+// swizzle inside 8-row atoms, rows rounded up to 16 only. An MMA tile (128 rows for A, TN for B)
+// is a plain byte range; the last tile of an operand is copied short and its remaining
+// shared-memory rows keep stale data, which only reaches output rows and columns beyond N (or P)
+// that the epilogues discard. B tiles are TN = nao_split_tn(S, F) rows.
 // H: one digit set, rows = basis functions, K = the 4 Ppad weighted columns reordered so that
-//    negative-weight columns come first, padded to a multiple of 16 (B negated on those steps).
+//    negative-weight columns come first, padded to a whole MMA K step (B negated on those steps).
 // Density: A rows = points, K = basis; B rows = basis (P' rows), K = basis.
 // MMA N (rows of a B tile) of the split path with S slices: each of the S slice groups holds
 // its own TN FP32 accumulator columns of the 512 tensor-memory columns.
-__host__ __device__ constexpr int nao_split_tn(int S) { return S <= 10 ? 48 : 32; }
+__host__ __device__ constexpr int nao_split_tn(int S, int F = NAO_DIGITS_BF16) {
+    return F == NAO_DIGITS_BF16 && S <= 10 ? 48 : 32;
+}
 
 struct SplitGeom {
     int n_kc, R16;               // H: K chunks, stored rows
     int n_kcN, P16, n_qt, n_jtN; // density: K chunks, stored A rows, 128-point tiles, TN-row B tiles
-    __host__ __device__ SplitGeom(int P, int N, int S, int TN = 0) {
-        if (TN == 0) TN = nao_split_tn(S);
+    __host__ __device__ SplitGeom(int P, int N, int S, int TN = 0, int F = NAO_DIGITS_BF16) {
+        if (TN == 0) TN = nao_split_tn(S, F);
+        const int C = nao_chunk_cols(F), ks = nao_kstep_cols(F);
         const int Ppad = (P + NAO_PPAD - 1) / NAO_PPAD * NAO_PPAD;
-        n_kc = (4 * Ppad + 16 + 63) / 64;
+        n_kc = (4 * Ppad + ks + C - 1) / C;
         R16 = (N + 15) / 16 * 16;
-        n_kcN = (N + 63) / 64;
+        n_kcN = (N + C - 1) / C;
         P16 = (P + 15) / 16 * 16;
         n_qt = (P + 127) / 128;
         n_jtN = (N + TN - 1) / TN;
@@ -184,26 +204,30 @@ struct HWork {  // one upper-triangular tile pair of one batch's h[B] (Eq. batch
 };
 
 // K segments of the split H contraction. A slice-order group's FP32 accumulator sums K products
-// of at most 2^10 for each of its g + 1 <= S slice pairs; it stays an exact integer while
-// K (g + 1) 2^10 < 2^24, i.e. K S < 2^14. A batch whose 4 Ppad weighted columns meet that bound
-// is one accumulation; a larger batch is accumulated in segments of nao_split_kc_seg(S) chunks
-// of 64 columns (64 kc_seg S < 2^14), each recombined and scattered into H on its own (H is a
-// sum over K, so the segments' FP64 partial sums simply add; Eq. H_decomp).
-__host__ __device__ constexpr int nao_split_kc_seg(int S) { return 255 / S; }
-__host__ __device__ inline int nao_split_h_nseg(int P, int S) {
+// of at most 2^(2 bits - 2) for each of its g + 1 <= S slice pairs; it stays an exact integer
+// while K S 2^(2 bits - 2) < 2^24 (nao_exact_ks). A batch whose 4 Ppad weighted columns meet that
+// bound is one accumulation; a larger batch is accumulated in segments of nao_split_kc_seg(S, F)
+// K chunks, each recombined and scattered into H on its own (H is a sum over K, so the segments'
+// FP64 partial sums simply add; Eq. H_decomp).
+__host__ __device__ constexpr int nao_split_kc_seg(int S, int F = NAO_DIGITS_BF16) {
+    return (nao_exact_ks(F) - 1) / (nao_chunk_cols(F) * S);
+}
+__host__ __device__ inline int nao_split_h_nseg(int P, int S, int F = NAO_DIGITS_BF16) {
     const int Ppad = (P + NAO_PPAD - 1) / NAO_PPAD * NAO_PPAD;
-    if (4 * Ppad * S < 16384) return 1;
-    const int n_kc = (4 * Ppad + 16 + 63) / 64, kcs = nao_split_kc_seg(S);
+    if (4 * Ppad * S < nao_exact_ks(F)) return 1;
+    const int C = nao_chunk_cols(F);
+    const int n_kc = (4 * Ppad + nao_kstep_cols(F) + C - 1) / C, kcs = nao_split_kc_seg(S, F);
     return (n_kc + kcs - 1) / kcs;
 }
 // K chunks [kc0, kc1) of segment seg of a batch with n_kc chunks.
-__host__ __device__ inline void nao_split_h_seg_range(int n_kc, int nseg, int seg, int S, int &kc0, int &kc1) {
+__host__ __device__ inline void nao_split_h_seg_range(int n_kc, int nseg, int seg, int S, int &kc0, int &kc1,
+                                                      int F = NAO_DIGITS_BF16) {
     if (nseg <= 1) {
         kc0 = 0;
         kc1 = n_kc;
         return;
     }
-    const int kcs = nao_split_kc_seg(S);
+    const int kcs = nao_split_kc_seg(S, F);
     kc0 = seg * kcs;
     kc1 = kc0 + kcs < n_kc ? kc0 + kcs : n_kc;
 }
@@ -211,8 +235,9 @@ __host__ __device__ inline void nao_split_h_seg_range(int n_kc, int nseg, int se
 // Split H work items of one batch (P points, N functions) for tile width TN and S slices: per
 // 128-row tile I, the TN-column tiles J >= floor(128 I / TN) (those reaching the upper
 // triangle), once per K segment.
-inline void nao_split_h_items(int32_t b, int P, int N, int TN, int S, std::vector<HWork> &out) {
-    const int nI = (N + 127) / 128, nJ = (N + TN - 1) / TN, nseg = nao_split_h_nseg(P, S);
+inline void nao_split_h_items(int32_t b, int P, int N, int TN, int S, std::vector<HWork> &out,
+                              int F = NAO_DIGITS_BF16) {
+    const int nI = (N + 127) / 128, nJ = (N + TN - 1) / TN, nseg = nao_split_h_nseg(P, S, F);
     for (int I = 0; I < nI; I++)
         for (int J = (I * 128) / TN; J < nJ; J++)
             for (int q = 0; q < nseg; q++) out.push_back({b, I, J, q});
@@ -275,7 +300,7 @@ struct nao_grid {
         int32_t nw0[2], nw1[2];
     };
     bool split_ready = false;
-    int split_S = 0;
+    int split_S = 0, split_F = 0;  // slices and digit format of the split set-up
     std::vector<SplitChunk> split_chunks;
     // density Hessian (FP64): chunks of batches whose 10-row evaluation fits the scratch, with
     // their density work ranges, and the per-batch scratch offsets of that layout
@@ -369,25 +394,26 @@ cudaError_t launch_set_pointers(double **dst, void *const *src, int32_t n, cudaS
 cudaError_t launch_zero_n(const DevSystem &s, const DWork *work, int32_t n_work, bool grad, cudaStream_t st);
 
 // ---- split path (split_tc.cu) ------------------------------------------------------------
-size_t split_smem_bytes(int S);
+// F: digit format (NAO_DIGITS_BF16, NAO_DIGITS_E4M3) in every split launcher below
+size_t split_smem_bytes(int S, int F);
 cudaError_t split_configure();
 cudaError_t launch_slice_h(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_rt, const double *scratch,
                            uint32_t terms, uint8_t *slices, const int64_t *sl_off, int32_t *expo, int32_t *neg16, int S,
-                           cudaStream_t st);
-// tn: tile width 48 (S <= 10 only) or 32; scatter = 0 skips the H scatter (autotuner timing).
+                           int F, cudaStream_t st);
+// tn: tile width 48 (bf16 digits, S <= 10 only) or 32; scatter = 0 skips the H scatter (autotuner timing).
 // work: items (batch, 128-row tile I, TN-column tile J) of nao_split_h_items; a persistent kernel
 // (one CTA per SM) walks them
 cudaError_t launch_h_tc(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
-                        const int64_t *sl_off, const int32_t *expo, const int32_t *neg16, int S, int tn, int scatter,
-                        int32_t *err, cudaStream_t st);
+                        const int64_t *sl_off, const int32_t *expo, const int32_t *neg16, int S, int F, int tn,
+                        int scatter, int32_t *err, cudaStream_t st);
 // tn_b: per-batch tile width (the P' tiles of the density follow it). grad: the scratch rows hold
 // [phi | grad phi] (4 Ppad) and P' = P over all tiles (density gradient)
 cudaError_t launch_slice_n(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_qt, int32_t max_rt,
                            const double *scratch, uint8_t *slices, const int64_t *sl_off, const int32_t *expo_q,
-                           int32_t *expo_b, const int32_t *tn_b, int S, bool grad, cudaStream_t st);
+                           int32_t *expo_b, const int32_t *tn_b, int S, int F, bool grad, cudaStream_t st);
 cudaError_t launch_n_tc(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
                         const int64_t *sl_off, const int32_t *expo_q, const int32_t *expo_b, const double *scratch, int S,
-                        int tn, bool grad, int32_t *err, cudaStream_t st);
+                        int F, int tn, bool grad, int32_t *err, cudaStream_t st);
 // One bounded mbarrier wait that nothing completes (the wait of the tensor-core pipelines): it gives
 // up after max_cycles SM cycles and records NAO_ERR_TIMEOUT in err[0] (code 1 in err[1]).
 cudaError_t launch_wait_timeout_probe(long long max_cycles, int32_t *err, cudaStream_t st);

@@ -23,6 +23,7 @@
 // Density: A = Phi^T (rows = points, K = basis), B = P' (rows j, P'_ij = c_IJ P_ij for TN-function
 // tiles I <= J with c_II = 1, c_IJ = 2, else 0) so that T_qj = sum_i phi_qi P'_ij and
 // n_q = sum_j T_qj phi_qj; one per-batch exponent is used for P'.
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
 
@@ -40,16 +41,17 @@ constexpr long long kWaitCycles = 400000000LL;  // ~0.2 s at 2 GHz: bounded mbar
 // slicing kernels FP64-bound.
 using split_bits::abs_bits;
 
-// S balanced base-64 digits (most significant first in dig[0]) of X = round(x 2^(6S-e)),
-// |x 2^-e| < 1/2, as exact small-integer floats. From x's bits x = +-m 2^(E-1075) (53-bit m):
-// |X| = m 2^-sh with sh = 1075 + e - 6S - E, rounded half up when sh > 0, held as a 128-bit
-// integer (hi:lo; more than 64 bits only for S > 10). |X| is cut into 18-bit chunks (three
-// digits each), exact in FP32, and the digits are peeled off from the bottom in FP32:
-// q = rint(v / 64), d = v - 64 q in [-32, 32], v <- q, the carry q (0 or 1 after a chunk's
-// three digits) joining the next chunk. The top digit keeps whatever remains, which the bound
-// on |X| keeps in [-32, 32]. Subnormal x and e = -10000 give zeros.
-// |X| = round(|x| 2^(6S-e)) as a 128-bit integer (hi:lo) from the bits of x, and the sign of x.
-template <int S>
+// S balanced base-2^B digits (B = 6: base 64, |d| <= 32, bf16; B = 5: base 32, |d| <= 16, e4m3;
+// most significant first in dig[0]) of X = round(x 2^(BS-e)), |x 2^-e| < 1/2, as exact
+// small-integer floats. From x's bits x = +-m 2^(E-1075) (53-bit m): |X| = m 2^-sh with
+// sh = 1075 + e - BS - E, rounded half up when sh > 0, held as a 128-bit integer (hi:lo; more
+// than 64 bits only for BS > 64). |X| is cut into chunks of D digits (3 x 6 = 18 or 4 x 5 = 20
+// bits; the fourth chunk takes the remaining 23 bits), exact in FP32, and the digits are peeled
+// off from the bottom in FP32: q = rint(v / 2^B), d = v - 2^B q in [-2^(B-1), 2^(B-1)], v <- q,
+// the carry q (0 or 1 after a chunk's digits) joining the next chunk. The top digit keeps
+// whatever remains, which the bound on |X| keeps in range. Subnormal x and e = -10000 give zeros.
+// |X| = round(|x| 2^(BS-e)) as a 128-bit integer (hi:lo) from the bits of x, and the sign of x.
+template <int S, int B>
 __device__ __forceinline__ void digit_integer(double x, int e, unsigned long long &lo, unsigned long long &hi,
                                               float &sgn) {
     const long long bits = __double_as_longlong(x);
@@ -58,11 +60,11 @@ __device__ __forceinline__ void digit_integer(double x, int e, unsigned long lon
     hi = 0;
     if (eb != 0 && e > -10000) {
         const unsigned long long m = ((unsigned long long)bits & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
-        const int sh = 1075 + e - 6 * S - eb;
+        const int sh = 1075 + e - B * S - eb;
         if (sh > 0) {
             lo = sh >= 63 ? 0ULL : (m + (1ULL << (sh - 1))) >> sh;
         } else {
-            const int k = -sh;  // <= 6 for S <= 10, <= 18 for S = 12
+            const int k = -sh;  // <= B S - 54: 18 for 12 bf16 slices, 26 for 16 e4m3 slices
             lo = m << k;
             hi = k > 0 ? m >> (64 - k) : 0ULL;
         }
@@ -70,43 +72,48 @@ __device__ __forceinline__ void digit_integer(double x, int e, unsigned long lon
     sgn = bits < 0 ? -1.0f : 1.0f;
 }
 
-// Chunk c (c = 0, 1, 2: 18 bits; c = 3: the 23 bits from bit 54) of |X| = (hi:lo).
+// Chunk c of |X| = (hi:lo): c = 0, 1, 2 the CB-bit fields (CB = 3 x 6 or 4 x 5 bits), c = 3 the
+// 23 bits from bit 3 CB.
+template <int B>
 __device__ __forceinline__ uint32_t digit_chunk(unsigned long long lo, unsigned long long hi, int c) {
-    return c == 0 ? (uint32_t)(lo & 0x3FFFFULL)
-         : c == 1 ? (uint32_t)((lo >> 18) & 0x3FFFFULL)
-         : c == 2 ? (uint32_t)((lo >> 36) & 0x3FFFFULL)
-                  : (uint32_t)(((lo >> 54) | (hi << 10)) & 0x7FFFFFULL);
+    constexpr int CB = B == 6 ? 18 : 20;
+    constexpr unsigned long long M = (1ULL << CB) - 1;
+    return c == 0 ? (uint32_t)(lo & M)
+         : c == 1 ? (uint32_t)((lo >> CB) & M)
+         : c == 2 ? (uint32_t)((lo >> (2 * CB)) & M)
+                  : (uint32_t)(((lo >> (3 * CB)) | (hi << (64 - 3 * CB))) & 0x7FFFFFULL);
 }
 
 // The S digits of two values x0, x1 at once (.x and .y of dig[s]) with packed FP32x2 arithmetic.
-// The sign is carried in the running value: v starts as sgn |X| mod 2^18 (sgn (2^23 + u) - sgn 2^23,
-// one packed FMA, exact), every later chunk enters as + sgn u 2^(18c) at its digit position, and
-// the peeling q = rint(v / 64), d = v - 64 q works on signed v as well: rint is odd-symmetric, so
+// The sign is carried in the running value: v starts as sgn (|X| mod 2^CB) (sgn (2^23 + u) - sgn 2^23,
+// one packed FMA, exact), every later chunk enters as + sgn u at its digit position, and the
+// peeling q = rint(v / 2^B), d = v - 2^B q works on signed v as well: rint is odd-symmetric, so
 // the digits are those of |X| times the sign.
-template <int S>
+template <int S, int B>
 __device__ __forceinline__ void digits2(double x0, double x1, int e, float2 (&dig)[S]) {
+    constexpr int D = B == 6 ? 3 : 4;  // digits per chunk
     unsigned long long lo0, hi0, lo1, hi1;
     float s0, s1;
-    digit_integer<S>(x0, e, lo0, hi0, s0);
-    digit_integer<S>(x1, e, lo1, hi1, s1);
+    digit_integer<S, B>(x0, e, lo0, hi0, s0);
+    digit_integer<S, B>(x1, e, lo1, hi1, s1);
     const float2 sgn = make_float2(s0, s1), nb = make_float2(-8388608.0f * s0, -8388608.0f * s1);
-    const float2 inv64 = make_float2(0.015625f, 0.015625f), big = make_float2(12582912.0f, 12582912.0f);
-    const float2 nbig = make_float2(-12582912.0f, -12582912.0f), m64 = make_float2(-64.0f, -64.0f);
+    const float2 inv = make_float2(1.0f / (1 << B), 1.0f / (1 << B)), big = make_float2(12582912.0f, 12582912.0f);
+    const float2 nbig = make_float2(-12582912.0f, -12582912.0f), mb = make_float2(-(float)(1 << B), -(float)(1 << B));
     auto chunk = [&](int c) {  // sgn u, u < 2^23, exactly
-        const float2 u = make_float2(__int_as_float(0x4B000000 | (int)digit_chunk(lo0, hi0, c)),
-                                     __int_as_float(0x4B000000 | (int)digit_chunk(lo1, hi1, c)));
+        const float2 u = make_float2(__int_as_float(0x4B000000 | (int)digit_chunk<B>(lo0, hi0, c)),
+                                     __int_as_float(0x4B000000 | (int)digit_chunk<B>(lo1, hi1, c)));
         return __ffma2_rn(sgn, u, nb);
     };
     float2 v = chunk(0);
 #pragma unroll
     for (int s = S - 1; s >= 0; s--) {
         const int t = S - 1 - s;  // digits already taken
-        if (t > 0 && t % 3 == 0) v = __fadd2_rn(v, chunk(t / 3));
+        if (t > 0 && t % D == 0) v = __fadd2_rn(v, chunk(t / D));
         if (s == 0) {
             dig[0] = v;
         } else {
-            const float2 q = __fadd2_rn(__ffma2_rn(v, inv64, big), nbig);  // rint(v / 64)
-            dig[s] = __ffma2_rn(q, m64, v);
+            const float2 q = __fadd2_rn(__ffma2_rn(v, inv, big), nbig);  // rint(v / 2^B)
+            dig[s] = __ffma2_rn(q, mb, v);
             v = q;
         }
     }
@@ -115,6 +122,33 @@ __device__ __forceinline__ void digits2(double x0, double x1, int e, float2 (&di
 // bf16 bit patterns of two small integers held exactly in floats (their low halves are zero).
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
     return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
+}
+
+// e4m3 bytes of four integers |d| <= 16 held in floats (each exact in e4m3), a at the lowest
+// address. cvt...e4m3x2 puts its first source in the upper byte of the pair.
+__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
+    unsigned short lo, hi;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(b), "f"(a));
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(d), "f"(c));
+    return (uint32_t)lo | ((uint32_t)hi << 16);
+}
+
+// Digits of the 128-byte row segment a lane owns in one K chunk: values x[0..LC-1] of its LC
+// consecutive columns (2 for bf16, 4 for e4m3), packed per slice into one 32-bit word.
+template <int S, int F>
+__device__ __forceinline__ void lane_digit_words(const double *x, int e, uint32_t (&w)[S]) {
+    constexpr int B = nao_digit_bits(F);
+    float2 d0[S];
+    digits2<S, B>(x[0], x[1], e, d0);
+    if constexpr (F == NAO_DIGITS_BF16) {
+#pragma unroll
+        for (int sl = 0; sl < S; sl++) w[sl] = pack_bf16x2(d0[sl].x, d0[sl].y);
+    } else {
+        float2 d1[S];
+        digits2<S, B>(x[2], x[3], e, d1);
+#pragma unroll
+        for (int sl = 0; sl < S; sl++) w[sl] = pack_e4m3x4(d0[sl].x, d0[sl].y, d1[sl].x, d1[sl].y);
+    }
 }
 
 // 2^E as an FP64 (0 below the normal range).
@@ -127,13 +161,14 @@ __device__ __forceinline__ double pow2(int E) {
 
 // ----------------------------------------------------------------------------------------
 // Hamiltonian slicing: one CTA per (batch, 64-row tile of basis functions). Columns are
-// reordered: the negative-weight ones (v < 0 on the potential part) first, padded to a
-// multiple of 16, then the rest, so that B = A and the sign is applied per 16-column K step.
+// reordered: the negative-weight ones (v < 0 on the potential part) first, padded to a whole
+// MMA K step (16 bf16 or 32 e4m3 columns), then the rest, so that B = A and the sign is applied
+// per K step.
 // One warp per row: the row's exponent (a pass over the row), then its digits (a second pass,
 // served from L2: the slices are written with evict-first stores so that they do not push the
 // rows out).
 // ----------------------------------------------------------------------------------------
-template <int S>
+template <int S, int F>
 __global__ void __launch_bounds__(256, S <= 10 ? 5 : 4) slice_h_kernel(DevSystem s, int32_t b0, const double *__restrict__ scratch,
                                                         uint32_t terms, uint8_t *__restrict__ slices,
                                                         const int64_t *__restrict__ sl_off, int32_t *__restrict__ expo,
@@ -141,16 +176,17 @@ __global__ void __launch_bounds__(256, S <= 10 ? 5 : 4) slice_h_kernel(DevSystem
     __shared__ double sd[4 * NAO_SPLIT_MAX_PPAD];
     __shared__ int sd_eb[4 * NAO_SPLIT_MAX_PPAD];    // biased exponent of sd (0: zero weight)
     __shared__ float sd_m[4 * NAO_SPLIT_MAX_PPAD];   // significand of sd in [1, 2), truncated
-    __shared__ short src[4 * NAO_SPLIT_MAX_PPAD + 64];
+    __shared__ short src[4 * NAO_SPLIT_MAX_PPAD + 128];
     __shared__ unsigned char negf[4 * NAO_SPLIT_MAX_PPAD];
     __shared__ int wsum[8];
     const int b = b0 + blockIdx.x, rt = blockIdx.y, m = s.sys.bmol[b];
     const int p0 = s.batch_off[b], P = s.batch_off[b + 1] - p0;
     const int Ppad = (P + NAO_PPAD - 1) & ~(NAO_PPAD - 1);
     const int N = s.rel_off[b + 1] - s.rel_off[b];
-    const SplitGeom G(P, N, S);
+    constexpr int C = nao_chunk_cols(F), KS = nao_kstep_cols(F), LC = C / 32;  // columns per lane
+    const SplitGeom G(P, N, S, 0, F);
     if (N == 0 || rt >= G.h_slice_tiles()) return;
-    const int K = 4 * Ppad, Kp = 64 * G.n_kc;
+    const int K = 4 * Ppad, Kp = C * G.n_kc;
     const double *E = scratch + s.scr_off[b];
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         const int c = k / Ppad, q = k - c * Ppad;
@@ -183,13 +219,13 @@ __global__ void __launch_bounds__(256, S <= 10 ? 5 : 4) slice_h_kernel(DevSystem
         total += wsum[w];
     }
     before += incl - cnt;
-    const int negpad = (total + 15) & ~15;
+    const int negpad = (total + KS - 1) / KS * KS;  // a whole MMA K step
     for (int k = kb; k < ke; k++) {
         const int pos = negf[k] ? before : negpad + k - before;
         before += negf[k];
         src[pos] = (short)k;
     }
-    if (rt == 0 && threadIdx.x == 0) neg16[b] = negpad / 16;
+    if (rt == 0 && threadIdx.x == 0) neg16[b] = negpad / KS;  // negated K steps
     __syncthreads();
     uint8_t *base = slices + sl_off[b];
     for (int lr = warp; lr < 64; lr += 8) {
@@ -202,18 +238,20 @@ __global__ void __launch_bounds__(256, S <= 10 ? 5 : 4) slice_h_kernel(DevSystem
         mk = __reduce_max_sync(0xffffffffu, mk);
         const int e = r < N ? split_bits::h_row_exponent(mk) : -10000;
         if (lane == 0 && r < N) expo[s.rel_off[b] + r] = e;
-        // two consecutive K columns per lane: a warp writes one 128-byte row segment per slice
+        // LC consecutive K columns per lane: a warp writes one 128-byte row segment per slice
         for (int kc = 0; kc < G.n_kc; kc++) {
-            const int k0 = 64 * kc + 2 * lane;
-            const int k0a = src[k0], k0b = src[k0 + 1];
-            const double xa = (k0a >= 0 && e > -10000) ? __ldcs(row + k0a) * sd[k0a] : 0.0;
-            const double xb = (k0b >= 0 && e > -10000) ? __ldcs(row + k0b) * sd[k0b] : 0.0;
-            float2 dg[S];
-            digits2<S>(xa, xb, e, dg);
-            const uint32_t off = tc::sw128_offset((uint32_t)r, (uint32_t)(2 * lane));
+            const int k0 = C * kc + LC * lane;
+            double x[LC];
 #pragma unroll
-            for (int sl = 0; sl < S; sl++)
-                __stcs(reinterpret_cast<unsigned int *>(base + G.h_block(sl, kc) + off), pack_bf16x2(dg[sl].x, dg[sl].y));
+            for (int c = 0; c < LC; c++) {
+                const int kk = src[k0 + c];
+                x[c] = (kk >= 0 && e > -10000) ? __ldcs(row + kk) * sd[kk] : 0.0;
+            }
+            uint32_t wd[S];
+            lane_digit_words<S, F>(x, e, wd);
+            const uint32_t off = tc::sw128_byte((uint32_t)r, (uint32_t)(4 * lane));
+#pragma unroll
+            for (int sl = 0; sl < S; sl++) __stcs(reinterpret_cast<unsigned int *>(base + G.h_block(sl, kc) + off), wd[sl]);
         }
     }
 }
@@ -221,26 +259,27 @@ __global__ void __launch_bounds__(256, S <= 10 ? 5 : 4) slice_h_kernel(DevSystem
 // ----------------------------------------------------------------------------------------
 // Density slicing.
 // Phi^T: one CTA (8 warps) per (batch, 32-point tile), the point exponents from the
-// evaluation. Per 64-function K chunk the CTA stages phi[i][q] (64 x 32, read along the points)
-// in shared memory and each warp writes its points' rows along K (two functions per lane, one
-// 128-byte row segment per slice). CTAs with blockIdx.y = 0 instead reduce the batch's
+// evaluation. Per K chunk (64 or 128 functions) the CTA stages phi[i][q] (chunk x 32, read along
+// the points) in shared memory and each warp writes its points' rows along K (2 or 4 functions
+// per lane, one 128-byte row segment per slice). CTAs with blockIdx.y = 0 instead reduce the batch's
 // exponent of P' (the upper-triangle tile pairs, read along rows of P).
 // ----------------------------------------------------------------------------------------
 __device__ __forceinline__ int tile_of(int i, int TN) { return i / TN; }
 
-template <int S>
+template <int S, int F>
 __global__ void __launch_bounds__(256) slice_nphi_kernel(DevSystem s, int32_t b0, const double *__restrict__ scratch,
                                                         uint8_t *__restrict__ slices, const int64_t *__restrict__ sl_off,
                                                         const int32_t *__restrict__ expo_q, int32_t *__restrict__ expo_b,
                                                         const int32_t *__restrict__ tn_b, int ld_mult, int full) {
-    __shared__ double t[32][65];
+    constexpr int C = nao_chunk_cols(F), LC = C / 32;
+    __shared__ double t[32][C + 1];
     __shared__ int red[8];
     const int b = b0 + blockIdx.x;
     const int p0 = s.batch_off[b], P = s.batch_off[b + 1] - p0;
     const int Ppad = (P + NAO_PPAD - 1) & ~(NAO_PPAD - 1);
     const int N = s.rel_off[b + 1] - s.rel_off[b];
     if (N == 0) return;
-    const SplitGeom G(P, N, S);
+    const SplitGeom G(P, N, S, 0, F);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (blockIdx.y == 0) {
         // max |P'_ij| over i <= j (P' is P on the diagonal tiles, 2 P off them, 0 below unless
@@ -279,8 +318,8 @@ __global__ void __launch_bounds__(256) slice_nphi_kernel(DevSystem s, int32_t b0
     uint8_t *base = slices + sl_off[b];
     for (int kc = 0; kc < G.n_kcN; kc++) {
 #pragma unroll
-        for (int h = 0; h < 8; h++) {
-            const int i = kc * 64 + warp + 8 * h;
+        for (int h = 0; h < C / 8; h++) {
+            const int i = kc * C + warp + 8 * h;
             t[lane][warp + 8 * h] = (i < N && qin) ? E[(int64_t)i * ld + q0 + lane] : 0.0;
         }
         __syncthreads();
@@ -288,12 +327,14 @@ __global__ void __launch_bounds__(256) slice_nphi_kernel(DevSystem s, int32_t b0
         for (int h = 0; h < 4; h++) {
             const int ql = warp * 4 + h, q = q0 + ql;
             if (q >= G.P16) break;
-            float2 dg[S];
-            digits2<S>(t[ql][2 * lane], t[ql][2 * lane + 1], eq[h], dg);
-            const uint32_t off = tc::sw128_offset((uint32_t)q, (uint32_t)(2 * lane));
+            double x[LC];
 #pragma unroll
-            for (int sl = 0; sl < S; sl++)
-                *reinterpret_cast<uint32_t *>(base + G.nA_block(sl, kc) + off) = pack_bf16x2(dg[sl].x, dg[sl].y);
+            for (int c = 0; c < LC; c++) x[c] = t[ql][LC * lane + c];
+            uint32_t wd[S];
+            lane_digit_words<S, F>(x, eq[h], wd);
+            const uint32_t off = tc::sw128_byte((uint32_t)q, (uint32_t)(4 * lane));
+#pragma unroll
+            for (int sl = 0; sl < S; sl++) *reinterpret_cast<uint32_t *>(base + G.nA_block(sl, kc) + off) = wd[sl];
         }
         __syncthreads();
     }
@@ -301,9 +342,9 @@ __global__ void __launch_bounds__(256) slice_nphi_kernel(DevSystem s, int32_t b0
 
 // P'_ij = c_IJ P[rel_i][rel_j] over TN-function tiles I = i/TN <= J = j/TN (c_II = 1,
 // c_IJ = 2; every (i, j) with c = 1 when full), read from P's upper triangle, with the batch's
-// exponent from slice_nphi_kernel. One CTA per (batch, 16 rows j), one warp per row, two
+// exponent from slice_nphi_kernel. One CTA per (batch, 16 rows j), one warp per row, 2 or 4
 // functions i per lane (one 128-byte row segment per slice).
-template <int S>
+template <int S, int F>
 __global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, uint8_t *__restrict__ slices,
                                                       const int64_t *__restrict__ sl_off,
                                                       const int32_t *__restrict__ expo_b,
@@ -312,7 +353,8 @@ __global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, 
     const int P = s.batch_off[b + 1] - s.batch_off[b];
     const int N = s.rel_off[b + 1] - s.rel_off[b];
     if (N == 0) return;
-    const SplitGeom G(P, N, S);
+    constexpr int C = nao_chunk_cols(F), LC = C / 32;
+    const SplitGeom G(P, N, S, 0, F);
     const int j0 = blockIdx.y * 16;
     if (j0 >= G.R16) return;
     const int32_t *rel = s.rel_idx + s.rel_off[b];
@@ -326,10 +368,10 @@ __global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, 
         const int64_t gj = jin ? rel[j] : 0;
         const int tj = tile_of(j, TN);
         for (int kc = 0; kc < G.n_kcN; kc++) {
-            double xp[2];
+            double xp[LC];
 #pragma unroll
-            for (int hh = 0; hh < 2; hh++) {
-                const int i = 64 * kc + 2 * lane + hh;
+            for (int hh = 0; hh < LC; hh++) {
+                const int i = C * kc + LC * lane + hh;
                 double x = 0.0;
                 if (jin && i < N && (full || tile_of(i, TN) <= tj)) {
                     const int64_t gi = rel[i];
@@ -342,12 +384,11 @@ __global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, 
                 }
                 xp[hh] = x;
             }
-            float2 dg[S];
-            digits2<S>(xp[0], xp[1], e, dg);
-            const uint32_t off = tc::sw128_offset((uint32_t)j, (uint32_t)(2 * lane));
+            uint32_t wd[S];
+            lane_digit_words<S, F>(xp, e, wd);
+            const uint32_t off = tc::sw128_byte((uint32_t)j, (uint32_t)(4 * lane));
 #pragma unroll
-            for (int sl = 0; sl < S; sl++)
-                *reinterpret_cast<uint32_t *>(base + G.nB_block(S, sl, kc) + off) = pack_bf16x2(dg[sl].x, dg[sl].y);
+            for (int sl = 0; sl < S; sl++) *reinterpret_cast<uint32_t *>(base + G.nB_block(S, sl, kc) + off) = wd[sl];
         }
     }
 }
@@ -369,31 +410,37 @@ constexpr size_t kSmemOptin = 232448;  // shared memory a CTA may opt into on th
 constexpr size_t kStaticSmem = 2048;   // room for the CTA's static shared memory (the PPipe barriers)
 
 // A-ring slots: as many 16 KB A tiles as fit beside the two B sets (S tiles of TN rows each),
-// at most kMaxRing: 8 for S = 11, 12 (TN = 32), 6 for S = 10 (TN = 48). A deeper ring lets the
-// producer's copies run further ahead of the MMAs that wait for them.
-__host__ __device__ constexpr int ring_slots(int S) {
-    return (int)((kSmemOptin - kStaticSmem - 1024 - 2 * (size_t)S * nao_split_tn(S) * 128) / 16384) < kMaxRing
-               ? (int)((kSmemOptin - kStaticSmem - 1024 - 2 * (size_t)S * nao_split_tn(S) * 128) / 16384)
+// at most kMaxRing: 8 for 11-12 bf16 slices (TN = 32), 6 for 10 (TN = 48), 7 for 14 e4m3 slices.
+// A deeper ring lets the producer's copies run further ahead of the MMAs that wait for them.
+__host__ __device__ constexpr int ring_slots(int S, int F) {
+    return (int)((kSmemOptin - kStaticSmem - 1024 - 2 * (size_t)S * nao_split_tn(S, F) * 128) / 16384) < kMaxRing
+               ? (int)((kSmemOptin - kStaticSmem - 1024 - 2 * (size_t)S * nao_split_tn(S, F) * 128) / 16384)
                : kMaxRing;
 }
 
-__host__ __device__ constexpr size_t pipe_smem_bytes(int S) {
-    return (size_t)ring_slots(S) * 16384 + 2 * (size_t)S * nao_split_tn(S) * 128 + 1024;
+__host__ __device__ constexpr size_t pipe_smem_bytes(int S, int F) {
+    return (size_t)ring_slots(S, F) * 16384 + 2 * (size_t)S * nao_split_tn(S, F) * 128 + 1024;
 }
-static_assert(ring_slots(12) >= 4 && ring_slots(10) >= 4 && ring_slots(4) >= 4, "A ring too shallow");
-static_assert(pipe_smem_bytes(12) + kStaticSmem <= kSmemOptin && pipe_smem_bytes(10) + kStaticSmem <= kSmemOptin,
+static_assert(ring_slots(12, 0) >= 4 && ring_slots(10, 0) >= 4 && ring_slots(4, 0) >= 4 && ring_slots(16, 1) >= 4,
+              "A ring too shallow");
+static_assert(pipe_smem_bytes(12, 0) + kStaticSmem <= kSmemOptin && pipe_smem_bytes(10, 0) + kStaticSmem <= kSmemOptin &&
+                  pipe_smem_bytes(16, 1) + kStaticSmem <= kSmemOptin,
               "split pipeline exceeds shared memory");
 
-// Integer recombination of the S group accumulators for 16 columns of this thread's row:
-// value = hi 64^-8 + lo 64^-11 + lo2 64^-14 (in units of 2^(e_i + e_j)) with
-// hi = sum_{g<=6} M_g 64^(6-g), lo = sum_{7<=g<=9} M_g 64^(9-g), lo2 = sum_{g>=10} M_g 64^(12-g);
-// all exact in 64 bits (|M_g| < 2^24).
+// Integer recombination of the S group accumulators M_g (|M_g| < 2^24, exact) for 16 columns of
+// this thread's row, in units of 2^(e_i + e_j):
+//   bf16 (base 64): hi = sum_{g<=6} M_g 64^(6-g) [units 2^-48], lo = sum_{7<=g<=9} M_g 64^(9-g)
+//     [2^-66], lo2 = sum_{g>=10} M_g 64^(12-g) [2^-84] (S = 11, 12 only);
+//   e4m3 (base 32): hi = sum_{g<=7} M_g 32^(7-g) [units 2^-45], lo = sum_{g>=8} M_g 32^(15-g)
+//     [2^-85] (S <= 16); lo2 stays 0.
+// Every part is exact in 64 bits (below 2^60.1).
 struct Parts16 {
     long long hi[16], lo[16], lo2[16];
 };
 
-template <int TN>
+template <int TN, int F>
 __device__ __forceinline__ void combine16(uint32_t tm_row, int c0, int S, Parts16 &v) {
+    constexpr int B = nao_digit_bits(F), GH = F == NAO_DIGITS_E4M3 ? 7 : 6, GL = F == NAO_DIGITS_E4M3 ? 15 : 9;
 #pragma unroll
     for (int jj = 0; jj < 16; jj++) v.hi[jj] = v.lo[jj] = v.lo2[jj] = 0;
     // three groups' loads in flight per wait
@@ -407,8 +454,8 @@ __device__ __forceinline__ void combine16(uint32_t tm_row, int c0, int S, Parts1
         for (int d = 0; d < 3; d++) {
             const int g = g0 + d;
             if (g >= S) break;
-            const int part = g <= 6 ? 0 : (TN == 48 || g <= 9 ? 1 : 2);  // TN = 48: S <= 10, no lo2
-            const long long w = 1LL << (6 * (part == 0 ? 6 - g : (part == 1 ? 9 - g : 12 - g)));
+            const int part = g <= GH ? 0 : (g <= GL ? 1 : 2);
+            const long long w = 1LL << (B * (part == 0 ? GH - g : (part == 1 ? GL - g : 12 - g)));
 #pragma unroll
             for (int jj = 0; jj < 16; jj++) {
                 const long long m = (long long)__float2int_rn(__uint_as_float(r[d][jj]));
@@ -419,6 +466,56 @@ __device__ __forceinline__ void combine16(uint32_t tm_row, int c0, int S, Parts1
         }
     }
 }
+
+// An H element from its parts as one 64-bit integer v and a tier t, the value being
+// v 2^(e_i + e_j - h_unit<F>(t)):
+//   bf16: lo' = lo + round(lo2 / 2^18); t = 0 (|hi| < 2^44): hi 2^18 + lo' exactly (unit 66);
+//         t = 1: 4 hi + round(lo' / 2^16) (unit 50; |4 hi| >= 2^46, relative error <= 2^-47);
+//   e4m3: t = 0 (|hi| < 2^22): hi 2^40 + lo exactly (unit 85); t = 1 (|hi| < 2^40):
+//         hi 2^22 + round(lo / 2^18) (unit 67; relative error <= 2^-45); t = 2:
+//         4 hi + round(lo / 2^38) (unit 47; relative error <= 2^-43).
+// (hi is in units of 2^-45 and lo of 2^-85 throughout: hi 2^k in units of 2^-(45 + k).)
+template <int F>
+__device__ __forceinline__ long long h_int(long long hi, long long lo, long long lo2, int &t) {
+    if constexpr (F == NAO_DIGITS_BF16) {
+        const long long l = lo + ((lo2 + (1LL << 17)) >> 18);
+        if (hi > -(1LL << 44) && hi < (1LL << 44)) {
+            t = 0;
+            return (hi << 18) + l;
+        }
+        t = 1;
+        return (hi << 2) + ((l + (1LL << 15)) >> 16);
+    } else {
+        if (hi > -(1LL << 22) && hi < (1LL << 22)) {
+            t = 0;
+            return (hi << 40) + lo;
+        }
+        if (hi > -(1LL << 40) && hi < (1LL << 40)) {
+            t = 1;
+            return (hi << 22) + ((lo + (1LL << 17)) >> 18);
+        }
+        t = 2;
+        return (hi << 2) + ((lo + (1LL << 37)) >> 38);
+    }
+}
+template <int F>
+__device__ __forceinline__ int h_unit(int t) {
+    return F == NAO_DIGITS_BF16 ? (t == 0 ? 66 : 50) : (t == 0 ? 85 : (t == 1 ? 67 : 47));
+}
+// A density T element as one 64-bit integer in units of 2^(e_q + e_b - n_unit<F>): 4 hi +
+// round(lo' / 2^16) (bf16, unit 50) or 4 hi + round(lo / 2^38) (e4m3, unit 47); |4 hi| < 2^62.1,
+// rounded by at most half a unit.
+template <int F>
+__device__ __forceinline__ long long n_int(long long hi, long long lo, long long lo2) {
+    if constexpr (F == NAO_DIGITS_BF16) {
+        const long long l = lo + ((lo2 + (1LL << 17)) >> 18);
+        return (hi << 2) + ((l + (1LL << 15)) >> 16);
+    } else {
+        return (hi << 2) + ((lo + (1LL << 37)) >> 38);
+    }
+}
+template <int F>
+__host__ __device__ constexpr int n_unit() { return F == NAO_DIGITS_BF16 ? 50 : 47; }
 
 __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
     return reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
@@ -445,7 +542,7 @@ struct HItem {  // geometry of one H work item
     int n_kc, kc0, kc1, neg16, b, m, N, ti, tj;  // K chunks [kc0, kc1) of the item's segment
 };
 
-template <int TN>
+template <int TN, int F>
 __device__ __forceinline__ HItem h_item(const DevSystem &s, const HWork *work, int32_t w, const uint8_t *slices,
                                         const int64_t *sl_off, const int32_t *neg16, int S) {
     HItem h;
@@ -456,7 +553,7 @@ __device__ __forceinline__ HItem h_item(const DevSystem &s, const HWork *work, i
     h.m = s.sys.bmol[h.b];
     const int P = s.batch_off[h.b + 1] - s.batch_off[h.b];
     h.N = s.rel_off[h.b + 1] - s.rel_off[h.b];
-    const SplitGeom G(P, h.N, S);
+    const SplitGeom G(P, h.N, S, TN, F);
     const uint8_t *base = slices + sl_off[h.b];
     h.blk = (size_t)G.R16 * 128;
     h.a0 = base + (size_t)it.ti * 128 * 128;
@@ -464,12 +561,12 @@ __device__ __forceinline__ HItem h_item(const DevSystem &s, const HWork *work, i
     h.a_bytes = (uint32_t)min(128, G.R16 - it.ti * 128) * 128u;
     h.b_bytes = (uint32_t)min(TN, G.R16 - it.tj * TN) * 128u;
     h.n_kc = G.n_kc;
-    nao_split_h_seg_range(G.n_kc, nao_split_h_nseg(P, S), it.pad, S, h.kc0, h.kc1);
+    nao_split_h_seg_range(G.n_kc, nao_split_h_nseg(P, S, F), it.pad, S, h.kc0, h.kc1, F);
     h.neg16 = neg16[h.b];
     return h;
 }
 
-template <int TN>
+template <int TN, int F>
 __global__ void __launch_bounds__(192, 1)
     h_tc_kernel(DevSystem s, const HWork *__restrict__ work, int32_t w0, int32_t n_work, const uint8_t *__restrict__ slices,
                 const int64_t *__restrict__ sl_off, const int32_t *__restrict__ expo,
@@ -478,7 +575,7 @@ __global__ void __launch_bounds__(192, 1)
     extern __shared__ uint8_t smem_dyn[];
     __shared__ PPipe pp;
     uint8_t *smem = align1024(smem_dyn);
-    const int RING = ring_slots(S);
+    const int RING = ring_slots(S, F);
     uint8_t *sA = smem, *sB = smem + (size_t)RING * 16384;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -512,10 +609,10 @@ __global__ void __launch_bounds__(192, 1)
         if (lane == 0) {
             int gk = 0;
             for (int w = blockIdx.x; w < n_work && !*abort; w += gridDim.x) {
-                const HItem h = h_item<TN>(s, work, w0 + w, slices, sl_off, neg16, S);
+                const HItem h = h_item<TN, F>(s, work, w0 + w, slices, sl_off, neg16, S);
                 const bool more = w + (int)gridDim.x < n_work;
                 HItem hn = h;
-                if (more) hn = h_item<TN>(s, work, w0 + w + gridDim.x, slices, sl_off, neg16, S);
+                if (more) hn = h_item<TN, F>(s, work, w0 + w + gridDim.x, slices, sl_off, neg16, S);
                 for (int kc = h.kc0; kc < h.kc1; kc++, gk++) {
                     // the next K chunk's slices (or the next item's first) towards L2, so that the
                     // ring's copies come from L2
@@ -549,7 +646,7 @@ __global__ void __launch_bounds__(192, 1)
         if (lane == 0) {
             int gk = 0, t = 0;
             for (int w = blockIdx.x; w < n_work && !*abort; w += gridDim.x, t++) {
-                const HItem h = h_item<TN>(s, work, w0 + w, slices, sl_off, neg16, S);
+                const HItem h = h_item<TN, F>(s, work, w0 + w, slices, sl_off, neg16, S);
                 // the accumulators of the previous item have been read
                 if (t >= 1 && !tc::mbar_wait(&pp.acc_empty, (t - 1) & 1, kWaitCycles)) { *abort = 1; break; }
                 tc::fence_after_sync();
@@ -567,13 +664,13 @@ __global__ void __launch_bounds__(192, 1)
                         const int ncols = TN * (S - sa);
                         for (int n0 = 0; n0 < ncols; n0 += 256) {
                             const int nn = ncols - n0 < 256 ? ncols - n0 : 256;
-                            const uint32_t idesc = tc::idesc_bf16_f32(128, nn);
+                            const uint32_t idesc = tc::idesc_digits<F>(128, nn);
                             const uint64_t bd = tc::sdesc_sw128(tc::smem_addr(bset + (size_t)n0 * 128));
                             const uint32_t dt = tm + (uint32_t)(sa * TN + n0);
 #pragma unroll
                             for (int ks = 0; ks < 4; ks++) {
                                 const uint32_t id = (kc * 4 + ks < h.neg16) ? (idesc | (1u << 14)) : idesc;
-                                tc::mma_bf16(dt, ad + 2 * ks, bd + 2 * ks, id, (first | sa | ks) ? 1u : 0u);
+                                tc::mma_digits<F>(dt, ad + 2 * ks, bd + 2 * ks, id, (first | sa | ks) ? 1u : 0u);
                             }
                         }
                         tc::mma_commit(&pp.emptyA[a]);
@@ -592,7 +689,7 @@ __global__ void __launch_bounds__(192, 1)
         int t = 0;
         const uint32_t tm_row = tm + ((uint32_t)(warp * 32) << 16);
         for (int w = blockIdx.x; w < n_work; w += gridDim.x, t++) {
-            const HItem h = h_item<TN>(s, work, w0 + w, slices, sl_off, neg16, S);
+            const HItem h = h_item<TN, F>(s, work, w0 + w, slices, sl_off, neg16, S);
             if (*abort || !tc::mbar_wait(&pp.acc_full, t & 1, kWaitCycles)) { *abort = 1; break; }
             tc::fence_after_sync();
             const int i = h.ti * 128 + warp * 32 + lane;
@@ -600,24 +697,21 @@ __global__ void __launch_bounds__(192, 1)
             const int32_t *rel = s.rel_idx + s.rel_off[h.b];
             const int32_t *ex = expo + s.rel_off[h.b];
             const int ei = row_ok ? ex[i] : -10000;
-            // h_ij as one 64-bit integer, exact as hi 2^18 + lo' where |hi| < 2^44, else
-            // 4 hi + round(lo' / 2^16) (|4 hi| >= 2^46: relative error <= 2^-47), with lo' = lo +
-            // round(lo2 / 2^18): the groups g >= 10 that only S = 11, 12 have are folded into lo at
-            // a cost of at most half a unit of lo, 2^-67 of 2^(e_i + e_j), far below the split's own
-            // truncation. The integers are formed before tensor memory is handed back, the
-            // conversion and the product by 2^(e_i + e_j - 66 or - 50) after.
+            // h_ij as one 64-bit integer v and a tier t (h_int: exact where the high part is
+            // small, else relative error <= 2^-43), formed before tensor memory is handed back;
+            // the conversion and the product by 2^(e_i + e_j - h_unit(t)) after.
             long long val[TN];
-            uint64_t small_mask = 0;
+            uint64_t t1_mask = 0, t2_mask = 0;
 #pragma unroll
             for (int c0 = 0; c0 < TN; c0 += 16) {
                 Parts16 v;
-                combine16<TN>(tm_row, c0, S, v);
+                combine16<TN, F>(tm_row, c0, S, v);
 #pragma unroll
                 for (int jj = 0; jj < 16; jj++) {
-                    const long long hi = v.hi[jj], lo = v.lo[jj] + ((v.lo2[jj] + (1LL << 17)) >> 18);
-                    const bool small = hi > -(1LL << 44) && hi < (1LL << 44);
-                    val[c0 + jj] = small ? (hi << 18) + lo : (hi << 2) + ((lo + (1LL << 15)) >> 16);
-                    small_mask |= (uint64_t)small << (c0 + jj);
+                    int t;
+                    val[c0 + jj] = h_int<F>(v.hi[jj], v.lo[jj], v.lo2[jj], t);
+                    t1_mask |= (uint64_t)(t == 1) << (c0 + jj);
+                    t2_mask |= (uint64_t)(t == 2) << (c0 + jj);
                 }
             }
             // tensor memory is free for the next item
@@ -631,9 +725,8 @@ __global__ void __launch_bounds__(192, 1)
                     const int j = h.tj * TN + jj;
                     if (j < h.N && j >= i) {
                         const int ej = ex[j];
-                        const double x = (ei > -10000 && ej > -10000)
-                                             ? (double)val[jj] * pow2(ei + ej - (((small_mask >> jj) & 1) ? 66 : 50))
-                                             : 0.0;
+                        const int t = ((t1_mask >> jj) & 1) ? 1 : (((t2_mask >> jj) & 1) ? 2 : 0);
+                        const double x = (ei > -10000 && ej > -10000) ? (double)val[jj] * pow2(ei + ej - h_unit<F>(t)) : 0.0;
                         h_add(s, h.m, gi, rel[j], x);
                     }
                 }
@@ -662,7 +755,7 @@ struct NItem {  // geometry of one density work item
     int nJ, n_kcN, R16, b, m, p0, P, Ppad, N, ti;
 };
 
-template <int TN>
+template <int TN, int F>
 __device__ __forceinline__ NItem n_item(const DevSystem &s, const HWork *work, int32_t w, const uint8_t *slices,
                                         const int64_t *sl_off, int S) {
     NItem h;
@@ -675,7 +768,7 @@ __device__ __forceinline__ NItem n_item(const DevSystem &s, const HWork *work, i
     h.P = s.batch_off[h.b + 1] - h.p0;
     h.Ppad = (h.P + NAO_PPAD - 1) & ~(NAO_PPAD - 1);
     h.N = s.rel_off[h.b + 1] - s.rel_off[h.b];
-    const SplitGeom G(h.P, h.N, S, TN);
+    const SplitGeom G(h.P, h.N, S, TN, F);
     const uint8_t *base = slices + sl_off[h.b];
     h.a0 = base + G.nA_block(0, 0) + (size_t)it.ti * 128 * 128;
     h.a_s = (size_t)G.n_kcN * G.P16 * 128;
@@ -691,13 +784,14 @@ __device__ __forceinline__ NItem n_item(const DevSystem &s, const HWork *work, i
 
 // K chunks of tile J: P' is zero for basis functions beyond tile J, so K stops at TN (J + 1)
 // (all of K for GRADN)
-template <int TN, bool GRADN>
+template <int TN, bool GRADN, int F>
 __device__ __forceinline__ int n_item_kc(const NItem &h, int J) {
-    const int nk = GRADN ? h.n_kcN : ((J + 1) * TN + 63) / 64;
+    constexpr int C = nao_chunk_cols(F);
+    const int nk = GRADN ? h.n_kcN : ((J + 1) * TN + C - 1) / C;
     return nk < h.n_kcN ? nk : h.n_kcN;
 }
 
-template <int TN, bool GRADN>
+template <int TN, bool GRADN, int F>
 __global__ void __launch_bounds__(192, 1)
     n_tc_kernel(DevSystem s, const HWork *__restrict__ work, int32_t w0, int32_t n_work, const uint8_t *__restrict__ slices,
                 const int64_t *__restrict__ sl_off, const int32_t *__restrict__ expo_q,
@@ -707,7 +801,7 @@ __global__ void __launch_bounds__(192, 1)
     extern __shared__ uint8_t smem_dyn[];
     __shared__ PPipe pp;
     uint8_t *smem = align1024(smem_dyn);
-    const int RING = ring_slots(S);
+    const int RING = ring_slots(S, F);
     uint8_t *sA = smem, *sB = smem + (size_t)RING * 16384;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -741,9 +835,9 @@ __global__ void __launch_bounds__(192, 1)
         if (lane == 0) {
             int gk = 0;
             for (int w = blockIdx.x; w < n_work && !*abort; w += gridDim.x) {
-                const NItem h = n_item<TN>(s, work, w0 + w, slices, sl_off, S);
+                const NItem h = n_item<TN, F>(s, work, w0 + w, slices, sl_off, S);
                 for (int J = 0; J < h.nJ && !*abort; J++) {
-                    const int nk = n_item_kc<TN, GRADN>(h, J);
+                    const int nk = n_item_kc<TN, GRADN, F>(h, J);
                     const uint8_t *bJ = h.b0 + (size_t)J * TN * 128;
                     const uint32_t b_bytes = (uint32_t)min(TN, h.R16 - J * TN) * 128u;
                     for (int kc = 0; kc < nk; kc++, gk++) {
@@ -782,9 +876,9 @@ __global__ void __launch_bounds__(192, 1)
         if (lane == 0) {
             int gk = 0, t = 0;
             for (int w = blockIdx.x; w < n_work && !*abort; w += gridDim.x) {
-                const NItem h = n_item<TN>(s, work, w0 + w, slices, sl_off, S);
+                const NItem h = n_item<TN, F>(s, work, w0 + w, slices, sl_off, S);
                 for (int J = 0; J < h.nJ && !*abort; J++, t++) {
-                    const int nk = n_item_kc<TN, GRADN>(h, J);
+                    const int nk = n_item_kc<TN, GRADN, F>(h, J);
                     // the accumulators of the previous tile have been read
                     if (t >= 1 && !tc::mbar_wait(&pp.acc_empty, (t - 1) & 1, kWaitCycles)) { *abort = 1; break; }
                     tc::fence_after_sync();
@@ -801,12 +895,12 @@ __global__ void __launch_bounds__(192, 1)
                             const int ncols = TN * (S - sa);
                             for (int n0 = 0; n0 < ncols; n0 += 256) {
                                 const int nn = ncols - n0 < 256 ? ncols - n0 : 256;
-                                const uint32_t idesc = tc::idesc_bf16_f32(128, nn);
+                                const uint32_t idesc = tc::idesc_digits<F>(128, nn);
                                 const uint64_t bd = tc::sdesc_sw128(tc::smem_addr(bset + (size_t)n0 * 128));
                                 const uint32_t dt = tm + (uint32_t)(sa * TN + n0);
 #pragma unroll
                                 for (int ks = 0; ks < 4; ks++)
-                                    tc::mma_bf16(dt, ad + 2 * ks, bd + 2 * ks, idesc, (kc | sa | ks) ? 1u : 0u);
+                                    tc::mma_digits<F>(dt, ad + 2 * ks, bd + 2 * ks, idesc, (kc | sa | ks) ? 1u : 0u);
                             }
                             tc::mma_commit(&pp.emptyA[a]);
                         }
@@ -825,18 +919,17 @@ __global__ void __launch_bounds__(192, 1)
         int t = 0;
         const uint32_t tm_row = tm + ((uint32_t)(warp * 32) << 16);
         for (int w = blockIdx.x; w < n_work && !*abort; w += gridDim.x) {
-            const NItem h = n_item<TN>(s, work, w0 + w, slices, sl_off, S);
+            const NItem h = n_item<TN, F>(s, work, w0 + w, slices, sl_off, S);
             const int q = h.ti * 128 + warp * 32 + lane;
             const bool row_ok = q < h.P;
             const double *E = scratch + s.scr_off[h.b];
             const int64_t ld = GRADN ? 4 * (int64_t)h.Ppad : (int64_t)h.Ppad;
-            // sum_j T_qj phi_qj (and grad phi) in units of 2^(e_q + e_b - 50): each T_qj as one
-            // 64-bit integer in those units, 4 hi + round(lo' / 2^16) (|4 hi| < 2^62.03; lo' = lo +
-            // round(lo2 / 2^18) folds the groups g >= 10 of S = 11, 12), rounded by at most 2^-1
-            // unit: the order of the split's truncation at S = 10 (the dropped groups g >= S reach
-            // K (S + 1) 2^(e_q + e_b - 6S - 2)) and below the FP64 evaluation's rounding in n. Then
-            // one conversion and one FMA per product, all integer work done before tensor memory is
-            // handed back (no FP64 arithmetic on that path).
+            // sum_j T_qj phi_qj (and grad phi) in units of 2^(e_q + e_b - n_unit): each T_qj as one
+            // 64-bit integer in those units (n_int: 2^-50 with bf16 digits, 2^-47 with e4m3),
+            // rounded by at most half a unit: about the split's own truncation at 10 bf16 slices
+            // (the dropped groups g >= S reach K (S + 1) 2^(e_q + e_b - 6S - 2)) and below the FP64
+            // evaluation's rounding in n. Then one conversion and one FMA per product, all integer
+            // work done before tensor memory is handed back (no FP64 arithmetic on that path).
             double part = 0.0, gpart[3] = {0.0, 0.0, 0.0};
             for (int J = 0; J < h.nJ; J++, t++) {
                 if (*abort || !tc::mbar_wait(&pp.acc_full, t & 1, kWaitCycles)) { *abort = 1; break; }
@@ -845,12 +938,9 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
                 for (int c0 = 0; c0 < TN; c0 += 16) {
                     Parts16 v;
-                    combine16<TN>(tm_row, c0, S, v);
+                    combine16<TN, F>(tm_row, c0, S, v);
 #pragma unroll
-                    for (int jj = 0; jj < 16; jj++) {
-                        const long long lo = v.lo[jj] + ((v.lo2[jj] + (1LL << 17)) >> 18);  // lo2: S = 11, 12
-                        val[c0 + jj] = (v.hi[jj] << 2) + ((lo + (1LL << 15)) >> 16);
-                    }
+                    for (int jj = 0; jj < 16; jj++) val[c0 + jj] = n_int<F>(v.hi[jj], v.lo[jj], v.lo2[jj]);
                 }
                 // tensor memory is free for the next tile
                 tc::fence_before_sync();
@@ -881,7 +971,7 @@ __global__ void __launch_bounds__(192, 1)
             if (row_ok) {
                 const int eq = expo_q[h.p0 + q], eb = expo_b[h.b];
                 const bool live = eq > -10000 && eb > -10000;
-                const double sc = pow2(eq + eb - 50);
+                const double sc = pow2(eq + eb - n_unit<F>());
                 *n_at(s, h.m, h.p0 + q) = live ? part * sc : 0.0;
                 if (GRADN)
 #pragma unroll
@@ -929,7 +1019,7 @@ __global__ void wait_timeout_probe_kernel(long long max_cycles, int32_t *__restr
 
 }  // namespace
 
-size_t split_smem_bytes(int S) { return pipe_smem_bytes(S); }
+size_t split_smem_bytes(int S, int F) { return pipe_smem_bytes(S, F); }
 
 cudaError_t launch_wait_timeout_probe(long long max_cycles, int32_t *err, cudaStream_t st) {
     wait_timeout_probe_kernel<<<1, 1, 0, st>>>(max_cycles, err);
@@ -947,10 +1037,13 @@ static int sm_count() {
 
 cudaError_t split_configure() {
     size_t bytes = 0;
-    for (int S = 4; S <= NAO_SPLIT_MAX_SLICES; S++) bytes = split_smem_bytes(S) > bytes ? split_smem_bytes(S) : bytes;
-    const void *fns[6] = {(const void *)h_tc_kernel<48>, (const void *)h_tc_kernel<32>,
-                          (const void *)n_tc_kernel<48, false>, (const void *)n_tc_kernel<32, false>,
-                          (const void *)n_tc_kernel<48, true>, (const void *)n_tc_kernel<32, true>};
+    for (int S = 4; S <= NAO_SPLIT_MAX_SLICES; S++) bytes = std::max(bytes, split_smem_bytes(S, NAO_DIGITS_BF16));
+    for (int S = 8; S <= NAO_SPLIT_MAX_SLICES_E4M3; S++) bytes = std::max(bytes, split_smem_bytes(S, NAO_DIGITS_E4M3));
+    const void *fns[] = {(const void *)h_tc_kernel<48, 0>,        (const void *)h_tc_kernel<32, 0>,
+                         (const void *)h_tc_kernel<32, 1>,        (const void *)n_tc_kernel<48, false, 0>,
+                         (const void *)n_tc_kernel<32, false, 0>, (const void *)n_tc_kernel<48, true, 0>,
+                         (const void *)n_tc_kernel<32, true, 0>,  (const void *)n_tc_kernel<32, false, 1>,
+                         (const void *)n_tc_kernel<32, true, 1>};
     for (const void *f : fns) {
         const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (e != cudaSuccess) return e;
@@ -958,41 +1051,57 @@ cudaError_t split_configure() {
     return cudaSuccess;
 }
 
-#define NAO_SPLIT_DISPATCH(S, CALL)                  \
-    switch (S) {                                    \
-        case 4: CALL(4); break;                     \
-        case 5: CALL(5); break;                     \
-        case 6: CALL(6); break;                     \
-        case 7: CALL(7); break;                     \
-        case 8: CALL(8); break;                     \
-        case 9: CALL(9); break;                     \
-        case 10: CALL(10); break;                   \
-        case 11: CALL(11); break;                   \
-        default: CALL(12); break;                   \
+// Slice counts with compiled slicers: 4..12 with bf16 digits, 8..16 with e4m3 digits.
+#define NAO_SPLIT_DISPATCH(S, F, CALL)                                                                 \
+    if (F == NAO_DIGITS_E4M3) {                                                                        \
+        switch (S) {                                                                                   \
+            case 8: CALL(8, 1); break;                                                                 \
+            case 9: CALL(9, 1); break;                                                                 \
+            case 10: CALL(10, 1); break;                                                               \
+            case 11: CALL(11, 1); break;                                                               \
+            case 12: CALL(12, 1); break;                                                               \
+            case 13: CALL(13, 1); break;                                                               \
+            case 14: CALL(14, 1); break;                                                               \
+            case 15: CALL(15, 1); break;                                                               \
+            default: CALL(16, 1); break;                                                               \
+        }                                                                                              \
+    } else {                                                                                           \
+        switch (S) {                                                                                   \
+            case 4: CALL(4, 0); break;                                                                 \
+            case 5: CALL(5, 0); break;                                                                 \
+            case 6: CALL(6, 0); break;                                                                 \
+            case 7: CALL(7, 0); break;                                                                 \
+            case 8: CALL(8, 0); break;                                                                 \
+            case 9: CALL(9, 0); break;                                                                 \
+            case 10: CALL(10, 0); break;                                                               \
+            case 11: CALL(11, 0); break;                                                               \
+            default: CALL(12, 0); break;                                                               \
+        }                                                                                              \
     }
 
 cudaError_t launch_slice_h(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_rt, const double *scratch,
                            uint32_t terms, uint8_t *slices, const int64_t *sl_off, int32_t *expo, int32_t *neg16, int S,
-                           cudaStream_t st) {
+                           int F, cudaStream_t st) {
     if (b1 <= b0 || max_rt <= 0) return cudaSuccess;
-#define NAO_SLICE_H(SS) \
-    slice_h_kernel<SS><<<dim3(b1 - b0, max_rt), 256, 0, st>>>(s, b0, scratch, terms, slices, sl_off, expo, neg16)
-    NAO_SPLIT_DISPATCH(S, NAO_SLICE_H)
+#define NAO_SLICE_H(SS, FF) \
+    slice_h_kernel<SS, FF><<<dim3(b1 - b0, max_rt), 256, 0, st>>>(s, b0, scratch, terms, slices, sl_off, expo, neg16)
+    NAO_SPLIT_DISPATCH(S, F, NAO_SLICE_H)
 #undef NAO_SLICE_H
     return cudaGetLastError();
 }
 
 cudaError_t launch_h_tc(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
-                        const int64_t *sl_off, const int32_t *expo, const int32_t *neg16, int S, int tn, int scatter,
-                        int32_t *err, cudaStream_t st) {
+                        const int64_t *sl_off, const int32_t *expo, const int32_t *neg16, int S, int F, int tn,
+                        int scatter, int32_t *err, cudaStream_t st) {
     if (n_work <= 0) return cudaSuccess;
     const int grid = n_work < sm_count() ? n_work : sm_count();  // persistent: one CTA per SM
-    if (tn == 48 && S <= 10)
-        h_tc_kernel<48><<<grid, 192, split_smem_bytes(S), st>>>(s, work, w0, n_work, slices, sl_off, expo, neg16, S,
-                                                               scatter, err);
-    else if (tn == 32)
-        h_tc_kernel<32><<<grid, 192, split_smem_bytes(S), st>>>(s, work, w0, n_work, slices, sl_off, expo, neg16, S,
-                                                               scatter, err);
+    const size_t sm = split_smem_bytes(S, F);
+    if (F == NAO_DIGITS_E4M3 && tn == 32)
+        h_tc_kernel<32, 1><<<grid, 192, sm, st>>>(s, work, w0, n_work, slices, sl_off, expo, neg16, S, scatter, err);
+    else if (F == NAO_DIGITS_BF16 && tn == 48 && S <= 10)
+        h_tc_kernel<48, 0><<<grid, 192, sm, st>>>(s, work, w0, n_work, slices, sl_off, expo, neg16, S, scatter, err);
+    else if (F == NAO_DIGITS_BF16 && tn == 32)
+        h_tc_kernel<32, 0><<<grid, 192, sm, st>>>(s, work, w0, n_work, slices, sl_off, expo, neg16, S, scatter, err);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
@@ -1000,37 +1109,39 @@ cudaError_t launch_h_tc(const DevSystem &s, const HWork *work, int32_t w0, int32
 
 cudaError_t launch_slice_n(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_qt, int32_t max_rt,
                            const double *scratch, uint8_t *slices, const int64_t *sl_off, const int32_t *expo_q,
-                           int32_t *expo_b, const int32_t *tn_b, int S, bool grad, cudaStream_t st) {
+                           int32_t *expo_b, const int32_t *tn_b, int S, int F, bool grad, cudaStream_t st) {
     if (b1 <= b0) return cudaSuccess;
     // y = 0: the exponent of P'; y >= 1: 32-point tiles (128 max_qt >= P16)
-#define NAO_SLICE_NPHI(SS)                                                                                   \
-    slice_nphi_kernel<SS><<<dim3(b1 - b0, 4 * max_qt + 1), 256, 0, st>>>(s, b0, scratch, slices, sl_off, expo_q, \
-                                                                         expo_b, tn_b, grad ? 4 : 1, grad ? 1 : 0)
-    NAO_SPLIT_DISPATCH(S, NAO_SLICE_NPHI)
+#define NAO_SLICE_NPHI(SS, FF)                                                                                    \
+    slice_nphi_kernel<SS, FF><<<dim3(b1 - b0, 4 * max_qt + 1), 256, 0, st>>>(s, b0, scratch, slices, sl_off, expo_q, \
+                                                                             expo_b, tn_b, grad ? 4 : 1, grad ? 1 : 0)
+    NAO_SPLIT_DISPATCH(S, F, NAO_SLICE_NPHI)
 #undef NAO_SLICE_NPHI
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || max_rt <= 0) return e;
     // 16 rows per CTA (64 max_rt >= R16)
-#define NAO_SLICE_NP(SS) \
-    slice_np_kernel<SS><<<dim3(b1 - b0, 4 * max_rt), 256, 0, st>>>(s, b0, slices, sl_off, expo_b, tn_b, grad ? 1 : 0)
-    NAO_SPLIT_DISPATCH(S, NAO_SLICE_NP)
+#define NAO_SLICE_NP(SS, FF) \
+    slice_np_kernel<SS, FF><<<dim3(b1 - b0, 4 * max_rt), 256, 0, st>>>(s, b0, slices, sl_off, expo_b, tn_b, grad ? 1 : 0)
+    NAO_SPLIT_DISPATCH(S, F, NAO_SLICE_NP)
 #undef NAO_SLICE_NP
     return cudaGetLastError();
 }
 
 cudaError_t launch_n_tc(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
                         const int64_t *sl_off, const int32_t *expo_q, const int32_t *expo_b, const double *scratch, int S,
-                        int tn, bool grad, int32_t *err, cudaStream_t st) {
+                        int F, int tn, bool grad, int32_t *err, cudaStream_t st) {
     if (n_work <= 0) return cudaSuccess;
-    if (tn != 32 && !(tn == 48 && S <= 10)) return cudaErrorInvalidValue;
-    const size_t sm = split_smem_bytes(S);
+    if (F == NAO_DIGITS_E4M3 ? tn != 32 : (tn != 32 && !(tn == 48 && S <= 10))) return cudaErrorInvalidValue;
+    const size_t sm = split_smem_bytes(S, F);
     const int grid = n_work < sm_count() ? n_work : sm_count();  // persistent: one CTA per SM
-#define NAO_N_TC(TNV, G) \
-    n_tc_kernel<TNV, G><<<grid, 192, sm, st>>>(s, work, w0, n_work, slices, sl_off, expo_q, expo_b, scratch, S, err)
-    if (tn == 48 && grad) NAO_N_TC(48, true);
-    else if (tn == 48) NAO_N_TC(48, false);
-    else if (grad) NAO_N_TC(32, true);
-    else NAO_N_TC(32, false);
+#define NAO_N_TC(TNV, G, FF) \
+    n_tc_kernel<TNV, G, FF><<<grid, 192, sm, st>>>(s, work, w0, n_work, slices, sl_off, expo_q, expo_b, scratch, S, err)
+    if (F == NAO_DIGITS_E4M3 && grad) NAO_N_TC(32, true, 1);
+    else if (F == NAO_DIGITS_E4M3) NAO_N_TC(32, false, 1);
+    else if (tn == 48 && grad) NAO_N_TC(48, true, 0);
+    else if (tn == 48) NAO_N_TC(48, false, 0);
+    else if (grad) NAO_N_TC(32, true, 0);
+    else NAO_N_TC(32, false, 0);
 #undef NAO_N_TC
     return cudaGetLastError();
 }

@@ -112,6 +112,32 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
+// Instruction descriptor of kind::f8f6f4 with E4M3 A and B (format code 0 at bits 7-9 and 10-12),
+// D FP32 (bits 4-5 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_e4m3_f32(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// D[tmem] (+)= A * B^T with E4M3 operands (K = 32 per instruction), issued by one thread.
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+// The MMA of digit format F (0: bf16, kind::f16; 1: e4m3, kind::f8f6f4) and its descriptor.
+template <int F>
+__host__ __device__ constexpr uint32_t idesc_digits(int M, int N) {
+    return F == 1 ? idesc_e4m3_f32(M, N) : idesc_bf16_f32(M, N);
+}
+template <int F>
+__device__ __forceinline__ void mma_digits(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accumulate) {
+    if constexpr (F == 1) mma_e4m3(d_tmem, adesc, bdesc, idesc, accumulate);
+    else mma_bf16(d_tmem, adesc, bdesc, idesc, accumulate);
+}
+
 // Arrive on the mbarrier once all previously issued tcgen05.mma of this thread completed.
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
@@ -122,6 +148,10 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
 // 128-byte swizzle: 16-byte chunk k/8 of row r is placed at chunk (k/8) ^ (r%8).
 __host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t r, uint32_t k) {
     return (r >> 3) * 1024u + (r & 7u) * 128u + ((((k >> 3) ^ (r & 7u)) & 7u) << 4) + (k & 7u) * 2u;
+}
+// The same for byte kb of row r (any element size): 16-byte chunk kb/16 goes to (kb/16) ^ (r%8).
+__host__ __device__ __forceinline__ uint32_t sw128_byte(uint32_t r, uint32_t kb) {
+    return (r >> 3) * 1024u + (r & 7u) * 128u + ((((kb >> 4) ^ (r & 7u)) & 7u) << 4) + (kb & 15u);
 }
 
 }  // namespace tc

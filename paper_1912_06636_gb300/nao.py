@@ -62,7 +62,7 @@ class Options(C.Structure):
     _fields_ = [
         ("max_batch_points", C.c_int32), ("split_slices", C.c_int32), ("deterministic", C.c_int32),
         ("device", C.c_int32), ("scratch_bytes", C.c_int64), ("capture_graph", C.c_int32),
-        ("autotune", C.c_int32),
+        ("autotune", C.c_int32), ("split_digits", C.c_int32),
     ]
 
 
@@ -607,6 +607,7 @@ class Grid:
                 self.h = nao_grid_create(system, device=device, **opts)
         self.info = nao_get_info(self.h)
         self.split_slices = int(opts.get("split_slices", nao_default_options().split_slices))
+        self.split_digits = int(opts.get("split_digits", 0))
         self.nb = int(self.info.n_basis)
         self.n_points = int(self.info.n_points)
         self.n_systems = int(self.info.n_systems)

@@ -77,9 +77,9 @@ def n_basis_of(system) -> int:
 def estimate_bytes(n_points: int, nb: int, max_batch_points: int, scratch_bytes: int, p_rank: int) -> int:
     """Upper estimate of one request's device memory: the handle (points and batch tables,
     reduced-basis lists bounded by every batch holding every function, evaluation scratch, the
-    split path's slices at twice the scratch) plus the request's H, P, v, v0, n, u and X."""
+    split path's slices at up to three times the scratch) plus the request's H, P, v, v0, n, u and X."""
     n_batches = max(1, math.ceil(n_points / max_batch_points))
-    handle = 48 * n_points + 16 * n_batches * nb + 3 * scratch_bytes + (8 << 20)
+    handle = 48 * n_points + 16 * n_batches * nb + 4 * scratch_bytes + (8 << 20)
     buffers = 16 * nb * nb + 8 * nb * p_rank + 40 * n_points
     return int(handle + buffers)
 
@@ -100,7 +100,8 @@ class _Slot:
 
 class Server:
     def __init__(self, prec="split", hbm_budget_bytes: int = 150 << 30, max_active: int = 16, device: int | None = None,
-                 split_slices: int | None = None, capture_graph: bool = True, keep_results: bool = False,
+                 split_slices: int | None = None, split_digits: int | None = None, capture_graph: bool = True,
+                 keep_results: bool = False,
                  scratch_bytes: int = 256 << 20, p_rank: int = 16, max_batch_points: int = 200):
         import torch
 
@@ -113,6 +114,8 @@ class Server:
                      "max_batch_points": int(max_batch_points)}
         if split_slices is not None:
             self.opts["split_slices"] = int(split_slices)
+        if split_digits is not None:
+            self.opts["split_digits"] = int(split_digits)
         self.keep = keep_results
         self.p_rank = int(p_rank)
         self.scratch_bytes = int(scratch_bytes)

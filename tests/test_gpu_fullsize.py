@@ -20,6 +20,8 @@ pytestmark = pytest.mark.gpu
 TOL = {"fp64": 1e-12, "fp32": 1e-6, "split": 1e-10}
 # the split path at the library's default slice count and at the count bench.py times here
 SPLIT_CASES = sorted({12, bench.BENCH_SLICES[1]})
+# e4m3 digits (base 32) at the slice count bench.py uses with them
+E4M3_CASES = [bench.BENCH_SLICES_E4M3[1]]
 
 
 def cuda(a):
@@ -48,13 +50,16 @@ def test_partition_and_relevance_bit_exact_fullsize(diamond):
     assert np.array_equal(ro, oro) and np.array_equal(ri, ori)
 
 
-@pytest.mark.parametrize("case", ["fp64", "fp32"] + [f"split{S}" for S in SPLIT_CASES])
+@pytest.mark.parametrize("case", ["fp64", "fp32"] + [f"split{S}" for S in SPLIT_CASES]
+                         + [f"e4m3_{S}" for S in E4M3_CASES])
 def test_fullsize_every_element(diamond, case):
     g, s = diamond["g"], diamond["s"]
-    prec = "split" if case.startswith("split") else case
+    prec = "split" if case.startswith(("split", "e4m3")) else case
     own = None
-    if prec == "split":
+    if case.startswith("split"):
         own = g = nao.Grid(s, device=0, max_batch_points=s.max_batch_points, split_slices=int(case[5:]))
+    elif case.startswith("e4m3"):
+        own = g = nao.Grid(s, device=0, max_batch_points=s.max_batch_points, split_slices=int(case[5:]), split_digits=1)
     H = g.integrate_h(cuda(diamond["v"]), prec=prec)
     n, ne = g.update_density(cuda(diamond["P"]), prec=prec)
     S = g.overlap(prec=prec)

@@ -133,3 +133,21 @@ def test_graphs_recorded_before_tuning_are_replaced(mols):
             assert rel_err(n1[i].cpu().numpy(), r["n"], r["D"]) <= 1e-10
             assert rel_err(n2[i].cpu().numpy(), r["n"], r["D"]) <= 1e-10
             assert abs(ne2[i].item() - r["ne"]) <= 1e-10 * abs(r["ne"])
+
+
+def test_every_molecule_matches_oracle_e4m3(mols):
+    """The setting bench.py times the batching configuration with: 14 e4m3 slices (base-32
+    digits, kind::f8f6f4), in a grouped handle of its own."""
+    systems, bs, refs = mols["systems"], mols["bs"], mols["refs"]
+    with nao.Grid(systems, device=0, batch_points=bs, split_slices=14, split_digits=1, capture_graph=1) as g:
+        Hs = g.integrate_h_many([cuda(r["v"]) for r in refs], prec="split")
+        ns, nes = g.update_density_many([cuda(r["P"]) for r in refs], prec="split")
+        torch.cuda.synchronize()
+        g.sync()
+        worst = 0.0
+        for m, r in enumerate(refs):
+            eh = rel_err(Hs[m].cpu().numpy(), r["H"], r["A"])
+            en = rel_err(ns[m].cpu().numpy(), r["n"], r["D"])
+            worst = max(worst, eh, en)
+            assert eh <= TOL["split"] and en <= TOL["split"], (m, eh, en)
+    print(f"e4m3: worst error {worst:.2e} over {len(refs)} molecules")

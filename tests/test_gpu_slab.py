@@ -25,6 +25,8 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 TOL = {"fp64": 1e-12, "fp32": 1e-6, "split": 1e-10}
 SPLIT_CASES = sorted({12, bench.BENCH_SLICES[2]})
+# e4m3 digits (base 32) at the slice count bench.py uses with them
+E4M3_CASES = [bench.BENCH_SLICES_E4M3[2]]
 # atoms of the block: 0 (B) with its in-layer neighbour 1 (B, 7.8 bohr) and 5, the layer above
 # (25, 26: A, 5.7 bohr), a pair in the middle of the slab (187, 188) with the atom above one of
 # them (212), and the far corner (374); 40 functions each (4s3p4d1f)
@@ -63,13 +65,16 @@ def test_slab_sizes(slab):
     assert np.count_nonzero(slab["Ab"]) > 0 and np.count_nonzero(slab["Ab"] == 0) > 0
 
 
-@pytest.mark.parametrize("case", ["fp64", "fp32"] + [f"split{S}" for S in SPLIT_CASES])
+@pytest.mark.parametrize("case", ["fp64", "fp32"] + [f"split{S}" for S in SPLIT_CASES]
+                         + [f"e4m3_{S}" for S in E4M3_CASES])
 def test_slab_block_and_samples(slab, case):
     g = slab["g"]
-    prec = "split" if case.startswith("split") else case
+    prec = "split" if case.startswith(("split", "e4m3")) else case
     own = None
-    if prec == "split":
+    if case.startswith("split"):
         own = g = nao.Grid(slab["s"], device=0, max_batch_points=200, split_slices=int(case[5:]))
+    elif case.startswith("e4m3"):
+        own = g = nao.Grid(slab["s"], device=0, max_batch_points=200, split_slices=int(case[5:]), split_digits=1)
     t0 = time.perf_counter()
     H = g.integrate_h(cuda(slab["v"]), prec=prec)
     Pd = cuda(slab["P"])

@@ -101,3 +101,62 @@ def test_split_rejects_batches_beyond_512_points(water, B, S):
         with pytest.raises(nao.NaoError) as e:
             g.integrate_h(cuda(water["v"]), prec="split")
         assert e.value.code == nao.NAO_ERR_UNSUPPORTED
+
+
+# ---- e4m3 digits (options.split_digits = 1): balanced base-32 digits, |d| <= 16, exact in e4m3,
+# kind::f8f6f4 MMAs; 5 bits per slice, so 14 slices carry 70 bits (11 bf16 slices carry 66).
+def test_e4m3_hamiltonian_and_density(water):
+    H, n, ne = run(water, split_digits=1, split_slices=14)
+    assert np.array_equal(H, H.T)
+    eH = rel_err(H, water["H"], water["A"])
+    en = rel_err(n, water["n"], water["D"])
+    print(f"e4m3 14 slices: e_H={eH:.2e} (raw {raw_rel_err(H, water['H'], water['A']):.2e}) e_n={en:.2e}")
+    assert eH <= TOL and en <= TOL
+    assert abs(ne - water["ne"]) <= TOL * abs(water["ne"])
+
+
+def test_e4m3_error_falls_with_slices(water):
+    errs = {}
+    for S in (8, 10, 12, 14, 16):
+        H, n, _ = run(water, split_digits=1, split_slices=S)
+        errs[S] = (rel_err(H, water["H"], water["A"]), rel_err(n, water["n"], water["D"]))
+    print("e4m3 errors by slices:", errs)
+    # 8 slices carry 40 bits (about 6.7 bf16 slices): well above FP64 rounding on this molecule,
+    # and about 32^2 more accurate two slices later
+    assert errs[8][0] > 1e-12 and errs[8][0] / max(errs[10][0], 1e-300) > 300.0
+    for S in (12, 14, 16):
+        assert errs[S][0] <= TOL and errs[S][1] <= TOL
+
+
+@pytest.mark.parametrize("B", [1, 37, 200, 400, 512])
+def test_e4m3_independent_of_batch_size(water, B):
+    H, n, _ = run(water, max_batch_points=B, split_digits=1, split_slices=14)
+    assert rel_err(H, water["H"], water["A"]) <= TOL
+    assert rel_err(n, water["n"], water["D"]) <= TOL
+
+
+def test_e4m3_overlap_kinetic_and_gradient(water):
+    s, o = water["s"], water["o"]
+    S_ref, SA = o.overlap(s.pt_xyz, s.pt_w)
+    T_ref, TA = o.hamiltonian(s.pt_xyz, s.pt_w, None, oracle.TERM_KINETIC)
+    g_ref, Dg = o.density_gradient(s.pt_xyz, water["P"])
+    with nao.Grid(s, device=0, split_digits=1, split_slices=14) as g:
+        S = g.overlap(prec="split").cpu().numpy()
+        T = g.integrate_h(None, nao.NAO_TERM_KINETIC, prec="split").cpu().numpy()
+        n, grad, _ = g.density_gradient(cuda(water["P"]), prec="split")
+        torch.cuda.synchronize()
+        g.sync()
+    assert rel_err(S, S_ref, SA) <= TOL
+    assert rel_err(T, T_ref, TA) <= TOL
+    assert rel_err(n.cpu().numpy(), water["n"], water["D"]) <= TOL
+    gr = grad.cpu().numpy()
+    for c in range(3):
+        assert rel_err(gr[c], g_ref[:, c], Dg[:, c]) <= TOL
+
+
+def test_digit_options_are_checked(water):
+    for opts in (dict(split_digits=2), dict(split_digits=1, split_slices=7), dict(split_digits=1, split_slices=17),
+                 dict(split_digits=0, split_slices=13)):
+        with pytest.raises(nao.NaoError) as e:
+            nao.Grid(water["s"], device=0, **opts)
+        assert e.value.code == nao.NAO_ERR_INVALID_ARG
