@@ -742,8 +742,8 @@ def main():
                 other[f"split_{d}_slices"] = {"unavailable": str(e)}
         line["other_precisions"] = other
         # the extensions on the same workload, one untimed and one timed call each: the density
-        # gradient (split, FP64) and Hessian (FP64), H with the meta-GGA term (split), the local
-        # Pulay matrix elements (FP64)
+        # gradient (split, FP64) and Hessian (FP64, FP32, split), H with the meta-GGA term (split), the
+        # local Pulay matrix elements (FP64, FP32)
         deriv = {}
         gbuf = torch.empty((3, g.n_points), dtype=torch.float64, device=dev)
         hbuf = torch.empty((6, g.n_points), dtype=torch.float64, device=dev)
@@ -754,8 +754,11 @@ def main():
             "gradient_split": lambda: g.density_gradient(P, prec="split", n=n, grad=gbuf, ne=ne, stream=stream),
             "gradient_fp64": lambda: g.density_gradient(P, prec="fp64", n=n, grad=gbuf, ne=ne, stream=stream),
             "hessian_fp64": lambda: g.density_hessian(P, prec="fp64", n=n, grad=gbuf, hess=hbuf, ne=ne, stream=stream),
+            "hessian_fp32": lambda: g.density_hessian(P, prec="fp32", n=n, grad=gbuf, hess=hbuf, ne=ne, stream=stream),
+            "hessian_split": lambda: g.density_hessian(P, prec="split", n=n, grad=gbuf, hess=hbuf, ne=ne, stream=stream),
             "h_with_tau_split": lambda: g.integrate_h_tau(v, vtau, prec="split", H=H, stream=stream),
             "pulay_matrices_fp64": lambda: g.pulay_matrices(v, prec="fp64", M=mbuf, S=sbuf, stream=stream),
+            "pulay_matrices_fp32": lambda: g.pulay_matrices(v, prec="fp32", M=mbuf, S=sbuf, stream=stream),
         }
         for name, call in calls.items():
             try:

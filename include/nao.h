@@ -281,12 +281,15 @@ nao_status nao_update_density_gradient_many(nao_grid *g, const double *const *P_
  * forces and stresses):
  *     d_a d_b n(r_p) = 2 sum_ij P_ij (phi_i d_a d_b phi_j + d_a phi_i d_b phi_j)   (P symmetric),
  * from the basis functions' second derivatives and the four products Phi P, (d_a Phi) P over all
- * of P, in FP64. hess_dev: device [6 * n_points], component-major in the order xx, xy, xz, yy,
- * yz, zz, original point order; n_dev, grad_dev and n_electrons_dev as
- * nao_update_density_gradient. Single-system handles only (grouped: NAO_ERR_INVALID_ARG);
- * NAO_FP64 only (NAO_FP32, NAO_SPLIT: NAO_ERR_UNSUPPORTED). A batch whose 10-row evaluation
- * (N_b x 10 Ppad FP64) exceeds the evaluation scratch returns NAO_ERR_UNSUPPORTED (raise
- * scratch_bytes).                                                                              */
+ * of P. NAO_FP64: everything in FP64; NAO_FP32: the derivatives are computed in FP64 and
+ * rounded once to FP32, the products and the per-tile epilogue run in FP32 (about 1e-6 of the
+ * magnitude sums); NAO_SPLIT: the derivatives in FP64, the four products as Ozaki slice products
+ * on the tensor cores (the handle's slice count and digit format; four passes, P' sliced once),
+ * epilogues in FP64 (about 1e-12 of the magnitude sums). hess_dev: device [6 * n_points],
+ * component-major in the order xx, xy, xz, yy, yz, zz, original point order; n_dev, grad_dev and
+ * n_electrons_dev as nao_update_density_gradient. Single-system handles only (grouped:
+ * NAO_ERR_INVALID_ARG). A batch whose 10-row evaluation (N_b x 10 Ppad values) exceeds the
+ * evaluation scratch returns NAO_ERR_UNSUPPORTED (raise scratch_bytes).                                                                              */
 nao_status nao_update_density_hessian(nao_grid *g, const double *P_dev, nao_precision prec, double *n_dev,
                                       double *grad_dev, double *hess_dev, double *n_electrons_dev, void *cuda_stream);
 
@@ -295,9 +298,10 @@ nao_status nao_update_density_hessian(nao_grid *g, const double *P_dev, nao_prec
  * matrix elements with basis-function indices as the paper describes for forces:
  *     M_dev[c*nb*nb + i*nb + j] = sum_p w_p d_c phi_i(r_p) (-1/2 lap + v_p) phi_j(r_p),
  *     S_dev[c*nb*nb + i*nb + j] = sum_p w_p d_c phi_i(r_p) phi_j(r_p),        c = x, y, z,
- * (not symmetric; both overwritten) from the basis functions' second derivatives, in FP64.
- * v_dev: device [n_points] original order, or NULL for v = 1. Single-system handles; NAO_FP64
- * only (others: NAO_ERR_UNSUPPORTED); scratch rules as nao_update_density_hessian.
+ * (not symmetric; both overwritten) from the basis functions' second derivatives, in FP64
+ * (NAO_FP64) or with the derivatives rounded once to FP32 and the products in FP32 (NAO_FP32;
+ * NAO_SPLIT: NAO_ERR_UNSUPPORTED). v_dev: device [n_points] original order, or NULL for v = 1.
+ * Single-system handles; scratch rules as nao_update_density_hessian.
  * nao_pulay_forces: F_dev[3*a + c] = 2 sum_{i on atom a} sum_j (n_ij M^c_ij - q_ij S^c_ij)
  * (grad_at phi_i = -grad phi_i for a function on atom a), n_dev and q_dev device [nb*nb]
  * row-major, F_dev device [3*n_atoms], overwritten.                                            */

@@ -514,7 +514,8 @@ nao_status build(nao_grid *g, const nao_system_desc *descs, int32_t n_sys, const
     std::vector<double> coef((size_t)g->n_fn * (nr - 1) * 4);
     for (int f = 0; f < g->n_fn; f++)
         nao_spline_coefficients(fn_tab.data() + (size_t)f * nr, nr, coef.data() + (size_t)f * (nr - 1) * 4);
-    std::vector<float> coef32(coef.begin(), coef.end());
+    std::vector<float> coef32(coef.begin(), coef.end()), coef_lo(coef.size());
+    for (size_t q = 0; q < coef.size(); q++) coef_lo[q] = (float)(coef[q] - (double)coef32[q]);
     // Segments whose cubic is ill-conditioned (coefficient magnitudes above 4x the smaller end
     // value, or above 4x the smaller end slope: the decaying tails of steep functions, the
     // approach to the cutoff, extrema) lose more than a few FP32 ulps to cancellation; the FP32
@@ -587,7 +588,7 @@ nao_status build(nao_grid *g, const nao_system_desc *descs, int32_t n_sys, const
     }
 
     double *d_coef, *d_rc;
-    float *d_coef32;
+    float *d_coef32, *d_coef_lo;
     double *d_inv_rk;
     int32_t *d_rel_off, *d_rel_idx, *d_rfn_off;
     RfnEntry *d_rfn;
@@ -596,6 +597,7 @@ nao_status build(nao_grid *g, const nao_system_desc *descs, int32_t n_sys, const
     int64_t *d_scr_off;
     uint8_t *d_seg64;
     if ((st = upload(g, &d_coef, coef.data(), coef.size())) || (st = upload(g, &d_coef32, coef32.data(), coef32.size())) ||
+        (st = upload(g, &d_coef_lo, coef_lo.data(), coef_lo.size())) ||
         (st = upload(g, &d_seg64, seg64.data(), seg64.size())) ||
         (st = upload(g, &d_inv_rk, inv_rk.data(), inv_rk.size())) ||
         (st = upload(g, &d_rc, fn_cut.data(), fn_cut.size())) ||
@@ -639,6 +641,7 @@ nao_status build(nao_grid *g, const nao_system_desc *descs, int32_t n_sys, const
     s.atom_xyz = d_atoms;
     s.coef = d_coef;
     s.coef_f32 = d_coef32;
+    s.coef_lo = d_coef_lo;
     s.inv_rk = d_inv_rk;
     s.seg64 = d_seg64;
     s.fn_rc = d_rc;
@@ -682,6 +685,8 @@ nao_status build(nao_grid *g, const nao_system_desc *descs, int32_t n_sys, const
                 if (m > 0) k *= std::sqrt(2.0);
             }
             s.knorm[l][m] = k;
+            s.knorm_h[l][m] = (float)k;
+            s.knorm_l[l][m] = (float)(k - (double)s.knorm_h[l][m]);
         }
     NAO_CUDA(cudaStreamSynchronize(g->setup));
     return NAO_OK;
@@ -735,6 +740,7 @@ int default_tn(int S, int F) { return nao_split_tn(S, F); }
 // density items (batch, 128-point tile, number of TN-function tiles).
 nao_status split_lists(nao_grid *g) {
     const int S = g->split_S, F = g->split_F;
+    g->split_lists_ver++;
     std::vector<HWork> hw[2], nw[2];
     for (auto &c : g->split_chunks) {
         for (int k = 0; k < 2; k++) {
@@ -930,7 +936,7 @@ nao_status split_tune(nao_grid *g, uint32_t terms, cudaStream_t st) {
         bool any = false;
         for (int32_t b = c.b0; b < c.b1; b++) any = any || (bucket[b] >= 0 && !choice[bucket[b]]);
         if (!any) continue;
-        cudaError_t ce = launch_eval(s, c.b0, c.b1, NAO_FP64, true, g->d_scratch, st);
+        cudaError_t ce = launch_eval(s, c.b0, c.b1, NAO_SPLIT, true, g->d_scratch, st);
         if (ce == cudaSuccess)
             ce = launch_slice_h(s, c.b0, c.b1, c.max_rt, g->d_scratch, terms, g->d_slices, g->d_sl_off_h, g->d_expo_h,
                                 g->d_neg16, S, g->split_F, st);
@@ -1044,7 +1050,7 @@ nao_status enqueue_h(nao_grid *g, uint32_t terms, nao_precision prec, cudaStream
     if (prec == NAO_SPLIT) {
         const int S = g->split_S;
         for (const auto &c : g->split_chunks) {
-            NAO_CUDA(timed(g, NAO_K_EVAL_GRAD, st, [&] { return launch_eval(s, c.b0, c.b1, NAO_FP64, true, g->d_scratch, st); }));
+            NAO_CUDA(timed(g, NAO_K_EVAL_GRAD, st, [&] { return launch_eval(s, c.b0, c.b1, NAO_SPLIT, true, g->d_scratch, st); }));
             NAO_CUDA(timed(g, NAO_K_SLICE, st, [&] {
                 return launch_slice_h(s, c.b0, c.b1, c.max_rt, g->d_scratch, terms, g->d_slices, g->d_sl_off_h,
                                       g->d_expo_h, g->d_neg16, S, g->split_F, st);
@@ -1250,6 +1256,19 @@ static nao_status create(const nao_system_desc *descs, int32_t n_sys, const int3
     }
     DeviceGuard guard(dev);
     if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
+    // Per-thread stack of this process's context: the evaluation kernels' frames (their per-l
+    // evaluation functions are calls, not inlined) reach about 1 KB, the default limit; the
+    // limit is raised to kStackBytes if it is lower (a limit of this context only, which ends
+    // with the process).
+    {
+        constexpr size_t kStackBytes = 2048;
+        size_t cur = 0;
+        if (cudaDeviceGetLimit(&cur, cudaLimitStackSize) != cudaSuccess ||
+            (cur < kStackBytes && cudaDeviceSetLimit(cudaLimitStackSize, kStackBytes) != cudaSuccess)) {
+            cudaGetLastError();
+            return fail(NAO_ERR_CUDA, "cannot set the per-thread stack size");
+        }
+    }
     nao_grid *g = new (std::nothrow) nao_grid();
     if (!g) return fail(NAO_ERR_OUT_OF_MEMORY, "host allocation failed");
     g->device = dev;
@@ -1508,6 +1527,65 @@ nao_status nao_update_density_gradient(nao_grid *g, const double *P_dev, nao_pre
     return nao_update_density_gradient_many(g, &P_dev, prec, &n_dev, &grad_dev, ne, cuda_stream);
 }
 
+// Split-path density Hessian plan (after split_setup and hess_plan): every non-empty
+// intersection of a Hessian chunk (the 10-row FP64 evaluation) with a split chunk (the slices),
+// its slicing grid extents and its density work items (all function tiles per 128-point tile,
+// heaviest first, per tile width), and the four point-exponent arrays.
+nao_status hess_split_plan(nao_grid *g) {
+    if (g->hess_split_ver == g->split_lists_ver && !g->hess_split.empty()) return NAO_OK;
+    const int S = g->split_S, F = g->split_F;
+    g->hess_split.clear();
+    std::vector<HWork> nw[2];
+    for (const auto &hc : g->hess_chunks)
+        for (const auto &sc : g->split_chunks) {
+            const int32_t lo = std::max(hc.b0, sc.b0), hi = std::min(hc.b1, sc.b1);
+            if (lo >= hi) continue;
+            nao_grid::HessSplitSub sub{lo, hi, 0, 0, {0, 0}, {0, 0}};
+            for (int k = 0; k < 2; k++) sub.nw0[k] = (int32_t)nw[k].size();
+            for (int32_t b = lo; b < hi; b++) {
+                const int P = g->Pb[b], N = g->Nb[b];
+                if (N == 0) continue;
+                const int TN = g->split_tn[b], k = TN == 48 ? 0 : 1;
+                const SplitGeom G(P, N, S, TN, F);
+                sub.max_qt = std::max<int32_t>(sub.max_qt, G.n_qt);
+                sub.max_rt = std::max<int32_t>(sub.max_rt, G.h_slice_tiles());
+                for (int Q = 0; Q < G.n_qt; Q++) nw[k].push_back({b, Q, G.n_jtN, 0});
+            }
+            for (int k = 0; k < 2; k++) {
+                std::stable_sort(nw[k].begin() + sub.nw0[k], nw[k].end(),
+                                 [](const HWork &x, const HWork &y) { return x.tj > y.tj; });
+                sub.nw1[k] = (int32_t)nw[k].size();
+            }
+            g->hess_split.push_back(sub);
+        }
+    for (auto &sub : g->hess_split) {
+        sub.nw0[1] += (int32_t)nw[0].size();
+        sub.nw1[1] += (int32_t)nw[0].size();
+    }
+    nw[0].insert(nw[0].end(), nw[1].begin(), nw[1].end());
+    nao_status st;
+    if ((int64_t)nw[0].size() > g->cap_hess_nw) {
+        if (g->d_hess_nw) {
+            NAO_CUDA(cudaStreamSynchronize(g->setup));
+            g->d_hess_nw = nullptr;  // the old list stays in g->allocs until the handle is destroyed
+        }
+        if ((st = dev_alloc(g, &g->d_hess_nw, std::max<size_t>(nw[0].size(), 1)))) {
+            g->hess_split.clear();
+            return st;
+        }
+        g->cap_hess_nw = (int64_t)std::max<size_t>(nw[0].size(), 1);
+    }
+    if (!g->d_expo4 && (st = dev_alloc(g, &g->d_expo4, 4 * (size_t)std::max<int64_t>(g->n_points, 1)))) {
+        g->hess_split.clear();
+        return st;
+    }
+    if (!nw[0].empty())
+        NAO_CUDA(copy_async(g->d_hess_nw, nw[0].data(), nw[0].size() * sizeof(HWork), cudaMemcpyHostToDevice, g->setup));
+    NAO_CUDA(cudaStreamSynchronize(g->setup));
+    g->hess_split_ver = g->split_lists_ver;
+    return NAO_OK;
+}
+
 nao_status nao_update_density_hessian(nao_grid *g, const double *P_dev, nao_precision prec, double *n_dev,
                                       double *grad_dev, double *hess_dev, double *n_electrons_dev, void *cuda_stream) {
     nao_status st = check_handle(g);
@@ -1515,11 +1593,12 @@ nao_status nao_update_density_hessian(nao_grid *g, const double *P_dev, nao_prec
     if (!P_dev || !n_dev || !grad_dev || !hess_dev)
         return fail(NAO_ERR_INVALID_ARG, "P_dev, n_dev, grad_dev or hess_dev is NULL");
     if ((st = check_prec(prec))) return st;
-    if (prec != NAO_FP64) return fail(NAO_ERR_UNSUPPORTED, "the density Hessian is built on the FP64 path only");
     DeviceGuard guard(g->device);
     if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
     CallEnd call_end(g, static_cast<cudaStream_t>(cuda_stream));
+    if (prec == NAO_SPLIT && (st = split_setup(g))) return st;
     if ((st = hess_plan(g))) return st;
+    if (prec == NAO_SPLIT && (st = hess_split_plan(g))) return st;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     set_tab(g, 2, 0, P_dev);
     set_tab(g, 3, 0, n_dev);
@@ -1527,10 +1606,40 @@ nao_status nao_update_density_hessian(nao_grid *g, const double *P_dev, nao_prec
     set_tab(g, 5, 0, grad_dev);
     if ((st = upload_tables(g, 2, 4, s))) return st;
     const DevSystem &sys = g->sys;
+    if (prec == NAO_SPLIT) {
+        // points of batches without basis functions get zeros; every other point is written by
+        // the first pass and completed by the three later ones
+        NAO_CUDA(cudaMemsetAsync(hess_dev, 0, 6 * (size_t)g->n_points * sizeof(double), s));
+        NAO_CUDA(launch_zero_n(sys, g->d_dwork, (int32_t)g->n_dwork, true, s));
+        const int S = g->split_S, F = g->split_F;
+        size_t k_sub = 0;
+        for (const auto &c : g->hess_chunks) {
+            NAO_CUDA(launch_eval_hess(sys, c.b0, c.b1, g->d_scratch, false, false, g->d_hess_off, s));
+            NAO_CUDA(launch_hess_point_expo(sys, c.b0, c.b1, g->d_scratch, g->d_hess_off, g->d_expo4, g->n_points, s));
+            for (; k_sub < g->hess_split.size() && g->hess_split[k_sub].b0 < c.b1; k_sub++) {
+                const auto &sub = g->hess_split[k_sub];
+                for (int comp = 0; comp < 4; comp++) {
+                    const int32_t *eq = g->d_expo4 + (size_t)comp * (size_t)g->n_points;
+                    NAO_CUDA(launch_slice_n_hess(sys, sub.b0, sub.b1, sub.max_qt, sub.max_rt, g->d_scratch,
+                                                 g->d_hess_off, comp, g->d_slices, g->d_sl_off_n, eq, g->d_expo_b,
+                                                 g->d_split_tn, S, F, s));
+                    for (int k = 0; k < 2; k++)
+                        NAO_CUDA(launch_n_tc_hess(sys, g->d_hess_nw, sub.nw0[k], sub.nw1[k] - sub.nw0[k], g->d_slices,
+                                                  g->d_sl_off_n, eq, g->d_expo_b, g->d_scratch, g->d_hess_off, comp,
+                                                  hess_dev, S, F, k == 0 ? 48 : 32, g->d_err, s));
+                }
+            }
+        }
+        if (n_electrons_dev) {
+            NAO_CUDA(launch_wn_partial(sys, g->d_dwork, 0, (int32_t)g->n_dwork, g->d_ne_part, s));
+            NAO_CUDA(launch_reduce_ne(sys, g->d_ne_part, g->d_sys_dw0, g->n_sys, s));
+        }
+        return mark_done(g, s);
+    }
     for (const auto &c : g->hess_chunks) {
-        NAO_CUDA(launch_eval_hess(sys, c.b0, c.b1, g->d_scratch, g->d_hess_off, s));
-        NAO_CUDA(launch_density_hess(sys, g->d_dwork, c.dw0, c.dw1 - c.dw0, g->d_scratch, g->d_hess_off, hess_dev,
-                                     g->d_ne_part, s));
+        NAO_CUDA(launch_eval_hess(sys, c.b0, c.b1, g->d_scratch, prec == NAO_FP32, false, g->d_hess_off, s));
+        NAO_CUDA(launch_density_hess(sys, g->d_dwork, c.dw0, c.dw1 - c.dw0, g->d_scratch, prec == NAO_FP32,
+                                     g->d_hess_off, hess_dev, g->d_ne_part, s));
     }
     if (n_electrons_dev) NAO_CUDA(launch_reduce_ne(sys, g->d_ne_part, g->d_sys_dw0, g->n_sys, s));
     return mark_done(g, s);
@@ -1542,7 +1651,8 @@ nao_status nao_pulay_matrices(nao_grid *g, const double *v_dev, nao_precision pr
     if (st || (st = check_single(g))) return st;
     if (!M_dev || !S_dev) return fail(NAO_ERR_INVALID_ARG, "M_dev or S_dev is NULL");
     if ((st = check_prec(prec))) return st;
-    if (prec != NAO_FP64) return fail(NAO_ERR_UNSUPPORTED, "the Pulay matrix elements are built on the FP64 path only");
+    if (prec == NAO_SPLIT)
+        return fail(NAO_ERR_UNSUPPORTED, "the Pulay matrix elements are built on the FP64 and FP32 paths only");
     DeviceGuard guard(g->device);
     if (!guard.ok) return fail(NAO_ERR_CUDA, "cannot select the device");
     CallEnd call_end(g, static_cast<cudaStream_t>(cuda_stream));
@@ -1556,9 +1666,9 @@ nao_status nao_pulay_matrices(nao_grid *g, const double *v_dev, nao_precision pr
     const DevSystem &sys = g->sys;
     for (size_t k = 0; k < g->hess_chunks.size(); k++) {
         const auto &c = g->hess_chunks[k];
-        NAO_CUDA(launch_eval_hess(sys, c.b0, c.b1, g->d_scratch, g->d_hess_off, s));
+        NAO_CUDA(launch_eval_hess(sys, c.b0, c.b1, g->d_scratch, prec == NAO_FP32, true, g->d_hess_off, s));
         NAO_CUDA(launch_pulay(sys, g->d_pulay_work, g->pulay_w0[k], g->pulay_w0[k + 1] - g->pulay_w0[k], g->d_scratch,
-                              g->d_hess_off, M_dev, S_dev, g->nb, s));
+                              prec == NAO_FP32, g->d_hess_off, M_dev, S_dev, g->nb, s));
     }
     return mark_done(g, s);
 }

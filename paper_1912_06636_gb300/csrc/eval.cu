@@ -16,6 +16,7 @@
 #include <cmath>
 #include <type_traits>
 
+#include "ff.h"
 #include "nao_internal.h"
 #include "split_bits.h"
 
@@ -295,11 +296,210 @@ __device__ __noinline__ void eval_group(const DevSystem &s, const AtomGroup &ag,
     }
 }
 
+// ----------------------------------------------------------------------------------------
+// The split path's evaluation in float-float arithmetic (csrc/ff.h): the same quantities and
+// recurrences as eval_group, with FP64 kept for the geometry (d, r^2, 1/r) and the radial
+// coordinate t (segment choice and log1p), converted once; everything that follows (the
+// solid-harmonic recurrence, the spline, the products) runs on the FP32 pipe with ~48-bit
+// significands. Results are stored as float-float pairs (FF2). Points within kNearNucleus of
+// the atom, and atoms with functions of l >= 5, take eval_group in FP64 instead.
+// ----------------------------------------------------------------------------------------
+__device__ __forceinline__ ffa::F ff_zero() { return ffa::F{0.0f, 0.0f}; }
+__device__ __forceinline__ ffa::F ff_of(float h) { return ffa::F{h, 0.0f}; }
+
+// A rational constant a / b (small integers) as a float-float: folded by the compiler once the
+// loops over l and m are unrolled.
+__device__ __forceinline__ ffa::F ff_ratio(int a, int b) {
+    const double c = (double)a / (double)b;
+    const float h = (float)c;
+    return ffa::F{h, (float)(c - (double)h)};
+}
+
+// Biased FP64 exponent of an upper bound of |v| (0: v is taken as zero): the exponent of v.h,
+// plus one when v.h's significand is within 2^-15 of 2 (v.l may then carry |v| into the next
+// binade). Subnormal v.h (|v| < 2^-126) counts as zero.
+__device__ __forceinline__ int ff_bound_eb(ffa::F v) {
+    const int b = __float_as_int(v.h) & 0x7FFFFFFF;
+    const int e = b >> 23;
+    if (e == 0) return 0;
+    return e + 896 + ((b & 0x7FFFFF) >= 0x7FFF00 ? 1 : 0);
+}
+
+template <typename OutT>
+__device__ __forceinline__ OutT ff_out(ffa::F v) {
+    if constexpr (std::is_same<OutT, FF2>::value) return FF2(v);
+    else return OutT(ffa::to_double(v));
+}
+
+template <int LMAX, bool GRAD, typename OutT, int EXPO>
+__device__ __noinline__ void eval_group_ff(const DevSystem &s, const AtomGroup &ag, double dx, double dy, double dz,
+                                          double r2, double r, double ur, const EvalOut<OutT> &o, int q, ExpoIn xi) {
+    using ffa::F;
+    // radial coordinate in FP64, as eval_group<double>
+    const double rr = fmax(r, s.r0);
+    const float sa = __logf((float)rr * (float)__ldg(s.inv_rk)) * (float)s.inv_delta;
+    int k = (int)floorf(sa);
+    k = k < 0 ? 0 : (k > s.n_rgrid - 2 ? s.n_rgrid - 2 : k);
+    double xr = fma(rr, __ldg(s.inv_rk + k), -1.0);
+    if (xr < 0.0 && k > 0) {
+        k--;
+        xr = fma(rr, __ldg(s.inv_rk + k), -1.0);
+    } else if (xr >= s.step_m1 && k < s.n_rgrid - 2) {
+        k++;
+        xr = fma(rr, __ldg(s.inv_rk + k), -1.0);
+    }
+    const F t = ffa::from_double(log1p_small(xr, s.step_m1) * s.inv_delta);
+    const F dr_scale = ffa::from_double(s.inv_delta * (r < s.r0 ? __ldg(s.inv_rk) : ur));
+    const F u = ffa::from_double(ur);
+    const F x = ffa::from_double(dx), y = ffa::from_double(dy), z = ffa::from_double(dz);
+    const F qq = ffa::from_double(r2);
+    const F x2 = ffa::twice(x), y2 = ffa::twice(y), z2 = ffa::twice(z);
+    // A_m + i B_m = (x + i y)^m
+    F A[LMAX + 1], B[LMAX + 1];
+    A[0] = ff_of(1.0f);
+    B[0] = ff_zero();
+#pragma unroll
+    for (int m = 1; m <= LMAX; m++) {
+        if (m == 1) {
+            A[1] = x;
+            B[1] = y;
+        } else {
+            A[m] = ffa::dot2(x, A[m - 1], ffa::neg(y), B[m - 1]);
+            B[m] = ffa::dot2(x, B[m - 1], y, A[m - 1]);
+        }
+    }
+    // Pi_{l-1}^m (c) and Pi_{l-2}^m (p) with their z and r^2 derivatives (see eval_group)
+    F Pc[LMAX + 1], Pcz[LMAX + 1], Pcq[LMAX + 1], Pp[LMAX + 1], Ppz[LMAX + 1], Ppq[LMAX + 1];
+#pragma unroll
+    for (int m = 0; m <= LMAX; m++) Pc[m] = Pcz[m] = Pcq[m] = Pp[m] = Ppz[m] = Ppq[m] = ff_zero();
+    int ri = ag.r0;
+    const int re = ag.r0 + ag.nr;
+    int pt_eb = 0;
+    F ul = ff_of(1.0f);  // u^l
+#pragma unroll
+    for (int l = 0; l <= LMAX; l++) {
+        F S[2 * LMAX + 1], Gx[2 * LMAX + 1], Gy[2 * LMAX + 1], Gz[2 * LMAX + 1];
+        bool zx[2 * LMAX + 1], zy[2 * LMAX + 1], zz[2 * LMAX + 1];
+#pragma unroll
+        for (int m = 0; m <= l; m++) {
+            F p, pz = ff_zero(), pq = ff_zero();
+            const bool zpz = (m == l), zpq = (l - m < 2);
+            if (m == l) {
+                p = ff_of((float)double_factorial_odd(m));  // an odd integer below 2^24: exact
+            } else if (m == l - 1) {
+                p = ffa::mulf(ffa::mul(z, Pc[m]), (float)(2 * m + 1));
+                pz = ffa::mulf(Pc[m], (float)(2 * m + 1));
+            } else {
+                const F c1 = ff_ratio(2 * l - 1, l - m), c2 = ff_ratio(l + m - 1, l - m);
+                const F nc2 = ffa::neg(c2);
+                p = ffa::dot2(c1, ffa::mul(z, Pc[m]), nc2, ffa::mul(qq, Pp[m]));
+                pz = ffa::mul(c1, ffa::fma(z, Pcz[m], Pc[m]));
+                if (l - 2 != m) pz = ffa::fma(nc2, ffa::mul(qq, Ppz[m]), pz);
+                const F pq_p = (l - 2 - m >= 2) ? ffa::fma(qq, Ppq[m], Pp[m]) : Pp[m];
+                pq = (l - 1 - m >= 2) ? ffa::dot2(c1, ffa::mul(z, Pcq[m]), nc2, pq_p) : ffa::mul(nc2, pq_p);
+            }
+            Pp[m] = Pc[m]; Ppz[m] = Pcz[m]; Ppq[m] = Pcq[m];
+            Pc[m] = p; Pcz[m] = pz; Pcq[m] = pq;
+            const F kn = ffa::F{s.knorm_h[l][m], s.knorm_l[l][m]};
+            const F kp = ffa::mul(kn, p);
+            const F kpq = zpq ? ff_zero() : ffa::mul(kn, pq);
+            const F kdx = zpq ? ff_zero() : ffa::mul(x2, kpq), kdy = zpq ? ff_zero() : ffa::mul(y2, kpq);
+            const F kdz = zpz ? (zpq ? ff_zero() : ffa::mul(z2, kpq))
+                              : (zpq ? ffa::mul(kn, pz) : ffa::fma(z2, kpq, ffa::mul(kn, pz)));
+            const bool zdz = zpz && zpq;
+            if (m == 0) {
+                S[l] = kp;
+                Gx[l] = kdx;
+                Gy[l] = kdy;
+                Gz[l] = kdz;
+                zx[l] = zy[l] = zpq;
+                zz[l] = zdz;
+            } else {
+                const F kpf = ffa::mulf(kp, (float)m);
+                S[l + m] = ffa::mul(kp, A[m]);
+                Gx[l + m] = zpq ? ffa::mul(kpf, A[m - 1]) : ffa::dot2(kdx, A[m], kpf, A[m - 1]);
+                Gy[l + m] = m == 1 ? (zpq ? ff_zero() : ffa::mul(kdy, A[m]))
+                                   : (zpq ? ffa::neg(ffa::mul(kpf, B[m - 1])) : ffa::dot2(kdy, A[m], ffa::neg(kpf), B[m - 1]));
+                Gz[l + m] = zdz ? ff_zero() : ffa::mul(kdz, A[m]);
+                S[l - m] = ffa::mul(kp, B[m]);
+                Gx[l - m] = m == 1 ? (zpq ? ff_zero() : ffa::mul(kdx, B[m]))
+                                   : (zpq ? ffa::mul(kpf, B[m - 1]) : ffa::dot2(kdx, B[m], kpf, B[m - 1]));
+                Gy[l - m] = zpq ? ffa::mul(kpf, A[m - 1]) : ffa::dot2(kdy, B[m], kpf, A[m - 1]);
+                Gz[l - m] = zdz ? ff_zero() : ffa::mul(kdz, B[m]);
+                zx[l + m] = false;
+                zy[l + m] = (m == 1 && zpq);
+                zz[l + m] = zz[l - m] = zdz;
+                zx[l - m] = (m == 1 && zpq);
+                zy[l - m] = false;
+            }
+        }
+        const F ulu = ffa::mul(ul, u);                       // u^(l+1)
+        const F a_dr = ffa::mul(dr_scale, ulu);               // dR/ds -> g'(r)/r
+        const F a_r = ffa::mulf(ffa::mul(u, ulu), (float)l);  // R -> the l R / r part of g'(r)/r
+        for (; ri < re; ri++) {
+            const RfnEntry e = s.rfn[ri];
+            if (e.l != l) break;
+            OutT fo[2 * LMAX + 1], xo[2 * LMAX + 1], yo[2 * LMAX + 1], zo[2 * LMAX + 1];
+            if (r < s.fn_rc[e.fn]) {
+                const size_t seg = (size_t)e.fn * (s.n_rgrid - 1) + k;
+                const float4 ch = __ldg(reinterpret_cast<const float4 *>(s.coef_f32 + seg * 4));
+                const float4 cl = __ldg(reinterpret_cast<const float4 *>(s.coef_lo + seg * 4));
+                const F c0{ch.x, cl.x}, c1{ch.y, cl.y}, c2{ch.z, cl.z}, c3{ch.w, cl.w};
+                // R = c0 + t (c1 + t a), dR/dt = c1 + t (2 a + c3 t), a = c2 + c3 t
+                const F a = ffa::fma(c3, t, c2);
+                const F R = ffa::fma(ffa::fma(a, t, c1), t, c0);
+                const F dRds = ffa::fma(ffa::fma(c3, t, ffa::twice(a)), t, c1);
+                const F g = ffa::mul(R, ul);
+                const F gpu = l == 0 ? ffa::mul(dRds, a_dr) : ffa::dot2(dRds, a_dr, ffa::neg(R), a_r);
+                const F gx = ffa::mul(gpu, x), gy = ffa::mul(gpu, y), gz = ffa::mul(gpu, z);
+#pragma unroll
+                for (int m = 0; m < 2 * l + 1; m++) {
+                    const F fv = ffa::mul(g, S[m]);
+                    if constexpr (EXPO == 1) pt_eb = max(pt_eb, ff_bound_eb(fv));
+                    fo[m] = ff_out<OutT>(fv);
+                    if (GRAD) {
+                        xo[m] = ff_out<OutT>(zx[m] ? ffa::mul(gx, S[m]) : ffa::dot2(gx, S[m], g, Gx[m]));
+                        yo[m] = ff_out<OutT>(zy[m] ? ffa::mul(gy, S[m]) : ffa::dot2(gy, S[m], g, Gy[m]));
+                        zo[m] = ff_out<OutT>(zz[m] ? ffa::mul(gz, S[m]) : ffa::dot2(gz, S[m], g, Gz[m]));
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < 2 * l + 1; m++) fo[m] = xo[m] = yo[m] = zo[m] = OutT(0);
+            }
+            store_rows(o, e.pos, 2 * l + 1, q, fo, xo, yo, zo, GRAD);
+        }
+        ul = ffa::mul(ul, u);
+    }
+    if constexpr (EXPO == 1) {
+        if (pt_eb > 0) atomicMax(xi.red + q, pt_eb);
+    }
+}
+
+// Arithmetic of the split path's evaluation: float-float (eval_group_ff), stored as FF2.
+struct FFTag {};
+template <typename T>
+struct out_of {
+    using type = T;
+};
+template <>
+struct out_of<FFTag> {
+    using type = FF2;
+};
+
 template <int LMAX, bool GRAD, typename T, int EXPO, typename OutT>
 __device__ __forceinline__ void eval_group_dispatch(const DevSystem &s, const AtomGroup &ag, double dx, double dy,
                                                     double dz, double r2, double r, double ur, const EvalOut<OutT> &o, int q,
                                                     const ExpoIn &xi) {
-    if constexpr (EXPO != 0 || std::is_same<T, double>::value)
+    if constexpr (std::is_same<T, FFTag>::value) {
+        // float-float up to l = 4; atoms with g functions and beyond, and points near a nucleus,
+        // in FP64 (instantiating the float-float code for l = 5, 6 would take the kernels' stack
+        // frames above 1 KB)
+        if (LMAX > 4 || r < kNearNucleus)
+            eval_group<LMAX, double, GRAD, OutT, EXPO>(s, ag, dx, dy, dz, r2, r, ur, o, q, xi);
+        else
+            eval_group_ff<LMAX < 4 ? LMAX : 4, GRAD, OutT, EXPO>(s, ag, dx, dy, dz, r2, r, ur, o, q, xi);
+    } else if constexpr (EXPO != 0 || std::is_same<T, double>::value)
         eval_group<LMAX, double, GRAD, OutT, EXPO>(s, ag, dx, dy, dz, r2, r, ur, o, q, xi);
     else if (r < kNearNucleus)
         eval_group<LMAX, double, GRAD, OutT, 0>(s, ag, dx, dy, dz, r2, r, ur, o, q, xi);
@@ -369,18 +569,20 @@ __device__ __forceinline__ EvalOut<T> batch_out(const DevSystem &s, int b, int P
 // One CTA per batch; the batch's block of scratch holds, per reduced-basis row j,
 // [phi | d/dx | d/dy | d/dz] over Ppad points each (GRAD) or phi alone, in type T.
 template <bool GRAD, typename T>
-__global__ void __launch_bounds__(256) eval_chunk_kernel(DevSystem s, int32_t b0, T *scratch) {
+__global__ void __launch_bounds__(256) eval_chunk_kernel(DevSystem s, int32_t b0, typename out_of<T>::type *scratch) {
+    using OutT = typename out_of<T>::type;
     const int b = b0 + blockIdx.x;
     const int P = s.batch_off[b + 1] - s.batch_off[b];
     const int Ppad = (P + NAO_PPAD - 1) & ~(NAO_PPAD - 1);
-    eval_batch<GRAD, T, 0>(s, b, batch_out<GRAD, T>(s, b, Ppad, scratch));
+    eval_batch<GRAD, T, 0>(s, b, batch_out<GRAD, OutT>(s, b, Ppad, scratch));
 }
 
-// The density's evaluation on the split path (FP64): as eval_chunk_kernel, and the point
-// exponents of the slicing: expo[batch_off[b] + q] = the exponent of point q, from the binade of
-// max_i |phi_iq| (split_bits::exponent_of_binade). Dynamic shared memory: n_red >= P_b ints.
+// The density's evaluation on the split path (float-float, FF2 values): as eval_chunk_kernel,
+// and the point exponents of the slicing: expo[batch_off[b] + q] = the exponent of point q, from
+// the binade of an upper bound of max_i |phi_iq| (split_bits::exponent_of_binade). Dynamic shared
+// memory: n_red >= P_b ints.
 template <bool GRAD>
-__global__ void __launch_bounds__(256) eval_split_kernel(DevSystem s, int32_t b0, double *scratch, int32_t *expo,
+__global__ void __launch_bounds__(256) eval_split_kernel(DevSystem s, int32_t b0, FF2 *scratch, int32_t *expo,
                                                          int n_red) {
     extern __shared__ int red_sh[];
     const int b = b0 + blockIdx.x;
@@ -388,7 +590,7 @@ __global__ void __launch_bounds__(256) eval_split_kernel(DevSystem s, int32_t b0
     const int Ppad = (P + NAO_PPAD - 1) & ~(NAO_PPAD - 1);
     for (int i = threadIdx.x; i < n_red; i += blockDim.x) red_sh[i] = 0;
     __syncthreads();
-    eval_batch<GRAD, double, 1>(s, b, batch_out<GRAD, double>(s, b, Ppad, scratch), red_sh);
+    eval_batch<GRAD, FFTag, 1>(s, b, batch_out<GRAD, FF2>(s, b, Ppad, scratch), red_sh);
     __syncthreads();
     for (int q = threadIdx.x; q < P; q += blockDim.x) expo[p0 + q] = split_bits::exponent_of_binade(red_sh[q]);
 }
@@ -424,6 +626,10 @@ cudaError_t launch_eval(const DevSystem &s, int32_t b0, int32_t b1, nao_precisio
         float *f = reinterpret_cast<float *>(scratch);
         if (grad) eval_chunk_kernel<true, float><<<b1 - b0, 256, 0, st>>>(s, b0, f);
         else eval_chunk_kernel<false, float><<<b1 - b0, 256, 0, st>>>(s, b0, f);
+    } else if (prec == NAO_SPLIT) {
+        FF2 *f = reinterpret_cast<FF2 *>(scratch);
+        if (grad) eval_chunk_kernel<true, FFTag><<<b1 - b0, 256, 0, st>>>(s, b0, f);
+        else eval_chunk_kernel<false, FFTag><<<b1 - b0, 256, 0, st>>>(s, b0, f);
     } else {
         if (grad) eval_chunk_kernel<true, double><<<b1 - b0, 256, 0, st>>>(s, b0, scratch);
         else eval_chunk_kernel<false, double><<<b1 - b0, 256, 0, st>>>(s, b0, scratch);
@@ -435,8 +641,9 @@ cudaError_t launch_eval_split(const DevSystem &s, int32_t b0, int32_t b1, bool g
                               int32_t n_red, cudaStream_t st) {
     if (b1 <= b0) return cudaSuccess;
     const size_t smem = (size_t)n_red * 4;
-    if (grad) eval_split_kernel<true><<<b1 - b0, 256, smem, st>>>(s, b0, scratch, expo, n_red);
-    else eval_split_kernel<false><<<b1 - b0, 256, smem, st>>>(s, b0, scratch, expo, n_red);
+    FF2 *f = reinterpret_cast<FF2 *>(scratch);
+    if (grad) eval_split_kernel<true><<<b1 - b0, 256, smem, st>>>(s, b0, f, expo, n_red);
+    else eval_split_kernel<false><<<b1 - b0, 256, smem, st>>>(s, b0, f, expo, n_red);
     return cudaGetLastError();
 }
 
@@ -445,6 +652,9 @@ cudaError_t launch_eval_one(const DevSystem &s, int32_t b, nao_precision prec, d
     if (prec == NAO_FP32) {
         if (grad) eval_export_kernel<true, float><<<1, 256, 0, st>>>(s, b, phi, grad);
         else eval_export_kernel<false, float><<<1, 256, 0, st>>>(s, b, phi, nullptr);
+    } else if (prec == NAO_SPLIT) {
+        if (grad) eval_export_kernel<true, FFTag><<<1, 256, 0, st>>>(s, b, phi, grad);
+        else eval_export_kernel<false, FFTag><<<1, 256, 0, st>>>(s, b, phi, nullptr);
     } else {
         if (grad) eval_export_kernel<true, double><<<1, 256, 0, st>>>(s, b, phi, grad);
         else eval_export_kernel<false, double><<<1, 256, 0, st>>>(s, b, phi, nullptr);

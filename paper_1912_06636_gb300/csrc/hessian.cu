@@ -1,5 +1,5 @@
-// Density Hessian on the FP64 path (Sec. 2: the six second derivatives of Eq. Density needed
-// for forces and stresses, each a "straightforward extension" of the density).
+// Density Hessian on the FP64 and FP32 paths (Sec. 2: the six second derivatives of Eq. Density
+// needed for forces and stresses, each a "straightforward extension" of the density).
 //
 // For symmetric P, differentiating n = sum_ij phi_i P_ij phi_j twice gives
 //   d_a d_b n = 2 sum_ij P_ij (phi_i d_a d_b phi_j + d_a phi_i d_b phi_j),
@@ -16,12 +16,15 @@
 //   g' = R' / r^l - l R / r^(l+1),  g'' = R'' / r^l - 2 l R' / r^(l+1) + l (l+1) R / r^(l+2),
 // with R' and R'' from the spline in s = ln(r / r0) / Delta (ds/dr = 1 / (r Delta),
 // d^2s/dr^2 = -1 / (r^2 Delta)). Every batch's block of scratch holds, per reduced-basis row,
-// 10 rows of Ppad points: phi, d/dx, d/dy, d/dz, xx, xy, xz, yy, yz, zz.
+// 10 rows of Ppad points: phi, d/dx, d/dy, d/dz, xx, xy, xz, yy, yz, zz, in the path's type T
+// (the values are computed in FP64 on both paths; the FP32 path rounds them once when storing).
+// For the Pulay terms (LAP) the fifth row holds the Laplacian xx + yy + zz instead, summed in
+// FP64 before the rounding (the three terms cancel where the Laplacian is small).
 //
 // Contraction: one CTA per 64-point density tile; for each 64-function tile J the four
-// products Phi P, (d_x Phi) P, (d_y Phi) P, (d_z Phi) P over all of K in FP64 (P read from its
-// upper triangle, so the matrix used is exactly symmetric), then the epilogue above. Every
-// point is written once (no atomics).
+// products Phi P, (d_x Phi) P, (d_y Phi) P, (d_z Phi) P over all of K in T (P read from its
+// upper triangle, so the matrix used is exactly symmetric), then the epilogue above in T, the
+// per-tile sums added in FP64. Every point is written once (no atomics).
 #include <cmath>
 
 #include "nao_internal.h"
@@ -39,9 +42,9 @@ __host__ __device__ constexpr double dfact_odd(int m) { return m <= 1 ? 1.0 : (2
 __device__ __forceinline__ int pair_a(int k) { return k < 3 ? 0 : (k < 5 ? 1 : 2); }
 __device__ __forceinline__ int pair_b(int k) { return k == 0 ? 0 : k == 1 ? 1 : k == 2 ? 2 : k == 3 ? 1 : 2; }
 
-template <int LMAX>
+template <int LMAX, typename OutT, bool LAP>
 __device__ __noinline__ void eval_group_hess(const DevSystem &s, const AtomGroup &ag, double x, double y, double z,
-                                             double r2, double r, double *E, int64_t rs, int64_t cs, int q) {
+                                             double r2, double r, OutT *E, int64_t rs, int64_t cs, int q) {
     // radial coordinate (the radial part is taken at r0 for r < r0)
     const double rr = fmax(r, s.r0);
     const double sc = log(rr / s.r0) * s.inv_delta;
@@ -159,31 +162,39 @@ __device__ __noinline__ void eval_group_hess(const DevSystem &s, const AtomGroup
                 Q = g2 * ur * ur - g1 * ur * ur * ur;
             }
             for (int mm = 0; mm < 2 * l + 1; mm++) {
-                double *row = E + (int64_t)(e.pos + mm) * rs + q;
+                OutT *row = E + (int64_t)(e.pos + mm) * rs + q;
                 const double Sv = S[mm];
-                row[0] = g * Sv;
+                row[0] = OutT(g * Sv);
 #pragma unroll
-                for (int a = 0; a < 3; a++) row[(1 + a) * cs] = G1 * xa[a] * Sv + g * Sg[a][mm];
+                for (int a = 0; a < 3; a++) row[(1 + a) * cs] = OutT(G1 * xa[a] * Sv + g * Sg[a][mm]);
+                double lap = 0.0;
 #pragma unroll
                 for (int kk = 0; kk < 6; kk++) {
                     const int a = pair_a(kk), b = pair_b(kk);
                     const double dab = a == b ? 1.0 : 0.0;
-                    row[(4 + kk) * cs] = Q * xa[a] * xa[b] * Sv + G1 * (dab * Sv + xa[b] * Sg[a][mm] + xa[a] * Sg[b][mm]) +
-                                         g * Sh[kk][mm];
+                    const double v = Q * xa[a] * xa[b] * Sv + G1 * (dab * Sv + xa[b] * Sg[a][mm] + xa[a] * Sg[b][mm]) +
+                                     g * Sh[kk][mm];
+                    if (LAP) {
+                        if (a == b) lap += v;  // xx + yy + zz, in that order
+                    } else {
+                        row[(4 + kk) * cs] = OutT(v);
+                    }
                 }
+                if (LAP) row[4 * cs] = OutT(lap);
             }
         }
         rl *= r;
     }
 }
 
-__global__ void __launch_bounds__(256) eval_hess_kernel(DevSystem s, int32_t b0, double *__restrict__ scratch,
+template <typename OutT, bool LAP>
+__global__ void __launch_bounds__(256) eval_hess_kernel(DevSystem s, int32_t b0, OutT *__restrict__ scratch,
                                                        const int64_t *__restrict__ hoff) {
     const int b = b0 + blockIdx.x;
     const int p0 = s.batch_off[b], P = s.batch_off[b + 1] - p0;
     const int Ppad = (P + NAO_PPAD - 1) & ~(NAO_PPAD - 1);
     const int g0 = s.agrp_off[b], ng = s.agrp_off[b + 1] - g0;
-    double *E = scratch + hoff[b];
+    OutT *E = scratch + hoff[b];
     const int64_t rs = (int64_t)HR * Ppad, cs = Ppad;
     for (int idx = threadIdx.x; idx < ng * Ppad; idx += blockDim.x) {
         const int gl = idx / Ppad, q = idx - gl * Ppad;
@@ -192,7 +203,7 @@ __global__ void __launch_bounds__(256) eval_hess_kernel(DevSystem s, int32_t b0,
             for (int ri = ag.r0; ri < ag.r0 + ag.nr; ri++) {
                 const RfnEntry e = s.rfn[ri];
                 for (int mm = 0; mm < 2 * e.l + 1; mm++)
-                    for (int c = 0; c < HR; c++) E[(int64_t)(e.pos + mm) * rs + c * cs + q] = 0.0;
+                    for (int c = 0; c < HR; c++) E[(int64_t)(e.pos + mm) * rs + c * cs + q] = OutT(0);
             }
             continue;
         }
@@ -202,23 +213,24 @@ __global__ void __launch_bounds__(256) eval_hess_kernel(DevSystem s, int32_t b0,
         const double r2 = dx * dx + dy * dy + dz * dz;
         const double r = sqrt(r2);
         switch (ag.lmax) {
-            case 0: eval_group_hess<0>(s, ag, dx, dy, dz, r2, r, E, rs, cs, q); break;
-            case 1: eval_group_hess<1>(s, ag, dx, dy, dz, r2, r, E, rs, cs, q); break;
-            case 2: eval_group_hess<2>(s, ag, dx, dy, dz, r2, r, E, rs, cs, q); break;
-            case 3: eval_group_hess<3>(s, ag, dx, dy, dz, r2, r, E, rs, cs, q); break;
-            case 4: eval_group_hess<4>(s, ag, dx, dy, dz, r2, r, E, rs, cs, q); break;
-            case 5: eval_group_hess<5>(s, ag, dx, dy, dz, r2, r, E, rs, cs, q); break;
-            default: eval_group_hess<6>(s, ag, dx, dy, dz, r2, r, E, rs, cs, q); break;
+            case 0: eval_group_hess<0, OutT, LAP>(s, ag, dx, dy, dz, r2, r, E, rs, cs, q); break;
+            case 1: eval_group_hess<1, OutT, LAP>(s, ag, dx, dy, dz, r2, r, E, rs, cs, q); break;
+            case 2: eval_group_hess<2, OutT, LAP>(s, ag, dx, dy, dz, r2, r, E, rs, cs, q); break;
+            case 3: eval_group_hess<3, OutT, LAP>(s, ag, dx, dy, dz, r2, r, E, rs, cs, q); break;
+            case 4: eval_group_hess<4, OutT, LAP>(s, ag, dx, dy, dz, r2, r, E, rs, cs, q); break;
+            case 5: eval_group_hess<5, OutT, LAP>(s, ag, dx, dy, dz, r2, r, E, rs, cs, q); break;
+            default: eval_group_hess<6, OutT, LAP>(s, ag, dx, dy, dz, r2, r, E, rs, cs, q); break;
         }
     }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(256) density_hess_kernel(DevSystem s, const DWork *__restrict__ work, int32_t w0,
-                                                          const double *__restrict__ scratch,
+                                                          const T *__restrict__ scratch,
                                                           const int64_t *__restrict__ hoff, double *__restrict__ hess,
                                                           double *__restrict__ ne_part) {
-    __shared__ __align__(16) double As[4][KC][TQ];  // phi, d/dx, d/dy, d/dz of rows i, at the tile's points
-    __shared__ __align__(16) double Bs[KC][TJ];     // P[rel_i][rel_j]
+    __shared__ __align__(16) T As[4][KC][TQ];  // phi, d/dx, d/dy, d/dz of rows i, at the tile's points
+    __shared__ __align__(16) T Bs[KC][TJ];     // P[rel_i][rel_j]
     __shared__ double acc_n[TQ], acc_g[3][TQ], acc_h[6][TQ];
     __shared__ double red[8];
     const DWork it = work[w0 + blockIdx.x];
@@ -227,7 +239,7 @@ __global__ void __launch_bounds__(256) density_hess_kernel(DevSystem s, const DW
     const int Ppad = (P + NAO_PPAD - 1) & ~(NAO_PPAD - 1);
     const int N = s.rel_off[b + 1] - s.rel_off[b];
     const int q0 = it.tp * TQ;
-    const double *E = scratch + hoff[b];
+    const T *E = scratch + hoff[b];
     const int64_t ld = (int64_t)HR * Ppad;
     const int32_t *rel = s.rel_idx + s.rel_off[b];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -238,19 +250,19 @@ __global__ void __launch_bounds__(256) density_hess_kernel(DevSystem s, const DW
     }
     const int nt = (N + TJ - 1) / TJ;
     for (int tj = 0; tj < nt; tj++) {
-        double T[4][4][4];
+        T Tm[4][4][4];
 #pragma unroll
         for (int c = 0; c < 4; c++)
 #pragma unroll
             for (int a = 0; a < 4; a++)
 #pragma unroll
-                for (int d = 0; d < 4; d++) T[c][a][d] = 0.0;
+                for (int d = 0; d < 4; d++) Tm[c][a][d] = T(0);
         for (int i0 = 0; i0 < N; i0 += KC) {
             __syncthreads();
             for (int u = tid; u < 4 * KC * TQ; u += blockDim.x) {
                 const int c = u / (KC * TQ), kk = (u / TQ) % KC, qq = u % TQ;
                 const int i = i0 + kk, q = q0 + qq;
-                As[c][kk][qq] = (i < N && q < Ppad) ? E[(int64_t)i * ld + (int64_t)c * Ppad + q] : 0.0;
+                As[c][kk][qq] = (i < N && q < Ppad) ? E[(int64_t)i * ld + (int64_t)c * Ppad + q] : T(0);
             }
             for (int u = tid; u < KC * TJ; u += blockDim.x) {
                 const int kk = u / TJ, jj = u % TJ;
@@ -261,21 +273,21 @@ __global__ void __launch_bounds__(256) density_hess_kernel(DevSystem s, const DW
                     if (gi > gj) { const int64_t tt = gi; gi = gj; gj = tt; }
                     pv = p_elem(s, m, gi, gj);
                 }
-                Bs[kk][jj] = pv;
+                Bs[kk][jj] = T(pv);
             }
             __syncthreads();
 #pragma unroll
             for (int kk = 0; kk < KC; kk++) {
-                double rb[4];
+                T rb[4];
 #pragma unroll
                 for (int d = 0; d < 4; d++) rb[d] = Bs[kk][tx * 4 + d];
 #pragma unroll
                 for (int c = 0; c < 4; c++)
 #pragma unroll
                     for (int a = 0; a < 4; a++) {
-                        const double ra = As[c][kk][ty * 4 + a];
+                        const T ra = As[c][kk][ty * 4 + a];
 #pragma unroll
-                        for (int d = 0; d < 4; d++) T[c][a][d] = fma(ra, rb[d], T[c][a][d]);
+                        for (int d = 0; d < 4; d++) Tm[c][a][d] = fma(ra, rb[d], Tm[c][a][d]);
                     }
             }
         }
@@ -283,21 +295,21 @@ __global__ void __launch_bounds__(256) density_hess_kernel(DevSystem s, const DW
 #pragma unroll
         for (int a = 0; a < 4; a++) {
             const int q = q0 + ty * 4 + a;
-            double pn = 0.0, pg[3] = {0.0, 0.0, 0.0}, ph[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+            T pn = T(0), pg[3] = {T(0), T(0), T(0)}, ph[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
 #pragma unroll
             for (int d = 0; d < 4; d++) {
                 const int j = tj * TJ + tx * 4 + d;
                 if (j < N && q < Ppad) {
-                    const double *f = E + (int64_t)j * ld + q;
-                    double fv[HR];
+                    const T *f = E + (int64_t)j * ld + q;
+                    T fv[HR];
 #pragma unroll
                     for (int c = 0; c < HR; c++) fv[c] = f[(int64_t)c * Ppad];
-                    pn = fma(T[0][a][d], fv[0], pn);
+                    pn = fma(Tm[0][a][d], fv[0], pn);
 #pragma unroll
-                    for (int c = 0; c < 3; c++) pg[c] = fma(T[0][a][d], fv[1 + c], pg[c]);
+                    for (int c = 0; c < 3; c++) pg[c] = fma(Tm[0][a][d], fv[1 + c], pg[c]);
 #pragma unroll
                     for (int kk = 0; kk < 6; kk++)
-                        ph[kk] = fma(T[1 + pair_a(kk)][a][d], fv[1 + pair_b(kk)], fma(T[0][a][d], fv[4 + kk], ph[kk]));
+                        ph[kk] = fma(Tm[1 + pair_a(kk)][a][d], fv[1 + pair_b(kk)], fma(Tm[0][a][d], fv[4 + kk], ph[kk]));
                 }
             }
 #pragma unroll
@@ -309,11 +321,11 @@ __global__ void __launch_bounds__(256) density_hess_kernel(DevSystem s, const DW
                 for (int kk = 0; kk < 6; kk++) ph[kk] += __shfl_xor_sync(0xffffffffu, ph[kk], o);
             }
             if (tx == 0) {
-                acc_n[ty * 4 + a] += pn;
+                acc_n[ty * 4 + a] += (double)pn;
 #pragma unroll
-                for (int c = 0; c < 3; c++) acc_g[c][ty * 4 + a] += 2.0 * pg[c];
+                for (int c = 0; c < 3; c++) acc_g[c][ty * 4 + a] += 2.0 * (double)pg[c];
 #pragma unroll
-                for (int kk = 0; kk < 6; kk++) acc_h[kk][ty * 4 + a] += 2.0 * ph[kk];
+                for (int kk = 0; kk < 6; kk++) acc_h[kk][ty * 4 + a] += 2.0 * (double)ph[kk];
             }
         }
     }
@@ -343,16 +355,25 @@ __global__ void __launch_bounds__(256) density_hess_kernel(DevSystem s, const DW
 
 }  // namespace
 
-cudaError_t launch_eval_hess(const DevSystem &s, int32_t b0, int32_t b1, double *scratch, const int64_t *hoff,
-                             cudaStream_t st) {
+cudaError_t launch_eval_hess(const DevSystem &s, int32_t b0, int32_t b1, void *scratch, bool fp32, bool lap,
+                             const int64_t *hoff, cudaStream_t st) {
     if (b1 <= b0) return cudaSuccess;
-    eval_hess_kernel<<<b1 - b0, 256, 0, st>>>(s, b0, scratch, hoff);
+    const int n = b1 - b0;
+    if (fp32 && lap) eval_hess_kernel<float, true><<<n, 256, 0, st>>>(s, b0, static_cast<float *>(scratch), hoff);
+    else if (fp32) eval_hess_kernel<float, false><<<n, 256, 0, st>>>(s, b0, static_cast<float *>(scratch), hoff);
+    else if (lap) eval_hess_kernel<double, true><<<n, 256, 0, st>>>(s, b0, static_cast<double *>(scratch), hoff);
+    else eval_hess_kernel<double, false><<<n, 256, 0, st>>>(s, b0, static_cast<double *>(scratch), hoff);
     return cudaGetLastError();
 }
 
-cudaError_t launch_density_hess(const DevSystem &s, const DWork *work, int32_t w0, int32_t n_work, const double *scratch,
-                                const int64_t *hoff, double *hess, double *ne_part, cudaStream_t st) {
+cudaError_t launch_density_hess(const DevSystem &s, const DWork *work, int32_t w0, int32_t n_work, const void *scratch,
+                                bool fp32, const int64_t *hoff, double *hess, double *ne_part, cudaStream_t st) {
     if (n_work <= 0) return cudaSuccess;
-    density_hess_kernel<<<n_work, 256, 0, st>>>(s, work, w0, scratch, hoff, hess, ne_part);
+    if (fp32)
+        density_hess_kernel<float><<<n_work, 256, 0, st>>>(s, work, w0, static_cast<const float *>(scratch), hoff, hess,
+                                                            ne_part);
+    else
+        density_hess_kernel<double><<<n_work, 256, 0, st>>>(s, work, w0, static_cast<const double *>(scratch), hoff,
+                                                             hess, ne_part);
     return cudaGetLastError();
 }

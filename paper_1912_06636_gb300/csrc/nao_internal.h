@@ -57,7 +57,8 @@ struct SysTables {
 struct DevSystem {
     const double *atom_xyz;   // [n_atoms*3]
     const double *coef;       // [n_fn][n_rgrid-1][4] spline coefficients in t
-    const float *coef_f32;    // same in FP32
+    const float *coef_f32;    // same in FP32 (rounded to nearest)
+    const float *coef_lo;     // c - coef_f32 rounded to FP32: (coef_f32, coef_lo) is c as a float-float
     const double *inv_rk;     // [n_rgrid] 1 / r_k of the logarithmic grid
     const uint8_t *seg64;     // [n_fn][n_rgrid-1] 1: the FP32 path evaluates this spline segment in FP64
     const double *fn_rc;      // [n_fn]
@@ -77,6 +78,7 @@ struct DevSystem {
     int64_t nb;               // total basis size over all systems
     SysTables sys;
     double knorm[NAO_LMAX + 1][NAO_LMAX + 1];  // sqrt((2l+1)/(4pi) (l-m)!/(l+m)!) (x sqrt2 for m>0)
+    float knorm_h[NAO_LMAX + 1][NAO_LMAX + 1], knorm_l[NAO_LMAX + 1][NAO_LMAX + 1];  // knorm as float-float
 };
 
 #ifdef __CUDACC__
@@ -309,6 +311,17 @@ struct nao_grid {
     };
     std::vector<HessChunk> hess_chunks;
     int64_t *d_hess_off = nullptr;
+    // density Hessian on the split path: ranges of batches inside one Hessian chunk and one
+    // split chunk, with their own density work items (rebuilt when the tile widths change)
+    struct HessSplitSub {
+        int32_t b0, b1, max_qt, max_rt;
+        int32_t nw0[2], nw1[2];  // items of width 48, 32 in d_hess_nw
+    };
+    std::vector<HessSplitSub> hess_split;
+    HWork *d_hess_nw = nullptr;
+    int64_t cap_hess_nw = 0;
+    int32_t *d_expo4 = nullptr;  // [4][n_points] point exponents of phi, d/dx, d/dy, d/dz phi
+    int split_lists_ver = 0, hess_split_ver = -1;
     // local Pulay force terms: every 64 x 64 tile pair of every batch, per Hessian chunk
     std::vector<int64_t> atom_basis;         // [n_atoms + 1] first global basis index of each atom
     std::vector<int32_t> pulay_w0;           // [hess_chunks + 1] work ranges
@@ -359,18 +372,20 @@ cudaError_t launch_eval(const DevSystem &s, int32_t b0, int32_t b1, nao_precisio
 // point exponents of the slicing into expo (by batch-ordered point; n_red >= P_b).
 cudaError_t launch_eval_split(const DevSystem &s, int32_t b0, int32_t b1, bool grad, double *scratch, int32_t *expo,
                               int32_t n_red, cudaStream_t st);
-// Density Hessian (FP64): evaluation of phi, grad phi and the six second derivatives (10 rows
-// of Ppad per function at scratch + hoff[b]) and the contraction (n, grad n into the pointer
+// Density Hessian (FP64, or FP32 with fp32): evaluation of phi, grad phi and the six second
+// derivatives (computed in FP64, stored as double or float: 10 rows of Ppad per function at
+// scratch + hoff[b] elements; lap: the fifth row holds the Laplacian, for the Pulay terms) and
+// the contraction in the same type (n, grad n into the pointer
 // tables' sections 3 and 5, the Hessian component-major into hess, per-tile w n into ne_part).
-cudaError_t launch_eval_hess(const DevSystem &s, int32_t b0, int32_t b1, double *scratch, const int64_t *hoff,
-                             cudaStream_t st);
-cudaError_t launch_density_hess(const DevSystem &s, const DWork *work, int32_t w0, int32_t n_work, const double *scratch,
-                                const int64_t *hoff, double *hess, double *ne_part, cudaStream_t st);
-// Local Pulay force terms (FP64): M^c += sum_q w d_c phi_i (-1/2 lap + v) phi_j and S^c += sum_q w
-// d_c phi_i phi_j over the full tile pairs of work items (batch, I, J) from the 10-row evaluation,
-// into M and S ([3][nb][nb], single system); and F[3 a + c] = 2 sum_{i on a} sum_j (n_ij M^c_ij -
-// q_ij S^c_ij).
-cudaError_t launch_pulay(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const double *scratch,
+cudaError_t launch_eval_hess(const DevSystem &s, int32_t b0, int32_t b1, void *scratch, bool fp32, bool lap,
+                             const int64_t *hoff, cudaStream_t st);
+cudaError_t launch_density_hess(const DevSystem &s, const DWork *work, int32_t w0, int32_t n_work, const void *scratch,
+                                bool fp32, const int64_t *hoff, double *hess, double *ne_part, cudaStream_t st);
+// Local Pulay force terms (FP64, or FP32 with fp32, from the Hessian evaluation of the same
+// type): M^c += sum_q w d_c phi_i (-1/2 lap + v) phi_j and S^c += sum_q w d_c phi_i phi_j over the
+// full tile pairs of work items (batch, I, J), into M and S ([3][nb][nb], single system); and
+// F[3 a + c] = 2 sum_{i on a} sum_j (n_ij M^c_ij - q_ij S^c_ij).
+cudaError_t launch_pulay(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const void *scratch, bool fp32,
                          const int64_t *hoff, double *M, double *S, int64_t nb, cudaStream_t st);
 cudaError_t launch_pulay_forces(const double *nmat, const double *qmat, const double *M, const double *S,
                                 const int64_t *atom_basis, int32_t n_atoms, int64_t nb, double *F, cudaStream_t st);
@@ -411,6 +426,20 @@ cudaError_t launch_h_tc(const DevSystem &s, const HWork *work, int32_t w0, int32
 cudaError_t launch_slice_n(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_qt, int32_t max_rt,
                            const double *scratch, uint8_t *slices, const int64_t *sl_off, const int32_t *expo_q,
                            int32_t *expo_b, const int32_t *tn_b, int S, int F, bool grad, cudaStream_t st);
+// The density Hessian on the split path (passes comp = 0..3 over the 10-row FP64 evaluation at
+// hoff: A = phi, then the gradient components; P' sliced with the first pass): slicing, the
+// four A operands' point exponents (expo4[comp n_points + p]) and the contraction passes
+// (comp 0 writes n, grad n and hess; comp a adds hess_(a, b), b >= a).
+cudaError_t launch_slice_n_hess(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_qt, int32_t max_rt,
+                                const double *scratch, const int64_t *hoff, int comp, uint8_t *slices,
+                                const int64_t *sl_off, const int32_t *expo_q, int32_t *expo_b, const int32_t *tn_b, int S,
+                                int F, cudaStream_t st);
+cudaError_t launch_hess_point_expo(const DevSystem &s, int32_t b0, int32_t b1, const double *scratch, const int64_t *hoff,
+                                   int32_t *expo4, int64_t n_points, cudaStream_t st);
+cudaError_t launch_n_tc_hess(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
+                             const int64_t *sl_off, const int32_t *expo_q, const int32_t *expo_b, const double *scratch,
+                             const int64_t *hoff, int comp, double *hess, int S, int F, int tn, int32_t *err,
+                             cudaStream_t st);
 cudaError_t launch_n_tc(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
                         const int64_t *sl_off, const int32_t *expo_q, const int32_t *expo_b, const double *scratch, int S,
                         int F, int tn, bool grad, int32_t *err, cudaStream_t st);

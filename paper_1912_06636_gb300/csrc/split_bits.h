@@ -33,14 +33,13 @@ __device__ __forceinline__ int exponent_of_binade(int eb) {
 // d_k of the Hamiltonian's column k = (component c, batch-ordered point p): w v on the potential
 // part (c = 0), w (kappa + v_tau) / 2 on the three gradient parts (Eq. H_decomp; kappa = 1 with
 // the kinetic term, v_tau with the meta-GGA term), 0 for a term that is off; the column's scale
-// is sqrt|d_k|.
+// is sqrt|d_k| (formed in the H slicer).
 __device__ __forceinline__ double h_column_weight(const DevSystem &s, int m, int p, int c, uint32_t terms) {
     const double w = s.pw[p];
     if (c == 0) return (terms & NAO_TERM_POTENTIAL) ? w * v_at(s, m, p) : 0.0;
     const double kin = (terms & NAO_TERM_KINETIC) ? 1.0 : 0.0;
     return 0.5 * w * ((terms & NAO_TERM_TAU) ? kin + vt_at(s, m, p) : kin);
 }
-__device__ __forceinline__ double h_column_scale(double d) { return sqrt(fabs(d)); }
 
 // Ordering key of |x sd| for the row maximum without an FP64 product: the product's biased
 // exponent is eb(x) + eb(sd) - 1023, plus 1 when the significands' product reaches 2 (taken as
@@ -52,6 +51,17 @@ __device__ __forceinline__ int h_row_key(double x, int ebs, float ms) {
     const int ebx = biased_exponent(xb);
     if (ebx == 0 || ebs == 0) return 0;
     return ebx + ebs + (significand_f(xb) * ms >= 1.999998f ? 1 : 0);
+}
+
+// The same key for a float-float factor x = h + l given by its high part h (FP32): the exponent
+// of h on the FP64 scale, and the threshold lowered to 2 - 2^-13 so that the low parts of x and
+// of sd (a few 2^-24 relative) cannot carry the product into the next binade unnoticed.
+__device__ __forceinline__ int h_row_key_ff(float xh, int ebs, float ms) {
+    const int xb = __float_as_int(xh);
+    const int ebx = (xb >> 23) & 0xFF;
+    if (ebx == 0 || ebs == 0) return 0;
+    const float sx = __int_as_float(0x3F800000 | (xb & 0x7FFFFF));
+    return ebx + 896 + ebs + (sx * ms >= 1.99988f ? 1 : 0);
 }
 
 // Row exponent from the maximum key of the row.

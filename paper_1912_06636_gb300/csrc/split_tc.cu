@@ -27,6 +27,7 @@
 #include <cmath>
 #include <type_traits>
 
+#include "ff.h"
 #include "nao_internal.h"
 #include "split_bits.h"
 #include "tc_ptx.h"
@@ -119,6 +120,76 @@ __device__ __forceinline__ void digits2(double x0, double x1, int e, float2 (&di
     }
 }
 
+// The digits of a float-float value without 128-bit integers: x = h + l is scaled by 2^(BS-e)
+// through its exponent fields (H = h 2^(BS-e), L = l 2^(BS-e), exact), and each part is cut into
+// balanced chunks of CB bits from the top in FP32: q = rint(R 2^-(c CB)), R <- R - q 2^(c CB),
+// for c = 3, 2, 1, then u_0 = rint(R). Every step is exact (R keeps a subset of the part's 24
+// significand bits; |R 2^-(c CB)| < 2^22 keeps the rounding by 1.5 2^23 valid), so
+// sum_c u_c 2^(c CB) = round(H) and the chunks of round(H) + round(L), summed per chunk (each at
+// most 2^(CB-1) in magnitude), feed the digit peeling below; the result is within one unit of
+// round(|h + l| 2^(BS-e)). A part below the FP32 normal range after scaling counts as zero.
+__device__ __forceinline__ float ff_scale_pow2(float v, int k) {
+    const int b = __float_as_int(v);
+    const int ex = (b >> 23) & 0xFF;
+    if (ex == 0 || ex + k <= 0) return 0.0f;
+    return __int_as_float(b + (k << 23));
+}
+
+__device__ __forceinline__ float rint_small(float y) {  // |y| < 2^22
+    return __fsub_rn(__fadd_rn(y, 12582912.0f), 12582912.0f);
+}
+
+template <int CB>
+__device__ __forceinline__ void ff_part_chunks(float P, float (&u)[4]) {
+    constexpr float W1 = (float)(1ULL << CB), W2 = W1 * W1, W3 = W2 * W1;
+    constexpr float I1 = 1.0f / W1, I2 = I1 * I1, I3 = I2 * I1;
+    float R = P;
+    const float q3 = rint_small(__fmul_rn(R, I3));
+    R = __fmaf_rn(-q3, W3, R);
+    const float q2 = rint_small(__fmul_rn(R, I2));
+    R = __fmaf_rn(-q2, W2, R);
+    const float q1 = rint_small(__fmul_rn(R, I1));
+    R = __fmaf_rn(-q1, W1, R);
+    u[0] += rint_small(R);
+    u[1] += q1;
+    u[2] += q2;
+    u[3] += q3;
+}
+
+template <int S, int B>
+__device__ __forceinline__ void ff_chunks(ffa::F x, int e, float (&u)[4]) {
+    constexpr int D = B == 6 ? 3 : 4, CB = D * B;
+    u[0] = u[1] = u[2] = u[3] = 0.0f;
+    if (e <= -10000) return;
+    const int k = B * S - e;
+    ff_part_chunks<CB>(ff_scale_pow2(x.h, k), u);
+    ff_part_chunks<CB>(ff_scale_pow2(x.l, k), u);
+}
+
+// The S digits of two float-float values at once (packed FP32x2 peeling, as for FP64 values).
+template <int S, int B>
+__device__ __forceinline__ void digits2(ffa::F x0, ffa::F x1, int e, float2 (&dig)[S]) {
+    constexpr int D = B == 6 ? 3 : 4;
+    float u0[4], u1[4];
+    ff_chunks<S, B>(x0, e, u0);
+    ff_chunks<S, B>(x1, e, u1);
+    const float2 inv = make_float2(1.0f / (1 << B), 1.0f / (1 << B)), big = make_float2(12582912.0f, 12582912.0f);
+    const float2 nbig = make_float2(-12582912.0f, -12582912.0f), mb = make_float2(-(float)(1 << B), -(float)(1 << B));
+    float2 v = make_float2(u0[0], u1[0]);
+#pragma unroll
+    for (int s = S - 1; s >= 0; s--) {
+        const int t = S - 1 - s;
+        if (t > 0 && t % D == 0) v = __fadd2_rn(v, make_float2(u0[t / D], u1[t / D]));
+        if (s == 0) {
+            dig[0] = v;
+        } else {
+            const float2 q = __fadd2_rn(__ffma2_rn(v, inv, big), nbig);
+            dig[s] = __ffma2_rn(q, mb, v);
+            v = q;
+        }
+    }
+}
+
 // bf16 bit patterns of two small integers held exactly in floats (their low halves are zero).
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
     return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
@@ -134,9 +205,9 @@ __device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float
 }
 
 // Digits of the 128-byte row segment a lane owns in one K chunk: values x[0..LC-1] of its LC
-// consecutive columns (2 for bf16, 4 for e4m3), packed per slice into one 32-bit word.
-template <int S, int F>
-__device__ __forceinline__ void lane_digit_words(const double *x, int e, uint32_t (&w)[S]) {
+// columns (2 for bf16, 4 for e4m3; FP64 or float-float), packed per slice into one 32-bit word.
+template <int S, int F, typename V>
+__device__ __forceinline__ void lane_digit_words(const V *x, int e, uint32_t (&w)[S]) {
     constexpr int B = nao_digit_bits(F);
     float2 d0[S];
     digits2<S, B>(x[0], x[1], e, d0);
@@ -164,18 +235,22 @@ __device__ __forceinline__ double pow2(int E) {
 // reordered: the negative-weight ones (v < 0 on the potential part) first, padded to a whole
 // MMA K step (16 bf16 or 32 e4m3 columns), then the rest, so that B = A and the sign is applied
 // per K step.
-// One warp per row: the row's exponent (a pass over the row), then its digits (a second pass,
-// served from L2: the slices are written with evict-first stores so that they do not push the
-// rows out).
+// One warp per row: the row's exponent (a pass over the row's K float-float values), then its
+// digits (a second pass, served from L2: the slices are written with evict-first stores so that
+// they do not push the rows out). Within each K step, lane l of the 8 lanes that write the
+// step's 32 bytes takes logical columns l, l + 8 (, l + 16, l + 24) of the step: a permutation
+// inside the K step, the same for every row (A and B of H are the same digit rows, so every
+// product is unchanged, and each K step keeps its sign), which keeps each load instruction of the
+// second pass on a few 64-byte runs of the row.
 // ----------------------------------------------------------------------------------------
 template <int S, int F>
-__global__ void __launch_bounds__(256, S <= 10 ? 5 : 4) slice_h_kernel(DevSystem s, int32_t b0, const double *__restrict__ scratch,
+__global__ void __launch_bounds__(256, S <= 10 ? 5 : 4) slice_h_kernel(DevSystem s, int32_t b0, const FF2 *__restrict__ scratch,
                                                         uint32_t terms, uint8_t *__restrict__ slices,
                                                         const int64_t *__restrict__ sl_off, int32_t *__restrict__ expo,
                                                         int32_t *__restrict__ neg16) {
-    __shared__ double sd[4 * NAO_SPLIT_MAX_PPAD];
+    __shared__ ffa::F sd[4 * NAO_SPLIT_MAX_PPAD];    // column scale as a float-float
     __shared__ int sd_eb[4 * NAO_SPLIT_MAX_PPAD];    // biased exponent of sd (0: zero weight)
-    __shared__ float sd_m[4 * NAO_SPLIT_MAX_PPAD];   // significand of sd in [1, 2), truncated
+    __shared__ float sd_m[4 * NAO_SPLIT_MAX_PPAD];   // significand of sd in [1, 2)
     __shared__ short src[4 * NAO_SPLIT_MAX_PPAD + 128];
     __shared__ unsigned char negf[4 * NAO_SPLIT_MAX_PPAD];
     __shared__ int wsum[8];
@@ -187,14 +262,24 @@ __global__ void __launch_bounds__(256, S <= 10 ? 5 : 4) slice_h_kernel(DevSystem
     const SplitGeom G(P, N, S, 0, F);
     if (N == 0 || rt >= G.h_slice_tiles()) return;
     const int K = 4 * Ppad, Kp = C * G.n_kc;
-    const double *E = scratch + s.scr_off[b];
+    const FF2 *E = scratch + s.scr_off[b];
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         const int c = k / Ppad, q = k - c * Ppad;
         const double d = q < P ? split_bits::h_column_weight(s, m, p0 + q, c, terms) : 0.0;
-        sd[k] = split_bits::h_column_scale(d);
-        const long long sb = __double_as_longlong(sd[k]);
-        sd_eb[k] = split_bits::biased_exponent(sb);
-        sd_m[k] = split_bits::significand_f(sb);
+        // sqrt|d| as a float-float: the FP32 square root s0 and one Newton correction
+        // (|d| - s0^2) / (2 s0), the residual formed exactly by one FP64 FMA (|d| below the FP32
+        // range counts as a zero weight)
+        const float a = __double2float_rn(fabs(d));
+        ffa::F sdf{0.0f, 0.0f};
+        if (a >= 1.17549435e-38f) {
+            const float s0 = __fsqrt_rn(a);
+            const double r = fma(-(double)s0, (double)s0, fabs(d));
+            sdf = ffa::quick(s0, __fmul_rn(__double2float_rn(r), __fdiv_rn(0.5f, s0)));
+        }
+        sd[k] = sdf;
+        const int sb = __float_as_int(sdf.h);
+        sd_eb[k] = sdf.h != 0.0f ? ((sb >> 23) & 0xFF) + 896 : 0;  // biased exponent on the FP64 scale
+        sd_m[k] = __int_as_float(0x3F800000 | (sb & 0x7FFFFF));
         negf[k] = d < 0.0 ? 1 : 0;
     }
     for (int k = threadIdx.x; k < Kp; k += blockDim.x) src[k] = -1;
@@ -228,24 +313,29 @@ __global__ void __launch_bounds__(256, S <= 10 ? 5 : 4) slice_h_kernel(DevSystem
     if (rt == 0 && threadIdx.x == 0) neg16[b] = negpad / KS;  // negated K steps
     __syncthreads();
     uint8_t *base = slices + sl_off[b];
+    // the logical column of this lane's value c inside a chunk (see above)
+    const int lcol = KS * (lane >> 3) + (lane & 7);
     for (int lr = warp; lr < 64; lr += 8) {
         const int r = rt * 64 + lr;
         if (r >= G.R16) break;
-        const double *row = E + (int64_t)(r < N ? r : 0) * K;
+        const float2 *row = reinterpret_cast<const float2 *>(E + (int64_t)(r < N ? r : 0) * K);
         int mk = 0;
         if (r < N)
-            for (int k = lane; k < K; k += 32) mk = max(mk, split_bits::h_row_key(row[k], sd_eb[k], sd_m[k]));
+            for (int k = lane; k < K; k += 32) mk = max(mk, split_bits::h_row_key_ff(row[k].x, sd_eb[k], sd_m[k]));
         mk = __reduce_max_sync(0xffffffffu, mk);
         const int e = r < N ? split_bits::h_row_exponent(mk) : -10000;
         if (lane == 0 && r < N) expo[s.rel_off[b] + r] = e;
-        // LC consecutive K columns per lane: a warp writes one 128-byte row segment per slice
         for (int kc = 0; kc < G.n_kc; kc++) {
-            const int k0 = C * kc + LC * lane;
-            double x[LC];
+            ffa::F x[LC];
 #pragma unroll
             for (int c = 0; c < LC; c++) {
-                const int kk = src[k0 + c];
-                x[c] = (kk >= 0 && e > -10000) ? __ldcs(row + kk) * sd[kk] : 0.0;
+                const int kk = src[C * kc + lcol + 8 * c];
+                if (kk >= 0 && e > -10000) {
+                    const float2 v = __ldcs(row + kk);
+                    x[c] = ffa::mul(ffa::F{v.x, v.y}, sd[kk]);
+                } else {
+                    x[c] = ffa::F{0.0f, 0.0f};
+                }
             }
             uint32_t wd[S];
             lane_digit_words<S, F>(x, e, wd);
@@ -266,13 +356,31 @@ __global__ void __launch_bounds__(256, S <= 10 ? 5 : 4) slice_h_kernel(DevSystem
 // ----------------------------------------------------------------------------------------
 __device__ __forceinline__ int tile_of(int i, int TN) { return i / TN; }
 
-template <int S, int F>
-__global__ void __launch_bounds__(256) slice_nphi_kernel(DevSystem s, int32_t b0, const double *__restrict__ scratch,
+template <typename V>
+struct StageOf {  // shared-memory staging type of the density slicer's input
+    using type = ffa::F;
+    __device__ static ffa::F get(const FF2 &v) { return v.f(); }
+    __device__ static ffa::F zero() { return ffa::F{0.0f, 0.0f}; }
+};
+template <>
+struct StageOf<double> {
+    using type = double;
+    __device__ static double get(double v) { return v; }
+    __device__ static double zero() { return 0.0; }
+};
+
+// V = FF2: the split path's float-float phi (rows of ld_mult Ppad at scr_off[b]); V = double: the
+// density Hessian's FP64 evaluation (rows of 10 Ppad at eoff[b]), component row coff (phi or one
+// gradient component). pexp = 0 leaves the P' exponent (blockIdx.y = 0) to another launch.
+template <int S, int F, typename V>
+__global__ void __launch_bounds__(256) slice_nphi_kernel(DevSystem s, int32_t b0, const V *__restrict__ scratch,
+                                                        const int64_t *__restrict__ eoff, int coff,
                                                         uint8_t *__restrict__ slices, const int64_t *__restrict__ sl_off,
                                                         const int32_t *__restrict__ expo_q, int32_t *__restrict__ expo_b,
-                                                        const int32_t *__restrict__ tn_b, int ld_mult, int full) {
+                                                        const int32_t *__restrict__ tn_b, int ld_mult, int full, int pexp) {
     constexpr int C = nao_chunk_cols(F), LC = C / 32;
-    __shared__ double t[32][C + 1];
+    using TT = typename StageOf<V>::type;
+    __shared__ TT t[32][C + 1];
     __shared__ int red[8];
     const int b = b0 + blockIdx.x;
     const int p0 = s.batch_off[b], P = s.batch_off[b + 1] - p0;
@@ -282,6 +390,7 @@ __global__ void __launch_bounds__(256) slice_nphi_kernel(DevSystem s, int32_t b0
     const SplitGeom G(P, N, S, 0, F);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (blockIdx.y == 0) {
+        if (!pexp) return;
         // max |P'_ij| over i <= j (P' is P on the diagonal tiles, 2 P off them, 0 below unless
         // full): the exponent field of |P| plus one off the diagonal tiles
         const int m = s.sys.bmol[b], TN = tn_b[b];
@@ -306,7 +415,7 @@ __global__ void __launch_bounds__(256) slice_nphi_kernel(DevSystem s, int32_t b0
     }
     const int q0 = (blockIdx.y - 1) * 32;
     if (q0 >= G.P16) return;
-    const double *E = scratch + s.scr_off[b];  // phi[i][q], row stride ld_mult Ppad (4: rows also hold grad phi)
+    const V *E = scratch + eoff[b] + (int64_t)coff * Ppad;  // row i at E + i ld_mult Ppad
     const int64_t ld = (int64_t)ld_mult * Ppad;
     const bool qin = q0 + lane < P;
     int eq[4];
@@ -320,16 +429,20 @@ __global__ void __launch_bounds__(256) slice_nphi_kernel(DevSystem s, int32_t b0
 #pragma unroll
         for (int h = 0; h < C / 8; h++) {
             const int i = kc * C + warp + 8 * h;
-            t[lane][warp + 8 * h] = (i < N && qin) ? E[(int64_t)i * ld + q0 + lane] : 0.0;
+            t[lane][warp + 8 * h] = (i < N && qin) ? StageOf<V>::get(E[(int64_t)i * ld + q0 + lane]) : StageOf<V>::zero();
         }
         __syncthreads();
 #pragma unroll
         for (int h = 0; h < 4; h++) {
             const int ql = warp * 4 + h, q = q0 + ql;
             if (q >= G.P16) break;
-            double x[LC];
+            // lane L packs functions L, L + 32 (, L + 64, L + 96) of the chunk into its word: both
+            // operands of the density's product (this A and slice_np_kernel's B) order K this way
+            // inside each chunk, which leaves every slice product unchanged and reads the staging
+            // rows without bank conflicts
+            TT x[LC];
 #pragma unroll
-            for (int c = 0; c < LC; c++) x[c] = t[ql][LC * lane + c];
+            for (int c = 0; c < LC; c++) x[c] = t[ql][lane + 32 * c];
             uint32_t wd[S];
             lane_digit_words<S, F>(x, eq[h], wd);
             const uint32_t off = tc::sw128_byte((uint32_t)q, (uint32_t)(4 * lane));
@@ -343,7 +456,7 @@ __global__ void __launch_bounds__(256) slice_nphi_kernel(DevSystem s, int32_t b0
 // P'_ij = c_IJ P[rel_i][rel_j] over TN-function tiles I = i/TN <= J = j/TN (c_II = 1,
 // c_IJ = 2; every (i, j) with c = 1 when full), read from P's upper triangle, with the batch's
 // exponent from slice_nphi_kernel. One CTA per (batch, 16 rows j), one warp per row, 2 or 4
-// functions i per lane (one 128-byte row segment per slice).
+// functions i per lane (i = lane + 32 c inside the chunk; one 128-byte row segment per slice).
 template <int S, int F>
 __global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, uint8_t *__restrict__ slices,
                                                       const int64_t *__restrict__ sl_off,
@@ -371,7 +484,7 @@ __global__ void __launch_bounds__(256) slice_np_kernel(DevSystem s, int32_t b0, 
             double xp[LC];
 #pragma unroll
             for (int hh = 0; hh < LC; hh++) {
-                const int i = C * kc + LC * lane + hh;
+                const int i = C * kc + lane + 32 * hh;  // the K order of slice_nphi_kernel
                 double x = 0.0;
                 if (jin && i < N && (full || tile_of(i, TN) <= tj)) {
                     const int64_t gi = rel[i];
@@ -791,12 +904,20 @@ __device__ __forceinline__ int n_item_kc(const NItem &h, int J) {
     return nk < h.n_kcN ? nk : h.n_kcN;
 }
 
-template <int TN, bool GRADN, int F>
+// MODE 0: n; 1: n and grad n (GRADN); 2: the density Hessian's first pass (A = Phi: n, grad n and
+// 2 sum_j T_qj d_a d_b phi_qj into hess); 3: a later pass (A = d_hc Phi: hess_(hc, b) +=
+// 2 sum_j T_qj d_b phi_qj for b >= hc). Modes 0, 1 read the float-float evaluation at scr_off,
+// modes 2, 3 the Hessian's 10-row FP64 evaluation at eoff.
+template <int TN, int MODE, int F>
 __global__ void __launch_bounds__(192, 1)
     n_tc_kernel(DevSystem s, const HWork *__restrict__ work, int32_t w0, int32_t n_work, const uint8_t *__restrict__ slices,
                 const int64_t *__restrict__ sl_off, const int32_t *__restrict__ expo_q,
-                const int32_t *__restrict__ expo_b, const double *__restrict__ scratch, int S,
+                const int32_t *__restrict__ expo_b, const void *__restrict__ scratch_v,
+                const int64_t *__restrict__ eoff, int S, int hc, double *__restrict__ hess,
                 int32_t *__restrict__ err) {
+    constexpr bool GRADN = MODE >= 1;  // P' over all of K
+    using V = typename std::conditional<(MODE >= 2), double, FF2>::type;
+    const V *scratch = static_cast<const V *>(scratch_v);
     constexpr uint32_t B_BLOCK = TN * 128;
     extern __shared__ uint8_t smem_dyn[];
     __shared__ PPipe pp;
@@ -837,7 +958,7 @@ __global__ void __launch_bounds__(192, 1)
             for (int w = blockIdx.x; w < n_work && !*abort; w += gridDim.x) {
                 const NItem h = n_item<TN, F>(s, work, w0 + w, slices, sl_off, S);
                 for (int J = 0; J < h.nJ && !*abort; J++) {
-                    const int nk = n_item_kc<TN, GRADN, F>(h, J);
+                    const int nk = n_item_kc<TN, (MODE >= 1), F>(h, J);
                     const uint8_t *bJ = h.b0 + (size_t)J * TN * 128;
                     const uint32_t b_bytes = (uint32_t)min(TN, h.R16 - J * TN) * 128u;
                     for (int kc = 0; kc < nk; kc++, gk++) {
@@ -878,7 +999,7 @@ __global__ void __launch_bounds__(192, 1)
             for (int w = blockIdx.x; w < n_work && !*abort; w += gridDim.x) {
                 const NItem h = n_item<TN, F>(s, work, w0 + w, slices, sl_off, S);
                 for (int J = 0; J < h.nJ && !*abort; J++, t++) {
-                    const int nk = n_item_kc<TN, GRADN, F>(h, J);
+                    const int nk = n_item_kc<TN, (MODE >= 1), F>(h, J);
                     // the accumulators of the previous tile have been read
                     if (t >= 1 && !tc::mbar_wait(&pp.acc_empty, (t - 1) & 1, kWaitCycles)) { *abort = 1; break; }
                     tc::fence_after_sync();
@@ -922,15 +1043,15 @@ __global__ void __launch_bounds__(192, 1)
             const NItem h = n_item<TN, F>(s, work, w0 + w, slices, sl_off, S);
             const int q = h.ti * 128 + warp * 32 + lane;
             const bool row_ok = q < h.P;
-            const double *E = scratch + s.scr_off[h.b];
-            const int64_t ld = GRADN ? 4 * (int64_t)h.Ppad : (int64_t)h.Ppad;
+            const V *E = scratch + eoff[h.b];
+            const int64_t ld = MODE >= 2 ? 10 * (int64_t)h.Ppad : (GRADN ? 4 * (int64_t)h.Ppad : (int64_t)h.Ppad);
             // sum_j T_qj phi_qj (and grad phi) in units of 2^(e_q + e_b - n_unit): each T_qj as one
             // 64-bit integer in those units (n_int: 2^-50 with bf16 digits, 2^-47 with e4m3),
             // rounded by at most half a unit: about the split's own truncation at 10 bf16 slices
             // (the dropped groups g >= S reach K (S + 1) 2^(e_q + e_b - 6S - 2)) and below the FP64
             // evaluation's rounding in n. Then one conversion and one FMA per product, all integer
             // work done before tensor memory is handed back (no FP64 arithmetic on that path).
-            double part = 0.0, gpart[3] = {0.0, 0.0, 0.0};
+            double part = 0.0, gpart[3] = {0.0, 0.0, 0.0}, hpart[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
             for (int J = 0; J < h.nJ; J++, t++) {
                 if (*abort || !tc::mbar_wait(&pp.acc_full, t & 1, kWaitCycles)) { *abort = 1; break; }
                 tc::fence_after_sync();
@@ -949,20 +1070,27 @@ __global__ void __launch_bounds__(192, 1)
                 if (row_ok) {
                     // the next tile's rows of phi towards L2 while this tile's products run
                     if (J + 1 < h.nJ) {
-                        const double *fn = E + (int64_t)(J + 1) * TN * ld + q;
+                        const V *fn = E + (int64_t)(J + 1) * TN * ld + q;
                         const int jn1 = min(TN, h.N - (J + 1) * TN);
                         for (int jj = 0; jj < jn1; jj++) asm volatile("prefetch.global.L2 [%0];" ::"l"(fn + jj * ld));
                     }
                     const int jn = min(TN, h.N - J * TN);
-                    const double *f = E + (int64_t)J * TN * ld + q;
+                    const V *f = E + (int64_t)J * TN * ld + q;
 #pragma unroll
                     for (int jj = 0; jj < TN; jj++) {
                         if (jj < jn) {
                             const double vj = (double)val[jj];
-                            part = fma(vj, f[jj * ld], part);
-                            if (GRADN)
+                            const V *fj = f + jj * ld;
+                            if (MODE <= 2) part = fma(vj, double(fj[0]), part);
+                            if (MODE == 1 || MODE == 2)
 #pragma unroll
-                                for (int d = 0; d < 3; d++) gpart[d] = fma(vj, f[jj * ld + (d + 1) * h.Ppad], gpart[d]);
+                                for (int d = 0; d < 3; d++) gpart[d] = fma(vj, double(fj[(d + 1) * h.Ppad]), gpart[d]);
+                            if (MODE == 2)
+#pragma unroll
+                                for (int k = 0; k < 6; k++) hpart[k] = fma(vj, double(fj[(4 + k) * h.Ppad]), hpart[k]);
+                            if (MODE == 3)  // T^hc_qj d_b phi_qj, b = 1..3 in hpart[b - 1]
+#pragma unroll
+                                for (int d = 0; d < 3; d++) hpart[d] = fma(vj, double(fj[(d + 1) * h.Ppad]), hpart[d]);
                         }
                     }
                 }
@@ -972,10 +1100,24 @@ __global__ void __launch_bounds__(192, 1)
                 const int eq = expo_q[h.p0 + q], eb = expo_b[h.b];
                 const bool live = eq > -10000 && eb > -10000;
                 const double sc = pow2(eq + eb - n_unit<F>());
-                *n_at(s, h.m, h.p0 + q) = live ? part * sc : 0.0;
-                if (GRADN)
+                if (MODE <= 2) *n_at(s, h.m, h.p0 + q) = live ? part * sc : 0.0;
+                if (MODE == 1 || MODE == 2)
 #pragma unroll
                     for (int d = 0; d < 3; d++) *gn_at(s, h.m, h.p0 + q, d) = live ? 2.0 * gpart[d] * sc : 0.0;
+                if (MODE >= 2) {
+                    // hess: component-major (xx, xy, xz, yy, yz, zz), the system's original point order
+                    const int64_t np = s.sys.np[h.m], o = s.perm[h.p0 + q] - s.sys.poff[h.m];
+                    if (MODE == 2) {
+#pragma unroll
+                        for (int k = 0; k < 6; k++) hess[k * np + o] = live ? 2.0 * hpart[k] * sc : 0.0;
+                    } else {
+                        // pair (hc, b) of components 1..3 -> 0, 1, 2 (x.), 3, 4 (y.), 5 (zz)
+                        const int kb = (hc - 1) * 3 - ((hc - 1) * (hc - 2)) / 2 - hc;
+#pragma unroll
+                        for (int d = 0; d < 3; d++)
+                            if (d + 1 >= hc && live) hess[(kb + d + 1) * np + o] += 2.0 * hpart[d] * sc;
+                    }
+                }
             }
         }
     }
@@ -1017,6 +1159,26 @@ __global__ void wait_timeout_probe_kernel(long long max_cycles, int32_t *__restr
     }
 }
 
+// Point exponents of the Hessian's four A operands (phi and the three gradient components, rows
+// c = 0..3 of the 10-row FP64 evaluation): expo4[c n_points + batch_off[b] + q] from the binade
+// of max_i |row c of function i at point q|. One CTA per batch.
+__global__ void __launch_bounds__(256) hess_point_expo_kernel(DevSystem s, int32_t b0, const double *__restrict__ scratch,
+                                                             const int64_t *__restrict__ hoff, int32_t *__restrict__ expo4,
+                                                             int64_t n_points) {
+    const int b = b0 + blockIdx.x;
+    const int p0 = s.batch_off[b], P = s.batch_off[b + 1] - p0;
+    const int Ppad = (P + NAO_PPAD - 1) & ~(NAO_PPAD - 1);
+    const int N = s.rel_off[b + 1] - s.rel_off[b];
+    const double *E = scratch + hoff[b];
+    const int64_t ld = 10 * (int64_t)Ppad;
+    for (int idx = threadIdx.x; idx < 4 * P; idx += blockDim.x) {
+        const int c = idx / P, q = idx - c * P;
+        int mx = 0;
+        for (int i = 0; i < N; i++) mx = max(mx, split_bits::biased_exponent(abs_bits(E[i * ld + (int64_t)c * Ppad + q])));
+        expo4[c * n_points + p0 + q] = split_bits::exponent_of_binade(mx);
+    }
+}
+
 }  // namespace
 
 size_t split_smem_bytes(int S, int F) { return pipe_smem_bytes(S, F); }
@@ -1039,11 +1201,14 @@ cudaError_t split_configure() {
     size_t bytes = 0;
     for (int S = 4; S <= NAO_SPLIT_MAX_SLICES; S++) bytes = std::max(bytes, split_smem_bytes(S, NAO_DIGITS_BF16));
     for (int S = 8; S <= NAO_SPLIT_MAX_SLICES_E4M3; S++) bytes = std::max(bytes, split_smem_bytes(S, NAO_DIGITS_E4M3));
-    const void *fns[] = {(const void *)h_tc_kernel<48, 0>,        (const void *)h_tc_kernel<32, 0>,
-                         (const void *)h_tc_kernel<32, 1>,        (const void *)n_tc_kernel<48, false, 0>,
-                         (const void *)n_tc_kernel<32, false, 0>, (const void *)n_tc_kernel<48, true, 0>,
-                         (const void *)n_tc_kernel<32, true, 0>,  (const void *)n_tc_kernel<32, false, 1>,
-                         (const void *)n_tc_kernel<32, true, 1>};
+    const void *fns[] = {(const void *)h_tc_kernel<48, 0>,    (const void *)h_tc_kernel<32, 0>,
+                         (const void *)h_tc_kernel<32, 1>,    (const void *)n_tc_kernel<48, 0, 0>,
+                         (const void *)n_tc_kernel<48, 1, 0>, (const void *)n_tc_kernel<48, 2, 0>,
+                         (const void *)n_tc_kernel<48, 3, 0>, (const void *)n_tc_kernel<32, 0, 0>,
+                         (const void *)n_tc_kernel<32, 1, 0>, (const void *)n_tc_kernel<32, 2, 0>,
+                         (const void *)n_tc_kernel<32, 3, 0>, (const void *)n_tc_kernel<32, 0, 1>,
+                         (const void *)n_tc_kernel<32, 1, 1>, (const void *)n_tc_kernel<32, 2, 1>,
+                         (const void *)n_tc_kernel<32, 3, 1>};
     for (const void *f : fns) {
         const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (e != cudaSuccess) return e;
@@ -1079,12 +1244,12 @@ cudaError_t split_configure() {
         }                                                                                              \
     }
 
-cudaError_t launch_slice_h(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_rt, const double *scratch,
-                           uint32_t terms, uint8_t *slices, const int64_t *sl_off, int32_t *expo, int32_t *neg16, int S,
-                           int F, cudaStream_t st) {
+cudaError_t launch_slice_h(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_rt, const double *scratch, uint32_t terms, uint8_t *slices, const int64_t *sl_off, int32_t *expo,
+                           int32_t *neg16, int S, int F, cudaStream_t st) {
     if (b1 <= b0 || max_rt <= 0) return cudaSuccess;
+    const FF2 *ev = reinterpret_cast<const FF2 *>(scratch);  // the split path's evaluation: float-float values
 #define NAO_SLICE_H(SS, FF) \
-    slice_h_kernel<SS, FF><<<dim3(b1 - b0, max_rt), 256, 0, st>>>(s, b0, scratch, terms, slices, sl_off, expo, neg16)
+    slice_h_kernel<SS, FF><<<dim3(b1 - b0, max_rt), 256, 0, st>>>(s, b0, ev, terms, slices, sl_off, expo, neg16)
     NAO_SPLIT_DISPATCH(S, F, NAO_SLICE_H)
 #undef NAO_SLICE_H
     return cudaGetLastError();
@@ -1111,10 +1276,11 @@ cudaError_t launch_slice_n(const DevSystem &s, int32_t b0, int32_t b1, int32_t m
                            const double *scratch, uint8_t *slices, const int64_t *sl_off, const int32_t *expo_q,
                            int32_t *expo_b, const int32_t *tn_b, int S, int F, bool grad, cudaStream_t st) {
     if (b1 <= b0) return cudaSuccess;
+    const FF2 *ev = reinterpret_cast<const FF2 *>(scratch);
     // y = 0: the exponent of P'; y >= 1: 32-point tiles (128 max_qt >= P16)
-#define NAO_SLICE_NPHI(SS, FF)                                                                                    \
-    slice_nphi_kernel<SS, FF><<<dim3(b1 - b0, 4 * max_qt + 1), 256, 0, st>>>(s, b0, scratch, slices, sl_off, expo_q, \
-                                                                             expo_b, tn_b, grad ? 4 : 1, grad ? 1 : 0)
+#define NAO_SLICE_NPHI(SS, FF)                                                                            \
+    slice_nphi_kernel<SS, FF, FF2><<<dim3(b1 - b0, 4 * max_qt + 1), 256, 0, st>>>(                        \
+        s, b0, ev, s.scr_off, 0, slices, sl_off, expo_q, expo_b, tn_b, grad ? 4 : 1, grad ? 1 : 0, 1)
     NAO_SPLIT_DISPATCH(S, F, NAO_SLICE_NPHI)
 #undef NAO_SLICE_NPHI
     cudaError_t e = cudaGetLastError();
@@ -1127,23 +1293,73 @@ cudaError_t launch_slice_n(const DevSystem &s, int32_t b0, int32_t b1, int32_t m
     return cudaGetLastError();
 }
 
-cudaError_t launch_n_tc(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
-                        const int64_t *sl_off, const int32_t *expo_q, const int32_t *expo_b, const double *scratch, int S,
-                        int F, int tn, bool grad, int32_t *err, cudaStream_t st) {
+cudaError_t launch_slice_n_hess(const DevSystem &s, int32_t b0, int32_t b1, int32_t max_qt, int32_t max_rt,
+                                const double *scratch, const int64_t *hoff, int comp, uint8_t *slices,
+                                const int64_t *sl_off, const int32_t *expo_q, int32_t *expo_b, const int32_t *tn_b, int S,
+                                int F, cudaStream_t st) {
+    if (b1 <= b0) return cudaSuccess;
+    const int first = comp == 0 ? 1 : 0;  // P' (its exponent and its slices) once, with the first pass
+#define NAO_SLICE_NPHI(SS, FF)                                                                                   \
+    slice_nphi_kernel<SS, FF, double><<<dim3(b1 - b0, 4 * max_qt + 1), 256, 0, st>>>(                            \
+        s, b0, scratch, hoff, comp, slices, sl_off, expo_q, expo_b, tn_b, 10, 1, first)
+    NAO_SPLIT_DISPATCH(S, F, NAO_SLICE_NPHI)
+#undef NAO_SLICE_NPHI
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !first || max_rt <= 0) return e;
+#define NAO_SLICE_NP(SS, FF) \
+    slice_np_kernel<SS, FF><<<dim3(b1 - b0, 4 * max_rt), 256, 0, st>>>(s, b0, slices, sl_off, expo_b, tn_b, 1)
+    NAO_SPLIT_DISPATCH(S, F, NAO_SLICE_NP)
+#undef NAO_SLICE_NP
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hess_point_expo(const DevSystem &s, int32_t b0, int32_t b1, const double *scratch, const int64_t *hoff,
+                                   int32_t *expo4, int64_t n_points, cudaStream_t st) {
+    if (b1 <= b0) return cudaSuccess;
+    hess_point_expo_kernel<<<b1 - b0, 256, 0, st>>>(s, b0, scratch, hoff, expo4, n_points);
+    return cudaGetLastError();
+}
+
+// One launch of n_tc_kernel<TN, MODE, F> for the width and digit format at hand.
+static cudaError_t launch_n_tc_mode(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work,
+                                    const uint8_t *slices, const int64_t *sl_off, const int32_t *expo_q,
+                                    const int32_t *expo_b, const void *ev, const int64_t *eoff, int S, int F, int tn,
+                                    int mode, int hc, double *hess, int32_t *err, cudaStream_t st) {
     if (n_work <= 0) return cudaSuccess;
     if (F == NAO_DIGITS_E4M3 ? tn != 32 : (tn != 32 && !(tn == 48 && S <= 10))) return cudaErrorInvalidValue;
     const size_t sm = split_smem_bytes(S, F);
     const int grid = n_work < sm_count() ? n_work : sm_count();  // persistent: one CTA per SM
-#define NAO_N_TC(TNV, G, FF) \
-    n_tc_kernel<TNV, G, FF><<<grid, 192, sm, st>>>(s, work, w0, n_work, slices, sl_off, expo_q, expo_b, scratch, S, err)
-    if (F == NAO_DIGITS_E4M3 && grad) NAO_N_TC(32, true, 1);
-    else if (F == NAO_DIGITS_E4M3) NAO_N_TC(32, false, 1);
-    else if (tn == 48 && grad) NAO_N_TC(48, true, 0);
-    else if (tn == 48) NAO_N_TC(48, false, 0);
-    else if (grad) NAO_N_TC(32, true, 0);
-    else NAO_N_TC(32, false, 0);
+#define NAO_N_TC(TNV, M, FF)                                                                                  \
+    n_tc_kernel<TNV, M, FF><<<grid, 192, sm, st>>>(s, work, w0, n_work, slices, sl_off, expo_q, expo_b, ev, eoff, S, hc, \
+                                                   hess, err)
+#define NAO_N_TC_MODES(TNV, FF)             \
+    switch (mode) {                         \
+        case 0: NAO_N_TC(TNV, 0, FF); break; \
+        case 1: NAO_N_TC(TNV, 1, FF); break; \
+        case 2: NAO_N_TC(TNV, 2, FF); break; \
+        default: NAO_N_TC(TNV, 3, FF); break; \
+    }
+    if (F == NAO_DIGITS_E4M3) NAO_N_TC_MODES(32, 1)
+    else if (tn == 48) NAO_N_TC_MODES(48, 0)
+    else NAO_N_TC_MODES(32, 0)
+#undef NAO_N_TC_MODES
 #undef NAO_N_TC
     return cudaGetLastError();
+}
+
+cudaError_t launch_n_tc(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
+                        const int64_t *sl_off, const int32_t *expo_q, const int32_t *expo_b, const double *scratch, int S,
+                        int F, int tn, bool grad, int32_t *err, cudaStream_t st) {
+    return launch_n_tc_mode(s, work, w0, n_work, slices, sl_off, expo_q, expo_b, scratch, s.scr_off, S, F, tn, grad ? 1 : 0,
+                            0, nullptr, err, st);
+}
+
+cudaError_t launch_n_tc_hess(const DevSystem &s, const HWork *work, int32_t w0, int32_t n_work, const uint8_t *slices,
+                             const int64_t *sl_off, const int32_t *expo_q, const int32_t *expo_b, const double *scratch,
+                             const int64_t *hoff, int comp, double *hess, int S, int F, int tn, int32_t *err,
+                             cudaStream_t st) {
+    return launch_n_tc_mode(s, work, w0, n_work, slices, sl_off, expo_q, expo_b, scratch, hoff, S, F, tn,
+                            comp == 0 ? 2 : 3, comp, hess, err, st);
 }
 
 cudaError_t launch_wn_partial(const DevSystem &s, const DWork *work, int32_t w0, int32_t n_work, double *ne_part,

@@ -718,7 +718,7 @@ class Grid:
 
     def density_hessian(self, P, prec="fp64", n=None, grad=None, hess=None, ne=None, stream=None, want_ne=True):
         """n, grad n ([3, n_points]), the density Hessian ([6, n_points]: xx, xy, xz, yy, yz, zz)
-        and N_e of a single-system handle (FP64)."""
+        and N_e of a single-system handle ("fp64", "fp32" or "split")."""
         import torch
 
         if n is None:

@@ -160,3 +160,46 @@ def test_digit_options_are_checked(water):
         with pytest.raises(nao.NaoError) as e:
             nao.Grid(water["s"], device=0, **opts)
         assert e.value.code == nao.NAO_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("case", ["water", "molecule_l3"])
+def test_split_evaluation_matches_oracle(case):
+    """The split path evaluates the basis in float-float arithmetic on the FP32 pipe (FP64 for the
+    geometry, the radial coordinate and points within 0.1 bohr of a nucleus). Per basis function,
+    with the function's largest magnitude over the whole grid as the scale (a spline keeps
+    absolute accuracy, so where a function is tiny, near its cutoff or near its own nucleus for
+    l > 0, only the error against that scale is meaningful), every value and gradient component
+    of several batches is checked against the FP64 evaluation of the same batch on the GPU and
+    against the oracle, both at 2e-13. Float-float keeps about 47 bits: a product loses up to ~3
+    units of 2^-48 and the solid-harmonic recurrence chains ~10 of them at l = 3, so near a nodal
+    surface of an f function (value ~0, terms of the order of the function's maximum) the
+    difference reaches ~1.3e-13 of the maximum; the FP64 evaluation itself sits ~1.1e-13 from the
+    oracle on water (the oracle's radial coordinate ln(r/r0)/Delta moves steep functions by that
+    much). Both stay far below what the split path's H and n need (1e-10 of the magnitude sums)."""
+    if case == "water":
+        s, bp = synth.config_water(), 200
+    else:
+        s, bp = synth.random_molecule(5, 7311, n_rad=12, n_theta=5, n_phi=6), 120
+        assert max(s.fn_l) >= 3
+    o = oracle.Oracle(s)
+    aphi, agrad = o.eval_dense(s.pt_xyz)
+    fscale = np.maximum(np.abs(aphi).max(axis=0), 1e-300)[:, None]           # [nb, 1]
+    gfscale = np.maximum(np.abs(agrad).max(axis=(0, 2)), 1e-300)[None, :, None]  # [1, nb, 1]
+    with nao.Grid(s, device=0, max_batch_points=bp) as g:
+        bo, pp, ro, ri = g.batches()
+        nonempty = np.nonzero(np.diff(ro))[0]
+        w_or = w_64 = 0.0
+        for b in nonempty[:: max(1, len(nonempty) // 12)]:
+            b = int(b)
+            pts = s.pt_xyz[pp[bo[b]:bo[b + 1]]]
+            rphi, rgrad = o.eval_dense(pts)
+            rel = ri[ro[b]:ro[b + 1]]
+            rphi = rphi[:, rel].T
+            rgrad = np.transpose(rgrad[:, rel, :], (2, 1, 0))
+            phi, grad = (t.cpu().numpy() for t in g.evaluate_batch(b, prec="split"))
+            phi64, grad64 = (t.cpu().numpy() for t in g.evaluate_batch(b, prec="fp64"))
+            scale, gscale = fscale[rel], gfscale[:, rel]
+            w_or = max(w_or, float(np.max(np.abs(phi - rphi) / scale)), float(np.max(np.abs(grad - rgrad) / gscale)))
+            w_64 = max(w_64, float(np.max(np.abs(phi - phi64) / scale)), float(np.max(np.abs(grad - grad64) / gscale)))
+        print(f"{case}: split evaluation, worst {w_64:.2e} against the GPU's FP64 evaluation, {w_or:.2e} against the oracle")
+        assert w_64 <= 2e-13 and w_or <= 2e-13

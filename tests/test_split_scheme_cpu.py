@@ -139,3 +139,50 @@ def test_split_density_error_per_slice_count():
     for S in (4, 6):
         assert err[S] / max(err[S + 2], 1e-300) > 500.0
     assert err[10] <= 1e-10
+
+
+def _rint_small(y):
+    # rint of |y| < 2^22 by adding and subtracting 1.5 2^23 in FP32 (the kernels' rounding)
+    c = np.float32(12582912.0)
+    return np.float32(np.float32(y + c) - c)
+
+
+def _part_chunks(P, CB):
+    """The slicers' top-down FP32 chunking of one scaled part P (an FP32 value): q_c =
+    rint(R 2^-(c CB)), R <- R - q_c 2^(c CB) for c = 3, 2, 1, then u_0 = rint(R). The FMA
+    R - q 2^(c CB) is emulated in FP64, where it is exact, then rounded to FP32."""
+    R = np.float32(P)
+    out = [0.0] * 4
+    for c in (3, 2, 1):
+        q = _rint_small(np.float32(R * np.float32(2.0 ** (-c * CB))))
+        R = np.float32(np.float64(R) - np.float64(q) * 2.0 ** (c * CB))
+        out[c] = q
+    out[0] = _rint_small(R)
+    return out
+
+
+@pytest.mark.parametrize("B,S", [(5, 8), (5, 14), (5, 16), (6, 4), (6, 10), (6, 12)])
+def test_float_float_chunks_are_exact(B, S):
+    """Digits of a float-float value x = h + l (the split path's evaluation) come from balanced
+    CB-bit chunks of round(h 2^(BS-e)) + round(l 2^(BS-e)), formed in FP32 without integer
+    arithmetic: every chunk is an exact integer of at most 2^CB in magnitude and the chunks sum
+    exactly to that integer (checked against Python's exact integers, ties aside), for values
+    spread over 60 binades below the row's bound |x 2^-e| < 1/2."""
+    from fractions import Fraction
+
+    rng = np.random.default_rng(B * 100 + S)
+    D = 3 if B == 6 else 4
+    CB, BS = D * B, B * S
+    for _ in range(3000):
+        e = int(rng.integers(-60, 60))
+        x = rng.uniform(-0.5, 0.5) * 2.0 ** (-int(rng.integers(0, 60))) * 2.0 ** e
+        h = np.float32(x)
+        lo = np.float32(x - np.float64(h))
+        H = np.float32(np.float64(h) * 2.0 ** (BS - e))
+        L = np.float32(np.float64(lo) * 2.0 ** (BS - e))
+        u = [a + b for a, b in zip(_part_chunks(H, CB), _part_chunks(L, CB))]
+        assert all(float(c) == int(c) and abs(c) <= 2 ** CB for c in u)
+        X = sum(int(u[c]) << (c * CB) if u[c] >= 0 else -((-int(u[c])) << (c * CB)) for c in range(4))
+        ref = round(Fraction(float(H))) + round(Fraction(float(L)))
+        assert abs(X - ref) <= 1
+        assert abs(X) < 2 ** (BS - 1) + 2
