@@ -641,6 +641,32 @@ __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
 // row each) read an item's accumulators into registers, hand tensor memory back to the MMA warp
 // ("acc_empty") and then scatter into H while the next item's MMAs run, so the scatter, the
 // tensor-memory reads and the next item's first loads overlap the MMAs.
+// The B tiles t = 0 .. nb-1 of one A slice as MMA pieces: one piece of nb TN columns up to
+// N = 256, else two halves of ceil(nb / 2) and floor(nb / 2) tiles (each at most 256 columns,
+// since nb TN <= 512, the tensor memory of one accumulator set). Every piece starts on a whole
+// tile, so on a multiple of 8 rows (one 128-byte swizzle atom). Two halves, issued alternately,
+// write disjoint accumulator columns: an MMA that accumulates into the columns of the one just
+// issued waits for it (about 97 cycles at this size, against about 60 for other columns), and
+// equal halves leave no narrow piece whose fixed cost exceeds its work.
+struct MmaPieces {
+    int n, c0[2], cols[2];
+    __device__ __forceinline__ MmaPieces(int nb, int TN) {
+        if (nb * TN <= 256) {
+            n = 1;
+            c0[0] = 0;
+            cols[0] = nb * TN;
+            c0[1] = cols[1] = 0;
+        } else {
+            const int h = (nb + 1) / 2;
+            n = 2;
+            c0[0] = 0;
+            cols[0] = h * TN;
+            c0[1] = h * TN;
+            cols[1] = (nb - h) * TN;
+        }
+    }
+};
+
 struct PPipe {
     uint64_t fullA[kMaxRing], emptyA[kMaxRing], fullB[2], emptyB[2];
     uint64_t acc_full, acc_empty, fin;
@@ -773,17 +799,19 @@ __global__ void __launch_bounds__(192, 1)
                         if (!tc::mbar_wait(&pp.fullA[a], ua & 1, kWaitCycles)) { *abort = 1; break; }
                         tc::fence_after_sync();
                         const uint64_t ad = tc::sdesc_sw128(tc::smem_addr(sA + (size_t)a * 16384));
-                        // pairs (sa, t = 0 .. S-1-sa): one MMA per 16-column K step (two above N = 256)
-                        const int ncols = TN * (S - sa);
-                        for (int n0 = 0; n0 < ncols; n0 += 256) {
-                            const int nn = ncols - n0 < 256 ? ncols - n0 : 256;
-                            const uint32_t idesc = tc::idesc_digits<F>(128, nn);
-                            const uint64_t bd = tc::sdesc_sw128(tc::smem_addr(bset + (size_t)n0 * 128));
-                            const uint32_t dt = tm + (uint32_t)(sa * TN + n0);
+                        // pairs (sa, t = 0 .. S-1-sa): one MMA per K step over the S - sa B tiles,
+                        // or two halves of them above N = 256 (mma_pieces), issued K step by K
+                        // step so that consecutive MMAs alternate between the halves' columns
+                        const MmaPieces pc(S - sa, TN);
 #pragma unroll
-                            for (int ks = 0; ks < 4; ks++) {
-                                const uint32_t id = (kc * 4 + ks < h.neg16) ? (idesc | (1u << 14)) : idesc;
-                                tc::mma_digits<F>(dt, ad + 2 * ks, bd + 2 * ks, id, (first | sa | ks) ? 1u : 0u);
+                        for (int ks = 0; ks < 4; ks++) {
+                            const bool neg = kc * 4 + ks < h.neg16;
+                            const uint32_t acc = (first | sa | ks) ? 1u : 0u;
+                            for (int p = 0; p < pc.n; p++) {
+                                const uint32_t idesc = tc::idesc_digits<F>(128, pc.cols[p]);
+                                const uint64_t bd = tc::sdesc_sw128(tc::smem_addr(bset + (size_t)pc.c0[p] * 128));
+                                tc::mma_digits<F>(tm + (uint32_t)(sa * TN + pc.c0[p]), ad + 2 * ks, bd + 2 * ks,
+                                                  neg ? (idesc | (1u << 14)) : idesc, acc);
                             }
                         }
                         tc::mma_commit(&pp.emptyA[a]);
@@ -1012,16 +1040,17 @@ __global__ void __launch_bounds__(192, 1)
                             if (!tc::mbar_wait(&pp.fullA[a], ua & 1, kWaitCycles)) { *abort = 1; break; }
                             tc::fence_after_sync();
                             const uint64_t ad = tc::sdesc_sw128(tc::smem_addr(sA + (size_t)a * 16384));
-                            // pairs (sa, t = 0 .. S-1-sa): one MMA per 16-column K step (two above N = 256)
-                            const int ncols = TN * (S - sa);
-                            for (int n0 = 0; n0 < ncols; n0 += 256) {
-                                const int nn = ncols - n0 < 256 ? ncols - n0 : 256;
-                                const uint32_t idesc = tc::idesc_digits<F>(128, nn);
-                                const uint64_t bd = tc::sdesc_sw128(tc::smem_addr(bset + (size_t)n0 * 128));
-                                const uint32_t dt = tm + (uint32_t)(sa * TN + n0);
+                            // pairs (sa, t = 0 .. S-1-sa), issued as in h_tc_kernel
+                            const MmaPieces pc(S - sa, TN);
 #pragma unroll
-                                for (int ks = 0; ks < 4; ks++)
-                                    tc::mma_digits<F>(dt, ad + 2 * ks, bd + 2 * ks, idesc, (kc | sa | ks) ? 1u : 0u);
+                            for (int ks = 0; ks < 4; ks++) {
+                                const uint32_t acc = (kc | sa | ks) ? 1u : 0u;
+                                for (int p = 0; p < pc.n; p++) {
+                                    const uint32_t idesc = tc::idesc_digits<F>(128, pc.cols[p]);
+                                    const uint64_t bd = tc::sdesc_sw128(tc::smem_addr(bset + (size_t)pc.c0[p] * 128));
+                                    tc::mma_digits<F>(tm + (uint32_t)(sa * TN + pc.c0[p]), ad + 2 * ks, bd + 2 * ks, idesc,
+                                                      acc);
+                                }
                             }
                             tc::mma_commit(&pp.emptyA[a]);
                         }
