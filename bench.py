@@ -217,12 +217,19 @@ def serving(n_requests: int, device: int, fp64_requests: int) -> dict:
 
 # DRAM bytes per algorithmic FLOP_H of the dominant kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum over the captured launches / their FLOP_H): the
-# split H contraction on the full 64-atom workload (both tile widths, 2 timed steps), the FP64
-# contraction on the 8-atom profiling case (a launch's traffic grows with tiles x K, i.e. with
+# FP64 contraction on the 8-atom profiling case (a launch's traffic grows with tiles x K, i.e. with
 # FLOP_H). Valid only for the kernel version and slice count the capture was taken with.
 TRAFFIC_PER_FLOP_H = {
-    (1, "h_split", 10): (24.984e9 / (2 * 9.1321260e10), "profiles/traffic_diamond64_split.md"),
     (1, "h_fp64", 0): ((359.834112e6 + 3.945472e6) / 4.6096304e9, "profiles/h_simt_kernel_diamond8_fp64.md"),
+}
+# DRAM bytes per issued tensor FLOP of the split H contraction, from one ncu capture of one launch
+# of the 125-atom slab (the first five layers of the 375-atom workload, the same batch shapes):
+# dram__bytes_read.sum + dram__bytes_write.sum over sm__ops_path_tensor_op_utcqmma_src_fp8_dst_fp32
+# (the slices are read from DRAM once and re-read from L2, so the traffic grows with the tiles
+# issued). Scaled by the issued FLOP of this run's average launch. Valid only for the kernel
+# version, digit format and slice count the capture was taken with (e4m3, 14 slices).
+TRAFFIC_PER_ISSUED_FLOP = {
+    (2, "h_split", 14): ((1.044792e9 + 5.37984e6) / 2.6126843904e12, "profiles/h_tc_kernel_slab125_e4m3.md"),
 }
 
 
@@ -645,6 +652,13 @@ def main():
                 roofline["issued_tflops"] = roofline["achieved"] * issued / useful
             except Exception as e:  # reported, never fatal
                 roofline["useful_area_frac"] = f"unavailable: {type(e).__name__}: {e}"
+            if tk in TRAFFIC_PER_ISSUED_FLOP and isinstance(roofline.get("issued_tflops"), float) and digits == "e4m3":
+                per_flop, src = TRAFFIC_PER_ISSUED_FLOP[tk]
+                issued_per_launch = roofline["issued_tflops"] * 1e12 * roofline["avg_launch_ms"] / 1e3
+                roofline["traffic"] = per_flop * issued_per_launch
+                roofline["traffic_unit"] = "bytes per launch"
+                roofline["traffic_source"] = (src + " (DRAM bytes per issued tensor FLOP of one 125-atom slab launch "
+                                              "x this run's issued FLOP per launch)")
 
     line = {
         "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
