@@ -186,3 +186,65 @@ def test_float_float_chunks_are_exact(B, S):
         ref = round(Fraction(float(H))) + round(Fraction(float(L)))
         assert abs(X - ref) <= 1
         assert abs(X) < 2 ** (BS - 1) + 2
+
+
+def _split_general(X, Y, S):
+    """Emulated split product X Y^T with one exponent per row of X and per row of Y (no sign
+    flips: the weights sit in Y), base-64 digits, the pairs s + t < S."""
+    def digits(M):
+        mx = np.abs(M).max(axis=1)
+        e = np.array([_exponent(m) for m in mx], dtype=np.int64)
+        r = M * np.exp2(-e.astype(np.float64))[:, None]
+        out = []
+        for _ in range(S):
+            t = r * 64.0
+            d = np.rint(t)
+            out.append(d)
+            r = t - d
+        return out, e
+
+    dx, ex = digits(X)
+    dy, ey = digits(Y)
+    acc = np.zeros((X.shape[0], Y.shape[0]))
+    for s in range(S):
+        for t in range(S - s):
+            acc += (dx[s] @ dy[t].T) * 2.0 ** (-6 * (s + t + 2))
+    return acc * np.exp2((ex[:, None] + ey[None, :]).astype(np.float64))
+
+
+def test_split_pulay_products_per_slice_count():
+    """The local Pulay matrix elements as split products (the split path's next step, no kernel
+    yet): M^c = (d_c Phi)^T W (-1/2 lap + v) Phi and S^c = (d_c Phi)^T W Phi per batch, with
+    separate digit sets for the two operands (the products are not symmetric) and one exponent
+    per operand row. On water the error against the oracle's matrices, measured against their
+    magnitude sums, falls about 64^2 per two slices, as for H, and 10 slices meet 1e-10."""
+    s = synth.config_water()
+    o = Oracle(s)
+    v = s.potential()
+    Mref, Sref, AM, AS = o.pulay_matrices(s.pt_xyz, s.pt_w, v)
+    off, perm = Oracle.partition(s.pt_xyz, 200)
+    ro, ri = o.relevance(s.pt_xyz, off, perm)
+    nb = s.n_basis
+    emuM = {S: np.zeros((3, nb, nb)) for S in (6, 8, 10)}
+    emuS = {S: np.zeros((3, nb, nb)) for S in (6, 8, 10)}
+    for b in range(len(off) - 1):
+        rel = ri[ro[b]:ro[b + 1]]
+        if len(rel) == 0:
+            continue
+        idx = perm[off[b]:off[b + 1]]
+        phi, grad, hess = o.eval_dense2(s.pt_xyz[idx])
+        lap = hess[:, :, 0] + hess[:, :, 3] + hess[:, :, 5]
+        w = s.pt_w[idx][:, None]
+        hphi = (w * (-0.5 * lap[:, rel] + v[idx][:, None] * phi[:, rel])).T   # [N, P]
+        wphi = (w * phi[:, rel]).T
+        ix = np.ix_(rel, rel)
+        for c in range(3):
+            A = grad[:, rel, c].T
+            for S in emuM:
+                emuM[S][c][ix] += _split_general(A, hphi, S)
+                emuS[S][c][ix] += _split_general(A, wphi, S)
+    err = {S: max(rel_err(emuM[S], Mref, AM), rel_err(emuS[S], Sref, AS)) for S in emuM}
+    print({S: f"{e:.2e}" for S, e in err.items()})
+    assert err[6] > 1e-12
+    assert err[6] / max(err[8], 1e-300) > 500.0
+    assert err[10] <= 1e-10
