@@ -7,7 +7,8 @@ slice products D_s D_t^T are summed exactly for s + t < S (the pairs with s + t 
 weight below 64^-S and are dropped); negative weights flip the sign of the B operand's columns.
 
 The density's T = Phi P is split the same way with one exponent per point (row of Phi) and
-one per batch (its block of P).
+one per batch (its block of P); the local Pulay matrix elements, for which no kernel exists yet,
+as a non-symmetric product with one exponent per row of each operand.
 
 The emulation takes the oracle's basis functions, so it checks the scheme and the tolerance the
 split path is held to, not the kernels (the GPU tests do that): the error against the FP64
