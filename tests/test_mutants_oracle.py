@@ -218,7 +218,9 @@ def _run_mutant(src, m):
     c_path.write_text(src.replace(old, new, 1))
     subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
                     "-D_DEFAULT_SOURCE", str(c_path), "-o", str(so_path), "-lm"], check=True, capture_output=True)
-    env = dict(os.environ, NAO_ORACLE_LIB=str(so_path), PYTHONDONTWRITEBYTECODE="1")
+    # one BLAS thread per run: the runs themselves go in parallel, one per core
+    env = dict(os.environ, NAO_ORACLE_LIB=str(so_path), PYTHONDONTWRITEBYTECODE="1", OMP_NUM_THREADS="1",
+               OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-rf", "-p", "no:cacheprovider", "-m", "not gpu", *PINS],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     failed = set(re.findall(r"^FAILED \S+?::(\w+)", r.stdout, flags=re.M))
