@@ -55,9 +55,11 @@ typedef enum {
  *   NAO_FP64  : FP64 everywhere.
  *   NAO_FP32  : basis functions and contractions in FP32 (FP64 inside 0.1 bohr of a
  *               nucleus), per-batch results accumulated into H / n in FP64.
- *   NAO_SPLIT : FP64 basis functions cut into bf16 integer slices (Ozaki splitting);
- *               the slice products run on the tcgen05 tensor cores with exact FP32
- *               accumulation and are recombined in FP64.                                 */
+ *   NAO_SPLIT : basis functions evaluated in float-float arithmetic (about 48 significant
+ *               bits; FP64 inside 0.1 bohr of a nucleus and for l >= 5), cut into integer
+ *               slices (Ozaki splitting; bf16 or e4m3 digits, options.split_digits); the
+ *               slice products run on the tcgen05 tensor cores with exact FP32 accumulation
+ *               and are recombined as 64-bit integers, then scaled into FP64.            */
 typedef enum { NAO_FP64 = 0, NAO_FP32 = 1, NAO_SPLIT = 2 } nao_precision;
 
 /* Terms of nao_integrate_h. The overlap s_ij (Eq. OverlapNoPeriodic) is
@@ -91,7 +93,7 @@ typedef struct {
 typedef struct {
     int32_t max_batch_points; /* target batch size B (Sec. 3.3.1; the paper uses 200 on GPUs); default 200 */
     int32_t split_slices;     /* slices per operand on the NAO_SPLIT path: 4..12 with bf16 digits
-                                 (default 12), 4..16 with e4m3 digits (split_digits). Each bf16
+                                 (default 12), 8..16 with e4m3 digits (split_digits). Each bf16
                                  slice adds 6 bits and each e4m3 slice 5: the error of an element
                                  falls about 64x (32x) per slice (measured e_H on an 8-atom cell
                                  with 20 radial shells: 1.6e-9 at 10, 4.6e-11 at 11, 8.6e-13 at 12
